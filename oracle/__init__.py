@@ -1,0 +1,373 @@
+"""FP64 CPU oracle of the CR-Solver hot path (test infrastructure only).
+
+This package wraps ``cr_oracle.cpp`` (plain C++17, double precision, complex-step derivatives)
+through ctypes. It is the slow reference the CUDA library is checked against: only the tests, the
+smoke check and the CPU-baseline leg of the benchmark may import it. It shares no code with the
+CUDA path, and the CUDA path never imports it.
+
+Arrays here are row-major "array of structures": states ``u[B][d]`` with ``d = 3 n`` and the
+tendons of segment i at ``u[:, 3 i : 3 i + 3]``; targets ``[P][7]`` = position then unit
+quaternion (w, x, y, z) for full-pose IK, or position then tip axis (and a zero) for 5-DoF IK;
+spheres ``[N_o][4]`` = centre then radius.
+
+Functions with no independent pin say "parity unpinned" in their docstring.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cr_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libcr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAXSEG = 8
+IK6, IK5 = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (FP64, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-pthread",
+               _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Robot(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nb", C.c_int32), ("pad", C.c_int32),
+                ("L", C.c_double * MAXSEG), ("rc", C.c_double * MAXSEG),
+                ("umax", C.c_double * MAXSEG), ("thmax", C.c_double * MAXSEG),
+                ("rbody", C.c_double)]
+
+
+class Weights(C.Structure):
+    _fields_ = [(k, C.c_double) for k in
+                ("wp", "wR", "rho_b", "rho_eq", "rho_k", "rho_c", "w_s", "w_len", "rho_v",
+                 "rho_a", "dt", "vmax", "amax", "delta")]
+
+
+class IkParams(C.Structure):
+    _fields_ = [("S", C.c_int32), ("n_final", C.c_int32), ("k_init", C.c_int32),
+                ("k_final", C.c_int32), ("lambda0", C.c_double), ("alpha0", C.c_double),
+                ("dedup_eps", C.c_double), ("lim_tol", C.c_double), ("pos_tol", C.c_double),
+                ("rot_tol", C.c_double), ("seed", C.c_uint64), ("p0", C.c_int64)]
+
+
+def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3) -> Robot:
+    n = len(L)
+    r = Robot()
+    r.n, r.m, r.nb, r.pad = n, m, nb, 0
+    rc = list(rc) if np.ndim(rc) else [rc] * n
+    umax = list(umax) if np.ndim(umax) else [umax] * n
+    thmax = [np.pi] * n if thmax is None else (list(thmax) if np.ndim(thmax) else [thmax] * n)
+    for i in range(n):
+        r.L[i], r.rc[i], r.umax[i], r.thmax[i] = L[i], rc[i], umax[i], thmax[i]
+    r.rbody = rc[0] if rbody is None else rbody
+    return r
+
+
+def make_weights(**kw) -> Weights:
+    w = Weights()
+    for f, _ in Weights._fields_:
+        setattr(w, f, float(kw[f]))
+    return w
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            L.orc_splitmix64_at.restype = C.c_uint64
+            L.orc_splitmix64_at.argtypes = [C.c_uint64, C.c_uint64]
+        return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _threads(threads):
+    return os.cpu_count() if threads is None else threads
+
+
+def fk(robot: Robot, u, backbone: bool = False):
+    """Forward kinematics (Eq. 1-3 chained). Returns (T[B,12], backbone[B, n*nb, 3] or None)."""
+    u = _f64(u)
+    B = u.shape[0]
+    T = np.zeros((B, 12))
+    bb = np.zeros((B, robot.n * robot.nb, 3)) if backbone else None
+    lib().orc_fk(C.byref(robot), _dp(u), C.c_int64(B), _dp(T), _dp(bb))
+    return T, bb
+
+
+def fk_rodrigues(robot: Robot, u):
+    """Forward kinematics through the Rodrigues form of Eq. 2-3 (no backbone)."""
+    u = _f64(u)
+    T = np.zeros((u.shape[0], 12))
+    lib().orc_fk_rodrigues(C.byref(robot), _dp(u), C.c_int64(u.shape[0]), _dp(T))
+    return T
+
+
+def bend(robot: Robot, u):
+    """(theta_i, phi_i) of every segment from the inverse of Eq. 4: [B, n, 2]."""
+    u = _f64(u)
+    out = np.zeros((u.shape[0], robot.n, 2))
+    lib().orc_bend(C.byref(robot), _dp(u), C.c_int64(u.shape[0]), _dp(out))
+    return out
+
+
+def tendon_lengths(rc, L, theta, phi, m=3):
+    """Eq. 4: l_j = L - r_c theta cos(alpha_j - phi), j = 1..m."""
+    out = np.zeros(m)
+    lib().orc_tendon_lengths(C.c_double(rc), C.c_double(L), C.c_double(theta), C.c_double(phi),
+                             C.c_int(m), _dp(out))
+    return out
+
+
+def tip_jacobian(robot: Robot, u):
+    """Tip Jacobian [B, 6, d] by complex step: d p/d u and world angular velocity per du."""
+    u = _f64(u)
+    d = robot.n * robot.m
+    J = np.zeros((u.shape[0], 6, d))
+    lib().orc_tip_jacobian(C.byref(robot), _dp(u), C.c_int64(u.shape[0]), _dp(J))
+    return J
+
+
+def so3_log(E):
+    E = _f64(E).reshape(-1, 9)
+    w = np.zeros((E.shape[0], 3))
+    lib().orc_so3_log(_dp(E), C.c_int64(E.shape[0]), _dp(w))
+    return w
+
+
+def quat_to_R(q):
+    q = _f64(q).reshape(-1, 4)
+    R = np.zeros((q.shape[0], 9))
+    lib().orc_quat_to_R(_dp(q), C.c_int64(q.shape[0]), _dp(R))
+    return R.reshape(-1, 3, 3)
+
+
+def ik_rows(robot: Robot, n_spheres: int) -> int:
+    return lib().orc_ik_rows(C.byref(robot), C.c_int(n_spheres))
+
+
+def _spheres(spheres):
+    if spheres is None or len(spheres) == 0:
+        return 0, None
+    s = _f64(spheres).reshape(-1, 4)
+    return s.shape[0], s
+
+
+def ik_eval(robot, weights, spheres, kind, targets, S, u, want=("F",), threads=None):
+    """IK residuals / cost / collision cost / gradient / Jacobian of every seed.
+
+    ``targets[P][7]``, seed b aims at target b // S. ``want`` picks among r, F, coll, g, J.
+    """
+    no, sp = _spheres(spheres)
+    u = _f64(u)
+    tg = _f64(targets).reshape(-1, 7)
+    B, d = u.shape
+    nr = ik_rows(robot, no)
+    out = {}
+    r = np.zeros((B, nr)) if "r" in want else None
+    F = np.zeros(B) if "F" in want else None
+    coll = np.zeros(B) if "coll" in want else None
+    g = np.zeros((B, d)) if "g" in want else None
+    J = np.zeros((B, nr, d)) if "J" in want else None
+    lib().orc_ik_eval(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
+                      _dp(tg), C.c_int64(S), _dp(u), C.c_int64(B), _dp(r), _dp(F), _dp(coll),
+                      _dp(g), _dp(J), C.c_int(_threads(threads)))
+    for k, v in (("r", r), ("F", F), ("coll", coll), ("g", g), ("J", J)):
+        if v is not None:
+            out[k] = v
+    return out
+
+
+def ik_param_grad(robot, weights, spheres, kind, targets, S, u):
+    """d(sum_b F_b)/d(L_1..n, r_c,1..n) by complex step: [2n]."""
+    no, sp = _spheres(spheres)
+    u = _f64(u)
+    tg = _f64(targets).reshape(-1, 7)
+    out = np.zeros(2 * robot.n)
+    lib().orc_ik_param_grad(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
+                            _dp(tg), C.c_int64(S), _dp(u), C.c_int64(u.shape[0]), _dp(out))
+    return out
+
+
+def ik_lm(robot, weights, spheres, kind, targets, S, u0, iters, lambda0=1e-3, history=False,
+          threads=None):
+    """Run ``iters`` LM iterations per seed. Returns dict u, lam, nu, F, acc[, hist]."""
+    no, sp = _spheres(spheres)
+    u = _f64(u0).copy()
+    tg = _f64(targets).reshape(-1, 7)
+    B, d = u.shape
+    lam = np.full(B, lambda0)
+    nu = np.full(B, 2.0)
+    F = np.zeros(B)
+    acc = np.zeros((B, iters), dtype=np.uint8)
+    hist = np.zeros((iters, B, d)) if history else None
+    lib().orc_ik_lm(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg),
+                    C.c_int64(S), _dp(u), C.c_int64(B), C.c_int(iters), _dp(lam), _dp(nu), _dp(F),
+                    _dp(hist), acc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                    C.c_int(_threads(threads)))
+    out = dict(u=u, lam=lam, nu=nu, F=F, acc=acc)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+def lm_linear(A, y, x0, iters, lambda0=1e-3):
+    A = _f64(A)
+    y = _f64(y)
+    x = _f64(x0).copy()
+    lam = C.c_double(lambda0)
+    nu = C.c_double(2.0)
+    F = C.c_double(0.0)
+    lib().orc_lm_linear(_dp(A), _dp(y), C.c_int(A.shape[0]), C.c_int(A.shape[1]), _dp(x),
+                        C.c_int(iters), C.byref(lam), C.byref(nu), C.byref(F))
+    return x, lam.value, nu.value, F.value
+
+
+def cholesky(A):
+    A = _f64(A)
+    Lm = np.zeros_like(A)
+    rc = lib().orc_cholesky(C.c_int(A.shape[0]), _dp(A), _dp(Lm))
+    return (Lm if rc == 0 else None)
+
+
+def project(v, b):
+    """Projection of each row of v[B][m] onto {|u_j| <= b, sum_j u_j = 0}."""
+    v = _f64(v)
+    u = np.zeros_like(v)
+    lib().orc_project(_dp(v), C.c_int64(v.shape[0]), C.c_int(v.shape[1]), C.c_double(b), _dp(u))
+    return u
+
+
+def ik_pg(robot, weights, spheres, kind, targets, S, u0, steps, alpha0, threads=None):
+    """Stage-one projected gradient on every seed. Returns (u, F)."""
+    no, sp = _spheres(spheres)
+    u = _f64(u0).copy()
+    tg = _f64(targets).reshape(-1, 7)
+    F = np.zeros(u.shape[0])
+    lib().orc_ik_pg(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg),
+                    C.c_int64(S), _dp(u), C.c_int64(u.shape[0]), C.c_int(steps),
+                    C.c_double(alpha0), _dp(F), C.c_int(_threads(threads)))
+    return u, F
+
+
+def splitmix64_at(s0: int, k: int) -> int:
+    return int(lib().orc_splitmix64_at(C.c_uint64(s0), C.c_uint64(k)))
+
+
+def seeds(robot, weights, spheres, base, p0, P, S):
+    """SampleSeeds: hexagon-uniform seeds from the counter-based generator, [P, S, d]."""
+    no, sp = _spheres(spheres)
+    d = robot.n * robot.m
+    u = np.zeros((P, S, d))
+    lib().orc_seeds(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_uint64(base),
+                    C.c_int64(p0), C.c_int64(P), C.c_int64(S), _dp(u))
+    return u
+
+
+def topk(cost, coll, u, k, dedup_eps):
+    """SelectTop of one problem on float32 keys: indices [k] (-1 where fewer candidates)."""
+    cost = np.ascontiguousarray(cost, dtype=np.float32)
+    coll = np.ascontiguousarray(coll, dtype=np.float32)
+    u = _f64(u)
+    out = np.zeros(k, dtype=np.int32)
+    lib().orc_topk(cost.ctypes.data_as(C.POINTER(C.c_float)),
+                   coll.ctypes.data_as(C.POINTER(C.c_float)), _dp(u), C.c_int64(u.shape[0]),
+                   C.c_int(u.shape[1]), C.c_int(k), C.c_double(dedup_eps),
+                   out.ctypes.data_as(C.POINTER(C.c_int32)))
+    return out
+
+
+@dataclasses.dataclass
+class IkConfig:
+    S: int = 32
+    n_final: int = 8
+    k_init: int = 0
+    k_final: int = 30
+    lambda0: float = 1e-3
+    alpha0: float = 1e-3
+    dedup_eps: float = 1e-4
+    lim_tol: float = 1e-5
+    pos_tol: float = 1e-3
+    rot_tol: float = float(np.deg2rad(1.0))
+    seed: int = 0
+    p0: int = 0
+
+    def c(self) -> IkParams:
+        p = IkParams()
+        for f, _ in IkParams._fields_:
+            setattr(p, f, getattr(self, f))
+        return p
+
+
+def solve_ik(robot, weights, spheres, kind, targets, cfg: IkConfig, threads=None, extra=False):
+    """Algorithm 1 per target. Returns dict u, F, pos, rot, success[, cand, stage1_F]."""
+    no, sp = _spheres(spheres)
+    tg = _f64(targets).reshape(-1, 7)
+    P = tg.shape[0]
+    d = robot.n * robot.m
+    u = np.zeros((P, d))
+    F = np.zeros(P)
+    pos = np.zeros(P)
+    rot = np.zeros(P)
+    suc = np.zeros(P, dtype=np.uint8)
+    cand = np.zeros((P, cfg.n_final), dtype=np.int32) if extra else None
+    s1 = np.zeros((P, cfg.S)) if extra else None
+    lib().orc_solve_ik(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
+                       _dp(tg), C.c_int64(P), C.byref(cfg.c()), _dp(u), _dp(F), _dp(pos),
+                       _dp(rot), suc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                       cand.ctypes.data_as(C.POINTER(C.c_int32)) if extra else None, _dp(s1),
+                       C.c_int(_threads(threads)))
+    out = dict(u=u, F=F, pos=pos, rot=rot, success=suc.astype(bool))
+    if extra:
+        out.update(cand=cand, stage1_F=s1)
+    return out
+
+
+def accept(robot, spheres, kind, targets, u, tol=1e-5):
+    """Final acceptance metrics: (pos err m, rot err rad, limits ok, collision-free)."""
+    no, sp = _spheres(spheres)
+    tg = _f64(targets).reshape(-1, 7)
+    u = _f64(u)
+    P = u.shape[0]
+    pos, rot = np.zeros(P), np.zeros(P)
+    lo, co = np.zeros(P, dtype=np.uint8), np.zeros(P, dtype=np.uint8)
+    lib().orc_accept(C.byref(robot), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg), _dp(u),
+                     C.c_int64(P), C.c_double(tol), _dp(pos), _dp(rot),
+                     lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return pos, rot, lo.astype(bool), co.astype(bool)
+
+
+def opcount_ik(robot, weights, spheres, kind, target, u):
+    """Algorithmic op counts of one IK state evaluation (Rodrigues form):
+    (forward flops, forward special calls, tangent flops, tangent special calls)."""
+    no, sp = _spheres(spheres)
+    out = (C.c_longlong * 4)()
+    lib().orc_opcount_ik(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
+                         _dp(_f64(target).reshape(7)), _dp(_f64(u)), out)
+    return tuple(int(x) for x in out)

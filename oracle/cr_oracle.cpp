@@ -1,0 +1,1210 @@
+// FP64 CPU oracle of the CR-Solver hot path (tendon-driven continuum robots).
+//
+// TEST INFRASTRUCTURE ONLY. This is the plain, slow, obviously-correct reference that the CUDA
+// library is checked against. It shares no code, header, table or helper with the CUDA path and
+// never includes any of its files. Only the test-suite, the smoke check and the CPU-baseline leg
+// of the benchmark load it. Product code must never call into it.
+//
+// What it computes, in the paper's order and notation:
+//   * Sec. III-A, Eq. 1-3: segment transform T_{i-1}^i = [R d; 0 1] with R = Z(phi) Y(theta) Z(-phi)
+//     and d = r [cos phi (1-cos theta), sin phi (1-cos theta), sin theta], r = L/theta, d = [0,0,L]
+//     at theta = 0 (written as its Taylor expansion about the straight configuration there).
+//   * Sec. III-B, Eq. 4: tendon length l_ij = L_i - r_c theta_i cos(alpha_j - phi_i), read per segment
+//     (each segment carries its own m tendons); the decision variable is the displacement
+//     u_ij = l_ij - L_i, and (theta_i, phi_i) follow from u_i by the exact inverse of Eq. 4.
+//   * Sec. IV-A: IK objective ||log(T_ee^-1 T_target)|| (Eq. ik_opt) read as the split residual
+//     [w_p (p_ee - p_t); w_R Log(R_t^T R_ee)], bound constraint (Eq. ik_limits), clearance
+//     constraint (Eq. ik_coll), trajectory objective and tendon velocity/acceleration limits
+//     (Eq. mp_length_only and the finite differences after it), path-following objective
+//     (Eq. constrained_mp).
+//   * Sec. IV-B, Eq. penalized_form: cost = f + rho_ineq Pi_ineq(c) + rho_eq Pi_eq(h) written as a
+//     least-squares sum 1/2 sum r^2 (Sec. VI calls it a penalised least-squares form) with
+//     squared-hinge inequality rows and plain equality rows.
+//   * Sec. IV-C: batched Levenberg-Marquardt with dense Cholesky (Marquardt diagonal scaling,
+//     gain-ratio damping update of Madsen, Nielsen and Tingleff).
+//   * Algorithm 1 (beam search IK): SampleSeeds -> ParallelOptimize(k_init) -> SelectTop(N_final) ->
+//     ParallelOptimize(k_final) -> argmin.
+//
+// Derivatives are taken by the complex-step method (Squire and Trapp 1998): for a real-analytic
+// function f, f'(x) = Im f(x + i h) / h up to O(h^2), with no subtractive cancellation, so with
+// h = 1e-30 the Jacobian is exact to rounding. Every function below is templated on its scalar so
+// that the same code runs on double, on std::complex<double> (for derivatives), and on an
+// op-counting scalar (for the algorithmic flop counts the benchmark divides by).
+//
+// Build: g++ -std=c++17 -O2 -fPIC -shared -ffp-contract=off -pthread (no -ffast-math, no SIMD
+// intrinsics; -ffp-contract=off keeps x86-64 and aarch64 results identical).
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <thread>
+#include <vector>
+
+typedef std::complex<double> cd;
+
+// ---------------------------------------------------------------------------------------------
+// Scalars: double, complex (complex step), and an op-counting scalar.
+// ---------------------------------------------------------------------------------------------
+
+// Op tally for algorithmic counts: forward ("value") flops and special-function calls, and the
+// flops / special calls of the linearised program (the tangent map, which the adjoint transposes
+// with the same number of multiply-adds). Single-threaded use only.
+struct OpTally {
+  long long f_flop, f_sfu, t_flop, t_sfu;
+};
+static OpTally g_tally = {0, 0, 0, 0};
+
+struct Cnt {
+  double v;  // value
+  bool a;    // depends on the differentiated input (tangent structurally non-zero)
+  Cnt() : v(0), a(false) {}
+  Cnt(double x) : v(x), a(false) {}
+  Cnt(double x, bool act) : v(x), a(act) {}
+};
+static inline Cnt operator+(Cnt x, Cnt y) {
+  g_tally.f_flop++;
+  if (x.a && y.a) g_tally.t_flop++;
+  return Cnt(x.v + y.v, x.a || y.a);
+}
+static inline Cnt operator-(Cnt x, Cnt y) {
+  g_tally.f_flop++;
+  if (x.a && y.a) g_tally.t_flop++;
+  return Cnt(x.v - y.v, x.a || y.a);
+}
+static inline Cnt operator-(Cnt x) { return Cnt(-x.v, x.a); }
+static inline Cnt operator*(Cnt x, Cnt y) {
+  g_tally.f_flop++;
+  if (x.a && y.a) g_tally.t_flop += 3;
+  else if (x.a || y.a) g_tally.t_flop += 1;
+  return Cnt(x.v * y.v, x.a || y.a);
+}
+static inline Cnt operator/(Cnt x, Cnt y) {
+  g_tally.f_flop++;
+  if (y.a) g_tally.t_flop += x.a ? 3 : 2;
+  else if (x.a) g_tally.t_flop += 1;
+  return Cnt(x.v / y.v, x.a || y.a);
+}
+static inline Cnt& operator+=(Cnt& x, Cnt y) { x = x + y; return x; }
+static inline Cnt& operator-=(Cnt& x, Cnt y) { x = x - y; return x; }
+static inline Cnt& operator*=(Cnt& x, Cnt y) { x = x * y; return x; }
+
+static inline double re(double x) { return x; }
+static inline double re(const cd& x) { return x.real(); }
+static inline double re(const Cnt& x) { return x.v; }
+
+static inline double Sqrt(double x) { return std::sqrt(x); }
+static inline cd Sqrt(const cd& x) { return std::sqrt(x); }
+static inline Cnt Sqrt(Cnt x) {
+  g_tally.f_sfu++;
+  if (x.a) g_tally.t_flop += 2;
+  return Cnt(std::sqrt(x.v), x.a);
+}
+static inline double Sin(double x) { return std::sin(x); }
+static inline cd Sin(const cd& x) { return std::sin(x); }
+static inline Cnt Sin(Cnt x) {
+  g_tally.f_sfu++;
+  if (x.a) { g_tally.t_sfu++; g_tally.t_flop++; }
+  return Cnt(std::sin(x.v), x.a);
+}
+static inline double Cos(double x) { return std::cos(x); }
+static inline cd Cos(const cd& x) { return std::cos(x); }
+static inline Cnt Cos(Cnt x) {
+  g_tally.f_sfu++;
+  if (x.a) { g_tally.t_sfu++; g_tally.t_flop++; }
+  return Cnt(std::cos(x.v), x.a);
+}
+static inline double Atan2(double y, double x) { return std::atan2(y, x); }
+// atan2 is not complex-analytic as a library call; its complex-step extension only needs the
+// first-order term: atan2(y, x) + i (x Im y - y Im x) / (x^2 + y^2), evaluated at the real parts.
+static inline cd Atan2(const cd& y, const cd& x) {
+  double xr = x.real(), yr = y.real();
+  double den = xr * xr + yr * yr;
+  double d = den > 0 ? (xr * y.imag() - yr * x.imag()) / den : 0.0;
+  return cd(std::atan2(yr, xr), d);
+}
+static inline Cnt Atan2(Cnt y, Cnt x) {
+  g_tally.f_sfu++;
+  if (x.a || y.a) g_tally.t_flop += 6;
+  return Cnt(std::atan2(y.v, x.v), x.a || y.a);
+}
+
+// Squared-hinge helper: max(0, x), decided on the real part (derivative 0 at exactly 0).
+template <class T> static inline T hinge(const T& x) { return re(x) > 0.0 ? x : T(0.0); }
+
+// ---------------------------------------------------------------------------------------------
+// Parameters (plain C structs, mirrored by ctypes in oracle/__init__.py)
+// ---------------------------------------------------------------------------------------------
+
+#define OR_MAXSEG 8
+
+struct OrRobot {
+  int32_t n;   // segments
+  int32_t m;   // tendons per segment (equally spaced, alpha_j = (j-1) 2 pi / m)
+  int32_t nb;  // backbone samples per segment (sample k at arc fraction k/nb, k = 1..nb)
+  int32_t pad;
+  double L[OR_MAXSEG];      // segment arc length (m)
+  double rc[OR_MAXSEG];     // tendon routing radius (m)
+  double umax[OR_MAXSEG];   // displacement bound |u_ij| <= umax_i (m)
+  double thmax[OR_MAXSEG];  // bending-angle limit (rad)
+  double rbody;             // backbone radius used by the clearance rows (m)
+};
+
+struct OrWeights {
+  double wp, wR;                         // pose residual weights (1/m, 1/rad)
+  double rho_b, rho_eq, rho_k, rho_c;    // penalty weights: bounds, sum-zero, curvature, clearance
+  double w_s, w_len, rho_v, rho_a;       // path smoothness, path length, tendon vel / acc
+  double dt, vmax, amax;                 // time step, tendon speed / acceleration limits
+  double delta;                          // safety margin of Eq. ik_coll (m)
+};
+
+enum { OR_IK6 = 0, OR_IK5 = 1 };
+
+// ---------------------------------------------------------------------------------------------
+// Kinematics (Sec. III)
+// ---------------------------------------------------------------------------------------------
+
+// Exact inverse of Eq. 4 for one segment. With u_j = l_j - L = -r_c theta cos(alpha_j - phi) and m
+// >= 3 equally spaced tendons, sum_j cos(alpha_j - phi) cos(alpha_j) = (m/2) cos(phi) and
+// sum_j cos(alpha_j - phi) sin(alpha_j) = (m/2) sin(phi). Returns tx = theta cos phi and
+// ty = theta sin phi.
+template <class T>
+static void tendon_to_bend(const T* u, int m, const T& rc, T& tx, T& ty) {
+  T sx(0.0), sy(0.0);
+  for (int j = 0; j < m; ++j) {
+    double alpha = 2.0 * M_PI * j / m;
+    sx += u[j] * T(std::cos(alpha));
+    sy += u[j] * T(std::sin(alpha));
+  }
+  T k = T(-2.0 / m) / rc;
+  tx = k * sx;
+  ty = k * sy;
+}
+
+// Eq. 4 forward: displacement of tendon j for a segment bent by (theta, phi).
+static double tendon_displacement(double rc, double theta, double phi, int j, int m) {
+  double alpha = 2.0 * M_PI * j / m;
+  return -rc * theta * std::cos(alpha - phi);
+}
+
+template <class T> static void rot_z(const T& a, T M[3][3]) {
+  T c = Cos(a), s = Sin(a);
+  M[0][0] = c;      M[0][1] = -s;     M[0][2] = T(0.0);
+  M[1][0] = s;      M[1][1] = c;      M[1][2] = T(0.0);
+  M[2][0] = T(0.0); M[2][1] = T(0.0); M[2][2] = T(1.0);
+}
+template <class T> static void rot_y(const T& a, T M[3][3]) {
+  T c = Cos(a), s = Sin(a);
+  M[0][0] = c;      M[0][1] = T(0.0); M[0][2] = s;
+  M[1][0] = T(0.0); M[1][1] = T(1.0); M[1][2] = T(0.0);
+  M[2][0] = -s;     M[2][1] = T(0.0); M[2][2] = c;
+}
+template <class T> static void matmul3(const T A[3][3], const T B[3][3], T C[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T s = A[i][0] * B[0][j];
+      s += A[i][1] * B[1][j];
+      s += A[i][2] * B[2][j];
+      C[i][j] = s;
+    }
+}
+
+// Below this theta^2 the segment uses the Taylor expansion of Eq. 2-3 about theta = 0 (the paper
+// only states d = [0,0,L] at theta = 0; phi is undefined there).
+static const double OR_SMALL_TH2 = 1e-8;
+
+// Rodrigues / series form of Eq. 2-3 in terms of (tx, ty) = theta (cos phi, sin phi):
+// R = I + s [w]x + c [w]x^2 with w = (-ty, tx, 0), s = sin(theta)/theta, c = (1-cos theta)/theta^2,
+// d = L (c tx, c ty, s). Identical to the ZYZ product; used for small theta (with the series of s
+// and c) and, with exact s and c, by the op counter as the minimal arithmetic form of Eq. 2-3.
+template <class T>
+static void segment_rodrigues(const T& tx, const T& ty, const T& L, const T& s, const T& c,
+                              T R[3][3], T d[3]) {
+  T cxy = c * tx * ty;
+  R[0][0] = T(1.0) - c * tx * tx; R[0][1] = -cxy;                 R[0][2] = s * tx;
+  R[1][0] = -cxy;                 R[1][1] = T(1.0) - c * ty * ty; R[1][2] = s * ty;
+  R[2][0] = -(s * tx);            R[2][1] = -(s * ty);            R[2][2] = T(1.0) - c * (tx * tx + ty * ty);
+  d[0] = L * c * tx;
+  d[1] = L * c * ty;
+  d[2] = L * s;
+}
+
+static bool g_count_minimal = false;  // op counting: use the minimal (Rodrigues) arithmetic form
+
+// Segment transform T_{i-1}^i of Eq. 1: rotation R (Eq. 2) and translation d (Eq. 3).
+template <class T>
+static void segment_transform(const T& tx, const T& ty, const T& L, T R[3][3], T d[3]) {
+  T th2 = tx * tx + ty * ty;
+  if (re(th2) < OR_SMALL_TH2) {
+    // Taylor series of sin(theta)/theta and (1-cos theta)/theta^2 in theta^2.
+    T s = T(1.0) - th2 / T(6.0) + th2 * th2 / T(120.0);
+    T c = T(0.5) - th2 / T(24.0) + th2 * th2 / T(720.0);
+    segment_rodrigues(tx, ty, L, s, c, R, d);
+    return;
+  }
+  T th = Sqrt(th2);
+  if (g_count_minimal) {
+    T h = th / T(2.0);
+    T sh = Sin(h), ch = Cos(h);
+    T sc = sh / h;
+    T s = sc * ch, c = T(0.5) * sc * sc;
+    segment_rodrigues(tx, ty, L, s, c, R, d);
+    return;
+  }
+  T phi = Atan2(ty, tx);
+  // Eq. 2: R = Z(phi) Y(theta) Z(-phi)
+  T Zp[3][3], Y[3][3], Zm[3][3], ZY[3][3];
+  rot_z(phi, Zp);
+  rot_y(th, Y);
+  rot_z(-phi, Zm);
+  matmul3(Zp, Y, ZY);
+  matmul3(ZY, Zm, R);
+  // Eq. 3 with r = L/theta; 1 - cos(theta) written as 2 sin^2(theta/2) (same value, no cancellation).
+  T r = L / th;
+  T sh = Sin(th / T(2.0));
+  T omc = T(2.0) * sh * sh;
+  d[0] = r * Cos(phi) * omc;
+  d[1] = r * Sin(phi) * omc;
+  d[2] = r * Sin(th);
+}
+
+// Per-segment kinematic parameters in scalar T (so that L and r_c can be differentiated).
+template <class T> struct Params {
+  T L[OR_MAXSEG];
+  T rc[OR_MAXSEG];
+};
+template <class T> static Params<T> params_of(const OrRobot& rb) {
+  Params<T> P;
+  for (int i = 0; i < rb.n; ++i) { P.L[i] = T(rb.L[i]); P.rc[i] = T(rb.rc[i]); }
+  return P;
+}
+
+// Forward kinematics by chaining Eq. 1 (T_0^n = T_0^1 T_1^2 ... T_{n-1}^n). Optionally writes the
+// base frame of every segment (Rb[i], pb[i] = frame i-1), the backbone samples and theta_i.
+template <class T> struct FkOut {
+  T R[3][3];
+  T p[3];
+  T Rb[OR_MAXSEG][3][3];
+  T pb[OR_MAXSEG][3];
+  T th2[OR_MAXSEG];
+};
+
+template <class T> struct NoDeduce { typedef T type; };
+
+template <class T>
+static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u, FkOut<T>& o,
+                               typename NoDeduce<T>::type* backbone /* [n*nb][3] or null */) {
+  T R[3][3] = {{T(1.0), T(0.0), T(0.0)}, {T(0.0), T(1.0), T(0.0)}, {T(0.0), T(0.0), T(1.0)}};
+  T p[3] = {T(0.0), T(0.0), T(0.0)};
+  for (int i = 0; i < rb.n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      o.pb[i][a] = p[a];
+      for (int b = 0; b < 3; ++b) o.Rb[i][a][b] = R[a][b];
+    }
+    T tx, ty;
+    tendon_to_bend(u + rb.m * i, rb.m, P.rc[i], tx, ty);
+    o.th2[i] = tx * tx + ty * ty;
+    if (backbone) {
+      // Backbone sample k: the arc of fraction sigma = k/nb, i.e. bending sigma*theta in the same
+      // plane phi over arc length sigma*L, placed in the segment's base frame.
+      for (int k = 1; k <= rb.nb; ++k) {
+        T sg = T((double)k / rb.nb);
+        T Rs[3][3], ds[3];
+        segment_transform(sg * tx, sg * ty, sg * P.L[i], Rs, ds);
+        T* q = backbone + 3 * (i * rb.nb + (k - 1));
+        for (int a = 0; a < 3; ++a) {
+          T s = p[a];
+          for (int b = 0; b < 3; ++b) s += R[a][b] * ds[b];
+          q[a] = s;
+        }
+      }
+    }
+    T Ri[3][3], di[3];
+    segment_transform(tx, ty, P.L[i], Ri, di);
+    T pn[3], Rn[3][3];
+    for (int a = 0; a < 3; ++a) {
+      T s = p[a];
+      for (int b = 0; b < 3; ++b) s += R[a][b] * di[b];
+      pn[a] = s;
+    }
+    matmul3(R, Ri, Rn);
+    for (int a = 0; a < 3; ++a) {
+      p[a] = pn[a];
+      for (int b = 0; b < 3; ++b) R[a][b] = Rn[a][b];
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    o.p[a] = p[a];
+    for (int b = 0; b < 3; ++b) o.R[a][b] = R[a][b];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// SO(3) logarithm and pose residual (Eq. ik_opt, Eq. error_eq)
+// ---------------------------------------------------------------------------------------------
+
+// Log: SO(3) -> so(3) as a 3-vector w = angle * axis, angle in [0, pi]. The angle is
+// atan2(|v|, (tr E - 1)/2) with v = vee(E - E^T)/2 = sin(angle) axis. Near angle 0 the factor
+// angle/sin(angle) = asin(s)/s is a series in s^2 = |v|^2 (no square root of a vanishing number).
+// Near angle pi the axis comes from the symmetric part (E + E^T)/2 = cos I + (1 - cos) n n^T,
+// with its sign chosen so that n . v >= 0 (Sola, Deray, Atchuthan 2018, Sec. on SO(3) log).
+template <class T> static void so3_log(const T E[3][3], T w[3]) {
+  T v[3] = {(E[2][1] - E[1][2]) / T(2.0), (E[0][2] - E[2][0]) / T(2.0), (E[1][0] - E[0][1]) / T(2.0)};
+  T cs = (E[0][0] + E[1][1] + E[2][2] - T(1.0)) / T(2.0);
+  T s2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  if (re(cs) > 0.0 && re(s2) < 1e-6) {
+    // asin(s)/s = 1 + s^2/6 + 3 s^4/40 + 5 s^6/112
+    T f = T(1.0) + s2 / T(6.0) + T(3.0) * s2 * s2 / T(40.0) + T(5.0) * s2 * s2 * s2 / T(112.0);
+    for (int a = 0; a < 3; ++a) w[a] = f * v[a];
+    return;
+  }
+  if (re(cs) < 0.0 && re(s2) < 1e-2) {
+    // near pi: n n^T = (S - cs I)/(1 - cs); take the column with the largest diagonal.
+    T S[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[a][b] = (E[a][b] + E[b][a]) / T(2.0);
+    int k = 0;
+    for (int a = 1; a < 3; ++a)
+      if (re(S[a][a]) > re(S[k][k])) k = a;
+    T den = T(1.0) - cs;
+    T nn_kk = (S[k][k] - cs) / den;
+    T nk = Sqrt(nn_kk);
+    T n[3];
+    for (int a = 0; a < 3; ++a) n[a] = (a == k) ? nk : (S[a][k] / den) / nk;
+    double dot = re(n[0]) * re(v[0]) + re(n[1]) * re(v[1]) + re(n[2]) * re(v[2]);
+    T sgn = T(dot < 0.0 ? -1.0 : 1.0);
+    T ang = Atan2(Sqrt(s2), cs);
+    for (int a = 0; a < 3; ++a) w[a] = sgn * ang * n[a];
+    return;
+  }
+  T sn = Sqrt(s2);
+  T ang = Atan2(sn, cs);
+  T f = ang / sn;
+  for (int a = 0; a < 3; ++a) w[a] = f * v[a];
+}
+
+// Unit quaternion (w, x, y, z) -> rotation matrix (Hamilton convention).
+static void quat_to_R(const double* q, double R[3][3]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double nrm = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= nrm; x /= nrm; y /= nrm; z /= nrm;
+  R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+  R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+  R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+// Pose residual rows (6): IK6 -> [w_p (p - p_t); w_R Log(R_t^T R)]; IK5 -> [w_p (p - p_t); w_R (z - z_t)]
+// where z is the tip axis (third column of R) and z_t the target axis.
+template <class T>
+static void pose_residual(int kind, const OrWeights& W, const double* tgt, const T R[3][3],
+                          const T p[3], T* r) {
+  for (int a = 0; a < 3; ++a) r[a] = T(W.wp) * (p[a] - T(tgt[a]));
+  if (kind == OR_IK5) {
+    double zn = std::sqrt(tgt[3] * tgt[3] + tgt[4] * tgt[4] + tgt[5] * tgt[5]);
+    for (int a = 0; a < 3; ++a) r[3 + a] = T(W.wR) * (R[a][2] - T(tgt[3 + a] / zn));
+    return;
+  }
+  double Rt[3][3];
+  quat_to_R(tgt + 3, Rt);
+  T E[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      T s = T(Rt[0][a]) * R[0][b];
+      s += T(Rt[1][a]) * R[1][b];
+      s += T(Rt[2][a]) * R[2][b];
+      E[a][b] = s;
+    }
+  T w[3];
+  so3_log(E, w);
+  for (int a = 0; a < 3; ++a) r[3 + a] = T(W.wR) * w[a];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Constraint rows (Eq. ik_limits, ik_coll; Eq. penalized_form with squared hinges)
+// ---------------------------------------------------------------------------------------------
+
+// Per-state constraint rows, appended at r; returns the number of rows.
+//   2d rows  sqrt(rho_b) max(0, u_ij - umax_i), sqrt(rho_b) max(0, -umax_i - u_ij)
+//   n rows   sqrt(rho_eq) sum_j u_ij                      (common mode is invisible to FK)
+//   n rows   sqrt(rho_k) max(0, theta_i - thmax_i)
+//   n*nb*no  sqrt(rho_c) max(0, r_s + r_body + delta - |p_ik - c_s|)   (sample-sphere pairs)
+template <class T>
+static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
+                                 const double* spheres, const T* u, const FkOut<T>& fk,
+                                 const T* backbone, T* r, T* coll_pen) {
+  int k = 0;
+  const int d = rb.n * rb.m;
+  T sb = T(std::sqrt(W.rho_b)), se = T(std::sqrt(W.rho_eq)), sk = T(std::sqrt(W.rho_k)),
+    sc = T(std::sqrt(W.rho_c));
+  for (int q = 0; q < d; ++q) {
+    int i = q / rb.m;
+    r[k++] = sb * hinge(u[q] - T(rb.umax[i]));
+    r[k++] = sb * hinge(T(-rb.umax[i]) - u[q]);
+  }
+  for (int i = 0; i < rb.n; ++i) {
+    T s(0.0);
+    for (int j = 0; j < rb.m; ++j) s += u[rb.m * i + j];
+    r[k++] = se * s;
+  }
+  for (int i = 0; i < rb.n; ++i) {
+    if (re(fk.th2[i]) > rb.thmax[i] * rb.thmax[i]) r[k++] = sk * (Sqrt(fk.th2[i]) - T(rb.thmax[i]));
+    else r[k++] = T(0.0);
+  }
+  T cp(0.0);
+  if (no > 0) {
+    for (int q = 0; q < rb.n * rb.nb; ++q) {
+      const T* x = backbone + 3 * q;
+      for (int s = 0; s < no; ++s) {
+        const double* sp = spheres + 4 * s;
+        T dx = x[0] - T(sp[0]), dy = x[1] - T(sp[1]), dz = x[2] - T(sp[2]);
+        double reach = sp[3] + rb.rbody + W.delta;
+        T dist2 = dx * dx + dy * dy + dz * dz;
+        if (re(dist2) < reach * reach) {
+          T row = sc * (T(reach) - Sqrt(dist2));
+          r[k++] = row;
+          cp += row * row;
+        } else {
+          r[k++] = T(0.0);
+        }
+      }
+    }
+  }
+  if (coll_pen) *coll_pen = cp;
+  return k;
+}
+
+static int state_constraint_count(const OrRobot& rb, int no) {
+  return 2 * rb.n * rb.m + 2 * rb.n + rb.n * rb.nb * no;
+}
+
+// Full IK residual of one seed: 6 pose rows followed by the constraint rows.
+template <class T>
+static int ik_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
+                       const double* spheres, int kind, const double* tgt, const T* u, T* r,
+                       T* coll_pen) {
+  FkOut<T> fk;
+  std::vector<T> bb(no > 0 ? 3 * rb.n * rb.nb : 0);
+  forward_kinematics(rb, P, u, fk, no > 0 ? bb.data() : nullptr);
+  pose_residual(kind, W, tgt, fk.R, fk.p, r);
+  return 6 + state_constraint_rows(rb, W, no, spheres, u, fk, no > 0 ? bb.data() : nullptr, r + 6,
+                                   coll_pen);
+}
+
+static int ik_rows(const OrRobot& rb, int no) { return 6 + state_constraint_count(rb, no); }
+
+template <class T> static T half_sq(const T* r, int m) {
+  T s(0.0);
+  for (int k = 0; k < m; ++k) s += r[k] * r[k];
+  return T(0.5) * s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Complex-step Jacobian of a residual function r(x): J[k][c] = Im r_k(x + i h e_c) / h.
+// ---------------------------------------------------------------------------------------------
+static const double CS_H = 1e-30;
+
+typedef std::function<void(const cd* x, cd* r)> CResFn;
+
+static void cs_jacobian(const CResFn& f, int nx, int nr, const double* x, double* J) {
+  std::vector<cd> xc(nx), rc(nr);
+  for (int c = 0; c < nx; ++c) {
+    for (int q = 0; q < nx; ++q) xc[q] = cd(x[q], q == c ? CS_H : 0.0);
+    f(xc.data(), rc.data());
+    for (int k = 0; k < nr; ++k) J[k * nx + c] = rc[k].imag() / CS_H;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Levenberg-Marquardt (Sec. IV-C): one iteration on a generic residual function.
+// ---------------------------------------------------------------------------------------------
+
+// Textbook Cholesky A = L L^T of a dense symmetric n x n matrix (row-major, lower part used).
+// Returns false on a non-positive pivot.
+static bool cholesky(int n, const double* A, double* Lm) {
+  for (int i = 0; i < n * n; ++i) Lm[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; ++k) s -= Lm[j * n + k] * Lm[j * n + k];
+    if (!(s > 0.0)) return false;
+    double ljj = std::sqrt(s);
+    Lm[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; ++k) t -= Lm[i * n + k] * Lm[j * n + k];
+      Lm[i * n + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+// Solve L L^T x = b.
+static void chol_solve(int n, const double* Lm, const double* b, double* x) {
+  std::vector<double> y(n);
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= Lm[i * n + k] * y[k];
+    y[i] = s / Lm[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= Lm[k * n + i] * x[k];
+    x[i] = s / Lm[i * n + i];
+  }
+}
+
+struct LmState {
+  double lambda, nu, F;
+};
+
+// One LM iteration (fixed-count schedule, no early exit):
+//  1. r, J at x; F = 1/2 |r|^2.
+//  2. A = J^T J + lambda D, D = diag(max(diag(J^T J), 1e-12)) (Marquardt scaling); g = J^T r.
+//  3. Cholesky of A; on a non-positive pivot: lambda <- lambda nu, nu <- 2 nu, x unchanged.
+//  4. delta = -A^{-1} g; gain ratio rho = (F - F(x + delta)) / (1/2 delta^T (lambda D delta - g)).
+//  5. Accept iff F(x + delta) < F: lambda <- lambda max(1/3, 1 - (2 rho - 1)^3), nu <- 2;
+//     otherwise lambda <- lambda nu, nu <- 2 nu.
+// Returns 1 if the step was accepted.
+static int lm_iteration(const std::function<void(const double*, double*)>& fr, const CResFn& fc,
+                        int nx, int nr, double* x, LmState& st) {
+  std::vector<double> r(nr), J((size_t)nr * nx), A((size_t)nx * nx), D(nx), g(nx), Lm((size_t)nx * nx),
+      delta(nx), xn(nx), rn(nr);
+  fr(x, r.data());
+  double F = 0;
+  for (int k = 0; k < nr; ++k) F += r[k] * r[k];
+  F *= 0.5;
+  st.F = F;
+  cs_jacobian(fc, nx, nr, x, J.data());
+  for (int a = 0; a < nx; ++a) {
+    double s = 0;
+    for (int k = 0; k < nr; ++k) s += J[(size_t)k * nx + a] * r[k];
+    g[a] = s;
+    for (int b = 0; b < nx; ++b) {
+      double t = 0;
+      for (int k = 0; k < nr; ++k) t += J[(size_t)k * nx + a] * J[(size_t)k * nx + b];
+      A[a * nx + b] = t;
+    }
+  }
+  for (int a = 0; a < nx; ++a) {
+    D[a] = std::max(A[a * nx + a], 1e-12);
+    A[a * nx + a] += st.lambda * D[a];
+  }
+  if (!cholesky(nx, A.data(), Lm.data())) {
+    st.lambda *= st.nu;
+    st.nu *= 2.0;
+    return 0;
+  }
+  std::vector<double> mg(nx);
+  for (int a = 0; a < nx; ++a) mg[a] = -g[a];
+  chol_solve(nx, Lm.data(), mg.data(), delta.data());
+  for (int a = 0; a < nx; ++a) xn[a] = x[a] + delta[a];
+  fr(xn.data(), rn.data());
+  double Fn = 0;
+  for (int k = 0; k < nr; ++k) Fn += rn[k] * rn[k];
+  Fn *= 0.5;
+  double pred = 0;
+  for (int a = 0; a < nx; ++a) pred += delta[a] * (st.lambda * D[a] * delta[a] - g[a]);
+  pred *= 0.5;
+  if (Fn < F) {
+    double rho = (F - Fn) / pred;
+    double t = 2.0 * rho - 1.0;
+    st.lambda *= std::max(1.0 / 3.0, 1.0 - t * t * t);
+    st.nu = 2.0;
+    for (int a = 0; a < nx; ++a) x[a] = xn[a];
+    st.F = Fn;
+    return 1;
+  }
+  st.lambda *= st.nu;
+  st.nu *= 2.0;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projection onto the feasible tendon set of one segment (stage one of Algorithm 1)
+// ---------------------------------------------------------------------------------------------
+
+// Euclidean projection of v (m values) onto {|u_j| <= b, sum_j u_j = 0}. By the KKT conditions the
+// projection is u_j = clamp(v_j - tau, -b, b) with tau the root of the non-increasing piecewise
+// linear function g(tau) = sum_j clamp(v_j - tau, -b, b). The oracle sorts the 2m breakpoints
+// v_j -/+ b, walks them until g changes sign and interpolates linearly on that piece.
+static void project_segment(const double* v, int m, double b, double* u) {
+  std::vector<double> bp;
+  for (int j = 0; j < m; ++j) { bp.push_back(v[j] - b); bp.push_back(v[j] + b); }
+  std::sort(bp.begin(), bp.end());
+  auto g = [&](double tau) {
+    double s = 0;
+    for (int j = 0; j < m; ++j) s += std::min(b, std::max(-b, v[j] - tau));
+    return s;
+  };
+  double tau = bp.back();
+  for (size_t q = 0; q + 1 < bp.size(); ++q) {
+    double g0 = g(bp[q]), g1 = g(bp[q + 1]);
+    if (g0 >= 0.0 && g1 <= 0.0) {
+      tau = (g0 == g1) ? bp[q] : bp[q] + g0 * (bp[q + 1] - bp[q]) / (g0 - g1);
+      break;
+    }
+  }
+  for (int j = 0; j < m; ++j) u[j] = std::min(b, std::max(-b, v[j] - tau));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Seeds (SampleSeeds of Algorithm 1): counter-based SplitMix64 and hexagon-uniform draws.
+// ---------------------------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the k-th output from state s0 is
+// mix(s0 + k * 0x9E3779B97F4A7C15), mix = the variant-13 finaliser of MurmurHash3.
+static uint64_t splitmix64_at(uint64_t s0, uint64_t k) {
+  uint64_t z = s0 + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+static double u01_from(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+
+// Counter of draw w (0..2) for problem p, seed s, attempt a (0..7), segment i (0..7).
+static uint64_t seed_counter(uint64_t p, uint64_t s, uint64_t a, uint64_t i, uint64_t w) {
+  return ((((p * 65536ULL + s) * 8ULL + a) * 8ULL + i) * 4ULL + w) + 1ULL;
+}
+
+// Uniform point of the hexagon {|u_j| <= b, sum u = 0} (m = 3): the hexagon with vertices
+// V_0..V_5 = (b,0,-b), (b,-b,0), (0,-b,b), (-b,0,b), (-b,b,0), (0,b,-b) in cyclic order is the
+// union of the three congruent rhombi {x V_2k + y V_2k+2 : x, y in [0,1]}, k = 0,1,2.
+static void hexagon_point(double b, double U0, double U1, double U2, double* u) {
+  static const int V[6][3] = {{1, 0, -1}, {1, -1, 0}, {0, -1, 1}, {-1, 0, 1}, {-1, 1, 0}, {0, 1, -1}};
+  int k = (int)(3.0 * U0);
+  if (k > 2) k = 2;
+  const int* A = V[2 * k];
+  const int* B = V[(2 * k + 2) % 6];
+  for (int j = 0; j < 3; ++j) {
+    double ta = A[j] == 0 ? 0.0 : (A[j] > 0 ? U1 * b : -(U1 * b));
+    double tb = B[j] == 0 ? 0.0 : (B[j] > 0 ? U2 * b : -(U2 * b));
+    u[j] = ta + tb;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batch helpers
+// ---------------------------------------------------------------------------------------------
+
+static void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& body) {
+  if (threads <= 1 || n <= 1) {
+    for (int64_t i = 0; i < n; ++i) body(i);
+    return;
+  }
+  std::vector<std::thread> pool;
+  int64_t chunk = (n + threads - 1) / threads;
+  for (int t = 0; t < threads; ++t) {
+    int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    pool.emplace_back([lo, hi, &body]() {
+      for (int64_t i = lo; i < hi; ++i) body(i);
+    });
+  }
+  for (auto& th : pool) th.join();
+}
+
+// IK residual closures for one seed.
+struct IkProblem {
+  const OrRobot* rb;
+  const OrWeights* W;
+  int no;
+  const double* spheres;
+  int kind;
+  const double* tgt;
+  int d() const { return rb->n * rb->m; }
+  int rows() const { return ik_rows(*rb, no); }
+  void res(const double* u, double* r) const {
+    Params<double> P = params_of<double>(*rb);
+    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r, (double*)nullptr);
+  }
+  void cres(const cd* u, cd* r) const {
+    Params<cd> P = params_of<cd>(*rb);
+    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r, (cd*)nullptr);
+  }
+  double cost(const double* u, double* coll) const {
+    std::vector<double> r(rows());
+    Params<double> P = params_of<double>(*rb);
+    double cp = 0;
+    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r.data(), &cp);
+    if (coll) *coll = 0.5 * cp;
+    return half_sq(r.data(), rows());
+  }
+  // gradient of the cost = J^T r
+  void grad(const double* u, double* g) const {
+    int nr = rows(), nx = d();
+    std::vector<double> r(nr), J((size_t)nr * nx);
+    res(u, r.data());
+    cs_jacobian([this](const cd* x, cd* rr) { cres(x, rr); }, nx, nr, u, J.data());
+    for (int a = 0; a < nx; ++a) {
+      double s = 0;
+      for (int k = 0; k < nr; ++k) s += J[(size_t)k * nx + a] * r[k];
+      g[a] = s;
+    }
+  }
+};
+
+// Stage-one projected-gradient rule (normalised gradient step with an adaptive length alpha):
+// trial x' = Pi(x - alpha g / |g|); accept iff F(x') < F(x), then alpha <- 1.25 alpha, else
+// alpha <- alpha / 2 and x is kept. Fixed number of steps.
+static void pg_run_one(const IkProblem& pb, double* u, int steps, double alpha0, double* F_out) {
+  const OrRobot& rb = *pb.rb;
+  int nx = pb.d();
+  std::vector<double> g(nx), x1(nx), v(nx), g1(nx);
+  double F = pb.cost(u, nullptr);
+  pb.grad(u, g.data());
+  double alpha = alpha0;
+  for (int it = 0; it < steps; ++it) {
+    double gn = 0;
+    for (int a = 0; a < nx; ++a) gn += g[a] * g[a];
+    gn = std::sqrt(gn);
+    double scale = gn > 0 ? alpha / gn : 0.0;
+    for (int a = 0; a < nx; ++a) v[a] = u[a] - scale * g[a];
+    for (int i = 0; i < rb.n; ++i) project_segment(v.data() + rb.m * i, rb.m, rb.umax[i], x1.data() + rb.m * i);
+    double F1 = pb.cost(x1.data(), nullptr);
+    if (F1 < F) {
+      pb.grad(x1.data(), g1.data());
+      for (int a = 0; a < nx; ++a) { u[a] = x1[a]; g[a] = g1[a]; }
+      F = F1;
+      alpha *= 1.25;
+    } else {
+      alpha *= 0.5;
+    }
+  }
+  if (F_out) *F_out = F;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Exported C API (row-major AoS arrays; B = batch of states)
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+int orc_version() { return 1; }
+
+// Forward kinematics: T_out[B][12] = R row-major (9) then p (3); backbone[B][n*nb][3] or null.
+int orc_fk(const OrRobot* rb, const double* u, int64_t B, double* T_out, double* backbone) {
+  int d = rb->n * rb->m;
+  Params<double> P = params_of<double>(*rb);
+  for (int64_t b = 0; b < B; ++b) {
+    FkOut<double> o;
+    forward_kinematics(*rb, P, u + d * b, o, backbone ? backbone + (size_t)3 * rb->n * rb->nb * b : nullptr);
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) T_out[12 * b + 3 * a + c] = o.R[a][c];
+    for (int a = 0; a < 3; ++a) T_out[12 * b + 9 + a] = o.p[a];
+  }
+  return 0;
+}
+
+// Same, with the minimal (Rodrigues) arithmetic form of Eq. 2-3 instead of the ZYZ product.
+int orc_fk_rodrigues(const OrRobot* rb, const double* u, int64_t B, double* T_out) {
+  g_count_minimal = true;
+  int rc = orc_fk(rb, u, B, T_out, nullptr);
+  g_count_minimal = false;
+  return rc;
+}
+
+// Tendon map: (theta, phi) of every segment, and Eq. 4 forward for round trips.
+int orc_bend(const OrRobot* rb, const double* u, int64_t B, double* theta_phi /*[B][n][2]*/) {
+  int d = rb->n * rb->m;
+  for (int64_t b = 0; b < B; ++b)
+    for (int i = 0; i < rb->n; ++i) {
+      double tx, ty;
+      tendon_to_bend(u + d * b + rb->m * i, rb->m, rb->rc[i], tx, ty);
+      theta_phi[2 * (rb->n * b + i)] = std::sqrt(tx * tx + ty * ty);
+      theta_phi[2 * (rb->n * b + i) + 1] = std::atan2(ty, tx);
+    }
+  return 0;
+}
+int orc_tendon_lengths(double rc, double L, double theta, double phi, int m, double* l_out) {
+  for (int j = 0; j < m; ++j) l_out[j] = L + tendon_displacement(rc, theta, phi, j, m);
+  return 0;
+}
+
+// Tip Jacobian [B][6][d]: rows 0-2 d p / d u, rows 3-5 the world angular velocity
+// vee(dR R^T) per unit du, by complex step on the forward kinematics.
+int orc_tip_jacobian(const OrRobot* rb, const double* u, int64_t B, double* J) {
+  int d = rb->n * rb->m;
+  Params<cd> P = params_of<cd>(*rb);
+  Params<double> Pd = params_of<double>(*rb);
+  for (int64_t b = 0; b < B; ++b) {
+    FkOut<double> o;
+    forward_kinematics(*rb, Pd, u + d * b, o, nullptr);
+    for (int c = 0; c < d; ++c) {
+      std::vector<cd> x(d);
+      for (int q = 0; q < d; ++q) x[q] = cd(u[d * b + q], q == c ? CS_H : 0.0);
+      FkOut<cd> oc;
+      forward_kinematics(*rb, P, x.data(), oc, nullptr);
+      double dR[3][3];
+      for (int a = 0; a < 3; ++a) {
+        J[(size_t)6 * d * b + a * d + c] = oc.p[a].imag() / CS_H;
+        for (int e = 0; e < 3; ++e) dR[a][e] = oc.R[a][e].imag() / CS_H;
+      }
+      double Wm[3][3];  // dR R^T
+      for (int a = 0; a < 3; ++a)
+        for (int e = 0; e < 3; ++e) {
+          double s = 0;
+          for (int k = 0; k < 3; ++k) s += dR[a][k] * o.R[e][k];
+          Wm[a][e] = s;
+        }
+      J[(size_t)6 * d * b + 3 * d + c] = 0.5 * (Wm[2][1] - Wm[1][2]);
+      J[(size_t)6 * d * b + 4 * d + c] = 0.5 * (Wm[0][2] - Wm[2][0]);
+      J[(size_t)6 * d * b + 5 * d + c] = 0.5 * (Wm[1][0] - Wm[0][1]);
+    }
+  }
+  return 0;
+}
+
+int orc_so3_log(const double* E /*[B][9]*/, int64_t B, double* w /*[B][3]*/) {
+  for (int64_t b = 0; b < B; ++b) {
+    double M[3][3];
+    for (int a = 0; a < 9; ++a) M[a / 3][a % 3] = E[9 * b + a];
+    so3_log(M, w + 3 * b);
+  }
+  return 0;
+}
+
+int orc_quat_to_R(const double* q, int64_t B, double* R /*[B][9]*/) {
+  for (int64_t b = 0; b < B; ++b) {
+    double M[3][3];
+    quat_to_R(q + 4 * b, M);
+    for (int a = 0; a < 9; ++a) R[9 * b + a] = M[a / 3][a % 3];
+  }
+  return 0;
+}
+
+int orc_ik_rows(const OrRobot* rb, int no) { return ik_rows(*rb, no); }
+
+// IK residuals r[B][rows], cost F[B], collision part of the cost coll[B] (nullable), gradient
+// g[B][d] (nullable) and residual Jacobian J[B][rows][d] (nullable). Target of seed b is
+// targets[7 * (b / S)].
+int orc_ik_eval(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+                const double* targets, int64_t S, const double* u, int64_t B, double* r, double* F,
+                double* coll, double* g, double* J, int threads) {
+  int d = rb->n * rb->m;
+  parallel_for(B, threads, [&](int64_t b) {
+    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    int nr = pb.rows();
+    std::vector<double> rr(nr);
+    pb.res(u + d * b, rr.data());
+    if (r) std::memcpy(r + (size_t)nr * b, rr.data(), sizeof(double) * nr);
+    if (F) F[b] = pb.cost(u + d * b, coll ? coll + b : nullptr);
+    else if (coll) pb.cost(u + d * b, coll + b);
+    if (g) pb.grad(u + d * b, g + (size_t)d * b);
+    if (J)
+      cs_jacobian([&pb](const cd* x, cd* rc) { pb.cres(x, rc); }, d, nr, u + d * b,
+                  J + (size_t)nr * d * b);
+  });
+  return 0;
+}
+
+// Gradient of the summed IK cost with respect to the kinematic parameters (L_i, r_c,i),
+// complex step on each parameter: grad[2n] = d/dL_1..n then d/dr_c,1..n of sum_b F_b.
+int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+                      int kind, const double* targets, int64_t S, const double* u, int64_t B,
+                      double* grad) {
+  int d = rb->n * rb->m;
+  for (int q = 0; q < 2 * rb->n; ++q) {
+    double acc = 0;
+    for (int64_t b = 0; b < B; ++b) {
+      Params<cd> P = params_of<cd>(*rb);
+      if (q < rb->n) P.L[q] += cd(0.0, CS_H);
+      else P.rc[q - rb->n] += cd(0.0, CS_H);
+      int nr = ik_rows(*rb, no);
+      std::vector<cd> x(d), r(nr);
+      for (int a = 0; a < d; ++a) x[a] = cd(u[d * b + a], 0.0);
+      ik_residual(*rb, P, *W, no, spheres, kind, targets + 7 * (b / S), x.data(), r.data(), (cd*)nullptr);
+      cd F = half_sq(r.data(), nr);
+      acc += F.imag() / CS_H;
+    }
+    grad[q] = acc;
+  }
+  return 0;
+}
+
+// Run `iters` LM iterations on each seed. u[B][d] is updated in place; hist (nullable) receives
+// the iterate after every iteration [iters][B][d]; lam/nu/F (in/out, [B]); acc[B][iters] (nullable)
+// the accept flags. lam/nu must be initialised by the caller (lambda0, 2).
+int orc_ik_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+              const double* targets, int64_t S, double* u, int64_t B, int iters, double* lam,
+              double* nu, double* F, double* hist, uint8_t* acc, int threads) {
+  int d = rb->n * rb->m;
+  parallel_for(B, threads, [&](int64_t b) {
+    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    LmState st{lam[b], nu[b], 0.0};
+    double* x = u + d * b;
+    for (int it = 0; it < iters; ++it) {
+      int a = lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
+                           [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), x, st);
+      if (acc) acc[(size_t)iters * b + it] = (uint8_t)a;
+      if (hist) std::memcpy(hist + ((size_t)it * B + b) * d, x, sizeof(double) * d);
+    }
+    lam[b] = st.lambda;
+    nu[b] = st.nu;
+    F[b] = pb.cost(x, nullptr);
+  });
+  return 0;
+}
+
+// LM on a linear residual r(x) = A x - y (A is [nr][nx]); used to pin the LM machinery.
+int orc_lm_linear(const double* A, const double* y, int nr, int nx, double* x, int iters,
+                  double* lam, double* nu, double* F) {
+  auto fr = [&](const double* xx, double* rr) {
+    for (int k = 0; k < nr; ++k) {
+      double s = -y[k];
+      for (int a = 0; a < nx; ++a) s += A[k * nx + a] * xx[a];
+      rr[k] = s;
+    }
+  };
+  auto fc = [&](const cd* xx, cd* rr) {
+    for (int k = 0; k < nr; ++k) {
+      cd s = -y[k];
+      for (int a = 0; a < nx; ++a) s += A[k * nx + a] * xx[a];
+      rr[k] = s;
+    }
+  };
+  LmState st{*lam, *nu, 0.0};
+  for (int it = 0; it < iters; ++it) lm_iteration(fr, fc, nx, nr, x, st);
+  *lam = st.lambda;
+  *nu = st.nu;
+  std::vector<double> r(nr);
+  fr(x, r.data());
+  double s = 0;
+  for (int k = 0; k < nr; ++k) s += r[k] * r[k];
+  *F = 0.5 * s;
+  return 0;
+}
+
+int orc_cholesky(int n, const double* A, double* Lm) { return cholesky(n, A, Lm) ? 0 : 1; }
+
+int orc_project(const double* v, int64_t B, int m, double b, double* u) {
+  for (int64_t q = 0; q < B; ++q) project_segment(v + m * q, m, b, u + m * q);
+  return 0;
+}
+
+// Stage-one projected gradient on every seed: u[B][d] in place, F[B] out.
+int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+              const double* targets, int64_t S, double* u, int64_t B, int steps, double alpha0,
+              double* F, int threads) {
+  int d = rb->n * rb->m;
+  parallel_for(B, threads, [&](int64_t b) {
+    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    pg_run_one(pb, u + d * b, steps, alpha0, F + b);
+  });
+  return 0;
+}
+
+uint64_t orc_splitmix64_at(uint64_t s0, uint64_t k) { return splitmix64_at(s0, k); }
+
+// Seeds of problem p (global index p0 + q): u[P][S][d]. With spheres, a seed whose backbone is
+// closer than r_s + r_body + delta to a sphere is redrawn (attempts 0..7; the last draw is kept).
+int orc_seeds(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, uint64_t base,
+              int64_t p0, int64_t P, int64_t S, double* u) {
+  int d = rb->n * rb->m;
+  Params<double> Pd = params_of<double>(*rb);
+  for (int64_t q = 0; q < P; ++q)
+    for (int64_t s = 0; s < S; ++s) {
+      double* x = u + ((size_t)q * S + s) * d;
+      for (int a = 0; a < 8; ++a) {
+        for (int i = 0; i < rb->n; ++i) {
+          double U[3];
+          for (int w = 0; w < 3; ++w)
+            U[w] = u01_from(splitmix64_at(base, seed_counter(p0 + q, s, a, i, w)));
+          hexagon_point(rb->umax[i], U[0], U[1], U[2], x + 3 * i);
+        }
+        if (no == 0) break;
+        FkOut<double> o;
+        std::vector<double> bb(3 * rb->n * rb->nb);
+        forward_kinematics(*rb, Pd, x, o, bb.data());
+        bool hit = false;
+        for (int k = 0; k < rb->n * rb->nb && !hit; ++k)
+          for (int c = 0; c < no && !hit; ++c) {
+            const double* sp = spheres + 4 * c;
+            double dx = bb[3 * k] - sp[0], dy = bb[3 * k + 1] - sp[1], dz = bb[3 * k + 2] - sp[2];
+            double reach = sp[3] + rb->rbody + W->delta;
+            if (dx * dx + dy * dy + dz * dz < reach * reach) hit = true;
+          }
+        if (!hit) break;
+      }
+    }
+  return 0;
+}
+
+// SelectTop of Algorithm 1 for one problem: candidates ranked by (cost, collision penalty, index)
+// ascending (non-finite costs last); a candidate within dedup_eps (max-norm) of an already kept
+// one is skipped; if fewer than k survive, the best skipped candidates fill the rest in rank
+// order. Keys are float32 so that both implementations decide in the same precision.
+int orc_topk(const float* cost, const float* coll, const double* u /*[S][d]*/, int64_t S, int d,
+             int k, double dedup_eps, int32_t* out) {
+  std::vector<int> idx(S);
+  for (int q = 0; q < S; ++q) idx[q] = q;
+  auto key = [&](int q) { return std::isfinite(cost[q]) ? cost[q] : INFINITY; };
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    float ka = key(a), kb = key(b);
+    if (ka != kb) return ka < kb;
+    if (coll[a] != coll[b]) return coll[a] < coll[b];
+    return a < b;
+  });
+  std::vector<int> kept, skipped;
+  for (int q : idx) {
+    if ((int)kept.size() == k) break;
+    bool dup = false;
+    for (int c : kept) {
+      double mx = 0;
+      for (int a = 0; a < d; ++a) mx = std::max(mx, std::fabs(u[(size_t)q * d + a] - u[(size_t)c * d + a]));
+      if (mx < dedup_eps) { dup = true; break; }
+    }
+    if (dup) skipped.push_back(q);
+    else kept.push_back(q);
+  }
+  for (size_t q = 0; kept.size() < (size_t)k && q < skipped.size(); ++q) kept.push_back(skipped[q]);
+  for (int q = 0; q < k; ++q) out[q] = q < (int)kept.size() ? kept[q] : -1;
+  return 0;
+}
+
+// Final acceptance of one solution: position error (m), rotation error (rad: Log angle for IK6,
+// angle between tip axes for IK5), limits (|u| <= umax + tol, |sum u| <= tol, theta <= thmax + tol)
+// and collision-free (every sample at least r_s + r_body from every sphere centre).
+static void accept_one(const OrRobot& rb, int no, const double* spheres, int kind,
+                       const double* tgt, const double* u, double tol, double* pos, double* rot,
+                       uint8_t* lim_ok, uint8_t* col_ok) {
+  Params<double> Pd = params_of<double>(rb);
+  FkOut<double> o;
+  std::vector<double> bb(3 * rb.n * rb.nb);
+  forward_kinematics(rb, Pd, u, o, bb.data());
+  double dp2 = 0;
+  for (int a = 0; a < 3; ++a) dp2 += (o.p[a] - tgt[a]) * (o.p[a] - tgt[a]);
+  *pos = std::sqrt(dp2);
+  if (kind == OR_IK5) {
+    double zn = std::sqrt(tgt[3] * tgt[3] + tgt[4] * tgt[4] + tgt[5] * tgt[5]);
+    double z[3] = {o.R[0][2], o.R[1][2], o.R[2][2]}, zt[3] = {tgt[3] / zn, tgt[4] / zn, tgt[5] / zn};
+    double cx = z[1] * zt[2] - z[2] * zt[1], cy = z[2] * zt[0] - z[0] * zt[2], cz = z[0] * zt[1] - z[1] * zt[0];
+    *rot = std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), z[0] * zt[0] + z[1] * zt[1] + z[2] * zt[2]);
+  } else {
+    double Rt[3][3], E[3][3], w[3];
+    quat_to_R(tgt + 3, Rt);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) E[a][b] = Rt[0][a] * o.R[0][b] + Rt[1][a] * o.R[1][b] + Rt[2][a] * o.R[2][b];
+    so3_log(E, w);
+    *rot = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  }
+  bool ok = true;
+  for (int i = 0; i < rb.n; ++i) {
+    double s = 0;
+    for (int j = 0; j < rb.m; ++j) {
+      double x = u[rb.m * i + j];
+      s += x;
+      if (std::fabs(x) > rb.umax[i] + tol) ok = false;
+    }
+    if (std::fabs(s) > tol) ok = false;
+    if (std::sqrt(o.th2[i]) > rb.thmax[i] + 1e-6) ok = false;
+  }
+  *lim_ok = ok;
+  bool free = true;
+  for (int k = 0; k < rb.n * rb.nb && free; ++k)
+    for (int c = 0; c < no && free; ++c) {
+      const double* sp = spheres + 4 * c;
+      double dx = bb[3 * k] - sp[0], dy = bb[3 * k + 1] - sp[1], dz = bb[3 * k + 2] - sp[2];
+      double reach = sp[3] + rb.rbody;
+      if (dx * dx + dy * dy + dz * dz < reach * reach) free = false;
+    }
+  *col_ok = free;
+}
+
+struct OrIkParams {
+  int32_t S, n_final, k_init, k_final;
+  double lambda0, alpha0, dedup_eps, lim_tol, pos_tol, rot_tol;
+  uint64_t seed;
+  int64_t p0;  // global index of the first problem (seed counter)
+};
+
+// Algorithm 1 per problem. Outputs u_out[P][d], F_out[P], pos[P], rot[P], success[P];
+// cand_out (nullable) [P][n_final] the SelectTop indices; stage1_F (nullable) [P][S].
+int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+                 const double* targets, int64_t P, const OrIkParams* prm, double* u_out,
+                 double* F_out, double* pos, double* rot, uint8_t* success, int32_t* cand_out,
+                 double* stage1_F, int threads) {
+  int d = rb->n * rb->m;
+  int S = prm->S, K = prm->n_final;
+  parallel_for(P, threads, [&](int64_t q) {
+    const double* tgt = targets + 7 * q;
+    IkProblem pb{rb, W, no, spheres, kind, tgt};
+    std::vector<double> U((size_t)S * d), F(S), C(S);
+    orc_seeds(rb, W, no, spheres, prm->seed, prm->p0 + q, 1, S, U.data());
+    // Stage one (ParallelOptimize with k_init steps): projected gradient on every seed.
+    for (int s = 0; s < S; ++s) {
+      if (prm->k_init > 0) pg_run_one(pb, U.data() + (size_t)s * d, prm->k_init, prm->alpha0, &F[s]);
+      F[s] = pb.cost(U.data() + (size_t)s * d, &C[s]);
+    }
+    if (stage1_F)
+      for (int s = 0; s < S; ++s) stage1_F[(size_t)q * S + s] = F[s];
+    // SelectTop: keys in float32.
+    std::vector<float> Ff(S), Cf(S);
+    for (int s = 0; s < S; ++s) { Ff[s] = (float)F[s]; Cf[s] = (float)C[s]; }
+    std::vector<int32_t> top(K);
+    orc_topk(Ff.data(), Cf.data(), U.data(), S, d, K, prm->dedup_eps, top.data());
+    if (cand_out)
+      for (int c = 0; c < K; ++c) cand_out[(size_t)q * K + c] = top[c];
+    // Stage two (ParallelOptimize with k_final LM iterations) and argmin of the final cost.
+    double bestF = INFINITY;
+    int best = -1;
+    std::vector<double> X((size_t)K * d);
+    for (int c = 0; c < K; ++c) {
+      double* x = X.data() + (size_t)c * d;
+      if (top[c] < 0) { for (int a = 0; a < d; ++a) x[a] = NAN; continue; }
+      std::memcpy(x, U.data() + (size_t)top[c] * d, sizeof(double) * d);
+      LmState st{prm->lambda0, 2.0, 0.0};
+      for (int it = 0; it < prm->k_final; ++it)
+        lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
+                     [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), x, st);
+      double Fc = pb.cost(x, nullptr);
+      if (Fc < bestF) { bestF = Fc; best = c; }
+    }
+    double* uo = u_out + (size_t)q * d;
+    if (best < 0) {
+      for (int a = 0; a < d; ++a) uo[a] = NAN;
+      F_out[q] = NAN; pos[q] = NAN; rot[q] = NAN; success[q] = 0;
+      return;
+    }
+    std::memcpy(uo, X.data() + (size_t)best * d, sizeof(double) * d);
+    F_out[q] = bestF;
+    uint8_t lim_ok, col_ok;
+    accept_one(*rb, no, spheres, kind, tgt, uo, prm->lim_tol, &pos[q], &rot[q], &lim_ok, &col_ok);
+    success[q] = (pos[q] <= prm->pos_tol && rot[q] <= prm->rot_tol && lim_ok && col_ok) ? 1 : 0;
+  });
+  return 0;
+}
+
+int orc_accept(const OrRobot* rb, int no, const double* spheres, int kind, const double* targets,
+               const double* u, int64_t P, double tol, double* pos, double* rot, uint8_t* lim_ok,
+               uint8_t* col_ok) {
+  int d = rb->n * rb->m;
+  for (int64_t q = 0; q < P; ++q)
+    accept_one(*rb, no, spheres, kind, targets + 7 * q, u + (size_t)d * q, tol, pos + q, rot + q,
+               lim_ok + q, col_ok + q);
+  return 0;
+}
+
+// Algorithmic op counts of one IK state evaluation in the minimal (Rodrigues) arithmetic form:
+// out[0..3] = forward flops, forward special-function calls, tangent flops, tangent special calls
+// (the tangent map of the cost w.r.t. u; a reverse sweep transposes it with the same count).
+int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+                   const double* target, const double* u, long long* out) {
+  int d = rb->n * rb->m;
+  g_count_minimal = true;
+  g_tally = {0, 0, 0, 0};
+  Params<Cnt> P;
+  for (int i = 0; i < rb->n; ++i) { P.L[i] = Cnt(rb->L[i]); P.rc[i] = Cnt(rb->rc[i]); }
+  std::vector<Cnt> x(d), r(ik_rows(*rb, no));
+  for (int a = 0; a < d; ++a) x[a] = Cnt(u[a], true);
+  ik_residual(*rb, P, *W, no, spheres, kind, target, x.data(), r.data(), (Cnt*)nullptr);
+  Cnt F = half_sq(r.data(), (int)r.size());
+  (void)F;
+  g_count_minimal = false;
+  out[0] = g_tally.f_flop;
+  out[1] = g_tally.f_sfu;
+  out[2] = g_tally.t_flop;
+  out[3] = g_tally.t_sfu;
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds workload definitions (robot geometry, penalty weights, solver settings) and
+random-number recipes only. It contains none of the method's arithmetic. Forward kinematics,
+costs and solvers live in the CUDA library and, separately, in the CPU oracle. Where an input
+needs kinematics (targets = FK of random states), the caller passes the FK function in.
+
+Recipes (all numpy PCG64, ``np.random.default_rng(seed)``):
+  * in-bound tendon states: per segment, (u_1, u_2) ~ U[-b, b]^2 and u_3 = -u_1 - u_2, redrawn
+    while |u_3| > b. This is uniform on the hexagon {|u_j| <= b, sum_j u_j = 0}, because the
+    hexagon is a linear image of the accepted part of the square.
+  * full-pose targets: FK of in-bound states, giving position plus unit quaternion (w >= 0).
+  * 5-DoF targets: position plus tip axis (the third column of R).
+  * spheres: centre uniform in a box, radius uniform in [r_lo, r_hi].
+
+The paper's benchmarks (1000 uniform IK targets, a 27-sphere lattice, shelf and cabinet scenes,
+letter-shaped paths) are replaced by these synthetic stand-ins of the same shape.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+W_P_DEFAULT = math.pi / 0.18  # 1 mm of position error weighs as much as 1 degree of rotation
+
+
+@dataclasses.dataclass(frozen=True)
+class RobotSpec:
+    L: tuple          # segment lengths (m)
+    rc: float         # tendon radius (m)
+    umax: float       # displacement bound |u| <= umax (m)
+    nb: int = 16      # backbone samples per segment
+    thmax: float = math.pi
+    rbody: float | None = None  # backbone radius for clearance (defaults to rc)
+
+    @property
+    def n(self) -> int:
+        return len(self.L)
+
+    @property
+    def d(self) -> int:
+        return 3 * len(self.L)
+
+    @property
+    def body_radius(self) -> float:
+        return self.rc if self.rbody is None else self.rbody
+
+
+@dataclasses.dataclass(frozen=True)
+class WeightSpec:
+    wp: float = W_P_DEFAULT
+    wR: float = 1.0
+    rho_b: float = 1e4
+    rho_eq: float = 1e4
+    rho_k: float = 1e4
+    rho_c: float = 1e4
+    w_s: float = 1.0
+    w_len: float = 1.0
+    rho_v: float = 1e4
+    rho_a: float = 1e4
+    dt: float = 0.05
+    vmax: float = 0.05
+    amax: float = 0.5
+    delta: float = 1e-3
+
+    def as_dict(self) -> dict:
+        return dataclasses.asdict(self)
+
+
+@dataclasses.dataclass(frozen=True)
+class IkSpec:
+    S: int                 # seeds per target
+    n_final: int           # candidates kept after stage one
+    k_init: int            # stage-one projected-gradient steps
+    k_final: int           # stage-two LM iterations
+    lambda0: float = 1e-3
+    alpha0: float = 1e-3   # first stage-one step length (m of tendon displacement)
+    dedup_eps: float = 1e-4
+    lim_tol: float = 1e-5
+    pos_tol: float = 1e-3
+    rot_tol: float = math.radians(1.0)
+    seed: int = 0
+
+
+# 1-segment, 3-tendon robot of the 5-DoF single-stage workload (256 targets, 32 seeds, 50 LM its).
+ROBOT_1SEG = RobotSpec(L=(0.10,), rc=0.005, umax=0.008)
+IK_1SEG = IkSpec(S=32, n_final=32, k_init=0, k_final=50)
+P_1SEG = 256
+
+# 3-segment, 9-tendon robot of the two-stage full-pose workload (4096 targets, 256 seeds -> 8).
+ROBOT_3SEG = RobotSpec(L=(0.12, 0.10, 0.08), rc=0.005, umax=0.010)
+IK_3SEG = IkSpec(S=256, n_final=8, k_init=64, k_final=30)
+P_3SEG = 4096
+
+WEIGHTS = WeightSpec()
+
+
+def hexagon_states(rng: np.random.Generator, count: int, n_seg: int, umax: float) -> np.ndarray:
+    """``count`` in-bound states [count, 3 n_seg], uniform on each segment's hexagon."""
+    out = np.empty((count, n_seg, 3))
+    for i in range(n_seg):
+        filled = 0
+        while filled < count:
+            k = 2 * (count - filled) + 16
+            a = rng.uniform(-umax, umax, size=(k, 2))
+            c = -a.sum(axis=1)
+            ok = np.abs(c) <= umax
+            take = min(int(ok.sum()), count - filled)
+            sel = np.nonzero(ok)[0][:take]
+            out[filled:filled + take, i, 0:2] = a[sel]
+            out[filled:filled + take, i, 2] = c[sel]
+            filled += take
+    return out.reshape(count, 3 * n_seg)
+
+
+def rotation_to_quaternion(R: np.ndarray) -> np.ndarray:
+    """Rotation matrices [N,3,3] -> unit quaternions (w, x, y, z) with w >= 0 (Shepperd)."""
+    R = np.asarray(R, dtype=np.float64).reshape(-1, 3, 3)
+    q = np.empty((R.shape[0], 4))
+    for b in range(R.shape[0]):
+        m = R[b]
+        tr = m[0, 0] + m[1, 1] + m[2, 2]
+        cands = [tr, m[0, 0], m[1, 1], m[2, 2]]
+        k = int(np.argmax(cands))
+        if k == 0:
+            s = math.sqrt(1.0 + tr) * 2
+            q[b] = [0.25 * s, (m[2, 1] - m[1, 2]) / s, (m[0, 2] - m[2, 0]) / s, (m[1, 0] - m[0, 1]) / s]
+        elif k == 1:
+            s = math.sqrt(1.0 + m[0, 0] - m[1, 1] - m[2, 2]) * 2
+            q[b] = [(m[2, 1] - m[1, 2]) / s, 0.25 * s, (m[0, 1] + m[1, 0]) / s, (m[0, 2] + m[2, 0]) / s]
+        elif k == 2:
+            s = math.sqrt(1.0 + m[1, 1] - m[0, 0] - m[2, 2]) * 2
+            q[b] = [(m[0, 2] - m[2, 0]) / s, (m[0, 1] + m[1, 0]) / s, 0.25 * s, (m[1, 2] + m[2, 1]) / s]
+        else:
+            s = math.sqrt(1.0 + m[2, 2] - m[0, 0] - m[1, 1]) * 2
+            q[b] = [(m[1, 0] - m[0, 1]) / s, (m[0, 2] + m[2, 0]) / s, (m[1, 2] + m[2, 1]) / s, 0.25 * s]
+        q[b] /= np.linalg.norm(q[b])
+        if q[b, 0] < 0:
+            q[b] = -q[b]
+    return q
+
+
+def pose_targets(T12: np.ndarray, kind: str) -> np.ndarray:
+    """Targets [P, 7] from FK output rows [P, 12] (R row-major, then p).
+
+    kind "pose": position + quaternion (w >= 0); kind "axis": position + tip axis + 0.
+    """
+    T12 = np.asarray(T12, dtype=np.float64).reshape(-1, 12)
+    R = T12[:, :9].reshape(-1, 3, 3)
+    p = T12[:, 9:12]
+    out = np.zeros((T12.shape[0], 7))
+    out[:, :3] = p
+    if kind == "pose":
+        out[:, 3:7] = rotation_to_quaternion(R)
+    elif kind == "axis":
+        out[:, 3:6] = R[:, :, 2]
+    else:
+        raise ValueError(kind)
+    return out
+
+
+def ik_workload(robot: RobotSpec, P: int, kind: str, fk, seed: int = 0):
+    """Targets for P IK problems: FK of hexagon-uniform states (seed), returns (targets, u_true).
+
+    ``fk(u[P, d]) -> T[P, 12]`` is supplied by the caller (oracle or CUDA path).
+    """
+    rng = np.random.default_rng(seed)
+    u_true = hexagon_states(rng, P, robot.n, robot.umax)
+    T = np.asarray(fk(u_true))
+    return pose_targets(T, kind), u_true
+
+
+def spheres_uniform(rng: np.random.Generator, count: int, lo, hi, r_lo: float, r_hi: float):
+    """``count`` spheres [count, 4]: centre uniform in the box [lo, hi], radius in [r_lo, r_hi]."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    c = rng.uniform(lo, hi, size=(count, 3))
+    r = rng.uniform(r_lo, r_hi, size=(count, 1))
+    return np.concatenate([c, r], axis=1)
