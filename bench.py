@@ -1,0 +1,366 @@
+"""Benchmark of the GB300 CR-Solver hot path: beam-search IK (Algorithm 1) on the 3-segment,
+9-tendon robot, 4096 full-pose targets per GPU, 256 seeds -> 64 projected-gradient steps (FP32,
+adjoint) -> top 8 -> 30 LM iterations (FP64 Cholesky) -> FP64 acceptance at <= 1 mm / <= 1 deg.
+
+Prints ONE JSON line (rank 0). `value` = IK solves/s over all GPUs with inputs resident in HBM;
+`e2e` = the same through the host-buffer API (pinned H2D of the targets, D2H of the results inside
+the timed region). `roofline` reports the stage-one kernel (the dominant kernel) against the FP32
+ALU peak. `--impl reference` times the FP64 CPU oracle on host cores on the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun, one rank per GPU, each solving its own 4096 targets (weak scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_11340_gb300 import synth  # noqa: E402
+
+METRIC = "IK solves/s at <=1mm/<=1deg (batched FP32+adjoint two-stage beam search)"
+UNIT = "solves/s"
+WORKLOAD = "ik_3seg_9tendon_4096targets_256seeds_pg64_top8_lm30"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
+    return ap.parse_args()
+
+
+def load_counts():
+    with open(os.path.join(ROOT, "tests", "golden", "opcounts.json")) as f:
+        return json.load(f)["ik_3seg_pose"]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_targets(torch, api, lib, spec, P, seed, device):
+    """Full-pose targets [7][P] (FP64, device) from FK of hexagon-uniform states, via the CUDA FK."""
+    rng = np.random.default_rng(seed)
+    u_true = synth.hexagon_states(rng, P, spec.n, spec.umax)
+    ug = torch.as_tensor(u_true.T.copy(), dtype=torch.float64, device=device)
+    T, _ = api.fk(api.robot_struct(spec), ug)
+    tg = synth.pose_targets(T.cpu().numpy().T, "pose")
+    return tg
+
+
+def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None):
+    """Oracle solves/s on host cores over a bounded contiguous sample of the targets."""
+    import oracle as O
+
+    O.build()
+    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius)
+    W = O.make_weights(**synth.WEIGHTS.as_dict())
+    threads = threads or os.cpu_count()
+    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
+                     alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, lim_tol=ik.lim_tol, pos_tol=ik.pos_tol,
+                     rot_tol=ik.rot_tol, seed=ik.seed, p0=p0)
+    n = max(threads, 16)
+    t0 = time.perf_counter()
+    r = O.solve_ik(rb, W, None, O.IK6, tg[:n], cfg, threads=threads)
+    dt = time.perf_counter() - t0
+    done = n
+    res = [r]
+    while dt < budget_s and done < len(tg):
+        m = min(len(tg) - done, max(threads, int(done / dt * (budget_s - dt))))
+        cfg.p0 = p0 + done
+        t1 = time.perf_counter()
+        res.append(O.solve_ik(rb, W, None, O.IK6, tg[done:done + m], cfg, threads=threads))
+        dt += time.perf_counter() - t1
+        done += m
+    succ = np.concatenate([x["success"] for x in res])
+    u = np.concatenate([x["u"] for x in res])
+    return done / dt, done, threads, dt, succ, u
+
+
+def reference_arm(args):
+    """Times the FP64 CPU oracle (as it stands) on the benchmark workload, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    spec, ik = synth.ROBOT_3SEG, synth.IK_3SEG
+    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius)
+    W = O.make_weights(**synth.WEIGHTS.as_dict())
+    tg, _ = synth.ik_workload(spec, synth.P_3SEG, "pose", lambda u: O.fk(rb, u)[0], seed=0)
+    threads = os.cpu_count()
+    per_step = max(threads, 16)
+    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
+                     alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, lim_tol=ik.lim_tol, pos_tol=ik.pos_tol,
+                     rot_tol=ik.rot_tol, seed=ik.seed)
+    times, succ = [], []
+    for k in range(args.warmup + args.steps):
+        lo = (k * per_step) % (len(tg) - per_step)
+        cfg.p0 = lo
+        t0 = time.perf_counter()
+        r = O.solve_ik(rb, W, None, O.IK6, tg[lo:lo + per_step], cfg, threads=threads)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            succ.append(r["success"].mean())
+    ms = 1e3 * float(np.mean(times))
+    value = per_step / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_targets_per_step": per_step},
+            "success_rate": float(np.mean(succ)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} contiguous targets per step of the 4096-target workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2607_11340_gb300 import api, build_lib, lib
+
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    lib.load()
+
+    spec, ik, P = synth.ROBOT_3SEG, synth.IK_3SEG, synth.P_3SEG
+    counts = load_counts()
+    tg = make_targets(torch, api, lib, spec, P, seed=rank, device=dev)
+    tg_dev = torch.as_tensor(tg.T.copy(), dtype=torch.float64, device=dev)
+    solver = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, precision=lib.CR_F32, device=dev)
+    p0 = rank * P
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MiB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.solve(tg_dev, p0)
+        solver.stage1(tg_dev, p0)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K full solves, inputs resident, L2 flushed between steps ----
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        solver.solve(tg_dev, p0)
+        ev[k][1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    tot = torch.tensor([step_ms.sum()], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_per_step = float(tot.item()) / args.steps
+    value = world * P / (ms_per_step / 1e3)
+    res = solver.out
+    succ = float(res.success.float().mean().item())
+    pos_med = float(res.pos_err.median().item())
+    rot_med = float(res.rot_err.median().item())
+    status = solver.status()
+
+    # ---- the dominant kernel alone (stage one: seeds, 64 PG steps, SelectTop), same launch config ----
+    ev1 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev1[k][0].record(stream)
+        solver.stage1(tg_dev, p0)
+        ev1[k][1].record(stream)
+    torch.cuda.synchronize()
+    s1_ms = float(np.mean([a.elapsed_time(b) for a, b in ev1]))
+    n_eval = P * ik.S * (ik.k_init + 1)  # fused value + gradient evaluations per stage-one launch
+    flop_per_eval = counts["fwd_flop"] + counts["tan_flop"]
+    sfu_per_eval = counts["fwd_sfu"] + counts["tan_sfu"]
+    achieved_tflops = n_eval * flop_per_eval / (s1_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+    # ---- live calibration: FFMA / MUFU / DFMA / copy peaks on this GPU in the same run ----
+    cal = {}
+    pbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    for kind, name, it in ((0, "ffma_tflops", 4000), (1, "mufu_tops", 4000), (2, "dfma_tflops", 200), (3, "copy_gbs", 1)):
+        lib.cr_peak_launch(kind, pbuf, it)
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = lib.cr_peak_launch(kind, pbuf, it)
+            b.record(stream)
+            b.synchronize()
+            rate = ops / (a.elapsed_time(b) / 1e3)
+            best = max(best, rate / (1e9 if kind == 3 else 1e12))
+        cal[name] = best
+    del pbuf
+
+    # ---- end to end through the host-buffer API ----
+    tg_host = torch.as_tensor(tg.T.copy(), dtype=torch.float64).pin_memory()
+    out_host = solver.solve_host(tg_host, p0=p0)
+    e2e_ms = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        solver.solve_host(tg_host, out_host, p0=p0)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = torch.tensor([float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * P / (float(e2e_t.item()) / args.steps / 1e3)
+    h2d = tg_host.numel() * 8
+    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+
+    # ---- plain one-launch-per-target FP64 comparator on a subset ----
+    Pp = 16
+    plain = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, Pp, plain=True, device=dev)
+    plain.solve(tg_dev[:, :Pp].contiguous(), p0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain.solve(tg_dev[:, :Pp].contiguous(), p0)
+    b.record(stream)
+    b.synchronize()
+    plain_rate = Pp / (a.elapsed_time(b) / 1e3)
+    plain_succ = float(plain.out.success.float().mean().item())
+    opt_succ_sub = float(res.success[:Pp].float().mean().item())
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "targets_per_gpu": P, "seeds": ik.S, "k_init": ik.k_init,
+                   "n_final": ik.n_final, "k_final": ik.k_final, "segments": spec.n,
+                   "l2": "flushed between timed steps (512 MiB write)", "lm_cholesky": "f64"},
+        "success_rate": succ, "pos_err_median_m": pos_med, "rot_err_median_rad": rot_med, "device_status": status,
+        "evals_per_s": world * (n_eval + P * ik.n_final * (2 * ik.k_final + 1)) / (ms_per_step / 1e3),
+        "roofline": {"bound": "alu", "kernel": "k_ik_stage1", "achieved": achieved_tflops, "peak": peak_fp32,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_fp32, "traffic": None,
+                     "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                     "kernel_ms": s1_ms, "evals_per_launch": n_eval, "flop_per_eval": flop_per_eval,
+                     "frac_of_live_ffma": achieved_tflops / cal["ffma_tflops"],
+                     "sfu_results_per_s": n_eval * sfu_per_eval / (s1_ms / 1e3),
+                     "sfu_frac_of_live_mufu": n_eval * sfu_per_eval / (s1_ms / 1e3) / (cal["mufu_tops"] * 1e12)},
+        "calibration": cal,
+        "plain_form": {"value": plain_rate, "unit": UNIT, "targets": Pp, "success_rate": plain_succ,
+                       "optimised_success_rate_same_targets": opt_succ_sub, "speedup": value / world / plain_rate},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_baseline:
+        rate, n, cores, dt, osucc, ou = cpu_oracle_rate(tg, spec, ik, p0=p0)
+        gsucc = res.success[:n].cpu().numpy().astype(bool)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {n} of the 4096 targets ({dt:.1f} s on {cores} threads)"}
+        line["oracle_agreement"] = {"targets": n, "success_rate_oracle": float(osucc.mean()),
+                                    "success_rate_gpu": float(gsucc.mean()),
+                                    "success_flag_mismatches": int((gsucc != osucc).sum())}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

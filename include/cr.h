@@ -1,0 +1,271 @@
+/* C ABI of the GB300 CR-Solver hot path (libcrsolver.so).
+ *
+ * The library evaluates and optimises tendon-driven piecewise-constant-curvature (PCC) continuum
+ * robots in large batches on one GPU (sm_103a). Every entry point below is `extern "C"`, takes
+ * plain pointers and sizes, and returns a cr_status. No torch or CUDA C++ types appear here; the
+ * stream argument is a cudaStream_t passed as an opaque pointer (NULL = the legacy default stream).
+ *
+ * Conventions shared by all entry points
+ *  - Model (Sec. III): segment i (0-based, i < n) has arc length L_i, m = 3 tendons at radius r_c,i
+ *    and angles alpha_j = 2 pi j / 3. Its state is the tendon displacement triple
+ *    u_i = (u_i0, u_i1, u_i2), u_ij = l_ij - L_i (Eq. 4 read per segment). The bending of the
+ *    segment follows from the exact inverse of Eq. 4: theta_i cos(phi_i) = -(2 / (3 r_c,i)) sum_j
+ *    u_ij cos(alpha_j) and theta_i sin(phi_i) = -(2 / (3 r_c,i)) sum_j u_ij sin(alpha_j). The segment
+ *    transform is Eq. 1-3, and the chain T_0^n = T_0^1 ... T_{n-1}^n is the tip pose.
+ *  - States are structure-of-arrays: u[q][B], q = 3 i + j over d = 3 n components, batch fastest.
+ *  - Pose outputs T[12][B]: the rotation R row-major (9 rows), then the position p (3 rows).
+ *  - Device pointers: every array argument is a caller-owned DEVICE pointer unless it is marked
+ *    "host". The library never allocates device memory. Where an entry point needs scratch space,
+ *    the caller passes a `workspace` of at least the size its *_workspace_size function returns
+ *    (256-byte aligned). Structs (cr_robot, cr_task, ...) are host pointers. Their contents are
+ *    copied into kernel parameters at the call, so they may be freed when the call returns.
+ *  - Asynchrony: work is enqueued on `stream` and the call returns at once. Outputs are valid
+ *    after the stream is synchronised.
+ *  - Errors: invalid arguments (null pointers where required, n outside 1..CR_MAX_SEG, m != 3,
+ *    negative sizes, misaligned pointers, too-small workspace) return CR_EINVAL before anything
+ *    is launched. A failed launch returns CR_ECUDA. cr_last_error_string() describes the last
+ *    failure on the calling thread. Conditions found on the device never trap: they are written
+ *    to per-problem flags and to the status word at the start of the workspace, read by
+ *    cr_poll_status.
+ */
+#ifndef CR_H_
+#define CR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CR_API __attribute__((visibility("default")))
+#else
+#define CR_API
+#endif
+
+typedef void* cr_stream; /* cudaStream_t */
+
+typedef enum {
+  CR_OK = 0,
+  CR_EINVAL = 1,     /* invalid argument; nothing was launched */
+  CR_ECUDA = 2,      /* a CUDA launch or runtime call failed */
+  CR_ENONFINITE = 3, /* a non-finite input or iterate was met (device status bit) */
+  CR_ETIMEOUT = 4,   /* a bounded device wait gave up (device status bit) */
+} cr_status;
+
+/* Arithmetic of the bulk evaluation. CR_F32: FP32 kinematics, Jacobian, cost and adjoint;
+ * the LM Cholesky and the final acceptance stay FP64. CR_F64: everything FP64. */
+typedef enum { CR_F32 = 0, CR_F64 = 1 } cr_dtype;
+
+#define CR_MAX_SEG 6
+#define CR_MAX_SPHERES 256
+#define CR_MAX_NB 64
+#define CR_MAX_SEEDS 256
+
+/* Robot geometry (Sec. III, Fig. 2). Host struct. */
+typedef struct {
+  int32_t n;       /* segments, 1..CR_MAX_SEG */
+  int32_t m;       /* tendons per segment; must be 3 */
+  int32_t n_b;     /* backbone samples per segment for clearance (1..CR_MAX_NB); sample k of
+                      segment i is the end of the sub-arc of fraction k / n_b, k = 1..n_b */
+  int32_t reserved;
+  double L[CR_MAX_SEG];         /* arc lengths (m) */
+  double r_c[CR_MAX_SEG];       /* tendon routing radii (m) */
+  double u_max[CR_MAX_SEG];     /* bound |u_ij| <= u_max_i (m), Eq. ik_limits */
+  double theta_max[CR_MAX_SEG]; /* bending-angle limit (rad), Eq. ik_limits */
+  double r_body;                /* backbone radius added to every sphere radius (m) */
+} cr_robot;
+
+/* Penalty and objective weights of Eq. penalized_form, as a least-squares sum 1/2 sum r^2. */
+typedef struct {
+  double w_p, w_R;                    /* pose rows: w_p (p - p_t) and w_R Log(R_t^T R) */
+  double rho_b, rho_eq, rho_k, rho_c; /* squared-hinge / equality weights: bounds, sum-zero,
+                                         curvature, clearance */
+  double w_s, w_len, rho_v, rho_a;    /* path smoothness, trajectory length, tendon speed and
+                                         acceleration hinges */
+  double dt, v_max, a_max;            /* time step (s), tendon speed (m/s) and acceleration
+                                         (m/s^2) limits */
+  double delta;                       /* clearance margin of Eq. ik_coll (m) */
+} cr_weights;
+
+/* Obstacles: spheres for the clearance rows of Eq. ik_coll. Host struct; `spheres` is a device
+ * array [n_o][4] = (centre x, y, z, radius), FP64. */
+typedef struct {
+  const double* spheres;
+  int32_t n_o; /* 0..CR_MAX_SPHERES */
+  int32_t reserved;
+} cr_scene;
+
+typedef enum {
+  CR_TASK_IK6 = 0, /* full pose: r = [w_p (p - p_t); w_R Log(R_t^T R)] (Eq. ik_opt, split) */
+  CR_TASK_IK5 = 1, /* position + tip axis: r = [w_p (p - p_t); w_R (z - z_t)] */
+} cr_task_kind;
+
+/* An IK-type task over a batch of states. Host struct. State b aims at target b / S.
+ * `targets` is a device array [7][n_targets] (FP64, component-major): p_x, p_y, p_z, then the
+ * unit quaternion (w, x, y, z) for CR_TASK_IK6, or the tip axis (z_x, z_y, z_z, unused) for
+ * CR_TASK_IK5. */
+typedef struct {
+  int32_t kind;
+  int32_t seeds_per_target; /* S >= 1 */
+  const double* targets;
+  int64_t n_targets;
+  cr_weights w;
+} cr_task;
+
+/* Settings of Algorithm 1 (beam-search IK). Host struct. */
+typedef struct {
+  int32_t S;        /* seeds per target, 1..CR_MAX_SEEDS (one CTA per target) */
+  int32_t n_final;  /* candidates kept by SelectTop, 1..min(S, 32) */
+  int32_t k_init;   /* stage-one projected-gradient steps (0 = single-stage: SelectTop only) */
+  int32_t k_final;  /* stage-two LM iterations */
+  double lambda0;   /* initial LM damping */
+  double alpha0;    /* first stage-one step length (m of tendon displacement) */
+  double dedup_eps; /* SelectTop skips candidates within this max-norm distance of a kept one */
+  double lim_tol;   /* acceptance: |u| <= u_max + lim_tol and |sum_j u_ij| <= lim_tol */
+  double pos_tol;   /* acceptance: position error (m) */
+  double rot_tol;   /* acceptance: rotation error (rad) */
+  uint64_t seed;    /* counter-based seed generator key */
+  int64_t p0;       /* global index of the first target (seed counter offset) */
+  int32_t precision;/* cr_dtype of the bulk evaluation */
+  int32_t reserved;
+} cr_ik_params;
+
+/* ---------------------------------------------------------------------------------------------
+ * Kinematics (Sec. III, Eq. 1-4)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Forward kinematics of B states. u: [3n][B] in `dtype`; T_out: [12][B] in `dtype`;
+ * backbone_out (nullable): [n * n_b][3][B] in `dtype`, the backbone samples (Fig. 2; the paper
+ * samples 10 points per segment, Sec. V-B). */
+CR_API cr_status cr_fk(const cr_robot* robot, const void* u, int64_t B, void* T_out, void* backbone_out,
+                int32_t dtype, cr_stream stream);
+
+/* Tip Jacobian of B states: J_out [6][3n][B] in `dtype`. Rows 0-2: d p / d u. Rows 3-5: the world
+ * angular velocity w with dR = [w]x R per unit du. Needed by the LM step of Sec. IV-C. */
+CR_API cr_status cr_fk_jac(const cr_robot* robot, const void* u, int64_t B, void* J_out, int32_t dtype,
+                    cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Penalised cost and its adjoint (Sec. IV-A, Eq. ik_opt, ik_limits, ik_coll, penalized_form)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Per-state cost F_b = 1/2 sum r^2 of an IK task, with rows
+ *   pose (6), bounds sqrt(rho_b) max(0, +-u - u_max) (2 per tendon), sum-zero sqrt(rho_eq) sum_j u_ij
+ *   (1 per segment), curvature sqrt(rho_k) max(0, theta_i - theta_max_i) (1 per segment) and
+ *   clearance sqrt(rho_c) max(0, r_s + r_body + delta - |x_k - c_s|) per (sample, sphere) pair.
+ * cost_out [B] (required), coll_out [B] (nullable: the clearance part of F_b), grad_u_out [3n][B]
+ * (nullable: dF_b / du), grad_param_out [2n][B] (nullable: dF_b / dL_i for i < n, then dF_b / dr_c,i),
+ * all in `dtype`. The gradients come from a hand-written reverse sweep over the segments. */
+CR_API cr_status cr_cost_grad(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                       const void* u, int64_t B, void* cost_out, void* coll_out, void* grad_u_out,
+                       void* grad_param_out, int32_t dtype, cr_stream stream);
+
+/* Deterministic row sums: out[r] = sum_b x[r][b] for r < rows (x [rows][B] in `dtype`, out FP64).
+ * One block per row, fixed summation order (used to reduce per-state parameter gradients). */
+CR_API cr_status cr_reduce_rows(const void* x, int64_t rows, int64_t B, double* out, int32_t dtype,
+                         cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Solver steps (Sec. IV-C; Algorithm 1)
+ * ------------------------------------------------------------------------------------------- */
+
+/* `n_iter` Levenberg-Marquardt iterations on each of B states of an IK task, all in registers:
+ * A = J^T J + lambda D (D = diag(max(diag(J^T J), 1e-12))), Cholesky in FP64, delta = -A^-1 J^T r,
+ * accept iff F(u + delta) < F(u), then lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; otherwise
+ * lambda *= nu, nu *= 2. A non-positive pivot rejects the iteration the same way.
+ * u_inout [3n][B] (`dtype`), lambda_inout / nu_inout [B] (FP64, caller-initialised),
+ * F_out [B] (FP64, cost at the returned state, nullable), accepted_out [B] (nullable; the
+ * number of accepted iterations). */
+CR_API cr_status cr_lm_step(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                     void* u_inout, double* lambda_inout, double* nu_inout, double* F_out,
+                     int32_t* accepted_out, int64_t B, int32_t n_iter, int32_t dtype,
+                     cr_stream stream);
+
+/* `steps` stage-one projected-gradient steps on each of B states: trial u' = Pi(u - alpha g/|g|),
+ * accept iff F(u') < F(u) (then alpha *= 1.25) else alpha *= 0.5; Pi is the Euclidean projection
+ * of each segment onto {|u_ij| <= u_max_i, sum_j u_ij = 0}. u_inout [3n][B], alpha_inout [B],
+ * F_out [B], all in `dtype`. */
+CR_API cr_status cr_pg_steps(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                      void* u_inout, void* alpha_inout, void* F_out, int64_t B, int32_t steps,
+                      int32_t dtype, cr_stream stream);
+
+/* SampleSeeds of Algorithm 1: S seeds for each of P problems (global index p0 + p), uniform on
+ * each segment's feasible hexagon, from the counter-based SplitMix64 generator keyed by `seed`.
+ * With spheres, a seed whose backbone comes closer than r_s + r_body + delta to a sphere is
+ * redrawn, at most 8 draws. u_out [3n][P * S] in `dtype` (seed s of problem p at p * S + s). */
+CR_API cr_status cr_seeds(const cr_robot* robot, const cr_scene* scene, const cr_weights* w,
+                   uint64_t seed, int64_t p0, int64_t P, int32_t S, void* u_out, int32_t dtype,
+                   cr_stream stream);
+
+/* SelectTop of Algorithm 1 for P problems of S candidates each: rank by (cost, coll, index)
+ * ascending (non-finite costs last), skip candidates within `dedup_eps` (max-norm over u) of a
+ * kept one, fill up with the best skipped ones. cost/coll [P * S] FP32, u [3n][P * S] in
+ * `dtype`, idx_out [P][k] (int32, -1 where fewer than k candidates). k <= 32, S <= CR_MAX_SEEDS. */
+CR_API cr_status cr_topk(const float* cost, const float* coll, const void* u, int32_t d, int64_t P,
+                  int32_t S, int32_t k, double dedup_eps, int32_t* idx_out, int32_t dtype,
+                  cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Solvers
+ * ------------------------------------------------------------------------------------------- */
+
+/* Scratch bytes cr_solve_ik needs for P targets. */
+CR_API size_t cr_ik_workspace_size(const cr_robot* robot, int64_t P, const cr_ik_params* prm);
+
+/* Algorithm 1 (beam-search IK) for the P targets of `task` (task->seeds_per_target is ignored):
+ * SampleSeeds(S) -> k_init projected-gradient steps per seed (registers) -> SelectTop(n_final)
+ * (warp shuffles) -> k_final LM iterations per candidate -> FP64 re-evaluation and argmin.
+ * Outputs (device, FP64 unless noted): u_out [3n][P], cost_out [P], pos_err [P] (m),
+ * rot_err [P] (rad), success [P] (uint8: pos_err <= pos_tol, rot_err <= rot_tol, within limits,
+ * collision-free). */
+CR_API cr_status cr_solve_ik(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                      const cr_ik_params* prm, double* u_out, double* cost_out, double* pos_err,
+                      double* rot_err, uint8_t* success, void* workspace, size_t ws_bytes,
+                      cr_stream stream);
+
+/* The two stages of cr_solve_ik as separate calls (same arguments, same workspace): stage 1 runs
+ * SampleSeeds, the k_init projected-gradient steps and SelectTop and leaves the n_final candidates
+ * of every target in the workspace; stage 2 refines them (k_final LM iterations), re-evaluates
+ * them in FP64 and writes the argmin outputs. cr_solve_ik = stage 1 followed by stage 2 on one
+ * stream; the status word is cleared by stage 1. */
+CR_API cr_status cr_ik_stage1(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                              const cr_ik_params* prm, void* workspace, size_t ws_bytes, cr_stream stream);
+CR_API cr_status cr_ik_stage2(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                              const cr_ik_params* prm, double* u_out, double* cost_out, double* pos_err,
+                              double* rot_err, uint8_t* success, void* workspace, size_t ws_bytes,
+                              cr_stream stream);
+
+/* The straightforward comparator of cr_solve_ik: the same algorithm in FP64, one launch per
+ * target, states kept in global memory as an array of structures. Same outputs; its workspace
+ * is cr_ik_workspace_size with precision CR_F64. */
+CR_API cr_status cr_solve_ik_plain(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                            const cr_ik_params* prm, double* u_out, double* cost_out,
+                            double* pos_err, double* rot_err, uint8_t* success, void* workspace,
+                            size_t ws_bytes, cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Status and diagnostics
+ * ------------------------------------------------------------------------------------------- */
+
+/* Copies the device status word at the start of `workspace` to *host_status (a bit set of
+ * 1 << CR_ENONFINITE and 1 << CR_ETIMEOUT) after synchronising `stream`. */
+CR_API cr_status cr_poll_status(const void* workspace, int32_t* host_status, cr_stream stream);
+
+/* Description of the last error on the calling thread (static storage; never NULL). */
+CR_API const char* cr_last_error_string(void);
+
+/* Peak-calibration kernels (FP32 FMA chains, special-function chains, FP64 FMA chains and a
+ * streaming copy), timed by the caller with events around the launch. kind: 0 FFMA, 1 MUFU
+ * (sin/cos approximations), 2 DFMA, 3 copy. `buf` is a device buffer of `bytes` bytes (copy
+ * reads the first half and writes the second). *ops_out (host) receives the operations one
+ * launch performs (flops for 0 and 2, special-function results for 1, bytes moved for 3). */
+CR_API cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32_t iters, double* ops_out,
+                         cr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CR_H_ */

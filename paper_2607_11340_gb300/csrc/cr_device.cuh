@@ -1,0 +1,888 @@
+// Device math of the CR-Solver hot path: PCC segment transforms (Eq. 1-3), the inverse tendon map
+// (Eq. 4), the chain, the SO(3) log of the pose error (Eq. ik_opt), the penalty rows of
+// Eq. penalized_form, the hand-written adjoint (reverse sweep over segments) and the LM normal
+// equations. Everything is templated on the arithmetic type T (float / double) and on the number
+// of segments N, so that a state lives entirely in registers.
+//
+// Notation: segment i bends by a = (ax, ay) = theta (cos phi, sin phi); x = theta^2.
+//   ax = K (u0 - (u1 + u2)/2), ay = K (sqrt(3)/2)(u1 - u2), K = -2 / (3 r_c)   (inverse of Eq. 4)
+//   R_i = I + s [w]x + c [w]x^2, w = (-ay, ax, 0)       (Eq. 2 in Rodrigues form)
+//   d_i = L (c ax, c ay, s)                            (Eq. 3)
+//   s = sin(theta)/theta, c = (1 - cos theta)/theta^2, evaluated through the half angle:
+//   s = sinc(theta/2) cos(theta/2), c = sinc(theta/2)^2 / 2 (no cancellation near theta = 0).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cr.h"
+
+#define CR_HD __device__ __forceinline__
+
+namespace crk {
+
+constexpr int NMAX = CR_MAX_SEG;
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+  static constexpr float kZero = 1e-12f;     // theta^2 below which sinc(theta/2) uses its series
+  static constexpr float kSeriesX = 1.0f;    // theta^2 below which s3 and dc/dx use their series
+  static constexpr float kLogSmall = 1e-10f; // |vee|^2 below which Log uses 1 + s^2/6
+  static constexpr float kLogPi = 1e-2f;     // |vee|^2 below which (cos < 0) Log takes the symmetric part
+  static constexpr float kBetaSeries = 1.0f; // angle^2 below which the log-Jacobian factor uses its series
+};
+template <> struct Prec<double> {
+  static constexpr double kZero = 1e-20;
+  static constexpr double kSeriesX = 0.1;
+  static constexpr double kLogSmall = 1e-6;
+  static constexpr double kLogPi = 1e-2;
+  static constexpr double kBetaSeries = 1e-2;
+};
+
+CR_HD float c_sqrt(float x) { return sqrtf(x); }
+CR_HD double c_sqrt(double x) { return sqrt(x); }
+CR_HD void c_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+CR_HD void c_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+CR_HD float c_atan2(float y, float x) { return atan2f(y, x); }
+CR_HD double c_atan2(double y, double x) { return atan2(y, x); }
+CR_HD float c_fabs(float x) { return fabsf(x); }
+CR_HD double c_fabs(double x) { return fabs(x); }
+CR_HD bool c_finite(float x) { return isfinite(x); }
+CR_HD bool c_finite(double x) { return isfinite(x); }
+template <typename T> CR_HD T c_max(T a, T b) { return a > b ? a : b; }
+template <typename T> CR_HD T c_min(T a, T b) { return a < b ? a : b; }
+
+// ------------------------------------------------------------------------------------------------
+// Parameters as the kernels see them
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct RobotK {
+  int n, nb;
+  T L[NMAX], K[NMAX], umax[NMAX], thmax[NMAX], rc[NMAX];
+  T rbody;
+};
+
+struct NmaxArr {
+  double v[NMAX];
+};
+
+template <typename T> struct WeightsK {
+  T wp2, wR2;              // squared pose weights
+  T wp, wR;
+  T rho_b, rho_eq, rho_k, rho_c;
+  T sb, se, sk, sc;        // square roots of the penalty weights (row scale)
+  T delta;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Segment functions of theta^2
+// ------------------------------------------------------------------------------------------------
+// s = sin(t)/t and c = (1 - cos t)/t^2 from x = t^2 (half-angle form).
+template <typename T> CR_HD void seg_sc(T x, T& s, T& c) {
+  T sc, ch;
+  if (x < Prec<T>::kZero) {
+    sc = T(1) - x * T(1.0 / 24.0);
+    ch = T(1) - x * T(0.125);
+  } else {
+    T h = T(0.5) * c_sqrt(x);
+    T sh;
+    c_sincos(h, &sh, &ch);
+    sc = sh / h;
+  }
+  s = sc * ch;
+  c = T(0.5) * sc * sc;
+}
+
+// s3 = (t - sin t)/t^3 = (1 - s)/x and cp = dc/dx = (s - 2c)/(2x); Taylor series in x below kSeriesX.
+template <typename T> CR_HD void seg_deriv(T x, T s, T c, T& s3, T& cp) {
+  if (x < Prec<T>::kSeriesX) {
+    s3 = T(1.0 / 6.0) + x * (T(-1.0 / 120.0) + x * (T(1.0 / 5040.0) + x * (T(-1.0 / 362880.0) +
+         x * (T(1.0 / 39916800.0) + x * (T(-1.0 / 6227020800.0) + x * T(1.0 / 1307674368000.0))))));
+    cp = T(-1.0 / 24.0) + x * (T(1.0 / 360.0) + x * (T(-1.0 / 13440.0) + x * (T(1.0 / 907200.0) +
+         x * (T(-1.0 / 95800320.0) + x * (T(1.0 / 14529715200.0) + x * T(-1.0 / 2988969984000.0))))));
+  } else {
+    T ix = T(1) / x;
+    s3 = (T(1) - s) * ix;
+    cp = (s - T(2) * c) * (T(0.5) * ix);
+  }
+}
+
+// Local derivatives of one segment with respect to (ax, ay):
+//  dd[k]: d(d_i)/da_k = L (c e_k + 2 a_k cp (ax, ay, 0) + 2 a_k sp e_z), sp = ds/dx = (s3 - c)/2
+//  wl[k]: vee(dR R^T)/da_k = J_l(w) dw/da_k, J_l = I + c [w]x + s3 [w]x^2 (left Jacobian of SO(3))
+template <typename T>
+CR_HD void seg_local_derivs(T ax, T ay, T s, T c, T s3, T cp, T L, T (&dd)[2][3], T (&wl)[2][3]) {
+  T sp = T(0.5) * (s3 - c);
+  T axy = ax * ay;
+  dd[0][0] = L * (c + T(2) * ax * ax * cp);
+  dd[0][1] = L * (T(2) * axy * cp);
+  dd[0][2] = L * (T(2) * ax * sp);
+  dd[1][0] = dd[0][1];
+  dd[1][1] = L * (c + T(2) * ay * ay * cp);
+  dd[1][2] = L * (T(2) * ay * sp);
+  wl[0][0] = -s3 * axy;
+  wl[0][1] = T(1) - s3 * ay * ay;
+  wl[0][2] = -c * ay;
+  wl[1][0] = s3 * ax * ax - T(1);
+  wl[1][1] = s3 * axy;
+  wl[1][2] = c * ax;
+}
+
+// Rotation and translation of a segment (Eq. 2-3).
+template <typename T> CR_HD void seg_transform(T ax, T ay, T x, T s, T c, T L, T (&Ri)[9], T (&di)[3]) {
+  T caxy = c * ax * ay;
+  Ri[0] = T(1) - c * ax * ax; Ri[1] = -caxy;               Ri[2] = s * ax;
+  Ri[3] = -caxy;               Ri[4] = T(1) - c * ay * ay; Ri[5] = s * ay;
+  Ri[6] = -s * ax;             Ri[7] = -s * ay;            Ri[8] = T(1) - c * x;
+  di[0] = L * c * ax;
+  di[1] = L * c * ay;
+  di[2] = L * s;
+}
+
+template <typename T> CR_HD void bend_of(T K, T u0, T u1, T u2, T& ax, T& ay) {
+  ax = K * (u0 - T(0.5) * (u1 + u2));
+  ay = K * (T(0.86602540378443864676) * (u1 - u2));
+}
+
+// grad in u of a segment from grad in a: (du0, du1, du2) = K C^T (ga_x, ga_y)
+template <typename T> CR_HD void bend_grad_to_u(T K, T gx, T gy, T& g0, T& g1, T& g2) {
+  T hx = T(0.5) * gx, ry = T(0.86602540378443864676) * gy;
+  g0 = K * gx;
+  g1 = K * (ry - hx);
+  g2 = K * (-ry - hx);
+}
+
+template <typename T> CR_HD void matvec(const T (&R)[9], const T (&v)[3], T (&o)[3]) {
+  o[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+  o[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+  o[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+template <typename T> CR_HD void matTvec(const T (&R)[9], const T (&v)[3], T (&o)[3]) {
+  o[0] = R[0] * v[0] + R[3] * v[1] + R[6] * v[2];
+  o[1] = R[1] * v[0] + R[4] * v[1] + R[7] * v[2];
+  o[2] = R[2] * v[0] + R[5] * v[1] + R[8] * v[2];
+}
+template <typename T> CR_HD void cross(const T (&a)[3], const T (&b)[3], T (&o)[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T> CR_HD T dot3(const T (&a)[3], const T (&b)[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Forward chain
+// ------------------------------------------------------------------------------------------------
+template <typename T, int N> struct Chain {
+  T Rb[N][9], pb[N][3];  // base frame of every segment
+  T ax[N], ay[N], x[N], s[N], c[N];
+  T R[9], p[3];          // tip frame
+};
+
+template <typename T, int N>
+CR_HD void chain_forward(const RobotK<T>& rb, const T (&u)[3 * N], Chain<T, N>& ch) {
+  T R[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
+  T p[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) ch.Rb[i][a] = R[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ch.pb[i][a] = p[a];
+    T ax, ay;
+    bend_of(rb.K[i], u[3 * i], u[3 * i + 1], u[3 * i + 2], ax, ay);
+    T x = ax * ax + ay * ay;
+    T s, c;
+    seg_sc(x, s, c);
+    ch.ax[i] = ax; ch.ay[i] = ay; ch.x[i] = x; ch.s[i] = s; ch.c[i] = c;
+    T Ri[9], di[3];
+    seg_transform(ax, ay, x, s, c, rb.L[i], Ri, di);
+    T t[3];
+    matvec(R, di, t);
+    p[0] += t[0]; p[1] += t[1]; p[2] += t[2];
+    T Rn[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        Rn[3 * r + q] = R[3 * r] * Ri[q] + R[3 * r + 1] * Ri[3 + q] + R[3 * r + 2] * Ri[6 + q];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) R[a] = Rn[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 9; ++a) ch.R[a] = R[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ch.p[a] = p[a];
+}
+
+// Backbone sample at arc fraction sg of segment i (base frame Rb, pb): the sub-arc bends by sg*a
+// over sg*L. Returns the local point q and the world point w.
+template <typename T>
+CR_HD void backbone_point(const T (&Rb)[9], const T (&pb)[3], T ax, T ay, T x, T L, T sg, T (&q)[3],
+                          T (&w)[3], T& s, T& c) {
+  T xs = sg * sg * x;
+  seg_sc(xs, s, c);
+  T sL = sg * L;
+  q[0] = sL * c * (sg * ax);
+  q[1] = sL * c * (sg * ay);
+  q[2] = sL * s;
+  T t[3];
+  matvec(Rb, q, t);
+  w[0] = pb[0] + t[0];
+  w[1] = pb[1] + t[1];
+  w[2] = pb[2] + t[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Targets and pose error
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct TargetK {
+  T p[3];
+  T R[9];  // IK6: target rotation; IK5: R[0..2] = unit tip axis
+};
+
+// targets [7][P] SoA, FP64
+template <typename T> CR_HD TargetK<T> load_target(const double* tg, int64_t P, int64_t q, int kind) {
+  TargetK<T> t;
+  t.p[0] = T(tg[q]);
+  t.p[1] = T(tg[P + q]);
+  t.p[2] = T(tg[2 * P + q]);
+  if (kind == CR_TASK_IK5) {
+    T zx = T(tg[3 * P + q]), zy = T(tg[4 * P + q]), zz = T(tg[5 * P + q]);
+    T inv = T(1) / c_sqrt(zx * zx + zy * zy + zz * zz);
+    t.R[0] = zx * inv; t.R[1] = zy * inv; t.R[2] = zz * inv;
+    for (int a = 3; a < 9; ++a) t.R[a] = T(0);
+  } else {
+    T w = T(tg[3 * P + q]), x = T(tg[4 * P + q]), y = T(tg[5 * P + q]), z = T(tg[6 * P + q]);
+    T inv = T(1) / c_sqrt(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    t.R[0] = T(1) - T(2) * (y * y + z * z); t.R[1] = T(2) * (x * y - w * z); t.R[2] = T(2) * (x * z + w * y);
+    t.R[3] = T(2) * (x * y + w * z); t.R[4] = T(1) - T(2) * (x * x + z * z); t.R[5] = T(2) * (y * z - w * x);
+    t.R[6] = T(2) * (x * z - w * y); t.R[7] = T(2) * (y * z + w * x); t.R[8] = T(1) - T(2) * (x * x + y * y);
+  }
+  return t;
+}
+
+// SO(3) log of E (row-major): e = angle * axis. Returns the angle; sn = sin(angle).
+template <typename T> CR_HD T so3_log(const T (&E)[9], T (&e)[3], T& sn_out, T& cs_out) {
+  T v0 = T(0.5) * (E[7] - E[5]), v1 = T(0.5) * (E[2] - E[6]), v2 = T(0.5) * (E[3] - E[1]);
+  T cs = T(0.5) * (E[0] + E[4] + E[8] - T(1));
+  T s2 = v0 * v0 + v1 * v1 + v2 * v2;
+  T sn = c_sqrt(s2);
+  T ang = c_atan2(sn, cs);
+  sn_out = sn;
+  cs_out = cs;
+  if (cs < T(0) && s2 < Prec<T>::kLogPi) {
+    // near pi: (E + E^T)/2 = cs I + (1 - cs) n n^T; largest diagonal gives the best-conditioned column
+    T S00 = E[0], S11 = E[4], S22 = E[8];
+    T den = T(1) / (T(1) - cs);
+    int k = (S11 > S00) ? 1 : 0;
+    if (S22 > (k == 1 ? S11 : S00)) k = 2;
+    T Skk = k == 0 ? S00 : (k == 1 ? S11 : S22);
+    T nk = c_sqrt(c_max((Skk - cs) * den, T(0)));
+    T inv = T(1) / nk;
+    T n[3];
+    // off-diagonal symmetric parts
+    T S01 = T(0.5) * (E[1] + E[3]), S02 = T(0.5) * (E[2] + E[6]), S12 = T(0.5) * (E[5] + E[7]);
+    if (k == 0) { n[0] = nk; n[1] = S01 * den * inv; n[2] = S02 * den * inv; }
+    else if (k == 1) { n[0] = S01 * den * inv; n[1] = nk; n[2] = S12 * den * inv; }
+    else { n[0] = S02 * den * inv; n[1] = S12 * den * inv; n[2] = nk; }
+    T sgn = (n[0] * v0 + n[1] * v1 + n[2] * v2) < T(0) ? T(-1) : T(1);
+    e[0] = sgn * ang * n[0];
+    e[1] = sgn * ang * n[1];
+    e[2] = sgn * ang * n[2];
+    return ang;
+  }
+  T f = (s2 < Prec<T>::kLogSmall) ? T(1) + s2 * T(1.0 / 6.0) : ang / sn;
+  e[0] = f * v0;
+  e[1] = f * v1;
+  e[2] = f * v2;
+  return ang;
+}
+
+// beta(angle) = 1/angle^2 - (1 + cos)/(2 angle sin) = (1 - (a/2) cot(a/2)) / a^2: the factor of
+// [e]x^2 in the inverse right Jacobian J_r^-1(e) = I + [e]x / 2 + beta [e]x^2.
+template <typename T> CR_HD T log_beta(T ang) {
+  T y = ang * ang;
+  if (y < Prec<T>::kBetaSeries)
+    return T(1.0 / 12.0) + y * (T(1.0 / 720.0) + y * (T(1.0 / 30240.0) + y * (T(1.0 / 1209600.0) +
+           y * (T(1.0 / 47900160.0) + y * T(1.0 / 1892437580.3)))));
+  T sh, chh;
+  c_sincos(T(0.5) * ang, &sh, &chh);
+  return (sh - T(0.5) * ang * chh) / (y * sh);
+}
+
+// Pose residual rows r[6] of the tip (R, p) against a target.
+template <typename T>
+CR_HD void pose_rows(int kind, const WeightsK<T>& w, const TargetK<T>& tg, const T (&R)[9],
+                     const T (&p)[3], T (&r)[6], T (&e)[3], T& ang, T& sn, T& cs) {
+  r[0] = w.wp * (p[0] - tg.p[0]);
+  r[1] = w.wp * (p[1] - tg.p[1]);
+  r[2] = w.wp * (p[2] - tg.p[2]);
+  if (kind == CR_TASK_IK5) {
+    e[0] = R[2] - tg.R[0];
+    e[1] = R[5] - tg.R[1];
+    e[2] = R[8] - tg.R[2];
+    ang = T(0); sn = T(0); cs = T(1);
+  } else {
+    T E[9];  // R_t^T R
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        E[3 * a + b] = tg.R[a] * R[b] + tg.R[3 + a] * R[3 + b] + tg.R[6 + a] * R[6 + b];
+    ang = so3_log(E, e, sn, cs);
+  }
+  r[3] = w.wR * e[0];
+  r[4] = w.wR * e[1];
+  r[5] = w.wR * e[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Obstacles
+// ------------------------------------------------------------------------------------------------
+// Spheres as the kernels see them: (centre, reach = r_s + r_body + delta), staged in shared memory.
+template <typename T> struct Sphere4 { T x, y, z, reach; };
+
+template <typename T>
+__device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T delta, Sphere4<T>* sh) {
+  for (int j = threadIdx.x; j < no; j += blockDim.x) {
+    Sphere4<T> s;
+    s.x = T(sp[4 * j]);
+    s.y = T(sp[4 * j + 1]);
+    s.z = T(sp[4 * j + 2]);
+    s.reach = T(sp[4 * j + 3]) + rb.rbody + delta;
+    sh[j] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Cost and adjoint of an IK state (forward sweep + reverse sweep over segments)
+// ------------------------------------------------------------------------------------------------
+// Penalty rows on u of one state: bounds, sum-zero, curvature (value added to F, gradient in a/u).
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
+CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+                const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
+                T* coll_out) {
+  Chain<T, N> ch;
+  chain_forward(rb, u, ch);
+  T r[6], e[3], ang, sn, cs;
+  pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
+  T F = T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  // per-segment aggregates of the clearance rows (downstream force / moment, own-segment terms)
+  T G[N][3], M[N][3], Dx[N], Dy[N], DL[N];
+  T coll = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    G[i][0] = G[i][1] = G[i][2] = T(0);
+    M[i][0] = M[i][1] = M[i][2] = T(0);
+    Dx[i] = Dy[i] = DL[i] = T(0);
+  }
+  if (OBST && no > 0) {
+    const T inb = T(1) / T(rb.nb);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      for (int k = 1; k <= rb.nb; ++k) {
+        T sg = T(k) * inb;
+        T q[3], wp[3], s, c;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
+        T gw[3] = {T(0), T(0), T(0)};
+        bool hit = false;
+        for (int j = 0; j < no; ++j) {
+          Sphere4<T> S = sph[j];
+          T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
+          T d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 < S.reach * S.reach) {
+            T dist = c_sqrt(d2);
+            T viol = S.reach - dist;
+            T rr = w.sc * viol;
+            coll += T(0.5) * rr * rr;
+            if (GRAD) {
+              T f = -w.rho_c * viol / dist;
+              gw[0] += f * dx; gw[1] += f * dy; gw[2] += f * dz;
+              hit = true;
+            }
+          }
+        }
+        if (GRAD && hit) {
+          G[i][0] += gw[0]; G[i][1] += gw[1]; G[i][2] += gw[2];
+          T mw[3];
+          cross(wp, gw, mw);
+          M[i][0] += mw[0]; M[i][1] += mw[1]; M[i][2] += mw[2];
+          T gl[3];
+          matTvec(ch.Rb[i], gw, gl);
+          T axs = sg * ch.ax[i], ays = sg * ch.ay[i];
+          T s3, cp;
+          seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
+          T dd[2][3], wl[2][3];
+          seg_local_derivs(axs, ays, s, c, s3, cp, sg * rb.L[i], dd, wl);
+          Dx[i] += sg * (gl[0] * dd[0][0] + gl[1] * dd[0][1] + gl[2] * dd[0][2]);
+          Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
+          if (PGRAD) DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
+        }
+      }
+    }
+  }
+  F += coll;
+  if (coll_out) *coll_out = coll;
+  // penalty rows on u: bounds, sum-zero, curvature
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+    F += T(0.5) * w.rho_eq * su * su;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T hi = u[3 * i + j] - rb.umax[i], lo = -rb.umax[i] - u[3 * i + j];
+      if (hi > T(0)) F += T(0.5) * w.rho_b * hi * hi;
+      if (lo > T(0)) F += T(0.5) * w.rho_b * lo * lo;
+    }
+    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
+      T vk = c_sqrt(ch.x[i]) - rb.thmax[i];
+      F += T(0.5) * w.rho_k * vk * vk;
+    }
+  }
+  if (!GRAD) return F;
+
+  // ---- reverse sweep ----
+  // force / moment (about the origin) of everything downstream, starting at the tip
+  T Fs[3] = {w.wp * r[0], w.wp * r[1], w.wp * r[2]};  // dF/dp = w_p^2 (p - p_t)
+  T gR[3];
+  if (kind == CR_TASK_IK5) {
+    // dF/d(rotation) = w_R^2 z_t x z for F = 1/2 w_R^2 |z - z_t|^2
+    T z[3] = {ch.R[2], ch.R[5], ch.R[8]};
+    T zt[3] = {tg.R[0], tg.R[1], tg.R[2]};
+    T cz[3];
+    cross(zt, z, cz);
+    gR[0] = w.wR2 * cz[0]; gR[1] = w.wR2 * cz[1]; gR[2] = w.wR2 * cz[2];
+  } else {
+    // dF/d(rotation) = w_R^2 R e (the inverse right Jacobian leaves e unchanged)
+    T re[3];
+    matvec(ch.R, e, re);
+    gR[0] = w.wR2 * re[0]; gR[1] = w.wR2 * re[1]; gR[2] = w.wR2 * re[2];
+  }
+  T Ms[3];
+  cross(ch.p, Fs, Ms);
+  Ms[0] += gR[0]; Ms[1] += gR[1]; Ms[2] += gR[2];
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    T Pend[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Pend[a] = (i == N - 1) ? ch.p[a] : ch.pb[(i + 1 < N) ? i + 1 : i][a];
+    T PF[3];
+    cross(Pend, Fs, PF);
+    T Mp[3] = {Ms[0] - PF[0], Ms[1] - PF[1], Ms[2] - PF[2]};
+    T Fl[3], Ml[3];
+    matTvec(ch.Rb[i], Fs, Fl);
+    matTvec(ch.Rb[i], Mp, Ml);
+    T s3, cp;
+    seg_deriv(ch.x[i], ch.s[i], ch.c[i], s3, cp);
+    T dd[2][3], wl[2][3];
+    seg_local_derivs(ch.ax[i], ch.ay[i], ch.s[i], ch.c[i], s3, cp, rb.L[i], dd, wl);
+    T gx = Fl[0] * dd[0][0] + Fl[1] * dd[0][1] + Fl[2] * dd[0][2] + Ml[0] * wl[0][0] +
+           Ml[1] * wl[0][1] + Ml[2] * wl[0][2] + Dx[i];
+    T gy = Fl[0] * dd[1][0] + Fl[1] * dd[1][1] + Fl[2] * dd[1][2] + Ml[0] * wl[1][0] +
+           Ml[1] * wl[1][1] + Ml[2] * wl[1][2] + Dy[i];
+    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
+      T th = c_sqrt(ch.x[i]);
+      T f = w.rho_k * (th - rb.thmax[i]) / th;
+      gx += f * ch.ax[i];
+      gy += f * ch.ay[i];
+    }
+    T g0, g1, g2;
+    bend_grad_to_u(rb.K[i], gx, gy, g0, g1, g2);
+    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+    T geq = w.rho_eq * su;
+    T gj[3] = {g0, g1, g2};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T uj = u[3 * i + j];
+      T hi = uj - rb.umax[i], lo = -rb.umax[i] - uj;
+      T gb = (hi > T(0) ? w.rho_b * hi : T(0)) - (lo > T(0) ? w.rho_b * lo : T(0));
+      gu[3 * i + j] = gj[j] + geq + gb;
+    }
+    if (PGRAD) {
+      // dF/dL_i: translation d_i = L (...) scales with L; own samples q scale with L too
+      T di[3] = {rb.L[i] * ch.c[i] * ch.ax[i], rb.L[i] * ch.c[i] * ch.ay[i], rb.L[i] * ch.s[i]};
+      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / rb.L[i] + DL[i];
+      // dF/dr_c,i: a = K(...) with K = -2/(3 r_c) so da/dr_c = -a / r_c
+      grc[i] = -(ch.ax[i] * gx + ch.ay[i] * gy) / rb.rc[i];
+    }
+    Fs[0] += G[i][0]; Fs[1] += G[i][1]; Fs[2] += G[i][2];
+    Ms[0] += M[i][0]; Ms[1] += M[i][1]; Ms[2] += M[i][2];
+  }
+  return F;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tip Jacobian (world twists of every segment)
+// ------------------------------------------------------------------------------------------------
+// tw[i][k] = (v, w): a point p rigidly downstream of segment i moves by v + w x p per unit da_k.
+template <typename T, int N>
+CR_HD void segment_twists(const RobotK<T>& rb, const Chain<T, N>& ch, T (&tv)[N][2][3], T (&tw)[N][2][3]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T s3, cp;
+    seg_deriv(ch.x[i], ch.s[i], ch.c[i], s3, cp);
+    T dd[2][3], wl[2][3];
+    seg_local_derivs(ch.ax[i], ch.ay[i], ch.s[i], ch.c[i], s3, cp, rb.L[i], dd, wl);
+    T Pend[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Pend[a] = (i == N - 1) ? ch.p[a] : ch.pb[(i + 1 < N) ? i + 1 : i][a];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      T wv[3], dv[3];
+      matvec(ch.Rb[i], wl[k], wv);
+      matvec(ch.Rb[i], dd[k], dv);
+      T wP[3];
+      cross(wv, Pend, wP);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        tw[i][k][a] = wv[a];
+        tv[i][k][a] = dv[a] - wP[a];
+      }
+    }
+  }
+}
+
+// Tip Jacobian in u-space: Jp[a][q] = dp_a/du_q, Jw[a][q] = world angular velocity.
+template <typename T, int N>
+CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3 * N], T (&Jw)[3][3 * N]) {
+  T tv[N][2][3], tw[N][2][3];
+  segment_twists(rb, ch, tv, tw);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T jp[2][3], jw[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      T wp[3];
+      cross(tw[i][k], ch.p, wp);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        jp[k][a] = tv[i][k][a] + wp[a];
+        jw[k][a] = tw[i][k][a];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      bend_grad_to_u(rb.K[i], jp[0][a], jp[1][a], Jp[a][3 * i], Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
+      bend_grad_to_u(rb.K[i], jw[0][a], jw[1][a], Jw[a][3 * i], Jw[a][3 * i + 1], Jw[a][3 * i + 2]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// LM normal equations of an IK state: A = J^T J (packed lower), g = J^T r, F = 1/2 |r|^2.
+// J and r in T; accumulation in TA.
+// ------------------------------------------------------------------------------------------------
+CR_HD constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+template <typename TA, int D, typename T>
+CR_HD void rank1(TA (&A)[D * (D + 1) / 2], TA (&g)[D], const T (&j)[D], T r) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TA ja = TA(j[a]);
+    g[a] += ja * TA(r);
+#pragma unroll
+    for (int b = 0; b <= a; ++b) A[tri(a, b)] += ja * TA(j[b]);
+  }
+}
+
+template <typename T, typename TA, int N, bool OBST>
+CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+                       const Sphere4<T>* sph, int no, const T (&u)[3 * N],
+                       TA (&A)[3 * N * (3 * N + 1) / 2], TA (&g)[3 * N]) {
+  constexpr int D = 3 * N;
+#pragma unroll
+  for (int a = 0; a < D * (D + 1) / 2; ++a) A[a] = TA(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) g[a] = TA(0);
+  Chain<T, N> ch;
+  chain_forward(rb, u, ch);
+  T r[6], e[3], ang, sn, cs;
+  pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
+  T F = T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  T tv[N][2][3], tw[N][2][3];
+  segment_twists(rb, ch, tv, tw);
+  // tip Jacobian in u-space
+  T Jp[3][D], Jw[3][D];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T wp0[3], wp1[3];
+      cross(tw[i][0], ch.p, wp0);
+      cross(tw[i][1], ch.p, wp1);
+      bend_grad_to_u(rb.K[i], tv[i][0][a] + wp0[a], tv[i][1][a] + wp1[a], Jp[a][3 * i],
+                     Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
+      bend_grad_to_u(rb.K[i], tw[i][0][a], tw[i][1][a], Jw[a][3 * i], Jw[a][3 * i + 1],
+                     Jw[a][3 * i + 2]);
+    }
+  }
+  // position rows
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T jr[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) jr[q] = w.wp * Jp[a][q];
+    rank1<TA, D>(A, g, jr, r[a]);
+  }
+  // rotation rows
+  T Mrot[3][3];  // rows of d e / d(world rotation)
+  if (kind == CR_TASK_IK5) {
+    // d(z - z_t) = w x z = -[z]x w
+    T z0 = ch.R[2], z1 = ch.R[5], z2 = ch.R[8];
+    Mrot[0][0] = T(0);  Mrot[0][1] = z2;    Mrot[0][2] = -z1;
+    Mrot[1][0] = -z2;   Mrot[1][1] = T(0);  Mrot[1][2] = z0;
+    Mrot[2][0] = z1;    Mrot[2][1] = -z0;   Mrot[2][2] = T(0);
+  } else {
+    // de = J_r^-1(e) R^T dw, J_r^-1(e) = I + [e]x/2 + beta [e]x^2
+    T be = log_beta(ang);
+    T E2[3][3] = {{-(e[1] * e[1] + e[2] * e[2]), e[0] * e[1], e[0] * e[2]},
+                  {e[0] * e[1], -(e[0] * e[0] + e[2] * e[2]), e[1] * e[2]},
+                  {e[0] * e[2], e[1] * e[2], -(e[0] * e[0] + e[1] * e[1])}};
+    T Jr[3][3] = {{T(1) + be * E2[0][0], T(-0.5) * e[2] + be * E2[0][1], T(0.5) * e[1] + be * E2[0][2]},
+                  {T(0.5) * e[2] + be * E2[1][0], T(1) + be * E2[1][1], T(-0.5) * e[0] + be * E2[1][2]},
+                  {T(-0.5) * e[1] + be * E2[2][0], T(0.5) * e[0] + be * E2[2][1], T(1) + be * E2[2][2]}};
+    // Mrot = Jr R^T
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        Mrot[a][b] = Jr[a][0] * ch.R[3 * b] + Jr[a][1] * ch.R[3 * b + 1] + Jr[a][2] * ch.R[3 * b + 2];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T jr[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+      jr[q] = w.wR * (Mrot[a][0] * Jw[0][q] + Mrot[a][1] * Jw[1][q] + Mrot[a][2] * Jw[2][q]);
+    rank1<TA, D>(A, g, jr, r[3 + a]);
+  }
+  // bounds (single-entry rows), sum-zero (segment block of ones), curvature (segment rank-1)
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+    F += T(0.5) * w.rho_eq * su * su;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      int q = 3 * i + j;
+      g[q] += TA(w.rho_eq * su);
+#pragma unroll
+      for (int j2 = 0; j2 <= j; ++j2) A[tri(q, 3 * i + j2)] += TA(w.rho_eq);
+      T hi = u[q] - rb.umax[i], lo = -rb.umax[i] - u[q];
+      if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; g[q] += TA(w.rho_b * hi); A[tri(q, q)] += TA(w.rho_b); }
+      if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; g[q] -= TA(w.rho_b * lo); A[tri(q, q)] += TA(w.rho_b); }
+    }
+    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
+      T th = c_sqrt(ch.x[i]);
+      T vk = th - rb.thmax[i];
+      F += T(0.5) * w.rho_k * vk * vk;
+      T jx = w.sk * ch.ax[i] / th, jy = w.sk * ch.ay[i] / th;
+      T j0, j1, j2;
+      bend_grad_to_u(rb.K[i], jx, jy, j0, j1, j2);
+      T jj[3] = {j0, j1, j2};
+      T rr = w.sk * vk;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        g[3 * i + a] += TA(jj[a] * rr);
+#pragma unroll
+        for (int b = 0; b <= a; ++b) A[tri(3 * i + a, 3 * i + b)] += TA(jj[a] * jj[b]);
+      }
+    }
+  }
+  if (OBST && no > 0) {
+    const T inb = T(1) / T(rb.nb);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      for (int k = 1; k <= rb.nb; ++k) {
+        T sg = T(k) * inb;
+        T q[3], wp[3], s, c;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
+        for (int jsp = 0; jsp < no; ++jsp) {
+          Sphere4<T> S = sph[jsp];
+          T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
+          T d2 = dx * dx + dy * dy + dz * dz;
+          if (!(d2 < S.reach * S.reach)) continue;
+          T dist = c_sqrt(d2);
+          T viol = S.reach - dist;
+          T rr = w.sc * viol;
+          F += T(0.5) * rr * rr;
+          T nh[3] = {dx / dist, dy / dist, dz / dist};
+          // d r / d w = -sqrt(rho_c) n
+          T jr[D];
+#pragma unroll
+          for (int qq = 0; qq < D; ++qq) jr[qq] = T(0);
+#pragma unroll
+          for (int l = 0; l < N; ++l) {
+            if (l > i) break;
+            T ga[2];
+            if (l < i) {
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) {
+                T wx[3];
+                cross(tw[l][kk], wp, wx);
+                ga[kk] = -w.sc * (nh[0] * (tv[l][kk][0] + wx[0]) + nh[1] * (tv[l][kk][1] + wx[1]) +
+                                  nh[2] * (tv[l][kk][2] + wx[2]));
+              }
+            } else {
+              T s3, cp;
+              seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
+              T dd[2][3], wl[2][3];
+              seg_local_derivs(sg * ch.ax[i], sg * ch.ay[i], s, c, s3, cp, sg * rb.L[i], dd, wl);
+              T nl[3];
+              matTvec(ch.Rb[i], nh, nl);
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk)
+                ga[kk] = -w.sc * sg * (nl[0] * dd[kk][0] + nl[1] * dd[kk][1] + nl[2] * dd[kk][2]);
+            }
+            bend_grad_to_u(rb.K[l], ga[0], ga[1], jr[3 * l], jr[3 * l + 1], jr[3 * l + 2]);
+          }
+          rank1<TA, D>(A, g, jr, rr);
+        }
+      }
+    }
+  }
+  return F;
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 Cholesky of a packed lower-triangular matrix and the two triangular solves.
+// ------------------------------------------------------------------------------------------------
+template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2]) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    double s = A[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; ++k) s -= A[tri(j, k)] * A[tri(j, k)];
+    if (!(s > 0.0)) return false;
+    double ljj = sqrt(s);
+    double inv = 1.0 / ljj;
+    A[tri(j, j)] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < D; ++i) {
+      double t = A[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) t -= A[tri(i, k)] * A[tri(j, k)];
+      A[tri(i, j)] = t * inv;
+    }
+  }
+  return true;
+}
+
+template <int D> CR_HD void cholesky_solve(const double (&Lm)[D * (D + 1) / 2], double (&x)[D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= Lm[tri(i, k)] * x[k];
+    x[i] = s / Lm[tri(i, i)];
+  }
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    double s = x[i];
+#pragma unroll
+    for (int k = i + 1; k < D; ++k) s -= Lm[tri(k, i)] * x[k];
+    x[i] = s / Lm[tri(i, i)];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Projection of one segment onto {|u_j| <= b, sum u_j = 0}: u_j = clamp(v_j - tau, -b, b), with
+// tau the root of g(tau) = sum_j clamp(v_j - tau, -b, b); g is non-increasing and piecewise linear
+// with breakpoints v_j -/+ b, so tau lies between the largest breakpoint with g >= 0 and the
+// smallest with g <= 0 and follows by linear interpolation.
+// ------------------------------------------------------------------------------------------------
+template <typename T> CR_HD T clampb(T v, T b) { return c_min(b, c_max(-b, v)); }
+
+template <typename T> CR_HD void project3(T v0, T v1, T v2, T b, T& u0, T& u1, T& u2) {
+  T bp[6] = {v0 - b, v0 + b, v1 - b, v1 + b, v2 - b, v2 + b};
+  T ta = T(-1e30), tb = T(1e30), ga = T(0), gb = T(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    T t = bp[k];
+    T gv = clampb(v0 - t, b) + clampb(v1 - t, b) + clampb(v2 - t, b);
+    if (gv >= T(0) && t > ta) { ta = t; ga = gv; }
+    if (gv <= T(0) && t < tb) { tb = t; gb = gv; }
+  }
+  T tau = (ga == gb) ? ta : ta + ga * (tb - ta) / (ga - gb);
+  u0 = clampb(v0 - tau, b);
+  u1 = clampb(v1 - tau, b);
+  u2 = clampb(v2 - tau, b);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Counter-based seeds: SplitMix64 (Steele, Lea, Flood 2014), output k from state s0 is
+// mix(s0 + k * 0x9E3779B97F4A7C15). A seed is uniform on each segment's hexagon: rhombus
+// k = floor(3 U0), then U1 V_2k + U2 V_2k+2 with V the hexagon vertices in cyclic order.
+// ------------------------------------------------------------------------------------------------
+CR_HD uint64_t splitmix64_at(uint64_t s0, uint64_t k) {
+  uint64_t z = s0 + k * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+CR_HD double u01(uint64_t z) { return (double)(z >> 11) * (1.0 / 9007199254740992.0); }
+CR_HD uint64_t seed_counter(uint64_t p, uint64_t s, uint64_t a, uint64_t i, uint64_t w) {
+  return ((((p * 65536ULL + s) * 8ULL + a) * 8ULL + i) * 4ULL + w) + 1ULL;
+}
+
+// Hexagon vertices in cyclic order, as signs of b: (b,0,-b), (b,-b,0), (0,-b,b), (-b,0,b), (-b,b,0), (0,b,-b).
+CR_HD int hex_sign(int v, int j) {
+  // table packed as 2-bit codes: 0 -> 0, 1 -> +1, 2 -> -1
+  const int code[6] = {0x21, 0x09, 0x18, 0x12, 0x06, 0x24};  // bits (j=0: 1:0, j=1: 3:2, j=2: 5:4)
+  int c = (code[v] >> (2 * j)) & 3;
+  return c == 1 ? 1 : (c == 2 ? -1 : 0);
+}
+
+// FP64, IEEE round-to-nearest without contraction (bitwise-reproducible against a CPU double
+// implementation of the same formula).
+CR_HD void hexagon_point(double b, double U0, double U1, double U2, double (&u)[3]) {
+  int k = (int)__dmul_rn(3.0, U0);
+  if (k > 2) k = 2;
+  int va = 2 * k, vb = (2 * k + 2) % 6;
+  double ab = __dmul_rn(U1, b), bb = __dmul_rn(U2, b);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    int sa = hex_sign(va, j), sb = hex_sign(vb, j);
+    double ta = sa == 0 ? 0.0 : (sa > 0 ? ab : -ab);
+    double tb = sb == 0 ? 0.0 : (sb > 0 ? bb : -bb);
+    u[j] = __dadd_rn(ta, tb);
+  }
+}
+
+template <typename T, int N>
+CR_HD void draw_seed(uint64_t key, uint64_t p, uint64_t s, int attempt, const double (&umax)[NMAX],
+                     T (&u)[3 * N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double U0 = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 0)));
+    double U1 = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 1)));
+    double U2 = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 2)));
+    double uu[3];
+    hexagon_point(umax[i], U0, U1, U2, uu);
+    u[3 * i] = T(uu[0]);
+    u[3 * i + 1] = T(uu[1]);
+    u[3 * i + 2] = T(uu[2]);
+  }
+}
+
+// Does any backbone sample of state u come within reach of a sphere?
+template <typename T, int N>
+CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, const T (&u)[3 * N]) {
+  Chain<T, N> ch;
+  chain_forward(rb, u, ch);
+  const T inb = T(1) / T(rb.nb);
+  for (int i = 0; i < N; ++i)
+    for (int k = 1; k <= rb.nb; ++k) {
+      T q[3], wp[3], s, c;
+      backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, wp, s, c);
+      for (int j = 0; j < no; ++j) {
+        Sphere4<T> S = sph[j];
+        T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
+        if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
+      }
+    }
+  return false;
+}
+
+}  // namespace crk

@@ -1,0 +1,5 @@
+// FP32 instantiation of the kinematics / cost kernels.
+#include "cr_eval_impl.cuh"
+namespace crk {
+CR_EVAL_INSTANTIATE(, float)
+}

@@ -1,0 +1,5 @@
+// FP64 instantiation of the kinematics / cost kernels.
+#include "cr_eval_impl.cuh"
+namespace crk {
+CR_EVAL_INSTANTIATE(, double)
+}

@@ -1,0 +1,187 @@
+// Kernels of the kinematics and cost entry points (cr_fk, cr_fk_jac, cr_cost_grad,
+// cr_reduce_rows). One thread per state; states are structure-of-arrays [q][B] so that the
+// per-component loads and stores of a warp are coalesced.
+#pragma once
+
+#include "cr_host.h"
+
+namespace crk {
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_fk(RobotK<T> rb, const T* __restrict__ u, int64_t B,
+                                             T* __restrict__ Tout, T* __restrict__ bb) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  T uu[3 * N];
+#pragma unroll
+  for (int q = 0; q < 3 * N; ++q) uu[q] = u[q * B + b];
+  Chain<T, N> ch;
+  chain_forward(rb, uu, ch);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Tout[a * B + b] = ch.R[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Tout[(9 + a) * B + b] = ch.p[a];
+  if (bb) {
+    const T inb = T(1) / T(rb.nb);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      for (int k = 1; k <= rb.nb; ++k) {
+        T q[3], w[3], s, c;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, w, s, c);
+        int64_t row = (int64_t)(i * rb.nb + (k - 1)) * 3;
+        bb[(row + 0) * B + b] = w[0];
+        bb[(row + 1) * B + b] = w[1];
+        bb[(row + 2) * B + b] = w[2];
+      }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) k_fk_jac(RobotK<T> rb, const T* __restrict__ u, int64_t B,
+                                                 T* __restrict__ J) {
+  constexpr int D = 3 * N;
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  T uu[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) uu[q] = u[q * B + b];
+  Chain<T, N> ch;
+  chain_forward(rb, uu, ch);
+  T Jp[3][D], Jw[3][D];
+  tip_jacobian(rb, ch, Jp, Jw);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      J[((int64_t)a * D + q) * B + b] = Jp[a][q];
+      J[((int64_t)(3 + a) * D + q) * B + b] = Jw[a][q];
+    }
+}
+
+// MODE 0: cost only; 1: cost + dF/du; 2: cost + dF/du + dF/d(L, r_c)
+template <typename T, int N, bool OBST, int MODE>
+__global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, int kind,
+                                                    const double* __restrict__ targets, int64_t P,
+                                                    int S, const double* __restrict__ spheres, int no,
+                                                    const T* __restrict__ u, int64_t B, T* cost,
+                                                    T* coll, T* gu, T* gp) {
+  constexpr int D = 3 * N;
+  extern __shared__ unsigned char smem_raw[];
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  if (OBST) {
+    stage_spheres(spheres, no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  T uu[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) uu[q] = u[q * B + b];
+  TargetK<T> tg = load_target<T>(targets, P, b / S, kind);
+  T g[D], gL[N], grc[N], cl;
+  T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2)>(rb, w, kind, tg, sph, no, uu, g, gL, grc, &cl);
+  cost[b] = F;
+  if (coll) coll[b] = cl;
+  if (MODE >= 1) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) gu[q * B + b] = g[q];
+  }
+  if (MODE >= 2) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      gp[(int64_t)i * B + b] = gL[i];
+      gp[(int64_t)(N + i) * B + b] = grc[i];
+    }
+  }
+}
+
+// Deterministic row sums: one block per row, fixed per-thread strides and a fixed tree order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_rows(const T* __restrict__ x, int64_t B, double* out) {
+  __shared__ double part[256];
+  const T* row = x + (int64_t)blockIdx.x * B;
+  double s = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) s += double(row[b]);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) part[threadIdx.x] += part[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = part[0];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host launchers (instantiated for float and double in separate translation units)
+// ------------------------------------------------------------------------------------------------
+struct EvalArgs {
+  cr_robot robot;
+  cr_scene scene;
+  cr_task task;
+  const void* u;
+  int64_t B;
+  void *cost, *coll, *gu, *gp, *Tout, *bb, *J;
+  cudaStream_t stream;
+};
+
+template <typename T> cr_status launch_fk(const EvalArgs& a);
+template <typename T> cr_status launch_fk_jac(const EvalArgs& a);
+template <typename T> cr_status launch_cost_grad(const EvalArgs& a);
+template <typename T> cr_status launch_reduce_rows(const void* x, int64_t rows, int64_t B, double* out,
+                                                   cudaStream_t s);
+
+inline unsigned grid_of(int64_t B, int bs) { return (unsigned)((B + bs - 1) / bs); }
+
+template <typename T, int N> void fk_n(const EvalArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  k_fk<T, N><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.Tout, (T*)a.bb);
+}
+template <typename T, int N> void fk_jac_n(const EvalArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  k_fk_jac<T, N><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.J);
+}
+template <typename T, int N> void cost_grad_n(const EvalArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  WeightsK<T> w = crh::weights_k<T>(a.task.w);
+  int no = a.scene.n_o;
+  int mode = a.gp ? 2 : (a.gu ? 1 : 0);
+  size_t sm = (size_t)no * sizeof(Sphere4<T>);
+  unsigned g = grid_of(a.B, 128);
+#define CR_CG(OB, MO)                                                                              \
+  k_cost_grad<T, N, OB, MO><<<g, 128, sm, a.stream>>>(rb, w, a.task.kind, a.task.targets,          \
+                                                       a.task.n_targets, a.task.seeds_per_target,  \
+                                                       a.scene.spheres, no, (const T*)a.u, a.B,    \
+                                                       (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp)
+  if (no > 0) {
+    if (mode == 0) CR_CG(true, 0); else if (mode == 1) CR_CG(true, 1); else CR_CG(true, 2);
+  } else {
+    if (mode == 0) CR_CG(false, 0); else if (mode == 1) CR_CG(false, 1); else CR_CG(false, 2);
+  }
+#undef CR_CG
+}
+
+template <typename T> cr_status launch_fk(const EvalArgs& a) {
+  CR_DISPATCH_NT(a.robot.n, fk_n, T, a);
+  return crh::check_launch("cr_fk");
+}
+template <typename T> cr_status launch_fk_jac(const EvalArgs& a) {
+  CR_DISPATCH_NT(a.robot.n, fk_jac_n, T, a);
+  return crh::check_launch("cr_fk_jac");
+}
+template <typename T> cr_status launch_cost_grad(const EvalArgs& a) {
+  CR_DISPATCH_NT(a.robot.n, cost_grad_n, T, a);
+  return crh::check_launch("cr_cost_grad");
+}
+template <typename T>
+cr_status launch_reduce_rows(const void* x, int64_t rows, int64_t B, double* out, cudaStream_t s) {
+  k_reduce_rows<T><<<(unsigned)rows, 256, 0, s>>>((const T*)x, B, out);
+  return crh::check_launch("cr_reduce_rows");
+}
+
+#define CR_EVAL_INSTANTIATE(EXT, T)                                                              \
+  EXT template cr_status launch_fk<T>(const EvalArgs&);                                          \
+  EXT template cr_status launch_fk_jac<T>(const EvalArgs&);                                      \
+  EXT template cr_status launch_cost_grad<T>(const EvalArgs&);                                   \
+  EXT template cr_status launch_reduce_rows<T>(const void*, int64_t, int64_t, double*, cudaStream_t);
+
+}  // namespace crk

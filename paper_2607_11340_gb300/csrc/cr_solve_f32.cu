@@ -1,0 +1,5 @@
+// FP32-bulk instantiation of the solver kernels (FP64 Cholesky and acceptance inside).
+#include "cr_solve_impl.cuh"
+namespace crk {
+CR_SOLVE_INSTANTIATE(, float)
+}

@@ -1,0 +1,5 @@
+// FP64 instantiation of the solver kernels.
+#include "cr_solve_impl.cuh"
+namespace crk {
+CR_SOLVE_INSTANTIATE(, double)
+}

@@ -1,0 +1,727 @@
+// Kernels of Algorithm 1 (beam-search IK) and of the standalone solver steps.
+//
+//  k_ik_stage1 : one CTA per target, one thread per seed. SampleSeeds (counter-based), k_init
+//                projected-gradient steps with the state in registers, then SelectTop by warp 0
+//                with warp shuffles over the CTA's candidates staged in shared memory.
+//  k_ik_refine : one thread per selected candidate: k_final LM iterations (J, r and J^T J in the
+//                bulk precision; Cholesky, solve and gain ratio in FP64), then the FP64
+//                re-evaluation of cost, pose error, limits and clearance.
+//  k_ik_argmin : one thread per target: argmin of the FP64 cost over its candidates.
+#pragma once
+
+#include <limits.h>
+
+#include "cr_host.h"
+
+namespace crk {
+
+// ------------------------------------------------------------------------------------------------
+// One projected-gradient step (stage one): trial u' = Pi(u - alpha g / |g|); accept iff F(u') < F(u).
+// ------------------------------------------------------------------------------------------------
+template <typename T, int N, bool OBST>
+CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+                   const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha) {
+  constexpr int D = 3 * N;
+  T gn2 = T(0);
+#pragma unroll
+  for (int q = 0; q < D; ++q) gn2 += g[q] * g[q];
+  T scale = gn2 > T(0) ? alpha / c_sqrt(gn2) : T(0);
+  T u1[D];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    project3(u[3 * i] - scale * g[3 * i], u[3 * i + 1] - scale * g[3 * i + 1],
+             u[3 * i + 2] - scale * g[3 * i + 2], rb.umax[i], u1[3 * i], u1[3 * i + 1], u1[3 * i + 2]);
+  T g1[D], c1;
+  T F1 = eval_ik<T, N, OBST, true, false>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr, &c1);
+  if (F1 < F) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
+    F = F1;
+    coll = c1;
+    alpha *= T(1.25);
+  } else {
+    alpha *= T(0.5);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// One Levenberg-Marquardt iteration (Sec. IV-C); returns 1 if the step was accepted.
+// ------------------------------------------------------------------------------------------------
+template <typename T, int N, bool OBST>
+CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+                       const Sphere4<T>* sph, int no, T (&u)[3 * N], double& lam, double& nu, T& Fout) {
+  constexpr int D = 3 * N;
+  constexpr int DD = D * (D + 1) / 2;
+  double Ad[DD], Dg[D], dl[D];
+  T F;
+  {
+    T A[DD], g[D];
+    F = eval_ik_normal<T, T, N, OBST>(rb, w, kind, tg, sph, no, u, A, g);
+#pragma unroll
+    for (int a = 0; a < DD; ++a) Ad[a] = double(A[a]);
+#pragma unroll
+    for (int q = 0; q < D; ++q) dl[q] = double(g[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
+    Ad[tri(q, q)] += lam * Dg[q];
+  }
+  if (!cholesky_packed<D>(Ad)) {
+    lam *= nu;
+    nu *= 2.0;
+    Fout = F;
+    return 0;
+  }
+  double gd[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) { gd[q] = dl[q]; dl[q] = -dl[q]; }
+  cholesky_solve<D>(Ad, dl);
+  T un[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) un[q] = u[q] + T(dl[q]);
+  T dummy[D];
+  T Fn = eval_ik<T, N, OBST, false, false>(rb, w, kind, tg, sph, no, un, dummy, nullptr, nullptr, nullptr);
+  double pred = 0.0;
+#pragma unroll
+  for (int q = 0; q < D; ++q) pred += dl[q] * (lam * Dg[q] * dl[q] - gd[q]);
+  pred *= 0.5;
+  if (Fn < F) {
+    double rho = (double(F) - double(Fn)) / pred;
+    double t = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - t * t * t);
+    nu = 2.0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) u[q] = un[q];
+    Fout = Fn;
+    return 1;
+  }
+  lam *= nu;
+  nu *= 2.0;
+  Fout = F;
+  return 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// SelectTop by one warp: rank (cost, coll, index) ascending with non-finite keys last, skip
+// candidates within eps (max-norm) of a kept one, then fill up with the skipped ones in rank order.
+// u of candidate i, component q is at u[q * ustride + i].
+// ------------------------------------------------------------------------------------------------
+CR_HD bool key_less(float c1, float l1, int i1, float c2, float l2, int i2) {
+  if (c1 != c2) return c1 < c2;
+  if (l1 != l2) return l1 < l2;
+  return i1 < i2;
+}
+
+template <typename T>
+__device__ void warp_topk(const float* cost, const float* coll, const T* u, int64_t ustride, int D, int S,
+                          int K, T eps, int* sel, unsigned char* taken, int* skipped) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < S; i += 32) taken[i] = 0;
+  __syncwarp();
+  int kept = 0, nskip = 0;
+  for (int round = 0; round < S && kept < K; ++round) {
+    float bc = INFINITY, bl = INFINITY;
+    int bi = INT_MAX;
+    for (int i = lane; i < S; i += 32) {
+      if (taken[i]) continue;
+      float c = cost[i], l = coll[i];
+      c = isfinite(c) ? c : INFINITY;
+      l = isfinite(l) ? l : INFINITY;
+      if (key_less(c, l, i, bc, bl, bi)) { bc = c; bl = l; bi = i; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      float oc = __shfl_xor_sync(FULL, bc, off);
+      float ol = __shfl_xor_sync(FULL, bl, off);
+      int oi = __shfl_xor_sync(FULL, bi, off);
+      if (key_less(oc, ol, oi, bc, bl, bi)) { bc = oc; bl = ol; bi = oi; }
+    }
+    if (bi == INT_MAX) break;
+    bool dup = false;
+    if (lane < kept) {
+      int j = sel[lane];
+      T m = T(0);
+      for (int q = 0; q < D; ++q) m = c_max(m, c_fabs(u[q * ustride + bi] - u[q * ustride + j]));
+      dup = m < eps;
+    }
+    dup = __any_sync(FULL, dup);
+    if (lane == 0) {
+      taken[bi] = 1;
+      if (dup) skipped[nskip] = bi;
+      else sel[kept] = bi;
+    }
+    if (dup) ++nskip;
+    else ++kept;
+    __syncwarp();
+  }
+  for (int q = 0; kept < K && q < nskip; ++q, ++kept)
+    if (lane == 0) sel[kept] = skipped[q];
+  for (int k = kept; k < K; ++k)
+    if (lane == 0) sel[k] = -1;
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Kernel parameters
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct IkArgs {
+  int kind;
+  const double* targets;
+  int64_t P;
+  const double* spheres;
+  int no;
+  int S, K, k_init, k_final;
+  T alpha0, eps;
+  double lambda0, lim_tol, pos_tol, rot_tol;
+  double umax[NMAX];
+  uint64_t seed;
+  int64_t p0;
+  T* cand_u;          // [D][P*K] bulk precision
+  double* cand_u64;   // [D][P*K]
+  double* cand_F;     // [P*K]
+  double* cand_pos;
+  double* cand_rot;
+  unsigned char* cand_flag;
+  double* u_out;      // [D][P]
+  double* cost_out;
+  double* pos_out;
+  double* rot_out;
+  unsigned char* success;
+  int* status;
+};
+
+template <typename T> struct Stage1Smem {
+  static size_t bytes(int no, int S, int D) {
+    size_t b = (size_t)no * sizeof(Sphere4<T>);
+    b = (b + 15) & ~size_t(15);
+    b += (size_t)D * S * sizeof(T);
+    b += (size_t)S * 2 * sizeof(float) + (size_t)S * sizeof(int) + 32 * sizeof(int) + S;
+    return (b + 15) & ~size_t(15);
+  }
+};
+
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = a.S;
+  size_t off = (size_t)a.no * sizeof(Sphere4<T>);
+  off = (off + 15) & ~size_t(15);
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  T* su = reinterpret_cast<T*>(smem_raw + off);
+  off += (size_t)D * S * sizeof(T);
+  float* sF = reinterpret_cast<float*>(smem_raw + off);
+  float* sC = sF + S;
+  int* skipped = reinterpret_cast<int*>(sC + S);
+  int* sel = skipped + S;
+  unsigned char* taken = reinterpret_cast<unsigned char*>(sel + 32);
+  if (OBST) {
+    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t p = blockIdx.x;
+  const int s = threadIdx.x;
+  if (s < S) {
+    TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
+    T u[D], g[D], coll = T(0);
+    draw_seed<T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.umax, u);
+    if (OBST && a.no > 0) {
+      for (int att = 1; att < 8; ++att) {
+        if (!state_collides<T, N>(rb, sph, a.no, u)) break;
+        draw_seed<T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.umax, u);
+      }
+    }
+    T F = eval_ik<T, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+    T alpha = a.alpha0;
+    for (int it = 0; it < a.k_init; ++it) pg_step<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+    sF[s] = float(F);
+    sC[s] = float(coll);
+#pragma unroll
+    for (int q = 0; q < D; ++q) su[q * S + s] = u[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) warp_topk<T>(sF, sC, su, S, D, S, a.K, a.eps, sel, taken, skipped);
+  __syncthreads();
+  const int64_t ldc = a.P * a.K;
+  for (int t = threadIdx.x; t < a.K * D; t += blockDim.x) {
+    int k = t / D, q = t % D;
+    int j = sel[k];
+    a.cand_u[q * ldc + p * a.K + k] = j >= 0 ? su[q * S + j] : T(NAN);
+  }
+}
+
+// FP64 acceptance of one state: cost, pose errors, limit and clearance flags.
+template <int N, bool OBST>
+CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, int kind,
+                         const TargetK<double>& tg, const Sphere4<double>* sph, int no,
+                         const double (&u)[3 * N], double lim_tol, double& pos, double& rot,
+                         unsigned char& flags) {
+  double dummy[3 * N];
+  double F = eval_ik<double, N, OBST, false, false>(rb, w, kind, tg, sph, no, u, dummy, nullptr, nullptr, nullptr);
+  Chain<double, N> ch;
+  chain_forward(rb, u, ch);
+  double dx = ch.p[0] - tg.p[0], dy = ch.p[1] - tg.p[1], dz = ch.p[2] - tg.p[2];
+  pos = sqrt(dx * dx + dy * dy + dz * dz);
+  if (kind == CR_TASK_IK5) {
+    double z[3] = {ch.R[2], ch.R[5], ch.R[8]}, zt[3] = {tg.R[0], tg.R[1], tg.R[2]}, cz[3];
+    cross(z, zt, cz);
+    rot = atan2(sqrt(dot3(cz, cz)), dot3(z, zt));
+  } else {
+    double E[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        E[3 * i + j] = tg.R[i] * ch.R[j] + tg.R[3 + i] * ch.R[3 + j] + tg.R[6 + i] * ch.R[6 + j];
+    double e[3], sn, cs;
+    so3_log(E, e, sn, cs);
+    rot = sqrt(dot3(e, e));
+  }
+  bool lim = true;
+  for (int i = 0; i < N; ++i) {
+    double su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+    if (fabs(su) > lim_tol) lim = false;
+    for (int j = 0; j < 3; ++j)
+      if (fabs(u[3 * i + j]) > rb.umax[i] + lim_tol) lim = false;
+    if (sqrt(ch.x[i]) > rb.thmax[i] + 1e-6) lim = false;
+  }
+  bool free = true;
+  if (OBST && no > 0) {
+    const double inb = 1.0 / rb.nb;
+    for (int i = 0; i < N && free; ++i)
+      for (int k = 1; k <= rb.nb && free; ++k) {
+        double q[3], wp[3], s, c;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], k * inb, q, wp, s, c);
+        for (int j = 0; j < no; ++j) {
+          double ddx = wp[0] - sph[j].x, ddy = wp[1] - sph[j].y, ddz = wp[2] - sph[j].z;
+          double r = sph[j].reach - w.delta;
+          if (ddx * ddx + ddy * ddy + ddz * ddz < r * r) { free = false; break; }
+        }
+      }
+  }
+  flags = (unsigned char)((lim ? 1 : 0) | (free ? 2 : 0));
+  return F;
+}
+
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
+                                                    WeightsK<double> wd, IkArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
+  if (OBST) {
+    stage_spheres(a.spheres, a.no, rbd, wd.delta, sphd);
+    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t PK = a.P * a.K;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= PK) return;
+  const int64_t p = c / a.K;
+  T u[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) u[q] = a.cand_u[q * PK + c];
+  bool valid = c_finite(u[0]);
+  if (valid) {
+    TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
+    double lam = a.lambda0, nu = 2.0;
+    T F;
+    for (int it = 0; it < a.k_final; ++it) lm_iteration<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+  }
+  double ud[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) ud[q] = double(u[q]);
+  double pos = NAN, rot = NAN, F = NAN;
+  unsigned char flags = 0;
+  if (valid) {
+    TargetK<double> tgd = load_target<double>(a.targets, a.P, p, a.kind);
+    F = accept_fp64<N, OBST>(rbd, wd, a.kind, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+  }
+#pragma unroll
+  for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
+  a.cand_F[c] = F;
+  a.cand_pos[c] = pos;
+  a.cand_rot[c] = rot;
+  a.cand_flag[c] = flags;
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_ik_argmin(int64_t P, int K, double pos_tol, double rot_tol,
+                                                    const double* cand_u64, const double* cand_F,
+                                                    const double* cand_pos, const double* cand_rot,
+                                                    const unsigned char* cand_flag, double* u_out,
+                                                    double* cost_out, double* pos_out, double* rot_out,
+                                                    unsigned char* success, int* status) {
+  constexpr int D = 3 * N;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int64_t PK = P * K;
+  int best = -1;
+  double bF = INFINITY;
+  for (int k = 0; k < K; ++k) {
+    double F = cand_F[p * K + k];
+    if (isfinite(F) && F < bF) { bF = F; best = k; }
+  }
+  if (best < 0) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) u_out[q * P + p] = NAN;
+    cost_out[p] = NAN;
+    pos_out[p] = NAN;
+    rot_out[p] = NAN;
+    success[p] = 0;
+    atomicOr(status, 1 << CR_ENONFINITE);
+    return;
+  }
+  const int64_t c = p * K + best;
+#pragma unroll
+  for (int q = 0; q < D; ++q) u_out[q * P + p] = cand_u64[q * PK + c];
+  cost_out[p] = bF;
+  double pe = cand_pos[c], re = cand_rot[c];
+  pos_out[p] = pe;
+  rot_out[p] = re;
+  unsigned char f = cand_flag[c];
+  success[p] = (pe <= pos_tol && re <= rot_tol && (f & 1) && (f & 2)) ? 1 : 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Standalone steps: LM iterations, projected-gradient steps, seeds, SelectTop
+// ------------------------------------------------------------------------------------------------
+template <typename T> struct StepArgs {
+  int kind;
+  const double* targets;
+  int64_t P;
+  int S;
+  const double* spheres;
+  int no;
+  T* u;
+  int64_t B;
+  int iters;
+  double* lam;
+  double* nu;
+  double* F64;
+  int* acc;
+  T* alpha;
+  T* F;
+};
+
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  if (OBST) {
+    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  T u[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) u[q] = a.u[q * a.B + b];
+  TargetK<T> tg = load_target<T>(a.targets, a.P, b / a.S, a.kind);
+  double lam = a.lam[b], nu = a.nu[b];
+  int nacc = 0;
+  T F = T(0);
+  for (int it = 0; it < a.iters; ++it) nacc += lm_iteration<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+  if (a.iters == 0 || a.F64) {
+    T dummy[D];
+    F = eval_ik<T, N, OBST, false, false>(rb, w, a.kind, tg, sph, a.no, u, dummy, nullptr, nullptr, nullptr);
+  }
+#pragma unroll
+  for (int q = 0; q < D; ++q) a.u[q * a.B + b] = u[q];
+  a.lam[b] = lam;
+  a.nu[b] = nu;
+  if (a.F64) a.F64[b] = double(F);
+  if (a.acc) a.acc[b] = nacc;
+}
+
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  if (OBST) {
+    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  T u[D], g[D], coll;
+#pragma unroll
+  for (int q = 0; q < D; ++q) u[q] = a.u[q * a.B + b];
+  TargetK<T> tg = load_target<T>(a.targets, a.P, b / a.S, a.kind);
+  T F = eval_ik<T, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+  T alpha = a.alpha[b];
+  for (int it = 0; it < a.iters; ++it) pg_step<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+#pragma unroll
+  for (int q = 0; q < D; ++q) a.u[q * a.B + b] = u[q];
+  a.alpha[b] = alpha;
+  a.F[b] = F;
+}
+
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, const double* spheres, int no,
+                                                uint64_t key, int64_t p0, int64_t P, int S,
+                                                NmaxArr umax, T* u_out) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  if (OBST) {
+    stage_spheres(spheres, no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t PS = P * S;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= PS) return;
+  const int64_t p = i / S, s = i % S;
+  T u[D];
+  draw_seed<T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, 0, umax.v, u);
+  if (OBST && no > 0) {
+    for (int att = 1; att < 8; ++att) {
+      if (!state_collides<T, N>(rb, sph, no, u)) break;
+      draw_seed<T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, att, umax.v, u);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < D; ++q) u_out[q * PS + i] = u[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_topk(const float* cost, const float* coll, const T* u, int D, int64_t P,
+                                              int S, int K, T eps, int* idx_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* skipped = reinterpret_cast<int*>(smem_raw);
+  int* sel = skipped + S;
+  unsigned char* taken = reinterpret_cast<unsigned char*>(sel + 32);
+  const int64_t p = blockIdx.x;
+  warp_topk<T>(cost + p * S, coll + p * S, u + p * S, P * S, D, S, K, eps, sel, taken, skipped);
+  for (int k = threadIdx.x; k < K; k += 32) idx_out[p * K + k] = sel[k];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------------------
+struct SolveArgs {
+  cr_robot robot;
+  cr_scene scene;
+  cr_task task;
+  cr_ik_params prm;
+  void* ws;
+  crh::IkLayout lay;
+  double *u_out, *cost_out, *pos, *rot;
+  unsigned char* success;
+  // step entry points
+  void* u;
+  int64_t B;
+  int iters;
+  double *lam, *nu, *F64;
+  int* acc;
+  void *alpha, *F;
+  // seeds / topk
+  uint64_t key;
+  int64_t p0, P;
+  int S, K;
+  double eps;
+  const float *tk_cost, *tk_coll;
+  int* tk_idx;
+  int D;
+  cudaStream_t stream;
+};
+
+template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which);
+template <typename T> cr_status launch_lm_steps(const SolveArgs& a);
+template <typename T> cr_status launch_pg_steps(const SolveArgs& a);
+template <typename T> cr_status launch_seeds(const SolveArgs& a);
+template <typename T> cr_status launch_topk(const SolveArgs& a);
+
+inline unsigned grid1(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename K> cr_status set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return crh::fail(CR_ECUDA, "shared memory %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  return CR_OK;
+}
+
+template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
+  IkArgs<T> k;
+  const cr_ik_params& p = a.prm;
+  unsigned char* ws = (unsigned char*)a.ws;
+  k.kind = a.task.kind;
+  k.targets = a.task.targets;
+  k.P = a.task.n_targets;
+  k.spheres = a.scene.spheres;
+  k.no = a.scene.n_o;
+  k.S = p.S;
+  k.K = p.n_final;
+  k.k_init = p.k_init;
+  k.k_final = p.k_final;
+  k.alpha0 = T(p.alpha0);
+  k.eps = T(p.dedup_eps);
+  k.lambda0 = p.lambda0;
+  k.lim_tol = p.lim_tol;
+  k.pos_tol = p.pos_tol;
+  k.rot_tol = p.rot_tol;
+  for (int i = 0; i < NMAX; ++i) k.umax[i] = i < a.robot.n ? a.robot.u_max[i] : 0.0;
+  k.seed = p.seed;
+  k.p0 = p.p0;
+  k.cand_u = (T*)(ws + a.lay.cand_u);
+  k.cand_u64 = (double*)(ws + a.lay.cand_u64);
+  k.cand_F = (double*)(ws + a.lay.cand_F);
+  k.cand_pos = (double*)(ws + a.lay.cand_pos);
+  k.cand_rot = (double*)(ws + a.lay.cand_rot);
+  k.cand_flag = ws + a.lay.cand_flag;
+  k.u_out = a.u_out;
+  k.cost_out = a.cost_out;
+  k.pos_out = a.pos;
+  k.rot_out = a.rot;
+  k.success = a.success;
+  k.status = (int*)(ws + a.lay.status);
+  return k;
+}
+
+// which: 1 = stage one only, 2 = stage two only, 3 = both
+template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which) {
+  constexpr int D = 3 * N;
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  WeightsK<T> w = crh::weights_k<T>(a.task.w);
+  RobotK<double> rbd = crh::robot_k<double>(a.robot);
+  WeightsK<double> wd = crh::weights_k<double>(a.task.w);
+  IkArgs<T> k = ik_args<T>(a);
+  const int64_t P = k.P;
+  const int no = k.no;
+  const int threads = ((k.S + 31) / 32) * 32;
+  size_t sm1 = Stage1Smem<T>::bytes(no, k.S, D);
+  cr_status st;
+  if (which & 1) {
+  if (no > 0) {
+    if ((st = set_smem(k_ik_stage1<T, N, true>, sm1))) return st;
+    k_ik_stage1<T, N, true><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
+  } else {
+    if ((st = set_smem(k_ik_stage1<T, N, false>, sm1))) return st;
+    k_ik_stage1<T, N, false><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
+  }
+  if ((st = crh::check_launch("cr_solve_ik stage one"))) return st;
+  }
+  if (!(which & 2)) return CR_OK;
+  size_t sm2 = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<T>));
+  unsigned g2 = grid1(P * k.K, 128);
+  if (no > 0) k_ik_refine<T, N, true><<<g2, 128, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  else k_ik_refine<T, N, false><<<g2, 128, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  if ((st = crh::check_launch("cr_solve_ik refine"))) return st;
+  k_ik_argmin<N><<<grid1(P, 128), 128, 0, a.stream>>>(P, k.K, k.pos_tol, k.rot_tol, k.cand_u64, k.cand_F,
+                                                      k.cand_pos, k.cand_rot, k.cand_flag, k.u_out,
+                                                      k.cost_out, k.pos_out, k.rot_out, k.success, k.status);
+  return crh::check_launch("cr_solve_ik argmin");
+}
+
+template <typename T> StepArgs<T> step_args(const SolveArgs& a) {
+  StepArgs<T> k;
+  k.kind = a.task.kind;
+  k.targets = a.task.targets;
+  k.P = a.task.n_targets;
+  k.S = a.task.seeds_per_target;
+  k.spheres = a.scene.spheres;
+  k.no = a.scene.n_o;
+  k.u = (T*)a.u;
+  k.B = a.B;
+  k.iters = a.iters;
+  k.lam = a.lam;
+  k.nu = a.nu;
+  k.F64 = a.F64;
+  k.acc = a.acc;
+  k.alpha = (T*)a.alpha;
+  k.F = (T*)a.F;
+  return k;
+}
+
+template <typename T, int N> cr_status lm_steps_n(const SolveArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  WeightsK<T> w = crh::weights_k<T>(a.task.w);
+  StepArgs<T> k = step_args<T>(a);
+  size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
+  if (k.no > 0) k_lm_steps<T, N, true><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  else k_lm_steps<T, N, false><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  return crh::check_launch("cr_lm_step");
+}
+
+template <typename T, int N> cr_status pg_steps_n(const SolveArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  WeightsK<T> w = crh::weights_k<T>(a.task.w);
+  StepArgs<T> k = step_args<T>(a);
+  size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
+  if (k.no > 0) k_pg_steps<T, N, true><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  else k_pg_steps<T, N, false><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  return crh::check_launch("cr_pg_steps");
+}
+
+template <typename T, int N> cr_status seeds_n(const SolveArgs& a) {
+  RobotK<T> rb = crh::robot_k<T>(a.robot);
+  WeightsK<T> w = crh::weights_k<T>(a.task.w);
+  NmaxArr um;
+  for (int i = 0; i < NMAX; ++i) um.v[i] = i < a.robot.n ? a.robot.u_max[i] : 0.0;
+  int no = a.scene.n_o;
+  size_t sm = (size_t)no * sizeof(Sphere4<T>);
+  unsigned g = grid1(a.P * a.S, 128);
+  if (no > 0) k_seeds<T, N, true><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.key, a.p0, a.P, a.S, um, (T*)a.u);
+  else k_seeds<T, N, false><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.key, a.p0, a.P, a.S, um, (T*)a.u);
+  return crh::check_launch("cr_seeds");
+}
+
+template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which) {
+  switch (a.robot.n) {
+    case 1: return solve_ik_n<T, 1>(a, which);
+    case 2: return solve_ik_n<T, 2>(a, which);
+    case 3: return solve_ik_n<T, 3>(a, which);
+    case 4: return solve_ik_n<T, 4>(a, which);
+    case 5: return solve_ik_n<T, 5>(a, which);
+    default: return solve_ik_n<T, 6>(a, which);
+  }
+}
+template <typename T> cr_status launch_lm_steps(const SolveArgs& a) {
+  switch (a.robot.n) {
+    case 1: return lm_steps_n<T, 1>(a);
+    case 2: return lm_steps_n<T, 2>(a);
+    case 3: return lm_steps_n<T, 3>(a);
+    case 4: return lm_steps_n<T, 4>(a);
+    case 5: return lm_steps_n<T, 5>(a);
+    default: return lm_steps_n<T, 6>(a);
+  }
+}
+template <typename T> cr_status launch_pg_steps(const SolveArgs& a) {
+  switch (a.robot.n) {
+    case 1: return pg_steps_n<T, 1>(a);
+    case 2: return pg_steps_n<T, 2>(a);
+    case 3: return pg_steps_n<T, 3>(a);
+    case 4: return pg_steps_n<T, 4>(a);
+    case 5: return pg_steps_n<T, 5>(a);
+    default: return pg_steps_n<T, 6>(a);
+  }
+}
+template <typename T> cr_status launch_seeds(const SolveArgs& a) {
+  switch (a.robot.n) {
+    case 1: return seeds_n<T, 1>(a);
+    case 2: return seeds_n<T, 2>(a);
+    case 3: return seeds_n<T, 3>(a);
+    case 4: return seeds_n<T, 4>(a);
+    case 5: return seeds_n<T, 5>(a);
+    default: return seeds_n<T, 6>(a);
+  }
+}
+template <typename T> cr_status launch_topk(const SolveArgs& a) {
+  size_t sm = (size_t)a.S * sizeof(int) + 32 * sizeof(int) + a.S;
+  k_topk<T><<<(unsigned)a.P, 32, sm, a.stream>>>(a.tk_cost, a.tk_coll, (const T*)a.u, a.D, a.P, a.S, a.K,
+                                                  T(a.eps), a.tk_idx);
+  return crh::check_launch("cr_topk");
+}
+
+#define CR_SOLVE_INSTANTIATE(EXT, T)                                \
+  EXT template cr_status launch_solve_ik<T>(const SolveArgs&, int); \
+  EXT template cr_status launch_lm_steps<T>(const SolveArgs&);      \
+  EXT template cr_status launch_pg_steps<T>(const SolveArgs&);      \
+  EXT template cr_status launch_seeds<T>(const SolveArgs&);         \
+  EXT template cr_status launch_topk<T>(const SolveArgs&);
+
+}  // namespace crk

@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libcrsolver.so (include/cr.h), with the same entry-point names.
+
+Only argument marshalling happens here: torch CUDA tensors are passed as raw device pointers, the
+current torch stream as the cudaStream_t, and host structs as ctypes Structures. Every step of the
+computation runs in the library's kernels. Loading fails loudly if the library was not built:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libcrsolver.so")
+
+CR_OK, CR_EINVAL, CR_ECUDA, CR_ENONFINITE, CR_ETIMEOUT = 0, 1, 2, 3, 4
+CR_F32, CR_F64 = 0, 1
+CR_TASK_IK6, CR_TASK_IK5 = 0, 1
+CR_MAX_SEG = 6
+CR_MAX_SPHERES = 256
+CR_MAX_NB = 64
+CR_MAX_SEEDS = 256
+
+EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step", "cr_pg_steps",
+           "cr_seeds", "cr_topk", "cr_ik_workspace_size", "cr_solve_ik", "cr_ik_stage1", "cr_ik_stage2",
+           "cr_solve_ik_plain",
+           "cr_poll_status", "cr_last_error_string", "cr_peak_launch")
+
+
+class CrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cr status {status}: {msg}")
+        self.status = status
+
+
+class cr_robot(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("n_b", C.c_int32), ("reserved", C.c_int32),
+                ("L", C.c_double * CR_MAX_SEG), ("r_c", C.c_double * CR_MAX_SEG),
+                ("u_max", C.c_double * CR_MAX_SEG), ("theta_max", C.c_double * CR_MAX_SEG),
+                ("r_body", C.c_double)]
+
+
+class cr_weights(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("w_p", "w_R", "rho_b", "rho_eq", "rho_k", "rho_c", "w_s",
+                                          "w_len", "rho_v", "rho_a", "dt", "v_max", "a_max", "delta")]
+
+
+class cr_scene(C.Structure):
+    _fields_ = [("spheres", C.c_void_p), ("n_o", C.c_int32), ("reserved", C.c_int32)]
+
+
+class cr_task(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("seeds_per_target", C.c_int32), ("targets", C.c_void_p),
+                ("n_targets", C.c_int64), ("w", cr_weights)]
+
+
+class cr_ik_params(C.Structure):
+    _fields_ = [("S", C.c_int32), ("n_final", C.c_int32), ("k_init", C.c_int32), ("k_final", C.c_int32),
+                ("lambda0", C.c_double), ("alpha0", C.c_double), ("dedup_eps", C.c_double),
+                ("lim_tol", C.c_double), ("pos_tol", C.c_double), ("rot_tol", C.c_double),
+                ("seed", C.c_uint64), ("p0", C.c_int64), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = C.c_void_p
+_SIGS = {
+    "cr_fk": [C.POINTER(cr_robot), _P, C.c_int64, _P, _P, C.c_int32, _P],
+    "cr_fk_jac": [C.POINTER(cr_robot), _P, C.c_int64, _P, C.c_int32, _P],
+    "cr_cost_grad": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P,
+                     _P, _P, C.c_int32, _P],
+    "cr_reduce_rows": [_P, C.c_int64, C.c_int64, _P, C.c_int32, _P],
+    "cr_lm_step": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, _P, _P, _P, _P,
+                   C.c_int64, C.c_int32, C.c_int32, _P],
+    "cr_pg_steps": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, _P, _P, C.c_int64,
+                    C.c_int32, C.c_int32, _P],
+    "cr_seeds": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_weights), C.c_uint64, C.c_int64,
+                 C.c_int64, C.c_int32, _P, C.c_int32, _P],
+    "cr_topk": [_P, _P, _P, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_double, _P, C.c_int32, _P],
+    "cr_solve_ik": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), C.POINTER(cr_ik_params),
+                    _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_ik_stage1": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), C.POINTER(cr_ik_params),
+                     _P, C.c_size_t, _P],
+    "cr_ik_stage2": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), C.POINTER(cr_ik_params),
+                     _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_solve_ik_plain": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task),
+                          C.POINTER(cr_ik_params), _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_poll_status": [_P, C.POINTER(C.c_int32), _P],
+    "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
+}
+
+
+def load(path: str | None = None):
+    """Load libcrsolver.so (raises if it is missing: build it with build_lib.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libcrsolver.so not found at {p}; run paper_2607_11340_gb300.build_lib.build()")
+        L = C.CDLL(p)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.cr_ik_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_ik_params)]
+        L.cr_ik_workspace_size.restype = C.c_size_t
+        L.cr_last_error_string.argtypes = []
+        L.cr_last_error_string.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def last_error() -> str:
+    return load().cr_last_error_string().decode()
+
+
+def _check(st: int):
+    if st != CR_OK:
+        raise CrError(st, last_error())
+
+
+def _ptr(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("CUDA tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float32:
+        return CR_F32
+    if t.dtype == torch.float64:
+        return CR_F64
+    raise ValueError(f"float32/float64 expected, got {t.dtype}")
+
+
+# --------------------------------------------------------------------------------------------
+# Same-name wrappers (tensors in, status checked)
+# --------------------------------------------------------------------------------------------
+def cr_fk(robot: cr_robot, u, T_out, backbone_out=None, stream=None):
+    B = u.shape[-1]
+    _check(load().cr_fk(C.byref(robot), _ptr(u), B, _ptr(T_out), _ptr(backbone_out), _dtype_code(u),
+                        _stream(stream)))
+
+
+def cr_fk_jac(robot: cr_robot, u, J_out, stream=None):
+    _check(load().cr_fk_jac(C.byref(robot), _ptr(u), u.shape[-1], _ptr(J_out), _dtype_code(u), _stream(stream)))
+
+
+def cr_cost_grad(robot, scene, task, u, cost_out, coll_out=None, grad_u_out=None, grad_param_out=None,
+                 stream=None):
+    _check(load().cr_cost_grad(C.byref(robot), C.byref(scene), C.byref(task), _ptr(u), u.shape[-1],
+                               _ptr(cost_out), _ptr(coll_out), _ptr(grad_u_out), _ptr(grad_param_out),
+                               _dtype_code(u), _stream(stream)))
+
+
+def cr_reduce_rows(x, out, stream=None):
+    _check(load().cr_reduce_rows(_ptr(x), x.shape[0], x.shape[1], _ptr(out), _dtype_code(x), _stream(stream)))
+
+
+def cr_lm_step(robot, scene, task, u, lam, nu, F_out=None, accepted_out=None, n_iter=1, stream=None):
+    _check(load().cr_lm_step(C.byref(robot), C.byref(scene), C.byref(task), _ptr(u), _ptr(lam), _ptr(nu),
+                             _ptr(F_out), _ptr(accepted_out), u.shape[-1], n_iter, _dtype_code(u),
+                             _stream(stream)))
+
+
+def cr_pg_steps(robot, scene, task, u, alpha, F_out, steps, stream=None):
+    _check(load().cr_pg_steps(C.byref(robot), C.byref(scene), C.byref(task), _ptr(u), _ptr(alpha), _ptr(F_out),
+                              u.shape[-1], steps, _dtype_code(u), _stream(stream)))
+
+
+def cr_seeds(robot, scene, weights, seed, p0, P, S, u_out, stream=None):
+    _check(load().cr_seeds(C.byref(robot), C.byref(scene), C.byref(weights), C.c_uint64(seed), p0, P, S,
+                           _ptr(u_out), _dtype_code(u_out), _stream(stream)))
+
+
+def cr_topk(cost, coll, u, P, S, k, dedup_eps, idx_out, stream=None):
+    _check(load().cr_topk(_ptr(cost), _ptr(coll), _ptr(u), u.shape[0], P, S, k, dedup_eps, _ptr(idx_out),
+                          _dtype_code(u), _stream(stream)))
+
+
+def cr_ik_workspace_size(robot, P, prm) -> int:
+    return int(load().cr_ik_workspace_size(C.byref(robot), P, C.byref(prm)))
+
+
+def cr_solve_ik(robot, scene, task, prm, u_out, cost_out, pos_err, rot_err, success, workspace, stream=None):
+    _check(load().cr_solve_ik(C.byref(robot), C.byref(scene), C.byref(task), C.byref(prm), _ptr(u_out),
+                              _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(success), _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_ik_stage1(robot, scene, task, prm, workspace, stream=None):
+    _check(load().cr_ik_stage1(C.byref(robot), C.byref(scene), C.byref(task), C.byref(prm), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_ik_stage2(robot, scene, task, prm, u_out, cost_out, pos_err, rot_err, success, workspace, stream=None):
+    _check(load().cr_ik_stage2(C.byref(robot), C.byref(scene), C.byref(task), C.byref(prm), _ptr(u_out),
+                               _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(success), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_solve_ik_plain(robot, scene, task, prm, u_out, cost_out, pos_err, rot_err, success, workspace,
+                      stream=None):
+    _check(load().cr_solve_ik_plain(C.byref(robot), C.byref(scene), C.byref(task), C.byref(prm), _ptr(u_out),
+                                    _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(success),
+                                    _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream(stream)))
+
+
+def cr_poll_status(workspace, stream=None) -> int:
+    out = C.c_int32(0)
+    _check(load().cr_poll_status(_ptr(workspace), C.byref(out), _stream(stream)))
+    return out.value
+
+
+def cr_peak_launch(kind: int, buf, iters: int, stream=None) -> float:
+    ops = C.c_double(0)
+    _check(load().cr_peak_launch(kind, _ptr(buf), buf.numel() * buf.element_size(), iters, C.byref(ops),
+                                 _stream(stream)))
+    return ops.value

@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads and exports every entry point
+include/cr.h declares, the ctypes mirrors of the structs have the C layout, and invalid
+arguments are rejected with CR_EINVAL before anything is launched."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cr.h")
+
+
+@pytest.fixture(scope="module")
+def crlib():
+    from paper_2607_11340_gb300 import build_lib, lib
+
+    build_lib.build()
+    return lib
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^CR_API\s+[\w\s\*]+?\b(cr_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(crlib):
+    names = declared_functions()
+    assert len(names) >= 14
+    L = crlib.load()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(crlib.EXPORTS)
+
+
+def test_struct_layout_matches_c(crlib, tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "cr.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(cr_robot), sizeof(cr_weights), sizeof(cr_scene), sizeof(cr_task), sizeof(cr_ik_params));
+  printf("%zu %zu %zu %zu\\n", offsetof(cr_robot, r_body), offsetof(cr_task, w), offsetof(cr_ik_params, seed), offsetof(cr_ik_params, precision));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    L = crlib
+    py = [C.sizeof(L.cr_robot), C.sizeof(L.cr_weights), C.sizeof(L.cr_scene), C.sizeof(L.cr_task),
+          C.sizeof(L.cr_ik_params), L.cr_robot.r_body.offset, L.cr_task.w.offset, L.cr_ik_params.seed.offset,
+          L.cr_ik_params.precision.offset]
+    assert [int(x) for x in out] == py
+
+
+def _robot(crlib, n=3):
+    r = crlib.cr_robot()
+    r.n, r.m, r.n_b = n, 3, 16
+    for i in range(n):
+        r.L[i], r.r_c[i], r.u_max[i], r.theta_max[i] = 0.1, 0.005, 0.01, 3.14
+    r.r_body = 0.005
+    return r
+
+
+def test_invalid_arguments_are_rejected(crlib):
+    L = crlib.load()
+    r = _robot(crlib)
+    dummy = C.c_void_p(256)
+    assert L.cr_fk(C.byref(r), dummy, 4, dummy, None, 0, None) == crlib.CR_OK or True  # never launched here
+    bad = _robot(crlib)
+    bad.n = 0
+    assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
+    assert "robot.n" in crlib.last_error()
+    bad = _robot(crlib)
+    bad.m = 4
+    assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
+    bad = _robot(crlib)
+    bad.L[1] = -1
+    assert L.cr_fk_jac(C.byref(bad), dummy, 4, dummy, 0, None) == crlib.CR_EINVAL
+    assert L.cr_fk(C.byref(r), None, 4, dummy, None, 0, None) == crlib.CR_EINVAL            # null u
+    assert L.cr_fk(C.byref(r), C.c_void_p(257), 4, dummy, None, 0, None) == crlib.CR_EINVAL  # misaligned
+    assert L.cr_fk(C.byref(r), dummy, -1, dummy, None, 0, None) == crlib.CR_EINVAL           # negative B
+    assert L.cr_fk(C.byref(r), dummy, 4, dummy, None, 7, None) == crlib.CR_EINVAL            # bad dtype
+    assert L.cr_fk(C.byref(r), None, 0, None, None, 0, None) == crlib.CR_OK                  # empty batch
+    # tasks: too few targets for the batch, bad kind
+    t = crlib.cr_task()
+    t.kind, t.seeds_per_target, t.targets, t.n_targets = 0, 4, 256, 2
+    sc = crlib.cr_scene()
+    assert L.cr_cost_grad(C.byref(r), C.byref(sc), C.byref(t), dummy, 9, dummy, None, None, None, 0, None) \
+        == crlib.CR_EINVAL
+    t.kind = 9
+    assert L.cr_cost_grad(C.byref(r), C.byref(sc), C.byref(t), dummy, 8, dummy, None, None, None, 0, None) \
+        == crlib.CR_EINVAL
+    sc.n_o = 300
+    t.kind = 0
+    assert L.cr_cost_grad(C.byref(r), C.byref(sc), C.byref(t), dummy, 8, dummy, None, None, None, 0, None) \
+        == crlib.CR_EINVAL
+    # solver params and workspace size
+    p = crlib.cr_ik_params()
+    p.S, p.n_final, p.k_init, p.k_final, p.lambda0 = 256, 8, 64, 30, 1e-3
+    ws = crlib.cr_ik_workspace_size(r, 100, p)
+    assert ws > 0 and ws % 256 == 0
+    assert crlib.cr_ik_workspace_size(r, 200, p) > ws
+    t = crlib.cr_task()
+    t.kind, t.seeds_per_target, t.targets, t.n_targets = 0, 1, 256, 100
+    outs = [dummy] * 4
+    assert L.cr_solve_ik(C.byref(r), None, C.byref(t), C.byref(p), *outs, dummy, dummy, ws - 256, None) \
+        == crlib.CR_EINVAL
+    assert "workspace" in crlib.last_error()
+    p.n_final = 40
+    assert L.cr_solve_ik(C.byref(r), None, C.byref(t), C.byref(p), *outs, dummy, dummy, ws, None) \
+        == crlib.CR_EINVAL
+    p.n_final, p.S = 8, 300
+    assert L.cr_solve_ik(C.byref(r), None, C.byref(t), C.byref(p), *outs, dummy, dummy, ws, None) \
+        == crlib.CR_EINVAL

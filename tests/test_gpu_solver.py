@@ -1,0 +1,248 @@
+"""GPU parity of the solver pieces against the FP64 oracle: counter-based seeds (bitwise),
+SelectTop (bitwise on float32 keys), projected-gradient and LM iterates, and Algorithm 1 end to
+end (success rate within 1 percentage point; FP64 mode reaches the oracle's solutions)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_util import TDT, TOL, dev_soa, host_aos, orc_robot, orc_weights, rowwise_rel, targets_dev
+from paper_2607_11340_gb300 import api, lib, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2607_11340_gb300 import build_lib
+
+    build_lib.build()
+    O.build()
+
+
+@pytest.mark.parametrize("spec", [synth.ROBOT_1SEG, synth.ROBOT_3SEG])
+def test_seeds_bitwise(spec):
+    P, S, p0, key = 37, 70, 11, 12345
+    rb = api.robot_struct(spec)
+    ref = O.seeds(orc_robot(spec), orc_weights(), None, key, p0, P, S).reshape(P * S, -1)
+    for prec in (lib.CR_F64, lib.CR_F32):
+        out = torch.empty((spec.d, P * S), dtype=TDT[prec], device="cuda")
+        lib.cr_seeds(rb, api.Scene(None).c, api.weights_struct(synth.WEIGHTS), key, p0, P, S, out)
+        got = host_aos(out)
+        want = ref if prec == lib.CR_F64 else ref.astype(np.float32).astype(np.float64)
+        assert np.array_equal(got, want)
+
+
+def test_seeds_with_spheres():
+    spec = synth.ROBOT_3SEG
+    P, S = 8, 64
+    sph = np.array([[0.0, 0.0, 0.1, 0.02], [0.05, 0.0, 0.2, 0.02], [-0.03, 0.04, 0.15, 0.015]])
+    ref = O.seeds(orc_robot(spec), orc_weights(), sph, 5, 0, P, S).reshape(P * S, -1)
+    out = torch.empty((spec.d, P * S), dtype=torch.float64, device="cuda")
+    lib.cr_seeds(api.robot_struct(spec), api.Scene(sph).c, api.weights_struct(synth.WEIGHTS), 5, 0, P, S, out)
+    same = np.all(host_aos(out) == ref, axis=1)
+    assert same.mean() >= 0.995  # a redraw decision may flip only for a sample on a sphere boundary
+
+
+def test_topk_bitwise():
+    rng = np.random.default_rng(200)
+    P, S, d, K = 19, 100, 9, 8
+    base = rng.normal(size=(6, d)) * 0.01
+    u = base[rng.integers(0, 6, P * S)] + rng.uniform(-3e-5, 3e-5, (P * S, d))
+    cost = rng.choice(np.linspace(0, 1, 30), P * S).astype(np.float32)
+    coll = rng.choice([0.0, 0.25], P * S).astype(np.float32)
+    cost[rng.integers(0, P * S, 10)] = np.nan
+    for eps in (0.0, 1e-4):
+        for prec in (lib.CR_F64, lib.CR_F32):
+            ug = dev_soa(u, TDT[prec])
+            idx = torch.empty((P, K), dtype=torch.int32, device="cuda")
+            lib.cr_topk(torch.tensor(cost).cuda(), torch.tensor(coll).cuda(), ug, P, S, K, eps, idx)
+            ub = host_aos(ug)
+            for p in range(P):
+                ref = O.topk(cost[p * S:(p + 1) * S], coll[p * S:(p + 1) * S], ub[p * S:(p + 1) * S], K, eps)
+                assert np.array_equal(idx[p].cpu().numpy(), ref), (eps, prec, p)
+
+
+def _ik_case(spec, kind, P, S, seed=300, spheres=None):
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose" if kind == lib.CR_TASK_IK6 else "axis", lambda x: O.fk(rbo, x)[0], seed)
+    u0 = O.seeds(rbo, orc_weights(), spheres, 7, 0, P, S).reshape(P * S, -1)
+    return rbo, tg, u0
+
+
+def test_pg_iterates_fp64():
+    spec = synth.ROBOT_3SEG
+    P, S, steps = 24, 16, 12
+    rbo, tg, u0 = _ik_case(spec, lib.CR_TASK_IK6, P, S)
+    ug = dev_soa(u0, torch.float64)
+    alpha = torch.full((P * S,), 1e-3, dtype=torch.float64, device="cuda")
+    F = torch.empty(P * S, dtype=torch.float64, device="cuda")
+    task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
+    lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, steps)
+    uo, Fo = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0, steps, 1e-3)
+    err = np.abs(host_aos(ug) - uo).max(axis=1) / spec.umax
+    assert np.mean(err <= 1e-10) >= 0.99, np.sort(err)[-5:]
+    ok = err <= 1e-10
+    np.testing.assert_allclose(F.cpu().numpy()[ok], Fo[ok], rtol=1e-11)
+
+
+def test_pg_one_step_fp32():
+    spec = synth.ROBOT_3SEG
+    P, S = 32, 16
+    rbo, tg, u0 = _ik_case(spec, lib.CR_TASK_IK6, P, S, seed=301)
+    ug = dev_soa(u0, torch.float32)
+    u0f = host_aos(ug)
+    alpha = torch.full((P * S,), 1e-3, dtype=torch.float32, device="cuda")
+    F = torch.empty(P * S, dtype=torch.float32, device="cuda")
+    task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
+    lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, 1)
+    uo, Fo = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0f, 1, 1e-3)
+    moved_g = np.any(host_aos(ug) != u0f, axis=1)
+    moved_o = np.any(uo != u0f, axis=1)
+    same = moved_g == moved_o
+    assert same.mean() >= 0.98
+    err = np.abs(host_aos(ug) - uo).max(axis=1)[same] / spec.umax
+    assert err.max() <= 1e-4
+    np.testing.assert_allclose(F.double().cpu().numpy()[same], Fo[same], rtol=1e-5)
+
+
+@pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
+def test_lm_iterates(prec):
+    """20 LM iterations, one call per iteration, against the oracle's iterate history.
+    FP64: 1e-10 of the bound. FP32 bulk (FP64 Cholesky): 1e-4 of the bound for the seeds whose
+    oracle accept decisions are not near-ties."""
+    spec = synth.ROBOT_3SEG
+    P, S, iters = 32, 4, 20
+    rbo, tg, u_true = None, None, None
+    rbo = orc_robot(spec)
+    rng = np.random.default_rng(302)
+    u_true = synth.hexagon_states(rng, P, 3, spec.umax)
+    tg = synth.pose_targets(O.fk(rbo, u_true)[0], "pose")
+    u0 = np.repeat(u_true, S, 0) + rng.normal(0, 1.5e-3, (P * S, 9))
+    ug = dev_soa(u0, TDT[prec])
+    u0b = host_aos(ug)
+    lam = torch.full((P * S,), 1e-3, dtype=torch.float64, device="cuda")
+    nu = torch.full((P * S,), 2.0, dtype=torch.float64, device="cuda")
+    task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
+    ref = O.ik_lm(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b, iters, history=True)
+    errs = []
+    for it in range(iters):
+        lib.cr_lm_step(api.robot_struct(spec), api.Scene(None).c, task, ug, lam, nu, n_iter=1)
+        errs.append(np.abs(host_aos(ug) - ref["hist"][it]).max(axis=1) / spec.umax)
+    errs = np.array(errs)
+    worst = errs.max(axis=0)
+    if prec == lib.CR_F64:
+        assert np.mean(worst <= 1e-10) >= 0.99, np.sort(worst)[-5:]
+    else:
+        assert np.mean(worst <= 1e-4) >= 0.95, np.sort(worst)[-8:]
+    assert np.mean(ref["F"] < 1e-12) > 0.5  # most seeds converge in 20 iterations
+
+
+def _solve(spec, ik, kind, tg, prec, plain=False, spheres=None, p0=0):
+    s = api.IkSolver(spec, ik, synth.WEIGHTS, kind, len(tg), api.Scene(spheres), prec, plain)
+    s.prm.p0 = p0
+    o = s.solve(targets_dev(tg), p0=p0)
+    torch.cuda.synchronize()
+    return dict(u=host_aos(o.u), F=o.cost.cpu().numpy(), pos=o.pos_err.cpu().numpy(),
+                rot=o.rot_err.cpu().numpy(), success=o.success.cpu().numpy().astype(bool),
+                status=s.status())
+
+
+def _oracle_solve(spec, ik, kind, tg, spheres=None, p0=0):
+    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
+                     alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, lim_tol=ik.lim_tol, pos_tol=ik.pos_tol,
+                     rot_tol=ik.rot_tol, seed=ik.seed, p0=p0)
+    return O.solve_ik(orc_robot(spec), orc_weights(), spheres, kind, tg, cfg)
+
+
+def test_solve_ik_1seg_fp64_full_size():
+    """The 1-segment 5-DoF workload at full size (256 targets, 32 seeds, 50 LM iterations, FP64,
+    single stage): same solutions as the oracle."""
+    spec, ik, P = synth.ROBOT_1SEG, synth.IK_1SEG, synth.P_1SEG
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "axis", lambda x: O.fk(rbo, x)[0], seed=0)
+    g = _solve(spec, ik, lib.CR_TASK_IK5, tg, lib.CR_F64)
+    o = _oracle_solve(spec, ik, lib.CR_TASK_IK5, tg)
+    assert abs(g["success"].mean() - o["success"].mean()) <= 0.01
+    assert g["success"].mean() >= 0.99
+    close = np.abs(g["u"] - o["u"]).max(axis=1) <= 1e-9
+    assert close.mean() >= 0.98
+    assert g["status"] == 0
+
+
+@pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
+def test_solve_ik_3seg_two_stage(prec):
+    spec = synth.ROBOT_3SEG
+    ik = synth.IK_3SEG
+    P = 48
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose", lambda x: O.fk(rbo, x)[0], seed=3)
+    g = _solve(spec, ik, lib.CR_TASK_IK6, tg, prec)
+    o = _oracle_solve(spec, ik, lib.CR_TASK_IK6, tg)
+    assert abs(g["success"].mean() - o["success"].mean()) <= 0.01 + 1.0 / P
+    # Several candidates may converge to different exact solutions (cost ~1e-30); which one the
+    # argmin keeps is then decided by rounding, so the unique part is checked instead: the
+    # success flags and the validity of every GPU solution under the oracle's own acceptance.
+    pos, rot, lim, col = O.accept(orc_robot(spec), None, lib.CR_TASK_IK6, tg, g["u"], ik.lim_tol)
+    np.testing.assert_allclose(g["pos"], pos, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(g["rot"], rot, rtol=1e-6, atol=1e-12)
+    ok = (pos <= ik.pos_tol) & (rot <= ik.rot_tol) & lim & col
+    assert np.array_equal(ok, g["success"])
+    if prec == lib.CR_F64:
+        # where the oracle's best cost is not an exact solution the argmin is meaningful: equal costs
+        sep = o["F"] > 1e-20
+        np.testing.assert_allclose(g["F"][sep], o["F"][sep], rtol=1e-8)
+    assert np.all(g["pos"][g["success"]] <= 1e-3)
+
+
+def test_solve_ik_full_size_sampled():
+    """The 3-segment two-stage workload at full size (4096 targets) in the launch configuration of
+    the benchmark; a contiguous sample of 48 targets is solved by the oracle (same seed counters)."""
+    spec, ik, P = synth.ROBOT_3SEG, synth.IK_3SEG, synth.P_3SEG
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose", lambda x: O.fk(rbo, x)[0], seed=0)
+    g = _solve(spec, ik, lib.CR_TASK_IK6, tg, lib.CR_F32)
+    lo = 1000
+    o = _oracle_solve(spec, ik, lib.CR_TASK_IK6, tg[lo:lo + 48], p0=lo)
+    gs = g["success"][lo:lo + 48]
+    assert np.sum(gs != o["success"]) <= 1
+    assert g["success"].mean() >= o["success"].mean() - 0.01 - 1.0 / 48
+    assert g["status"] == 0
+
+
+def test_plain_form_matches_optimised_fp64():
+    spec = synth.ROBOT_3SEG
+    ik = synth.IkSpec(S=64, n_final=4, k_init=16, k_final=10)
+    P = 6
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose", lambda x: O.fk(rbo, x)[0], seed=4)
+    a = _solve(spec, ik, lib.CR_TASK_IK6, tg, lib.CR_F64)
+    b = _solve(spec, ik, lib.CR_TASK_IK6, tg, lib.CR_F64, plain=True)
+    assert np.array_equal(a["success"], b["success"])
+    np.testing.assert_allclose(b["u"], a["u"], atol=1e-10)
+
+
+def test_solve_ik_ragged_and_obstacles():
+    """Seeds not a multiple of the warp size, a 2-segment robot, obstacles, and a non-finite target."""
+    spec = synth.RobotSpec(L=(0.1, 0.08), rc=0.005, umax=0.01, nb=8)
+    ik = synth.IkSpec(S=45, n_final=5, k_init=20, k_final=20)
+    P = 9
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose", lambda x: O.fk(rbo, x)[0], seed=5)
+    sph = np.array([[0.03, 0.0, 0.12, 0.01], [-0.02, 0.03, 0.08, 0.008]])
+    g = _solve(spec, ik, lib.CR_TASK_IK6, tg, lib.CR_F64, spheres=sph)
+    o = _oracle_solve(spec, ik, lib.CR_TASK_IK6, tg, spheres=sph)
+    assert np.sum(g["success"] != o["success"]) <= 1
+    tg[2, 0] = np.nan
+    g2 = _solve(spec, ik, lib.CR_TASK_IK6, tg, lib.CR_F32, spheres=sph)
+    assert not g2["success"][2] and np.isnan(g2["F"][2])
+    assert g2["status"] & (1 << lib.CR_ENONFINITE)
+
+
+def test_peak_kernels_run():
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    for kind in range(4):
+        assert lib.cr_peak_launch(kind, buf, 2) > 0
+    torch.cuda.synchronize()
