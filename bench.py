@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     return ap.parse_args()
 
 
@@ -212,7 +213,7 @@ def main():
         dist.barrier()
     lib.load()
 
-    spec, ik, P = synth.ROBOT_3SEG, synth.IK_3SEG, synth.P_3SEG
+    spec, ik, P = synth.ROBOT_3SEG, synth.IK_3SEG, args.targets
     counts = load_counts()
     tg = make_targets(torch, api, lib, spec, P, seed=rank, device=dev)
     tg_dev = torch.as_tensor(tg.T.copy(), dtype=torch.float64, device=dev)
