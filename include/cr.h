@@ -245,6 +245,24 @@ CR_API cr_status cr_solve_ik_plain(const cr_robot* robot, const cr_scene* scene,
                             double* pos_err, double* rot_err, uint8_t* success, void* workspace,
                             size_t ws_bytes, cr_stream stream);
 
+/* Allocation-free variant of cr_solve_ik (the paper has no counterpart: it is a service to
+ * callers that must not allocate device memory, such as a real-time control loop that reserves
+ * everything at start-up or a host program that gives out device memory from its own pool).
+ * Same arguments and outputs as cr_solve_ik, without the workspace: the scratch is a file-scope
+ * device array of CR_STATIC_WS_BYTES bytes that every GPU loading the library holds until exit.
+ * Sizes whose scratch (cr_ik_workspace_size) exceeds it return CR_EINVAL. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current,
+ * so make the first call before any stream capture. All calls share the array and overwrite it
+ * (the status word at its start is cleared by each call; cr_poll_status cannot read it, the
+ * per-target outputs carry the result): calls that overlap on the GPU race and must be serialised
+ * by the caller. Allocates nothing. */
+#define CR_STATIC_WS_BYTES ((size_t)8 << 20)
+CR_API cr_status cr_solve_ik_static(const cr_robot* robot, const cr_scene* scene, const cr_task* task,
+                                    const cr_ik_params* prm, double* u_out, double* cost_out, double* pos_err,
+                                    double* rot_err, uint8_t* success, cr_stream stream);
+/* Capacity of that array in bytes (CR_STATIC_WS_BYTES). */
+CR_API size_t cr_static_workspace_capacity(void);
+
 /* ---------------------------------------------------------------------------------------------
  * Status and diagnostics
  * ------------------------------------------------------------------------------------------- */

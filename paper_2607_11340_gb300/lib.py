@@ -25,7 +25,8 @@ CR_MAX_SEEDS = 256
 EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step", "cr_pg_steps",
            "cr_seeds", "cr_topk", "cr_ik_workspace_size", "cr_solve_ik", "cr_ik_stage1", "cr_ik_stage2",
            "cr_solve_ik_plain",
-           "cr_poll_status", "cr_last_error_string", "cr_peak_launch")
+           "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
+           "cr_static_workspace_capacity")
 
 
 class CrError(RuntimeError):
@@ -88,6 +89,8 @@ _SIGS = {
                      _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
     "cr_solve_ik_plain": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task),
                           C.POINTER(cr_ik_params), _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_solve_ik_static": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task),
+                           C.POINTER(cr_ik_params), _P, _P, _P, _P, _P, _P],
     "cr_poll_status": [_P, C.POINTER(C.c_int32), _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
 }
@@ -109,6 +112,8 @@ def load(path: str | None = None):
             f.restype = C.c_int
         L.cr_ik_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_ik_params)]
         L.cr_ik_workspace_size.restype = C.c_size_t
+        L.cr_static_workspace_capacity.argtypes = []
+        L.cr_static_workspace_capacity.restype = C.c_size_t
         L.cr_last_error_string.argtypes = []
         L.cr_last_error_string.restype = C.c_char_p
         _lib = L
@@ -224,6 +229,17 @@ def cr_solve_ik_plain(robot, scene, task, prm, u_out, cost_out, pos_err, rot_err
                                     _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(success),
                                     _ptr(workspace), workspace.numel() * workspace.element_size(),
                                     _stream(stream)))
+
+
+def cr_solve_ik_static(robot, scene, task, prm, u_out, cost_out, pos_err, rot_err, success, stream=None):
+    """cr_solve_ik without a workspace argument (scratch is a static device array; allocates nothing)."""
+    _check(load().cr_solve_ik_static(C.byref(robot), C.byref(scene), C.byref(task), C.byref(prm), _ptr(u_out),
+                                     _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(success),
+                                     _stream(stream)))
+
+
+def cr_static_workspace_capacity() -> int:
+    return int(load().cr_static_workspace_capacity())
 
 
 def cr_poll_status(workspace, stream=None) -> int:
