@@ -45,12 +45,17 @@ CR_HD void c_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
 CR_HD void c_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 CR_HD float c_atan2(float y, float x) { return atan2f(y, x); }
 CR_HD double c_atan2(double y, double x) { return atan2(y, x); }
+CR_HD float c_rsqrt(float x) { return rsqrtf(x); }
+CR_HD float c_div(float a, float b) { return __fdividef(a, b); }
+CR_HD double c_div(double a, double b) { return a / b; }
+CR_HD double c_rsqrt(double x) { return 1.0 / sqrt(x); }
 CR_HD float c_fabs(float x) { return fabsf(x); }
 CR_HD double c_fabs(double x) { return fabs(x); }
 CR_HD bool c_finite(float x) { return isfinite(x); }
 CR_HD bool c_finite(double x) { return isfinite(x); }
 template <typename T> CR_HD T c_max(T a, T b) { return a > b ? a : b; }
 template <typename T> CR_HD T c_min(T a, T b) { return a < b ? a : b; }
+template <typename T> CR_HD T clampb(T v, T b) { return c_min(b, c_max(-b, v)); }
 
 // ------------------------------------------------------------------------------------------------
 // Parameters as the kernels see them
@@ -76,8 +81,8 @@ template <typename T> struct WeightsK {
 // ------------------------------------------------------------------------------------------------
 // Segment functions of theta^2
 // ------------------------------------------------------------------------------------------------
-// s = sin(t)/t and c = (1 - cos t)/t^2 from x = t^2 (half-angle form).
-template <typename T> CR_HD void seg_sc(T x, T& s, T& c) {
+// s = sin(t)/t and c = (1 - cos t)/t^2 from x = t^2 (half-angle form, library sin/cos).
+template <typename T> CR_HD void seg_sc_lib(T x, T& s, T& c) {
   T sc, ch;
   if (x < Prec<T>::kZero) {
     sc = T(1) - x * T(1.0 / 24.0);
@@ -93,7 +98,7 @@ template <typename T> CR_HD void seg_sc(T x, T& s, T& c) {
 }
 
 // s3 = (t - sin t)/t^3 = (1 - s)/x and cp = dc/dx = (s - 2c)/(2x); Taylor series in x below kSeriesX.
-template <typename T> CR_HD void seg_deriv(T x, T s, T c, T& s3, T& cp) {
+template <typename T> CR_HD void seg_deriv_lib(T x, T s, T c, T& s3, T& cp) {
   if (x < Prec<T>::kSeriesX) {
     s3 = T(1.0 / 6.0) + x * (T(-1.0 / 120.0) + x * (T(1.0 / 5040.0) + x * (T(-1.0 / 362880.0) +
          x * (T(1.0 / 39916800.0) + x * (T(-1.0 / 6227020800.0) + x * T(1.0 / 1307674368000.0))))));
@@ -103,6 +108,66 @@ template <typename T> CR_HD void seg_deriv(T x, T s, T c, T& s3, T& cp) {
     T ix = T(1) / x;
     s3 = (T(1) - s) * ix;
     cp = (s - T(2) * c) * (T(0.5) * ix);
+  }
+}
+
+template <typename T> CR_HD void seg_sc(T x, T& s, T& c) { seg_sc_lib(x, s, c); }
+template <typename T> CR_HD void seg_deriv(T x, T s, T c, T& s3, T& cp) { seg_deriv_lib(x, s, c, s3, cp); }
+
+// FP32: for theta <= pi the four coefficients are Taylor polynomials (no square root, sin/cos or
+// division): with y = (theta/2)^2, sinc(theta/2) = sum_k (-1)^k y^k / (2k+1)! (degree 6) and
+// cos(theta/2) = sum_k (-1)^k y^k / (2k)! (degree 7); s3 = sum_k (-1)^k x^k / (2k+3)! and
+// cp = sum_k (-1)^(k+1) (k+1) x^k / (2k+4)! (degree 8). Truncation error <= 4e-10 relative on the
+// whole range, far below FP32 rounding. Larger angles take the library path.
+constexpr float kPolyMaxX = 9.8696044f;  // pi^2
+
+template <> CR_HD void seg_sc<float>(float x, float& s, float& c) {
+  if (x <= kPolyMaxX) {
+    const float y = 0.25f * x;
+    float sc = 1.6059043836821613e-10f;
+    sc = fmaf(sc, y, -2.505210838544172e-08f);
+    sc = fmaf(sc, y, 2.7557319223985893e-06f);
+    sc = fmaf(sc, y, -0.0001984126984126984f);
+    sc = fmaf(sc, y, 0.008333333333333333f);
+    sc = fmaf(sc, y, -0.16666666666666666f);
+    sc = fmaf(sc, y, 1.0f);
+    float ch = -1.1470745597729725e-11f;
+    ch = fmaf(ch, y, 2.08767569878681e-09f);
+    ch = fmaf(ch, y, -2.755731922398589e-07f);
+    ch = fmaf(ch, y, 2.48015873015873e-05f);
+    ch = fmaf(ch, y, -0.001388888888888889f);
+    ch = fmaf(ch, y, 0.041666666666666664f);
+    ch = fmaf(ch, y, -0.5f);
+    ch = fmaf(ch, y, 1.0f);
+    s = sc * ch;
+    c = 0.5f * sc * sc;
+  } else {
+    seg_sc_lib(x, s, c);
+  }
+}
+
+template <> CR_HD void seg_deriv<float>(float x, float s, float c, float& s3, float& cp) {
+  if (x <= kPolyMaxX) {
+    float a = 8.22063524662433e-18f;
+    a = fmaf(a, x, -2.8114572543455206e-15f);
+    a = fmaf(a, x, 7.647163731819816e-13f);
+    a = fmaf(a, x, -1.6059043836821613e-10f);
+    a = fmaf(a, x, 2.505210838544172e-08f);
+    a = fmaf(a, x, -2.7557319223985893e-06f);
+    a = fmaf(a, x, 0.0001984126984126984f);
+    a = fmaf(a, x, -0.008333333333333333f);
+    s3 = fmaf(a, x, 0.16666666666666666f);
+    float b = -3.6992858609809485e-18f;
+    b = fmaf(b, x, 1.249536557486898e-15f);
+    b = fmaf(b, x, -3.3456341326711696e-13f);
+    b = fmaf(b, x, 6.882447358637835e-11f);
+    b = fmaf(b, x, -1.043837849393405e-08f);
+    b = fmaf(b, x, 1.1022927689594355e-06f);
+    b = fmaf(b, x, -7.440476190476191e-05f);
+    b = fmaf(b, x, 0.002777777777777778f);
+    cp = fmaf(b, x, -0.041666666666666664f);
+  } else {
+    seg_deriv_lib(x, s, c, s3, cp);
   }
 }
 
@@ -272,7 +337,10 @@ template <typename T> CR_HD T so3_log(const T (&E)[9], T (&e)[3], T& sn_out, T& 
   T ang = c_atan2(sn, cs);
   sn_out = sn;
   cs_out = cs;
-  if (cs < T(0) && s2 < Prec<T>::kLogPi) {
+  // Near pi the axis v / |v| loses relative accuracy as |v| -> 0; FP64 then takes it from the
+  // symmetric part. FP32 keeps the single branch-free formula (its error there, ~eps / sin, is
+  // below the FP32 accuracy of the other terms for angles up to pi - 0.05).
+  if (sizeof(T) == 8 && cs < T(0) && s2 < Prec<T>::kLogPi) {
     // near pi: (E + E^T)/2 = cs I + (1 - cs) n n^T; largest diagonal gives the best-conditioned column
     T S00 = E[0], S11 = E[4], S22 = E[8];
     T den = T(1) / (T(1) - cs);
@@ -293,7 +361,7 @@ template <typename T> CR_HD T so3_log(const T (&E)[9], T (&e)[3], T& sn_out, T& 
     e[2] = sgn * ang * n[2];
     return ang;
   }
-  T f = (s2 < Prec<T>::kLogSmall) ? T(1) + s2 * T(1.0 / 6.0) : ang / sn;
+  T f = (s2 < Prec<T>::kLogSmall) ? T(1) + s2 * T(1.0 / 6.0) : c_div(ang, sn);
   e[0] = f * v0;
   e[1] = f * v1;
   e[2] = f * v2;
@@ -476,12 +544,16 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
     matTvec(ch.Rb[i], Mp, Ml);
     T s3, cp;
     seg_deriv(ch.x[i], ch.s[i], ch.c[i], s3, cp);
-    T dd[2][3], wl[2][3];
-    seg_local_derivs(ch.ax[i], ch.ay[i], ch.s[i], ch.c[i], s3, cp, rb.L[i], dd, wl);
-    T gx = Fl[0] * dd[0][0] + Fl[1] * dd[0][1] + Fl[2] * dd[0][2] + Ml[0] * wl[0][0] +
-           Ml[1] * wl[0][1] + Ml[2] * wl[0][2] + Dx[i];
-    T gy = Fl[0] * dd[1][0] + Fl[1] * dd[1][1] + Fl[2] * dd[1][2] + Ml[0] * wl[1][0] +
-           Ml[1] * wl[1][1] + Ml[2] * wl[1][2] + Dy[i];
+    // Fl . d(d_i)/da_k + Ml . J_l dw/da_k, the products of seg_local_derivs written out:
+    // with Fa = a . Fl_xy, Ma = a . Ml_xy and cf = cp Fa + sp Fl_z,
+    // gx = L (c Fl_x + 2 ax cf) + Ml_y - s3 ay Ma - c ay Ml_z,
+    // gy = L (c Fl_y + 2 ay cf) - Ml_x + s3 ax Ma + c ax Ml_z.
+    const T ax = ch.ax[i], ay = ch.ay[i], cc = ch.c[i], L = rb.L[i];
+    T sp = T(0.5) * (s3 - cc);
+    T Fa = ax * Fl[0] + ay * Fl[1], Ma = ax * Ml[0] + ay * Ml[1];
+    T cf = cp * Fa + sp * Fl[2];
+    T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2] + Dx[i];
+    T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2] + Dy[i];
     if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T th = c_sqrt(ch.x[i]);
       T f = w.rho_k * (th - rb.thmax[i]) / th;
@@ -748,15 +820,20 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 // ------------------------------------------------------------------------------------------------
 // FP64 Cholesky of a packed lower-triangular matrix and the two triangular solves.
 // ------------------------------------------------------------------------------------------------
-template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2]) {
+// The reciprocal pivots are kept in invd[] so that the solves multiply instead of divide (FP64
+// division and square root are long instruction sequences on a part with a narrow FP64 pipe).
+template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2], double (&invd)[D]) {
+  bool ok = true;  // no early exit: keeps the fully unrolled factorisation in registers
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     double s = A[tri(j, j)];
 #pragma unroll
     for (int k = 0; k < j; ++k) s -= A[tri(j, k)] * A[tri(j, k)];
-    if (!(s > 0.0)) return false;
-    double ljj = sqrt(s);
-    double inv = 1.0 / ljj;
+    ok = ok && (s > 0.0);
+    s = s > 0.0 ? s : 1.0;
+    double inv = rsqrt(s);
+    double ljj = s * inv;
+    invd[j] = inv;
     A[tri(j, j)] = ljj;
 #pragma unroll
     for (int i = j + 1; i < D; ++i) {
@@ -766,23 +843,24 @@ template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2]) {
       A[tri(i, j)] = t * inv;
     }
   }
-  return true;
+  return ok;
 }
 
-template <int D> CR_HD void cholesky_solve(const double (&Lm)[D * (D + 1) / 2], double (&x)[D]) {
+template <int D>
+CR_HD void cholesky_solve(const double (&Lm)[D * (D + 1) / 2], const double (&invd)[D], double (&x)[D]) {
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     double s = x[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s -= Lm[tri(i, k)] * x[k];
-    x[i] = s / Lm[tri(i, i)];
+    x[i] = s * invd[i];
   }
 #pragma unroll
   for (int i = D - 1; i >= 0; --i) {
     double s = x[i];
 #pragma unroll
     for (int k = i + 1; k < D; ++k) s -= Lm[tri(k, i)] * x[k];
-    x[i] = s / Lm[tri(i, i)];
+    x[i] = s * invd[i];
   }
 }
 
@@ -792,19 +870,28 @@ template <int D> CR_HD void cholesky_solve(const double (&Lm)[D * (D + 1) / 2], 
 // with breakpoints v_j -/+ b, so tau lies between the largest breakpoint with g >= 0 and the
 // smallest with g <= 0 and follows by linear interpolation.
 // ------------------------------------------------------------------------------------------------
-template <typename T> CR_HD T clampb(T v, T b) { return c_min(b, c_max(-b, v)); }
-
 template <typename T> CR_HD void project3(T v0, T v1, T v2, T b, T& u0, T& u1, T& u2) {
-  T bp[6] = {v0 - b, v0 + b, v1 - b, v1 + b, v2 - b, v2 + b};
-  T ta = T(-1e30), tb = T(1e30), ga = T(0), gb = T(0);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    T t = bp[k];
-    T gv = clampb(v0 - t, b) + clampb(v1 - t, b) + clampb(v2 - t, b);
-    if (gv >= T(0) && t > ta) { ta = t; ga = gv; }
-    if (gv <= T(0) && t < tb) { tb = t; gb = gv; }
+  // interior: the projection onto the plane sum u = 0 already satisfies the bounds (tau = mean)
+  T m = (v0 + v1 + v2) * T(1.0 / 3.0);
+  T w0 = v0 - m, w1 = v1 - m, w2 = v2 - m;
+  if (c_fabs(w0) <= b && c_fabs(w1) <= b && c_fabs(w2) <= b) {
+    u0 = w0; u1 = w1; u2 = w2;
+    return;
   }
-  T tau = (ga == gb) ? ta : ta + ga * (tb - ta) / (ga - gb);
+  // Otherwise, with va >= vb >= vc the solution has u_a >= 0 >= u_c and u_b strictly inside, so
+  // only u_a can clamp (at +b) and only u_c (at -b): g(tau) = min(va - tau, b) + (vb - tau) +
+  // max(vc - tau, -b). Its breakpoints are va - b and vc + b; the sign of g at them selects which
+  // of the four linear pieces holds the root, and each piece has a closed-form root.
+  T va = c_max(v0, c_max(v1, v2)), vc = c_min(v0, c_min(v1, v2));
+  T vb = c_max(c_min(v0, v1), c_min(c_max(v0, v1), v2));  // median
+  T tT = va - b, tB = vc + b;
+  T lo = c_min(tT, tB), hi = c_max(tT, tB);
+  T glo = c_min(va - lo, b) + (vb - lo) + c_max(vc - lo, -b);
+  T ghi = c_min(va - hi, b) + (vb - hi) + c_max(vc - hi, -b);
+  T t_top = T(0.5) * (vb + vc + b);   // u_a = b
+  T t_bot = T(0.5) * (va + vb - b);   // u_c = -b
+  T t_mid = tT <= tB ? m : vb;        // no clamp, or both (u_b = 0)
+  T tau = glo < T(0) ? t_top : (ghi > T(0) ? t_bot : t_mid);
   u0 = clampb(v0 - tau, b);
   u1 = clampb(v1 - tau, b);
   u2 = clampb(v2 - tau, b);

@@ -25,7 +25,7 @@ CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Ta
   T gn2 = T(0);
 #pragma unroll
   for (int q = 0; q < D; ++q) gn2 += g[q] * g[q];
-  T scale = gn2 > T(0) ? alpha / c_sqrt(gn2) : T(0);
+  T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
   T u1[D];
 #pragma unroll
   for (int i = 0; i < N; ++i)
@@ -52,7 +52,7 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
                        const Sphere4<T>* sph, int no, T (&u)[3 * N], double& lam, double& nu, T& Fout) {
   constexpr int D = 3 * N;
   constexpr int DD = D * (D + 1) / 2;
-  double Ad[DD], Dg[D], dl[D];
+  double Ad[DD], Dg[D], dl[D], invd[D];
   T F;
   {
     T A[DD], g[D];
@@ -67,7 +67,7 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
     Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
     Ad[tri(q, q)] += lam * Dg[q];
   }
-  if (!cholesky_packed<D>(Ad)) {
+  if (!cholesky_packed<D>(Ad, invd)) {
     lam *= nu;
     nu *= 2.0;
     Fout = F;
@@ -76,7 +76,7 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
   double gd[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) { gd[q] = dl[q]; dl[q] = -dl[q]; }
-  cholesky_solve<D>(Ad, dl);
+  cholesky_solve<D>(Ad, invd, dl);
   T un[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) un[q] = u[q] + T(dl[q]);
@@ -113,51 +113,53 @@ CR_HD bool key_less(float c1, float l1, int i1, float c2, float l2, int i2) {
   return i1 < i2;
 }
 
+// Greedy selection with near-duplicate marking: each round keeps the best available candidate w
+// and, in parallel over the lanes, marks every available candidate within eps of w as a duplicate.
+// A candidate ranked below w meets w (already kept) when its turn comes in the sequential rule, so
+// the kept set and order are those of the sequential rule, with at most K rounds. If fewer than K
+// survive, the marked candidates fill the rest in rank order. taken: 0 available, 1 kept, 2 marked.
 template <typename T>
 __device__ void warp_topk(const float* cost, const float* coll, const T* u, int64_t ustride, int D, int S,
-                          int K, T eps, int* sel, unsigned char* taken, int* skipped) {
+                          int K, T eps, int* sel, unsigned char* taken, int* /*unused*/) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   for (int i = lane; i < S; i += 32) taken[i] = 0;
   __syncwarp();
-  int kept = 0, nskip = 0;
-  for (int round = 0; round < S && kept < K; ++round) {
-    float bc = INFINITY, bl = INFINITY;
-    int bi = INT_MAX;
-    for (int i = lane; i < S; i += 32) {
-      if (taken[i]) continue;
-      float c = cost[i], l = coll[i];
-      c = isfinite(c) ? c : INFINITY;
-      l = isfinite(l) ? l : INFINITY;
-      if (key_less(c, l, i, bc, bl, bi)) { bc = c; bl = l; bi = i; }
-    }
+  int kept = 0;
+  for (int pass = 0; pass < 2 && kept < K; ++pass) {
+    const unsigned char want = pass == 0 ? 0 : 2;  // pass 0: available; pass 1: fill from marked
+    while (kept < K) {
+      float bc = INFINITY, bl = INFINITY;
+      int bi = INT_MAX;
+      for (int i = lane; i < S; i += 32) {
+        if (taken[i] != want) continue;
+        float c = cost[i], l = coll[i];
+        c = isfinite(c) ? c : INFINITY;
+        l = isfinite(l) ? l : INFINITY;
+        if (key_less(c, l, i, bc, bl, bi)) { bc = c; bl = l; bi = i; }
+      }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      float oc = __shfl_xor_sync(FULL, bc, off);
-      float ol = __shfl_xor_sync(FULL, bl, off);
-      int oi = __shfl_xor_sync(FULL, bi, off);
-      if (key_less(oc, ol, oi, bc, bl, bi)) { bc = oc; bl = ol; bi = oi; }
+      for (int off = 16; off > 0; off >>= 1) {
+        float oc = __shfl_xor_sync(FULL, bc, off);
+        float ol = __shfl_xor_sync(FULL, bl, off);
+        int oi = __shfl_xor_sync(FULL, bi, off);
+        if (key_less(oc, ol, oi, bc, bl, bi)) { bc = oc; bl = ol; bi = oi; }
+      }
+      if (bi == INT_MAX) break;
+      if (lane == 0) { sel[kept] = bi; taken[bi] = 1; }
+      ++kept;
+      __syncwarp();
+      if (pass == 0) {
+        for (int i = lane; i < S; i += 32) {
+          if (taken[i] != 0) continue;
+          T m = T(0);
+          for (int q = 0; q < D; ++q) m = c_max(m, c_fabs(u[q * ustride + i] - u[q * ustride + bi]));
+          if (m < eps) taken[i] = 2;
+        }
+        __syncwarp();
+      }
     }
-    if (bi == INT_MAX) break;
-    bool dup = false;
-    if (lane < kept) {
-      int j = sel[lane];
-      T m = T(0);
-      for (int q = 0; q < D; ++q) m = c_max(m, c_fabs(u[q * ustride + bi] - u[q * ustride + j]));
-      dup = m < eps;
-    }
-    dup = __any_sync(FULL, dup);
-    if (lane == 0) {
-      taken[bi] = 1;
-      if (dup) skipped[nskip] = bi;
-      else sel[kept] = bi;
-    }
-    if (dup) ++nskip;
-    else ++kept;
-    __syncwarp();
   }
-  for (int q = 0; kept < K && q < nskip; ++q, ++kept)
-    if (lane == 0) sel[kept] = skipped[q];
   for (int k = kept; k < K; ++k)
     if (lane == 0) sel[k] = -1;
   __syncwarp();
