@@ -371,3 +371,134 @@ def opcount_ik(robot, weights, spheres, kind, target, u):
     lib().orc_opcount_ik(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
                          _dp(_f64(target).reshape(7)), _dp(_f64(u)), out)
     return tuple(int(x) for x in out)
+
+
+# ---------------------------------------------------------------------------------------------
+# Trajectory planning, path following, calibration
+# ---------------------------------------------------------------------------------------------
+def _per_problem_spheres(spheres, P):
+    """spheres [P][no][4] (or None) -> (no, flat array)."""
+    if spheres is None:
+        return 0, None
+    s = _f64(spheres).reshape(P, -1, 4)
+    return s.shape[1], np.ascontiguousarray(s)
+
+
+def traj_rows(robot, n_spheres, Tn):
+    return lib().orc_traj_rows(C.byref(robot), C.c_int(n_spheres), C.c_int(Tn))
+
+
+def traj_eval(robot, weights, spheres, u_start, goal, x, want=("F",), threads=None):
+    """Trajectory cost F [P], gradient g [P][Tn-1][d], residuals r [P][rows].
+    x: free states [P][Tn-1][d]; u_start [P][d]; goal [P][7]; spheres [P][no][4] or None."""
+    x = _f64(x)
+    P, Tm1, d = x.shape
+    no, sp = _per_problem_spheres(spheres, P)
+    us, gl = _f64(u_start).reshape(P, d), _f64(goal).reshape(P, 7)
+    F = np.zeros(P) if "F" in want else None
+    g = np.zeros((P, Tm1, d)) if "g" in want else None
+    r = np.zeros((P, traj_rows(robot, no, Tm1 + 1))) if "r" in want else None
+    rc = lib().orc_traj_eval(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(us), _dp(gl),
+                             C.c_int(Tm1 + 1), _dp(x), C.c_int64(P), _dp(F), _dp(g), _dp(r),
+                             C.c_int(_threads(threads)))
+    assert rc == 0
+    return {k: v for k, v in (("F", F), ("g", g), ("r", r)) if v is not None}
+
+
+def traj_pg(robot, weights, spheres, u_start, goal, x0, steps, alpha0, threads=None):
+    x = _f64(x0).copy()
+    P, Tm1, d = x.shape
+    no, sp = _per_problem_spheres(spheres, P)
+    F = np.zeros(P)
+    lib().orc_traj_pg(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(u_start)), _dp(_f64(goal)),
+                      C.c_int(Tm1 + 1), _dp(x), C.c_int64(P), C.c_int(steps), C.c_double(alpha0), _dp(F),
+                      C.c_int(_threads(threads)))
+    return x, F
+
+
+def solve_traj(robot, weights, spheres, u_start, goal, Tn, ik_cfg: "IkConfig", k_traj, alpha0, threads=None):
+    us = _f64(u_start)
+    P, d = us.shape
+    no, sp = _per_problem_spheres(spheres, P)
+    X = np.zeros((P, Tn, d))
+    F, gp, gr, sv, sa = (np.zeros(P) for _ in range(5))
+    lo, co = np.zeros(P, np.uint8), np.zeros(P, np.uint8)
+    lib().orc_solve_traj(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(us), _dp(_f64(goal)),
+                         C.c_int64(P), C.c_int(Tn), C.byref(ik_cfg.c()), C.c_int(k_traj), C.c_double(alpha0),
+                         _dp(X), _dp(F), _dp(gp), _dp(gr), _dp(sv), _dp(sa),
+                         lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)),
+                         C.c_int(_threads(threads)))
+    return dict(x=X, F=F, goal_pos=gp, goal_rot=gr, speed=sv, accel=sa, lim_ok=lo.astype(bool),
+                col_ok=co.astype(bool))
+
+
+def calibrate(robot, U, Pm, theta0, iters, lambda0=1e-3, history=False):
+    """LM on theta = (L_1..n, r_c,1..n) from known displacements U [K][d] and tip positions Pm [K][3]."""
+    U, Pm = _f64(U), _f64(Pm)
+    th = _f64(theta0).copy()
+    F = C.c_double(0)
+    hist = np.zeros((iters, th.size)) if history else None
+    lib().orc_calibrate(C.byref(robot), _dp(U), _dp(Pm), C.c_int(U.shape[0]), _dp(th), C.c_int(iters),
+                        C.c_double(lambda0), C.byref(F), _dp(hist))
+    out = dict(theta=th, F=F.value)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+def calib_jacobian(robot, U, Pm, theta):
+    U, Pm = _f64(U), _f64(Pm)
+    J = np.zeros((3 * U.shape[0], 2 * robot.n))
+    lib().orc_calib_jacobian(C.byref(robot), _dp(U), _dp(Pm), C.c_int(U.shape[0]), _dp(_f64(theta)), _dp(J))
+    return J
+
+
+def path_rows(robot, n_spheres, H):
+    return lib().orc_path_rows(C.byref(robot), C.c_int(n_spheres), C.c_int(H))
+
+
+def path_residual(robot, weights, spheres, wp, x, jacobian=False):
+    """One path: spheres [no][4] or None, wp [H][7], x [H][d] -> r (and the full J by complex step)."""
+    no, sp = _spheres(spheres)
+    x = _f64(x)
+    H, d = x.shape
+    nr = path_rows(robot, no, H)
+    r = np.zeros(nr)
+    J = np.zeros((nr, H * d)) if jacobian else None
+    lib().orc_path_residual(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(wp)), C.c_int(H),
+                            _dp(x), _dp(r), _dp(J))
+    return (r, J) if jacobian else r
+
+
+def path_lm(robot, weights, spheres, wp, x0, iters, lambda0=1e-3, history=False):
+    no, sp = _spheres(spheres)
+    x = _f64(x0).copy()
+    H, d = x.shape
+    lam, nu, F = C.c_double(lambda0), C.c_double(2.0), C.c_double(0)
+    hist = np.zeros((iters, H, d)) if history else None
+    acc = np.zeros(iters, np.uint8)
+    lib().orc_path_lm(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(wp)), C.c_int(H), _dp(x),
+                      C.c_int(iters), C.byref(lam), C.byref(nu), C.byref(F), _dp(hist),
+                      acc.ctypes.data_as(C.POINTER(C.c_uint8)))
+    out = dict(x=x, lam=lam.value, nu=nu.value, F=F.value, acc=acc)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+def solve_path(robot, weights, spheres, wp, ik_cfg: "IkConfig", k_warm, k_joint, threads=None):
+    """Path following for P paths: spheres [P][no][4] or None, wp [P][H][7]."""
+    wp = _f64(wp)
+    P, H, _ = wp.shape
+    no, sp = _per_problem_spheres(spheres, P)
+    d = robot.n * robot.m
+    X = np.zeros((P, H, d))
+    SX = np.zeros((P, H, d))
+    F = np.zeros(P)
+    pos, rot = np.zeros((P, H)), np.zeros((P, H))
+    lo, co = np.zeros(P, np.uint8), np.zeros(P, np.uint8)
+    lib().orc_solve_path(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(wp), C.c_int64(P), C.c_int(H),
+                         C.byref(ik_cfg.c()), C.c_int(k_warm), C.c_int(k_joint), _dp(X), _dp(F), _dp(pos), _dp(rot),
+                         _dp(SX), lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)),
+                         C.c_int(_threads(threads)))
+    return dict(x=X, stage_x=SX, F=F, pos=pos, rot=rot, lim_ok=lo.astype(bool), col_ok=co.astype(bool))

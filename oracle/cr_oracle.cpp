@@ -24,6 +24,13 @@
 //     gain-ratio damping update of Madsen, Nielsen and Tingleff).
 //   * Algorithm 1 (beam search IK): SampleSeeds -> ParallelOptimize(k_init) -> SelectTop(N_final) ->
 //     ParallelOptimize(k_final) -> argmin.
+//   * Trajectory planning (Sec. IV-A, Eq. mp_length_only with the tendon speed / acceleration
+//     limits by finite differences; Alg. 2's refinement stage after the linear initialiser of
+//     Sec. V-C): goal IK, linear interpolation, projected-gradient refinement of all states.
+//   * Path following (Sec. IV-A, Eq. constrained_mp; Sec. IV-B "Path Following"): IK at the first
+//     waypoint, warm-started per-waypoint IK, then joint LM over all waypoints with successive-state
+//     smoothness rows and a dense Cholesky of the whole normal matrix.
+//   * Kinematic calibration of segment lengths and tendon radii from measured tip positions (LM).
 //
 // Derivatives are taken by the complex-step method (Squire and Trapp 1998): for a real-analytic
 // function f, f'(x) = Im f(x + i h) / h up to O(h^2), with no subtractive cancellation, so with
@@ -1204,6 +1211,456 @@ int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* 
   out[1] = g_tally.f_sfu;
   out[2] = g_tally.t_flop;
   out[3] = g_tally.t_sfu;
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Generic LM iteration on a normal-equation callback (used where J is assembled blockwise)
+// ---------------------------------------------------------------------------------------------
+
+// normal(x, A, g) returns F(x) and fills A = J^T J (nx*nx, row-major) and g = J^T r; cost(x) = F.
+// Same rule as lm_iteration above.
+static int lm_iteration_ag(const std::function<double(const double*, double*, double*)>& normal,
+                           const std::function<double(const double*)>& cost, int nx, double* x,
+                           LmState& st) {
+  std::vector<double> A((size_t)nx * nx), g(nx), D(nx), Lm((size_t)nx * nx), delta(nx), xn(nx), mg(nx);
+  double F = normal(x, A.data(), g.data());
+  st.F = F;
+  for (int a = 0; a < nx; ++a) {
+    D[a] = std::max(A[(size_t)a * nx + a], 1e-12);
+    A[(size_t)a * nx + a] += st.lambda * D[a];
+  }
+  if (!cholesky(nx, A.data(), Lm.data())) {
+    st.lambda *= st.nu;
+    st.nu *= 2.0;
+    return 0;
+  }
+  for (int a = 0; a < nx; ++a) mg[a] = -g[a];
+  chol_solve(nx, Lm.data(), mg.data(), delta.data());
+  for (int a = 0; a < nx; ++a) xn[a] = x[a] + delta[a];
+  double Fn = cost(xn.data());
+  double pred = 0;
+  for (int a = 0; a < nx; ++a) pred += delta[a] * (st.lambda * D[a] * delta[a] - g[a]);
+  pred *= 0.5;
+  if (Fn < F) {
+    double rho = (F - Fn) / pred;
+    double t = 2.0 * rho - 1.0;
+    st.lambda *= std::max(1.0 / 3.0, 1.0 - t * t * t);
+    st.nu = 2.0;
+    for (int a = 0; a < nx; ++a) x[a] = xn[a];
+    st.F = Fn;
+    return 1;
+  }
+  st.lambda *= st.nu;
+  st.nu *= 2.0;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Trajectory planning
+// ---------------------------------------------------------------------------------------------
+
+// Residual of one trajectory of Tn >= 2 states; u_0 = u_start is fixed and x holds u_1..u_{Tn-1}.
+// Rows, for t = 1..Tn-1 in order: path length sqrt(w_len)(p_t - p_{t-1}) (3, a sum-of-squares
+// reading of the length objective), tendon speed hinges sqrt(rho_v) max(0, +-(u_t - u_{t-1})/dt -
+// v_max) (2d), the state rows of u_t; for t >= 2 the acceleration hinges sqrt(rho_a) max(0,
+// +-(u_t - 2 u_{t-1} + u_{t-2})/dt^2 - a_max) (2d). Last, the goal pose rows (6, full pose) of
+// u_{Tn-1}. Tendon lengths are L_i + u_ij with fixed L_i, so tendon speeds are differences of u.
+template <class T>
+static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
+                         const double* spheres, const double* u_start, const double* goal, int Tn,
+                         const T* x, T* r) {
+  const int d = rb.n * rb.m;
+  const int nbp = 3 * rb.n * rb.nb;
+  std::vector<T> U((size_t)Tn * d), bb(no > 0 ? (size_t)Tn * nbp : 0);
+  for (int a = 0; a < d; ++a) U[a] = T(u_start[a]);
+  for (int t = 1; t < Tn; ++t)
+    for (int a = 0; a < d; ++a) U[(size_t)t * d + a] = x[(size_t)(t - 1) * d + a];
+  std::vector<FkOut<T>> fk(Tn);
+  for (int t = 0; t < Tn; ++t)
+    forward_kinematics(rb, P, &U[(size_t)t * d], fk[t], no > 0 ? &bb[(size_t)t * nbp] : nullptr);
+  T sl = T(std::sqrt(W.w_len)), sv = T(std::sqrt(W.rho_v)), sa = T(std::sqrt(W.rho_a));
+  int k = 0;
+  for (int t = 1; t < Tn; ++t) {
+    for (int a = 0; a < 3; ++a) r[k++] = sl * (fk[t].p[a] - fk[t - 1].p[a]);
+    for (int q = 0; q < d; ++q) {
+      T v = (U[(size_t)t * d + q] - U[(size_t)(t - 1) * d + q]) / T(W.dt);
+      r[k++] = sv * hinge(v - T(W.vmax));
+      r[k++] = sv * hinge(T(-W.vmax) - v);
+    }
+    k += state_constraint_rows(rb, W, no, spheres, &U[(size_t)t * d], fk[t],
+                               no > 0 ? &bb[(size_t)t * nbp] : (const T*)nullptr, r + k, (T*)nullptr);
+    if (t >= 2) {
+      for (int q = 0; q < d; ++q) {
+        T acc = (U[(size_t)t * d + q] - T(2.0) * U[(size_t)(t - 1) * d + q] + U[(size_t)(t - 2) * d + q]) /
+                T(W.dt * W.dt);
+        r[k++] = sa * hinge(acc - T(W.amax));
+        r[k++] = sa * hinge(T(-W.amax) - acc);
+      }
+    }
+  }
+  pose_residual(OR_IK6, W, goal, fk[Tn - 1].R, fk[Tn - 1].p, r + k);
+  k += 6;
+  return k;
+}
+
+static int traj_rows(const OrRobot& rb, int no, int Tn) {
+  const int d = rb.n * rb.m;
+  return (Tn - 1) * (3 + 2 * d + state_constraint_count(rb, no)) + std::max(0, Tn - 2) * 2 * d + 6;
+}
+
+struct TrajProblem {
+  const OrRobot* rb;
+  const OrWeights* W;
+  int no;
+  const double* spheres;
+  const double* u_start;
+  const double* goal;
+  int Tn;
+  int nx() const { return (Tn - 1) * rb->n * rb->m; }
+  int rows() const { return traj_rows(*rb, no, Tn); }
+  double cost(const double* x) const {
+    std::vector<double> r(rows());
+    Params<double> P = params_of<double>(*rb);
+    traj_residual(*rb, P, *W, no, spheres, u_start, goal, Tn, x, r.data());
+    return half_sq(r.data(), rows());
+  }
+  // gradient of F by complex step on F itself
+  void grad(const double* x, double* g) const {
+    int n = nx();
+    std::vector<cd> xc(n), r(rows());
+    Params<cd> P = params_of<cd>(*rb);
+    for (int c = 0; c < n; ++c) {
+      for (int q = 0; q < n; ++q) xc[q] = cd(x[q], q == c ? CS_H : 0.0);
+      traj_residual(*rb, P, *W, no, spheres, u_start, goal, Tn, xc.data(), r.data());
+      g[c] = half_sq(r.data(), rows()).imag() / CS_H;
+    }
+  }
+};
+
+// Projected-gradient refinement of a trajectory (same step rule as stage one of Algorithm 1, with
+// the norm taken over all free states and the projection applied to every state's segments).
+static void traj_pg(const TrajProblem& tp, double* x, int steps, double alpha0, double* F_out) {
+  const OrRobot& rb = *tp.rb;
+  int n = tp.nx(), d = rb.n * rb.m;
+  std::vector<double> g(n), x1(n), v(n), g1(n);
+  double F = tp.cost(x);
+  tp.grad(x, g.data());
+  double alpha = alpha0;
+  for (int it = 0; it < steps; ++it) {
+    double gn = 0;
+    for (int a = 0; a < n; ++a) gn += g[a] * g[a];
+    gn = std::sqrt(gn);
+    double scale = gn > 0 ? alpha / gn : 0.0;
+    for (int a = 0; a < n; ++a) v[a] = x[a] - scale * g[a];
+    for (int t = 0; t < tp.Tn - 1; ++t)
+      for (int i = 0; i < rb.n; ++i)
+        project_segment(&v[(size_t)t * d + rb.m * i], rb.m, rb.umax[i], &x1[(size_t)t * d + rb.m * i]);
+    double F1 = tp.cost(x1.data());
+    if (F1 < F) {
+      tp.grad(x1.data(), g1.data());
+      for (int a = 0; a < n; ++a) { x[a] = x1[a]; g[a] = g1[a]; }
+      F = F1;
+      alpha *= 1.25;
+    } else {
+      alpha *= 0.5;
+    }
+  }
+  if (F_out) *F_out = F;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Path following
+// ---------------------------------------------------------------------------------------------
+
+// Rows of one waypoint t against its reference pose: the IK residual (pose + state rows).
+// The path residual stacks the waypoint rows for t = 0..H-1, then the smoothness rows
+// sqrt(w_s)(u_t - u_{t-1}) for t = 1..H-1 (d each).
+template <class T>
+static int path_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
+                         const double* spheres, const double* wp, int H, const T* x, T* r) {
+  const int d = rb.n * rb.m;
+  int k = 0;
+  for (int t = 0; t < H; ++t)
+    k += ik_residual(rb, P, W, no, spheres, OR_IK6, wp + 7 * t, x + (size_t)t * d, r + k, (T*)nullptr);
+  T ss = T(std::sqrt(W.w_s));
+  for (int t = 1; t < H; ++t)
+    for (int q = 0; q < d; ++q) r[k++] = ss * (x[(size_t)t * d + q] - x[(size_t)(t - 1) * d + q]);
+  return k;
+}
+
+static int path_rows(const OrRobot& rb, int no, int H) {
+  return H * ik_rows(rb, no) + (H - 1) * rb.n * rb.m;
+}
+
+struct PathProblem {
+  const OrRobot* rb;
+  const OrWeights* W;
+  int no;
+  const double* spheres;
+  const double* wp;
+  int H;
+  int d() const { return rb->n * rb->m; }
+  int nx() const { return H * d(); }
+  double cost(const double* x) const {
+    std::vector<double> r(path_rows(*rb, no, H));
+    Params<double> P = params_of<double>(*rb);
+    path_residual(*rb, P, *W, no, spheres, wp, H, x, r.data());
+    return half_sq(r.data(), (int)r.size());
+  }
+  // F, A = J^T J and g = J^T r. The waypoint rows of t depend only on u_t, so their Jacobian block
+  // is taken by complex step over u_t alone; each smoothness row has entries +-sqrt(w_s).
+  double normal(const double* x, double* A, double* g) const {
+    const int dd = d(), n = nx();
+    for (size_t a = 0; a < (size_t)n * n; ++a) A[a] = 0.0;
+    for (int a = 0; a < n; ++a) g[a] = 0.0;
+    double F = 0.0;
+    for (int t = 0; t < H; ++t) {
+      IkProblem pb{rb, W, no, spheres, OR_IK6, wp + 7 * t};
+      int nr = pb.rows();
+      std::vector<double> r(nr), J((size_t)nr * dd);
+      pb.res(x + (size_t)t * dd, r.data());
+      cs_jacobian([&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, dd, nr, x + (size_t)t * dd, J.data());
+      for (int k = 0; k < nr; ++k) F += 0.5 * r[k] * r[k];
+      for (int a = 0; a < dd; ++a) {
+        double s = 0;
+        for (int k = 0; k < nr; ++k) s += J[(size_t)k * dd + a] * r[k];
+        g[t * dd + a] += s;
+        for (int b = 0; b < dd; ++b) {
+          double m = 0;
+          for (int k = 0; k < nr; ++k) m += J[(size_t)k * dd + a] * J[(size_t)k * dd + b];
+          A[(size_t)(t * dd + a) * n + t * dd + b] += m;
+        }
+      }
+    }
+    const double ss = std::sqrt(W->w_s);
+    for (int t = 1; t < H; ++t)
+      for (int q = 0; q < dd; ++q) {
+        int i1 = t * dd + q, i0 = (t - 1) * dd + q;  // row = ss (x[i1] - x[i0])
+        double r = ss * (x[i1] - x[i0]);
+        F += 0.5 * r * r;
+        g[i1] += ss * r;
+        g[i0] -= ss * r;
+        A[(size_t)i1 * n + i1] += ss * ss;
+        A[(size_t)i0 * n + i0] += ss * ss;
+        A[(size_t)i1 * n + i0] -= ss * ss;
+        A[(size_t)i0 * n + i1] -= ss * ss;
+      }
+    return F;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Calibration: r(theta) = p(u_k; L, r_c) - p_k, k < K, theta = (L_1..n, r_c,1..n)
+// ---------------------------------------------------------------------------------------------
+template <class T>
+static void calib_residual(const OrRobot& rb, const double* U, const double* Pm, int K, const T* theta, T* r) {
+  const int d = rb.n * rb.m;
+  Params<T> P;
+  for (int i = 0; i < rb.n; ++i) { P.L[i] = theta[i]; P.rc[i] = theta[rb.n + i]; }
+  std::vector<T> u(d);
+  for (int k = 0; k < K; ++k) {
+    for (int a = 0; a < d; ++a) u[a] = T(U[(size_t)k * d + a]);
+    FkOut<T> o;
+    forward_kinematics(rb, P, u.data(), o, (T*)nullptr);
+    for (int a = 0; a < 3; ++a) r[3 * k + a] = o.p[a] - T(Pm[3 * k + a]);
+  }
+}
+
+extern "C" {
+
+int orc_traj_rows(const OrRobot* rb, int no, int Tn) { return traj_rows(*rb, no, Tn); }
+
+// Trajectory cost / gradient / residuals of P problems. u_start [P][d], goal [P][7], spheres
+// [P][no][4] (per problem), x [P][(Tn-1)][d] (the free states u_1..u_{Tn-1}).
+int orc_traj_eval(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+                  const double* u_start, const double* goal, int Tn, const double* x, int64_t P,
+                  double* F, double* g, double* r, int threads) {
+  if (Tn < 2) return 1;
+  const int d = rb->n * rb->m;
+  parallel_for(P, threads, [&](int64_t q) {
+    TrajProblem tp{rb, W, no, no > 0 ? spheres + (size_t)4 * no * q : nullptr, u_start + (size_t)d * q,
+                   goal + 7 * q, Tn};
+    const double* xq = x + (size_t)tp.nx() * q;
+    if (F) F[q] = tp.cost(xq);
+    if (g) tp.grad(xq, g + (size_t)tp.nx() * q);
+    if (r) {
+      Params<double> Pd = params_of<double>(*rb);
+      traj_residual(*rb, Pd, *W, no, tp.spheres, tp.u_start, tp.goal, Tn, xq, r + (size_t)tp.rows() * q);
+    }
+  });
+  return 0;
+}
+
+int orc_traj_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* u_start,
+                const double* goal, int Tn, double* x, int64_t P, int steps, double alpha0, double* F, int threads) {
+  const int d = rb->n * rb->m;
+  parallel_for(P, threads, [&](int64_t q) {
+    TrajProblem tp{rb, W, no, no > 0 ? spheres + (size_t)4 * no * q : nullptr, u_start + (size_t)d * q,
+                   goal + 7 * q, Tn};
+    traj_pg(tp, x + (size_t)tp.nx() * q, steps, alpha0, F + q);
+  });
+  return 0;
+}
+
+// Trajectory planning per problem: IK to the goal pose (Algorithm 1 with ik_prm, seed counter p0 +
+// q), linear interpolation u_t = u_start + (t / (Tn-1)) (u_goal - u_start), then k_traj
+// projected-gradient steps. x_out [P][Tn][d] (all states, u_0 included); F_out [P]; goal_pos /
+// goal_rot [P]; speed / accel [P]: the largest |du|/dt / v_max and |d2u|/dt^2 / a_max; lim_ok /
+// col_ok [P]: every state within limits / collision-free.
+int orc_solve_traj(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+                   const double* u_start, const double* goal, int64_t P, int Tn, const OrIkParams* ik_prm,
+                   int k_traj, double alpha0, double* x_out, double* F_out, double* goal_pos, double* goal_rot,
+                   double* speed, double* accel, uint8_t* lim_ok, uint8_t* col_ok, int threads) {
+  const int d = rb->n * rb->m;
+  parallel_for(P, threads, [&](int64_t q) {
+    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    OrIkParams prm = *ik_prm;
+    prm.p0 = ik_prm->p0 + q;
+    double ug[OR_MAXSEG * 3], Fg, pe, re;
+    uint8_t ok;
+    orc_solve_ik(rb, W, no, sp, OR_IK6, goal + 7 * q, 1, &prm, ug, &Fg, &pe, &re, &ok, nullptr, nullptr, 1);
+    double* X = x_out + (size_t)Tn * d * q;
+    const double* u0 = u_start + (size_t)d * q;
+    for (int t = 0; t < Tn; ++t)
+      for (int a = 0; a < d; ++a) X[(size_t)t * d + a] = u0[a] + (double)t / (Tn - 1) * (ug[a] - u0[a]);
+    TrajProblem tp{rb, W, no, sp, u0, goal + 7 * q, Tn};
+    traj_pg(tp, X + d, k_traj, alpha0, F_out + q);
+    double pos, rot;
+    uint8_t lo, co;
+    accept_one(*rb, no, sp, OR_IK6, goal + 7 * q, X + (size_t)(Tn - 1) * d, ik_prm->lim_tol, &pos, &rot, &lo, &co);
+    goal_pos[q] = pos;
+    goal_rot[q] = rot;
+    bool lim = true, col = true;
+    for (int t = 0; t < Tn; ++t) {
+      double p2, r2;
+      uint8_t l2, c2;
+      accept_one(*rb, no, sp, OR_IK6, goal + 7 * q, X + (size_t)t * d, ik_prm->lim_tol, &p2, &r2, &l2, &c2);
+      lim = lim && l2;
+      col = col && c2;
+    }
+    double vm = 0, am = 0;
+    for (int t = 1; t < Tn; ++t)
+      for (int a = 0; a < d; ++a) {
+        vm = std::max(vm, std::fabs(X[(size_t)t * d + a] - X[(size_t)(t - 1) * d + a]) / W->dt / W->vmax);
+        if (t >= 2)
+          am = std::max(am, std::fabs(X[(size_t)t * d + a] - 2 * X[(size_t)(t - 1) * d + a] + X[(size_t)(t - 2) * d + a]) /
+                                (W->dt * W->dt) / W->amax);
+      }
+    speed[q] = vm;
+    accel[q] = am;
+    lim_ok[q] = lim;
+    col_ok[q] = col;
+  });
+  return 0;
+}
+
+// Calibration by LM on theta = (L, r_c): U [K][d] known displacements, Pm [K][3] measured tip
+// positions. theta [2n] in/out (initial guess in), hist [iters][2n] nullable, F_out = final cost.
+int orc_calibrate(const OrRobot* rb, const double* U, const double* Pm, int K, double* theta, int iters,
+                  double lambda0, double* F_out, double* hist) {
+  const int np = 2 * rb->n, nr = 3 * K;
+  auto fr = [&](const double* th, double* r) { calib_residual(*rb, U, Pm, K, th, r); };
+  auto fc = [&](const cd* th, cd* r) { calib_residual(*rb, U, Pm, K, th, r); };
+  LmState st{lambda0, 2.0, 0.0};
+  for (int it = 0; it < iters; ++it) {
+    lm_iteration(fr, fc, np, nr, theta, st);
+    if (hist) std::memcpy(hist + (size_t)it * np, theta, sizeof(double) * np);
+  }
+  std::vector<double> r(nr);
+  fr(theta, r.data());
+  *F_out = half_sq(r.data(), nr);
+  return 0;
+}
+
+// Jacobian of the calibration residual [3K][2n] by complex step (for the covariance pin).
+int orc_calib_jacobian(const OrRobot* rb, const double* U, const double* Pm, int K, const double* theta, double* J) {
+  auto fc = [&](const cd* th, cd* r) { calib_residual(*rb, U, Pm, K, th, r); };
+  cs_jacobian(fc, 2 * rb->n, 3 * K, theta, J);
+  return 0;
+}
+
+int orc_path_rows(const OrRobot* rb, int no, int H) { return path_rows(*rb, no, H); }
+
+// Path residual r [rows] of one path (spheres [no][4], waypoints wp [H][7], x [H][d]); and its full
+// Jacobian J [rows][H d] by complex step over all H d variables (small H; pins the blockwise
+// assembly of the normal equations).
+int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp,
+                      int H, const double* x, double* r, double* J) {
+  Params<double> Pd = params_of<double>(*rb);
+  path_residual(*rb, Pd, *W, no, spheres, wp, H, x, r);
+  if (J) {
+    const int n = H * rb->n * rb->m, nr = path_rows(*rb, no, H);
+    cs_jacobian([&](const cd* xx, cd* rr) {
+      Params<cd> P = params_of<cd>(*rb);
+      path_residual(*rb, P, *W, no, spheres, wp, H, xx, rr);
+    }, n, nr, x, J);
+  }
+  return 0;
+}
+
+// Joint LM on one path: x [H][d] in/out, iters iterations; hist [iters][H][d] nullable.
+int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp, int H,
+                double* x, int iters, double* lam, double* nu, double* F_out, double* hist, uint8_t* acc) {
+  PathProblem pp{rb, W, no, spheres, wp, H};
+  LmState st{*lam, *nu, 0.0};
+  const int n = pp.nx();
+  for (int it = 0; it < iters; ++it) {
+    int a = lm_iteration_ag([&](const double* xx, double* A, double* g) { return pp.normal(xx, A, g); },
+                            [&](const double* xx) { return pp.cost(xx); }, n, x, st);
+    if (acc) acc[it] = (uint8_t)a;
+    if (hist) std::memcpy(hist + (size_t)it * n, x, sizeof(double) * n);
+  }
+  *lam = st.lambda;
+  *nu = st.nu;
+  *F_out = pp.cost(x);
+  return 0;
+}
+
+// Path following per path: IK at waypoint 0 (Algorithm 1 with ik_prm, seed counter p0 + q), then
+// for t >= 1 k_warm LM iterations of the waypoint's IK residual from u*_{t-1}, then k_joint joint
+// LM iterations over the whole path (lambda0 = ik_prm->lambda0). spheres [P][no][4], wp [P][H][7].
+// Outputs x_out [P][H][d], F_out [P] (joint cost), pos / rot [P][H] (per-waypoint errors),
+// stage_x [P][H][d] (nullable: the trajectory before the joint stage), lim_ok / col_ok [P].
+int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp,
+                   int64_t P, int H, const OrIkParams* ik_prm, int k_warm, int k_joint, double* x_out,
+                   double* F_out, double* pos, double* rot, double* stage_x, uint8_t* lim_ok, uint8_t* col_ok,
+                   int threads) {
+  const int d = rb->n * rb->m;
+  parallel_for(P, threads, [&](int64_t q) {
+    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    const double* wq = wp + (size_t)7 * H * q;
+    double* X = x_out + (size_t)H * d * q;
+    OrIkParams prm = *ik_prm;
+    prm.p0 = ik_prm->p0 + q;
+    double Fg, pe, re;
+    uint8_t ok;
+    orc_solve_ik(rb, W, no, sp, OR_IK6, wq, 1, &prm, X, &Fg, &pe, &re, &ok, nullptr, nullptr, 1);
+    for (int t = 1; t < H; ++t) {
+      double* xt = X + (size_t)t * d;
+      std::memcpy(xt, X + (size_t)(t - 1) * d, sizeof(double) * d);
+      IkProblem pb{rb, W, no, sp, OR_IK6, wq + 7 * t};
+      LmState st{ik_prm->lambda0, 2.0, 0.0};
+      for (int it = 0; it < k_warm; ++it)
+        lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
+                     [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), xt, st);
+    }
+    if (stage_x) std::memcpy(stage_x + (size_t)H * d * q, X, sizeof(double) * H * d);
+    double lam = ik_prm->lambda0, nu = 2.0;
+    orc_path_lm(rb, W, no, sp, wq, H, X, k_joint, &lam, &nu, &F_out[q], nullptr, nullptr);
+    bool lim = true, col = true;
+    for (int t = 0; t < H; ++t) {
+      uint8_t lo, co;
+      accept_one(*rb, no, sp, OR_IK6, wq + 7 * t, X + (size_t)t * d, ik_prm->lim_tol, &pos[(size_t)H * q + t],
+                 &rot[(size_t)H * q + t], &lo, &co);
+      lim = lim && lo;
+      col = col && co;
+    }
+    lim_ok[q] = lim;
+    col_ok[q] = col;
+  });
   return 0;
 }
 

@@ -179,3 +179,95 @@ def spheres_uniform(rng: np.random.Generator, count: int, lo, hi, r_lo: float, r
     c = rng.uniform(lo, hi, size=(count, 3))
     r = rng.uniform(r_lo, r_hi, size=(count, 1))
     return np.concatenate([c, r], axis=1)
+
+
+# ---------------------------------------------------------------------------------------------
+# Path following: 4-segment, 12-tendon robot; 512 paths of 64 waypoints; 32 spheres per path
+# ---------------------------------------------------------------------------------------------
+ROBOT_4SEG = RobotSpec(L=(0.10, 0.10, 0.10, 0.10), rc=0.005, umax=0.010, nb=16)
+P_PATH, H_PATH, NO_PATH = 512, 64, 32
+IK_PATH0 = IkSpec(S=64, n_final=8, k_init=32, k_final=30)   # the first waypoint
+K_WARM, K_JOINT = 30, 20                                     # per-waypoint warm start, joint LM
+
+# Trajectory planning: 3-segment robot; 256 problems of 32 states; 64 spheres per problem
+P_TRAJ, T_TRAJ, NO_TRAJ = 256, 32, 64
+IK_GOAL = IkSpec(S=64, n_final=4, k_init=32, k_final=30)     # IK to the goal pose
+K_TRAJ, ALPHA_TRAJ = 100, 1e-3
+
+# Calibration: 1024 measured tip positions, noise sigma = 0.5 mm, parameters off by up to 5%
+K_CALIB, SIGMA_CALIB, PERTURB_CALIB, ITERS_CALIB = 1024, 5e-4, 0.05, 20
+
+
+def bezier_states(rng: np.random.Generator, P: int, H: int, n_seg: int, umax: float) -> np.ndarray:
+    """[P][H][3 n_seg]: cubic Bezier curves in u-space through 4 hexagon-uniform control states,
+    sampled at H uniform parameter values (a convex combination, so in bounds with sum zero)."""
+    ctrl = hexagon_states(rng, 4 * P, n_seg, umax).reshape(P, 4, 3 * n_seg)
+    s = np.linspace(0.0, 1.0, H)
+    w = np.stack([(1 - s) ** 3, 3 * s * (1 - s) ** 2, 3 * s ** 2 * (1 - s), s ** 3], axis=1)  # [H][4]
+    return np.einsum("hk,pkd->phd", w, ctrl)
+
+
+def spheres_clear_of(rng: np.random.Generator, count: int, points: np.ndarray, margin_box: float,
+                     r_lo: float, r_hi: float, clearance: float, max_tries: int = 100000) -> np.ndarray:
+    """``count`` spheres [count][4] with centres uniform in the bounding box of ``points`` [M][3]
+    dilated by ``margin_box``, radius uniform in [r_lo, r_hi], each redrawn while its surface is
+    closer than ``clearance`` to any of the points."""
+    lo = points.min(axis=0) - margin_box
+    hi = points.max(axis=0) + margin_box
+    out = []
+    tries = 0
+    while len(out) < count and tries < max_tries:
+        tries += 1
+        c = rng.uniform(lo, hi)
+        r = rng.uniform(r_lo, r_hi)
+        if np.min(np.linalg.norm(points - c, axis=1)) >= r + clearance:
+            out.append(np.concatenate([c, [r]]))
+    if len(out) < count:
+        raise RuntimeError("could not place the spheres")
+    return np.array(out)
+
+
+def path_workload(robot: RobotSpec, P: int, H: int, n_spheres: int, fk_backbone, seed: int = 0,
+                  weights: WeightSpec = WEIGHTS):
+    """Reference paths: wp [P][H][7] (position + quaternion of FK of a Bezier curve in u-space),
+    the ground-truth states [P][H][d], spheres [P][n_spheres][4] clear of the ground-truth backbone
+    by r_body + delta. ``fk_backbone(u [N][d]) -> (T [N][12], backbone [N][n*nb][3])``."""
+    rng = np.random.default_rng(seed)
+    states = bezier_states(rng, P, H, robot.n, robot.umax)
+    T, bb = fk_backbone(states.reshape(P * H, -1))
+    wp = pose_targets(T, "pose").reshape(P, H, 7)
+    bb = np.asarray(bb).reshape(P, -1, 3)
+    sph = np.stack([spheres_clear_of(rng, n_spheres, bb[p], 0.02, 0.005, 0.015,
+                                     robot.body_radius + weights.delta) for p in range(P)]) if n_spheres else None
+    return wp, states, sph
+
+
+def traj_workload(robot: RobotSpec, P: int, n_spheres: int, fk_backbone, seed: int = 0,
+                  weights: WeightSpec = WEIGHTS):
+    """Trajectory problems: u_start [P][d] (uniform in bounds), goal [P][7] (full pose of FK of
+    another uniform state), spheres [P][n_spheres][4] clear of the start and goal backbones."""
+    rng = np.random.default_rng(seed)
+    us = hexagon_states(rng, P, robot.n, robot.umax)
+    ug = hexagon_states(rng, P, robot.n, robot.umax)
+    T, bb = fk_backbone(np.concatenate([us, ug]))
+    goal = pose_targets(np.asarray(T)[P:], "pose")
+    bb = np.asarray(bb)
+    sph = None
+    if n_spheres:
+        sph = np.stack([spheres_clear_of(rng, n_spheres, np.concatenate([bb[p], bb[P + p]]), 0.03, 0.005, 0.015,
+                                         robot.body_radius + weights.delta) for p in range(P)])
+    return us, goal, sph, ug
+
+
+def calib_workload(robot: RobotSpec, K: int, fk_with_params, seed: int = 0, sigma: float = SIGMA_CALIB,
+                   perturb: float = PERTURB_CALIB):
+    """Calibration data: U [K][d] uniform in bounds, true parameters theta_true = (L, r_c) scaled by
+    1 + U(-perturb, perturb) each, measured tip positions FK(U; theta_true) + N(0, sigma^2).
+    ``fk_with_params(U, L [n], rc [n]) -> T [K][12]``. Returns (U, Pm, theta_true, theta_nominal)."""
+    rng = np.random.default_rng(seed)
+    U = hexagon_states(rng, K, robot.n, robot.umax)
+    nominal = np.concatenate([np.array(robot.L, float), np.full(robot.n, robot.rc)])
+    true = nominal * (1.0 + rng.uniform(-perturb, perturb, nominal.shape))
+    T = np.asarray(fk_with_params(U, true[:robot.n], true[robot.n:]))
+    Pm = T[:, 9:12] + rng.normal(0.0, sigma, (K, 3))
+    return U, Pm, true, nominal
