@@ -31,6 +31,10 @@ WORKLOAD = "ik_3seg_9tendon_4096targets_256seeds_pg64_top8_lm30"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
+# DRAM bytes (read + write) of one stage-one launch per target, from an ncu capture of the same
+# kernel at 608 targets (dram__bytes_read.sum + dram__bytes_write.sum = 112,128 B); traffic grows in
+# proportion to the targets (each CTA reads its target and writes its candidates).
+STAGE1_DRAM_BYTES_PER_TARGET = 112128 / 608
 
 
 def parse():
@@ -278,7 +282,8 @@ def main():
     # ---- live calibration: FFMA / MUFU / DFMA / copy peaks on this GPU in the same run ----
     cal = {}
     pbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
-    for kind, name, it in ((0, "ffma_tflops", 4000), (1, "mufu_tops", 4000), (2, "dfma_tflops", 200), (3, "copy_gbs", 1)):
+    for kind, name, it in ((0, "ffma_tflops", 4000), (1, "mufu_tops", 4000), (2, "dfma_tflops", 200), (3, "copy_gbs", 1),
+                           (4, "dfma_one_lane_tflops", 200)):
         lib.cr_peak_launch(kind, pbuf, it)
         best = 0.0
         for _ in range(3):
@@ -337,7 +342,8 @@ def main():
         "success_rate": succ, "pos_err_median_m": pos_med, "rot_err_median_rad": rot_med, "device_status": status,
         "evals_per_s": world * (n_eval + P * ik.n_final * (2 * ik.k_final + 1)) / (ms_per_step / 1e3),
         "roofline": {"bound": "alu", "kernel": "k_ik_stage1", "achieved": achieved_tflops, "peak": peak_fp32,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_fp32, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / peak_fp32,
+                     "traffic": STAGE1_DRAM_BYTES_PER_TARGET * P,
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
                      "kernel_ms": s1_ms, "evals_per_launch": n_eval, "flop_per_eval": flop_per_eval,
                      "frac_of_live_ffma": achieved_tflops / cal["ffma_tflops"],

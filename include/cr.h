@@ -276,7 +276,8 @@ CR_API const char* cr_last_error_string(void);
 
 /* Peak-calibration kernels (FP32 FMA chains, special-function chains, FP64 FMA chains and a
  * streaming copy), timed by the caller with events around the launch. kind: 0 FFMA, 1 MUFU
- * (sin/cos approximations), 2 DFMA, 3 copy. `buf` is a device buffer of `bytes` bytes (copy
+ * (sin/cos approximations), 2 DFMA, 3 copy, 4 DFMA with one active lane per warp (how the FP64
+ * pipe charges partly active warps). `buf` is a device buffer of `bytes` bytes (copy
  * reads the first half and writes the second). *ops_out (host) receives the operations one
  * launch performs (flops for 0 and 2, special-function results for 1, bytes moved for 3). */
 CR_API cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32_t iters, double* ops_out,

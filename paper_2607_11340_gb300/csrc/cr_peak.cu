@@ -45,6 +45,22 @@ __global__ void __launch_bounds__(256) k_peak_dfma(double* out, int iters) {
   if (s == 12345.678) out[threadIdx.x] = s;
 }
 
+// DFMA chains on one lane of every warp: how the FP64 pipe charges an instruction whose warp has
+// a single active lane (the other lanes skip the loop).
+__global__ void __launch_bounds__(256) k_peak_dfma_lane(double* out, int iters) {
+  if ((threadIdx.x & 31) != 0) return;
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+  const double m = 0.9999999, c = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    }
+  }
+  double s = a0 + a1 + a2 + a3;
+  if (s == 12345.678) out[threadIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(256) k_peak_copy(const float4* __restrict__ src, float4* __restrict__ dst, size_t n) {
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
@@ -83,6 +99,10 @@ extern "C" cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32
     case 2:
       k_peak_dfma<<<blocks, threads, 0, s>>>((double*)buf, iters);
       *ops_out = nthr * iters * 8 * 4 * 2.0;
+      break;
+    case 4:
+      k_peak_dfma_lane<<<blocks, threads, 0, s>>>((double*)buf, iters);
+      *ops_out = nthr / 32 * iters * 8 * 4 * 2.0;
       break;
     case 3: {
       size_t n = bytes / 2 / sizeof(float4);
