@@ -90,11 +90,13 @@ typedef struct {
 } cr_weights;
 
 /* Obstacles: spheres for the clearance rows of Eq. ik_coll. Host struct; `spheres` is a device
- * array [n_o][4] = (centre x, y, z, radius), FP64. */
+ * array [n_o][4] = (centre x, y, z, radius), FP64, shared by all problems; with per_problem = 1 it
+ * is [P][n_o][4] and problem p uses its own n_o spheres (trajectory and path workloads place
+ * obstacles around each problem). */
 typedef struct {
   const double* spheres;
-  int32_t n_o; /* 0..CR_MAX_SPHERES */
-  int32_t reserved;
+  int32_t n_o;         /* 0..CR_MAX_SPHERES */
+  int32_t per_problem; /* 0: one sphere set for all problems; 1: one set per problem */
 } cr_scene;
 
 typedef enum {
@@ -262,6 +264,69 @@ CR_API cr_status cr_solve_ik_static(const cr_robot* robot, const cr_scene* scene
                                     double* rot_err, uint8_t* success, cr_stream stream);
 /* Capacity of that array in bytes (CR_STATIC_WS_BYTES). */
 CR_API size_t cr_static_workspace_capacity(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Trajectory planning (Sec. IV-A, Eq. mp_length_only and the tendon speed / acceleration limits
+ * by finite differences; Alg. 2 refinement after the linear initialiser of Sec. V-C)
+ * ------------------------------------------------------------------------------------------- */
+
+/* P trajectories of T states u_0..u_{T-1}; u_0 = u_start is fixed. Host struct; device arrays:
+ * u_start [3n][P] and goal [7][P] (full pose: position + quaternion w, x, y, z), FP64. The cost of
+ * one trajectory is 1/2 sum r^2 over, for t = 1..T-1: path length rows sqrt(w_len)(p_t - p_{t-1}),
+ * tendon speed hinges sqrt(rho_v) max(0, +-(u_t - u_{t-1})/dt - v_max), the state rows of u_t
+ * (bounds, sum-zero, curvature, clearance); for t >= 2 the acceleration hinges sqrt(rho_a)
+ * max(0, +-(u_t - 2 u_{t-1} + u_{t-2})/dt^2 - a_max); and the goal pose rows of u_{T-1}. */
+typedef struct {
+  const double* u_start;
+  const double* goal;
+  int64_t P;
+  int32_t T; /* 2..256 */
+  int32_t reserved;
+  cr_weights w;
+} cr_traj_task;
+
+/* Trajectory cost per problem (cost_out [P]) of the free states x [3n][P * (T-1)] (state t >= 1 of
+ * problem p at column p * (T-1) + t - 1), and optionally its gradient grad_out [3n][P * (T-1)] by
+ * the hand-written adjoint; with upstream [P] (nullable) the gradient of problem p is scaled by
+ * upstream[p] (a vector-Jacobian product). The adjoint recomputes the kinematics instead of storing
+ * them. All arrays in `dtype`. */
+CR_API cr_status cr_traj_cost(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                              const void* x, void* cost_out, void* grad_out, const void* upstream, int32_t dtype,
+                              cr_stream stream);
+
+/* Scratch bytes of cr_solve_traj. */
+CR_API size_t cr_traj_workspace_size(const cr_robot* robot, int64_t P, const cr_ik_params* goal_ik);
+
+/* Trajectory planning: IK to every goal pose (Algorithm 1 with goal_ik), linear interpolation
+ * u_t = u_start + t/(T-1) (u_goal - u_start), then k_traj projected-gradient steps of all free
+ * states (step rule of stage one, norm over the whole trajectory). Outputs (device, FP64): X_out
+ * [3n][P * T] (all states), cost_out [P], goal_pos / goal_rot [P] (m, rad), speed / accel [P]
+ * (largest |du|/dt / v_max and |d2u|/dt^2 / a_max), lim_ok / col_ok [P] (uint8: every state within
+ * limits / collision-free). goal_ik->precision selects the bulk precision of the whole solve. */
+CR_API cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                               const cr_ik_params* goal_ik, int32_t k_traj, double alpha0, double* X_out,
+                               double* cost_out, double* goal_pos, double* goal_rot, double* speed, double* accel,
+                               uint8_t* lim_ok, uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Kinematic calibration and vector-Jacobian products (differentiation w.r.t. the robot)
+ * ------------------------------------------------------------------------------------------- */
+
+/* LM calibration of theta = (L_1..n, r_c,1..n) from K known displacements U [3n][K] (`dtype`) and
+ * measured tip positions P_meas [3][K] (FP64): residual p(u_k; theta) - p_k. theta (device, FP64,
+ * [2n]) holds the initial guess and receives the estimate; F_out (device, [1]) the final cost;
+ * hist (device, nullable, [iters][2n]) the iterates. Same LM rule as cr_lm_step; J^T J and J^T r
+ * reduced in FP64 in a fixed order, Cholesky in FP64. Runs as one CTA of 1024 threads. */
+CR_API cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_meas, int64_t K, double* theta,
+                              int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype,
+                              cr_stream stream);
+
+/* Vector-Jacobian product of the IK cost: grad_u_out[:, b] = upstream[b] dF_b/du_b and
+ * grad_param_out [2n] (FP64) = sum_b upstream[b] dF_b/d(L, r_c). workspace: [2n][B] in `dtype`.
+ * upstream [B], grad_u_out [3n][B] in `dtype`. The adjoint recomputes the forward sweep. */
+CR_API cr_status cr_cost_vjp(const cr_robot* robot, const cr_scene* scene, const cr_task* task, const void* u,
+                             int64_t B, const void* upstream, void* grad_u_out, double* grad_param_out, void* workspace,
+                             int32_t dtype, cr_stream stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Status and diagnostics

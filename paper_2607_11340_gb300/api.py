@@ -32,18 +32,21 @@ def weights_struct(w: synth.WeightSpec) -> lib.cr_weights:
 
 
 class Scene:
-    """Spheres [n_o][4] (centre, radius) resident on the device in FP64."""
+    """Spheres resident on the device in FP64: [n_o][4] (centre, radius) shared by all problems, or
+    [P][n_o][4] with per_problem=True (each problem its own set)."""
 
-    def __init__(self, spheres=None, device="cuda"):
+    def __init__(self, spheres=None, device="cuda", per_problem=False):
         if spheres is None or len(spheres) == 0:
             self.spheres = None
             self.n_o = 0
         else:
-            self.spheres = torch.as_tensor(spheres, dtype=torch.float64, device=device).reshape(-1, 4).contiguous()
-            self.n_o = self.spheres.shape[0]
+            t = torch.as_tensor(spheres, dtype=torch.float64, device=device)
+            self.spheres = (t.reshape(t.shape[0], -1, 4) if per_problem else t.reshape(-1, 4)).contiguous()
+            self.n_o = self.spheres.shape[-2]
         self.c = lib.cr_scene()
         self.c.spheres = self.spheres.data_ptr() if self.spheres is not None else None
         self.c.n_o = self.n_o
+        self.c.per_problem = 1 if (per_problem and self.n_o > 0) else 0
 
 
 def task_struct(kind: int, targets_soa: torch.Tensor, S: int, weights: synth.WeightSpec) -> lib.cr_task:
@@ -184,3 +187,114 @@ def solve_ik(robot_spec, ik_spec, weights, kind, targets_soa, scene=None, precis
     s = IkSolver(robot_spec, ik_spec, weights, kind, targets_soa.shape[1], scene, precision, plain,
                  device=targets_soa.device)
     return s.solve(targets_soa)
+
+
+# ---------------------------------------------------------------------------------------------
+# Differentiation: the hand-written adjoint behind torch.autograd.Function (recompute-in-backward)
+# ---------------------------------------------------------------------------------------------
+class IkCost(torch.autograd.Function):
+    """Per-state IK cost F_b(u_b; L, r_c). forward(u [d][B], L [n], r_c [n], ctx_data) -> cost [B].
+
+    backward recomputes the forward sweep inside the adjoint kernel (nothing but the inputs is
+    saved) and returns dF/du (scaled by the upstream gradient) and sum_b upstream_b dF_b/d(L, r_c).
+    ``ctx_data`` = (RobotSpec, Scene, task struct); L and r_c are host tensors (small).
+    """
+
+    @staticmethod
+    def forward(ctx, u, L, rc, ctx_data):
+        spec, scene, task = ctx_data
+        robot = robot_struct(spec)
+        for i in range(spec.n):
+            robot.L[i] = float(L[i])
+            robot.r_c[i] = float(rc[i])
+        cost = torch.empty(u.shape[1], dtype=u.dtype, device=u.device)
+        lib.cr_cost_grad(robot, scene.c, task, u.contiguous(), cost)
+        ctx.save_for_backward(u)
+        ctx.robot, ctx.scene, ctx.task, ctx.n = robot, scene, task, spec.n
+        ctx.param_dtype, ctx.param_device = L.dtype, L.device
+        return cost
+
+    @staticmethod
+    def backward(ctx, gcost):
+        (u,) = ctx.saved_tensors
+        gu = torch.empty_like(u)
+        gp = torch.empty(2 * ctx.n, dtype=torch.float64, device=u.device)
+        ws = torch.empty((2 * ctx.n, u.shape[1]), dtype=u.dtype, device=u.device)
+        lib.cr_cost_vjp(ctx.robot, ctx.scene.c, ctx.task, u.contiguous(), gcost.contiguous().to(u.dtype), gu, gp, ws)
+        gp = gp.to(ctx.param_device, ctx.param_dtype)
+        return gu, gp[:ctx.n], gp[ctx.n:], None
+
+
+class TrajCost(torch.autograd.Function):
+    """Trajectory cost per problem: forward(x [d][P*(T-1)], ctx_data) -> cost [P] (free states only;
+    u_0 = u_start is fixed). backward recomputes the kinematics in the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, x, ctx_data):
+        robot, scene, task = ctx_data
+        cost = torch.empty(task.P, dtype=x.dtype, device=x.device)
+        lib.cr_traj_cost(robot, scene.c, task, x.contiguous(), cost)
+        ctx.save_for_backward(x)
+        ctx.data = ctx_data
+        return cost
+
+    @staticmethod
+    def backward(ctx, gcost):
+        (x,) = ctx.saved_tensors
+        robot, scene, task = ctx.data
+        cost = torch.empty(task.P, dtype=x.dtype, device=x.device)
+        g = torch.empty_like(x)
+        lib.cr_traj_cost(robot, scene.c, task, x.contiguous(), cost, g, gcost.contiguous().to(x.dtype))
+        return g, None
+
+
+def traj_task_struct(u_start_soa, goal_soa, T: int, weights: synth.WeightSpec) -> lib.cr_traj_task:
+    """u_start_soa [d][P], goal_soa [7][P]: contiguous CUDA float64 (kept alive by the struct)."""
+    t = lib.cr_traj_task()
+    t._keep = (u_start_soa, goal_soa)
+    t.u_start = u_start_soa.data_ptr()
+    t.goal = goal_soa.data_ptr()
+    t.P = u_start_soa.shape[1]
+    t.T = T
+    t.w = weights_struct(weights)
+    return t
+
+
+class TrajSolver:
+    """Trajectory planning for P problems of T states (goal IK, linear initialisation, projected
+    gradient refinement)."""
+
+    def __init__(self, robot_spec, goal_ik: synth.IkSpec, weights, P, T, scene: Scene | None = None,
+                 precision=lib.CR_F32, k_traj=synth.K_TRAJ, alpha0=synth.ALPHA_TRAJ, device="cuda"):
+        self.robot = robot_struct(robot_spec)
+        self.weights = weights
+        self.P, self.T, self.k_traj, self.alpha0 = P, T, k_traj, alpha0
+        self.scene = scene or Scene(None)
+        self.prm = ik_params_struct(goal_ik, precision)
+        d = robot_spec.d
+        self.workspace = torch.empty(lib.cr_traj_workspace_size(self.robot, P, self.prm), dtype=torch.uint8,
+                                     device=device)
+        z = lambda *s, dt=torch.float64: torch.empty(s, dtype=dt, device=device)
+        self.X, self.cost, self.goal_pos, self.goal_rot = z(d, P * T), z(P), z(P), z(P)
+        self.speed, self.accel = z(P), z(P)
+        self.lim_ok, self.col_ok = z(P, dt=torch.uint8), z(P, dt=torch.uint8)
+
+    def solve(self, u_start_soa, goal_soa, p0: int = 0):
+        task = traj_task_struct(u_start_soa, goal_soa, self.T, self.weights)
+        self._task = task
+        self.prm.p0 = p0
+        lib.cr_solve_traj(self.robot, self.scene.c, task, self.prm, self.k_traj, self.alpha0, self.X, self.cost,
+                          self.goal_pos, self.goal_rot, self.speed, self.accel, self.lim_ok, self.col_ok,
+                          self.workspace)
+        return self
+
+
+def calibrate(robot_spec, U_soa, P_meas_soa, theta0, iters=synth.ITERS_CALIB, lambda0=1e-3, history=False):
+    """LM calibration of (L, r_c): U_soa [d][K] (float32/64 CUDA), P_meas_soa [3][K] FP64 CUDA.
+    Returns (theta [2n], F, hist or None) as device tensors."""
+    robot = robot_struct(robot_spec)
+    theta = torch.as_tensor(theta0, dtype=torch.float64, device=U_soa.device).clone()
+    F = torch.empty(1, dtype=torch.float64, device=U_soa.device)
+    hist = torch.empty((iters, 2 * robot_spec.n), dtype=torch.float64, device=U_soa.device) if history else None
+    lib.cr_calibrate(robot, U_soa, P_meas_soa, theta, iters, lambda0, F, hist)
+    return theta, F, hist

@@ -49,7 +49,16 @@ cr_status check_scene(const cr_scene* s) {
   if (!s) return CR_OK;  // no scene = no obstacles
   if (s->n_o < 0 || s->n_o > CR_MAX_SPHERES)
     return fail(CR_EINVAL, "scene.n_o = %d outside 0..%d", s->n_o, CR_MAX_SPHERES);
+  if (s->per_problem != 0 && s->per_problem != 1) return fail(CR_EINVAL, "scene.per_problem must be 0 or 1");
   if (s->n_o > 0) return check_ptr(s->spheres, 8, "scene.spheres", true);
+  return CR_OK;
+}
+
+cr_status check_scene_shared(const cr_scene* s) {
+  cr_status st = check_scene(s);
+  if (st) return st;
+  if (s && s->per_problem && s->n_o > 0)
+    return fail(CR_EINVAL, "this entry point takes one sphere set for the whole batch (per_problem = 0)");
   return CR_OK;
 }
 

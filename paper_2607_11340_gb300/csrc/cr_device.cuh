@@ -425,26 +425,26 @@ __device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T d
 }
 
 // ------------------------------------------------------------------------------------------------
-// Cost and adjoint of an IK state (forward sweep + reverse sweep over segments)
+// Cost and adjoint of one state, in two phases
 // ------------------------------------------------------------------------------------------------
-// Penalty rows on u of one state: bounds, sum-zero, curvature (value added to F, gradient in a/u).
-template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
-CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
-                T* coll_out) {
-  Chain<T, N> ch;
-  chain_forward(rb, u, ch);
-  T r[6], e[3], ang, sn, cs;
-  pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
-  T F = T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
-  // per-segment aggregates of the clearance rows (downstream force / moment, own-segment terms)
+// Per-segment aggregates of the clearance rows for the reverse sweep: G, M = force and moment (about
+// the origin) of the segment's own samples, Dx / Dy / DL = their direct terms in (ax, ay, L).
+template <typename T, int N> struct StateAgg {
   T G[N][3], M[N][3], Dx[N], Dy[N], DL[N];
+};
+
+// Forward phase: chain, clearance rows (and their aggregates when GRAD), and the penalty rows on u
+// (bounds, sum-zero, curvature). Returns their part of F; *coll_out = the clearance part.
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
+CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T>* sph, int no,
+                      const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out) {
+  chain_forward(rb, u, ch);
   T coll = T(0);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    G[i][0] = G[i][1] = G[i][2] = T(0);
-    M[i][0] = M[i][1] = M[i][2] = T(0);
-    Dx[i] = Dy[i] = DL[i] = T(0);
+    ag.G[i][0] = ag.G[i][1] = ag.G[i][2] = T(0);
+    ag.M[i][0] = ag.M[i][1] = ag.M[i][2] = T(0);
+    ag.Dx[i] = ag.Dy[i] = ag.DL[i] = T(0);
   }
   if (OBST && no > 0) {
     const T inb = T(1) / T(rb.nb);
@@ -473,10 +473,10 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
           }
         }
         if (GRAD && hit) {
-          G[i][0] += gw[0]; G[i][1] += gw[1]; G[i][2] += gw[2];
+          ag.G[i][0] += gw[0]; ag.G[i][1] += gw[1]; ag.G[i][2] += gw[2];
           T mw[3];
           cross(wp, gw, mw);
-          M[i][0] += mw[0]; M[i][1] += mw[1]; M[i][2] += mw[2];
+          ag.M[i][0] += mw[0]; ag.M[i][1] += mw[1]; ag.M[i][2] += mw[2];
           T gl[3];
           matTvec(ch.Rb[i], gw, gl);
           T axs = sg * ch.ax[i], ays = sg * ch.ay[i];
@@ -484,16 +484,15 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
           seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
           T dd[2][3], wl[2][3];
           seg_local_derivs(axs, ays, s, c, s3, cp, sg * rb.L[i], dd, wl);
-          Dx[i] += sg * (gl[0] * dd[0][0] + gl[1] * dd[0][1] + gl[2] * dd[0][2]);
-          Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
-          if (PGRAD) DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
+          ag.Dx[i] += sg * (gl[0] * dd[0][0] + gl[1] * dd[0][1] + gl[2] * dd[0][2]);
+          ag.Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
+          if (PGRAD) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
         }
       }
     }
   }
-  F += coll;
   if (coll_out) *coll_out = coll;
-  // penalty rows on u: bounds, sum-zero, curvature
+  T F = coll;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
@@ -509,28 +508,21 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
       F += T(0.5) * w.rho_k * vk * vk;
     }
   }
-  if (!GRAD) return F;
+  return F;
+}
 
-  // ---- reverse sweep ----
-  // force / moment (about the origin) of everything downstream, starting at the tip
-  T Fs[3] = {w.wp * r[0], w.wp * r[1], w.wp * r[2]};  // dF/dp = w_p^2 (p - p_t)
-  T gR[3];
-  if (kind == CR_TASK_IK5) {
-    // dF/d(rotation) = w_R^2 z_t x z for F = 1/2 w_R^2 |z - z_t|^2
-    T z[3] = {ch.R[2], ch.R[5], ch.R[8]};
-    T zt[3] = {tg.R[0], tg.R[1], tg.R[2]};
-    T cz[3];
-    cross(zt, z, cz);
-    gR[0] = w.wR2 * cz[0]; gR[1] = w.wR2 * cz[1]; gR[2] = w.wR2 * cz[2];
-  } else {
-    // dF/d(rotation) = w_R^2 R e (the inverse right Jacobian leaves e unchanged)
-    T re[3];
-    matvec(ch.R, e, re);
-    gR[0] = w.wR2 * re[0]; gR[1] = w.wR2 * re[1]; gR[2] = w.wR2 * re[2];
-  }
+// Reverse phase: given dF/dp at the tip (Ftip) and the world moment of dF/d(tip rotation) (Rtip),
+// sweep the segments from the tip to the base: the force and moment of everything downstream of
+// segment i act on (ax_i, ay_i) through the segment's local derivatives. Adds the penalty gradients
+// and writes dF/du (and dF/dL, dF/dr_c when PGRAD).
+template <typename T, int N, bool PGRAD>
+CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)[3 * N], const Chain<T, N>& ch,
+                         const StateAgg<T, N>& ag, const T (&Ftip)[3], const T (&Rtip)[3], T (&gu)[3 * N], T* gL,
+                         T* grc) {
+  T Fs[3] = {Ftip[0], Ftip[1], Ftip[2]};
   T Ms[3];
   cross(ch.p, Fs, Ms);
-  Ms[0] += gR[0]; Ms[1] += gR[1]; Ms[2] += gR[2];
+  Ms[0] += Rtip[0]; Ms[1] += Rtip[1]; Ms[2] += Rtip[2];
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
     T Pend[3];
@@ -552,8 +544,8 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
     T sp = T(0.5) * (s3 - cc);
     T Fa = ax * Fl[0] + ay * Fl[1], Ma = ax * Ml[0] + ay * Ml[1];
     T cf = cp * Fa + sp * Fl[2];
-    T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2] + Dx[i];
-    T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2] + Dy[i];
+    T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2] + ag.Dx[i];
+    T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2] + ag.Dy[i];
     if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T th = c_sqrt(ch.x[i]);
       T f = w.rho_k * (th - rb.thmax[i]) / th;
@@ -575,13 +567,52 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
     if (PGRAD) {
       // dF/dL_i: translation d_i = L (...) scales with L; own samples q scale with L too
       T di[3] = {rb.L[i] * ch.c[i] * ch.ax[i], rb.L[i] * ch.c[i] * ch.ay[i], rb.L[i] * ch.s[i]};
-      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / rb.L[i] + DL[i];
+      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / rb.L[i] + ag.DL[i];
       // dF/dr_c,i: a = K(...) with K = -2/(3 r_c) so da/dr_c = -a / r_c
       grc[i] = -(ch.ax[i] * gx + ch.ay[i] * gy) / rb.rc[i];
     }
-    Fs[0] += G[i][0]; Fs[1] += G[i][1]; Fs[2] += G[i][2];
-    Ms[0] += M[i][0]; Ms[1] += M[i][1]; Ms[2] += M[i][2];
+    Fs[0] += ag.G[i][0]; Fs[1] += ag.G[i][1]; Fs[2] += ag.G[i][2];
+    Ms[0] += ag.M[i][0]; Ms[1] += ag.M[i][1]; Ms[2] += ag.M[i][2];
   }
+}
+
+// Tip force and moment of the pose rows: dF/dp = w_p^2 (p - p_t); for IK6 the rotation term is
+// w_R^2 R e (the inverse right Jacobian leaves e unchanged), for IK5 (F = 1/2 w_R^2 |z - z_t|^2) it is
+// w_R^2 z_t x z.
+template <typename T>
+CR_HD void pose_tip_force(int kind, const WeightsK<T>& w, const TargetK<T>& tg, const T (&R)[9], const T (&r)[6],
+                          const T (&e)[3], T (&Ftip)[3], T (&Rtip)[3]) {
+  Ftip[0] = w.wp * r[0];
+  Ftip[1] = w.wp * r[1];
+  Ftip[2] = w.wp * r[2];
+  if (kind == CR_TASK_IK5) {
+    T z[3] = {R[2], R[5], R[8]};
+    T zt[3] = {tg.R[0], tg.R[1], tg.R[2]};
+    T cz[3];
+    cross(zt, z, cz);
+    Rtip[0] = w.wR2 * cz[0]; Rtip[1] = w.wR2 * cz[1]; Rtip[2] = w.wR2 * cz[2];
+  } else {
+    T re[3];
+    matvec(R, e, re);
+    Rtip[0] = w.wR2 * re[0]; Rtip[1] = w.wR2 * re[1]; Rtip[2] = w.wR2 * re[2];
+  }
+}
+
+// Cost (and adjoint) of an IK state: the two phases around the pose rows.
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
+CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+                const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
+                T* coll_out) {
+  Chain<T, N> ch;
+  StateAgg<T, N> ag;
+  T F = state_forward<T, N, OBST, GRAD, PGRAD>(rb, w, sph, no, u, ch, ag, coll_out);
+  T r[6], e[3], ang, sn, cs;
+  pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
+  F += T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  if (!GRAD) return F;
+  T Ftip[3], Rtip[3];
+  pose_tip_force(kind, w, tg, ch.R, r, e, Ftip, Rtip);
+  state_reverse<T, N, PGRAD>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
   return F;
 }
 

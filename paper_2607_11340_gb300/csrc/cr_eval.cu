@@ -51,7 +51,7 @@ cr_status cr_cost_grad(const cr_robot* robot, const cr_scene* scene, const cr_ta
                        const void* u, int64_t B, void* cost_out, void* coll_out, void* grad_u_out,
                        void* grad_param_out, int32_t dtype, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_task(task, B)) ||
+  if ((st = check_robot(robot)) || (st = check_scene_shared(scene)) || (st = check_task(task, B)) ||
       (st = check_dtype(dtype)))
     return st;
   if (B < 0) return fail(CR_EINVAL, "cr_cost_grad: B < 0");
@@ -76,6 +76,37 @@ cr_status cr_cost_grad(const cr_robot* robot, const cr_scene* scene, const cr_ta
   a.gp = grad_param_out;
   a.stream = stream_of(stream);
   return dtype == CR_F64 ? crk::launch_cost_grad<double>(a) : crk::launch_cost_grad<float>(a);
+}
+
+cr_status cr_cost_vjp(const cr_robot* robot, const cr_scene* scene, const cr_task* task, const void* u, int64_t B,
+                      const void* upstream, void* grad_u_out, double* grad_param_out, void* workspace, int32_t dtype,
+                      cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_scene_shared(scene)) || (st = check_task(task, B)) ||
+      (st = check_dtype(dtype)))
+    return st;
+  if (B < 0) return fail(CR_EINVAL, "cr_cost_vjp: B < 0");
+  if (B == 0) return CR_OK;
+  size_t es = dsize(dtype);
+  if ((st = check_ptr(u, es, "u", true)) || (st = check_ptr(upstream, es, "upstream", true)) ||
+      (st = check_ptr(grad_u_out, es, "grad_u_out", true)) ||
+      (st = check_ptr(grad_param_out, 8, "grad_param_out", false)) ||
+      (st = check_ptr(workspace, es, "workspace", grad_param_out != nullptr)))
+    return st;
+  crk::EvalArgs a{};
+  a.robot = *robot;
+  if (scene) a.scene = *scene;
+  a.task = *task;
+  a.u = u;
+  a.B = B;
+  a.gu = grad_u_out;
+  a.gp = grad_param_out ? workspace : nullptr;
+  a.upstream = upstream;
+  a.stream = stream_of(stream);
+  st = dtype == CR_F64 ? crk::launch_cost_grad<double>(a) : crk::launch_cost_grad<float>(a);
+  if (st || !grad_param_out) return st;
+  return dtype == CR_F64 ? crk::launch_reduce_rows<double>(workspace, 2 * robot->n, B, grad_param_out, a.stream)
+                         : crk::launch_reduce_rows<float>(workspace, 2 * robot->n, B, grad_param_out, a.stream);
 }
 
 cr_status cr_reduce_rows(const void* x, int64_t rows, int64_t B, double* out, int32_t dtype,

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, 
                                                     const double* __restrict__ targets, int64_t P,
                                                     int S, const double* __restrict__ spheres, int no,
                                                     const T* __restrict__ u, int64_t B, T* cost,
-                                                    T* coll, T* gu, T* gp) {
+                                                    T* coll, T* gu, T* gp, const T* __restrict__ upstream) {
   constexpr int D = 3 * N;
   extern __shared__ unsigned char smem_raw[];
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
@@ -80,17 +80,18 @@ __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, 
   TargetK<T> tg = load_target<T>(targets, P, b / S, kind);
   T g[D], gL[N], grc[N], cl;
   T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2)>(rb, w, kind, tg, sph, no, uu, g, gL, grc, &cl);
-  cost[b] = F;
+  if (cost) cost[b] = F;
   if (coll) coll[b] = cl;
+  const T up = upstream ? upstream[b] : T(1);  // vector-Jacobian product weight
   if (MODE >= 1) {
 #pragma unroll
-    for (int q = 0; q < D; ++q) gu[q * B + b] = g[q];
+    for (int q = 0; q < D; ++q) gu[q * B + b] = up * g[q];
   }
   if (MODE >= 2) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      gp[(int64_t)i * B + b] = gL[i];
-      gp[(int64_t)(N + i) * B + b] = grc[i];
+      gp[(int64_t)i * B + b] = up * gL[i];
+      gp[(int64_t)(N + i) * B + b] = up * grc[i];
     }
   }
 }
@@ -121,6 +122,7 @@ struct EvalArgs {
   const void* u;
   int64_t B;
   void *cost, *coll, *gu, *gp, *Tout, *bb, *J;
+  const void* upstream;
   cudaStream_t stream;
 };
 
@@ -151,7 +153,8 @@ template <typename T, int N> void cost_grad_n(const EvalArgs& a) {
   k_cost_grad<T, N, OB, MO><<<g, 128, sm, a.stream>>>(rb, w, a.task.kind, a.task.targets,          \
                                                        a.task.n_targets, a.task.seeds_per_target,  \
                                                        a.scene.spheres, no, (const T*)a.u, a.B,    \
-                                                       (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp)
+                                                       (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp, \
+                                                       (const T*)a.upstream)
   if (no > 0) {
     if (mode == 0) CR_CG(true, 0); else if (mode == 1) CR_CG(true, 1); else CR_CG(true, 2);
   } else {

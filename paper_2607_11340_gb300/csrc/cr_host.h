@@ -22,6 +22,7 @@ inline size_t dsize(int32_t dtype) { return dtype == CR_F64 ? 8 : 4; }
 
 cr_status check_robot(const cr_robot* r);
 cr_status check_scene(const cr_scene* s);
+cr_status check_scene_shared(const cr_scene* s);
 cr_status check_task(const cr_task* t, int64_t B);
 cr_status check_dtype(int32_t dtype);
 cr_status check_ptr(const void* p, size_t align, const char* name, bool required);

@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sphere4<double>* sph = reinterpret_cast<Sphere4<double>*>(smem_raw);
   if (OBST) {
-    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
     __syncthreads();
   }
   const int S = a.S, K = a.K;

@@ -95,7 +95,7 @@ cr_status cr_lm_step(const cr_robot* robot, const cr_scene* scene, const cr_task
                      int32_t* accepted_out, int64_t B, int32_t n_iter, int32_t dtype,
                      cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_task(task, B)) ||
+  if ((st = check_robot(robot)) || (st = check_scene_shared(scene)) || (st = check_task(task, B)) ||
       (st = check_dtype(dtype)))
     return st;
   if (B < 0 || n_iter < 0) return fail(CR_EINVAL, "cr_lm_step: negative size");
@@ -124,7 +124,7 @@ cr_status cr_pg_steps(const cr_robot* robot, const cr_scene* scene, const cr_tas
                       void* u_inout, void* alpha_inout, void* F_out, int64_t B, int32_t steps,
                       int32_t dtype, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_task(task, B)) ||
+  if ((st = check_robot(robot)) || (st = check_scene_shared(scene)) || (st = check_task(task, B)) ||
       (st = check_dtype(dtype)))
     return st;
   if (B < 0 || steps < 0) return fail(CR_EINVAL, "cr_pg_steps: negative size");

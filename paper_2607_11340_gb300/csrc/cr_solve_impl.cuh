@@ -174,6 +174,7 @@ template <typename T> struct IkArgs {
   int64_t P;
   const double* spheres;
   int no;
+  int sph_pp;  // spheres are per problem: [P][no][4]
   int S, K, k_init, k_final;
   T alpha0, eps;
   double lambda0, lim_tol, pos_tol, rot_tol;
@@ -219,11 +220,11 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
   int* skipped = reinterpret_cast<int*>(sC + S);
   int* sel = skipped + S;
   unsigned char* taken = reinterpret_cast<unsigned char*>(sel + 32);
+  const int64_t p = blockIdx.x;
   if (OBST) {
-    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
     __syncthreads();
   }
-  const int64_t p = blockIdx.x;
   const int s = threadIdx.x;
   if (s < S) {
     TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
@@ -312,14 +313,17 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
+  const int64_t PK = a.P * a.K;
+  // shared sphere set: 128 candidates per block; per-problem sets: one block (warp) per target
+  const int64_t c = a.sph_pp ? (int64_t)blockIdx.x * a.K + threadIdx.x
+                             : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (OBST) {
-    stage_spheres(a.spheres, a.no, rbd, wd.delta, sphd);
-    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    const double* sp = a.spheres + (a.sph_pp ? (int64_t)blockIdx.x * a.no * 4 : 0);
+    stage_spheres(sp, a.no, rbd, wd.delta, sphd);
+    stage_spheres(sp, a.no, rb, w.delta, sph);
     __syncthreads();
   }
-  const int64_t PK = a.P * a.K;
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= PK) return;
+  if (c >= PK || (a.sph_pp && (int)threadIdx.x >= a.K)) return;
   const int64_t p = c / a.K;
   T u[D];
 #pragma unroll
@@ -462,20 +466,22 @@ __global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, S
   a.F[b] = F;
 }
 
+// sph_pp = 0: blocks of 128 consecutive seeds; sph_pp = 1: blockIdx.y = problem, its own spheres.
 template <typename T, int N, bool OBST>
 __global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, const double* spheres, int no,
-                                                uint64_t key, int64_t p0, int64_t P, int S,
+                                                int sph_pp, uint64_t key, int64_t p0, int64_t P, int S,
                                                 NmaxArr umax, T* u_out) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
   if (OBST) {
-    stage_spheres(spheres, no, rb, w.delta, sph);
+    stage_spheres(spheres + (sph_pp ? (int64_t)blockIdx.y * no * 4 : 0), no, rb, w.delta, sph);
     __syncthreads();
   }
   const int64_t PS = P * S;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= PS) return;
+  const int64_t i = sph_pp ? (int64_t)blockIdx.y * S + (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                           : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= PS || (sph_pp && (int64_t)blockIdx.x * blockDim.x + threadIdx.x >= S)) return;
   const int64_t p = i / S, s = i % S;
   T u[D];
   draw_seed<T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, 0, umax.v, u);
@@ -556,6 +562,7 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
   k.P = a.task.n_targets;
   k.spheres = a.scene.spheres;
   k.no = a.scene.n_o;
+  k.sph_pp = (a.scene.per_problem && a.scene.n_o > 0) ? 1 : 0;
   k.S = p.S;
   k.K = p.n_final;
   k.k_init = p.k_init;
@@ -609,9 +616,10 @@ template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which)
   }
   if (!(which & 2)) return CR_OK;
   size_t sm2 = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<T>));
-  unsigned g2 = grid1(P * k.K, 128);
-  if (no > 0) k_ik_refine<T, N, true><<<g2, 128, sm2, a.stream>>>(rb, w, rbd, wd, k);
-  else k_ik_refine<T, N, false><<<g2, 128, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  unsigned g2 = k.sph_pp ? (unsigned)P : grid1(P * k.K, 128);
+  int b2 = k.sph_pp ? 32 : 128;
+  if (no > 0) k_ik_refine<T, N, true><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  else k_ik_refine<T, N, false><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   if ((st = crh::check_launch("cr_solve_ik refine"))) return st;
   k_ik_argmin<N><<<grid1(P, 128), 128, 0, a.stream>>>(P, k.K, k.pos_tol, k.rot_tol, k.cand_u64, k.cand_F,
                                                       k.cand_pos, k.cand_rot, k.cand_flag, k.u_out,
@@ -665,10 +673,11 @@ template <typename T, int N> cr_status seeds_n(const SolveArgs& a) {
   NmaxArr um;
   for (int i = 0; i < NMAX; ++i) um.v[i] = i < a.robot.n ? a.robot.u_max[i] : 0.0;
   int no = a.scene.n_o;
+  int pp = a.scene.per_problem ? 1 : 0;
   size_t sm = (size_t)no * sizeof(Sphere4<T>);
-  unsigned g = grid1(a.P * a.S, 128);
-  if (no > 0) k_seeds<T, N, true><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.key, a.p0, a.P, a.S, um, (T*)a.u);
-  else k_seeds<T, N, false><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.key, a.p0, a.P, a.S, um, (T*)a.u);
+  dim3 g = pp ? dim3(grid1(a.S, 128), (unsigned)a.P) : dim3(grid1(a.P * a.S, 128));
+  if (no > 0) k_seeds<T, N, true><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, um, (T*)a.u);
+  else k_seeds<T, N, false><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, um, (T*)a.u);
   return crh::check_launch("cr_seeds");
 }
 

@@ -1,0 +1,147 @@
+// C ABI of trajectory planning and calibration: cr_traj_cost, cr_traj_workspace_size, cr_solve_traj,
+// cr_calibrate.
+#include "cr_traj_impl.cuh"
+
+namespace crk {
+CR_TRAJ_INSTANTIATE(extern, float)
+CR_TRAJ_INSTANTIATE(extern, double)
+}
+
+using namespace crh;
+
+namespace {
+
+cr_status check_traj_task(const cr_traj_task* t) {
+  if (!t) return fail(CR_EINVAL, "traj task is NULL");
+  if (t->P < 0) return fail(CR_EINVAL, "traj task: P < 0");
+  if (t->T < 2 || t->T > 256) return fail(CR_EINVAL, "traj task: T = %d outside 2..256", t->T);
+  if (!(t->w.dt > 0) || !(t->w.v_max > 0) || !(t->w.a_max > 0)) return fail(CR_EINVAL, "traj task: dt, v_max, a_max must be > 0");
+  cr_status st;
+  if ((st = check_ptr(t->u_start, 8, "u_start", t->P > 0)) || (st = check_ptr(t->goal, 8, "goal", t->P > 0))) return st;
+  return CR_OK;
+}
+
+struct TrajWs {
+  size_t ik, ug, cost, pos, rot, succ, total;
+};
+
+TrajWs traj_ws(const cr_robot& r, int64_t P, const cr_ik_params& g) {
+  TrajWs w;
+  size_t off = 0;
+  w.ik = off; off = align256(off + cr_ik_workspace_size(&r, P, &g));
+  w.ug = off; off = align256(off + (size_t)3 * r.n * P * 8);
+  w.cost = off; off = align256(off + (size_t)P * 8);
+  w.pos = off; off = align256(off + (size_t)P * 8);
+  w.rot = off; off = align256(off + (size_t)P * 8);
+  w.succ = off; off = align256(off + (size_t)P);
+  w.total = off;
+  return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+cr_status cr_traj_cost(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task, const void* x,
+                       void* cost_out, void* grad_out, const void* upstream, int32_t dtype, cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_traj_task(task)) ||
+      (st = check_dtype(dtype)))
+    return st;
+  if (task->P == 0) return CR_OK;
+  size_t es = dsize(dtype);
+  if ((st = check_ptr(x, es, "x", true)) || (st = check_ptr(cost_out, es, "cost_out", true)) ||
+      (st = check_ptr(grad_out, es, "grad_out", false)) || (st = check_ptr(upstream, es, "upstream", false)))
+    return st;
+  crk::TrajLaunch l{};
+  l.robot = *robot;
+  if (scene) l.scene = *scene;
+  l.task = *task;
+  l.x = x;
+  l.cost = cost_out;
+  l.grad = grad_out;
+  l.upstream = upstream;
+  l.stream = stream_of(stream);
+  return dtype == CR_F64 ? crk::launch_traj_cost<double>(l) : crk::launch_traj_cost<float>(l);
+}
+
+size_t cr_traj_workspace_size(const cr_robot* robot, int64_t P, const cr_ik_params* goal_ik) {
+  if (!robot || !goal_ik || P < 0) return 0;
+  return traj_ws(*robot, P, *goal_ik).total;
+}
+
+cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                        const cr_ik_params* goal_ik, int32_t k_traj, double alpha0, double* X_out, double* cost_out,
+                        double* goal_pos, double* goal_rot, double* speed, double* accel, uint8_t* lim_ok,
+                        uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_traj_task(task))) return st;
+  if (!goal_ik) return fail(CR_EINVAL, "goal_ik is NULL");
+  if (k_traj < 0 || !(alpha0 >= 0)) return fail(CR_EINVAL, "k_traj < 0 or alpha0 < 0");
+  const int64_t P = task->P;
+  if (P == 0) return CR_OK;
+  if ((st = check_ptr(X_out, 8, "X_out", true)) || (st = check_ptr(cost_out, 8, "cost_out", true)) ||
+      (st = check_ptr(goal_pos, 8, "goal_pos", true)) || (st = check_ptr(goal_rot, 8, "goal_rot", true)) ||
+      (st = check_ptr(speed, 8, "speed", true)) || (st = check_ptr(accel, 8, "accel", true)) ||
+      (st = check_ptr(lim_ok, 1, "lim_ok", true)) || (st = check_ptr(col_ok, 1, "col_ok", true)) ||
+      (st = check_ptr(workspace, 256, "workspace", true)))
+    return st;
+  TrajWs lay = traj_ws(*robot, P, *goal_ik);
+  if (ws_bytes < lay.total) return fail(CR_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, lay.total);
+  unsigned char* ws = (unsigned char*)workspace;
+  // 1. IK to the goal poses (per-problem spheres when the scene has them)
+  cr_task it{};
+  it.kind = CR_TASK_IK6;
+  it.seeds_per_target = 1;
+  it.targets = task->goal;
+  it.n_targets = P;
+  it.w = task->w;
+  double* ug = (double*)(ws + lay.ug);
+  if ((st = cr_solve_ik(robot, scene, &it, goal_ik, ug, (double*)(ws + lay.cost), (double*)(ws + lay.pos),
+                        (double*)(ws + lay.rot), ws + lay.succ, ws + lay.ik, lay.ug - lay.ik, stream)))
+    return st;
+  // 2. linear initialisation and projected-gradient refinement
+  crk::TrajLaunch l{};
+  l.robot = *robot;
+  if (scene) l.scene = *scene;
+  l.task = *task;
+  l.u_goal = ug;
+  l.k_traj = k_traj;
+  l.alpha0 = alpha0;
+  l.lim_tol = goal_ik->lim_tol;
+  l.X_out = X_out;
+  l.F_out = cost_out;
+  l.goal_pos = goal_pos;
+  l.goal_rot = goal_rot;
+  l.speed = speed;
+  l.accel = accel;
+  l.lim_ok = lim_ok;
+  l.col_ok = col_ok;
+  l.stream = stream_of(stream);
+  return goal_ik->precision == CR_F64 ? crk::launch_traj_solve<double>(l) : crk::launch_traj_solve<float>(l);
+}
+
+cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_meas, int64_t K, double* theta,
+                       int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype, cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_dtype(dtype))) return st;
+  if (K < 1 || iters < 0 || !(lambda0 > 0)) return fail(CR_EINVAL, "cr_calibrate: K >= 1, iters >= 0, lambda0 > 0");
+  if ((st = check_ptr(U, dsize(dtype), "U", true)) || (st = check_ptr(P_meas, 8, "P_meas", true)) ||
+      (st = check_ptr(theta, 8, "theta", true)) || (st = check_ptr(F_out, 8, "F_out", true)) ||
+      (st = check_ptr(hist, 8, "hist", false)))
+    return st;
+  crk::TrajLaunch l{};
+  l.robot = *robot;
+  l.U = U;
+  l.Pm = P_meas;
+  l.K = K;
+  l.iters = iters;
+  l.lambda0 = lambda0;
+  l.theta_dev = theta;
+  l.F_dev = F_out;
+  l.hist_dev = hist;
+  l.stream = stream_of(stream);
+  return dtype == CR_F64 ? crk::launch_calibrate<double>(l) : crk::launch_calibrate<float>(l);
+}
+
+}  // extern "C"

@@ -1,0 +1,613 @@
+// Trajectory planning (Sec. IV-A, Eq. mp_length_only with the tendon speed / acceleration limits by
+// finite differences) and kinematic calibration.
+//
+// One CTA per trajectory, one thread per timestep t. Each thread runs the forward phase of its own
+// state (chain, clearance, penalty rows), shares its tip position and tendon state through shared
+// memory, evaluates the coupling rows it owns (length, speed, acceleration between t and its
+// predecessors), shares their derivatives, and runs the reverse phase of its state with the tip
+// force of the length rows (and of the goal pose at the last state). Sums over the trajectory are
+// deterministic block reductions.
+#pragma once
+
+#include "cr_solve_impl.cuh"
+
+namespace crk {
+
+template <typename T> struct TrajW {
+  T dt, vmax, amax, w_len, rho_v, rho_a;
+};
+
+// Deterministic block sum: butterfly inside each warp, then every thread adds the warp totals in
+// warp order. red[] holds 32 values; blockDim.x is a multiple of 32.
+template <typename T> __device__ T block_sum(T v, T* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = T(0);
+  for (int k = 0; k < nw; ++k) s += red[k];
+  return s;
+}
+template <typename T> __device__ T block_max(T v, T* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = c_max(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int k = 1; k < nw; ++k) s = c_max(s, red[k]);
+  return s;
+}
+
+// Shared buffers of one trajectory: tip positions [Tn][3], states [Tn][D], speed and acceleration
+// row derivatives [Tn][D] each, reduction scratch [32].
+template <typename T> struct TrajSmem {
+  T* p;
+  T* u;
+  T* sv;
+  T* sa;
+  T* red;
+  __host__ __device__ static size_t bytes(int Tn, int D) { return sizeof(T) * ((size_t)Tn * (3 + 3 * D) + 32); }
+  __device__ void carve(unsigned char* base, int Tn, int D) {
+    T* q = reinterpret_cast<T*>(base);
+    p = q;
+    u = p + (size_t)Tn * 3;
+    sv = u + (size_t)Tn * D;
+    sa = sv + (size_t)Tn * D;
+    red = sa + (size_t)Tn * D;
+  }
+};
+
+// Thread t's share of the trajectory cost; with GRAD, gu = dF/du_t (zero for t = 0 and t >= Tn).
+// Every thread of the block must call it (it synchronises).
+template <typename T, int N, bool OBST, bool GRAD>
+__device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TrajW<T>& tw, int t, int Tn,
+                             const T (&u)[3 * N], const TargetK<T>& goal, const Sphere4<T>* sph, int no,
+                             TrajSmem<T>& sm, T (&gu)[3 * N]) {
+  constexpr int D = 3 * N;
+  const bool active = t < Tn;
+  Chain<T, N> ch;
+  StateAgg<T, N> ag;
+  T F = T(0);
+  T Ftip[3] = {T(0), T(0), T(0)}, Rtip[3] = {T(0), T(0), T(0)};
+  if (active) {
+    if (t == 0) {
+      chain_forward(rb, u, ch);  // the start state is fixed: only its tip enters the length rows
+    } else {
+      F = state_forward<T, N, OBST, GRAD, false>(rb, w, sph, no, u, ch, ag, nullptr);
+    }
+    if (t == Tn - 1) {
+      T r[6], e[3], ang, sn, cs;
+      pose_rows(CR_TASK_IK6, w, goal, ch.R, ch.p, r, e, ang, sn, cs);
+      F += T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+      if (GRAD) pose_tip_force(CR_TASK_IK6, w, goal, ch.R, r, e, Ftip, Rtip);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sm.p[t * 3 + a] = ch.p[a];
+#pragma unroll
+    for (int q = 0; q < D; ++q) sm.u[t * D + q] = u[q];
+  }
+  __syncthreads();
+  T sv[D], sa[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) { sv[q] = T(0); sa[q] = T(0); }
+  if (active && t >= 1) {
+    T dp0 = ch.p[0] - sm.p[(t - 1) * 3], dp1 = ch.p[1] - sm.p[(t - 1) * 3 + 1], dp2 = ch.p[2] - sm.p[(t - 1) * 3 + 2];
+    F += T(0.5) * tw.w_len * (dp0 * dp0 + dp1 * dp1 + dp2 * dp2);
+    const T idt = T(1) / tw.dt, idt2 = idt * idt;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      T v = (u[q] - sm.u[(t - 1) * D + q]) * idt;
+      T hu = v - tw.vmax, hl = -tw.vmax - v;
+      hu = hu > T(0) ? hu : T(0);
+      hl = hl > T(0) ? hl : T(0);
+      F += T(0.5) * tw.rho_v * (hu * hu + hl * hl);
+      sv[q] = tw.rho_v * (hu - hl) * idt;
+      if (t >= 2) {
+        T acc = (u[q] - T(2) * sm.u[(t - 1) * D + q] + sm.u[(t - 2) * D + q]) * idt2;
+        T au = acc - tw.amax, al = -tw.amax - acc;
+        au = au > T(0) ? au : T(0);
+        al = al > T(0) ? al : T(0);
+        F += T(0.5) * tw.rho_a * (au * au + al * al);
+        sa[q] = tw.rho_a * (au - al) * idt2;
+      }
+    }
+  }
+  if (!GRAD) return F;
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) { sm.sv[t * D + q] = sv[q]; sm.sa[t * D + q] = sa[q]; }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < D; ++q) gu[q] = T(0);
+  if (active && t >= 1) {
+    // length rows (t-1, t) and (t, t+1) act on the tip of state t
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T f = tw.w_len * (ch.p[a] - sm.p[(t - 1) * 3 + a]);
+      if (t + 1 < Tn) f -= tw.w_len * (sm.p[(t + 1) * 3 + a] - ch.p[a]);
+      Ftip[a] += f;
+    }
+    state_reverse<T, N, false>(rb, w, u, ch, ag, Ftip, Rtip, gu, nullptr, nullptr);
+    // speed rows of t and t+1, acceleration rows of t, t+1 and t+2 act on u_t directly
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      T g = sv[q] + sa[q];
+      if (t + 1 < Tn) g += -sm.sv[(t + 1) * D + q] - T(2) * sm.sa[(t + 1) * D + q];
+      if (t + 2 < Tn) g += sm.sa[(t + 2) * D + q];
+      gu[q] += g;
+    }
+  }
+  return F;
+}
+
+template <typename T> struct TrajArgs {
+  const double* u_start;  // [D][P]
+  const double* goal;     // [7][P]
+  int64_t P;
+  int Tn;
+  const double* spheres;
+  int no;
+  int sph_pp;
+  // cost / gradient
+  const T* x;             // [D][P*(Tn-1)]
+  T* cost;
+  T* grad;
+  const T* upstream;
+  // solve
+  const double* u_goal;   // [D][P]
+  int k_traj;
+  T alpha0;
+  double lim_tol;
+  double dt_d, vmax_d, amax_d;
+  double* X_out;          // [D][P*Tn]
+  double* F_out;
+  double* goal_pos;
+  double* goal_rot;
+  double* speed;
+  double* accel;
+  unsigned char* lim_ok;
+  unsigned char* col_ok;
+};
+
+template <typename T, int N, bool OBST, bool GRAD>
+__global__ void __launch_bounds__(256) k_traj_cost(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, TrajArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t p = blockIdx.x;
+  const int t = threadIdx.x, Tn = a.Tn;
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  size_t off = ((size_t)a.no * sizeof(Sphere4<T>) + 15) & ~size_t(15);
+  TrajSmem<T> sm;
+  sm.carve(smem_raw + off, Tn, D);
+  if (OBST) {
+    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
+    __syncthreads();
+  }
+  const int64_t ld = a.P * (Tn - 1);
+  T u[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    if (t == 0) u[q] = T(a.u_start[q * a.P + p]);
+    else if (t < Tn) u[q] = a.x[q * ld + p * (Tn - 1) + (t - 1)];
+    else u[q] = T(0);
+  }
+  TargetK<T> goal = load_target<T>(a.goal, a.P, p, CR_TASK_IK6);
+  T gu[D];
+  T F = traj_state_eval<T, N, OBST, GRAD>(rb, w, tw, t, Tn, u, goal, sph, a.no, sm, gu);
+  T Ft = block_sum(F, sm.red);
+  if (t == 0) a.cost[p] = Ft;
+  if (GRAD && t >= 1 && t < Tn) {
+    T s = a.upstream ? a.upstream[p] : T(1);
+#pragma unroll
+    for (int q = 0; q < D; ++q) a.grad[q * ld + p * (Tn - 1) + (t - 1)] = s * gu[q];
+  }
+}
+
+// Trajectory planning after the goal IK: linear initialisation, k_traj projected-gradient steps of
+// all free states, FP64 metrics of the result.
+template <typename T, int N, bool OBST>
+__global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, RobotK<double> rbd,
+                                                     WeightsK<double> wd, TrajArgs<T> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t p = blockIdx.x;
+  const int t = threadIdx.x, Tn = a.Tn;
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<T>));
+  size_t off = ((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15);
+  TrajSmem<T> sm;
+  sm.carve(smem_raw + off, Tn, D);
+  if (OBST) {
+    const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
+    stage_spheres(sp, a.no, rb, w.delta, sph);
+    stage_spheres(sp, a.no, rbd, wd.delta, sphd);
+    __syncthreads();
+  }
+  const bool active = t < Tn;
+  T u[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    double u0 = a.u_start[q * a.P + p], ug = a.u_goal[q * a.P + p];
+    u[q] = active ? T(u0 + (double)t / (Tn - 1) * (ug - u0)) : T(0);
+  }
+  TargetK<T> goal = load_target<T>(a.goal, a.P, p, CR_TASK_IK6);
+  T g[D];
+  T F = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u, goal, sph, a.no, sm, g), sm.red);
+  T alpha = a.alpha0;
+  const bool free_state = active && t >= 1;
+  for (int it = 0; it < a.k_traj; ++it) {
+    T gn2l = T(0);
+#pragma unroll
+    for (int q = 0; q < D; ++q) gn2l += g[q] * g[q];
+    T gn2 = block_sum(gn2l, sm.red);
+    T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
+    T u1[D];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (free_state)
+        project3(u[3 * i] - scale * g[3 * i], u[3 * i + 1] - scale * g[3 * i + 1], u[3 * i + 2] - scale * g[3 * i + 2],
+                 rb.umax[i], u1[3 * i], u1[3 * i + 1], u1[3 * i + 2]);
+      else {
+        u1[3 * i] = u[3 * i]; u1[3 * i + 1] = u[3 * i + 1]; u1[3 * i + 2] = u[3 * i + 2];
+      }
+    }
+    T g1[D];
+    T F1 = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u1, goal, sph, a.no, sm, g1), sm.red);
+    if (F1 < F) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
+      F = F1;
+      alpha *= T(1.25);
+    } else {
+      alpha *= T(0.5);
+    }
+  }
+  // outputs and FP64 metrics
+  double ud[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) ud[q] = double(u[q]);
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) a.X_out[q * (a.P * Tn) + p * Tn + t] = ud[q];
+  }
+  double pos = 0, rot = 0;
+  unsigned char flags = 3;
+  if (active) {
+    TargetK<double> gd = load_target<double>(a.goal, a.P, p, CR_TASK_IK6);
+    accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, gd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+  }
+  // speed / acceleration ratios in FP64 over the states shared in a double buffer
+  double* sd = reinterpret_cast<double*>(smem_raw + off + ((TrajSmem<T>::bytes(Tn, D) + 15) & ~size_t(15)));
+  double* redd = sd + (size_t)Tn * D;
+  if (active)
+#pragma unroll
+    for (int q = 0; q < D; ++q) sd[t * D + q] = ud[q];
+  __syncthreads();
+  double vmax_r = 0, amax_r = 0;
+  if (active && t >= 1) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      vmax_r = fmax(vmax_r, fabs(ud[q] - sd[(t - 1) * D + q]) / a.dt_d / a.vmax_d);
+      if (t >= 2)
+        amax_r = fmax(amax_r, fabs(ud[q] - 2.0 * sd[(t - 1) * D + q] + sd[(t - 2) * D + q]) / (a.dt_d * a.dt_d) / a.amax_d);
+    }
+  }
+  double vr = block_max(vmax_r, redd);
+  double ar = block_max(amax_r, redd);
+  double lim = block_max(double((flags & 1) ? 0 : 1), redd);
+  double col = block_max(double((flags & 2) ? 0 : 1), redd);
+  if (t == Tn - 1) {
+    a.goal_pos[p] = pos;
+    a.goal_rot[p] = rot;
+  }
+  if (t == 0) {
+    a.F_out[p] = double(F);
+    a.speed[p] = vr;
+    a.accel[p] = ar;
+    a.lim_ok[p] = lim == 0.0;
+    a.col_ok[p] = col == 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Calibration: one CTA. theta = (L_1..n, r_c,1..n); residual p(u_k; theta) - p_k.
+// ------------------------------------------------------------------------------------------------
+// dp/dL_i = Rb_i d_i / L_i (everything after segment i translates); dp/dr_c,i = -(ax dp/dax +
+// ay dp/day) / r_c with dp/da_k = v + w x p from the segment twists.
+template <typename T, int N>
+__device__ void calib_rows(const RobotK<T>& rb, const T (&u)[3 * N], const double* pm, T (&r)[3], T (&J)[3][2 * N]) {
+  Chain<T, N> ch;
+  chain_forward(rb, u, ch);
+  T tv[N][2][3], tw[N][2][3];
+  segment_twists(rb, ch, tv, tw);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r[a] = ch.p[a] - T(pm[a]);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T di[3], Rd[3];
+    di[0] = rb.L[i] * ch.c[i] * ch.ax[i];
+    di[1] = rb.L[i] * ch.c[i] * ch.ay[i];
+    di[2] = rb.L[i] * ch.s[i];
+    matvec(ch.Rb[i], di, Rd);
+    T wp0[3], wp1[3];
+    cross(tw[i][0], ch.p, wp0);
+    cross(tw[i][1], ch.p, wp1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      J[a][i] = Rd[a] / rb.L[i];
+      T dpx = tv[i][0][a] + wp0[a], dpy = tv[i][1][a] + wp1[a];
+      J[a][N + i] = -(ch.ax[i] * dpx + ch.ay[i] * dpy) / rb.rc[i];
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(1024) k_calibrate(RobotK<T> rb0, const T* __restrict__ U, const double* __restrict__ Pm,
+                                                     int64_t K, int iters, double lambda0, double* theta_io,
+                                                     double* F_out, double* hist) {
+  constexpr int D = 3 * N, NP = 2 * N, NA = NP * (NP + 1) / 2;
+  __shared__ double red[32];
+  __shared__ double th[NP], thn[NP], A[NA], g[NP], Dg[NP], invd[NP], dl[NP];
+  __shared__ double sF, sFn, lam, nu;
+  __shared__ int ok;
+  if (threadIdx.x < NP) th[threadIdx.x] = theta_io[threadIdx.x];
+  if (threadIdx.x == 0) { lam = lambda0; nu = 2.0; }
+  __syncthreads();
+  auto robot_of = [&](const double* theta) {
+    RobotK<T> rb = rb0;
+    for (int i = 0; i < N; ++i) {
+      rb.L[i] = T(theta[i]);
+      rb.rc[i] = T(theta[N + i]);
+      rb.K[i] = T(-2.0 / (3.0 * theta[N + i]));
+    }
+    return rb;
+  };
+  for (int it = 0; it < iters; ++it) {
+    RobotK<T> rb = robot_of(th);
+    double la[NA], lg[NP], lF = 0;
+    for (int a = 0; a < NA; ++a) la[a] = 0;
+    for (int a = 0; a < NP; ++a) lg[a] = 0;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+      T u[D];
+      for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
+      double pm[3] = {Pm[k], Pm[K + k], Pm[2 * K + k]};
+      T r[3], J[3][NP];
+      calib_rows<T, N>(rb, u, pm, r, J);
+      for (int a = 0; a < 3; ++a) {
+        lF += 0.5 * double(r[a]) * double(r[a]);
+        for (int x = 0; x < NP; ++x) {
+          lg[x] += double(J[a][x]) * double(r[a]);
+          for (int y = 0; y <= x; ++y) la[tri(x, y)] += double(J[a][x]) * double(J[a][y]);
+        }
+      }
+    }
+    for (int a = 0; a < NA; ++a) {
+      double v = block_sum(la[a], red);
+      if (threadIdx.x == 0) A[a] = v;
+    }
+    for (int a = 0; a < NP; ++a) {
+      double v = block_sum(lg[a], red);
+      if (threadIdx.x == 0) g[a] = v;
+    }
+    double Fc = block_sum(lF, red);
+    if (threadIdx.x == 0) {
+      sF = Fc;
+      double Ad[NA];
+      for (int a = 0; a < NA; ++a) Ad[a] = A[a];
+      for (int q = 0; q < NP; ++q) {
+        Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
+        Ad[tri(q, q)] += lam * Dg[q];
+      }
+      double iv[NP];
+      ok = cholesky_packed<NP>(Ad, iv) ? 1 : 0;
+      if (ok) {
+        double x[NP];
+        for (int q = 0; q < NP; ++q) x[q] = -g[q];
+        cholesky_solve<NP>(Ad, iv, x);
+        for (int q = 0; q < NP; ++q) { dl[q] = x[q]; thn[q] = th[q] + x[q]; }
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      RobotK<T> rbn = robot_of(thn);
+      double lFn = 0;
+      for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+        T u[D];
+        for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
+        Chain<T, N> ch;
+        chain_forward(rbn, u, ch);
+        for (int a = 0; a < 3; ++a) {
+          double ra = double(ch.p[a] - T(Pm[a * K + k]));
+          lFn += 0.5 * ra * ra;
+        }
+      }
+      double Fn = block_sum(lFn, red);
+      if (threadIdx.x == 0) {
+        double pred = 0;
+        for (int q = 0; q < NP; ++q) pred += dl[q] * (lam * Dg[q] * dl[q] - g[q]);
+        pred *= 0.5;
+        if (Fn < sF) {
+          double rho = (sF - Fn) / pred, tt = 2.0 * rho - 1.0;
+          lam *= fmax(1.0 / 3.0, 1.0 - tt * tt * tt);
+          nu = 2.0;
+          for (int q = 0; q < NP; ++q) th[q] = thn[q];
+          sF = Fn;
+        } else {
+          lam *= nu;
+          nu *= 2.0;
+        }
+      }
+    } else if (threadIdx.x == 0) {
+      lam *= nu;
+      nu *= 2.0;
+    }
+    __syncthreads();
+    if (hist && threadIdx.x < NP) hist[it * NP + threadIdx.x] = th[threadIdx.x];
+  }
+  // final cost
+  RobotK<T> rb = robot_of(th);
+  double lF = 0;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+    T u[D];
+    for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
+    Chain<T, N> ch;
+    chain_forward(rb, u, ch);
+    for (int a = 0; a < 3; ++a) {
+      double ra = double(ch.p[a] - T(Pm[a * K + k]));
+      lF += 0.5 * ra * ra;
+    }
+  }
+  double Fc = block_sum(lF, red);
+  if (threadIdx.x < NP) theta_io[threadIdx.x] = th[threadIdx.x];
+  if (threadIdx.x == 0) *F_out = Fc;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------------------
+struct TrajLaunch {
+  cr_robot robot;
+  cr_scene scene;
+  cr_traj_task task;
+  const void* x;
+  void *cost, *grad;
+  const void* upstream;
+  // solve
+  const double* u_goal;
+  int k_traj;
+  double alpha0, lim_tol;
+  double *X_out, *F_out, *goal_pos, *goal_rot, *speed, *accel;
+  unsigned char *lim_ok, *col_ok;
+  // calibration
+  const void* U;
+  const double* Pm;
+  int64_t K;
+  int iters;
+  double lambda0;
+  double *theta_dev, *F_dev, *hist_dev;
+  cudaStream_t stream;
+};
+
+template <typename T> cr_status launch_traj_cost(const TrajLaunch& l);
+template <typename T> cr_status launch_traj_solve(const TrajLaunch& l);
+template <typename T> cr_status launch_calibrate(const TrajLaunch& l);
+
+template <typename T> TrajW<T> traj_w(const cr_weights& w) {
+  TrajW<T> t;
+  t.dt = T(w.dt);
+  t.vmax = T(w.v_max);
+  t.amax = T(w.a_max);
+  t.w_len = T(w.w_len);
+  t.rho_v = T(w.rho_v);
+  t.rho_a = T(w.rho_a);
+  return t;
+}
+
+template <typename T> TrajArgs<T> traj_args(const TrajLaunch& l) {
+  TrajArgs<T> a{};
+  a.u_start = l.task.u_start;
+  a.goal = l.task.goal;
+  a.P = l.task.P;
+  a.Tn = l.task.T;
+  a.spheres = l.scene.spheres;
+  a.no = l.scene.n_o;
+  a.sph_pp = (l.scene.per_problem && l.scene.n_o > 0) ? 1 : 0;
+  a.x = (const T*)l.x;
+  a.cost = (T*)l.cost;
+  a.grad = (T*)l.grad;
+  a.upstream = (const T*)l.upstream;
+  a.u_goal = l.u_goal;
+  a.k_traj = l.k_traj;
+  a.alpha0 = T(l.alpha0);
+  a.lim_tol = l.lim_tol;
+  a.dt_d = l.task.w.dt;
+  a.vmax_d = l.task.w.v_max;
+  a.amax_d = l.task.w.a_max;
+  a.X_out = l.X_out;
+  a.F_out = l.F_out;
+  a.goal_pos = l.goal_pos;
+  a.goal_rot = l.goal_rot;
+  a.speed = l.speed;
+  a.accel = l.accel;
+  a.lim_ok = l.lim_ok;
+  a.col_ok = l.col_ok;
+  return a;
+}
+
+template <typename T, int N> cr_status traj_cost_n(const TrajLaunch& l) {
+  constexpr int D = 3 * N;
+  RobotK<T> rb = crh::robot_k<T>(l.robot);
+  WeightsK<T> w = crh::weights_k<T>(l.task.w);
+  TrajW<T> tw = traj_w<T>(l.task.w);
+  TrajArgs<T> a = traj_args<T>(l);
+  const int threads = ((a.Tn + 31) / 32) * 32;
+  size_t sm = (((size_t)a.no * sizeof(Sphere4<T>) + 15) & ~size_t(15)) + TrajSmem<T>::bytes(a.Tn, D);
+  cr_status st;
+  if (a.no > 0) {
+    if (l.grad) { if ((st = set_smem(k_traj_cost<T, N, true, true>, sm))) return st;
+      k_traj_cost<T, N, true, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
+    else { if ((st = set_smem(k_traj_cost<T, N, true, false>, sm))) return st;
+      k_traj_cost<T, N, true, false><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
+  } else {
+    if (l.grad) { if ((st = set_smem(k_traj_cost<T, N, false, true>, sm))) return st;
+      k_traj_cost<T, N, false, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
+    else { if ((st = set_smem(k_traj_cost<T, N, false, false>, sm))) return st;
+      k_traj_cost<T, N, false, false><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
+  }
+  return crh::check_launch("cr_traj_cost");
+}
+
+template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
+  constexpr int D = 3 * N;
+  RobotK<T> rb = crh::robot_k<T>(l.robot);
+  WeightsK<T> w = crh::weights_k<T>(l.task.w);
+  RobotK<double> rbd = crh::robot_k<double>(l.robot);
+  WeightsK<double> wd = crh::weights_k<double>(l.task.w);
+  TrajW<T> tw = traj_w<T>(l.task.w);
+  TrajArgs<T> a = traj_args<T>(l);
+  const int threads = ((a.Tn + 31) / 32) * 32;
+  size_t sm = (((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15)) +
+              ((TrajSmem<T>::bytes(a.Tn, D) + 15) & ~size_t(15)) + ((size_t)a.Tn * D + 32) * sizeof(double);
+  cr_status st;
+  if (a.no > 0) {
+    if ((st = set_smem(k_traj_solve<T, N, true>, sm))) return st;
+    k_traj_solve<T, N, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
+  } else {
+    if ((st = set_smem(k_traj_solve<T, N, false>, sm))) return st;
+    k_traj_solve<T, N, false><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
+  }
+  return crh::check_launch("cr_solve_traj");
+}
+
+template <typename T, int N> cr_status calibrate_n(const TrajLaunch& l) {
+  RobotK<T> rb = crh::robot_k<T>(l.robot);
+  k_calibrate<T, N><<<1, 1024, 0, l.stream>>>(rb, (const T*)l.U, l.Pm, l.K, l.iters, l.lambda0, l.theta_dev, l.F_dev,
+                                               l.hist_dev);
+  return crh::check_launch("cr_calibrate");
+}
+
+#define CR_TRAJ_DISPATCH(FN, T, l)         \
+  switch ((l).robot.n) {                   \
+    case 1: return FN<T, 1>(l);            \
+    case 2: return FN<T, 2>(l);            \
+    case 3: return FN<T, 3>(l);            \
+    case 4: return FN<T, 4>(l);            \
+    case 5: return FN<T, 5>(l);            \
+    default: return FN<T, 6>(l);           \
+  }
+
+template <typename T> cr_status launch_traj_cost(const TrajLaunch& l) { CR_TRAJ_DISPATCH(traj_cost_n, T, l) }
+template <typename T> cr_status launch_traj_solve(const TrajLaunch& l) { CR_TRAJ_DISPATCH(traj_solve_n, T, l) }
+template <typename T> cr_status launch_calibrate(const TrajLaunch& l) { CR_TRAJ_DISPATCH(calibrate_n, T, l) }
+
+#define CR_TRAJ_INSTANTIATE(EXT, T)                                  \
+  EXT template cr_status launch_traj_cost<T>(const TrajLaunch&);     \
+  EXT template cr_status launch_traj_solve<T>(const TrajLaunch&);    \
+  EXT template cr_status launch_calibrate<T>(const TrajLaunch&);
+
+}  // namespace crk

@@ -26,7 +26,8 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_seeds", "cr_topk", "cr_ik_workspace_size", "cr_solve_ik", "cr_ik_stage1", "cr_ik_stage2",
            "cr_solve_ik_plain",
            "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
-           "cr_static_workspace_capacity")
+           "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
+           "cr_calibrate", "cr_cost_vjp")
 
 
 class CrError(RuntimeError):
@@ -48,12 +49,17 @@ class cr_weights(C.Structure):
 
 
 class cr_scene(C.Structure):
-    _fields_ = [("spheres", C.c_void_p), ("n_o", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("spheres", C.c_void_p), ("n_o", C.c_int32), ("per_problem", C.c_int32)]
 
 
 class cr_task(C.Structure):
     _fields_ = [("kind", C.c_int32), ("seeds_per_target", C.c_int32), ("targets", C.c_void_p),
                 ("n_targets", C.c_int64), ("w", cr_weights)]
+
+
+class cr_traj_task(C.Structure):
+    _fields_ = [("u_start", C.c_void_p), ("goal", C.c_void_p), ("P", C.c_int64), ("T", C.c_int32),
+                ("reserved", C.c_int32), ("w", cr_weights)]
 
 
 class cr_ik_params(C.Structure):
@@ -92,6 +98,12 @@ _SIGS = {
     "cr_solve_ik_static": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task),
                            C.POINTER(cr_ik_params), _P, _P, _P, _P, _P, _P],
     "cr_poll_status": [_P, C.POINTER(C.c_int32), _P],
+    "cr_traj_cost": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_traj_task), _P, _P, _P, _P, C.c_int32, _P],
+    "cr_solve_traj": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_traj_task), C.POINTER(cr_ik_params),
+                      C.c_int32, C.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_calibrate": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P],
+    "cr_cost_vjp": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P, _P, _P,
+                    C.c_int32, _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
 }
 
@@ -112,6 +124,8 @@ def load(path: str | None = None):
             f.restype = C.c_int
         L.cr_ik_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_ik_params)]
         L.cr_ik_workspace_size.restype = C.c_size_t
+        L.cr_traj_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_ik_params)]
+        L.cr_traj_workspace_size.restype = C.c_size_t
         L.cr_static_workspace_capacity.argtypes = []
         L.cr_static_workspace_capacity.restype = C.c_size_t
         L.cr_last_error_string.argtypes = []
@@ -240,6 +254,33 @@ def cr_solve_ik_static(robot, scene, task, prm, u_out, cost_out, pos_err, rot_er
 
 def cr_static_workspace_capacity() -> int:
     return int(load().cr_static_workspace_capacity())
+
+
+def cr_traj_cost(robot, scene, task, x, cost_out, grad_out=None, upstream=None, stream=None):
+    _check(load().cr_traj_cost(C.byref(robot), C.byref(scene), C.byref(task), _ptr(x), _ptr(cost_out), _ptr(grad_out),
+                               _ptr(upstream), _dtype_code(x), _stream(stream)))
+
+
+def cr_traj_workspace_size(robot, P, goal_ik) -> int:
+    return int(load().cr_traj_workspace_size(C.byref(robot), P, C.byref(goal_ik)))
+
+
+def cr_solve_traj(robot, scene, task, goal_ik, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot, speed, accel,
+                  lim_ok, col_ok, workspace, stream=None):
+    _check(load().cr_solve_traj(C.byref(robot), C.byref(scene), C.byref(task), C.byref(goal_ik), k_traj, alpha0,
+                                _ptr(X_out), _ptr(cost_out), _ptr(goal_pos), _ptr(goal_rot), _ptr(speed), _ptr(accel),
+                                _ptr(lim_ok), _ptr(col_ok), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_calibrate(robot, U, P_meas, theta, iters, lambda0, F_out, hist=None, stream=None):
+    _check(load().cr_calibrate(C.byref(robot), _ptr(U), _ptr(P_meas), U.shape[-1], _ptr(theta), iters, lambda0,
+                               _ptr(F_out), _ptr(hist), _dtype_code(U), _stream(stream)))
+
+
+def cr_cost_vjp(robot, scene, task, u, upstream, grad_u_out, grad_param_out=None, workspace=None, stream=None):
+    _check(load().cr_cost_vjp(C.byref(robot), C.byref(scene), C.byref(task), _ptr(u), u.shape[-1], _ptr(upstream),
+                              _ptr(grad_u_out), _ptr(grad_param_out), _ptr(workspace), _dtype_code(u), _stream(stream)))
 
 
 def cr_poll_status(workspace, stream=None) -> int:
