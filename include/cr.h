@@ -309,6 +309,37 @@ CR_API cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, con
                                uint8_t* lim_ok, uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Path following (Sec. IV-A, Eq. constrained_mp; Sec. IV-B, "Path Following")
+ * ------------------------------------------------------------------------------------------- */
+
+/* P reference paths of H full-pose waypoints. Host struct; waypoints is a device array [7][P * H]
+ * (FP64; waypoint t of path p at column p * H + t: position, then quaternion w, x, y, z). */
+typedef struct {
+  const double* waypoints;
+  int64_t P;
+  int32_t H; /* 2..128 */
+  int32_t reserved;
+  cr_weights w;
+} cr_path_task;
+
+/* Scratch bytes of cr_solve_path. */
+CR_API size_t cr_path_workspace_size(const cr_robot* robot, int64_t P, int32_t H, const cr_ik_params* first_ik);
+
+/* Path following:
+ *  1. exploration: IK at waypoint 0 (Algorithm 1 with first_ik), then for t = 1..H-1 k_warm LM
+ *     iterations of waypoint t's IK residual starting from the solution at t-1 (bulk precision);
+ *  2. refinement: k_joint LM iterations over all waypoints jointly, residual = every waypoint's IK
+ *     rows plus the smoothness rows sqrt(w_s)(u_t - u_{t-1}); the normal matrix is block tridiagonal
+ *     and is factorised by a block Cholesky in FP64 (lambda0 and the LM rule of cr_lm_step).
+ * Outputs (device, FP64): X_out [3n][P * H], cost_out [P] (joint cost), pos_err / rot_err [P * H],
+ * lim_ok / col_ok [P] (uint8: every waypoint within limits / collision-free). first_ik->precision
+ * selects the bulk precision of the whole solve. */
+CR_API cr_status cr_solve_path(const cr_robot* robot, const cr_scene* scene, const cr_path_task* task,
+                               const cr_ik_params* first_ik, int32_t k_warm, int32_t k_joint, double* X_out,
+                               double* cost_out, double* pos_err, double* rot_err, uint8_t* lim_ok, uint8_t* col_ok,
+                               void* workspace, size_t ws_bytes, cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Kinematic calibration and vector-Jacobian products (differentiation w.r.t. the robot)
  * ------------------------------------------------------------------------------------------- */
 

@@ -298,3 +298,49 @@ def calibrate(robot_spec, U_soa, P_meas_soa, theta0, iters=synth.ITERS_CALIB, la
     hist = torch.empty((iters, 2 * robot_spec.n), dtype=torch.float64, device=U_soa.device) if history else None
     lib.cr_calibrate(robot, U_soa, P_meas_soa, theta, iters, lambda0, F, hist)
     return theta, F, hist
+
+
+# ---------------------------------------------------------------------------------------------
+# Path following
+# ---------------------------------------------------------------------------------------------
+def path_task_struct(wp_soa, H: int, weights: synth.WeightSpec) -> lib.cr_path_task:
+    """wp_soa [7][P*H] contiguous CUDA float64 (kept alive by the struct)."""
+    t = lib.cr_path_task()
+    t._keep = wp_soa
+    t.waypoints = wp_soa.data_ptr()
+    t.P = wp_soa.shape[1] // H
+    t.H = H
+    t.w = weights_struct(weights)
+    return t
+
+
+def waypoints_soa(wp, device="cuda"):
+    """wp [P][H][7] host -> device [7][P*H]."""
+    wp = torch.as_tensor(wp, dtype=torch.float64)
+    P, H, _ = wp.shape
+    return wp.reshape(P * H, 7).T.contiguous().to(device)
+
+
+class PathSolver:
+    """Path following for P paths of H waypoints (exploration sweep, joint LM refinement)."""
+
+    def __init__(self, robot_spec, first_ik: synth.IkSpec, weights, P, H, scene: Scene | None = None,
+                 precision=lib.CR_F32, k_warm=synth.K_WARM, k_joint=synth.K_JOINT, device="cuda"):
+        self.robot = robot_struct(robot_spec)
+        self.weights = weights
+        self.P, self.H, self.k_warm, self.k_joint = P, H, k_warm, k_joint
+        self.scene = scene or Scene(None)
+        self.prm = ik_params_struct(first_ik, precision)
+        d = robot_spec.d
+        self.workspace = torch.empty(lib.cr_path_workspace_size(self.robot, P, H, self.prm), dtype=torch.uint8,
+                                     device=device)
+        z = lambda *s, dt=torch.float64: torch.empty(s, dtype=dt, device=device)
+        self.X, self.cost, self.pos, self.rot = z(d, P * H), z(P), z(P * H), z(P * H)
+        self.lim_ok, self.col_ok = z(P, dt=torch.uint8), z(P, dt=torch.uint8)
+
+    def solve(self, wp_soa, p0: int = 0):
+        self._task = path_task_struct(wp_soa, self.H, self.weights)
+        self.prm.p0 = p0
+        lib.cr_solve_path(self.robot, self.scene.c, self._task, self.prm, self.k_warm, self.k_joint, self.X, self.cost,
+                          self.pos, self.rot, self.lim_ok, self.col_ok, self.workspace)
+        return self

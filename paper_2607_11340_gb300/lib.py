@@ -27,7 +27,7 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_solve_ik_plain",
            "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
            "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
-           "cr_calibrate", "cr_cost_vjp")
+           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path")
 
 
 class CrError(RuntimeError):
@@ -60,6 +60,11 @@ class cr_task(C.Structure):
 class cr_traj_task(C.Structure):
     _fields_ = [("u_start", C.c_void_p), ("goal", C.c_void_p), ("P", C.c_int64), ("T", C.c_int32),
                 ("reserved", C.c_int32), ("w", cr_weights)]
+
+
+class cr_path_task(C.Structure):
+    _fields_ = [("waypoints", C.c_void_p), ("P", C.c_int64), ("H", C.c_int32), ("reserved", C.c_int32),
+                ("w", cr_weights)]
 
 
 class cr_ik_params(C.Structure):
@@ -101,6 +106,8 @@ _SIGS = {
     "cr_traj_cost": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_traj_task), _P, _P, _P, _P, C.c_int32, _P],
     "cr_solve_traj": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_traj_task), C.POINTER(cr_ik_params),
                       C.c_int32, C.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_solve_path": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_path_task), C.POINTER(cr_ik_params),
+                      C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
     "cr_calibrate": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P],
     "cr_cost_vjp": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P, _P, _P,
                     C.c_int32, _P],
@@ -126,6 +133,8 @@ def load(path: str | None = None):
         L.cr_ik_workspace_size.restype = C.c_size_t
         L.cr_traj_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_ik_params)]
         L.cr_traj_workspace_size.restype = C.c_size_t
+        L.cr_path_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.c_int32, C.POINTER(cr_ik_params)]
+        L.cr_path_workspace_size.restype = C.c_size_t
         L.cr_static_workspace_capacity.argtypes = []
         L.cr_static_workspace_capacity.restype = C.c_size_t
         L.cr_last_error_string.argtypes = []
@@ -271,6 +280,17 @@ def cr_solve_traj(robot, scene, task, goal_ik, k_traj, alpha0, X_out, cost_out, 
                                 _ptr(X_out), _ptr(cost_out), _ptr(goal_pos), _ptr(goal_rot), _ptr(speed), _ptr(accel),
                                 _ptr(lim_ok), _ptr(col_ok), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_path_workspace_size(robot, P, H, first_ik) -> int:
+    return int(load().cr_path_workspace_size(C.byref(robot), P, H, C.byref(first_ik)))
+
+
+def cr_solve_path(robot, scene, task, first_ik, k_warm, k_joint, X_out, cost_out, pos_err, rot_err, lim_ok, col_ok,
+                  workspace, stream=None):
+    _check(load().cr_solve_path(C.byref(robot), C.byref(scene), C.byref(task), C.byref(first_ik), k_warm, k_joint,
+                                _ptr(X_out), _ptr(cost_out), _ptr(pos_err), _ptr(rot_err), _ptr(lim_ok), _ptr(col_ok),
+                                _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def cr_calibrate(robot, U, P_meas, theta, iters, lambda0, F_out, hist=None, stream=None):
