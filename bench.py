@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
+    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib"],
+                    help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
 
@@ -193,10 +195,120 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def time_steps(torch, fn, steps, flush, stream):
+    """Median and mean of CUDA-event times of fn() over `steps` steps, L2 flushed before each."""
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), float(np.mean(ts))
+
+
+def other_workload(args):
+    """Times one of the other workloads on one GPU and prints its JSON line."""
+    import torch
+
+    from paper_2607_11340_gb300 import api, build_lib, lib
+
+    build_lib.build()
+    lib.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(0)
+    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic"}
+    if args.workload == "ik1":
+        spec, ik, P = synth.ROBOT_1SEG, synth.IK_1SEG, synth.P_1SEG
+        u = synth.hexagon_states(rng, P, spec.n, spec.umax)
+        T, _ = api.fk(api.robot_struct(spec), torch.as_tensor(u.T.copy(), dtype=torch.float64, device=dev))
+        tg = torch.as_tensor(synth.pose_targets(T.cpu().numpy().T, "axis").T.copy(), dtype=torch.float64, device=dev)
+        s = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK5, P, precision=lib.CR_F64, device=dev)
+        fn = lambda: s.solve(tg)
+        units, unit, metric = P, "solves/s", "IK solves/s, 1-segment 5-DoF, FP64, single stage (32 seeds, 50 LM)"
+        wl = "ik_1seg_256targets_32seeds_lm50_fp64"
+        extra = lambda: {"success_rate": float(s.out.success.float().mean())}
+        dtype = "f64"
+    elif args.workload == "path":
+        spec, ik, P, H = synth.ROBOT_4SEG, synth.IK_PATH0, synth.P_PATH, synth.H_PATH
+
+        def fkb(uu):
+            T, bb = api.fk(api.robot_struct(spec), torch.as_tensor(uu.T.copy(), dtype=torch.float64, device=dev), True)
+            return T.cpu().numpy().T, bb.cpu().numpy().transpose(2, 0, 1)
+
+        wp, _, sph = synth.path_workload(spec, P, H, synth.NO_PATH, fkb, seed=0)
+        s = api.PathSolver(spec, ik, synth.WEIGHTS, P, H, api.Scene(sph, per_problem=True), device=dev)
+        wps = api.waypoints_soa(wp, device=dev)
+        fn = lambda: s.solve(wps)
+        units, unit, metric = P, "paths/s", "path following paths/s (64 waypoints, 32 spheres, FP32 + FP64 block Cholesky)"
+        wl = "path_4seg_512paths_64wp_32spheres_warm30_joint20"
+        extra = lambda: {"tracked_rate_1mm": float((s.pos.reshape(P, H).max(1).values <= 1e-3).float().mean()),
+                         "waypoint_solves_per_s": None,
+                         "pos_err_median_m": float(s.pos.median()), "rot_err_median_rad": float(s.rot.median())}
+        dtype = "f32"
+    elif args.workload == "traj":
+        spec, ik, P, Tn = synth.ROBOT_3SEG, synth.IK_GOAL, synth.P_TRAJ, synth.T_TRAJ
+
+        def fkb(uu):
+            T, bb = api.fk(api.robot_struct(spec), torch.as_tensor(uu.T.copy(), dtype=torch.float64, device=dev), True)
+            return T.cpu().numpy().T, bb.cpu().numpy().transpose(2, 0, 1)
+
+        us, goal, sph, _ = synth.traj_workload(spec, P, synth.NO_TRAJ, fkb, seed=0)
+        s = api.TrajSolver(spec, ik, synth.WEIGHTS, P, Tn, api.Scene(sph, per_problem=True), device=dev)
+        usd = torch.as_tensor(us.T.copy(), dtype=torch.float64, device=dev)
+        gd = torch.as_tensor(goal.T.copy(), dtype=torch.float64, device=dev)
+        fn = lambda: s.solve(usd, gd)
+        units, unit, metric = P, "trajectories/s", "trajectory planning trajectories/s (32 states, 64 spheres, 100 PG steps)"
+        wl = "traj_3seg_256problems_32states_64spheres_pg100"
+        extra = lambda: {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
+                         "collision_free_rate": float(s.col_ok.float().mean()),
+                         "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+        dtype = "f32"
+    else:
+        spec = synth.ROBOT_3SEG
+
+        def fkp(U, L, rc):
+            r = api.robot_struct(spec)
+            for i in range(spec.n):
+                r.L[i], r.r_c[i] = L[i], rc[i]
+            T, _ = api.fk(r, torch.as_tensor(U.T.copy(), dtype=torch.float64, device=dev))
+            return T.cpu().numpy().T
+
+        U, Pm, true, nom = synth.calib_workload(spec, synth.K_CALIB, fkp, seed=0)
+        Ud = torch.as_tensor(U.T.copy(), dtype=torch.float32, device=dev)
+        Pd = torch.as_tensor(Pm.T.copy(), dtype=torch.float64, device=dev)
+        res = {}
+
+        def fn():
+            res["th"] = api.calibrate(spec, Ud, Pd, nom)[0]
+
+        units, unit, metric = 1, "calibrations/s", "calibration of 6 parameters from 1024 noisy poses (20 LM iterations)"
+        wl = "calib_3seg_1024poses"
+        extra = lambda: {"param_rel_err_max": float(np.abs(res["th"].cpu().numpy() / true - 1).max())}
+        dtype = "f32"
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    med, mean = time_steps(torch, fn, args.steps, flush, stream)
+    line.update({"metric": metric, "value": units / (mean / 1e3), "unit": unit, "ms_per_step": mean,
+                 "ms_per_step_median": med, "dtype": dtype,
+                 "config": {"workload": wl, "l2": "flushed between timed steps (512 MiB write)"}})
+    line.update(extra())
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload != "ik3":
+        other_workload(args)
         return
     import torch
     import torch.distributed as dist
