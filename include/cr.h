@@ -379,6 +379,15 @@ CR_API const char* cr_last_error_string(void);
 CR_API cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32_t iters, double* ops_out,
                          cr_stream stream);
 
+/* Elementwise run of a device helper the solvers rely on, for checking it against CUDA's own
+ * operations (the paper has no counterpart; this is numerics verification). which:
+ * CR_CHECK_RECIP: out[i] = FP64 reciprocal of in[i] as the block solves of cr_solve_path compute it
+ * (Newton-Raphson from the single-precision approximation; within a few ulp of 1/in[i]).
+ * in, out: device arrays of n doubles (8-byte aligned). Asynchronous on `stream`; CR_EINVAL for a
+ * NULL or misaligned pointer, n < 0 or an unknown helper. */
+#define CR_CHECK_RECIP 0
+CR_API cr_status cr_device_check(int32_t which, const double* in, double* out, int64_t n, cr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ CR_HD double c_fabs(double x) { return fabs(x); }
 CR_HD bool c_finite(float x) { return isfinite(x); }
 CR_HD bool c_finite(double x) { return isfinite(x); }
 template <typename T> CR_HD T c_max(T a, T b) { return a > b ? a : b; }
+template <typename T> CR_HD T c_abs(T a) { return a < T(0) ? -a : a; }
 template <typename T> CR_HD T c_min(T a, T b) { return a < b ? a : b; }
 template <typename T> CR_HD T clampb(T v, T b) { return c_min(b, c_max(-b, v)); }
 
@@ -424,6 +425,65 @@ __device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T d
   }
 }
 
+// Broad phase of the clearance rows. Spheres j0 .. j0 + cnt - 1 (cnt <= 64) that may come within reach
+// of some backbone sample of segment i are the set bits of mask[i]. The backbone has unit speed in arc
+// length, so every sample of segment i lies within L_i / 2 of the segment's mid-arc point; a sphere
+// whose centre is farther than L_i / 2 + reach from that point reaches none of them. The margin (a
+// 1e-4 fraction of the magnitudes involved) covers rounding, so a culled pair is one the exact
+// per-sample test rejects as well and the active set is unchanged.
+template <typename T, int N>
+CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, const Sphere4<T>* sph, int j0, int cnt,
+                                uint64_t (&mask)[N]) {
+  T lsum = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) lsum += rb.L[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T q[3], m[3], s, c;
+    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5), q, m, s, c);
+    const T half = T(0.5) * rb.L[i];
+    uint64_t mk = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const Sphere4<T> S = sph[j0 + j];
+      const T dx = m[0] - S.x, dy = m[1] - S.y, dz = m[2] - S.z;
+      const T lim = half + S.reach + T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
+      if (dx * dx + dy * dy + dz * dz < lim * lim) mk |= 1ull << j;
+    }
+    mask[i] = mk;
+  }
+}
+
+// The same sets computed by a warp: lane l tests spheres j0 + l and j0 + l + 32 against every
+// segment and the ballots assemble the masks (identical in all lanes afterwards).
+template <typename T, int N>
+__device__ void warp_segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, const Sphere4<T>* sph, int j0,
+                                          int cnt, uint64_t (&mask)[N]) {
+  const int lane = threadIdx.x & 31;
+  T lsum = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) lsum += rb.L[i];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T q[3], m[3], s, c;
+    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5), q, m, s, c);
+    const T half = T(0.5) * rb.L[i];
+    uint64_t mk = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      bool hit = false;
+      if (j < cnt) {
+        const Sphere4<T> S = sph[j0 + j];
+        const T dx = m[0] - S.x, dy = m[1] - S.y, dz = m[2] - S.z;
+        const T lim = half + S.reach + T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
+        hit = dx * dx + dy * dy + dz * dz < lim * lim;
+      }
+      mk |= (uint64_t)__ballot_sync(0xffffffffu, hit) << (32 * h);
+    }
+    mask[i] = mk;
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Cost and adjoint of one state, in two phases
 // ------------------------------------------------------------------------------------------------
@@ -448,16 +508,20 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
   }
   if (OBST && no > 0) {
     const T inb = T(1) / T(rb.nb);
+    for (int j0 = 0; j0 < no; j0 += 64) {
+    uint64_t mk[N];
+    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
+      if (!mk[i]) continue;
       for (int k = 1; k <= rb.nb; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
         T gw[3] = {T(0), T(0), T(0)};
         bool hit = false;
-        for (int j = 0; j < no; ++j) {
-          Sphere4<T> S = sph[j];
+        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
           if (d2 < S.reach * S.reach) {
@@ -489,6 +553,7 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
           if (PGRAD) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
         }
       }
+    }
     }
   }
   if (coll_out) *coll_out = coll;
@@ -795,14 +860,18 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
   }
   if (OBST && no > 0) {
     const T inb = T(1) / T(rb.nb);
+    for (int j0 = 0; j0 < no; j0 += 64) {
+    uint64_t mk[N];
+    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
+      if (!mk[i]) continue;
       for (int k = 1; k <= rb.nb; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
-        for (int jsp = 0; jsp < no; ++jsp) {
-          Sphere4<T> S = sph[jsp];
+        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
           if (!(d2 < S.reach * S.reach)) continue;
@@ -844,8 +913,31 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
         }
       }
     }
+    }
   }
   return F;
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 reciprocal for the pivots of the block solves
+// ------------------------------------------------------------------------------------------------
+// 1/d by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r), started from the
+// single-precision hardware approximation (PTX rcp.approx.f32, within 1 ulp of float). The seed's
+// relative error e (<= 2^-22 with the rounding of d to float) becomes e^2 after one step and e^4
+// after two, below FP64 rounding, so the result is within a few ulp of 1/d. Four FMAs on the FP64
+// pipe instead of the longer division sequence. Outside the single-precision normal range the
+// division is taken.
+CR_HD double recip_nr(double d) {
+  const double ad = d < 0.0 ? -d : d;
+  if (!(ad > 1e-37 && ad < 1e37)) return 1.0 / d;
+  const float f = __double2float_rn(d);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f));
+  double r = double(rf);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -990,16 +1082,22 @@ CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, co
   Chain<T, N> ch;
   chain_forward(rb, u, ch);
   const T inb = T(1) / T(rb.nb);
-  for (int i = 0; i < N; ++i)
-    for (int k = 1; k <= rb.nb; ++k) {
-      T q[3], wp[3], s, c;
-      backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, wp, s, c);
-      for (int j = 0; j < no; ++j) {
-        Sphere4<T> S = sph[j];
-        T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
-        if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
+  for (int j0 = 0; j0 < no; j0 += 64) {
+    uint64_t mk[N];
+    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+    for (int i = 0; i < N; ++i) {
+      if (!mk[i]) continue;
+      for (int k = 1; k <= rb.nb; ++k) {
+        T q[3], wp[3], s, c;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, wp, s, c);
+        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
+          T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
+          if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
+        }
       }
     }
+  }
   return false;
 }
 

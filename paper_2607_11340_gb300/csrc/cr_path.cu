@@ -33,7 +33,7 @@ PathWs path_ws(const cr_robot& r, int64_t P, int H, const cr_ik_params& g) {
   w.rot = off; off = align256(off + (size_t)P * 8);
   w.succ = off; off = align256(off + (size_t)P);
   w.X = off; off = align256(off + D * P * H * tb);
-  w.Z = off; off = align256(off + (size_t)P * H * D * D * 8);
+  w.Z = off; off = align256(off + (size_t)P * H * crk::path_z_stride((int)D) * 8);
   w.total = off;
   return w;
 }

@@ -8,8 +8,9 @@
 //                 lanes for the clearance rows. Lane l owns entries l, l+32, l+64 of the packed
 //                 normal matrix; lane 0 factorises it (bulk precision: this is exploration).
 //  k_path_joint : one CTA per path. Thread t evaluates waypoint t's rows and its block of J^T J;
-//                 the FP64 block Cholesky over t (S_t = A_t - w_s^2 S_{t-1}^-1, forward and back
-//                 substitution) spreads each 12x12 step over the CTA.
+//                 one warp runs the FP64 block elimination over t (S_t = M_t - w_s^2 S_{t-1}^-1,
+//                 forward and back substitution), each block inverted by a symmetric sweep whose
+//                 packed entries are spread over the 32 lanes, so a block step needs no CTA barrier.
 #pragma once
 
 #include "cr_traj_impl.cuh"
@@ -28,7 +29,7 @@ template <typename T> struct PathArgs {
   T w_s;
   const double* u0;       // [D][P]   first waypoint (IK result)
   T* X;                   // [D][P*H] working states (bulk precision)
-  double* Z;              // [P][H][D*D] block inverses of the joint solve
+  double* Z;              // [P][H][path_z_stride(D)] swept blocks -S_t^-1 of the joint solve
   double* X_out;          // [D][P*H]
   double* F_out;          // [P]
   double* pos;            // [P*H]
@@ -170,15 +171,26 @@ __device__ T warp_waypoint_eval(const RobotK<T>& rb, const WeightsK<T>& w, const
   if (OBST && no > 0) {
     const T inb = T(1) / T(rb.nb);
     const int ns = N * rb.nb;
+    for (int j0 = 0; j0 < no; j0 += 64) {
+    uint64_t mk[N];
+    warp_segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
     // active pairs found by each lane, processed one at a time by the whole warp
     for (int base = 0; base < ns; base += 32) {
       const int sidx = base + lane;
       const bool mine = sidx < ns;
       const int i = mine ? sidx / rb.nb : 0, k = mine ? sidx % rb.nb + 1 : 1;
+      // candidate spheres of the segments these 32 samples belong to (the same in every lane)
+      const int i_lo = base / rb.nb, i_hi = (base + 31 < ns ? base + 31 : ns - 1) / rb.nb;
+      uint64_t um = 0;
+#pragma unroll
+      for (int ii = 0; ii < N; ++ii)
+        if (ii >= i_lo && ii <= i_hi) um |= mk[ii];
+      if (!um) continue;
       T q[3], wpt[3], s, c;
       T sg = T(k) * inb;
       if (mine) backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wpt, s, c);
-      for (int jsp = 0; jsp < no; ++jsp) {
+      for (uint64_t bits = um; bits; bits &= bits - 1) {
+        const int jsp = j0 + __ffsll((long long)bits) - 1;
         bool act = false;
         T dist = T(0), viol = T(0), dx = T(0), dy = T(0), dz = T(0);
         if (mine) {
@@ -238,6 +250,7 @@ __device__ T warp_waypoint_eval(const RobotK<T>& rb, const WeightsK<T>& w, const
           own_rank1<T, D>(lane, ow, sj, Aown, gown, jr, rr);
         }
       }
+    }
     }
   }
 #pragma unroll
@@ -374,39 +387,165 @@ __global__ void __launch_bounds__(128) k_path_warm(RobotK<T> rb, WeightsK<T> w, 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Refinement: joint LM over the path, FP64 block-tridiagonal Cholesky
+// Refinement: joint LM over the path, FP64 block-tridiagonal elimination
 // ------------------------------------------------------------------------------------------------
-// Blocks: diagonal A_t (+ smoothness w_s I per neighbour, + lambda D), off-diagonal -w_s I.
-// Forward: S_0 = A_0, S_t = A_t - w_s^2 S_{t-1}^-1, y_0 = -g_0, y_t = -g_t + w_s S_{t-1}^-1 y_{t-1};
-// backward: x_{H-1} = S^-1 y_{H-1}, x_t = S_t^-1 (y_t + w_s x_{t+1}). Each S_t is factorised
-// S_t = L L^T (Cholesky), its inverse Z_t = L^-T L^-1 kept for the Schur update and the back sweep.
+// Entries of the augmented (D+1)x(D+1) packed lower triangle [[S, b], [b^T, *]] owned by a lane of
+// the solving warp: e = lane + 32 s. Row D is the right-hand side; (D, D) is carried but unused.
+template <int D> struct AugSlots {
+  static constexpr int DA = (D + 1) * (D + 2) / 2;
+  static constexpr int SL = (DA + 31) / 32;
+  int r[SL], c[SL];
+  bool on[SL];
+};
+template <int D> __device__ AugSlots<D> aug_slots(int lane) {
+  AugSlots<D> o;
+#pragma unroll
+  for (int s = 0; s < AugSlots<D>::SL; ++s) {
+    const int e = lane + 32 * s;
+    o.on[s] = e < AugSlots<D>::DA;
+    int a = 0;
+    while (o.on[s] && (a + 1) * (a + 2) / 2 <= e) ++a;
+    o.r[s] = a;
+    o.c[s] = o.on[s] ? e - a * (a + 1) / 2 : 0;
+  }
+  return o;
+}
+// doubles of Z storage per block (the swept slots of one block, slot-major)
+template <int D> constexpr int aug_stride() { return AugSlots<D>::SL * 32; }
+
+// Symmetric sweep (Gauss-Jordan elimination without pivoting, valid for a positive definite S) of
+// pivots 0..D-1 of the augmented matrix held in the warp's slots. Pivot k maps d = S_kk to -1/d, the
+// rest of row and column k to S_ik / d and every other entry to S_ij - S_ik S_kj / d. Afterwards the
+// S block holds -S^-1 and row D holds (S^-1 b)^T. Returns false if a pivot is not positive. col and
+// colr are the warp's scratch of D + 1 doubles: column k, and column k scaled by 1/d.
+template <int D>
+__device__ bool sweep_aug(double (&v)[AugSlots<D>::SL], const AugSlots<D>& sl, double* col, double* colr) {
+  constexpr int SL = AugSlots<D>::SL;
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+      if (sl.on[s] && (sl.r[s] == k || sl.c[s] == k)) col[sl.r[s] == k ? sl.c[s] : sl.r[s]] = v[s];
+    __syncwarp();
+    double d = col[k];
+    ok = ok && d > 0.0;
+    d = d > 0.0 ? d : 1.0;
+    const double ri = recip_nr(d);
+    if (lane <= D) colr[lane] = col[lane] * ri;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      if (!sl.on[s]) continue;
+      const int i = sl.r[s], j = sl.c[s];
+      const double upd = fma(-colr[i], col[j], v[s]);
+      v[s] = (i == k) ? ((j == k) ? -ri : colr[j]) : ((j == k) ? colr[i] : upd);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+// The joint LM system is block tridiagonal: diagonal blocks M_t = J_t^T J_t + w_s nb_t I + lambda D_t
+// (nb_t = number of neighbours of waypoint t), off-diagonal blocks -w_s I, right-hand side r = -g.
+// Block elimination: S_0 = M_0, S_t = M_t - w_s^2 S_{t-1}^-1; z_t = S_t^-1 (r_t + w_s z_{t-1});
+// x_{H-1} = z_{H-1}, x_t = z_t + w_s S_t^-1 x_{t+1}. One warp runs it in FP64: the sweep of the
+// augmented [S_t, r_t + w_s z_{t-1}] gives -S_t^-1 (kept in registers for the next Schur update and
+// stored to Zg for the back substitution) and z_t together.
+//   Af [H][DD] J^T J blocks (bulk precision), g [H][D], z [H][D] (z_t, then x_t in place)
+template <typename TA, int D>
+__device__ bool joint_solve_warp(const TA* Af, const double* g, double* z, double* Zg, double* col, double* colr,
+                                 double* Zs, int H, double ws, double lam) {
+  constexpr int SL = AugSlots<D>::SL, DD = D * (D + 1) / 2, ZS = aug_stride<D>();
+  const int lane = threadIdx.x & 31;
+  const AugSlots<D> sl = aug_slots<D>(lane);
+  const double ws2 = ws * ws;
+  double v[SL];
+  bool ok = true;
+  for (int t = 0; t < H; ++t) {
+    const double nb = double((t > 0) + (t + 1 < H));
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      if (!sl.on[s]) continue;
+      const int i = sl.r[s], j = sl.c[s];
+      double a;
+      if (i < D) {
+        a = double(Af[(size_t)t * DD + tri(i, j)]);
+        if (i == j) {
+          a += ws * nb;
+          a += lam * fmax(a, 1e-12);
+        }
+        if (t > 0) a = fma(ws2, v[s], a);  // v = -S_{t-1}^-1
+      } else {
+        a = j < D ? -g[t * D + j] + (t > 0 ? ws * z[(t - 1) * D + j] : 0.0) : 0.0;
+      }
+      v[s] = a;
+    }
+    ok = sweep_aug<D>(v, sl, col, colr) && ok;
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      Zg[(size_t)t * ZS + s * 32 + lane] = v[s];
+      if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) z[t * D + sl.c[s]] = v[s];
+    }
+    __syncwarp();
+  }
+  // back substitution: x_t = z_t - w_s V_t x_{t+1}, V_t = -S_t^-1 as stored
+  double nxt[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) nxt[s] = H >= 2 ? Zg[(size_t)(H - 2) * ZS + s * 32 + lane] : 0.0;
+  for (int t = H - 2; t >= 0; --t) {
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+      if (sl.on[s] && sl.r[s] < D) Zs[tri(sl.r[s], sl.c[s])] = nxt[s];
+    if (t > 0) {
+#pragma unroll
+      for (int s = 0; s < SL; ++s) nxt[s] = Zg[(size_t)(t - 1) * ZS + s * 32 + lane];
+    }
+    __syncwarp();
+    if (lane < D) {
+      double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; j += 2) {
+        acc0 = fma(Zs[lane >= j ? tri(lane, j) : tri(j, lane)], z[(t + 1) * D + j], acc0);
+        if (j + 1 < D) acc1 = fma(Zs[lane >= j + 1 ? tri(lane, j + 1) : tri(j + 1, lane)], z[(t + 1) * D + j + 1], acc1);
+      }
+      z[t * D + lane] = fma(-ws, acc0 + acc1, z[t * D + lane]);
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+// One CTA per path, one thread per waypoint (blockDim = H rounded up to a warp). Per iteration:
+// every thread forms its waypoint's J^T J block and gradient (bulk precision) plus the smoothness
+// terms; warp 0 solves the block system in FP64; all threads evaluate the trial path.
 template <typename T, int N, bool OBST>
-__global__ void __launch_bounds__(160) k_path_joint(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
+__global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
                                                      WeightsK<double> wd, PathArgs<T> a) {
-  constexpr int D = 3 * N, DD = D * (D + 1) / 2, D2 = D * D;
+  constexpr int D = 3 * N, DD = D * (D + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t p = blockIdx.x;
   const int tid = threadIdx.x, H = a.H;
   const int64_t PH = a.P * H;
-  // shared layout: spheres (T, double) | A [H][DD] | g [H][D] | Dg [H][D] | y [H][D] | S [D2] | L [D2] | W [D2] | red
+  // shared layout: spheres (T, double) | g [H][D] | z [H][D] | col, colr [32] | Zs [DD] | red [32] |
+  // misc [8] | Af [H][DD] (T) | ush [H][D] (T)
   size_t off = 0;
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
   off += (size_t)a.no * sizeof(Sphere4<T>);
   Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw + off);
   off += (size_t)a.no * sizeof(Sphere4<double>);
   off = (off + 15) & ~size_t(15);
-  double* A = reinterpret_cast<double*>(smem_raw + off);
-  double* g = A + (size_t)H * DD;
-  double* Dg = g + (size_t)H * D;
-  double* y = Dg + (size_t)H * D;
-  double* xs = y + (size_t)H * D;  // the step
-  double* S = xs + (size_t)H * D;
-  double* Lm = S + D2;
-  double* Wm = Lm + D2;
-  double* red = Wm + D2;        // [32]
-  double* misc = red + 32;      // [8]: ok flag, F, Fn, pred
-  T* ush = reinterpret_cast<T*>(misc + 8);  // [H][D] current states (for the smoothness coupling)
-  double* Zg = a.Z + (size_t)p * H * D2;
+  double* g = reinterpret_cast<double*>(smem_raw + off);
+  double* z = g + (size_t)H * D;
+  double* col = z + (size_t)H * D;
+  double* colr = col + 32;
+  double* Zs = colr + 32;
+  double* red = Zs + DD;
+  double* misc = red + 32;  // [8]: ok flag
+  T* Af = reinterpret_cast<T*>(misc + 8);
+  T* ush = Af + (size_t)H * DD;
+  double* Zg = a.Z + (size_t)p * H * aug_stride<D>();
   if (OBST) {
     const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
     stage_spheres(sp, a.no, rb, w.delta, sph);
@@ -444,13 +583,13 @@ __global__ void __launch_bounds__(160) k_path_joint(RobotK<T> rb, WeightsK<T> w,
   };
 
   for (int it = 0; it < a.k_joint; ++it) {
-    // 1. blocks of J^T J and J^T r of every waypoint, plus the smoothness rows
+    // 1. J^T J block and J^T r of every waypoint, plus the smoothness rows' gradient
     double Fl = 0.0;
     if (wthr) {
       T At[DD], gt[D];
       Fl = double(eval_ik_normal<T, T, N, OBST>(rb, w, CR_TASK_IK6, tg, sph, a.no, u, At, gt));
 #pragma unroll
-      for (int e = 0; e < DD; ++e) A[tid * DD + e] = double(At[e]);
+      for (int e = 0; e < DD; ++e) Af[tid * DD + e] = At[e];
 #pragma unroll
       for (int q = 0; q < D; ++q) {
         g[tid * D + q] = double(gt[q]);
@@ -459,7 +598,6 @@ __global__ void __launch_bounds__(160) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     }
     __syncthreads();
     if (wthr) {
-      const int nb = (tid > 0) + (tid + 1 < H);
 #pragma unroll
       for (int q = 0; q < D; ++q) {
         double s = 0.0, uq = double(u[q]);
@@ -470,103 +608,34 @@ __global__ void __launch_bounds__(160) k_path_joint(RobotK<T> rb, WeightsK<T> w,
         }
         if (tid + 1 < H) s -= ws * (double(ush[(tid + 1) * D + q]) - uq);
         g[tid * D + q] += s;
-        A[tid * DD + tri(q, q)] += ws * nb;
-        double dg = fmax(A[tid * DD + tri(q, q)], 1e-12);
-        Dg[tid * D + q] = dg;
-        A[tid * DD + tri(q, q)] += lam * dg;
       }
     }
     const double F = block_sum(Fl, red);
     __syncthreads();
-    // 2. forward elimination over t (FP64)
-    if (tid == 0) misc[0] = 1.0;
-    __syncthreads();
-    for (int t = 0; t < H; ++t) {
-      for (int e = tid; e < D2; e += blockDim.x) {
-        const int i = e / D, j = e % D;
-        double s = (i >= j) ? A[t * DD + tri(i, j)] : A[t * DD + tri(j, i)];
-        if (t > 0) s -= ws * ws * Zg[(size_t)(t - 1) * D2 + e];
-        S[e] = s;
-      }
-      __syncthreads();
-      // Cholesky of S (right-looking; L in Lm, lower part)
-      for (int j = 0; j < D; ++j) {
-        if (tid == 0) {
-          double s = S[j * D + j];
-          if (!(s > 0.0)) { misc[0] = 0.0; s = 1.0; }
-          double iv = rsqrt(s);
-          Lm[j * D + j] = s * iv;
-          misc[1] = iv;
-        }
-        __syncthreads();
-        const double iv = misc[1];
-        if (tid > j && tid < D) Lm[tid * D + j] = S[tid * D + j] * iv;
-        __syncthreads();
-        for (int e = tid; e < D2; e += blockDim.x) {
-          const int i = e / D, k = e % D;
-          if (k > j && i >= k) S[i * D + k] -= Lm[i * D + j] * Lm[k * D + j];
-        }
-        __syncthreads();
-      }
-      // W = L^-1 (columns in parallel), then Z_t = W^T W
-      if (tid < D) {
-        const int c = tid;
-        for (int i = 0; i < D; ++i) {
-          double v;
-          if (i < c) v = 0.0;
-          else if (i == c) v = 1.0 / Lm[c * D + c];
-          else {
-            double s = 0.0;
-            for (int k = c; k < i; ++k) s += Lm[i * D + k] * Wm[k * D + c];
-            v = -s / Lm[i * D + i];
-          }
-          Wm[i * D + c] = v;
-        }
-      }
-      __syncthreads();
-      for (int e = tid; e < D2; e += blockDim.x) {
-        const int i = e / D, j = e % D;
-        double s = 0.0;
-        for (int k = (i > j ? i : j); k < D; ++k) s += Wm[k * D + i] * Wm[k * D + j];
-        Zg[(size_t)t * D2 + e] = s;
-      }
-      // y_t = -g_t + w_s Z_{t-1} y_{t-1}
-      if (tid < D) {
-        double s = -g[t * D + tid];
-        if (t > 0)
-          for (int k = 0; k < D; ++k) s += ws * Zg[(size_t)(t - 1) * D2 + tid * D + k] * y[(t - 1) * D + k];
-        y[t * D + tid] = s;
-      }
-      __syncthreads();
+    // 2. FP64 block elimination (warp 0)
+    if (tid < 32) {
+      const bool okw = joint_solve_warp<T, D>(Af, g, z, Zg, col, colr, Zs, H, ws, lam);
+      if (tid == 0) misc[0] = okw ? 1.0 : 0.0;
     }
-    const bool ok = misc[0] != 0.0;
-    // 3. back substitution: x_{H-1} = Z y_{H-1}; x_t = Z_t (y_t + w_s x_{t+1})
-    if (!ok) {
+    __syncthreads();
+    if (misc[0] == 0.0) {
       lam *= nu;
       nu *= 2.0;
+      __syncthreads();
       continue;
     }
-    for (int t = H - 1; t >= 0; --t) {
-      if (tid < D) {
-        double xt = 0.0;
-        for (int k = 0; k < D; ++k) {
-          double rhs = y[t * D + k] + (t + 1 < H ? ws * xs[(t + 1) * D + k] : 0.0);
-          xt += Zg[(size_t)t * D2 + tid * D + k] * rhs;
-        }
-        xs[t * D + tid] = xt;
-      }
-      __syncthreads();
-    }
-    // 4. trial, gain ratio 1/2 x^T (lambda D x - g), accept
+    // 3. trial, gain ratio 1/2 x^T (lambda D x - g), accept
     T un[D];
     double predl = 0.0;
 #pragma unroll
-    for (int q = 0; q < D; ++q) un[q] = wthr ? u[q] + T(xs[tid * D + q]) : u[q];
+    for (int q = 0; q < D; ++q) un[q] = wthr ? u[q] + T(z[tid * D + q]) : u[q];
     if (wthr) {
+      const double nb = double((tid > 0) + (tid + 1 < H));
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        double xq = xs[tid * D + q];
-        predl += xq * (lam * Dg[tid * D + q] * xq - g[tid * D + q]);
+        const double xq = z[tid * D + q];
+        const double dg = fmax(double(Af[tid * DD + tri(q, q)]) + ws * nb, 1e-12);
+        predl += xq * (lam * dg * xq - g[tid * D + q]);
       }
     }
     const double pred = 0.5 * block_sum(predl, red);
@@ -658,10 +727,13 @@ template <typename T> PathArgs<T> path_args(const PathLaunch& l) {
 inline size_t path_joint_smem(int no, int H, int D, size_t tsize) {
   size_t off = (size_t)no * (4 * tsize + 32);
   off = (off + 15) & ~size_t(15);
-  off += sizeof(double) * ((size_t)H * (D * (D + 1) / 2 + 4 * D) + 3 * (size_t)D * D + 32 + 8);
-  off += tsize * (size_t)H * D;
+  off += sizeof(double) * ((size_t)2 * H * D + 64 + (size_t)D * (D + 1) / 2 + 32 + 8);
+  off += tsize * ((size_t)H * D * (D + 1) / 2 + (size_t)H * D);
   return off;
 }
+
+// doubles of the joint solve's block storage per waypoint (the workspace's Z region)
+inline int path_z_stride(int D) { return ((D + 1) * (D + 2) / 2 + 31) / 32 * 32; }
 
 template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   constexpr int D = 3 * N, DD = D * (D + 1) / 2;
@@ -683,7 +755,7 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   }
   if ((st = crh::check_launch("cr_solve_path exploration"))) return st;
   // refinement
-  const int threads = a.H <= 128 ? 160 : ((a.H + 31) / 32) * 32;
+  const int threads = ((a.H + 31) / 32) * 32;
   size_t smj = path_joint_smem(a.no, a.H, D, sizeof(T));
   if (a.no > 0) {
     if ((st = set_smem(k_path_joint<T, N, true>, smj))) return st;

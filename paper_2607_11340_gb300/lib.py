@@ -27,7 +27,7 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_solve_ik_plain",
            "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
            "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
-           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path")
+           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check")
 
 
 class CrError(RuntimeError):
@@ -112,6 +112,7 @@ _SIGS = {
     "cr_cost_vjp": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P, _P, _P,
                     C.c_int32, _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
+    "cr_device_check": [C.c_int32, _P, _P, C.c_int64, _P],
 }
 
 
@@ -307,6 +308,13 @@ def cr_poll_status(workspace, stream=None) -> int:
     out = C.c_int32(0)
     _check(load().cr_poll_status(_ptr(workspace), C.byref(out), _stream(stream)))
     return out.value
+
+
+CR_CHECK_RECIP = 0
+
+
+def cr_device_check(which: int, x, out, stream=None):
+    _check(load().cr_device_check(which, _ptr(x), _ptr(out), x.numel(), _stream(stream)))
 
 
 def cr_peak_launch(kind: int, buf, iters: int, stream=None) -> float:
