@@ -3,10 +3,10 @@
 // its own IK residual), then the refinement: joint LM over all H waypoints with the successive-
 // state smoothness rows sqrt(w_s)(u_t - u_{t-1}), whose normal matrix is block tridiagonal.
 //
-//  k_path_warm  : one warp per path. Every lane holds the path's state and evaluates the
-//                 kinematics (identical in all lanes); the backbone samples are split over the
-//                 lanes for the clearance rows. Lane l owns entries l, l+32, l+64 of the packed
-//                 normal matrix; lane 0 factorises it (bulk precision: this is exploration).
+//  k_path_warm  : one warp per path. Every lane holds the path's state; residual rows are formed
+//                 column-wise (lane q: entry q), J^T J accumulates in packed slots spread over the
+//                 lanes, the damped system is solved by a warp sweep (bulk precision: this is
+//                 exploration); backbone samples are split over the lanes for the clearance rows.
 //  k_path_joint : one CTA per path. Thread t evaluates waypoint t's rows and its block of J^T J;
 //                 one warp runs the FP64 block elimination over t (S_t = M_t - w_s^2 S_{t-1}^-1,
 //                 forward and back substitution), each block inverted by a symmetric sweep whose
@@ -14,6 +14,7 @@
 #pragma once
 
 #include "cr_traj_impl.cuh"
+#include "cr_warp.cuh"
 
 namespace crk {
 
@@ -41,236 +42,41 @@ template <typename T> struct PathArgs {
 // ------------------------------------------------------------------------------------------------
 // Exploration: warp-cooperative LM on one waypoint's IK residual
 // ------------------------------------------------------------------------------------------------
-// Entries of the packed normal matrix owned by this lane: lane, lane + 32, lane + 64.
-struct Owned {
-  int r[3], c[3];
-  bool on[3];
-};
-template <int D> CR_HD Owned owned_entries(int lane) {
-  Owned o;
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    int e = lane + 32 * s;
-    o.on[s] = e < D * (D + 1) / 2;
-    int a = 0;
-    while (o.on[s] && (a + 1) * (a + 2) / 2 <= e) ++a;
-    o.r[s] = a;
-    o.c[s] = o.on[s] ? e - a * (a + 1) / 2 : 0;
-  }
-  return o;
+// Per-warp shared scratch: spheres [no] | col, colr, sx, sdg [32 each]
+template <typename T> __host__ __device__ inline size_t warm_warp_bytes(int no) {
+  return (((size_t)no * sizeof(Sphere4<T>) + 15) / 16 * 16) + 4 * 32 * sizeof(T);
 }
 
-// Adds the rank-1 update j j^T (and j r to g) to this lane's entries; the row goes through the
-// warp's shared scratch sj[D] (every lane holds the same j).
-template <typename T, int D>
-__device__ void own_rank1(int lane, const Owned& ow, T* sj, T (&Aown)[3], T& gown, const T (&j)[D], T r) {
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < D; ++q)
-    if (lane == q) sj[q] = j[q];
-  __syncwarp();
-#pragma unroll
-  for (int s = 0; s < 3; ++s)
-    if (ow.on[s]) Aown[s] += sj[ow.r[s]] * sj[ow.c[s]];
-  if (lane < D) gown += sj[lane] * r;
-}
-
-// F, and (when NORMAL) this lane's entries of J^T J and g, of the waypoint residual at u.
-// Identical kinematics in every lane; samples lane, lane + 32, ... for the clearance rows.
-template <typename T, int N, bool OBST, bool NORMAL>
-__device__ T warp_waypoint_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, const Sphere4<T>* sph,
-                                int no, const T (&u)[3 * N], const Owned& ow, T* sj, T (&Aown)[3], T& gown) {
+template <typename T, int N, bool OBST>
+__device__ void warm_sweep_warp(const RobotK<T>& rb, const WeightsK<T>& w, const double* wp, int64_t PH, int64_t base,
+                                int H, int k_warm, T lam0, const Sphere4<T>* sph, int no, T (&u)[3 * N], T* scratch,
+                                T* Xout, int64_t xstride) {
   constexpr int D = 3 * N;
   const int lane = threadIdx.x & 31;
-  Aown[0] = Aown[1] = Aown[2] = T(0);
-  gown = T(0);
-  Chain<T, N> ch;
-  chain_forward(rb, u, ch);
-  T r[6], e[3], ang, sn, cs;
-  pose_rows(CR_TASK_IK6, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
-  T Fonce = T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
-  T tv[N][2][3], tw[N][2][3];
-  if (NORMAL) {
-    segment_twists(rb, ch, tv, tw);
-    // pose rows: position then rotation (J_r^-1(e) R^T applied to the angular part)
-    T be = log_beta(ang);
-    T E2[3][3] = {{-(e[1] * e[1] + e[2] * e[2]), e[0] * e[1], e[0] * e[2]},
-                  {e[0] * e[1], -(e[0] * e[0] + e[2] * e[2]), e[1] * e[2]},
-                  {e[0] * e[2], e[1] * e[2], -(e[0] * e[0] + e[1] * e[1])}};
-    T Jr[3][3] = {{T(1) + be * E2[0][0], T(-0.5) * e[2] + be * E2[0][1], T(0.5) * e[1] + be * E2[0][2]},
-                  {T(0.5) * e[2] + be * E2[1][0], T(1) + be * E2[1][1], T(-0.5) * e[0] + be * E2[1][2]},
-                  {T(-0.5) * e[1] + be * E2[2][0], T(0.5) * e[0] + be * E2[2][1], T(1) + be * E2[2][2]}};
-    T Mrot[3][3];
+  const AugSlots<D> sl = aug_slots<D>(lane);
+  T* col = scratch;
+  T* colr = col + 32;
+  T* sx = colr + 32;
+  T* sdg = sx + 32;
+  for (int t = 1; t < H; ++t) {
+    TargetK<T> tg = load_target<T>(wp, PH, base + t, CR_TASK_IK6);
+    T lam = lam0, nu = T(2);
+    for (int it = 0; it < k_warm; ++it) warp_lm_step<T, N, OBST>(rb, w, tg, sph, no, u, sl, lam, nu, col, colr, sx, sdg);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-        Mrot[a][b] = Jr[a][0] * ch.R[3 * b] + Jr[a][1] * ch.R[3 * b + 1] + Jr[a][2] * ch.R[3 * b + 2];
-#pragma unroll
-    for (int row = 0; row < 6; ++row) {
-      T jr[D];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T ga[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          T wpv[3];
-          cross(tw[i][k], ch.p, wpv);
-          T jp[3] = {tv[i][k][0] + wpv[0], tv[i][k][1] + wpv[1], tv[i][k][2] + wpv[2]};
-          if (row < 3) ga[k] = w.wp * jp[row];
-          else {
-            const int a = row - 3;
-            ga[k] = w.wR * (Mrot[a][0] * tw[i][k][0] + Mrot[a][1] * tw[i][k][1] + Mrot[a][2] * tw[i][k][2]);
-          }
-        }
-        bend_grad_to_u(rb.K[i], ga[0], ga[1], jr[3 * i], jr[3 * i + 1], jr[3 * i + 2]);
-      }
-      own_rank1<T, D>(lane, ow, sj, Aown, gown, jr, r[row]);
-    }
+    for (int q = 0; q < D; ++q)
+      if (q == lane) Xout[q * xstride + t] = u[q];
   }
-  // penalty rows on u (counted once: every lane adds its own entries, F is taken from lane 0)
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
-    Fonce += T(0.5) * w.rho_eq * su * su;
-    if (NORMAL) {
-      T j[D];
-#pragma unroll
-      for (int q = 0; q < D; ++q) j[q] = (q / 3 == i) ? w.se : T(0);
-      own_rank1<T, D>(lane, ow, sj, Aown, gown, j, w.se * su);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int q = 3 * i + a;
-      T hi = u[q] - rb.umax[i], lo = -rb.umax[i] - u[q];
-      if (hi > T(0) || lo > T(0)) {
-        T v = hi > T(0) ? hi : lo, sgn = hi > T(0) ? T(1) : T(-1);
-        Fonce += T(0.5) * w.rho_b * v * v;
-        if (NORMAL) {
-          T j[D];
-#pragma unroll
-          for (int qq = 0; qq < D; ++qq) j[qq] = qq == q ? sgn * w.sb : T(0);
-          own_rank1<T, D>(lane, ow, sj, Aown, gown, j, w.sb * v);
-        }
-      }
-    }
-    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
-      T th = c_sqrt(ch.x[i]);
-      T vk = th - rb.thmax[i];
-      Fonce += T(0.5) * w.rho_k * vk * vk;
-      if (NORMAL) {
-        T j[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) j[q] = T(0);
-        bend_grad_to_u(rb.K[i], w.sk * ch.ax[i] / th, w.sk * ch.ay[i] / th, j[3 * i], j[3 * i + 1], j[3 * i + 2]);
-        own_rank1<T, D>(lane, ow, sj, Aown, gown, j, w.sk * vk);
-      }
-    }
-  }
-  T Fsplit = T(0);
-  if (OBST && no > 0) {
-    const T inb = T(1) / T(rb.nb);
-    const int ns = N * rb.nb;
-    for (int j0 = 0; j0 < no; j0 += 64) {
-    uint64_t mk[N];
-    warp_segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
-    // active pairs found by each lane, processed one at a time by the whole warp
-    for (int base = 0; base < ns; base += 32) {
-      const int sidx = base + lane;
-      const bool mine = sidx < ns;
-      const int i = mine ? sidx / rb.nb : 0, k = mine ? sidx % rb.nb + 1 : 1;
-      // candidate spheres of the segments these 32 samples belong to (the same in every lane)
-      const int i_lo = base / rb.nb, i_hi = (base + 31 < ns ? base + 31 : ns - 1) / rb.nb;
-      uint64_t um = 0;
-#pragma unroll
-      for (int ii = 0; ii < N; ++ii)
-        if (ii >= i_lo && ii <= i_hi) um |= mk[ii];
-      if (!um) continue;
-      T q[3], wpt[3], s, c;
-      T sg = T(k) * inb;
-      if (mine) backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wpt, s, c);
-      for (uint64_t bits = um; bits; bits &= bits - 1) {
-        const int jsp = j0 + __ffsll((long long)bits) - 1;
-        bool act = false;
-        T dist = T(0), viol = T(0), dx = T(0), dy = T(0), dz = T(0);
-        if (mine) {
-          Sphere4<T> S = sph[jsp];
-          dx = wpt[0] - S.x; dy = wpt[1] - S.y; dz = wpt[2] - S.z;
-          T d2 = dx * dx + dy * dy + dz * dz;
-          if (d2 < S.reach * S.reach) {
-            act = true;
-            dist = c_sqrt(d2);
-            viol = S.reach - dist;
-            Fsplit += T(0.5) * w.rho_c * viol * viol;
-          }
-        }
-        if (!NORMAL) continue;
-        unsigned m = __ballot_sync(0xffffffffu, act);
-        while (m) {
-          const int src = __ffs(m) - 1;
-          m &= m - 1;
-          // the active lane's sample and normal, broadcast to the warp
-          const int si = __shfl_sync(0xffffffffu, i, src), sk = __shfl_sync(0xffffffffu, k, src);
-          T nx = __shfl_sync(0xffffffffu, dx / dist, src), ny = __shfl_sync(0xffffffffu, dy / dist, src),
-            nz = __shfl_sync(0xffffffffu, dz / dist, src);
-          T rr = w.sc * __shfl_sync(0xffffffffu, viol, src);
-          T px = __shfl_sync(0xffffffffu, wpt[0], src), py = __shfl_sync(0xffffffffu, wpt[1], src),
-            pz = __shfl_sync(0xffffffffu, wpt[2], src);
-          T nh[3] = {nx, ny, nz}, pw[3] = {px, py, pz};
-          T jr[D];
-#pragma unroll
-          for (int qq = 0; qq < D; ++qq) jr[qq] = T(0);
-          const T sgk = T(sk) * inb;
-#pragma unroll
-          for (int l = 0; l < N; ++l) {
-            if (l > si) break;
-            T ga[2];
-            if (l < si) {
-#pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                T wx[3];
-                cross(tw[l][kk], pw, wx);
-                ga[kk] = -w.sc * (nh[0] * (tv[l][kk][0] + wx[0]) + nh[1] * (tv[l][kk][1] + wx[1]) +
-                                  nh[2] * (tv[l][kk][2] + wx[2]));
-              }
-            } else {
-              T ss, cc, s3, cp;
-              seg_sc(sgk * sgk * ch.x[l], ss, cc);
-              seg_deriv(sgk * sgk * ch.x[l], ss, cc, s3, cp);
-              T dd[2][3], wl[2][3];
-              seg_local_derivs(sgk * ch.ax[l], sgk * ch.ay[l], ss, cc, s3, cp, sgk * rb.L[l], dd, wl);
-              T nl[3];
-              matTvec(ch.Rb[l], nh, nl);
-#pragma unroll
-              for (int kk = 0; kk < 2; ++kk)
-                ga[kk] = -w.sc * sgk * (nl[0] * dd[kk][0] + nl[1] * dd[kk][1] + nl[2] * dd[kk][2]);
-            }
-            bend_grad_to_u(rb.K[l], ga[0], ga[1], jr[3 * l], jr[3 * l + 1], jr[3 * l + 2]);
-          }
-          own_rank1<T, D>(lane, ow, sj, Aown, gown, jr, rr);
-        }
-      }
-    }
-    }
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) Fsplit += __shfl_xor_sync(0xffffffffu, Fsplit, off);
-  return __shfl_sync(0xffffffffu, Fonce, 0) + Fsplit;
 }
 
 template <typename T, int N, bool OBST>
 __global__ void __launch_bounds__(128) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathArgs<T> a) {
-  constexpr int D = 3 * N, DD = D * (D + 1) / 2;
+  constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * 4 + wid;
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw) + (size_t)wid * a.no;
-  T* sA = reinterpret_cast<T*>(smem_raw + ((size_t)4 * a.no * sizeof(Sphere4<T>) + 15) / 16 * 16) +
-          (size_t)wid * (DD + 3 * D + 2);
-  T* sg = sA + DD;
-  T* sd = sg + D;       // step [D], ok flag [D]
-  T* sj = sd + D + 2;   // row scratch [D]
-  const Owned ow = owned_entries<D>(lane);
+  unsigned char* mine = smem_raw + (size_t)wid * warm_warp_bytes<T>(a.no);
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(mine);
+  T* scratch = reinterpret_cast<T*>(mine + ((size_t)a.no * sizeof(Sphere4<T>) + 15) / 16 * 16);
   const bool live = p < a.P;
   if (OBST && live) {
     const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
@@ -289,164 +95,12 @@ __global__ void __launch_bounds__(128) k_path_warm(RobotK<T> rb, WeightsK<T> w, 
 #pragma unroll
   for (int q = 0; q < D; ++q) u[q] = T(a.u0[q * a.P + p]);
   if (lane < D) a.X[lane * PH + p * H] = T(a.u0[lane * a.P + p]);
-  for (int t = 1; t < H; ++t) {
-    TargetK<T> tg = load_target<T>(a.wp, PH, p * H + t, CR_TASK_IK6);
-    double lam = a.lambda0, nu = 2.0;
-    for (int it = 0; it < a.k_warm; ++it) {
-      T Aown[3], gown;
-      T F = warp_waypoint_eval<T, N, OBST, true>(rb, w, tg, sph, a.no, u, ow, sj, Aown, gown);
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-        if (lane + 32 * s < DD) sA[lane + 32 * s] = Aown[s];
-      if (lane < D) sg[lane] = gown;
-      __syncwarp();
-      // lane 0: damped Cholesky and solve (exploration: bulk precision); sd[D] = step, sd[D+1] = ok
-      if (lane == 0) {
-        T Am[DD], Dg[D], x[D], inv[D];
-#pragma unroll
-        for (int e = 0; e < DD; ++e) Am[e] = sA[e];
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          Dg[q] = c_max(Am[tri(q, q)], T(1e-12));
-          Am[tri(q, q)] += T(lam) * Dg[q];
-        }
-        bool ok = true;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          T s = Am[tri(j, j)];
-#pragma unroll
-          for (int k = 0; k < j; ++k) s -= Am[tri(j, k)] * Am[tri(j, k)];
-          ok = ok && (s > T(0));
-          s = s > T(0) ? s : T(1);
-          T iv = c_rsqrt(s);
-          inv[j] = iv;
-          Am[tri(j, j)] = s * iv;
-#pragma unroll
-          for (int i = j + 1; i < D; ++i) {
-            T t2 = Am[tri(i, j)];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t2 -= Am[tri(i, k)] * Am[tri(j, k)];
-            Am[tri(i, j)] = t2 * iv;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-          T s = -sg[i];
-#pragma unroll
-          for (int k = 0; k < i; ++k) s -= Am[tri(i, k)] * x[k];
-          x[i] = s * inv[i];
-        }
-#pragma unroll
-        for (int i = D - 1; i >= 0; --i) {
-          T s = x[i];
-#pragma unroll
-          for (int k = i + 1; k < D; ++k) s -= Am[tri(k, i)] * x[k];
-          x[i] = s * inv[i];
-        }
-        T pred = T(0);
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          sd[q] = x[q];
-          pred += x[q] * (T(lam) * Dg[q] * x[q] - sg[q]);
-        }
-        sA[0] = T(0.5) * pred;  // reuse: predicted reduction
-        sd[D] = ok ? T(1) : T(0);
-      }
-      __syncwarp();
-      const bool ok = sd[D] != T(0);
-      if (!ok) {
-        lam *= nu;
-        nu *= 2.0;
-        __syncwarp();
-        continue;
-      }
-      T un[D];
-#pragma unroll
-      for (int q = 0; q < D; ++q) un[q] = u[q] + sd[q];
-      const double pred = double(sA[0]);
-      __syncwarp();
-      T dummyA[3], dummyg;
-      T Fn = warp_waypoint_eval<T, N, OBST, false>(rb, w, tg, sph, a.no, un, ow, sj, dummyA, dummyg);
-      if (Fn < F) {
-        double rho = (double(F) - double(Fn)) / pred, tt = 2.0 * rho - 1.0;
-        lam *= fmax(1.0 / 3.0, 1.0 - tt * tt * tt);
-        nu = 2.0;
-#pragma unroll
-        for (int q = 0; q < D; ++q) u[q] = un[q];
-      } else {
-        lam *= nu;
-        nu *= 2.0;
-      }
-    }
-    if (lane < D) {
-#pragma unroll
-      for (int q = 0; q < D; ++q)
-        if (q == lane) a.X[q * PH + p * H + t] = u[q];
-    }
-  }
+  warm_sweep_warp<T, N, OBST>(rb, w, a.wp, PH, p * H, H, a.k_warm, T(a.lambda0), sph, a.no, u, scratch, a.X + p * H, PH);
 }
 
 // ------------------------------------------------------------------------------------------------
 // Refinement: joint LM over the path, FP64 block-tridiagonal elimination
 // ------------------------------------------------------------------------------------------------
-// Entries of the augmented (D+1)x(D+1) packed lower triangle [[S, b], [b^T, *]] owned by a lane of
-// the solving warp: e = lane + 32 s. Row D is the right-hand side; (D, D) is carried but unused.
-template <int D> struct AugSlots {
-  static constexpr int DA = (D + 1) * (D + 2) / 2;
-  static constexpr int SL = (DA + 31) / 32;
-  int r[SL], c[SL];
-  bool on[SL];
-};
-template <int D> __device__ AugSlots<D> aug_slots(int lane) {
-  AugSlots<D> o;
-#pragma unroll
-  for (int s = 0; s < AugSlots<D>::SL; ++s) {
-    const int e = lane + 32 * s;
-    o.on[s] = e < AugSlots<D>::DA;
-    int a = 0;
-    while (o.on[s] && (a + 1) * (a + 2) / 2 <= e) ++a;
-    o.r[s] = a;
-    o.c[s] = o.on[s] ? e - a * (a + 1) / 2 : 0;
-  }
-  return o;
-}
-// doubles of Z storage per block (the swept slots of one block, slot-major)
-template <int D> constexpr int aug_stride() { return AugSlots<D>::SL * 32; }
-
-// Symmetric sweep (Gauss-Jordan elimination without pivoting, valid for a positive definite S) of
-// pivots 0..D-1 of the augmented matrix held in the warp's slots. Pivot k maps d = S_kk to -1/d, the
-// rest of row and column k to S_ik / d and every other entry to S_ij - S_ik S_kj / d. Afterwards the
-// S block holds -S^-1 and row D holds (S^-1 b)^T. Returns false if a pivot is not positive. col and
-// colr are the warp's scratch of D + 1 doubles: column k, and column k scaled by 1/d.
-template <int D>
-__device__ bool sweep_aug(double (&v)[AugSlots<D>::SL], const AugSlots<D>& sl, double* col, double* colr) {
-  constexpr int SL = AugSlots<D>::SL;
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-#pragma unroll
-    for (int s = 0; s < SL; ++s)
-      if (sl.on[s] && (sl.r[s] == k || sl.c[s] == k)) col[sl.r[s] == k ? sl.c[s] : sl.r[s]] = v[s];
-    __syncwarp();
-    double d = col[k];
-    ok = ok && d > 0.0;
-    d = d > 0.0 ? d : 1.0;
-    const double ri = recip_nr(d);
-    if (lane <= D) colr[lane] = col[lane] * ri;
-    __syncwarp();
-#pragma unroll
-    for (int s = 0; s < SL; ++s) {
-      if (!sl.on[s]) continue;
-      const int i = sl.r[s], j = sl.c[s];
-      const double upd = fma(-colr[i], col[j], v[s]);
-      v[s] = (i == k) ? ((j == k) ? -ri : colr[j]) : ((j == k) ? colr[i] : upd);
-    }
-    __syncwarp();
-  }
-  return ok;
-}
-
 // The joint LM system is block tridiagonal: diagonal blocks M_t = J_t^T J_t + w_s nb_t I + lambda D_t
 // (nb_t = number of neighbours of waypoint t), off-diagonal blocks -w_s I, right-hand side r = -g.
 // Block elimination: S_0 = M_0, S_t = M_t - w_s^2 S_{t-1}^-1; z_t = S_t^-1 (r_t + w_s z_{t-1});
@@ -482,7 +136,7 @@ __device__ bool joint_solve_warp(const TA* Af, const double* g, double* z, doubl
       }
       v[s] = a;
     }
-    ok = sweep_aug<D>(v, sl, col, colr) && ok;
+    ok = sweep_aug<double, D>(v, sl, col, colr) && ok;
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       Zg[(size_t)t * ZS + s * 32 + lane] = v[s];
@@ -744,7 +398,7 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   PathArgs<T> a = path_args<T>(l);
   cr_status st;
   // exploration sweep
-  size_t smw = (((size_t)4 * a.no * sizeof(Sphere4<T>) + 15) / 16 * 16) + (size_t)4 * (DD + 3 * D + 2) * sizeof(T);
+  size_t smw = 4 * warm_warp_bytes<T>(a.no);
   unsigned gw = (unsigned)((a.P + 3) / 4);
   if (a.no > 0) {
     if ((st = set_smem(k_path_warm<T, N, true>, smw))) return st;
