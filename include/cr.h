@@ -379,6 +379,92 @@ CR_API const char* cr_last_error_string(void);
 CR_API cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32_t iters, double* ops_out,
                          cr_stream stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Ragged batch (serving-shaped): IK and path-following problems of mixed segment count, waypoint
+ * count, seed count and obstacle count in one CUDA-graph launch of persistent kernels over a work
+ * queue. The paper runs each problem on its own (Algorithm 1, Sec. IV); the batching is the GPU
+ * form of running many of them at once.
+ *
+ * Item i (caller's order) uses the first n_i segments of `family`, waypoints
+ * targets[:, w_i .. w_i + H_i - 1] (w_i = sum_{j<i} H_j, targets a device [7][W] FP64 array as in
+ * cr_path_task, W = sum H) and spheres[o_i .. o_i + n_o_i - 1] (o_i = sum_{j<i} n_o_j, a device
+ * [*][4] FP64 array). An IK item (H = 1) is Algorithm 1 on its target with S_i seeds; a path item is
+ * the path pipeline of cr_solve_path (first-waypoint IK with S_i seeds, exploration sweep of k_warm
+ * LM iterations per waypoint, k_joint joint LM iterations). Outputs (device): u_out item-packed,
+ * item i's block [3 n_i][H_i] (component-major) starting at sum_{j<i} 3 n_j H_j; cost_out [N];
+ * pos_err, rot_err [W] (FP64 acceptance per waypoint); flags_out [N]: bit 0 success (every waypoint
+ * within pos_tol / rot_tol, limits and clearance), bit 1 limits met, bit 2 collision-free;
+ * t_done_ns [N]: completion time of the item after the batch start (%globaltimer, ns).
+ * ------------------------------------------------------------------------------------------- */
+#define CR_ITEM_IK 0
+#define CR_ITEM_PATH 1
+#define CR_BATCH_MAX_SPHERES 64
+#define CR_BATCH_MAX_H 128
+
+typedef struct {
+  int32_t kind; /* CR_ITEM_IK (H must be 1) or CR_ITEM_PATH */
+  int32_t n;    /* segments, 1..CR_MAX_SEG */
+  int32_t H;    /* waypoints, 1..CR_BATCH_MAX_H */
+  int32_t S;    /* seeds of the (first-waypoint) IK, 1..CR_MAX_SEEDS */
+  int32_t n_o;  /* spheres, 0..CR_BATCH_MAX_SPHERES */
+  int32_t reserved;
+} cr_batch_item;
+
+typedef struct {
+  cr_ik_params ik;        /* n_final, k_init, k_final, lambda0, alpha0, dedup_eps, lim_tol, pos_tol,
+                             rot_tol, seed, p0 (item i draws seeds as problem p0 + i); S and
+                             precision are ignored (per item; FP32 bulk, FP64 solves) */
+  int32_t k_warm, k_joint;
+  int32_t seeds_per_unit; /* seeds one warp takes per work unit: 32, 64, 128 or 256; 0: chosen by
+                             timing the candidates in cr_batch_plan_create */
+  int32_t reserved;
+} cr_batch_params;
+
+typedef struct cr_batch_plan cr_batch_plan;
+
+/* Workspace bytes for the batch (also covers every seeds_per_unit candidate); 0 on bad input. */
+CR_API size_t cr_batch_workspace_size(const cr_robot* family, const cr_batch_item* items, int64_t N,
+                                      const cr_batch_params* prm);
+
+/* Validates the batch, builds the work queue (longest estimated item first) in `workspace`
+ * (caller-owned device memory, >= cr_batch_workspace_size bytes, 256-byte aligned), captures the
+ * CUDA graph (start node + one persistent kernel per segment count present, as parallel branches)
+ * and returns the plan (host object). With seeds_per_unit = 0 every candidate is run and timed on
+ * `stream` (the outputs then hold a valid result). Synchronises `stream`. All pointers stay bound
+ * to the plan: cr_batch_plan_run re-solves the batch from the current contents of targets and
+ * spheres. CR_EINVAL for a bad item (kind, n, H, S, n_o out of range, IK with H != 1), NULL or
+ * misaligned pointers, or a short workspace. */
+CR_API cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* w, const cr_batch_item* items,
+                                      int64_t N, const cr_batch_params* prm, const double* targets,
+                                      const double* spheres, double* u_out, double* cost_out, double* pos_err,
+                                      double* rot_err, uint8_t* flags_out, uint64_t* t_done_ns, void* workspace,
+                                      size_t ws_bytes, cr_stream stream, cr_batch_plan** plan);
+/* One graph launch on `stream` (asynchronous). Two runs of one plan must not overlap. */
+CR_API cr_status cr_batch_plan_run(cr_batch_plan* plan, cr_stream stream);
+/* The plan's seeds per unit, number of work units and resident worker warps (host pointers, each
+ * may be NULL). */
+CR_API cr_status cr_batch_plan_info(const cr_batch_plan* plan, int32_t* seeds_per_unit, int64_t* units,
+                                    int64_t* workers);
+/* Frees the plan (graph, streams, events); the caller makes sure no run is in flight. */
+CR_API cr_status cr_batch_plan_destroy(cr_batch_plan* plan);
+/* Plan, run, synchronise and free in one call (seeds_per_unit 0 takes 64, without timing). */
+CR_API cr_status cr_solve_batch(const cr_robot* family, const cr_weights* w, const cr_batch_item* items, int64_t N,
+                                const cr_batch_params* prm, const double* targets, const double* spheres,
+                                double* u_out, double* cost_out, double* pos_err, double* rot_err,
+                                uint8_t* flags_out, uint64_t* t_done_ns, void* workspace, size_t ws_bytes,
+                                cr_stream stream);
+
+/* The plain form of the same batch, for comparison: one cr_solve_ik / cr_solve_path call per item
+ * (P = 1) in the caller's order on `stream`, each followed by a completion stamp. Same outputs,
+ * except that flags_out bits 1 and 2 are set for path items only. Workspace: */
+CR_API size_t cr_batch_plain_workspace_size(const cr_robot* family, const cr_batch_item* items, int64_t N,
+                                            const cr_batch_params* prm);
+CR_API cr_status cr_solve_batch_plain(const cr_robot* family, const cr_weights* w, const cr_batch_item* items,
+                                      int64_t N, const cr_batch_params* prm, const double* targets,
+                                      const double* spheres, double* u_out, double* cost_out, double* pos_err,
+                                      double* rot_err, uint8_t* flags_out, uint64_t* t_done_ns, void* workspace,
+                                      size_t ws_bytes, cr_stream stream);
+
 /* Elementwise run of a device helper the solvers rely on, for checking it against CUDA's own
  * operations (the paper has no counterpart; this is numerics verification). which:
  * CR_CHECK_RECIP: out[i] = FP64 reciprocal of in[i] as the block solves of cr_solve_path compute it

@@ -344,3 +344,93 @@ class PathSolver:
         lib.cr_solve_path(self.robot, self.scene.c, self._task, self.prm, self.k_warm, self.k_joint, self.X, self.cost,
                           self.pos, self.rot, self.lim_ok, self.col_ok, self.workspace)
         return self
+
+
+# ------------------------------------------------------------------------------------------------
+# Ragged batch
+# ------------------------------------------------------------------------------------------------
+class BatchSolver:
+    """A ragged batch of items (kind, n, H, S, n_o) -- IK (H = 1) or path -- solved by one CUDA-graph
+    launch of persistent kernels. Inputs stay resident: targets [7][W] and spheres [sum n_o][4] on the
+    device; ``plan()`` builds the queue and graph once, ``run()`` re-solves from the current inputs."""
+
+    def __init__(self, family: synth.RobotSpec, items, ik: synth.IkSpec, weights: synth.WeightSpec,
+                 k_warm: int = synth.K_WARM, k_joint: int = synth.K_JOINT, seeds_per_unit: int = 0,
+                 device="cuda"):
+        import numpy as np
+
+        self.family = robot_struct(family)
+        self.weights = weights_struct(weights)
+        self.items_np = np.asarray(items, dtype=np.int64).reshape(-1, 5)
+        self.items = lib._batch_items(self.items_np)
+        self.prm = lib.cr_batch_params()
+        self.prm.ik = ik_params_struct(ik, lib.CR_F32)
+        self.prm.k_warm, self.prm.k_joint, self.prm.seeds_per_unit = k_warm, k_joint, seeds_per_unit
+        it = self.items_np
+        self.N = len(it)
+        self.W = int(it[:, 2].sum())
+        self.n_sph = int(it[:, 4].sum())
+        self.n_states = int((3 * it[:, 1] * it[:, 2]).sum())
+        self.device = device
+        z = lambda n, dt=torch.float64: torch.empty(max(n, 1), dtype=dt, device=device)
+        self.targets = torch.zeros((7, self.W), dtype=torch.float64, device=device)
+        self.spheres = torch.zeros((max(self.n_sph, 1), 4), dtype=torch.float64, device=device)
+        self.u, self.cost, self.pos, self.rot = z(self.n_states), z(self.N), z(self.W), z(self.W)
+        self.flags, self.t_done = z(self.N, torch.uint8), z(self.N, torch.int64)
+        self.workspace = torch.empty(lib.cr_batch_workspace_size(self.family, self.items, self.prm),
+                                     dtype=torch.uint8, device=device)
+        self._plan = None
+
+    def set_inputs(self, targets, spheres):
+        """targets [W][7] (position + quaternion per waypoint, items in order), spheres [sum n_o][4]."""
+        self.targets.copy_(torch.as_tensor(targets, dtype=torch.float64).T)
+        if self.n_sph:
+            self.spheres[: self.n_sph].copy_(torch.as_tensor(spheres, dtype=torch.float64))
+
+    def plan(self):
+        if self._plan is not None:
+            lib.cr_batch_plan_destroy(self._plan)
+        self._plan = lib.cr_batch_plan_create(self.family, self.weights, self.items, self.prm, self.targets,
+                                              self.spheres, self.u, self.cost, self.pos, self.rot, self.flags,
+                                              self.t_done, self.workspace)
+        return lib.cr_batch_plan_info(self._plan)
+
+    def run(self):
+        if self._plan is None:
+            self.plan()
+        lib.cr_batch_plan_run(self._plan)
+        return self
+
+    def solve_plain(self):
+        """The plain per-problem form into fresh outputs: dict of u, cost, pos, rot, flags, t_done."""
+        out = {k: torch.empty_like(v) for k, v in
+               dict(u=self.u, cost=self.cost, pos=self.pos, rot=self.rot, flags=self.flags, t_done=self.t_done).items()}
+        ws = torch.empty(lib.cr_batch_plain_workspace_size(self.family, self.items, self.prm), dtype=torch.uint8,
+                         device=self.device)
+        lib.cr_solve_batch_plain(self.family, self.weights, self.items, self.prm, self.targets, self.spheres,
+                                 out["u"], out["cost"], out["pos"], out["rot"], out["flags"], out["t_done"], ws)
+        return out
+
+    def item_states(self, i: int, u=None):
+        """[H][3n] states of item i from an item-packed output (default: the batch result)."""
+        u = self.u if u is None else u
+        it = self.items_np
+        off = int((3 * it[:i, 1] * it[:i, 2]).sum())
+        d, H = 3 * int(it[i, 1]), int(it[i, 2])
+        return u[off:off + d * H].reshape(d, H).T
+
+    def __del__(self):
+        try:
+            if self._plan is not None:
+                lib.cr_batch_plan_destroy(self._plan)
+        except Exception:
+            pass
+
+
+def family_fk_backbone(family: synth.RobotSpec, device="cuda"):
+    """fk_backbone_n(n, U [M][3n]) for ragged_workload: FK of the family's first n segments."""
+    def f(n, U):
+        spec = dataclasses.replace(family, L=family.L[:n])
+        T, bb = fk(robot_struct(spec), torch.as_tensor(U.T.copy(), dtype=torch.float64, device=device), True)
+        return T.cpu().numpy().T, bb.cpu().numpy().transpose(2, 0, 1)
+    return f

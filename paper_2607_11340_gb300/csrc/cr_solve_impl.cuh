@@ -118,7 +118,13 @@ CR_HD bool key_less(float c1, float l1, int i1, float c2, float l2, int i2) {
 // A candidate ranked below w meets w (already kept) when its turn comes in the sequential rule, so
 // the kept set and order are those of the sequential rule, with at most K rounds. If fewer than K
 // survive, the marked candidates fill the rest in rank order. taken: 0 available, 1 kept, 2 marked.
-template <typename T>
+// Loads that bypass L1 (ld.global.cg) for candidates written by other SMs in the same launch.
+template <bool CG, typename V> __device__ __forceinline__ V cand_ld(const V* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
+template <typename T, bool CG = false>
 __device__ void warp_topk(const float* cost, const float* coll, const T* u, int64_t ustride, int D, int S,
                           int K, T eps, int* sel, unsigned char* taken, int* /*unused*/) {
   const unsigned FULL = 0xffffffffu;
@@ -133,7 +139,7 @@ __device__ void warp_topk(const float* cost, const float* coll, const T* u, int6
       int bi = INT_MAX;
       for (int i = lane; i < S; i += 32) {
         if (taken[i] != want) continue;
-        float c = cost[i], l = coll[i];
+        float c = cand_ld<CG>(cost + i), l = cand_ld<CG>(coll + i);
         c = isfinite(c) ? c : INFINITY;
         l = isfinite(l) ? l : INFINITY;
         if (key_less(c, l, i, bc, bl, bi)) { bc = c; bl = l; bi = i; }
@@ -153,7 +159,8 @@ __device__ void warp_topk(const float* cost, const float* coll, const T* u, int6
         for (int i = lane; i < S; i += 32) {
           if (taken[i] != 0) continue;
           T m = T(0);
-          for (int q = 0; q < D; ++q) m = c_max(m, c_fabs(u[q * ustride + i] - u[q * ustride + bi]));
+          for (int q = 0; q < D; ++q)
+            m = c_max(m, c_fabs(cand_ld<CG>(u + q * ustride + i) - cand_ld<CG>(u + q * ustride + bi)));
           if (m < eps) taken[i] = 2;
         }
         __syncwarp();

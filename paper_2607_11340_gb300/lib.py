@@ -27,7 +27,9 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_solve_ik_plain",
            "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
            "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
-           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check")
+           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check",
+           "cr_batch_workspace_size", "cr_batch_plan_create", "cr_batch_plan_run", "cr_batch_plan_info",
+           "cr_batch_plan_destroy", "cr_solve_batch", "cr_batch_plain_workspace_size", "cr_solve_batch_plain")
 
 
 class CrError(RuntimeError):
@@ -75,6 +77,20 @@ class cr_ik_params(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+CR_ITEM_IK, CR_ITEM_PATH = 0, 1
+CR_BATCH_MAX_SPHERES, CR_BATCH_MAX_H = 64, 128
+
+
+class cr_batch_item(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("H", C.c_int32), ("S", C.c_int32), ("n_o", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class cr_batch_params(C.Structure):
+    _fields_ = [("ik", cr_ik_params), ("k_warm", C.c_int32), ("k_joint", C.c_int32),
+                ("seeds_per_unit", C.c_int32), ("reserved", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -113,6 +129,16 @@ _SIGS = {
                     C.c_int32, _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
     "cr_device_check": [C.c_int32, _P, _P, C.c_int64, _P],
+    "cr_batch_plan_create": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
+                             C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P,
+                             C.POINTER(C.c_void_p)],
+    "cr_batch_plan_run": [_P, _P],
+    "cr_batch_plan_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "cr_batch_plan_destroy": [_P],
+    "cr_solve_batch": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
+                       C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_solve_batch_plain": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
+                             C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
 }
 
 
@@ -136,6 +162,10 @@ def load(path: str | None = None):
         L.cr_traj_workspace_size.restype = C.c_size_t
         L.cr_path_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.c_int32, C.POINTER(cr_ik_params)]
         L.cr_path_workspace_size.restype = C.c_size_t
+        for nm in ("cr_batch_workspace_size", "cr_batch_plain_workspace_size"):
+            getattr(L, nm).argtypes = [C.POINTER(cr_robot), C.POINTER(cr_batch_item), C.c_int64,
+                                       C.POINTER(cr_batch_params)]
+            getattr(L, nm).restype = C.c_size_t
         L.cr_static_workspace_capacity.argtypes = []
         L.cr_static_workspace_capacity.restype = C.c_size_t
         L.cr_last_error_string.argtypes = []
@@ -322,3 +352,59 @@ def cr_peak_launch(kind: int, buf, iters: int, stream=None) -> float:
     _check(load().cr_peak_launch(kind, _ptr(buf), buf.numel() * buf.element_size(), iters, C.byref(ops),
                                  _stream(stream)))
     return ops.value
+
+
+def _batch_items(items):
+    """(N, 6) int array or a list of (kind, n, H, S, n_o) -> ctypes array of cr_batch_item."""
+    arr = (cr_batch_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = cr_batch_item(int(it[0]), int(it[1]), int(it[2]), int(it[3]), int(it[4]), 0)
+    return arr
+
+
+def cr_batch_workspace_size(robot, items, prm) -> int:
+    return load().cr_batch_workspace_size(C.byref(robot), items, len(items), C.byref(prm))
+
+
+def cr_batch_plain_workspace_size(robot, items, prm) -> int:
+    return load().cr_batch_plain_workspace_size(C.byref(robot), items, len(items), C.byref(prm))
+
+
+def cr_batch_plan_create(robot, weights, items, prm, targets, spheres, u_out, cost, pos, rot, flags, t_done,
+                         workspace, stream=None):
+    plan = C.c_void_p()
+    _check(load().cr_batch_plan_create(C.byref(robot), C.byref(weights), items, len(items), C.byref(prm),
+                                       _ptr(targets), _ptr(spheres), _ptr(u_out), _ptr(cost), _ptr(pos), _ptr(rot),
+                                       _ptr(flags), _ptr(t_done), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _stream(stream), C.byref(plan)))
+    return plan
+
+
+def cr_batch_plan_run(plan, stream=None):
+    _check(load().cr_batch_plan_run(plan, _stream(stream)))
+
+
+def cr_batch_plan_info(plan):
+    spu, units, workers = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(load().cr_batch_plan_info(plan, C.byref(spu), C.byref(units), C.byref(workers)))
+    return spu.value, units.value, workers.value
+
+
+def cr_batch_plan_destroy(plan):
+    _check(load().cr_batch_plan_destroy(plan))
+
+
+def cr_solve_batch(robot, weights, items, prm, targets, spheres, u_out, cost, pos, rot, flags, t_done, workspace,
+                   stream=None):
+    _check(load().cr_solve_batch(C.byref(robot), C.byref(weights), items, len(items), C.byref(prm), _ptr(targets),
+                                 _ptr(spheres), _ptr(u_out), _ptr(cost), _ptr(pos), _ptr(rot), _ptr(flags),
+                                 _ptr(t_done), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                 _stream(stream)))
+
+
+def cr_solve_batch_plain(robot, weights, items, prm, targets, spheres, u_out, cost, pos, rot, flags, t_done,
+                         workspace, stream=None):
+    _check(load().cr_solve_batch_plain(C.byref(robot), C.byref(weights), items, len(items), C.byref(prm),
+                                       _ptr(targets), _ptr(spheres), _ptr(u_out), _ptr(cost), _ptr(pos), _ptr(rot),
+                                       _ptr(flags), _ptr(t_done), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)))

@@ -271,3 +271,83 @@ def calib_workload(robot: RobotSpec, K: int, fk_with_params, seed: int = 0, sigm
     T = np.asarray(fk_with_params(U, true[:robot.n], true[robot.n:]))
     Pm = T[:, 9:12] + rng.normal(0.0, sigma, (K, 3))
     return U, Pm, true, nominal
+
+
+# Ragged serving batch: 16384 items, each an IK (H = 1) or a path with probability 1/2; segment count
+# U{1..6}, waypoints U{1..128} (paths), seeds U{16..256}, spheres U{0..64}; every segment of the
+# family is L = 0.10 m, r_c = 5 mm, |u| <= 10 mm.
+ROBOT_FAMILY = RobotSpec(L=(0.10,) * 6, rc=0.005, umax=0.010, nb=16)
+N_RAGGED = 16384
+IK_RAGGED = IkSpec(S=0, n_final=8, k_init=64, k_final=30)  # S per item
+
+
+def ragged_items(rng: np.random.Generator, N: int) -> np.ndarray:
+    """[N][5] int: (kind 0 IK / 1 path, n, H, S, n_o) drawn from the distributions above."""
+    kind = rng.integers(0, 2, N)
+    n = rng.integers(1, 7, N)
+    H = np.where(kind == 1, rng.integers(1, 129, N), 1)
+    S = rng.integers(16, 257, N)
+    no = rng.integers(0, 65, N)
+    return np.stack([kind, n, H, S, no], axis=1).astype(np.int64)
+
+
+def spheres_clear_fast(rng: np.random.Generator, count: int, points: np.ndarray, margin_box: float, r_lo: float,
+                       r_hi: float, clearance: float) -> np.ndarray:
+    """As spheres_clear_of (same distribution: centres uniform in the dilated bounding box, radii
+    uniform, rejected while closer than ``clearance`` to a point), drawing candidates in blocks and
+    testing them against a k-d tree of the points."""
+    from scipy.spatial import cKDTree
+
+    if count == 0:
+        return np.zeros((0, 4))
+    lo, hi = points.min(axis=0) - margin_box, points.max(axis=0) + margin_box
+    tree = cKDTree(points)
+    out = []
+    for _ in range(1000):
+        c = rng.uniform(lo, hi, (4 * count, 3))
+        r = rng.uniform(r_lo, r_hi, 4 * count)
+        d, _ = tree.query(c)
+        ok = d >= r + clearance
+        out.extend(np.concatenate([c[ok], r[ok, None]], axis=1))
+        if len(out) >= count:
+            return np.array(out[:count])
+    raise RuntimeError("could not place the spheres")
+
+
+def ragged_workload(N: int, fk_backbone_n, seed: int = 0, items: np.ndarray | None = None,
+                    robot: RobotSpec = ROBOT_FAMILY, weights: WeightSpec = WEIGHTS):
+    """Items [N][5], targets [W][7] (W = sum H; item i's waypoints follow those of item i - 1),
+    spheres [sum n_o][4] (item-packed) and the ground-truth states (list of [H][3n] arrays). IK
+    targets are FK poses of hexagon-uniform states, path waypoints FK poses along a Bezier curve in
+    u-space; an item's spheres are clear of its ground-truth backbone by r_body + delta.
+    ``fk_backbone_n(n, u [M][3n]) -> (T [M][12], backbone [M][n*nb][3])``."""
+    rng = np.random.default_rng(seed)
+    if items is None:
+        items = ragged_items(rng, N)
+    N = len(items)
+    states = [None] * N
+    for i, (kind, n, H, S, no) in enumerate(items):
+        states[i] = (bezier_states(rng, 1, int(H), int(n), robot.umax)[0] if kind == 1
+                     else hexagon_states(rng, 1, int(n), robot.umax))
+    Hs = items[:, 2]
+    woff = np.concatenate([[0], np.cumsum(Hs)])
+    targets = np.zeros((int(woff[-1]), 7))
+    backbones = [None] * N
+    for n in range(1, 7):
+        idx = np.nonzero(items[:, 1] == n)[0]
+        if len(idx) == 0:
+            continue
+        U = np.concatenate([states[i] for i in idx])
+        T, bb = fk_backbone_n(n, U)
+        T, bb = np.asarray(T), np.asarray(bb)
+        poses = pose_targets(T, "pose")
+        o = 0
+        for i in idx:
+            h = int(Hs[i])
+            targets[woff[i]:woff[i] + h] = poses[o:o + h]
+            backbones[i] = bb[o:o + h].reshape(-1, 3)
+            o += h
+    clear = robot.body_radius + weights.delta
+    sph = [spheres_clear_fast(rng, int(items[i, 4]), backbones[i], 0.02, 0.005, 0.015, clear) for i in range(N)]
+    spheres = np.concatenate(sph) if sum(len(s) for s in sph) else np.zeros((0, 4))
+    return items, targets, spheres, states

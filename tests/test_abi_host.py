@@ -116,3 +116,33 @@ def test_invalid_arguments_are_rejected(crlib):
     p.n_final, p.S = 8, 300
     assert L.cr_solve_ik(C.byref(r), None, C.byref(t), C.byref(p), *outs, dummy, dummy, ws, None) \
         == crlib.CR_EINVAL
+
+
+def test_batch_items_are_validated(crlib):
+    """Ragged batch: every out-of-range item field, a bad seeds_per_unit and an IK item with H != 1
+    are rejected before any device call; the struct layout matches the header."""
+    L = crlib.load()
+    r = _robot(crlib, n=6)
+    w = crlib.cr_weights()
+    p = crlib.cr_batch_params()
+    p.ik.n_final, p.ik.k_init, p.ik.k_final, p.ik.lambda0 = 8, 16, 10, 1e-3
+    p.k_warm, p.k_joint, p.seeds_per_unit = 5, 5, 64
+    dummy = C.c_void_p(256)
+    good = [(0, 3, 1, 64, 4), (1, 6, 128, 256, 64)]
+    bad = [(2, 3, 1, 64, 0), (0, 0, 1, 64, 0), (0, 7, 1, 64, 0), (0, 3, 2, 64, 0), (1, 3, 129, 64, 0),
+           (1, 3, 0, 64, 0), (0, 3, 1, 0, 0), (0, 3, 1, 257, 0), (0, 3, 1, 64, 65), (0, 3, 1, 64, -1)]
+    outs = [dummy] * 8
+    for it in bad:
+        items = crlib._batch_items(good + [it])
+        assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 3, C.byref(p), *outs, dummy, 1 << 30, None) \
+            == crlib.CR_EINVAL, it
+        assert crlib.cr_batch_workspace_size(r, items, p) == 0
+        assert L.cr_solve_batch_plain(C.byref(r), C.byref(w), items, 3, C.byref(p), *outs, dummy, 1 << 30, None) \
+            == crlib.CR_EINVAL, it
+    items = crlib._batch_items(good)
+    p.seeds_per_unit = 48
+    assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 2, C.byref(p), *outs, dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL
+    assert "seeds_per_unit" in crlib.last_error()
+    assert C.sizeof(crlib.cr_batch_item) == 24
+    assert crlib.cr_batch_params.k_warm.offset == C.sizeof(crlib.cr_ik_params)
