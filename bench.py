@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
-    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib"],
+    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib", "ragged"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
@@ -268,6 +268,53 @@ def other_workload(args):
         extra = lambda: {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
                          "collision_free_rate": float(s.col_ok.float().mean()),
                          "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+        dtype = "f32"
+    elif args.workload == "ragged":
+        fam = synth.ROBOT_FAMILY
+        items, targets, spheres, _ = synth.ragged_workload(synth.N_RAGGED, api.family_fk_backbone(fam, dev), seed=0)
+        s = api.BatchSolver(fam, items, synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=0, device=dev)
+        s.set_inputs(targets, spheres)
+        spu, n_units, workers = s.plan()
+        fn = lambda: s.run()
+        units, unit = len(items), "problems/s"
+        metric = "ragged batch problems/s (16384 mixed IK / path items, one graph launch)"
+        wl = "ragged_16384_items_n1-6_H1-128_S16-256_no0-64"
+        W = int(items[:, 2].sum())
+
+        def lat(t_ns):
+            t = np.asarray(t_ns, dtype=np.float64) / 1e6
+            return {"p50_ms": float(np.percentile(t, 50)), "p99_ms": float(np.percentile(t, 99)),
+                    "max_ms": float(t.max())}
+
+        def subset(nsub=256):
+            """The plain per-problem form against the batch on the first nsub items, same order."""
+            sub = api.BatchSolver(fam, items[:nsub], synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=spu, device=dev)
+            sub.set_inputs(targets[: int(items[:nsub, 2].sum())], spheres[: int(items[:nsub, 4].sum())])
+            sub.plan()
+            sub.run()
+            torch.cuda.synchronize()
+            out = {}
+            for name, run in (("batch", lambda: sub.run()), ("plain", lambda: sub.solve_plain())):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                r = run()
+                b.record()
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                t_ns = (sub.t_done if name == "batch" else r["t_done"]).cpu().numpy()
+                fl = (sub.flags if name == "batch" else r["flags"]).cpu().numpy()
+                out[name] = {"items": nsub, "problems_per_s": nsub / (ms / 1e3), "ms": ms,
+                             "success_rate": float((fl & 1).mean()), **lat(t_ns)}
+            return out
+
+        def extra():
+            t_ns = s.t_done.cpu().numpy()
+            fl = s.flags.cpu().numpy()
+            return {"waypoint_solves_per_s": W / (line["ms_per_step"] / 1e3), "latency": lat(t_ns),
+                    "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu, "work_units": n_units,
+                    "worker_warps": workers, "items_ik": int((items[:, 0] == 0).sum()),
+                    "items_path": int((items[:, 0] == 1).sum()), "waypoints": W, "vs_plain_subset": subset()}
+
         dtype = "f32"
     else:
         spec = synth.ROBOT_3SEG

@@ -469,9 +469,12 @@ CR_API cr_status cr_solve_batch_plain(const cr_robot* family, const cr_weights* 
  * operations (the paper has no counterpart; this is numerics verification). which:
  * CR_CHECK_RECIP: out[i] = FP64 reciprocal of in[i] as the block solves of cr_solve_path compute it
  * (Newton-Raphson from the single-precision approximation; within a few ulp of 1/in[i]).
+ * CR_CHECK_SIN, CR_CHECK_COS: out[i] = sin(in[i]), cos(in[i]) as the FP64 kinematics compute them.
  * in, out: device arrays of n doubles (8-byte aligned). Asynchronous on `stream`; CR_EINVAL for a
  * NULL or misaligned pointer, n < 0 or an unknown helper. */
 #define CR_CHECK_RECIP 0
+#define CR_CHECK_SIN 1
+#define CR_CHECK_COS 2
 CR_API cr_status cr_device_check(int32_t which, const double* in, double* out, int64_t n, cr_stream stream);
 
 #ifdef __cplusplus

@@ -60,10 +60,10 @@ namespace {
 
 constexpr int kSpuCandidates[] = {32, 64, 128, 256};
 
-size_t batch_smem() { return (size_t)crk::kBatchWarps * crk::kBatchWarpSmem; }
+size_t batch_smem(int) { return (size_t)crk::kBatchWarps * crk::kBatchWarpSmem; }
 
 int blocks_per_sm(int n) {
-  const size_t sm = batch_smem();
+  const size_t sm = batch_smem(n);
   switch (n) {
     case 1: return crk::batch_blocks_per_sm<1>(sm);
     case 2: return crk::batch_blocks_per_sm<2>(sm);
@@ -75,7 +75,7 @@ int blocks_per_sm(int n) {
 }
 
 cr_status prepare(int n) {
-  const size_t sm = batch_smem();
+  const size_t sm = batch_smem(n);
   switch (n) {
     case 1: return crk::batch_prepare<1>(sm);
     case 2: return crk::batch_prepare<2>(sm);
@@ -87,7 +87,7 @@ cr_status prepare(int n) {
 }
 
 cr_status launch(int n, const cr_robot& fam, const cr_weights& w, const crk::BatchArgs& a, int grid, cudaStream_t s) {
-  const size_t sm = batch_smem();
+  const size_t sm = batch_smem(n);
   switch (n) {
     case 1: return crk::batch_launch<1>(fam, w, a, grid, sm, s);
     case 2: return crk::batch_launch<2>(fam, w, a, grid, sm, s);

@@ -143,10 +143,11 @@ __device__ double joint_lm_warp(const RobotK<float>& rb, const WeightsK<float>& 
     float* Xn = cur ? X0 : X1;
     double Fl = 0.0;
     for (int t = lane; t < H; t += 32) {
-      float u[D], At[DD], gt[D];
+      float u[D], gt[D];
 #pragma unroll
       for (int q = 0; q < D; ++q) u[q] = Xc[q * H + t];
       const TargetK<float> tg = load_target<float>(targets, W, wp0 + t, CR_TASK_IK6);
+      float At[DD];
       Fl += double(eval_ik_normal<float, float, N, true>(rb, w, CR_TASK_IK6, tg, sph, no, u, At, gt));
 #pragma unroll
       for (int e = 0; e < DD; ++e) Af[(size_t)t * DD + e] = At[e];
@@ -232,20 +233,21 @@ __device__ void batch_finish(const RobotK<float>& rb, const WeightsK<float>& w, 
   double ud[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) ud[q] = NAN;
+  const TargetK<float> tg = load_target<float>(a.targets, a.W, it.wp, CR_TASK_IK6);
+  const TargetK<double> tgd = load_target<double>(a.targets, a.W, it.wp, CR_TASK_IK6);
+  // lane k refines candidate sel[k]: k_final LM iterations, FP64 Cholesky in registers
   const int j = lane < K ? sel[lane] : -1;
   if (j >= 0) {
     float uu[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) uu[q] = __ldcg(cu + q * S + j);
     if (c_finite(uu[0])) {
-      const TargetK<float> tg = load_target<float>(a.targets, a.W, it.wp, CR_TASK_IK6);
       double lam = a.lambda0, nu = 2.0;
       float Fi;
       for (int itn = 0; itn < a.k_final; ++itn)
         lm_iteration<float, N, true>(rb, w, CR_TASK_IK6, tg, sph, it.no, uu, lam, nu, Fi);
 #pragma unroll
       for (int q = 0; q < D; ++q) ud[q] = double(uu[q]);
-      const TargetK<double> tgd = load_target<double>(a.targets, a.W, it.wp, CR_TASK_IK6);
       Fk = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, it.no, ud, a.lim_tol, pos, rot, fl);
     }
   }
@@ -327,7 +329,7 @@ __device__ void batch_finish(const RobotK<float>& rb, const WeightsK<float>& w, 
 }
 
 template <int N>
-__global__ void __launch_bounds__(128) k_batch(RobotK<float> rb, WeightsK<float> w, RobotK<double> rbd,
+__global__ void __maxnreg__(255) k_batch(RobotK<float> rb, WeightsK<float> w, RobotK<double> rbd,
                                                 WeightsK<double> wd, BatchArgs a) {
   constexpr int D = 3 * N;
   const unsigned FULL = 0xffffffffu;

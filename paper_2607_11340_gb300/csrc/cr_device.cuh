@@ -41,7 +41,10 @@ template <> struct Prec<double> {
 
 CR_HD float c_sqrt(float x) { return sqrtf(x); }
 CR_HD double c_sqrt(double x) { return sqrt(x); }
-CR_HD void c_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+// FP32 sin and cos through sincospif: its reduction modulo 2 is exact, so no large-argument
+// reduction subroutine is called (such a call caps the register allocation of the whole kernel).
+CR_HD void c_sincos(float x, float* s, float* c) { sincospif(x * 0.31830988618379067f, s, c); }
+// FP64: the library sincos (the FP64 results follow the oracle's decisions to the last bits).
 CR_HD void c_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 CR_HD float c_atan2(float y, float x) { return atan2f(y, x); }
 CR_HD double c_atan2(double y, double x) { return atan2(y, x); }
@@ -453,6 +456,31 @@ CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, cons
   }
 }
 
+// Second level: the samples k0..k1 of segment i (arc fractions k / n_b) lie within
+// (k1 - k0) L_i / (2 n_b) of the point at fraction (k0 + k1) / (2 n_b); of the candidates `cand`
+// (bits relative to j0) those within that radius + reach of it, with the same rounding margin.
+constexpr int kCullGroup = 4;  // backbone samples per second-level ball
+template <typename T, int N>
+CR_HD uint64_t group_sphere_mask(const RobotK<T>& rb, const Chain<T, N>& ch, int i, int k0, int k1,
+                                 const Sphere4<T>* sph, int j0, uint64_t cand) {
+  T lsum = T(0);
+#pragma unroll
+  for (int l = 0; l < N; ++l) lsum += rb.L[l];
+  const T inb = c_div(T(1), T(rb.nb));
+  T q[3], m[3], s, c;
+  backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5) * T(k0 + k1) * inb, q, m, s, c);
+  const T rad = T(0.5) * T(k1 - k0) * rb.L[i] * inb;
+  uint64_t out = 0;
+  for (uint64_t b = cand; b; b &= b - 1) {
+    const int jj = __ffsll((long long)b) - 1;
+    const Sphere4<T> S = sph[j0 + jj];
+    const T dx = m[0] - S.x, dy = m[1] - S.y, dz = m[2] - S.z;
+    const T lim = rad + S.reach + T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
+    if (dx * dx + dy * dy + dz * dz < lim * lim) out |= 1ull << jj;
+  }
+  return out;
+}
+
 // The same sets computed by a warp: lane l tests spheres j0 + l and j0 + l + 32 against every
 // segment and the ballots assemble the masks (identical in all lanes afterwards).
 template <typename T, int N>
@@ -514,13 +542,17 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
-      for (int k = 1; k <= rb.nb; ++k) {
+      for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
+      const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      if (!gm) continue;
+      for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
         T gw[3] = {T(0), T(0), T(0)};
         bool hit = false;
-        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+        for (uint64_t bits = gm; bits; bits &= bits - 1) {
           Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
@@ -552,6 +584,7 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
           ag.Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
           if (PGRAD) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
         }
+      }
       }
     }
     }
@@ -744,8 +777,9 @@ CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3
 // ------------------------------------------------------------------------------------------------
 CR_HD constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
-template <typename TA, int D, typename T>
-CR_HD void rank1(TA (&A)[D * (D + 1) / 2], TA (&g)[D], const T (&j)[D], T r) {
+// A is any indexable packed lower triangle (normally a register array).
+template <typename TA, int D, typename T, typename AArr>
+CR_HD void rank1(AArr&& A, TA (&g)[D], const T (&j)[D], T r) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     TA ja = TA(j[a]);
@@ -755,10 +789,9 @@ CR_HD void rank1(TA (&A)[D * (D + 1) / 2], TA (&g)[D], const T (&j)[D], T r) {
   }
 }
 
-template <typename T, typename TA, int N, bool OBST>
+template <typename T, typename TA, int N, bool OBST, typename AArr>
 CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                       const Sphere4<T>* sph, int no, const T (&u)[3 * N],
-                       TA (&A)[3 * N * (3 * N + 1) / 2], TA (&g)[3 * N]) {
+                       const Sphere4<T>* sph, int no, const T (&u)[3 * N], AArr&& A, TA (&g)[3 * N]) {
   constexpr int D = 3 * N;
 #pragma unroll
   for (int a = 0; a < D * (D + 1) / 2; ++a) A[a] = TA(0);
@@ -866,11 +899,15 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
-      for (int k = 1; k <= rb.nb; ++k) {
+      for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
+      const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      if (!gm) continue;
+      for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
-        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+        for (uint64_t bits = gm; bits; bits &= bits - 1) {
           Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
@@ -911,6 +948,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
           }
           rank1<TA, D>(A, g, jr, rr);
         }
+      }
       }
     }
     }
@@ -1087,14 +1125,19 @@ CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, co
     segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
-      for (int k = 1; k <= rb.nb; ++k) {
+      for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
+      const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      if (!gm) continue;
+      for (int k = k0; k <= k1; ++k) {
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, wp, s, c);
-        for (uint64_t bits = mk[i]; bits; bits &= bits - 1) {
+        for (uint64_t bits = gm; bits; bits &= bits - 1) {
           Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
         }
+      }
       }
     }
   }

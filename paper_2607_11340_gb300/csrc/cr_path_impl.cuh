@@ -69,7 +69,9 @@ __device__ void warm_sweep_warp(const RobotK<T>& rb, const WeightsK<T>& w, const
 }
 
 template <typename T, int N, bool OBST>
-__global__ void __launch_bounds__(128) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathArgs<T> a) {
+// 128 threads; the register cap is explicit (the default heuristic settles below what the exploration
+// step needs and spills).
+__global__ void __maxnreg__(255) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -295,19 +295,32 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
       if (fabs(u[3 * i + j]) > rb.umax[i] + lim_tol) lim = false;
     if (sqrt(ch.x[i]) > rb.thmax[i] + 1e-6) lim = false;
   }
+  // clearance without the margin (radius r_s + r_body); the broad phase uses the larger reach
   bool free = true;
   if (OBST && no > 0) {
     const double inb = 1.0 / rb.nb;
-    for (int i = 0; i < N && free; ++i)
-      for (int k = 1; k <= rb.nb && free; ++k) {
-        double q[3], wp[3], s, c;
-        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], k * inb, q, wp, s, c);
-        for (int j = 0; j < no; ++j) {
-          double ddx = wp[0] - sph[j].x, ddy = wp[1] - sph[j].y, ddz = wp[2] - sph[j].z;
-          double r = sph[j].reach - w.delta;
-          if (ddx * ddx + ddy * ddy + ddz * ddz < r * r) { free = false; break; }
+    for (int j0 = 0; j0 < no && free; j0 += 64) {
+      uint64_t mk[N];
+      segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        if (!mk[i] || !free) continue;
+        for (int k0 = 1; k0 <= rb.nb && free; k0 += kCullGroup) {
+          const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
+          const uint64_t gm = group_sphere_mask<double, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+          for (int k = k0; k <= k1 && gm && free; ++k) {
+            double q[3], wp[3], s, c;
+            backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], k * inb, q, wp, s, c);
+            for (uint64_t bits = gm; bits; bits &= bits - 1) {
+              const int j = j0 + __ffsll((long long)bits) - 1;
+              double ddx = wp[0] - sph[j].x, ddy = wp[1] - sph[j].y, ddz = wp[2] - sph[j].z;
+              double r = sph[j].reach - w.delta;
+              if (ddx * ddx + ddy * ddy + ddz * ddz < r * r) { free = false; break; }
+            }
+          }
         }
       }
+    }
   }
   flags = (unsigned char)((lim ? 1 : 0) | (free ? 2 : 0));
   return F;

@@ -226,10 +226,17 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
         for (int k0 = 0; k0 < rb.nb; k0 += 32) {
           const int k = k0 + lane + 1;
           const bool mine = k <= rb.nb;
+          // second level: this lane's group of kCullGroup samples, then the union over the warp
+          const int kg0 = (k - 1) / kCullGroup * kCullGroup + 1;
+          const int kg1 = kg0 + kCullGroup - 1 < rb.nb ? kg0 + kCullGroup - 1 : rb.nb;
+          const uint64_t gml = mine ? group_sphere_mask<T, N>(rb, ch, ii, kg0, kg1, sph, j0, mk[ii]) : 0ull;
+          const uint64_t um = (uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)gml) |
+                              ((uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)(gml >> 32)) << 32);
+          if (!um) continue;
           T q[3], wpt[3], s, c;
           backbone_point(ch.Rb[ii], ch.pb[ii], ch.ax[ii], ch.ay[ii], ch.x[ii], rb.L[ii], T(mine ? k : 1) * inb, q,
                          wpt, s, c);
-          for (uint64_t bits = mk[ii]; bits; bits &= bits - 1) {
+          for (uint64_t bits = um; bits; bits &= bits - 1) {
             const Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
             const T dx = wpt[0] - S.x, dy = wpt[1] - S.y, dz = wpt[2] - S.z;
             const T d2 = dx * dx + dy * dy + dz * dz;
@@ -286,63 +293,67 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
 }
 
 // One damped LM step of the warp's state (Nielsen's lambda update, strict-decrease acceptance).
-// Returns the cost after the step. The warp's scratch: col, colr, sx, sdg (D + 1 values each).
-template <typename T, int N, bool OBST>
+// The residual, J^T J and the costs are in the bulk precision T; the damped system is solved, and
+// the gain ratio formed, in V (T for exploration, double for a refinement). Returns the cost after
+// the step. The warp's scratch: col, colr, sx, sdg (D + 1 values of V each).
+template <typename T, int N, bool OBST, typename V = T>
 __device__ T warp_lm_step(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, const Sphere4<T>* sph,
-                          int no, T (&u)[3 * N], const AugSlots<3 * N>& sl, T& lam, T& nu, T* col, T* colr, T* sx,
-                          T* sdg) {
+                          int no, T (&u)[3 * N], const AugSlots<3 * N>& sl, V& lam, V& nu, V* col, V* colr, V* sx,
+                          V* sdg) {
   constexpr int D = 3 * N, SL = AugSlots<D>::SL;
   const int lane = threadIdx.x & 31;
   T A[SL], gq;
   const T F = warp_eval<T, N, OBST, true>(rb, w, tg, sph, no, u, sl, A, gq);
   // damped, augmented system [A + lam D | -g]
+  V Av[SL];
 #pragma unroll
   for (int s = 0; s < SL; ++s) {
     const int i = sl.r[s], j = sl.c[s];
     const T gj = __shfl_sync(0xffffffffu, gq, j < D ? j : 0);
+    Av[s] = V(A[s]);
     if (!sl.on[s]) continue;
     if (i < D && i == j) {
-      const T dg = c_max(A[s], T(1e-12));
+      const V dg = c_max(Av[s], V(1e-12));
       sdg[i] = dg;
-      A[s] += lam * dg;
+      Av[s] += lam * dg;
     } else if (i == D) {
-      A[s] = j < D ? -gj : T(0);
+      Av[s] = j < D ? -V(gj) : V(0);
     }
   }
-  const bool ok = sweep_aug<T, D>(A, sl, col, colr);
+  const bool ok = sweep_aug<V, D>(Av, sl, col, colr);
   if (!ok) {
     lam *= nu;
-    nu *= T(2);
+    nu *= V(2);
     return F;
   }
 #pragma unroll
   for (int s = 0; s < SL; ++s)
-    if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) sx[sl.c[s]] = A[s];
+    if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) sx[sl.c[s]] = Av[s];
   __syncwarp();
-  T predl = T(0);
+  V predl = V(0);
   if (lane < D) {
-    const T xq = sx[lane];
-    predl = xq * (lam * sdg[lane] * xq - gq);
+    const V xq = sx[lane];
+    predl = xq * (lam * sdg[lane] * xq - V(gq));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) predl += __shfl_xor_sync(0xffffffffu, predl, off);
-  const T pred = T(0.5) * predl;
+  const V pred = V(0.5) * predl;
   T un[D];
 #pragma unroll
-  for (int q = 0; q < D; ++q) un[q] = u[q] + sx[q];
+  for (int q = 0; q < D; ++q) un[q] = u[q] + T(sx[q]);
   __syncwarp();
   T Ad[SL], gd;
   const T Fn = warp_eval<T, N, OBST, false>(rb, w, tg, sph, no, un, sl, Ad, gd);
   if (Fn < F) {
-    const T rho = c_div(F - Fn, pred), tt = T(2) * rho - T(1);
-    lam *= c_max(T(1) / T(3), T(1) - tt * tt * tt);
-    nu = T(2);
+    const V rho = c_div(V(F) - V(Fn), pred), tt = V(2) * rho - V(1);
+    lam *= c_max(V(1) / V(3), V(1) - tt * tt * tt);
+    nu = V(2);
 #pragma unroll
     for (int q = 0; q < D; ++q) u[q] = un[q];
     return Fn;
   }
   lam *= nu;
-  nu *= T(2);
+  nu *= V(2);
   return F;
 }
 

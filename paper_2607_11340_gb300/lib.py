@@ -340,7 +340,7 @@ def cr_poll_status(workspace, stream=None) -> int:
     return out.value
 
 
-CR_CHECK_RECIP = 0
+CR_CHECK_RECIP, CR_CHECK_SIN, CR_CHECK_COS = 0, 1, 2
 
 
 def cr_device_check(which: int, x, out, stream=None):

@@ -24,3 +24,21 @@ def test_recip_newton_within_ulps():
     exact = 1.0 / x
     ulp = np.abs(r - exact) / np.spacing(np.abs(exact))
     assert ulp.max() <= 2.0, (ulp.max(), x[ulp.argmax()])
+
+
+def test_fp64_sincos_within_ulps():
+    """The FP64 sine and cosine of the kinematics against the host's: within 4 ulp of the result (the
+    two sides' roundings together), near the zeros of sin and cos included, over |x| <= 1e4 and tiny
+    arguments."""
+    from paper_2607_11340_gb300 import lib
+
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.uniform(-4, 4, 40000), rng.uniform(-1e4, 1e4, 20000), 10.0 ** rng.uniform(-300, 0, 5000),
+                        np.arange(-20, 21) * (np.pi / 2), [1e-310]])
+    xd = torch.as_tensor(x, device="cuda")
+    for which, ref in ((lib.CR_CHECK_SIN, np.sin(x)), (lib.CR_CHECK_COS, np.cos(x))):
+        out = torch.empty_like(xd)
+        lib.cr_device_check(which, xd, out)
+        r = out.cpu().numpy()
+        ulp = np.abs(r - ref) / np.spacing(np.maximum(np.abs(ref), 1e-300))
+        assert ulp.max() <= 4.0, (which, ulp.max(), x[ulp.argmax()])
