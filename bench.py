@@ -43,8 +43,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-baseline", action="store_true",
+                    help="skip the CPU oracle sample (and, for the ragged batch, the per-problem comparison)")
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
+    ap.add_argument("--items", type=int, default=synth.N_RAGGED,
+                    help="items of the ragged batch (default 16384; smaller for profiling cases)")
     ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib", "ragged"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
@@ -271,14 +274,14 @@ def other_workload(args):
         dtype = "f32"
     elif args.workload == "ragged":
         fam = synth.ROBOT_FAMILY
-        items, targets, spheres, _ = synth.ragged_workload(synth.N_RAGGED, api.family_fk_backbone(fam, dev), seed=0)
+        items, targets, spheres, _ = synth.ragged_workload(args.items, api.family_fk_backbone(fam, dev), seed=0)
         s = api.BatchSolver(fam, items, synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=0, device=dev)
         s.set_inputs(targets, spheres)
         spu, n_units, workers = s.plan()
         fn = lambda: s.run()
         units, unit = len(items), "problems/s"
-        metric = "ragged batch problems/s (16384 mixed IK / path items, one graph launch)"
-        wl = "ragged_16384_items_n1-6_H1-128_S16-256_no0-64"
+        metric = f"ragged batch problems/s ({args.items} mixed IK / path items, one graph launch)"
+        wl = f"ragged_{args.items}_items_n1-6_H1-128_S16-256_no0-64"
         W = int(items[:, 2].sum())
 
         def lat(t_ns):
@@ -313,7 +316,8 @@ def other_workload(args):
             return {"waypoint_solves_per_s": W / (line["ms_per_step"] / 1e3), "latency": lat(t_ns),
                     "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu, "work_units": n_units,
                     "worker_warps": workers, "items_ik": int((items[:, 0] == 0).sum()),
-                    "items_path": int((items[:, 0] == 1).sum()), "waypoints": W, "vs_plain_subset": subset()}
+                    "items_path": int((items[:, 0] == 1).sum()), "waypoints": W,
+                    "vs_plain_subset": None if args.no_baseline else subset()}
 
         dtype = "f32"
     else:
@@ -442,7 +446,7 @@ def main():
     cal = {}
     pbuf = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
     for kind, name, it in ((0, "ffma_tflops", 4000), (1, "mufu_tops", 4000), (2, "dfma_tflops", 200), (3, "copy_gbs", 1),
-                           (4, "dfma_one_lane_tflops", 200)):
+                           (4, "dfma_one_lane_tflops", 200), (5, "ffma2_tflops", 4000)):
         lib.cr_peak_launch(kind, pbuf, it)
         best = 0.0
         for _ in range(3):

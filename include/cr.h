@@ -343,14 +343,21 @@ CR_API cr_status cr_solve_path(const cr_robot* robot, const cr_scene* scene, con
  * Kinematic calibration and vector-Jacobian products (differentiation w.r.t. the robot)
  * ------------------------------------------------------------------------------------------- */
 
+/* Bytes of device workspace cr_calibrate needs for K poses (0 on invalid arguments). */
+CR_API size_t cr_calibrate_workspace_size(const cr_robot* robot, int64_t K);
+
 /* LM calibration of theta = (L_1..n, r_c,1..n) from K known displacements U [3n][K] (`dtype`) and
  * measured tip positions P_meas [3][K] (FP64): residual p(u_k; theta) - p_k. theta (device, FP64,
  * [2n]) holds the initial guess and receives the estimate; F_out (device, [1]) the final cost;
  * hist (device, nullable, [iters][2n]) the iterates. Same LM rule as cr_lm_step; J^T J and J^T r
- * reduced in FP64 in a fixed order, Cholesky in FP64. Runs as one CTA of 1024 threads. */
+ * reduced in FP64 in a fixed order (per block of 128 poses, then over the blocks in order),
+ * Cholesky in FP64. Per iteration one many-block launch forms the partial sums and one single-block
+ * launch solves, evaluates the trial cost and applies the rule. `workspace` (device, 8-byte
+ * aligned, at least cr_calibrate_workspace_size bytes, caller-owned) holds the damping state and
+ * the partial sums; it is overwritten. */
 CR_API cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_meas, int64_t K, double* theta,
                               int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype,
-                              cr_stream stream);
+                              void* workspace, size_t ws_bytes, cr_stream stream);
 
 /* Vector-Jacobian product of the IK cost: grad_u_out[:, b] = upstream[b] dF_b/du_b and
  * grad_param_out [2n] (FP64) = sum_b upstream[b] dF_b/d(L, r_c). workspace: [2n][B] in `dtype`.
@@ -373,9 +380,10 @@ CR_API const char* cr_last_error_string(void);
 /* Peak-calibration kernels (FP32 FMA chains, special-function chains, FP64 FMA chains and a
  * streaming copy), timed by the caller with events around the launch. kind: 0 FFMA, 1 MUFU
  * (sin/cos approximations), 2 DFMA, 3 copy, 4 DFMA with one active lane per warp (how the FP64
- * pipe charges partly active warps). `buf` is a device buffer of `bytes` bytes (copy
- * reads the first half and writes the second). *ops_out (host) receives the operations one
- * launch performs (flops for 0 and 2, special-function results for 1, bytes moved for 3). */
+ * pipe charges partly active warps), 5 paired FFMA (two FP32 FMAs per lane per instruction).
+ * `buf` is a device buffer of `bytes` bytes (copy reads the first half and writes the second).
+ * *ops_out (host) receives the operations one launch performs (flops for 0, 2, 4 and 5,
+ * special-function results for 1, bytes moved for 3). */
 CR_API cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32_t iters, double* ops_out,
                          cr_stream stream);
 

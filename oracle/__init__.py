@@ -46,10 +46,13 @@ def build(force: bool = False) -> str:
 
 
 class Robot(C.Structure):
-    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nb", C.c_int32), ("pad", C.c_int32),
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nb", C.c_int32), ("model", C.c_int32),
                 ("L", C.c_double * MAXSEG), ("rc", C.c_double * MAXSEG),
                 ("umax", C.c_double * MAXSEG), ("thmax", C.c_double * MAXSEG),
-                ("rbody", C.c_double)]
+                ("rbody", C.c_double), ("lmin", C.c_double * MAXSEG), ("lmax", C.c_double * MAXSEG)]
+
+
+MODEL_TENDON, MODEL_ARC = 0, 1
 
 
 class Weights(C.Structure):
@@ -65,10 +68,17 @@ class IkParams(C.Structure):
                 ("rot_tol", C.c_double), ("seed", C.c_uint64), ("p0", C.c_int64)]
 
 
-def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3) -> Robot:
+def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3, lmin=None, lmax=None) -> Robot:
+    """Tendon model; with lmin/lmax given, the arc model (per segment (theta cos phi, theta sin phi,
+    L) with lmin <= L <= lmax; L then only sets the nominal length)."""
     n = len(L)
     r = Robot()
-    r.n, r.m, r.nb, r.pad = n, m, nb, 0
+    r.n, r.m, r.nb, r.model = n, m, nb, (MODEL_ARC if lmin is not None else MODEL_TENDON)
+    if lmin is not None:
+        lmin = list(lmin) if np.ndim(lmin) else [lmin] * n
+        lmax = list(lmax) if np.ndim(lmax) else [lmax] * n
+        for i in range(n):
+            r.lmin[i], r.lmax[i] = lmin[i], lmax[i]
     rc = list(rc) if np.ndim(rc) else [rc] * n
     umax = list(umax) if np.ndim(umax) else [umax] * n
     thmax = [np.pi] * n if thmax is None else (list(thmax) if np.ndim(thmax) else [thmax] * n)
@@ -261,6 +271,16 @@ def project(v, b):
     v = _f64(v)
     u = np.zeros_like(v)
     lib().orc_project(_dp(v), C.c_int64(v.shape[0]), C.c_int(v.shape[1]), C.c_double(b), _dp(u))
+    return u
+
+
+def project_arc(v, thmax, lmin, lmax):
+    """Arc model: projection of each row (tx, ty, L) of v[B][3] onto {|(tx, ty)| <= thmax} x
+    [lmin, lmax]."""
+    v = _f64(v)
+    u = np.zeros_like(v)
+    lib().orc_project_arc(_dp(v), C.c_int64(v.shape[0]), C.c_double(thmax), C.c_double(lmin), C.c_double(lmax),
+                          _dp(u))
     return u
 
 

@@ -151,13 +151,22 @@ struct OrRobot {
   int32_t n;   // segments
   int32_t m;   // tendons per segment (equally spaced, alpha_j = (j-1) 2 pi / m)
   int32_t nb;  // backbone samples per segment (sample k at arc fraction k/nb, k = 1..nb)
-  int32_t pad;
+  int32_t model;  // decision variables: OR_MODEL_TENDON or OR_MODEL_ARC (see below)
   double L[OR_MAXSEG];      // segment arc length (m)
   double rc[OR_MAXSEG];     // tendon routing radius (m)
   double umax[OR_MAXSEG];   // displacement bound |u_ij| <= umax_i (m)
   double thmax[OR_MAXSEG];  // bending-angle limit (rad)
   double rbody;             // backbone radius used by the clearance rows (m)
+  double lmin[OR_MAXSEG];   // OR_MODEL_ARC: arc-length bounds lmin_i <= L_i <= lmax_i (m)
+  double lmax[OR_MAXSEG];
 };
+
+// Decision variables of a segment. OR_MODEL_TENDON: the m tendon displacements u_ij (Eq. 4 gives
+// theta, phi; L is the robot's). OR_MODEL_ARC: the paper's own configuration q_i = (theta, phi, L)
+// of Sec. IV-A, with L free within [lmin, lmax] (extendable segments) and (theta, phi) written in
+// Cartesian form (theta cos phi, theta sin phi): the same configurations, smooth at theta = 0 where
+// phi is undefined. Three variables per segment in both models.
+enum { OR_MODEL_TENDON = 0, OR_MODEL_ARC = 1 };
 
 struct OrWeights {
   double wp, wR;                         // pose residual weights (1/m, 1/rad)
@@ -310,8 +319,15 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
       o.pb[i][a] = p[a];
       for (int b = 0; b < 3; ++b) o.Rb[i][a][b] = R[a][b];
     }
-    T tx, ty;
-    tendon_to_bend(u + rb.m * i, rb.m, P.rc[i], tx, ty);
+    T tx, ty, Li;
+    if (rb.model == OR_MODEL_ARC) {
+      tx = u[3 * i];
+      ty = u[3 * i + 1];
+      Li = u[3 * i + 2];
+    } else {
+      tendon_to_bend(u + rb.m * i, rb.m, P.rc[i], tx, ty);
+      Li = P.L[i];
+    }
     o.th2[i] = tx * tx + ty * ty;
     if (backbone) {
       // Backbone sample k: the arc of fraction sigma = k/nb, i.e. bending sigma*theta in the same
@@ -319,7 +335,7 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
       for (int k = 1; k <= rb.nb; ++k) {
         T sg = T((double)k / rb.nb);
         T Rs[3][3], ds[3];
-        segment_transform(sg * tx, sg * ty, sg * P.L[i], Rs, ds);
+        segment_transform(sg * tx, sg * ty, sg * Li, Rs, ds);
         T* q = backbone + 3 * (i * rb.nb + (k - 1));
         for (int a = 0; a < 3; ++a) {
           T s = p[a];
@@ -329,7 +345,7 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
       }
     }
     T Ri[3][3], di[3];
-    segment_transform(tx, ty, P.L[i], Ri, di);
+    segment_transform(tx, ty, Li, Ri, di);
     T pn[3], Rn[3][3];
     for (int a = 0; a < 3; ++a) {
       T s = p[a];
@@ -433,8 +449,12 @@ static void pose_residual(int kind, const OrWeights& W, const double* tgt, const
 // ---------------------------------------------------------------------------------------------
 
 // Per-state constraint rows, appended at r; returns the number of rows.
+// OR_MODEL_TENDON:
 //   2d rows  sqrt(rho_b) max(0, u_ij - umax_i), sqrt(rho_b) max(0, -umax_i - u_ij)
 //   n rows   sqrt(rho_eq) sum_j u_ij                      (common mode is invisible to FK)
+// OR_MODEL_ARC (Eq. ik_limits on q = (theta, phi, L)):
+//   2n rows  sqrt(rho_b) max(0, L_i - lmax_i), sqrt(rho_b) max(0, lmin_i - L_i)
+// both:
 //   n rows   sqrt(rho_k) max(0, theta_i - thmax_i)
 //   n*nb*no  sqrt(rho_c) max(0, r_s + r_body + delta - |p_ik - c_s|)   (sample-sphere pairs)
 template <class T>
@@ -445,15 +465,22 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
   const int d = rb.n * rb.m;
   T sb = T(std::sqrt(W.rho_b)), se = T(std::sqrt(W.rho_eq)), sk = T(std::sqrt(W.rho_k)),
     sc = T(std::sqrt(W.rho_c));
-  for (int q = 0; q < d; ++q) {
-    int i = q / rb.m;
-    r[k++] = sb * hinge(u[q] - T(rb.umax[i]));
-    r[k++] = sb * hinge(T(-rb.umax[i]) - u[q]);
-  }
-  for (int i = 0; i < rb.n; ++i) {
-    T s(0.0);
-    for (int j = 0; j < rb.m; ++j) s += u[rb.m * i + j];
-    r[k++] = se * s;
+  if (rb.model == OR_MODEL_ARC) {
+    for (int i = 0; i < rb.n; ++i) {
+      r[k++] = sb * hinge(u[3 * i + 2] - T(rb.lmax[i]));
+      r[k++] = sb * hinge(T(rb.lmin[i]) - u[3 * i + 2]);
+    }
+  } else {
+    for (int q = 0; q < d; ++q) {
+      int i = q / rb.m;
+      r[k++] = sb * hinge(u[q] - T(rb.umax[i]));
+      r[k++] = sb * hinge(T(-rb.umax[i]) - u[q]);
+    }
+    for (int i = 0; i < rb.n; ++i) {
+      T s(0.0);
+      for (int j = 0; j < rb.m; ++j) s += u[rb.m * i + j];
+      r[k++] = se * s;
+    }
   }
   for (int i = 0; i < rb.n; ++i) {
     if (re(fk.th2[i]) > rb.thmax[i] * rb.thmax[i]) r[k++] = sk * (Sqrt(fk.th2[i]) - T(rb.thmax[i]));
@@ -483,6 +510,7 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
 }
 
 static int state_constraint_count(const OrRobot& rb, int no) {
+  if (rb.model == OR_MODEL_ARC) return 3 * rb.n + rb.n * rb.nb * no;
   return 2 * rb.n * rb.m + 2 * rb.n + rb.n * rb.nb * no;
 }
 
@@ -655,6 +683,24 @@ static void project_segment(const double* v, int m, double b, double* u) {
   for (int j = 0; j < m; ++j) u[j] = std::min(b, std::max(-b, v[j] - tau));
 }
 
+// OR_MODEL_ARC: Euclidean projection onto {theta <= thmax} x [lmin, lmax] (a disk times an
+// interval, so each factor projects on its own): the bend (tx, ty) is scaled back radially onto
+// the disk, L is clamped.
+static void project_arc(const double* v, double thmax, double lmin, double lmax, double* u) {
+  const double r = std::sqrt(v[0] * v[0] + v[1] * v[1]);
+  const double f = r > thmax ? thmax / r : 1.0;
+  u[0] = v[0] * f;
+  u[1] = v[1] * f;
+  u[2] = std::min(lmax, std::max(lmin, v[2]));
+}
+
+static void project_state(const OrRobot& rb, const double* v, double* u) {
+  for (int i = 0; i < rb.n; ++i) {
+    if (rb.model == OR_MODEL_ARC) project_arc(v + 3 * i, rb.thmax[i], rb.lmin[i], rb.lmax[i], u + 3 * i);
+    else project_segment(v + rb.m * i, rb.m, rb.umax[i], u + rb.m * i);
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Seeds (SampleSeeds of Algorithm 1): counter-based SplitMix64 and hexagon-uniform draws.
 // ---------------------------------------------------------------------------------------------
@@ -688,6 +734,32 @@ static void hexagon_point(double b, double U0, double U1, double U2, double* u) 
     double tb = B[j] == 0 ? 0.0 : (B[j] > 0 ? U2 * b : -(U2 * b));
     u[j] = ta + tb;
   }
+}
+
+// OR_MODEL_ARC seed of one segment: L uniform on [lmin, lmax] (draw 0) and the bend (tx, ty)
+// uniform on the disk of radius thmax by rejection from the enclosing square: try t = 0..7 draws
+// the square's point from counters (draw 1 and draw 2) + t * 2^48 (beyond every draw counter of
+// problems p < 2^24) and keeps the first inside; if none is, the last is scaled onto the circle.
+static void arc_seed_point(uint64_t key, uint64_t p, uint64_t s, uint64_t a, uint64_t i, double thmax,
+                           double lmin, double lmax, double* q) {
+  const double UL = u01_from(splitmix64_at(key, seed_counter(p, s, a, i, 0)));
+  double x = 0, y = 0;
+  bool in = false;
+  for (uint64_t t = 0; t < 8 && !in; ++t) {
+    const double X = u01_from(splitmix64_at(key, seed_counter(p, s, a, i, 1) + (t << 48)));
+    const double Y = u01_from(splitmix64_at(key, seed_counter(p, s, a, i, 2) + (t << 48)));
+    x = (2.0 * X - 1.0) * thmax;
+    y = (2.0 * Y - 1.0) * thmax;
+    in = x * x + y * y <= thmax * thmax;
+  }
+  if (!in) {
+    const double f = thmax / std::sqrt(x * x + y * y);
+    x = x * f;
+    y = y * f;
+  }
+  q[0] = x;
+  q[1] = y;
+  q[2] = lmin + UL * (lmax - lmin);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -767,7 +839,7 @@ static void pg_run_one(const IkProblem& pb, double* u, int steps, double alpha0,
     gn = std::sqrt(gn);
     double scale = gn > 0 ? alpha / gn : 0.0;
     for (int a = 0; a < nx; ++a) v[a] = u[a] - scale * g[a];
-    for (int i = 0; i < rb.n; ++i) project_segment(v.data() + rb.m * i, rb.m, rb.umax[i], x1.data() + rb.m * i);
+    project_state(rb, v.data(), x1.data());
     double F1 = pb.cost(x1.data(), nullptr);
     if (F1 < F) {
       pb.grad(x1.data(), g1.data());
@@ -988,6 +1060,12 @@ int orc_project(const double* v, int64_t B, int m, double b, double* u) {
   return 0;
 }
 
+// OR_MODEL_ARC projection of B segment states v[B][3] onto {theta <= thmax} x [lmin, lmax].
+int orc_project_arc(const double* v, int64_t B, double thmax, double lmin, double lmax, double* u) {
+  for (int64_t q = 0; q < B; ++q) project_arc(v + 3 * q, thmax, lmin, lmax, u + 3 * q);
+  return 0;
+}
+
 // Stage-one projected gradient on every seed: u[B][d] in place, F[B] out.
 int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int steps, double alpha0,
@@ -1013,6 +1091,10 @@ int orc_seeds(const OrRobot* rb, const OrWeights* W, int no, const double* spher
       double* x = u + ((size_t)q * S + s) * d;
       for (int a = 0; a < 8; ++a) {
         for (int i = 0; i < rb->n; ++i) {
+          if (rb->model == OR_MODEL_ARC) {
+            arc_seed_point(base, p0 + q, s, a, i, rb->thmax[i], rb->lmin[i], rb->lmax[i], x + 3 * i);
+            continue;
+          }
           double U[3];
           for (int w = 0; w < 3; ++w)
             U[w] = u01_from(splitmix64_at(base, seed_counter(p0 + q, s, a, i, w)));
@@ -1069,7 +1151,8 @@ int orc_topk(const float* cost, const float* coll, const double* u /*[S][d]*/, i
 }
 
 // Final acceptance of one solution: position error (m), rotation error (rad: Log angle for IK6,
-// angle between tip axes for IK5), limits (|u| <= umax + tol, |sum u| <= tol, theta <= thmax + tol)
+// angle between tip axes for IK5), limits (|u| <= umax + tol, |sum u| <= tol, or for OR_MODEL_ARC
+// lmin - tol <= L <= lmax + tol; theta <= thmax + tol)
 // and collision-free (every sample at least r_s + r_body from every sphere centre).
 static void accept_one(const OrRobot& rb, int no, const double* spheres, int kind,
                        const double* tgt, const double* u, double tol, double* pos, double* rot,
@@ -1096,13 +1179,18 @@ static void accept_one(const OrRobot& rb, int no, const double* spheres, int kin
   }
   bool ok = true;
   for (int i = 0; i < rb.n; ++i) {
-    double s = 0;
-    for (int j = 0; j < rb.m; ++j) {
-      double x = u[rb.m * i + j];
-      s += x;
-      if (std::fabs(x) > rb.umax[i] + tol) ok = false;
+    if (rb.model == OR_MODEL_ARC) {
+      const double L = u[3 * i + 2];
+      if (L > rb.lmax[i] + tol || L < rb.lmin[i] - tol) ok = false;
+    } else {
+      double s = 0;
+      for (int j = 0; j < rb.m; ++j) {
+        double x = u[rb.m * i + j];
+        s += x;
+        if (std::fabs(x) > rb.umax[i] + tol) ok = false;
+      }
+      if (std::fabs(s) > tol) ok = false;
     }
-    if (std::fabs(s) > tol) ok = false;
     if (std::sqrt(o.th2[i]) > rb.thmax[i] + 1e-6) ok = false;
   }
   *lim_ok = ok;

@@ -296,7 +296,8 @@ def calibrate(robot_spec, U_soa, P_meas_soa, theta0, iters=synth.ITERS_CALIB, la
     theta = torch.as_tensor(theta0, dtype=torch.float64, device=U_soa.device).clone()
     F = torch.empty(1, dtype=torch.float64, device=U_soa.device)
     hist = torch.empty((iters, 2 * robot_spec.n), dtype=torch.float64, device=U_soa.device) if history else None
-    lib.cr_calibrate(robot, U_soa, P_meas_soa, theta, iters, lambda0, F, hist)
+    ws = torch.empty(lib.cr_calibrate_workspace_size(robot, U_soa.shape[-1]), dtype=torch.uint8, device=U_soa.device)
+    lib.cr_calibrate(robot, U_soa, P_meas_soa, theta, iters, lambda0, F, hist, ws)
     return theta, F, hist
 
 

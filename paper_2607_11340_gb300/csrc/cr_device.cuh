@@ -523,7 +523,10 @@ template <typename T, int N> struct StateAgg {
 
 // Forward phase: chain, clearance rows (and their aggregates when GRAD), and the penalty rows on u
 // (bounds, sum-zero, curvature). Returns their part of F; *coll_out = the clearance part.
-template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
+// BOX = false leaves out the bound and sum-zero rows: on the feasible set {|u_j| <= b, sum u_j = 0}
+// they vanish, so callers whose state was just projected onto it skip them (in FP32 the sum-zero
+// row would only add the rounding residue of the projection).
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true>
 CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T>* sph, int no,
                       const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out) {
   chain_forward(rb, u, ch);
@@ -593,13 +596,15 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
   T F = coll;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
-    F += T(0.5) * w.rho_eq * su * su;
+    if (BOX) {
+      T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+      F += T(0.5) * w.rho_eq * su * su;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T hi = u[3 * i + j] - rb.umax[i], lo = -rb.umax[i] - u[3 * i + j];
-      if (hi > T(0)) F += T(0.5) * w.rho_b * hi * hi;
-      if (lo > T(0)) F += T(0.5) * w.rho_b * lo * lo;
+      for (int j = 0; j < 3; ++j) {
+        T hi = u[3 * i + j] - rb.umax[i], lo = -rb.umax[i] - u[3 * i + j];
+        if (hi > T(0)) F += T(0.5) * w.rho_b * hi * hi;
+        if (lo > T(0)) F += T(0.5) * w.rho_b * lo * lo;
+      }
     }
     if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T vk = c_sqrt(ch.x[i]) - rb.thmax[i];
@@ -612,8 +617,8 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
 // Reverse phase: given dF/dp at the tip (Ftip) and the world moment of dF/d(tip rotation) (Rtip),
 // sweep the segments from the tip to the base: the force and moment of everything downstream of
 // segment i act on (ax_i, ay_i) through the segment's local derivatives. Adds the penalty gradients
-// and writes dF/du (and dF/dL, dF/dr_c when PGRAD).
-template <typename T, int N, bool PGRAD>
+// and writes dF/du (and dF/dL, dF/dr_c when PGRAD). BOX as in state_forward.
+template <typename T, int N, bool PGRAD, bool BOX = true>
 CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)[3 * N], const Chain<T, N>& ch,
                          const StateAgg<T, N>& ag, const T (&Ftip)[3], const T (&Rtip)[3], T (&gu)[3 * N], T* gL,
                          T* grc) {
@@ -652,15 +657,20 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     }
     T g0, g1, g2;
     bend_grad_to_u(rb.K[i], gx, gy, g0, g1, g2);
-    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
-    T geq = w.rho_eq * su;
     T gj[3] = {g0, g1, g2};
+    if (BOX) {
+      T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+      T geq = w.rho_eq * su;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T uj = u[3 * i + j];
-      T hi = uj - rb.umax[i], lo = -rb.umax[i] - uj;
-      T gb = (hi > T(0) ? w.rho_b * hi : T(0)) - (lo > T(0) ? w.rho_b * lo : T(0));
-      gu[3 * i + j] = gj[j] + geq + gb;
+      for (int j = 0; j < 3; ++j) {
+        T uj = u[3 * i + j];
+        T hi = uj - rb.umax[i], lo = -rb.umax[i] - uj;
+        T gb = (hi > T(0) ? w.rho_b * hi : T(0)) - (lo > T(0) ? w.rho_b * lo : T(0));
+        gu[3 * i + j] = gj[j] + geq + gb;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gu[3 * i + j] = gj[j];
     }
     if (PGRAD) {
       // dF/dL_i: translation d_i = L (...) scales with L; own samples q scale with L too
@@ -696,21 +706,21 @@ CR_HD void pose_tip_force(int kind, const WeightsK<T>& w, const TargetK<T>& tg, 
   }
 }
 
-// Cost (and adjoint) of an IK state: the two phases around the pose rows.
-template <typename T, int N, bool OBST, bool GRAD, bool PGRAD>
+// Cost (and adjoint) of an IK state: the two phases around the pose rows. BOX as in state_forward.
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true>
 CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                 const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
                 T* coll_out) {
   Chain<T, N> ch;
   StateAgg<T, N> ag;
-  T F = state_forward<T, N, OBST, GRAD, PGRAD>(rb, w, sph, no, u, ch, ag, coll_out);
+  T F = state_forward<T, N, OBST, GRAD, PGRAD, BOX>(rb, w, sph, no, u, ch, ag, coll_out);
   T r[6], e[3], ang, sn, cs;
   pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
   F += T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
   if (!GRAD) return F;
   T Ftip[3], Rtip[3];
   pose_tip_force(kind, w, tg, ch.R, r, e, Ftip, Rtip);
-  state_reverse<T, N, PGRAD>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
+  state_reverse<T, N, PGRAD, BOX>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
   return F;
 }
 

@@ -1,4 +1,5 @@
-// Peak-calibration kernels, timed by the caller in the same run as the solver: FP32 FMA chains,
+// Peak-calibration kernels, timed by the caller in the same run as the solver: FP32 FMA chains
+// (scalar and paired),
 // special-function (MUFU sin/cos approximation) chains, FP64 FMA chains and a streaming copy.
 // Each thread runs several independent dependency chains so that the pipes, not latency, bound it.
 #include "cr_host.h"
@@ -17,6 +18,22 @@ __global__ void __launch_bounds__(256) k_peak_ffma(float* out, int iters) {
     }
   }
   float s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (s == 12345.678f) out[threadIdx.x] = s;
+}
+
+// The same chains with the paired FP32 instruction (two independent FMAs per lane per instruction).
+__global__ void __launch_bounds__(256) k_peak_ffma2(float* out, int iters) {
+  const float b0 = threadIdx.x * 1e-3f;
+  float2 a0 = make_float2(b0, b0 + 1), a1 = make_float2(b0 + 2, b0 + 3), a2 = make_float2(b0 + 4, b0 + 5),
+         a3 = make_float2(b0 + 6, b0 + 7);
+  const float2 m = make_float2(0.999999f, 0.999999f), c = make_float2(1e-7f, 1e-7f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a0 = __ffma2_rn(a0, m, c); a1 = __ffma2_rn(a1, m, c); a2 = __ffma2_rn(a2, m, c); a3 = __ffma2_rn(a3, m, c);
+    }
+  }
+  float s = a0.x + a0.y + a1.x + a1.y + a2.x + a2.y + a3.x + a3.y;
   if (s == 12345.678f) out[threadIdx.x] = s;
 }
 
@@ -90,6 +107,10 @@ extern "C" cr_status cr_peak_launch(int32_t kind, void* buf, size_t bytes, int32
   switch (kind) {
     case 0:
       k_peak_ffma<<<blocks, threads, 0, s>>>((float*)buf, iters);
+      *ops_out = nthr * iters * 16 * 8 * 2.0;
+      break;
+    case 5:
+      k_peak_ffma2<<<blocks, threads, 0, s>>>((float*)buf, iters);
       *ops_out = nthr * iters * 16 * 8 * 2.0;
       break;
     case 1:

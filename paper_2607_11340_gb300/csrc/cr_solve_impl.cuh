@@ -17,6 +17,9 @@ namespace crk {
 
 // ------------------------------------------------------------------------------------------------
 // One projected-gradient step (stage one): trial u' = Pi(u - alpha g / |g|); accept iff F(u') < F(u).
+// The trial point is feasible, so its bound and sum-zero rows are zero: the FP32 form leaves them out
+// (in FP32 the sum-zero row would only contribute the projection's rounding residue); the FP64 form
+// evaluates them, term by term like the FP64 definition.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N, bool OBST>
 CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
@@ -32,7 +35,7 @@ CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Ta
     project3(u[3 * i] - scale * g[3 * i], u[3 * i + 1] - scale * g[3 * i + 1],
              u[3 * i + 2] - scale * g[3 * i + 2], rb.umax[i], u1[3 * i], u1[3 * i + 1], u1[3 * i + 2]);
   T g1[D], c1;
-  T F1 = eval_ik<T, N, OBST, true, false>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr, &c1);
+  T F1 = eval_ik<T, N, OBST, true, false, (sizeof(T) == 8)>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr, &c1);
   if (F1 < F) {
 #pragma unroll
     for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
@@ -182,6 +185,7 @@ template <typename T> struct IkArgs {
   const double* spheres;
   int no;
   int sph_pp;  // spheres are per problem: [P][no][4]
+  int tpb;     // per-problem spheres: targets per refine block (their sphere sets staged side by side)
   int S, K, k_init, k_final;
   T alpha0, eps;
   double lambda0, lim_tol, pos_tol, rot_tol;
@@ -331,19 +335,33 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
                                                     WeightsK<double> wd, IkArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nset = a.sph_pp ? a.tpb : 1;  // sphere sets staged by this block
   Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
+  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw + (size_t)nset * a.no * sizeof(Sphere4<double>));
   const int64_t PK = a.P * a.K;
-  // shared sphere set: 128 candidates per block; per-problem sets: one block (warp) per target
-  const int64_t c = a.sph_pp ? (int64_t)blockIdx.x * a.K + threadIdx.x
+  // shared sphere set: one candidate per thread; per-problem sets: tpb targets per block, K threads
+  // each
+  const int jt = a.sph_pp ? (int)threadIdx.x / a.K : 0;
+  const int64_t c = a.sph_pp ? ((int64_t)blockIdx.x * a.tpb + jt) * a.K + (int)threadIdx.x % a.K
                              : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (OBST) {
-    const double* sp = a.spheres + (a.sph_pp ? (int64_t)blockIdx.x * a.no * 4 : 0);
-    stage_spheres(sp, a.no, rbd, wd.delta, sphd);
-    stage_spheres(sp, a.no, rb, w.delta, sph);
+    if (a.sph_pp) {
+      const int64_t t0 = (int64_t)blockIdx.x * a.tpb;
+      const int ntb = (int)(a.P - t0 < a.tpb ? a.P - t0 : a.tpb);
+      for (int e = threadIdx.x; e < ntb * a.no; e += blockDim.x) {
+        const double* q = a.spheres + ((t0 + e / a.no) * a.no + e % a.no) * 4;
+        sphd[e] = Sphere4<double>{q[0], q[1], q[2], q[3] + rbd.rbody + wd.delta};
+        sph[e] = Sphere4<T>{T(q[0]), T(q[1]), T(q[2]), T(q[3]) + rb.rbody + w.delta};
+      }
+    } else {
+      stage_spheres(a.spheres, a.no, rbd, wd.delta, sphd);
+      stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    }
     __syncthreads();
+    sphd += jt * a.no;
+    sph += jt * a.no;
   }
-  if (c >= PK || (a.sph_pp && (int)threadIdx.x >= a.K)) return;
+  if (c >= PK || (a.sph_pp && jt >= a.tpb)) return;
   const int64_t p = c / a.K;
   T u[D];
 #pragma unroll
@@ -583,6 +601,7 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
   k.spheres = a.scene.spheres;
   k.no = a.scene.n_o;
   k.sph_pp = (a.scene.per_problem && a.scene.n_o > 0) ? 1 : 0;
+  k.tpb = 1;
   k.S = p.S;
   k.K = p.n_final;
   k.k_init = p.k_init;
@@ -635,10 +654,27 @@ template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which)
   if ((st = crh::check_launch("cr_solve_ik stage one"))) return st;
   }
   if (!(which & 2)) return CR_OK;
-  size_t sm2 = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<T>));
-  unsigned g2 = k.sph_pp ? (unsigned)P : grid1(P * k.K, 128);
-  int b2 = k.sph_pp ? 32 : 128;
-  if (no > 0) k_ik_refine<T, N, true><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  // per-problem spheres: one warp per block. With K >= 8 it holds 32 / K (at most 4) targets, their
+  // sphere sets side by side in shared memory, so that the FP64 instructions run with all lanes busy
+  // (the FP64 pipe charges a whole warp). With fewer candidates per target it holds one: more
+  // targets per warp make the lanes' clearance loops diverge (the warp runs the union of their
+  // trips), which costs more than the idle FP64 lanes (measured on the 4-candidate goal IK of the
+  // trajectory workload).
+  const size_t per_set = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<T>));
+  k.tpb = 1;
+  if (k.sph_pp && k.K >= 8) {
+    k.tpb = 32 / k.K;
+    const int cap = (int)((96 * 1024) / (per_set > 0 ? per_set : 1));
+    if (k.tpb > cap) k.tpb = cap;
+    if (k.tpb < 1) k.tpb = 1;
+  }
+  size_t sm2 = per_set * k.tpb;
+  unsigned g2 = k.sph_pp ? grid1(P, k.tpb) : grid1(P * k.K, 128);
+  int b2 = k.sph_pp ? ((k.tpb * k.K + 31) / 32) * 32 : 128;
+  if (no > 0) {
+    if ((st = set_smem(k_ik_refine<T, N, true>, sm2))) return st;
+    k_ik_refine<T, N, true><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  }
   else k_ik_refine<T, N, false><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   if ((st = crh::check_launch("cr_solve_ik refine"))) return st;
   k_ik_argmin<N><<<grid1(P, 128), 128, 0, a.stream>>>(P, k.K, k.pos_tol, k.rot_tol, k.cand_u64, k.cand_F,

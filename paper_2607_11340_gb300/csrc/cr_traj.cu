@@ -121,15 +121,24 @@ cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_t
   return goal_ik->precision == CR_F64 ? crk::launch_traj_solve<double>(l) : crk::launch_traj_solve<float>(l);
 }
 
+size_t cr_calibrate_workspace_size(const cr_robot* robot, int64_t K) {
+  if (!robot || robot->n < 1 || robot->n > CR_MAX_SEG || K < 1) return 0;
+  return crk::calibrate_ws_bytes(robot->n, K);
+}
+
 cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_meas, int64_t K, double* theta,
-                       int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype, cr_stream stream) {
+                       int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype, void* workspace,
+                       size_t ws_bytes, cr_stream stream) {
   cr_status st;
   if ((st = check_robot(robot)) || (st = check_dtype(dtype))) return st;
   if (K < 1 || iters < 0 || !(lambda0 > 0)) return fail(CR_EINVAL, "cr_calibrate: K >= 1, iters >= 0, lambda0 > 0");
   if ((st = check_ptr(U, dsize(dtype), "U", true)) || (st = check_ptr(P_meas, 8, "P_meas", true)) ||
       (st = check_ptr(theta, 8, "theta", true)) || (st = check_ptr(F_out, 8, "F_out", true)) ||
-      (st = check_ptr(hist, 8, "hist", false)))
+      (st = check_ptr(hist, 8, "hist", false)) || (st = check_ptr(workspace, 8, "workspace", true)))
     return st;
+  if (ws_bytes < crk::calibrate_ws_bytes(robot->n, K))
+    return fail(CR_EINVAL, "cr_calibrate: workspace of %zu bytes, %zu needed", ws_bytes,
+                crk::calibrate_ws_bytes(robot->n, K));
   crk::TrajLaunch l{};
   l.robot = *robot;
   l.U = U;
@@ -140,6 +149,7 @@ cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_mea
   l.theta_dev = theta;
   l.F_dev = F_out;
   l.hist_dev = hist;
+  l.calib_ws = workspace;
   l.stream = stream_of(stream);
   return dtype == CR_F64 ? crk::launch_calibrate<double>(l) : crk::launch_calibrate<float>(l);
 }

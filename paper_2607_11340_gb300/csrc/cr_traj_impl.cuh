@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
 }
 
 // ------------------------------------------------------------------------------------------------
-// Calibration: one CTA. theta = (L_1..n, r_c,1..n); residual p(u_k; theta) - p_k.
+// Calibration: theta = (L_1..n, r_c,1..n); residual p(u_k; theta) - p_k.
 // ------------------------------------------------------------------------------------------------
 // dp/dL_i = Rb_i d_i / L_i (everything after segment i translates); dp/dr_c,i = -(ax dp/dax +
 // ay dp/day) / r_c with dp/da_k = v + w x p from the segment twists.
@@ -346,125 +346,176 @@ __device__ void calib_rows(const RobotK<T>& rb, const T (&u)[3 * N], const doubl
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(1024) k_calibrate(RobotK<T> rb0, const T* __restrict__ U, const double* __restrict__ Pm,
-                                                     int64_t K, int iters, double lambda0, double* theta_io,
-                                                     double* F_out, double* hist) {
-  constexpr int D = 3 * N, NP = 2 * N, NA = NP * (NP + 1) / 2;
-  __shared__ double red[32];
-  __shared__ double th[NP], thn[NP], A[NA], g[NP], Dg[NP], invd[NP], dl[NP];
-  __shared__ double sF, sFn, lam, nu;
-  __shared__ int ok;
-  if (threadIdx.x < NP) th[threadIdx.x] = theta_io[threadIdx.x];
-  if (threadIdx.x == 0) { lam = lambda0; nu = 2.0; }
-  __syncthreads();
-  auto robot_of = [&](const double* theta) {
-    RobotK<T> rb = rb0;
-    for (int i = 0; i < N; ++i) {
-      rb.L[i] = T(theta[i]);
-      rb.rc[i] = T(theta[N + i]);
-      rb.K[i] = T(-2.0 / (3.0 * theta[N + i]));
-    }
-    return rb;
-  };
-  for (int it = 0; it < iters; ++it) {
-    RobotK<T> rb = robot_of(th);
-    double la[NA], lg[NP], lF = 0;
-    for (int a = 0; a < NA; ++a) la[a] = 0;
-    for (int a = 0; a < NP; ++a) lg[a] = 0;
-    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-      T u[D];
-      for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
-      double pm[3] = {Pm[k], Pm[K + k], Pm[2 * K + k]};
-      T r[3], J[3][NP];
-      calib_rows<T, N>(rb, u, pm, r, J);
-      for (int a = 0; a < 3; ++a) {
-        lF += 0.5 * double(r[a]) * double(r[a]);
-        for (int x = 0; x < NP; ++x) {
-          lg[x] += double(J[a][x]) * double(r[a]);
-          for (int y = 0; y <= x; ++y) la[tri(x, y)] += double(J[a][x]) * double(J[a][y]);
-        }
-      }
-    }
-    for (int a = 0; a < NA; ++a) {
-      double v = block_sum(la[a], red);
-      if (threadIdx.x == 0) A[a] = v;
-    }
-    for (int a = 0; a < NP; ++a) {
-      double v = block_sum(lg[a], red);
-      if (threadIdx.x == 0) g[a] = v;
-    }
-    double Fc = block_sum(lF, red);
-    if (threadIdx.x == 0) {
-      sF = Fc;
-      double Ad[NA];
-      for (int a = 0; a < NA; ++a) Ad[a] = A[a];
-      for (int q = 0; q < NP; ++q) {
-        Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
-        Ad[tri(q, q)] += lam * Dg[q];
-      }
-      double iv[NP];
-      ok = cholesky_packed<NP>(Ad, iv) ? 1 : 0;
-      if (ok) {
-        double x[NP];
-        for (int q = 0; q < NP; ++q) x[q] = -g[q];
-        cholesky_solve<NP>(Ad, iv, x);
-        for (int q = 0; q < NP; ++q) { dl[q] = x[q]; thn[q] = th[q] + x[q]; }
-      }
-    }
-    __syncthreads();
-    if (ok) {
-      RobotK<T> rbn = robot_of(thn);
-      double lFn = 0;
-      for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-        T u[D];
-        for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
-        Chain<T, N> ch;
-        chain_forward(rbn, u, ch);
-        for (int a = 0; a < 3; ++a) {
-          double ra = double(ch.p[a] - T(Pm[a * K + k]));
-          lFn += 0.5 * ra * ra;
-        }
-      }
-      double Fn = block_sum(lFn, red);
-      if (threadIdx.x == 0) {
-        double pred = 0;
-        for (int q = 0; q < NP; ++q) pred += dl[q] * (lam * Dg[q] * dl[q] - g[q]);
-        pred *= 0.5;
-        if (Fn < sF) {
-          double rho = (sF - Fn) / pred, tt = 2.0 * rho - 1.0;
-          lam *= fmax(1.0 / 3.0, 1.0 - tt * tt * tt);
-          nu = 2.0;
-          for (int q = 0; q < NP; ++q) th[q] = thn[q];
-          sF = Fn;
-        } else {
-          lam *= nu;
-          nu *= 2.0;
-        }
-      }
-    } else if (threadIdx.x == 0) {
-      lam *= nu;
-      nu *= 2.0;
-    }
-    __syncthreads();
-    if (hist && threadIdx.x < NP) hist[it * NP + threadIdx.x] = th[threadIdx.x];
+// Multi-block form. Per LM iteration, k_calib_accum (one thread per pose, 128 poses per block) adds
+// each block's contributions to J^T J (packed), J^T r and F = 1/2 sum r^2 in FP64 (warp butterflies,
+// then the four warps in order) into part[block][.]; k_calib_step (one block) adds the partials in
+// block order, factors the damped system in FP64, evaluates the trial cost over all poses and applies
+// the LM rule to theta (in place), lambda and nu (workspace). All sums have a fixed order.
+constexpr int kCalibThreads = 128;
+template <int N> constexpr int calib_nv() { return (2 * N) * (2 * N + 1) / 2 + 2 * N + 1; }
+
+template <typename T, int N> __device__ RobotK<T> calib_robot(RobotK<T> rb, const double* theta) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    rb.L[i] = T(theta[i]);
+    rb.rc[i] = T(theta[N + i]);
+    rb.K[i] = T(-2.0 / (3.0 * theta[N + i]));
   }
-  // final cost
-  RobotK<T> rb = robot_of(th);
-  double lF = 0;
+  return rb;
+}
+
+__device__ inline double warp_sum_d(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kCalibThreads) k_calib_accum(RobotK<T> rb0, const T* __restrict__ U,
+                                                              const double* __restrict__ Pm, int64_t K,
+                                                              const double* theta, double* part) {
+  constexpr int D = 3 * N, NP = 2 * N, NV = calib_nv<N>();
+  __shared__ double red[kCalibThreads / 32][NV];
+  __shared__ double th[NP];
+  if (threadIdx.x < NP) th[threadIdx.x] = theta[threadIdx.x];
+  __syncthreads();
+  const RobotK<T> rb = calib_robot<T, N>(rb0, th);
+  const int64_t k = (int64_t)blockIdx.x * kCalibThreads + threadIdx.x;
+  T r[3] = {T(0), T(0), T(0)}, J[3][NP];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int x = 0; x < NP; ++x) J[a][x] = T(0);
+  if (k < K) {
+    T u[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
+    const double pm[3] = {Pm[k], Pm[K + k], Pm[2 * K + k]};
+    calib_rows<T, N>(rb, u, pm, r, J);
+  }
+  double Jd[3][NP], rd[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    rd[a] = double(r[a]);
+#pragma unroll
+    for (int x = 0; x < NP; ++x) Jd[a][x] = double(J[a][x]);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int v = 0;
+#pragma unroll
+  for (int x = 0; x < NP; ++x)
+#pragma unroll
+    for (int y = 0; y <= x; ++y, ++v) {
+      const double c = warp_sum_d(fma(Jd[2][x], Jd[2][y], fma(Jd[1][x], Jd[1][y], Jd[0][x] * Jd[0][y])));
+      if (lane == 0) red[wid][v] = c;
+    }
+#pragma unroll
+  for (int x = 0; x < NP; ++x, ++v) {
+    const double c = warp_sum_d(fma(Jd[2][x], rd[2], fma(Jd[1][x], rd[1], Jd[0][x] * rd[0])));
+    if (lane == 0) red[wid][v] = c;
+  }
+  {
+    const double c = warp_sum_d(0.5 * fma(rd[2], rd[2], fma(rd[1], rd[1], rd[0] * rd[0])));
+    if (lane == 0) red[wid][v] = c;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += kCalibThreads) {
+    double s = red[0][e];
+    for (int w = 1; w < kCalibThreads / 32; ++w) s += red[w][e];
+    part[(int64_t)blockIdx.x * NV + e] = s;
+  }
+}
+
+// Cost 1/2 sum |p(u_k; theta) - p_k|^2 (FP32 kinematics, FP64 sum) over all poses by one block.
+template <typename T, int N>
+__device__ double calib_cost_block(const RobotK<T>& rb, const T* __restrict__ U, const double* __restrict__ Pm,
+                                   int64_t K, double* red) {
+  constexpr int D = 3 * N;
+  double lF = 0.0;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
     T u[D];
+#pragma unroll
     for (int q = 0; q < D; ++q) u[q] = U[q * K + k];
     Chain<T, N> ch;
     chain_forward(rb, u, ch);
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double ra = double(ch.p[a] - T(Pm[a * K + k]));
+      const double ra = double(ch.p[a] - T(Pm[a * K + k]));
       lF += 0.5 * ra * ra;
     }
   }
-  double Fc = block_sum(lF, red);
-  if (threadIdx.x < NP) theta_io[threadIdx.x] = th[threadIdx.x];
-  if (threadIdx.x == 0) *F_out = Fc;
+  return block_sum(lF, red);
+}
+
+// state: [0] lambda, [1] nu; part: [nblk][NV]
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_calib_step(RobotK<T> rb0, const T* __restrict__ U, const double* __restrict__ Pm,
+                                                     int64_t K, int nblk, int it, double lambda0, double* theta,
+                                                     double* state, const double* part, double* hist) {
+  constexpr int NP = 2 * N, NA = NP * (NP + 1) / 2, NV = calib_nv<N>();
+  __shared__ double tot[NV], thn[NP], red[32];
+  __shared__ int ok;
+  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+    double s = part[e];
+    for (int b = 1; b < nblk; ++b) s += part[(int64_t)b * NV + e];
+    tot[e] = s;
+  }
+  __syncthreads();
+  double lam = it == 0 ? lambda0 : state[0], nu = it == 0 ? 2.0 : state[1];
+  double dl[NP], Dg[NP];
+  if (threadIdx.x == 0) {
+    double Ad[NA], iv[NP];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) Ad[a] = tot[a];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
+      Ad[tri(q, q)] += lam * Dg[q];
+    }
+    ok = cholesky_packed<NP>(Ad, iv) ? 1 : 0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) dl[q] = -tot[NA + q];
+    if (ok) {
+      cholesky_solve<NP>(Ad, iv, dl);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) thn[q] = theta[q] + dl[q];
+    }
+  }
+  __syncthreads();
+  double Fn = 0.0;
+  if (ok) Fn = calib_cost_block<T, N>(calib_robot<T, N>(rb0, thn), U, Pm, K, red);
+  if (threadIdx.x == 0) {
+    const double F = tot[NV - 1];
+    if (ok && Fn < F) {
+      double pred = 0.0;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) pred += dl[q] * (lam * Dg[q] * dl[q] - tot[NA + q]);
+      pred *= 0.5;
+      const double rho = (F - Fn) / pred, tt = 2.0 * rho - 1.0;
+      lam *= fmax(1.0 / 3.0, 1.0 - tt * tt * tt);
+      nu = 2.0;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) theta[q] = thn[q];
+    } else {
+      lam *= nu;
+      nu *= 2.0;
+    }
+    state[0] = lam;
+    state[1] = nu;
+  }
+  __syncthreads();
+  if (hist && threadIdx.x < NP) hist[(int64_t)it * NP + threadIdx.x] = theta[threadIdx.x];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_calib_final(RobotK<T> rb0, const T* __restrict__ U, const double* __restrict__ Pm,
+                                                      int64_t K, const double* theta, double* F_out) {
+  constexpr int NP = 2 * N;
+  __shared__ double th[NP], red[32];
+  if (threadIdx.x < NP) th[threadIdx.x] = theta[threadIdx.x];
+  __syncthreads();
+  const double F = calib_cost_block<T, N>(calib_robot<T, N>(rb0, th), U, Pm, K, red);
+  if (threadIdx.x == 0) *F_out = F;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -490,6 +541,7 @@ struct TrajLaunch {
   int iters;
   double lambda0;
   double *theta_dev, *F_dev, *hist_dev;
+  void* calib_ws;
   cudaStream_t stream;
 };
 
@@ -586,9 +638,24 @@ template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
 
 template <typename T, int N> cr_status calibrate_n(const TrajLaunch& l) {
   RobotK<T> rb = crh::robot_k<T>(l.robot);
-  k_calibrate<T, N><<<1, 1024, 0, l.stream>>>(rb, (const T*)l.U, l.Pm, l.K, l.iters, l.lambda0, l.theta_dev, l.F_dev,
-                                               l.hist_dev);
+  const int nblk = (int)((l.K + kCalibThreads - 1) / kCalibThreads);
+  double* state = (double*)l.calib_ws;
+  double* part = state + 2;
+  const T* U = (const T*)l.U;
+  for (int it = 0; it < l.iters; ++it) {
+    k_calib_accum<T, N><<<nblk, kCalibThreads, 0, l.stream>>>(rb, U, l.Pm, l.K, l.theta_dev, part);
+    k_calib_step<T, N><<<1, 256, 0, l.stream>>>(rb, U, l.Pm, l.K, nblk, it, l.lambda0, l.theta_dev, state, part,
+                                                 l.hist_dev);
+  }
+  k_calib_final<T, N><<<1, 256, 0, l.stream>>>(rb, U, l.Pm, l.K, l.theta_dev, l.F_dev);
   return crh::check_launch("cr_calibrate");
+}
+
+// Workspace of cr_calibrate: lambda, nu, then the per-block partial sums.
+inline size_t calibrate_ws_bytes(int n, int64_t K) {
+  const int NP = 2 * n;
+  const int64_t nblk = (K + kCalibThreads - 1) / kCalibThreads;
+  return (size_t)(2 + nblk * (NP * (NP + 1) / 2 + NP + 1)) * sizeof(double);
 }
 
 #define CR_TRAJ_DISPATCH(FN, T, l)         \

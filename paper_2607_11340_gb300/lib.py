@@ -27,7 +27,7 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_solve_ik_plain",
            "cr_poll_status", "cr_last_error_string", "cr_peak_launch", "cr_solve_ik_static",
            "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
-           "cr_calibrate", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check",
+           "cr_calibrate", "cr_calibrate_workspace_size", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check",
            "cr_batch_workspace_size", "cr_batch_plan_create", "cr_batch_plan_run", "cr_batch_plan_info",
            "cr_batch_plan_destroy", "cr_solve_batch", "cr_batch_plain_workspace_size", "cr_solve_batch_plain")
 
@@ -124,7 +124,8 @@ _SIGS = {
                       C.c_int32, C.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
     "cr_solve_path": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_path_task), C.POINTER(cr_ik_params),
                       C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
-    "cr_calibrate": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P],
+    "cr_calibrate": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P,
+                     C.c_size_t, _P],
     "cr_cost_vjp": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P, _P, _P,
                     C.c_int32, _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
@@ -162,6 +163,8 @@ def load(path: str | None = None):
         L.cr_traj_workspace_size.restype = C.c_size_t
         L.cr_path_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.c_int32, C.POINTER(cr_ik_params)]
         L.cr_path_workspace_size.restype = C.c_size_t
+        L.cr_calibrate_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64]
+        L.cr_calibrate_workspace_size.restype = C.c_size_t
         for nm in ("cr_batch_workspace_size", "cr_batch_plain_workspace_size"):
             getattr(L, nm).argtypes = [C.POINTER(cr_robot), C.POINTER(cr_batch_item), C.c_int64,
                                        C.POINTER(cr_batch_params)]
@@ -324,9 +327,14 @@ def cr_solve_path(robot, scene, task, first_ik, k_warm, k_joint, X_out, cost_out
                                 _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
-def cr_calibrate(robot, U, P_meas, theta, iters, lambda0, F_out, hist=None, stream=None):
+def cr_calibrate_workspace_size(robot, K) -> int:
+    return int(load().cr_calibrate_workspace_size(C.byref(robot), K))
+
+
+def cr_calibrate(robot, U, P_meas, theta, iters, lambda0, F_out, hist, workspace, stream=None):
     _check(load().cr_calibrate(C.byref(robot), _ptr(U), _ptr(P_meas), U.shape[-1], _ptr(theta), iters, lambda0,
-                               _ptr(F_out), _ptr(hist), _dtype_code(U), _stream(stream)))
+                               _ptr(F_out), _ptr(hist), _dtype_code(U), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def cr_cost_vjp(robot, scene, task, u, upstream, grad_u_out, grad_param_out=None, workspace=None, stream=None):

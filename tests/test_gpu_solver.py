@@ -241,6 +241,34 @@ def test_solve_ik_ragged_and_obstacles():
     assert g2["status"] & (1 << lib.CR_ENONFINITE)
 
 
+@pytest.mark.parametrize("K", [5, 10])
+def test_solve_ik_per_problem_spheres_fp64(K):
+    """Each target with its own sphere set: 5 candidates per target (one target per refine warp) and
+    10 (three targets per warp, 2 idle lanes), 30 targets (a partial last block), FP64 against the
+    oracle run target by target with that target's spheres."""
+    spec = synth.RobotSpec(L=(0.1, 0.08), rc=0.005, umax=0.01, nb=8)
+    ik = synth.IkSpec(S=40, n_final=K, k_init=12, k_final=15)
+    P, no = 30, 3
+    rbo = orc_robot(spec)
+    tg, _ = synth.ik_workload(spec, P, "pose", lambda x: O.fk(rbo, x)[0], seed=7)
+    rng = np.random.default_rng(8)
+    sph = np.concatenate([rng.uniform(-0.05, 0.05, (P, no, 2)), rng.uniform(0.05, 0.15, (P, no, 1)),
+                          rng.uniform(0.005, 0.012, (P, no, 1))], axis=2)
+    s = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, api.Scene(sph, per_problem=True), lib.CR_F64)
+    o = s.solve(targets_dev(tg))
+    torch.cuda.synchronize()
+    gu, gs = host_aos(o.u), o.success.cpu().numpy().astype(bool)
+    assert s.status() == 0
+    agree = 0
+    for p in range(P):
+        r = _oracle_solve(spec, ik, lib.CR_TASK_IK6, tg[p:p + 1], spheres=sph[p], p0=p)
+        agree += int(bool(r["success"][0]) == gs[p])
+        if r["success"][0] and gs[p]:
+            pos, rot, lim, col = O.accept(rbo, sph[p], lib.CR_TASK_IK6, tg[p:p + 1], gu[p:p + 1], ik.lim_tol)
+            assert lim[0] and col[0] and pos[0] <= ik.pos_tol
+    assert agree >= P - 1
+
+
 def test_peak_kernels_run():
     buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
     for kind in range(4):

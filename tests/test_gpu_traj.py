@@ -158,3 +158,28 @@ def test_calibration_parity_full_size(prec):
         # FP32 residuals (|r| ~ 0.5 mm out of 0.3 m) change the estimate by far less than the noise
         np.testing.assert_allclose(th, ref["theta"], rtol=2e-4)
     assert np.abs(th / true - 1).max() < 5e-3
+
+
+def test_calibration_iterates_partial_block():
+    """K = 300 poses (two full blocks of 128 and a partial one) on a 2-segment robot, FP64: every LM
+    iterate against the oracle's, and an undersized workspace is refused."""
+    spec = synth.RobotSpec(L=(0.1, 0.08), rc=0.005, umax=0.01)
+
+    def fkp(U, L, rc):
+        return O.fk(O.make_robot(list(L), list(rc), spec.umax, nb=spec.nb), U)[0]
+
+    U, Pm, true, nom = synth.calib_workload(spec, 300, fkp, seed=5)
+    ref = O.calibrate(orc_robot(spec), U, Pm, nom, 12, history=True)
+    th, F, hist = api.calibrate(spec, dev_soa(U, torch.float64), dev_soa(Pm, torch.float64), nom, iters=12,
+                                history=True)
+    np.testing.assert_allclose(hist.cpu().numpy(), ref["hist"], rtol=1e-10)
+    np.testing.assert_allclose(th.cpu().numpy(), ref["theta"], rtol=1e-10)
+    np.testing.assert_allclose(F.item(), ref["F"], rtol=1e-9)
+    robot = api.robot_struct(spec)
+    Ud, Pd = dev_soa(U, torch.float64), dev_soa(Pm, torch.float64)
+    small = torch.empty(lib.cr_calibrate_workspace_size(robot, 300) - 8, dtype=torch.uint8, device="cuda")
+    th2 = torch.as_tensor(nom, dtype=torch.float64, device="cuda").clone()
+    F2 = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(RuntimeError):
+        lib.cr_calibrate(robot, Ud, Pd, th2, 3, 1e-3, F2, None, small)
+
