@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     ap.add_argument("--items", type=int, default=synth.N_RAGGED,
                     help="items of the ragged batch (default 16384; smaller for profiling cases)")
-    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib", "ragged"],
+    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib", "ragged", "e1", "e2"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
@@ -129,12 +129,13 @@ def make_targets(torch, api, lib, spec, P, seed, device):
     return tg
 
 
-def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None):
+def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=None):
     """Oracle solves/s on host cores over a bounded contiguous sample of the targets."""
     import oracle as O
 
     O.build()
-    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius)
+    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius,
+                      lmin=spec.lmin, lmax=spec.lmax)
     W = O.make_weights(**synth.WEIGHTS.as_dict())
     threads = threads or os.cpu_count()
     cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
@@ -142,7 +143,7 @@ def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None):
                      rot_tol=ik.rot_tol, seed=ik.seed, p0=p0)
     n = max(threads, 16)
     t0 = time.perf_counter()
-    r = O.solve_ik(rb, W, None, O.IK6, tg[:n], cfg, threads=threads)
+    r = O.solve_ik(rb, W, spheres, O.IK6, tg[:n], cfg, threads=threads)
     dt = time.perf_counter() - t0
     done = n
     res = [r]
@@ -150,7 +151,7 @@ def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None):
         m = min(len(tg) - done, max(threads, int(done / dt * (budget_s - dt))))
         cfg.p0 = p0 + done
         t1 = time.perf_counter()
-        res.append(O.solve_ik(rb, W, None, O.IK6, tg[done:done + m], cfg, threads=threads))
+        res.append(O.solve_ik(rb, W, spheres, O.IK6, tg[done:done + m], cfg, threads=threads))
         dt += time.perf_counter() - t1
         done += m
     succ = np.concatenate([x["success"] for x in res])
@@ -167,7 +168,8 @@ def reference_arm(args):
 
     O.build()
     spec, ik = synth.ROBOT_3SEG, synth.IK_3SEG
-    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius)
+    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius,
+                      lmin=spec.lmin, lmax=spec.lmax)
     W = O.make_weights(**synth.WEIGHTS.as_dict())
     tg, _ = synth.ik_workload(spec, synth.P_3SEG, "pose", lambda u: O.fk(rb, u)[0], seed=0)
     threads = os.cpu_count()
@@ -271,6 +273,62 @@ def other_workload(args):
         extra = lambda: {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
                          "collision_free_rate": float(s.col_ok.float().mean()),
                          "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+        dtype = "f32"
+    elif args.workload in ("e1", "e2"):
+        # the paper's own IK benchmarks in its (theta, phi, L) parameterisation (Sec. V-B)
+        ik = synth.IK_E1
+        rbs = {}
+
+        def fkb_of(spec):
+            def fkb(q):
+                T, bb = api.fk(api.robot_struct(spec), torch.as_tensor(q.T.copy(), dtype=torch.float64, device=dev), True)
+                return T.cpu().numpy().T, bb.cpu().numpy().transpose(2, 0, 1)
+            return fkb
+
+        cases = []
+        if args.workload == "e1":
+            spec, P = synth.ROBOT_E1, synth.P_E1
+            tg, _ = synth.e1_workload(spec, P, lambda q: fkb_of(spec)(q)[0], seed=0)
+            cases.append(("3seg_ext", spec, tg, None))
+            metric = "IK solves/s, paper's arc model, 3 extendable 1 m segments, no obstacles (128 seeds -> top 8, 200 its)"
+            wl = "e1_arc_3seg_ext_1000targets_128seeds_top8_pg150_lm50"
+        else:
+            for name, spec in (("4seg_ext", synth.ROBOT_E2_EXT), ("3seg_fixed", synth.ROBOT_E2_FIXED)):
+                tg, _, sph = synth.e2_workload(spec, synth.P_E2, fkb_of(spec), seed=0)
+                cases.append((name, spec, tg, sph))
+            metric = "IK solves/s, paper's arc model, 4 extendable 1 m segments, 27-sphere lattice (128 seeds -> top 8, 200 its)"
+            wl = "e2_arc_4seg_ext_lattice27_100targets_128seeds_top8_pg150_lm50"
+        for name, spec, tg, sph in cases:
+            s_ = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, len(tg), api.Scene(sph), precision=lib.CR_F32,
+                              device=dev)
+            rbs[name] = (s_, torch.as_tensor(tg.T.copy(), dtype=torch.float64, device=dev), spec, tg, sph)
+        first = cases[0][0]
+        s, tgd = rbs[first][0], rbs[first][1]
+        fn = lambda: s.solve(tgd)
+        units, unit = len(cases[0][2]), "solves/s"
+
+        def extra():
+            out = {"success_rate": float(s.out.success.float().mean()), "pos_err_median_m": float(s.out.pos_err.median()),
+                   "rot_err_median_rad": float(s.out.rot_err.median()), "device_status": s.status()}
+            for name, (s2, tg2, spec2, tgh, sph) in rbs.items():
+                if name == first:
+                    continue
+                for _ in range(3):
+                    s2.solve(tg2)
+                med2, mean2 = time_steps(torch, lambda: s2.solve(tg2), args.steps, flush, stream)
+                out[name] = {"value": len(tgh) / (mean2 / 1e3), "unit": "solves/s", "ms_per_step": mean2,
+                             "success_rate": float(s2.out.success.float().mean())}
+            if not args.no_baseline:
+                spec1, tgh1, sph1 = rbs[first][2], rbs[first][3], rbs[first][4]
+                rate, n, cores, dt, osucc, _ = cpu_oracle_rate(tgh1, spec1, ik, budget_s=10.0, spheres=sph1)
+                gs = s.out.success[:n].cpu().numpy().astype(bool)
+                out["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                       "sample": f"first {n} targets ({dt:.1f} s on {cores} threads)"}
+                out["oracle_agreement"] = {"targets": n, "success_rate_oracle": float(osucc.mean()),
+                                           "success_rate_gpu": float(gs.mean()),
+                                           "success_flag_mismatches": int((gs != osucc).sum())}
+            return out
+
         dtype = "f32"
     elif args.workload == "ragged":
         fam = synth.ROBOT_FAMILY

@@ -63,18 +63,32 @@ typedef enum { CR_F32 = 0, CR_F64 = 1 } cr_dtype;
 #define CR_MAX_NB 64
 #define CR_MAX_SEEDS 256
 
+/* Decision variables of a segment (cr_robot.model). Three per segment in both models.
+ * CR_MODEL_TENDON: the tendon displacements u_ij = l_ij - L_i of Eq. 4; the exact inverse of Eq. 4
+ *   gives the bend (theta_i, phi_i), L_i is the robot's; bounds |u_ij| <= u_max_i, sum_j u_ij = 0.
+ * CR_MODEL_ARC: the paper's own segment configuration q_i = (theta_i, phi_i, L_i) of Sec. IV-A in
+ *   Cartesian form (theta cos phi, theta sin phi, L): the same configurations, smooth at theta = 0
+ *   where phi is undefined. L_i is free within [l_min_i, l_max_i] (extendable segments; equal bounds
+ *   pin it); bounds theta_i <= theta_max_i. Entry points that take the arc model: cr_fk,
+ *   cr_fk_jac, cr_cost_grad, cr_seeds, cr_lm_step, cr_pg_steps, cr_solve_ik (and its two stages)
+ *   for 1..4 segments; the others return CR_EINVAL for it. */
+typedef enum { CR_MODEL_TENDON = 0, CR_MODEL_ARC = 1 } cr_model;
+#define CR_MAX_SEG_ARC 4
+
 /* Robot geometry (Sec. III, Fig. 2). Host struct. */
 typedef struct {
   int32_t n;       /* segments, 1..CR_MAX_SEG */
   int32_t m;       /* tendons per segment; must be 3 */
   int32_t n_b;     /* backbone samples per segment for clearance (1..CR_MAX_NB); sample k of
                       segment i is the end of the sub-arc of fraction k / n_b, k = 1..n_b */
-  int32_t reserved;
-  double L[CR_MAX_SEG];         /* arc lengths (m) */
+  int32_t model;   /* cr_model */
+  double L[CR_MAX_SEG];         /* arc lengths (m); CR_MODEL_ARC: unused (the state holds them) */
   double r_c[CR_MAX_SEG];       /* tendon routing radii (m) */
   double u_max[CR_MAX_SEG];     /* bound |u_ij| <= u_max_i (m), Eq. ik_limits */
   double theta_max[CR_MAX_SEG]; /* bending-angle limit (rad), Eq. ik_limits */
   double r_body;                /* backbone radius added to every sphere radius (m) */
+  double l_min[CR_MAX_SEG];     /* CR_MODEL_ARC: length bounds l_min_i <= L_i <= l_max_i (m) */
+  double l_max[CR_MAX_SEG];
 } cr_robot;
 
 /* Penalty and objective weights of Eq. penalized_form, as a least-squares sum 1/2 sum r^2. */

@@ -12,12 +12,15 @@ from . import synth
 
 def robot_struct(spec: synth.RobotSpec) -> lib.cr_robot:
     r = lib.cr_robot()
-    r.n, r.m, r.n_b, r.reserved = spec.n, 3, spec.nb, 0
+    r.n, r.m, r.n_b = spec.n, 3, spec.nb
+    r.model = lib.CR_MODEL_ARC if spec.is_arc else lib.CR_MODEL_TENDON
     for i in range(spec.n):
         r.L[i] = spec.L[i]
         r.r_c[i] = spec.rc
         r.u_max[i] = spec.umax
         r.theta_max[i] = spec.thmax
+        if spec.is_arc:
+            r.l_min[i], r.l_max[i] = spec.lmin, spec.lmax
     r.r_body = spec.body_radius
     return r
 

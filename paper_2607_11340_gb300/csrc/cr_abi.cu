@@ -42,6 +42,19 @@ cr_status check_robot(const cr_robot* r) {
       return fail(CR_EINVAL, "segment %d: L, r_c, u_max and theta_max must be positive", i);
   }
   if (!(r->r_body >= 0)) return fail(CR_EINVAL, "robot.r_body must be >= 0");
+  if (r->model != CR_MODEL_TENDON && r->model != CR_MODEL_ARC)
+    return fail(CR_EINVAL, "robot.model = %d is not a cr_model", r->model);
+  if (r->model == CR_MODEL_ARC) {
+    if (r->n > CR_MAX_SEG_ARC) return fail(CR_EINVAL, "arc model: robot.n = %d above %d", r->n, CR_MAX_SEG_ARC);
+    for (int i = 0; i < r->n; ++i)
+      if (!(r->l_min[i] > 0) || !(r->l_max[i] >= r->l_min[i]))
+        return fail(CR_EINVAL, "arc model, segment %d: need 0 < l_min <= l_max", i);
+  }
+  return CR_OK;
+}
+
+cr_status check_tendon_model(const cr_robot* r, const char* what) {
+  if (r && r->model != CR_MODEL_TENDON) return fail(CR_EINVAL, "%s takes the tendon model only", what);
   return CR_OK;
 }
 

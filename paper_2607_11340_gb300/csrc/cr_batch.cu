@@ -117,7 +117,7 @@ cr_status check_items(const cr_robot* family, const cr_batch_item* items, int64_
   }
   cr_robot r = *family;
   r.n = nmax;
-  if ((st = check_robot(&r))) return st;
+  if ((st = check_robot(&r)) || (st = check_tendon_model(&r, "the ragged batch"))) return st;
   const cr_ik_params& p = prm->ik;
   if (p.n_final < 1 || p.n_final > 32 || p.k_init < 0 || p.k_final < 0 || prm->k_warm < 0 || prm->k_joint < 0)
     return fail(CR_EINVAL, "batch: bad iteration counts or n_final");

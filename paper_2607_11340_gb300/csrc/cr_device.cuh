@@ -68,6 +68,7 @@ template <typename T> struct RobotK {
   int n, nb;
   T L[NMAX], K[NMAX], umax[NMAX], thmax[NMAX], rc[NMAX];
   T rbody;
+  T lmin[NMAX], lmax[NMAX];  // CR_MODEL_ARC length bounds
 };
 
 struct NmaxArr {
@@ -245,10 +246,38 @@ template <typename T> CR_HD T dot3(const T (&a)[3], const T (&b)[3]) {
 template <typename T, int N> struct Chain {
   T Rb[N][9], pb[N][3];  // base frame of every segment
   T ax[N], ay[N], x[N], s[N], c[N];
+  T L[N];                // arc lengths: the robot's (tendon model) or the state's (arc model)
   T R[9], p[3];          // tip frame
 };
 
-template <typename T, int N>
+// Bend a = (theta cos phi, theta sin phi) and length of segment i from the state (see cr_model).
+template <int MODEL, typename T, int N>
+CR_HD void segment_state(const RobotK<T>& rb, const T (&u)[3 * N], int i, T& ax, T& ay, T& L) {
+  if (MODEL == CR_MODEL_ARC) {
+    ax = u[3 * i];
+    ay = u[3 * i + 1];
+    L = u[3 * i + 2];
+  } else {
+    bend_of(rb.K[i], u[3 * i], u[3 * i + 1], u[3 * i + 2], ax, ay);
+    L = rb.L[i];
+  }
+}
+
+// State columns of segment i from the derivatives (gx, gy) with respect to its bend: the tendon
+// model maps them through the inverse of Eq. 4 (dF/du = K C^T g); the arc model's first two state
+// components are the bend itself (its third, the length, is filled by the caller).
+template <int MODEL, typename T>
+CR_HD void bend_cols(const RobotK<T>& rb, int i, T gx, T gy, T& c0, T& c1, T& c2) {
+  if (MODEL == CR_MODEL_ARC) {
+    c0 = gx;
+    c1 = gy;
+    c2 = T(0);
+  } else {
+    bend_grad_to_u(rb.K[i], gx, gy, c0, c1, c2);
+  }
+}
+
+template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 CR_HD void chain_forward(const RobotK<T>& rb, const T (&u)[3 * N], Chain<T, N>& ch) {
   T R[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
   T p[3] = {T(0), T(0), T(0)};
@@ -258,14 +287,14 @@ CR_HD void chain_forward(const RobotK<T>& rb, const T (&u)[3 * N], Chain<T, N>& 
     for (int a = 0; a < 9; ++a) ch.Rb[i][a] = R[a];
 #pragma unroll
     for (int a = 0; a < 3; ++a) ch.pb[i][a] = p[a];
-    T ax, ay;
-    bend_of(rb.K[i], u[3 * i], u[3 * i + 1], u[3 * i + 2], ax, ay);
+    T ax, ay, Li;
+    segment_state<MODEL, T, N>(rb, u, i, ax, ay, Li);
     T x = ax * ax + ay * ay;
     T s, c;
     seg_sc(x, s, c);
-    ch.ax[i] = ax; ch.ay[i] = ay; ch.x[i] = x; ch.s[i] = s; ch.c[i] = c;
+    ch.ax[i] = ax; ch.ay[i] = ay; ch.x[i] = x; ch.s[i] = s; ch.c[i] = c; ch.L[i] = Li;
     T Ri[9], di[3];
-    seg_transform(ax, ay, x, s, c, rb.L[i], Ri, di);
+    seg_transform(ax, ay, x, s, c, Li, Ri, di);
     T t[3];
     matvec(R, di, t);
     p[0] += t[0]; p[1] += t[1]; p[2] += t[2];
@@ -439,12 +468,12 @@ CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, cons
                                 uint64_t (&mask)[N]) {
   T lsum = T(0);
 #pragma unroll
-  for (int i = 0; i < N; ++i) lsum += rb.L[i];
+  for (int i = 0; i < N; ++i) lsum += ch.L[i];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     T q[3], m[3], s, c;
-    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5), q, m, s, c);
-    const T half = T(0.5) * rb.L[i];
+    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(0.5), q, m, s, c);
+    const T half = T(0.5) * ch.L[i];
     uint64_t mk = 0;
     for (int j = 0; j < cnt; ++j) {
       const Sphere4<T> S = sph[j0 + j];
@@ -465,11 +494,11 @@ CR_HD uint64_t group_sphere_mask(const RobotK<T>& rb, const Chain<T, N>& ch, int
                                  const Sphere4<T>* sph, int j0, uint64_t cand) {
   T lsum = T(0);
 #pragma unroll
-  for (int l = 0; l < N; ++l) lsum += rb.L[l];
+  for (int l = 0; l < N; ++l) lsum += ch.L[l];
   const T inb = c_div(T(1), T(rb.nb));
   T q[3], m[3], s, c;
-  backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5) * T(k0 + k1) * inb, q, m, s, c);
-  const T rad = T(0.5) * T(k1 - k0) * rb.L[i] * inb;
+  backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(0.5) * T(k0 + k1) * inb, q, m, s, c);
+  const T rad = T(0.5) * T(k1 - k0) * ch.L[i] * inb;
   uint64_t out = 0;
   for (uint64_t b = cand; b; b &= b - 1) {
     const int jj = __ffsll((long long)b) - 1;
@@ -489,12 +518,12 @@ __device__ void warp_segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>
   const int lane = threadIdx.x & 31;
   T lsum = T(0);
 #pragma unroll
-  for (int i = 0; i < N; ++i) lsum += rb.L[i];
+  for (int i = 0; i < N; ++i) lsum += ch.L[i];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     T q[3], m[3], s, c;
-    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(0.5), q, m, s, c);
-    const T half = T(0.5) * rb.L[i];
+    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(0.5), q, m, s, c);
+    const T half = T(0.5) * ch.L[i];
     uint64_t mk = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -526,10 +555,10 @@ template <typename T, int N> struct StateAgg {
 // BOX = false leaves out the bound and sum-zero rows: on the feasible set {|u_j| <= b, sum u_j = 0}
 // they vanish, so callers whose state was just projected onto it skip them (in FP32 the sum-zero
 // row would only add the rounding residue of the projection).
-template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true>
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
 CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T>* sph, int no,
                       const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out) {
-  chain_forward(rb, u, ch);
+  chain_forward<T, N, MODEL>(rb, u, ch);
   T coll = T(0);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
@@ -552,7 +581,7 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
       for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
-        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sg, q, wp, s, c);
         T gw[3] = {T(0), T(0), T(0)};
         bool hit = false;
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
@@ -582,10 +611,10 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
           T s3, cp;
           seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
           T dd[2][3], wl[2][3];
-          seg_local_derivs(axs, ays, s, c, s3, cp, sg * rb.L[i], dd, wl);
+          seg_local_derivs(axs, ays, s, c, s3, cp, sg * ch.L[i], dd, wl);
           ag.Dx[i] += sg * (gl[0] * dd[0][0] + gl[1] * dd[0][1] + gl[2] * dd[0][2]);
           ag.Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
-          if (PGRAD) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / rb.L[i];
+          if (PGRAD || MODEL == CR_MODEL_ARC) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / ch.L[i];
         }
       }
       }
@@ -596,7 +625,11 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
   T F = coll;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    if (BOX) {
+    if (BOX && MODEL == CR_MODEL_ARC) {  // length bounds of the extendable segment
+      T hi = ch.L[i] - rb.lmax[i], lo = rb.lmin[i] - ch.L[i];
+      if (hi > T(0)) F += T(0.5) * w.rho_b * hi * hi;
+      if (lo > T(0)) F += T(0.5) * w.rho_b * lo * lo;
+    } else if (BOX) {
       T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
       F += T(0.5) * w.rho_eq * su * su;
 #pragma unroll
@@ -617,8 +650,10 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
 // Reverse phase: given dF/dp at the tip (Ftip) and the world moment of dF/d(tip rotation) (Rtip),
 // sweep the segments from the tip to the base: the force and moment of everything downstream of
 // segment i act on (ax_i, ay_i) through the segment's local derivatives. Adds the penalty gradients
-// and writes dF/du (and dF/dL, dF/dr_c when PGRAD). BOX as in state_forward.
-template <typename T, int N, bool PGRAD, bool BOX = true>
+// and writes dF/du (and dF/dL, dF/dr_c when PGRAD). BOX as in state_forward. In the arc model the
+// state's own lengths take the place of dF/du_i2 (dF/dL_i: everything beyond the segment's end moves
+// with d_i, its own samples scale with L_i).
+template <typename T, int N, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
 CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)[3 * N], const Chain<T, N>& ch,
                          const StateAgg<T, N>& ag, const T (&Ftip)[3], const T (&Rtip)[3], T (&gu)[3 * N], T* gL,
                          T* grc) {
@@ -643,7 +678,7 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     // with Fa = a . Fl_xy, Ma = a . Ml_xy and cf = cp Fa + sp Fl_z,
     // gx = L (c Fl_x + 2 ax cf) + Ml_y - s3 ay Ma - c ay Ml_z,
     // gy = L (c Fl_y + 2 ay cf) - Ml_x + s3 ax Ma + c ax Ml_z.
-    const T ax = ch.ax[i], ay = ch.ay[i], cc = ch.c[i], L = rb.L[i];
+    const T ax = ch.ax[i], ay = ch.ay[i], cc = ch.c[i], L = ch.L[i];
     T sp = T(0.5) * (s3 - cc);
     T Fa = ax * Fl[0] + ay * Fl[1], Ma = ax * Ml[0] + ay * Ml[1];
     T cf = cp * Fa + sp * Fl[2];
@@ -656,9 +691,19 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
       gy += f * ch.ay[i];
     }
     T g0, g1, g2;
-    bend_grad_to_u(rb.K[i], gx, gy, g0, g1, g2);
+    bend_cols<MODEL>(rb, i, gx, gy, g0, g1, g2);
     T gj[3] = {g0, g1, g2};
-    if (BOX) {
+    if (MODEL == CR_MODEL_ARC) {
+      const T di[3] = {ch.L[i] * ch.c[i] * ch.ax[i], ch.L[i] * ch.c[i] * ch.ay[i], ch.L[i] * ch.s[i]};
+      T gl = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i] + ag.DL[i];
+      if (BOX) {
+        T hi = ch.L[i] - rb.lmax[i], lo = rb.lmin[i] - ch.L[i];
+        gl += (hi > T(0) ? w.rho_b * hi : T(0)) - (lo > T(0) ? w.rho_b * lo : T(0));
+      }
+      gu[3 * i] = gj[0];
+      gu[3 * i + 1] = gj[1];
+      gu[3 * i + 2] = gl;
+    } else if (BOX) {
       T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
       T geq = w.rho_eq * su;
 #pragma unroll
@@ -674,8 +719,8 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     }
     if (PGRAD) {
       // dF/dL_i: translation d_i = L (...) scales with L; own samples q scale with L too
-      T di[3] = {rb.L[i] * ch.c[i] * ch.ax[i], rb.L[i] * ch.c[i] * ch.ay[i], rb.L[i] * ch.s[i]};
-      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / rb.L[i] + ag.DL[i];
+      T di[3] = {ch.L[i] * ch.c[i] * ch.ax[i], ch.L[i] * ch.c[i] * ch.ay[i], ch.L[i] * ch.s[i]};
+      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i] + ag.DL[i];
       // dF/dr_c,i: a = K(...) with K = -2/(3 r_c) so da/dr_c = -a / r_c
       grc[i] = -(ch.ax[i] * gx + ch.ay[i] * gy) / rb.rc[i];
     }
@@ -707,20 +752,20 @@ CR_HD void pose_tip_force(int kind, const WeightsK<T>& w, const TargetK<T>& tg, 
 }
 
 // Cost (and adjoint) of an IK state: the two phases around the pose rows. BOX as in state_forward.
-template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true>
+template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
 CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                 const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
                 T* coll_out) {
   Chain<T, N> ch;
   StateAgg<T, N> ag;
-  T F = state_forward<T, N, OBST, GRAD, PGRAD, BOX>(rb, w, sph, no, u, ch, ag, coll_out);
+  T F = state_forward<T, N, OBST, GRAD, PGRAD, BOX, MODEL>(rb, w, sph, no, u, ch, ag, coll_out);
   T r[6], e[3], ang, sn, cs;
   pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
   F += T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
   if (!GRAD) return F;
   T Ftip[3], Rtip[3];
   pose_tip_force(kind, w, tg, ch.R, r, e, Ftip, Rtip);
-  state_reverse<T, N, PGRAD, BOX>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
+  state_reverse<T, N, PGRAD, BOX, MODEL>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
   return F;
 }
 
@@ -735,7 +780,7 @@ CR_HD void segment_twists(const RobotK<T>& rb, const Chain<T, N>& ch, T (&tv)[N]
     T s3, cp;
     seg_deriv(ch.x[i], ch.s[i], ch.c[i], s3, cp);
     T dd[2][3], wl[2][3];
-    seg_local_derivs(ch.ax[i], ch.ay[i], ch.s[i], ch.c[i], s3, cp, rb.L[i], dd, wl);
+    seg_local_derivs(ch.ax[i], ch.ay[i], ch.s[i], ch.c[i], s3, cp, ch.L[i], dd, wl);
     T Pend[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) Pend[a] = (i == N - 1) ? ch.p[a] : ch.pb[(i + 1 < N) ? i + 1 : i][a];
@@ -755,8 +800,16 @@ CR_HD void segment_twists(const RobotK<T>& rb, const Chain<T, N>& ch, T (&tv)[N]
   }
 }
 
-// Tip Jacobian in u-space: Jp[a][q] = dp_a/du_q, Jw[a][q] = world angular velocity.
+// Arc model: translation of everything beyond segment i per unit length, Rb_i (c a_x, c a_y, s)
+// (d_i is proportional to L_i; the segment's rotation does not depend on it).
 template <typename T, int N>
+CR_HD void length_dir(const Chain<T, N>& ch, int i, T (&v)[3]) {
+  const T d[3] = {ch.c[i] * ch.ax[i], ch.c[i] * ch.ay[i], ch.s[i]};
+  matvec(ch.Rb[i], d, v);
+}
+
+// Tip Jacobian in state space: Jp[a][q] = dp_a/du_q, Jw[a][q] = world angular velocity.
+template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3 * N], T (&Jw)[3][3 * N]) {
   T tv[N][2][3], tw[N][2][3];
   segment_twists(rb, ch, tv, tw);
@@ -775,8 +828,14 @@ CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      bend_grad_to_u(rb.K[i], jp[0][a], jp[1][a], Jp[a][3 * i], Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
-      bend_grad_to_u(rb.K[i], jw[0][a], jw[1][a], Jw[a][3 * i], Jw[a][3 * i + 1], Jw[a][3 * i + 2]);
+      bend_cols<MODEL>(rb, i, jp[0][a], jp[1][a], Jp[a][3 * i], Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
+      bend_cols<MODEL>(rb, i, jw[0][a], jw[1][a], Jw[a][3 * i], Jw[a][3 * i + 1], Jw[a][3 * i + 2]);
+    }
+    if (MODEL == CR_MODEL_ARC) {
+      T v[3];
+      length_dir(ch, i, v);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Jp[a][3 * i + 2] = v[a];
     }
   }
 }
@@ -799,7 +858,7 @@ CR_HD void rank1(AArr&& A, TA (&g)[D], const T (&j)[D], T r) {
   }
 }
 
-template <typename T, typename TA, int N, bool OBST, typename AArr>
+template <typename T, typename TA, int N, bool OBST, int MODEL = CR_MODEL_TENDON, typename AArr>
 CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                        const Sphere4<T>* sph, int no, const T (&u)[3 * N], AArr&& A, TA (&g)[3 * N]) {
   constexpr int D = 3 * N;
@@ -808,7 +867,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 #pragma unroll
   for (int a = 0; a < D; ++a) g[a] = TA(0);
   Chain<T, N> ch;
-  chain_forward(rb, u, ch);
+  chain_forward<T, N, MODEL>(rb, u, ch);
   T r[6], e[3], ang, sn, cs;
   pose_rows(kind, w, tg, ch.R, ch.p, r, e, ang, sn, cs);
   T F = T(0.5) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
@@ -823,10 +882,19 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
       T wp0[3], wp1[3];
       cross(tw[i][0], ch.p, wp0);
       cross(tw[i][1], ch.p, wp1);
-      bend_grad_to_u(rb.K[i], tv[i][0][a] + wp0[a], tv[i][1][a] + wp1[a], Jp[a][3 * i],
-                     Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
-      bend_grad_to_u(rb.K[i], tw[i][0][a], tw[i][1][a], Jw[a][3 * i], Jw[a][3 * i + 1],
-                     Jw[a][3 * i + 2]);
+      bend_cols<MODEL>(rb, i, tv[i][0][a] + wp0[a], tv[i][1][a] + wp1[a], Jp[a][3 * i],
+                       Jp[a][3 * i + 1], Jp[a][3 * i + 2]);
+      bend_cols<MODEL>(rb, i, tw[i][0][a], tw[i][1][a], Jw[a][3 * i], Jw[a][3 * i + 1],
+                       Jw[a][3 * i + 2]);
+    }
+  }
+  T ldir[N][3];  // arc model: d(point beyond segment i) / dL_i
+  if (MODEL == CR_MODEL_ARC) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      length_dir(ch, i, ldir[i]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Jp[a][3 * i + 2] = ldir[i][a];
     }
   }
   // position rows
@@ -872,17 +940,24 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
   // bounds (single-entry rows), sum-zero (segment block of ones), curvature (segment rank-1)
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
-    F += T(0.5) * w.rho_eq * su * su;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      int q = 3 * i + j;
-      g[q] += TA(w.rho_eq * su);
-#pragma unroll
-      for (int j2 = 0; j2 <= j; ++j2) A[tri(q, 3 * i + j2)] += TA(w.rho_eq);
-      T hi = u[q] - rb.umax[i], lo = -rb.umax[i] - u[q];
+    if (MODEL == CR_MODEL_ARC) {  // length bounds: single-entry rows on the length column
+      const int q = 3 * i + 2;
+      T hi = ch.L[i] - rb.lmax[i], lo = rb.lmin[i] - ch.L[i];
       if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; g[q] += TA(w.rho_b * hi); A[tri(q, q)] += TA(w.rho_b); }
       if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; g[q] -= TA(w.rho_b * lo); A[tri(q, q)] += TA(w.rho_b); }
+    } else {
+      T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+      F += T(0.5) * w.rho_eq * su * su;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        int q = 3 * i + j;
+        g[q] += TA(w.rho_eq * su);
+#pragma unroll
+        for (int j2 = 0; j2 <= j; ++j2) A[tri(q, 3 * i + j2)] += TA(w.rho_eq);
+        T hi = u[q] - rb.umax[i], lo = -rb.umax[i] - u[q];
+        if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; g[q] += TA(w.rho_b * hi); A[tri(q, q)] += TA(w.rho_b); }
+        if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; g[q] -= TA(w.rho_b * lo); A[tri(q, q)] += TA(w.rho_b); }
+      }
     }
     if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T th = c_sqrt(ch.x[i]);
@@ -890,7 +965,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
       F += T(0.5) * w.rho_k * vk * vk;
       T jx = w.sk * ch.ax[i] / th, jy = w.sk * ch.ay[i] / th;
       T j0, j1, j2;
-      bend_grad_to_u(rb.K[i], jx, jy, j0, j1, j2);
+      bend_cols<MODEL>(rb, i, jx, jy, j0, j1, j2);
       T jj[3] = {j0, j1, j2};
       T rr = w.sk * vk;
 #pragma unroll
@@ -916,7 +991,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
       for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
         T q[3], wp[3], s, c;
-        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], sg, q, wp, s, c);
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sg, q, wp, s, c);
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
           Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
@@ -934,8 +1009,10 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 #pragma unroll
           for (int l = 0; l < N; ++l) {
             if (l > i) break;
-            T ga[2];
+            T ga[2], gl = T(0);
             if (l < i) {
+              if (MODEL == CR_MODEL_ARC)
+                gl = -w.sc * (nh[0] * ldir[l][0] + nh[1] * ldir[l][1] + nh[2] * ldir[l][2]);
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk) {
                 T wx[3];
@@ -947,14 +1024,17 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
               T s3, cp;
               seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
               T dd[2][3], wl[2][3];
-              seg_local_derivs(sg * ch.ax[i], sg * ch.ay[i], s, c, s3, cp, sg * rb.L[i], dd, wl);
+              seg_local_derivs(sg * ch.ax[i], sg * ch.ay[i], s, c, s3, cp, sg * ch.L[i], dd, wl);
               T nl[3];
               matTvec(ch.Rb[i], nh, nl);
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk)
                 ga[kk] = -w.sc * sg * (nl[0] * dd[kk][0] + nl[1] * dd[kk][1] + nl[2] * dd[kk][2]);
+              if (MODEL == CR_MODEL_ARC)  // the own sample q scales with L_i
+                gl = -w.sc * (nl[0] * q[0] + nl[1] * q[1] + nl[2] * q[2]) / ch.L[i];
             }
-            bend_grad_to_u(rb.K[l], ga[0], ga[1], jr[3 * l], jr[3 * l + 1], jr[3 * l + 2]);
+            bend_cols<MODEL>(rb, l, ga[0], ga[1], jr[3 * l], jr[3 * l + 1], jr[3 * l + 2]);
+            if (MODEL == CR_MODEL_ARC) jr[3 * l + 2] = gl;
           }
           rank1<TA, D>(A, g, jr, rr);
         }
@@ -1068,6 +1148,29 @@ template <typename T> CR_HD void project3(T v0, T v1, T v2, T b, T& u0, T& u1, T
   u2 = clampb(v2 - tau, b);
 }
 
+// Arc model: projection onto {theta <= theta_max} x [l_min, l_max] (a disk times an interval, each
+// factor on its own): the bend scaled back radially onto the disk, the length clamped.
+template <typename T>
+CR_HD void project_arc(T v0, T v1, T v2, T thmax, T lmin, T lmax, T& u0, T& u1, T& u2) {
+  const T r2 = v0 * v0 + v1 * v1;
+  const T f = r2 > thmax * thmax ? thmax / c_sqrt(r2) : T(1);
+  u0 = v0 * f;
+  u1 = v1 * f;
+  u2 = c_min(lmax, c_max(lmin, v2));
+}
+
+template <int MODEL, typename T, int N>
+CR_HD void project_state(const RobotK<T>& rb, const T (&v)[3 * N], T (&u)[3 * N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (MODEL == CR_MODEL_ARC)
+      project_arc(v[3 * i], v[3 * i + 1], v[3 * i + 2], rb.thmax[i], rb.lmin[i], rb.lmax[i], u[3 * i], u[3 * i + 1],
+                  u[3 * i + 2]);
+    else
+      project3(v[3 * i], v[3 * i + 1], v[3 * i + 2], rb.umax[i], u[3 * i], u[3 * i + 1], u[3 * i + 2]);
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Counter-based seeds: SplitMix64 (Steele, Lea, Flood 2014), output k from state s0 is
 // mix(s0 + k * 0x9E3779B97F4A7C15). A seed is uniform on each segment's hexagon: rhombus
@@ -1124,11 +1227,65 @@ CR_HD void draw_seed(uint64_t key, uint64_t p, uint64_t s, int attempt, const do
   }
 }
 
-// Does any backbone sample of state u come within reach of a sphere?
+// Bounds of the seed draws, FP64: the tendon model's u_max, the arc model's theta_max and lengths.
+struct SeedBox {
+  double umax[NMAX], thmax[NMAX], lmin[NMAX], lmax[NMAX];
+};
+
+// Arc-model seed (see cr_model): L_i uniform on [l_min, l_max] (draw 0); the bend uniform on the disk
+// of radius theta_max by rejection from the enclosing square, try t = 0..7 taking the square's point
+// from draws 1 and 2 at counters offset by t 2^48 (beyond every draw counter of problems p < 2^24);
+// if no try falls inside, the last is scaled onto the circle. FP64 with explicit roundings (no
+// contraction), bitwise reproducible against a CPU double implementation of the same steps.
 template <typename T, int N>
+CR_HD void draw_seed_arc(uint64_t key, uint64_t p, uint64_t s, int attempt, const SeedBox& bx, T (&u)[3 * N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const double th = bx.thmax[i], th2 = __dmul_rn(th, th);
+    const double UL = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 0)));
+    double x = 0.0, y = 0.0;
+    bool in = false;
+    for (uint64_t t = 0; t < 8 && !in; ++t) {
+      const double X = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 1) + (t << 48)));
+      const double Y = u01(splitmix64_at(key, seed_counter(p, s, attempt, i, 2) + (t << 48)));
+      x = __dmul_rn(__dsub_rn(__dmul_rn(2.0, X), 1.0), th);
+      y = __dmul_rn(__dsub_rn(__dmul_rn(2.0, Y), 1.0), th);
+      in = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)) <= th2;
+    }
+    if (!in) {
+      const double f = __ddiv_rn(th, __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+      x = __dmul_rn(x, f);
+      y = __dmul_rn(y, f);
+    }
+    u[3 * i] = T(x);
+    u[3 * i + 1] = T(y);
+    u[3 * i + 2] = T(__dadd_rn(bx.lmin[i], __dmul_rn(UL, __dsub_rn(bx.lmax[i], bx.lmin[i]))));
+  }
+}
+
+inline SeedBox seed_box(const cr_robot& r) {
+  SeedBox b;
+  for (int i = 0; i < NMAX; ++i) {
+    const bool on = i < r.n;
+    b.umax[i] = on ? r.u_max[i] : 0.0;
+    b.thmax[i] = on ? r.theta_max[i] : 0.0;
+    b.lmin[i] = on && r.model == CR_MODEL_ARC ? r.l_min[i] : 0.0;
+    b.lmax[i] = on && r.model == CR_MODEL_ARC ? r.l_max[i] : 0.0;
+  }
+  return b;
+}
+
+template <int MODEL, typename T, int N>
+CR_HD void draw_seed_m(uint64_t key, uint64_t p, uint64_t s, int attempt, const SeedBox& bx, T (&u)[3 * N]) {
+  if (MODEL == CR_MODEL_ARC) draw_seed_arc<T, N>(key, p, s, attempt, bx, u);
+  else draw_seed<T, N>(key, p, s, attempt, bx.umax, u);
+}
+
+// Does any backbone sample of state u come within reach of a sphere?
+template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, const T (&u)[3 * N]) {
   Chain<T, N> ch;
-  chain_forward(rb, u, ch);
+  chain_forward<T, N, MODEL>(rb, u, ch);
   const T inb = T(1) / T(rb.nb);
   for (int j0 = 0; j0 < no; j0 += 64) {
     uint64_t mk[N];
@@ -1141,7 +1298,7 @@ CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, co
       if (!gm) continue;
       for (int k = k0; k <= k1; ++k) {
         T q[3], wp[3], s, c;
-        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, wp, s, c);
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(k) * inb, q, wp, s, c);
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
           Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;

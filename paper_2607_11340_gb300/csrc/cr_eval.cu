@@ -82,8 +82,8 @@ cr_status cr_cost_vjp(const cr_robot* robot, const cr_scene* scene, const cr_tas
                       const void* upstream, void* grad_u_out, double* grad_param_out, void* workspace, int32_t dtype,
                       cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene_shared(scene)) || (st = check_task(task, B)) ||
-      (st = check_dtype(dtype)))
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "cr_cost_vjp")) ||
+      (st = check_scene_shared(scene)) || (st = check_task(task, B)) || (st = check_dtype(dtype)))
     return st;
   if (B < 0) return fail(CR_EINVAL, "cr_cost_vjp: B < 0");
   if (B == 0) return CR_OK;

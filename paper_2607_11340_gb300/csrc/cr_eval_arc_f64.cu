@@ -1,0 +1,5 @@
+// Arc-model (double) instantiation of the kinematics / cost kernels, 1..4 segments.
+#include "cr_eval_impl.cuh"
+namespace crk {
+CR_EVAL_ARC_INSTANTIATE(, double)
+}

@@ -1,5 +1,6 @@
 // FP64 instantiation of the kinematics / cost kernels.
 #include "cr_eval_impl.cuh"
 namespace crk {
+CR_EVAL_ARC_INSTANTIATE(extern, double)
 CR_EVAL_INSTANTIATE(, double)
 }

@@ -7,7 +7,7 @@
 
 namespace crk {
 
-template <typename T, int N>
+template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_fk(RobotK<T> rb, const T* __restrict__ u, int64_t B,
                                              T* __restrict__ Tout, T* __restrict__ bb) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(128) k_fk(RobotK<T> rb, const T* __restrict__ 
 #pragma unroll
   for (int q = 0; q < 3 * N; ++q) uu[q] = u[q * B + b];
   Chain<T, N> ch;
-  chain_forward(rb, uu, ch);
+  chain_forward<T, N, MODEL>(rb, uu, ch);
 #pragma unroll
   for (int a = 0; a < 9; ++a) Tout[a * B + b] = ch.R[a];
 #pragma unroll
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(128) k_fk(RobotK<T> rb, const T* __restrict__ 
     for (int i = 0; i < N; ++i)
       for (int k = 1; k <= rb.nb; ++k) {
         T q[3], w[3], s, c;
-        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], T(k) * inb, q, w, s, c);
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(k) * inb, q, w, s, c);
         int64_t row = (int64_t)(i * rb.nb + (k - 1)) * 3;
         bb[(row + 0) * B + b] = w[0];
         bb[(row + 1) * B + b] = w[1];
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) k_fk(RobotK<T> rb, const T* __restrict__ 
   }
 }
 
-template <typename T, int N>
+template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_fk_jac(RobotK<T> rb, const T* __restrict__ u, int64_t B,
                                                  T* __restrict__ J) {
   constexpr int D = 3 * N;
@@ -46,9 +46,9 @@ __global__ void __launch_bounds__(128) k_fk_jac(RobotK<T> rb, const T* __restric
 #pragma unroll
   for (int q = 0; q < D; ++q) uu[q] = u[q * B + b];
   Chain<T, N> ch;
-  chain_forward(rb, uu, ch);
+  chain_forward<T, N, MODEL>(rb, uu, ch);
   T Jp[3][D], Jw[3][D];
-  tip_jacobian(rb, ch, Jp, Jw);
+  tip_jacobian<T, N, MODEL>(rb, ch, Jp, Jw);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_fk_jac(RobotK<T> rb, const T* __restric
 }
 
 // MODE 0: cost only; 1: cost + dF/du; 2: cost + dF/du + dF/d(L, r_c)
-template <typename T, int N, bool OBST, int MODE>
+template <typename T, int N, bool OBST, int MODE, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, int kind,
                                                     const double* __restrict__ targets, int64_t P,
                                                     int S, const double* __restrict__ spheres, int no,
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, 
   for (int q = 0; q < D; ++q) uu[q] = u[q * B + b];
   TargetK<T> tg = load_target<T>(targets, P, b / S, kind);
   T g[D], gL[N], grc[N], cl;
-  T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2)>(rb, w, kind, tg, sph, no, uu, g, gL, grc, &cl);
+  T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2), true, MODEL>(rb, w, kind, tg, sph, no, uu, g, gL, grc, &cl);
   if (cost) cost[b] = F;
   if (coll) coll[b] = cl;
   const T up = upstream ? upstream[b] : T(1);  // vector-Jacobian product weight
@@ -134,15 +134,15 @@ template <typename T> cr_status launch_reduce_rows(const void* x, int64_t rows, 
 
 inline unsigned grid_of(int64_t B, int bs) { return (unsigned)((B + bs - 1) / bs); }
 
-template <typename T, int N> void fk_n(const EvalArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> void fk_n(const EvalArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
-  k_fk<T, N><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.Tout, (T*)a.bb);
+  k_fk<T, N, MODEL><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.Tout, (T*)a.bb);
 }
-template <typename T, int N> void fk_jac_n(const EvalArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> void fk_jac_n(const EvalArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
-  k_fk_jac<T, N><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.J);
+  k_fk_jac<T, N, MODEL><<<grid_of(a.B, 128), 128, 0, a.stream>>>(rb, (const T*)a.u, a.B, (T*)a.J);
 }
-template <typename T, int N> void cost_grad_n(const EvalArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> void cost_grad_n(const EvalArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   int no = a.scene.n_o;
@@ -150,7 +150,7 @@ template <typename T, int N> void cost_grad_n(const EvalArgs& a) {
   size_t sm = (size_t)no * sizeof(Sphere4<T>);
   unsigned g = grid_of(a.B, 128);
 #define CR_CG(OB, MO)                                                                              \
-  k_cost_grad<T, N, OB, MO><<<g, 128, sm, a.stream>>>(rb, w, a.task.kind, a.task.targets,          \
+  k_cost_grad<T, N, OB, MO, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.task.kind, a.task.targets,   \
                                                        a.task.n_targets, a.task.seeds_per_target,  \
                                                        a.scene.spheres, no, (const T*)a.u, a.B,    \
                                                        (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp, \
@@ -163,18 +163,37 @@ template <typename T, int N> void cost_grad_n(const EvalArgs& a) {
 #undef CR_CG
 }
 
+// The arc model's launchers (1..CR_MAX_SEG_ARC segments) live in their own translation units.
+#define CR_EVAL_ARC(FN, T, a)                  \
+  switch ((a).robot.n) {                       \
+    case 1: FN<T, 1, CR_MODEL_ARC>(a); break;  \
+    case 2: FN<T, 2, CR_MODEL_ARC>(a); break;  \
+    case 3: FN<T, 3, CR_MODEL_ARC>(a); break;  \
+    default: FN<T, 4, CR_MODEL_ARC>(a); break; \
+  }
+template <typename T> void launch_eval_arc(const EvalArgs& a, int what) {
+  if (what == 0) { CR_EVAL_ARC(fk_n, T, a) }
+  else if (what == 1) { CR_EVAL_ARC(fk_jac_n, T, a) }
+  else { CR_EVAL_ARC(cost_grad_n, T, a) }
+}
+
 template <typename T> cr_status launch_fk(const EvalArgs& a) {
-  CR_DISPATCH_NT(a.robot.n, fk_n, T, a);
+  if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 0);
+  else CR_DISPATCH_NT(a.robot.n, fk_n, T, a);
   return crh::check_launch("cr_fk");
 }
 template <typename T> cr_status launch_fk_jac(const EvalArgs& a) {
-  CR_DISPATCH_NT(a.robot.n, fk_jac_n, T, a);
+  if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 1);
+  else CR_DISPATCH_NT(a.robot.n, fk_jac_n, T, a);
   return crh::check_launch("cr_fk_jac");
 }
 template <typename T> cr_status launch_cost_grad(const EvalArgs& a) {
-  CR_DISPATCH_NT(a.robot.n, cost_grad_n, T, a);
+  if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 2);
+  else CR_DISPATCH_NT(a.robot.n, cost_grad_n, T, a);
   return crh::check_launch("cr_cost_grad");
 }
+
+#define CR_EVAL_ARC_INSTANTIATE(EXT, T) EXT template void launch_eval_arc<T>(const EvalArgs&, int);
 template <typename T>
 cr_status launch_reduce_rows(const void* x, int64_t rows, int64_t B, double* out, cudaStream_t s) {
   k_reduce_rows<T><<<(unsigned)rows, 256, 0, s>>>((const T*)x, B, out);

@@ -21,6 +21,7 @@ inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 inline size_t dsize(int32_t dtype) { return dtype == CR_F64 ? 8 : 4; }
 
 cr_status check_robot(const cr_robot* r);
+cr_status check_tendon_model(const cr_robot* r, const char* what);  // CR_EINVAL for the arc model
 cr_status check_scene(const cr_scene* s);
 cr_status check_scene_shared(const cr_scene* s);
 cr_status check_task(const cr_task* t, int64_t B);
@@ -40,6 +41,11 @@ template <typename T> crk::RobotK<T> robot_k(const cr_robot& r) {
     k.rc[i] = T(on ? r.r_c[i] : 1.0);
   }
   k.rbody = T(r.r_body);
+  for (int i = 0; i < crk::NMAX; ++i) {
+    bool on = i < r.n && r.model == CR_MODEL_ARC;
+    k.lmin[i] = T(on ? r.l_min[i] : 0.0);
+    k.lmax[i] = T(on ? r.l_max[i] : 0.0);
+  }
   return k;
 }
 

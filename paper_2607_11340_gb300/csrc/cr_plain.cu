@@ -21,11 +21,11 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
   TargetK<double> tg = load_target<double>(a.targets, a.P, p, a.kind);
   if (s < S) {
     double u[D];
-    draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.umax, u);
+    draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.box.umax, u);
     if (OBST && a.no > 0)
       for (int att = 1; att < 8; ++att) {
         if (!state_collides<double, N>(rb, sph, a.no, u)) break;
-        draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.umax, u);
+        draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box.umax, u);
       }
     for (int q = 0; q < D; ++q) U[s * D + q] = u[q];
     double g[D], coll;
@@ -132,7 +132,9 @@ extern "C" cr_status cr_solve_ik_plain(const cr_robot* robot, const cr_scene* sc
                                        double* pos_err, double* rot_err, uint8_t* success, void* workspace,
                                        size_t ws_bytes, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene))) return st;
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "cr_solve_ik_plain")) ||
+      (st = check_scene(scene)))
+    return st;
   if (!prm || !task) return fail(CR_EINVAL, "NULL params / task");
   if (prm->S < 1 || prm->S > CR_MAX_SEEDS || prm->n_final < 1 || prm->n_final > 32 || prm->n_final > prm->S ||
       prm->k_init < 0 || prm->k_final < 0)

@@ -1,0 +1,5 @@
+// Arc-model (FP64) instantiation of the solver kernels, 1..4 segments.
+#include "cr_solve_impl.cuh"
+namespace crk {
+CR_SOLVE_ARC_INSTANTIATE(, double)
+}

@@ -21,7 +21,7 @@ namespace crk {
 // (in FP32 the sum-zero row would only contribute the projection's rounding residue); the FP64 form
 // evaluates them, term by term like the FP64 definition.
 // ------------------------------------------------------------------------------------------------
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                    const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha) {
   constexpr int D = 3 * N;
@@ -29,13 +29,13 @@ CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Ta
 #pragma unroll
   for (int q = 0; q < D; ++q) gn2 += g[q] * g[q];
   T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
-  T u1[D];
+  T v[D], u1[D];
 #pragma unroll
-  for (int i = 0; i < N; ++i)
-    project3(u[3 * i] - scale * g[3 * i], u[3 * i + 1] - scale * g[3 * i + 1],
-             u[3 * i + 2] - scale * g[3 * i + 2], rb.umax[i], u1[3 * i], u1[3 * i + 1], u1[3 * i + 2]);
+  for (int q = 0; q < D; ++q) v[q] = u[q] - scale * g[q];
+  project_state<MODEL, T, N>(rb, v, u1);
   T g1[D], c1;
-  T F1 = eval_ik<T, N, OBST, true, false, (sizeof(T) == 8)>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr, &c1);
+  T F1 = eval_ik<T, N, OBST, true, false, (sizeof(T) == 8), MODEL>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr,
+                                                                   &c1);
   if (F1 < F) {
 #pragma unroll
     for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
@@ -50,7 +50,7 @@ CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Ta
 // ------------------------------------------------------------------------------------------------
 // One Levenberg-Marquardt iteration (Sec. IV-C); returns 1 if the step was accepted.
 // ------------------------------------------------------------------------------------------------
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                        const Sphere4<T>* sph, int no, T (&u)[3 * N], double& lam, double& nu, T& Fout) {
   constexpr int D = 3 * N;
@@ -59,7 +59,7 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
   T F;
   {
     T A[DD], g[D];
-    F = eval_ik_normal<T, T, N, OBST>(rb, w, kind, tg, sph, no, u, A, g);
+    F = eval_ik_normal<T, T, N, OBST, MODEL>(rb, w, kind, tg, sph, no, u, A, g);
 #pragma unroll
     for (int a = 0; a < DD; ++a) Ad[a] = double(A[a]);
 #pragma unroll
@@ -84,7 +84,8 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 #pragma unroll
   for (int q = 0; q < D; ++q) un[q] = u[q] + T(dl[q]);
   T dummy[D];
-  T Fn = eval_ik<T, N, OBST, false, false>(rb, w, kind, tg, sph, no, un, dummy, nullptr, nullptr, nullptr);
+  T Fn = eval_ik<T, N, OBST, false, false, true, MODEL>(rb, w, kind, tg, sph, no, un, dummy, nullptr, nullptr,
+                                                       nullptr);
   double pred = 0.0;
 #pragma unroll
   for (int q = 0; q < D; ++q) pred += dl[q] * (lam * Dg[q] * dl[q] - gd[q]);
@@ -189,7 +190,7 @@ template <typename T> struct IkArgs {
   int S, K, k_init, k_final;
   T alpha0, eps;
   double lambda0, lim_tol, pos_tol, rot_tol;
-  double umax[NMAX];
+  SeedBox box;        // seed bounds (FP64)
   uint64_t seed;
   int64_t p0;
   T* cand_u;          // [D][P*K] bulk precision
@@ -216,7 +217,7 @@ template <typename T> struct Stage1Smem {
   }
 };
 
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -240,16 +241,17 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
   if (s < S) {
     TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
     T u[D], g[D], coll = T(0);
-    draw_seed<T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.umax, u);
+    draw_seed_m<MODEL, T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.box, u);
     if (OBST && a.no > 0) {
       for (int att = 1; att < 8; ++att) {
-        if (!state_collides<T, N>(rb, sph, a.no, u)) break;
-        draw_seed<T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.umax, u);
+        if (!state_collides<T, N, MODEL>(rb, sph, a.no, u)) break;
+        draw_seed_m<MODEL, T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box, u);
       }
     }
-    T F = eval_ik<T, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+    T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
     T alpha = a.alpha0;
-    for (int it = 0; it < a.k_init; ++it) pg_step<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+    for (int it = 0; it < a.k_init; ++it)
+      pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
     sF[s] = float(F);
     sC[s] = float(coll);
 #pragma unroll
@@ -267,15 +269,16 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
 }
 
 // FP64 acceptance of one state: cost, pose errors, limit and clearance flags.
-template <int N, bool OBST>
+template <int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, int kind,
                          const TargetK<double>& tg, const Sphere4<double>* sph, int no,
                          const double (&u)[3 * N], double lim_tol, double& pos, double& rot,
                          unsigned char& flags) {
   double dummy[3 * N];
-  double F = eval_ik<double, N, OBST, false, false>(rb, w, kind, tg, sph, no, u, dummy, nullptr, nullptr, nullptr);
+  double F = eval_ik<double, N, OBST, false, false, true, MODEL>(rb, w, kind, tg, sph, no, u, dummy, nullptr, nullptr,
+                                                                nullptr);
   Chain<double, N> ch;
-  chain_forward(rb, u, ch);
+  chain_forward<double, N, MODEL>(rb, u, ch);
   double dx = ch.p[0] - tg.p[0], dy = ch.p[1] - tg.p[1], dz = ch.p[2] - tg.p[2];
   pos = sqrt(dx * dx + dy * dy + dz * dz);
   if (kind == CR_TASK_IK5) {
@@ -293,10 +296,14 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
   }
   bool lim = true;
   for (int i = 0; i < N; ++i) {
-    double su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
-    if (fabs(su) > lim_tol) lim = false;
-    for (int j = 0; j < 3; ++j)
-      if (fabs(u[3 * i + j]) > rb.umax[i] + lim_tol) lim = false;
+    if (MODEL == CR_MODEL_ARC) {
+      if (u[3 * i + 2] > rb.lmax[i] + lim_tol || u[3 * i + 2] < rb.lmin[i] - lim_tol) lim = false;
+    } else {
+      double su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
+      if (fabs(su) > lim_tol) lim = false;
+      for (int j = 0; j < 3; ++j)
+        if (fabs(u[3 * i + j]) > rb.umax[i] + lim_tol) lim = false;
+    }
     if (sqrt(ch.x[i]) > rb.thmax[i] + 1e-6) lim = false;
   }
   // clearance without the margin (radius r_s + r_body); the broad phase uses the larger reach
@@ -314,7 +321,7 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
           const uint64_t gm = group_sphere_mask<double, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
           for (int k = k0; k <= k1 && gm && free; ++k) {
             double q[3], wp[3], s, c;
-            backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], rb.L[i], k * inb, q, wp, s, c);
+            backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], k * inb, q, wp, s, c);
             for (uint64_t bits = gm; bits; bits &= bits - 1) {
               const int j = j0 + __ffsll((long long)bits) - 1;
               double ddx = wp[0] - sph[j].x, ddy = wp[1] - sph[j].y, ddz = wp[2] - sph[j].z;
@@ -330,7 +337,7 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
   return F;
 }
 
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
                                                     WeightsK<double> wd, IkArgs<T> a) {
   constexpr int D = 3 * N;
@@ -371,7 +378,8 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
     TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
     double lam = a.lambda0, nu = 2.0;
     T F;
-    for (int it = 0; it < a.k_final; ++it) lm_iteration<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+    for (int it = 0; it < a.k_final; ++it)
+      lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
   }
   double ud[D];
 #pragma unroll
@@ -380,7 +388,7 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
   unsigned char flags = 0;
   if (valid) {
     TargetK<double> tgd = load_target<double>(a.targets, a.P, p, a.kind);
-    F = accept_fp64<N, OBST>(rbd, wd, a.kind, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+    F = accept_fp64<N, OBST, MODEL>(rbd, wd, a.kind, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
   }
 #pragma unroll
   for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
@@ -449,7 +457,7 @@ template <typename T> struct StepArgs {
   T* F;
 };
 
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -467,10 +475,12 @@ __global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, S
   double lam = a.lam[b], nu = a.nu[b];
   int nacc = 0;
   T F = T(0);
-  for (int it = 0; it < a.iters; ++it) nacc += lm_iteration<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+  for (int it = 0; it < a.iters; ++it)
+    nacc += lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
   if (a.iters == 0 || a.F64) {
     T dummy[D];
-    F = eval_ik<T, N, OBST, false, false>(rb, w, a.kind, tg, sph, a.no, u, dummy, nullptr, nullptr, nullptr);
+    F = eval_ik<T, N, OBST, false, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, dummy, nullptr, nullptr,
+                                                       nullptr);
   }
 #pragma unroll
   for (int q = 0; q < D; ++q) a.u[q * a.B + b] = u[q];
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, S
   if (a.acc) a.acc[b] = nacc;
 }
 
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -495,9 +505,10 @@ __global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, S
 #pragma unroll
   for (int q = 0; q < D; ++q) u[q] = a.u[q * a.B + b];
   TargetK<T> tg = load_target<T>(a.targets, a.P, b / a.S, a.kind);
-  T F = eval_ik<T, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+  T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
   T alpha = a.alpha[b];
-  for (int it = 0; it < a.iters; ++it) pg_step<T, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+  for (int it = 0; it < a.iters; ++it)
+    pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
 #pragma unroll
   for (int q = 0; q < D; ++q) a.u[q * a.B + b] = u[q];
   a.alpha[b] = alpha;
@@ -505,10 +516,10 @@ __global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, S
 }
 
 // sph_pp = 0: blocks of 128 consecutive seeds; sph_pp = 1: blockIdx.y = problem, its own spheres.
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, const double* spheres, int no,
                                                 int sph_pp, uint64_t key, int64_t p0, int64_t P, int S,
-                                                NmaxArr umax, T* u_out) {
+                                                SeedBox box, T* u_out) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
@@ -522,11 +533,11 @@ __global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, cons
   if (i >= PS || (sph_pp && (int64_t)blockIdx.x * blockDim.x + threadIdx.x >= S)) return;
   const int64_t p = i / S, s = i % S;
   T u[D];
-  draw_seed<T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, 0, umax.v, u);
+  draw_seed_m<MODEL, T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, 0, box, u);
   if (OBST && no > 0) {
     for (int att = 1; att < 8; ++att) {
-      if (!state_collides<T, N>(rb, sph, no, u)) break;
-      draw_seed<T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, att, umax.v, u);
+      if (!state_collides<T, N, MODEL>(rb, sph, no, u)) break;
+      draw_seed_m<MODEL, T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, att, box, u);
     }
   }
 #pragma unroll
@@ -612,7 +623,7 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
   k.lim_tol = p.lim_tol;
   k.pos_tol = p.pos_tol;
   k.rot_tol = p.rot_tol;
-  for (int i = 0; i < NMAX; ++i) k.umax[i] = i < a.robot.n ? a.robot.u_max[i] : 0.0;
+  k.box = seed_box(a.robot);
   k.seed = p.seed;
   k.p0 = p.p0;
   k.cand_u = (T*)(ws + a.lay.cand_u);
@@ -631,7 +642,7 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
 }
 
 // which: 1 = stage one only, 2 = stage two only, 3 = both
-template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(const SolveArgs& a, int which) {
   constexpr int D = 3 * N;
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
@@ -645,11 +656,11 @@ template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which)
   cr_status st;
   if (which & 1) {
   if (no > 0) {
-    if ((st = set_smem(k_ik_stage1<T, N, true>, sm1))) return st;
-    k_ik_stage1<T, N, true><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
+    if ((st = set_smem(k_ik_stage1<T, N, true, MODEL>, sm1))) return st;
+    k_ik_stage1<T, N, true, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
   } else {
-    if ((st = set_smem(k_ik_stage1<T, N, false>, sm1))) return st;
-    k_ik_stage1<T, N, false><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
+    if ((st = set_smem(k_ik_stage1<T, N, false, MODEL>, sm1))) return st;
+    k_ik_stage1<T, N, false, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
   }
   if ((st = crh::check_launch("cr_solve_ik stage one"))) return st;
   }
@@ -672,10 +683,10 @@ template <typename T, int N> cr_status solve_ik_n(const SolveArgs& a, int which)
   unsigned g2 = k.sph_pp ? grid1(P, k.tpb) : grid1(P * k.K, 128);
   int b2 = k.sph_pp ? ((k.tpb * k.K + 31) / 32) * 32 : 128;
   if (no > 0) {
-    if ((st = set_smem(k_ik_refine<T, N, true>, sm2))) return st;
-    k_ik_refine<T, N, true><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+    if ((st = set_smem(k_ik_refine<T, N, true, MODEL>, sm2))) return st;
+    k_ik_refine<T, N, true, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   }
-  else k_ik_refine<T, N, false><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+  else k_ik_refine<T, N, false, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   if ((st = crh::check_launch("cr_solve_ik refine"))) return st;
   k_ik_argmin<N><<<grid1(P, 128), 128, 0, a.stream>>>(P, k.K, k.pos_tol, k.rot_tol, k.cand_u64, k.cand_F,
                                                       k.cand_pos, k.cand_rot, k.cand_flag, k.u_out,
@@ -703,41 +714,51 @@ template <typename T> StepArgs<T> step_args(const SolveArgs& a) {
   return k;
 }
 
-template <typename T, int N> cr_status lm_steps_n(const SolveArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status lm_steps_n(const SolveArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
   size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0) k_lm_steps<T, N, true><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
-  else k_lm_steps<T, N, false><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  if (k.no > 0) k_lm_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  else k_lm_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_lm_step");
 }
 
-template <typename T, int N> cr_status pg_steps_n(const SolveArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status pg_steps_n(const SolveArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
   size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0) k_pg_steps<T, N, true><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
-  else k_pg_steps<T, N, false><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  if (k.no > 0) k_pg_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  else k_pg_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_pg_steps");
 }
 
-template <typename T, int N> cr_status seeds_n(const SolveArgs& a) {
+template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status seeds_n(const SolveArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
-  NmaxArr um;
-  for (int i = 0; i < NMAX; ++i) um.v[i] = i < a.robot.n ? a.robot.u_max[i] : 0.0;
+  const SeedBox box = seed_box(a.robot);
   int no = a.scene.n_o;
   int pp = a.scene.per_problem ? 1 : 0;
   size_t sm = (size_t)no * sizeof(Sphere4<T>);
   dim3 g = pp ? dim3(grid1(a.S, 128), (unsigned)a.P) : dim3(grid1(a.P * a.S, 128));
-  if (no > 0) k_seeds<T, N, true><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, um, (T*)a.u);
-  else k_seeds<T, N, false><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, um, (T*)a.u);
+  if (no > 0)
+    k_seeds<T, N, true, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, box,
+                                                         (T*)a.u);
+  else
+    k_seeds<T, N, false, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, box,
+                                                          (T*)a.u);
   return crh::check_launch("cr_seeds");
 }
 
+// The arc model's launchers (1..CR_MAX_SEG_ARC segments) live in their own translation units.
+template <typename T> cr_status launch_solve_ik_arc(const SolveArgs& a, int which);
+template <typename T> cr_status launch_lm_steps_arc(const SolveArgs& a);
+template <typename T> cr_status launch_pg_steps_arc(const SolveArgs& a);
+template <typename T> cr_status launch_seeds_arc(const SolveArgs& a);
+
 template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which) {
+  if (a.robot.model == CR_MODEL_ARC) return launch_solve_ik_arc<T>(a, which);
   switch (a.robot.n) {
     case 1: return solve_ik_n<T, 1>(a, which);
     case 2: return solve_ik_n<T, 2>(a, which);
@@ -748,6 +769,7 @@ template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which) {
   }
 }
 template <typename T> cr_status launch_lm_steps(const SolveArgs& a) {
+  if (a.robot.model == CR_MODEL_ARC) return launch_lm_steps_arc<T>(a);
   switch (a.robot.n) {
     case 1: return lm_steps_n<T, 1>(a);
     case 2: return lm_steps_n<T, 2>(a);
@@ -758,6 +780,7 @@ template <typename T> cr_status launch_lm_steps(const SolveArgs& a) {
   }
 }
 template <typename T> cr_status launch_pg_steps(const SolveArgs& a) {
+  if (a.robot.model == CR_MODEL_ARC) return launch_pg_steps_arc<T>(a);
   switch (a.robot.n) {
     case 1: return pg_steps_n<T, 1>(a);
     case 2: return pg_steps_n<T, 2>(a);
@@ -768,6 +791,7 @@ template <typename T> cr_status launch_pg_steps(const SolveArgs& a) {
   }
 }
 template <typename T> cr_status launch_seeds(const SolveArgs& a) {
+  if (a.robot.model == CR_MODEL_ARC) return launch_seeds_arc<T>(a);
   switch (a.robot.n) {
     case 1: return seeds_n<T, 1>(a);
     case 2: return seeds_n<T, 2>(a);
@@ -783,6 +807,27 @@ template <typename T> cr_status launch_topk(const SolveArgs& a) {
                                                   T(a.eps), a.tk_idx);
   return crh::check_launch("cr_topk");
 }
+
+#define CR_ARC_DISPATCH(FN, T, N_, ...)                              \
+  switch (N_) {                                                      \
+    case 1: return FN<T, 1, CR_MODEL_ARC>(__VA_ARGS__);              \
+    case 2: return FN<T, 2, CR_MODEL_ARC>(__VA_ARGS__);              \
+    case 3: return FN<T, 3, CR_MODEL_ARC>(__VA_ARGS__);              \
+    default: return FN<T, 4, CR_MODEL_ARC>(__VA_ARGS__);             \
+  }
+
+template <typename T> cr_status launch_solve_ik_arc(const SolveArgs& a, int which) {
+  CR_ARC_DISPATCH(solve_ik_n, T, a.robot.n, a, which)
+}
+template <typename T> cr_status launch_lm_steps_arc(const SolveArgs& a) { CR_ARC_DISPATCH(lm_steps_n, T, a.robot.n, a) }
+template <typename T> cr_status launch_pg_steps_arc(const SolveArgs& a) { CR_ARC_DISPATCH(pg_steps_n, T, a.robot.n, a) }
+template <typename T> cr_status launch_seeds_arc(const SolveArgs& a) { CR_ARC_DISPATCH(seeds_n, T, a.robot.n, a) }
+
+#define CR_SOLVE_ARC_INSTANTIATE(EXT, T)                                \
+  EXT template cr_status launch_solve_ik_arc<T>(const SolveArgs&, int); \
+  EXT template cr_status launch_lm_steps_arc<T>(const SolveArgs&);      \
+  EXT template cr_status launch_pg_steps_arc<T>(const SolveArgs&);      \
+  EXT template cr_status launch_seeds_arc<T>(const SolveArgs&);
 
 #define CR_SOLVE_INSTANTIATE(EXT, T)                                \
   EXT template cr_status launch_solve_ik<T>(const SolveArgs&, int); \

@@ -45,7 +45,8 @@ extern "C" {
 cr_status cr_traj_cost(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task, const void* x,
                        void* cost_out, void* grad_out, const void* upstream, int32_t dtype, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_traj_task(task)) ||
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "trajectory entry points")) ||
+      (st = check_scene(scene)) || (st = check_traj_task(task)) ||
       (st = check_dtype(dtype)))
     return st;
   if (task->P == 0) return CR_OK;
@@ -75,7 +76,9 @@ cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_t
                         double* goal_pos, double* goal_rot, double* speed, double* accel, uint8_t* lim_ok,
                         uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_scene(scene)) || (st = check_traj_task(task))) return st;
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "trajectory entry points")) ||
+      (st = check_scene(scene)) || (st = check_traj_task(task)))
+    return st;
   if (!goal_ik) return fail(CR_EINVAL, "goal_ik is NULL");
   if (k_traj < 0 || !(alpha0 >= 0)) return fail(CR_EINVAL, "k_traj < 0 or alpha0 < 0");
   const int64_t P = task->P;
@@ -130,7 +133,8 @@ cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_mea
                        int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype, void* workspace,
                        size_t ws_bytes, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_dtype(dtype))) return st;
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "cr_calibrate")) || (st = check_dtype(dtype)))
+    return st;
   if (K < 1 || iters < 0 || !(lambda0 > 0)) return fail(CR_EINVAL, "cr_calibrate: K >= 1, iters >= 0, lambda0 > 0");
   if ((st = check_ptr(U, dsize(dtype), "U", true)) || (st = check_ptr(P_meas, 8, "P_meas", true)) ||
       (st = check_ptr(theta, 8, "theta", true)) || (st = check_ptr(F_out, 8, "F_out", true)) ||

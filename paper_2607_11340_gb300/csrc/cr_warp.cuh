@@ -234,7 +234,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
                               ((uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)(gml >> 32)) << 32);
           if (!um) continue;
           T q[3], wpt[3], s, c;
-          backbone_point(ch.Rb[ii], ch.pb[ii], ch.ax[ii], ch.ay[ii], ch.x[ii], rb.L[ii], T(mine ? k : 1) * inb, q,
+          backbone_point(ch.Rb[ii], ch.pb[ii], ch.ax[ii], ch.ay[ii], ch.x[ii], ch.L[ii], T(mine ? k : 1) * inb, q,
                          wpt, s, c);
           for (uint64_t bits = um; bits; bits &= bits - 1) {
             const Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
@@ -272,7 +272,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
                 seg_sc(sgk * sgk * ch.x[ii], ss, cc);
                 seg_deriv(sgk * sgk * ch.x[ii], ss, cc, s3, cp);
                 T dd[2][3], wl[2][3];
-                seg_local_derivs(sgk * ch.ax[ii], sgk * ch.ay[ii], ss, cc, s3, cp, sgk * rb.L[ii], dd, wl);
+                seg_local_derivs(sgk * ch.ax[ii], sgk * ch.ay[ii], ss, cc, s3, cp, sgk * ch.L[ii], dd, wl);
                 const T nh[3] = {nx, ny, nz};
                 T nl[3];
                 matTvec(ch.Rb[ii], nh, nl);

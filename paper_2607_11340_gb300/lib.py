@@ -39,10 +39,14 @@ class CrError(RuntimeError):
 
 
 class cr_robot(C.Structure):
-    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("n_b", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("n_b", C.c_int32), ("model", C.c_int32),
                 ("L", C.c_double * CR_MAX_SEG), ("r_c", C.c_double * CR_MAX_SEG),
                 ("u_max", C.c_double * CR_MAX_SEG), ("theta_max", C.c_double * CR_MAX_SEG),
-                ("r_body", C.c_double)]
+                ("r_body", C.c_double), ("l_min", C.c_double * CR_MAX_SEG), ("l_max", C.c_double * CR_MAX_SEG)]
+
+
+CR_MODEL_TENDON, CR_MODEL_ARC = 0, 1
+CR_MAX_SEG_ARC = 4
 
 
 class cr_weights(C.Structure):

@@ -34,6 +34,12 @@ class RobotSpec:
     nb: int = 16      # backbone samples per segment
     thmax: float = math.pi
     rbody: float | None = None  # backbone radius for clearance (defaults to rc)
+    lmin: float | None = None   # arc model (the paper's (theta, phi, L) per segment): length bounds
+    lmax: float | None = None
+
+    @property
+    def is_arc(self) -> bool:
+        return self.lmin is not None
 
     @property
     def n(self) -> int:
@@ -351,3 +357,69 @@ def ragged_workload(N: int, fk_backbone_n, seed: int = 0, items: np.ndarray | No
     sph = [spheres_clear_fast(rng, int(items[i, 4]), backbones[i], 0.02, 0.005, 0.015, clear) for i in range(N)]
     spheres = np.concatenate(sph) if sum(len(s) for s in sph) else np.zeros((0, 4))
     return items, targets, spheres, states
+
+
+# ---------------------------------------------------------------------------------------------
+# The paper's own IK benchmarks, arc model (Sec. V-B): segments of 1.0 m and radius 0.1 m,
+# theta in [0, pi], phi in [0, 2 pi], L fixed at 1.0 m or extendable in [0.5, 1.5] m, 10 backbone
+# points per segment, 128 seeds -> top 8 within a budget of 200 iterations.
+# ---------------------------------------------------------------------------------------------
+def arc_robot(n: int, extendable: bool) -> RobotSpec:
+    lo, hi = (0.5, 1.5) if extendable else (1.0, 1.0)
+    return RobotSpec(L=(1.0,) * n, rc=0.1, umax=0.01, nb=10, thmax=math.pi, rbody=0.1, lmin=lo, lmax=hi)
+
+
+ROBOT_E1 = arc_robot(3, True)
+ROBOT_E2_FIXED, ROBOT_E2_EXT = arc_robot(3, False), arc_robot(4, True)
+P_E1, P_E2 = 1000, 100
+# 200 iterations split as 150 projected-gradient steps and 50 LM iterations; the step length and the
+# near-duplicate radius are in the arc state's units (rad, m)
+IK_E1 = IkSpec(S=128, n_final=8, k_init=150, k_final=50, alpha0=0.05, dedup_eps=1e-3)
+LATTICE_R = 0.2
+
+
+def arc_states(rng: np.random.Generator, count: int, spec: RobotSpec) -> np.ndarray:
+    """Configurations uniform in the paper's parameters, theta ~ U[0, theta_max], phi ~ U[0, 2 pi),
+    L ~ U[lmin, lmax], as arc states (theta cos phi, theta sin phi, L) [count][3n]."""
+    th = rng.uniform(0.0, spec.thmax, (count, spec.n))
+    ph = rng.uniform(0.0, 2 * math.pi, (count, spec.n))
+    L = rng.uniform(spec.lmin, spec.lmax, (count, spec.n))
+    return np.stack([th * np.cos(ph), th * np.sin(ph), L], axis=2).reshape(count, 3 * spec.n)
+
+
+def lattice_spheres(radius: float = LATTICE_R) -> np.ndarray:
+    """Sec. V-B's 3 x 3 x 3 lattice of spheres of radius 0.2 m, 0.8 m apart in x and y and 1.0 m in z.
+    The paper does not place it; here it is centred on the base axis at heights 1, 2 and 3 m, so the
+    robot's straight configuration runs through its middle column. [27][4]"""
+    g = [(x, y, z, radius) for z in (1.0, 2.0, 3.0) for y in (-0.8, 0.0, 0.8) for x in (-0.8, 0.0, 0.8)]
+    return np.array(g, dtype=np.float64)
+
+
+def e1_workload(spec: RobotSpec, P: int, fk, seed: int = 0):
+    """Sec. V-B without obstacles: P full-pose targets from FK of uniform configurations.
+    ``fk(q [N][3n]) -> T [N][12]``. Returns (targets [P][7], configurations [P][3n])."""
+    rng = np.random.default_rng(seed)
+    q = arc_states(rng, P, spec)
+    return pose_targets(fk(q), "pose"), q
+
+
+def e2_workload(spec: RobotSpec, P: int, fk_backbone, seed: int = 0, weights: WeightSpec = WEIGHTS):
+    """Sec. V-B with the sphere lattice: P collision-free targets, FK of uniform configurations
+    whose backbone samples all stay r_s + r_body + delta clear of every sphere (rejection).
+    ``fk_backbone(q [N][3n]) -> (T [N][12], backbone [N][n*nb][3])``. Returns (targets [P][7],
+    configurations [P][3n], spheres [27][4])."""
+    rng = np.random.default_rng(seed)
+    sph = lattice_spheres()
+    reach = sph[:, 3] + spec.body_radius + weights.delta
+    got_T, got_q = [], []
+    while sum(len(t) for t in got_T) < P:
+        q = arc_states(rng, 4 * P, spec)
+        T, bb = fk_backbone(q)
+        d2 = ((bb[:, :, None, :] - sph[None, None, :, :3]) ** 2).sum(-1)
+        ok = (d2 >= reach[None, None, :] ** 2).all(axis=(1, 2))
+        got_T.append(T[ok])
+        got_q.append(q[ok])
+    T = np.concatenate(got_T)[:P]
+    q = np.concatenate(got_q)[:P]
+    return pose_targets(T, "pose"), q, sph
+

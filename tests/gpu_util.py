@@ -13,7 +13,7 @@ TDT = {lib.CR_F64: torch.float64, lib.CR_F32: torch.float32}
 
 def orc_robot(spec: synth.RobotSpec, thmax=None):
     return O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax if thmax is None else thmax,
-                        nb=spec.nb, rbody=spec.body_radius)
+                        nb=spec.nb, rbody=spec.body_radius, lmin=spec.lmin, lmax=spec.lmax)
 
 
 def orc_weights(w: synth.WeightSpec = synth.WEIGHTS):
