@@ -42,7 +42,7 @@ def test_struct_layout_matches_c(crlib, tmp_path):
 #include "cr.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(cr_robot), sizeof(cr_weights), sizeof(cr_scene), sizeof(cr_task), sizeof(cr_ik_params));
-  printf("%zu %zu %zu %zu\\n", offsetof(cr_robot, r_body), offsetof(cr_task, w), offsetof(cr_ik_params, seed), offsetof(cr_ik_params, precision));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(cr_robot, r_body), offsetof(cr_robot, l_max), offsetof(cr_task, w), offsetof(cr_ik_params, seed), offsetof(cr_ik_params, precision));
   return 0;
 }
 """)
@@ -51,7 +51,8 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     L = crlib
     py = [C.sizeof(L.cr_robot), C.sizeof(L.cr_weights), C.sizeof(L.cr_scene), C.sizeof(L.cr_task),
-          C.sizeof(L.cr_ik_params), L.cr_robot.r_body.offset, L.cr_task.w.offset, L.cr_ik_params.seed.offset,
+          C.sizeof(L.cr_ik_params), L.cr_robot.r_body.offset, L.cr_robot.l_max.offset, L.cr_task.w.offset,
+          L.cr_ik_params.seed.offset,
           L.cr_ik_params.precision.offset]
     assert [int(x) for x in out] == py
 
@@ -146,3 +147,39 @@ def test_batch_items_are_validated(crlib):
     assert "seeds_per_unit" in crlib.last_error()
     assert C.sizeof(crlib.cr_batch_item) == 24
     assert crlib.cr_batch_params.k_warm.offset == C.sizeof(crlib.cr_ik_params)
+
+
+def test_arc_model_is_validated(crlib):
+    """Arc model: up to CR_MAX_SEG_ARC segments, 0 < l_min <= l_max, a known model code; the entry
+    points that take the tendon model only refuse it; all before any device call."""
+    L = crlib.load()
+    dummy = C.c_void_p(256)
+
+    def arc(n=3):
+        r = _robot(crlib, n)
+        r.model = crlib.CR_MODEL_ARC
+        for i in range(n):
+            r.l_min[i], r.l_max[i] = 0.5, 1.5
+        return r
+
+    r = arc()
+    for bad in (arc(5), arc()):
+        if bad.n == 3:
+            bad.l_min[1], bad.l_max[1] = 1.0, 0.9
+        assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
+    bad = arc()
+    bad.model = 2
+    assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
+    assert "model" in crlib.last_error()
+    # tendon-only entry points
+    assert L.cr_calibrate(C.byref(r), dummy, dummy, 4, dummy, 2, 1e-3, dummy, None, 0, dummy, 1 << 20, None) \
+        == crlib.CR_EINVAL
+    assert "tendon model" in crlib.last_error()
+    w = crlib.cr_weights()
+    p = crlib.cr_batch_params()
+    p.ik.n_final, p.ik.k_init, p.ik.k_final, p.ik.lambda0 = 8, 16, 10, 1e-3
+    p.seeds_per_unit = 64
+    items = crlib._batch_items([(0, 3, 1, 64, 4)])
+    assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 1, C.byref(p), *([dummy] * 8), dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL
+    assert C.sizeof(crlib.cr_robot) == crlib.cr_robot.l_max.offset + 8 * crlib.CR_MAX_SEG
