@@ -53,9 +53,9 @@ def parse():
     return ap.parse_args()
 
 
-def load_counts():
+def load_counts(key="ik_3seg_pose"):
     with open(os.path.join(ROOT, "tests", "golden", "opcounts.json")) as f:
-        return json.load(f)["ik_3seg_pose"]
+        return json.load(f)[key]
 
 
 def measured_peaks():
@@ -310,6 +310,19 @@ def other_workload(args):
         def extra():
             out = {"success_rate": float(s.out.success.float().mean()), "pos_err_median_m": float(s.out.pos_err.median()),
                    "rot_err_median_rad": float(s.out.rot_err.median()), "device_status": s.status()}
+            if args.workload == "e1":
+                # stage one alone (seeds, PG steps, SelectTop) against the FP32 peak, as for the headline
+                s.stage1(tgd)
+                s1_med, s1_ms = time_steps(torch, lambda: s.stage1(tgd), args.steps, flush, stream)
+                c = load_counts("ik_arc_3seg_pose")
+                n_eval = units * ik.S * (ik.k_init + 1)
+                fl = c["fwd_flop"] + c["tan_flop"]
+                ach = n_eval * fl / (s1_ms / 1e3) / 1e12
+                sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+                peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+                out["roofline"] = {"bound": "alu", "kernel": "k_ik_stage1 (arc model)", "achieved": ach, "peak": peak,
+                                   "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "kernel_ms": s1_ms,
+                                   "evals_per_launch": n_eval, "flop_per_eval": fl}
             for name, (s2, tg2, spec2, tgh, sph) in rbs.items():
                 if name == first:
                     continue

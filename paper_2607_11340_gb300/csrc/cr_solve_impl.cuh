@@ -12,6 +12,7 @@
 #include <limits.h>
 
 #include "cr_host.h"
+#include "cr_warp.cuh"
 
 namespace crk {
 
@@ -398,6 +399,67 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
   a.cand_flag[c] = flags;
 }
 
+// Refine of problems with their own spheres and few candidates (K < 8): FP32 bulk, full pose,
+// tendon model. One block per target, one warp per candidate: the warp runs the LM iterations
+// cooperatively (warp_lm_step: lane q forms entry q of each residual row, the packed J^T J lives in
+// slots spread over the lanes, the backbone samples of the clearance rows are split over the lanes)
+// and solves the damped system in FP64 by the symmetric sweep of the augmented matrix (the pivots
+// of its LDL^T factorisation); the FP64 acceptance follows. With one candidate per thread a warp of
+// such a target would have K of its 32 lanes busy in both the FP32 and the FP64 work.
+template <int N>
+__global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, WeightsK<float> w, RobotK<double> rbd,
+                                                       WeightsK<double> wd, IkArgs<float> a) {
+  constexpr int D = 3 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
+  Sphere4<float>* sph = reinterpret_cast<Sphere4<float>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
+  double* scr = reinterpret_cast<double*>(smem_raw + (size_t)a.no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)));
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* col = scr + wid * 128;
+  double* colr = col + 32;
+  double* sx = colr + 32;
+  double* sdg = sx + 32;
+  const int64_t p = blockIdx.x;
+  const double* sp = a.spheres + p * a.no * 4;
+  for (int e = threadIdx.x; e < a.no; e += blockDim.x) {
+    const double* q = sp + 4 * e;
+    sphd[e] = Sphere4<double>{q[0], q[1], q[2], q[3] + rbd.rbody + wd.delta};
+    sph[e] = Sphere4<float>{float(q[0]), float(q[1]), float(q[2]), float(q[3]) + rb.rbody + w.delta};
+  }
+  __syncthreads();
+  if (wid >= a.K) return;
+  const int64_t PK = a.P * a.K;
+  const int64_t c = p * a.K + wid;
+  float u[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) u[q] = a.cand_u[q * PK + c];
+  const bool valid = c_finite(u[0]);  // the same in every lane
+  if (valid) {
+    const TargetK<float> tg = load_target<float>(a.targets, a.P, p, CR_TASK_IK6);
+    const AugSlots<D> sl = aug_slots<D>(lane);
+    double lam = a.lambda0, nu = 2.0;
+    for (int it = 0; it < a.k_final; ++it)
+      warp_lm_step<float, N, true, double>(rb, w, tg, sph, a.no, u, sl, lam, nu, col, colr, sx, sdg);
+  }
+  double ud[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) ud[q] = double(u[q]);
+  double pos = NAN, rot = NAN, F = NAN;
+  unsigned char flags = 0;
+  if (valid) {
+    const TargetK<double> tgd = load_target<double>(a.targets, a.P, p, CR_TASK_IK6);
+    F = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
+    a.cand_F[c] = F;
+    a.cand_pos[c] = pos;
+    a.cand_rot[c] = rot;
+    a.cand_flag[c] = flags;
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(128) k_ik_argmin(int64_t P, int K, double pos_tol, double rot_tol,
                                                     const double* cand_u64, const double* cand_F,
@@ -685,7 +747,17 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   // against 0.95 ms for 4096 targets x 8 candidates)
   unsigned g2 = k.sph_pp ? grid1(P, k.tpb) : grid1(P * k.K, 32);
   int b2 = k.sph_pp ? ((k.tpb * k.K + 31) / 32) * 32 : 32;
-  if (no > 0) {
+  bool warp_refine = false;
+  if constexpr (sizeof(T) == 4 && MODEL == CR_MODEL_TENDON) {
+    if (k.sph_pp && k.K < 8 && k.kind == CR_TASK_IK6) {
+      const size_t smw = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)) + (size_t)k.K * 128 * sizeof(double);
+      if ((st = set_smem(k_ik_refine_warp<N>, smw))) return st;
+      k_ik_refine_warp<N><<<(unsigned)P, 32 * k.K, smw, a.stream>>>(rb, w, rbd, wd, k);
+      warp_refine = true;
+    }
+  }
+  if (warp_refine) {
+  } else if (no > 0) {
     if ((st = set_smem(k_ik_refine<T, N, true, MODEL>, sm2))) return st;
     k_ik_refine<T, N, true, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   }

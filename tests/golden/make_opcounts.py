@@ -17,10 +17,17 @@ from paper_2607_11340_gb300 import synth  # noqa: E402
 
 
 def counts(spec, kind, n_states=64):
-    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
+    if spec.is_arc:
+        rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius,
+                          lmin=spec.lmin, lmax=spec.lmax)
+    else:
+        rb = O.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
     W = O.make_weights(**synth.WEIGHTS.as_dict())
     rng = np.random.default_rng(0)
-    u = synth.hexagon_states(rng, n_states + 1, spec.n, spec.umax)
+    if spec.is_arc:
+        u = synth.arc_states(rng, n_states + 1, spec)
+    else:
+        u = synth.hexagon_states(rng, n_states + 1, spec.n, spec.umax)
     tg = synth.pose_targets(O.fk(rb, u[:1])[0], "pose" if kind == O.IK6 else "axis")[0]
     c = np.array([O.opcount_ik(rb, W, None, kind, tg, u[1 + i]) for i in range(n_states)], dtype=float)
     m = c.mean(axis=0)  # branches (series vs closed form) make the count state-dependent
@@ -31,6 +38,7 @@ def main():
     out = {
         "ik_3seg_pose": counts(synth.ROBOT_3SEG, O.IK6),
         "ik_1seg_axis": counts(synth.ROBOT_1SEG, O.IK5),
+        "ik_arc_3seg_pose": counts(synth.ROBOT_E1, O.IK6),
     }
     path = os.path.join(HERE, "opcounts.json")
     with open(path, "w") as f:
