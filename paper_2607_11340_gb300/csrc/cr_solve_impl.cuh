@@ -414,7 +414,8 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
   Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
   Sphere4<float>* sph = reinterpret_cast<Sphere4<float>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
   double* scr = reinterpret_cast<double*>(smem_raw + (size_t)a.no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)));
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;  // blockDim = 32 K: warp wid, candidate wid
+  double* sud = scr + (size_t)a.K * 128;                       // refined states [K][D] for the acceptance
   double* col = scr + wid * 128;
   double* colr = col + 32;
   double* sx = colr + 32;
@@ -427,30 +428,38 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
     sph[e] = Sphere4<float>{float(q[0]), float(q[1]), float(q[2]), float(q[3]) + rb.rbody + w.delta};
   }
   __syncthreads();
-  if (wid >= a.K) return;
   const int64_t PK = a.P * a.K;
-  const int64_t c = p * a.K + wid;
-  float u[D];
+  {
+    const int64_t c = p * a.K + wid;
+    float u[D];
 #pragma unroll
-  for (int q = 0; q < D; ++q) u[q] = a.cand_u[q * PK + c];
-  const bool valid = c_finite(u[0]);  // the same in every lane
-  if (valid) {
-    const TargetK<float> tg = load_target<float>(a.targets, a.P, p, CR_TASK_IK6);
-    const AugSlots<D> sl = aug_slots<D>(lane);
-    double lam = a.lambda0, nu = 2.0;
-    for (int it = 0; it < a.k_final; ++it)
-      warp_lm_step<float, N, true, double>(rb, w, tg, sph, a.no, u, sl, lam, nu, col, colr, sx, sdg);
-  }
-  double ud[D];
+    for (int q = 0; q < D; ++q) u[q] = a.cand_u[q * PK + c];
+    if (c_finite(u[0])) {  // the same in every lane
+      const TargetK<float> tg = load_target<float>(a.targets, a.P, p, CR_TASK_IK6);
+      const AugSlots<D> sl = aug_slots<D>(lane);
+      double lam = a.lambda0, nu = 2.0;
+      for (int it = 0; it < a.k_final; ++it)
+        warp_lm_step<float, N, true, double>(rb, w, tg, sph, a.no, u, sl, lam, nu, col, colr, sx, sdg);
+    }
+    if (lane == 0) {
 #pragma unroll
-  for (int q = 0; q < D; ++q) ud[q] = double(u[q]);
-  double pos = NAN, rot = NAN, F = NAN;
-  unsigned char flags = 0;
-  if (valid) {
-    const TargetK<double> tgd = load_target<double>(a.targets, a.P, p, CR_TASK_IK6);
-    F = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+      for (int q = 0; q < D; ++q) sud[wid * D + q] = double(u[q]);
+    }
   }
-  if (lane == 0) {
+  __syncthreads();
+  // FP64 acceptance, one lane per candidate (the FP64 pipe charges whole warps: K lanes of one warp
+  // instead of K warps running the same check in all their lanes)
+  if (wid == 0 && lane < a.K) {
+    const int64_t c = p * a.K + lane;
+    double ud[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) ud[q] = sud[lane * D + q];
+    double pos = NAN, rot = NAN, F = NAN;
+    unsigned char flags = 0;
+    if (isfinite(ud[0])) {
+      const TargetK<double> tgd = load_target<double>(a.targets, a.P, p, CR_TASK_IK6);
+      F = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+    }
 #pragma unroll
     for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
     a.cand_F[c] = F;
@@ -750,7 +759,8 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   bool warp_refine = false;
   if constexpr (sizeof(T) == 4 && MODEL == CR_MODEL_TENDON) {
     if (k.sph_pp && k.K < 8 && k.kind == CR_TASK_IK6) {
-      const size_t smw = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)) + (size_t)k.K * 128 * sizeof(double);
+      const size_t smw = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)) +
+                         (size_t)k.K * (128 + D) * sizeof(double);
       if ((st = set_smem(k_ik_refine_warp<N>, smw))) return st;
       k_ik_refine_warp<N><<<(unsigned)P, 32 * k.K, smw, a.stream>>>(rb, w, rbd, wd, k);
       warp_refine = true;

@@ -43,14 +43,20 @@ template <typename T> __device__ T block_max(T v, T* red) {
 }
 
 // Shared buffers of one trajectory: tip positions [Tn][3], states [Tn][D], speed and acceleration
-// row derivatives [Tn][D] each, reduction scratch [32].
+// row derivatives [Tn][D] each, reduction scratch [32]; for the split evaluation (two threads per
+// state, see traj_state_eval) the second thread's clearance aggregates [Tn][8 N] and the gradient
+// handed back to it [Tn][D].
 template <typename T> struct TrajSmem {
   T* p;
   T* u;
   T* sv;
   T* sa;
   T* red;
-  __host__ __device__ static size_t bytes(int Tn, int D) { return sizeof(T) * ((size_t)Tn * (3 + 3 * D) + 32); }
+  T* xag;
+  T* xg;
+  __host__ __device__ static size_t bytes(int Tn, int D) {
+    return sizeof(T) * ((size_t)Tn * (3 + 3 * D) + 32 + (size_t)Tn * (8 * (D / 3) + D));
+  }
   __device__ void carve(unsigned char* base, int Tn, int D) {
     T* q = reinterpret_cast<T*>(base);
     p = q;
@@ -58,21 +64,50 @@ template <typename T> struct TrajSmem {
     sv = u + (size_t)Tn * D;
     sa = sv + (size_t)Tn * D;
     red = sa + (size_t)Tn * D;
+    xag = red + 32;
+    xg = xag + (size_t)Tn * 8 * (D / 3);
   }
 };
 
 // Thread t's share of the trajectory cost; with GRAD, gu = dF/du_t (zero for t = 0 and t >= Tn).
-// Every thread of the block must call it (it synchronises).
+// Every thread of the block must call it (it synchronises). Split evaluation (split = true): two
+// threads per state, each with its own part of the spheres (sph, no); the helper (aux = true) adds
+// only the clearance rows of its spheres to F and passes their force / moment aggregates to the
+// owner through shared memory, the owner runs everything else and hands the gradient back.
 template <typename T, int N, bool OBST, bool GRAD>
 __device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TrajW<T>& tw, int t, int Tn,
                              const T (&u)[3 * N], const TargetK<T>& goal, const Sphere4<T>* sph, int no,
-                             TrajSmem<T>& sm, T (&gu)[3 * N]) {
+                             TrajSmem<T>& sm, T (&gu)[3 * N], bool split = false, bool aux = false) {
   constexpr int D = 3 * N;
   const bool active = t < Tn;
   Chain<T, N> ch;
   StateAgg<T, N> ag;
   T F = T(0);
   T Ftip[3] = {T(0), T(0), T(0)}, Rtip[3] = {T(0), T(0), T(0)};
+  if (aux) {
+    if (active && t >= 1) {
+      T coll = T(0);
+      state_forward<T, N, OBST, GRAD, false>(rb, w, sph, no, u, ch, ag, &coll);
+      F = coll;
+      if (GRAD) {
+        T* x = sm.xag + (size_t)t * 8 * N;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) { x[6 * i + a] = ag.G[i][a]; x[6 * i + 3 + a] = ag.M[i][a]; }
+          x[6 * N + 2 * i] = ag.Dx[i];
+          x[6 * N + 2 * i + 1] = ag.Dy[i];
+        }
+      }
+    }
+    __syncthreads();
+    if (!GRAD) return F;
+    __syncthreads();
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < D; ++q) gu[q] = (active && t >= 1) ? sm.xg[(size_t)t * D + q] : T(0);
+    return F;
+  }
   if (active) {
     if (t == 0) {
       chain_forward(rb, u, ch);  // the start state is fixed: only its tip enters the length rows
@@ -124,6 +159,16 @@ __device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const Tr
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < D; ++q) gu[q] = T(0);
+  if (split && active && t >= 1) {  // add the helper's clearance aggregates
+    const T* x = sm.xag + (size_t)t * 8 * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { ag.G[i][a] += x[6 * i + a]; ag.M[i][a] += x[6 * i + 3 + a]; }
+      ag.Dx[i] += x[6 * N + 2 * i];
+      ag.Dy[i] += x[6 * N + 2 * i + 1];
+    }
+  }
   if (active && t >= 1) {
     // length rows (t-1, t) and (t, t+1) act on the tip of state t
 #pragma unroll
@@ -141,6 +186,13 @@ __device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const Tr
       if (t + 2 < Tn) g += sm.sa[(t + 2) * D + q];
       gu[q] += g;
     }
+  }
+  if (split) {  // hand the gradient to the helper thread of the same state
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < D; ++q) sm.xg[(size_t)t * D + q] = gu[q];
+    }
+    __syncthreads();
   }
   return F;
 }
@@ -216,7 +268,11 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t p = blockIdx.x;
-  const int t = threadIdx.x, Tn = a.Tn;
+  const int Tn = a.Tn, Wt = ((Tn + 31) / 32) * 32;
+  // split evaluation (blockDim = 2 Wt): thread t and t + Wt share state t, each with half the spheres
+  const bool split = (int)blockDim.x == 2 * Wt;
+  const bool aux = split && (int)threadIdx.x >= Wt;
+  const int t = aux ? (int)threadIdx.x - Wt : (int)threadIdx.x;
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
   Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<T>));
   size_t off = ((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15);
@@ -229,6 +285,9 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
     __syncthreads();
   }
   const bool active = t < Tn;
+  const int nh = split ? (a.no + 1) / 2 : a.no;
+  const Sphere4<T>* sph_m = aux ? sph + nh : sph;
+  const int no_m = aux ? a.no - nh : nh;
   T u[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) {
@@ -237,13 +296,14 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   }
   TargetK<T> goal = load_target<T>(a.goal, a.P, p, CR_TASK_IK6);
   T g[D];
-  T F = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u, goal, sph, a.no, sm, g), sm.red);
+  T F = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u, goal, sph_m, no_m, sm, g, split, aux),
+                  sm.red);
   T alpha = a.alpha0;
   const bool free_state = active && t >= 1;
   for (int it = 0; it < a.k_traj; ++it) {
     T gn2l = T(0);
 #pragma unroll
-    for (int q = 0; q < D; ++q) gn2l += g[q] * g[q];
+    for (int q = 0; q < D; ++q) gn2l += aux ? T(0) : g[q] * g[q];  // the helper holds a copy
     T gn2 = block_sum(gn2l, sm.red);
     T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
     T u1[D];
@@ -257,7 +317,8 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
       }
     }
     T g1[D];
-    T F1 = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u1, goal, sph, a.no, sm, g1), sm.red);
+    T F1 = block_sum(traj_state_eval<T, N, OBST, true>(rb, w, tw, t, Tn, u1, goal, sph_m, no_m, sm, g1, split, aux),
+                     sm.red);
     if (F1 < F) {
 #pragma unroll
       for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
@@ -271,25 +332,26 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   double ud[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) ud[q] = double(u[q]);
-  if (active) {
+  const bool owner = active && !aux;  // outputs and FP64 metrics from one thread per state
+  if (owner) {
 #pragma unroll
     for (int q = 0; q < D; ++q) a.X_out[q * (a.P * Tn) + p * Tn + t] = ud[q];
   }
   double pos = 0, rot = 0;
   unsigned char flags = 3;
-  if (active) {
+  if (owner) {
     TargetK<double> gd = load_target<double>(a.goal, a.P, p, CR_TASK_IK6);
     accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, gd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
   }
   // speed / acceleration ratios in FP64 over the states shared in a double buffer
   double* sd = reinterpret_cast<double*>(smem_raw + off + ((TrajSmem<T>::bytes(Tn, D) + 15) & ~size_t(15)));
   double* redd = sd + (size_t)Tn * D;
-  if (active)
+  if (owner)
 #pragma unroll
     for (int q = 0; q < D; ++q) sd[t * D + q] = ud[q];
   __syncthreads();
   double vmax_r = 0, amax_r = 0;
-  if (active && t >= 1) {
+  if (owner && t >= 1) {
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       vmax_r = fmax(vmax_r, fabs(ud[q] - sd[(t - 1) * D + q]) / a.dt_d / a.vmax_d);
@@ -301,11 +363,11 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   double ar = block_max(amax_r, redd);
   double lim = block_max(double((flags & 1) ? 0 : 1), redd);
   double col = block_max(double((flags & 2) ? 0 : 1), redd);
-  if (t == Tn - 1) {
+  if (!aux && t == Tn - 1) {
     a.goal_pos[p] = pos;
     a.goal_rot[p] = rot;
   }
-  if (t == 0) {
+  if (!aux && t == 0) {
     a.F_out[p] = double(F);
     a.speed[p] = vr;
     a.accel[p] = ar;
@@ -622,7 +684,10 @@ template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
   WeightsK<double> wd = crh::weights_k<double>(l.task.w);
   TrajW<T> tw = traj_w<T>(l.task.w);
   TrajArgs<T> a = traj_args<T>(l);
-  const int threads = ((a.Tn + 31) / 32) * 32;
+  // FP32 with spheres: two threads per state share the clearance rows (the FP64 form keeps one, its
+  // sums in the oracle's order)
+  const int Wt = ((a.Tn + 31) / 32) * 32;
+  const int threads = (sizeof(T) == 4 && a.no >= 2 && 2 * Wt <= 256) ? 2 * Wt : Wt;
   size_t sm = (((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15)) +
               ((TrajSmem<T>::bytes(a.Tn, D) + 15) & ~size_t(15)) + ((size_t)a.Tn * D + 32) * sizeof(double);
   cr_status st;
