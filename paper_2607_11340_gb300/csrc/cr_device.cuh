@@ -122,9 +122,12 @@ template <typename T> CR_HD void seg_deriv(T x, T s, T c, T& s3, T& cp) { seg_de
 // FP32: for theta <= pi the four coefficients are Taylor polynomials (no square root, sin/cos or
 // division): with y = (theta/2)^2, sinc(theta/2) = sum_k (-1)^k y^k / (2k+1)! (degree 6) and
 // cos(theta/2) = sum_k (-1)^k y^k / (2k)! (degree 7); s3 = sum_k (-1)^k x^k / (2k+3)! and
-// cp = sum_k (-1)^(k+1) (k+1) x^k / (2k+4)! (degree 8). Truncation error <= 4e-10 relative on the
-// whole range, far below FP32 rounding. Larger angles take the library path.
-constexpr float kPolyMaxX = 9.8696044f;  // pi^2
+// cp = sum_k (-1)^(k+1) (k+1) x^k / (2k+4)! (degree 8). Truncation error <= 2e-9 relative up to
+// theta^2 = 9.87 (theta <= 3.1417; 5e-11 absolute for s, which vanishes at theta = pi), far below
+// FP32 rounding. The bound sits just above pi^2 so that a
+// bend projected onto theta = pi (whose theta^2 rounds up to pi^2 (1 + 2e-7)) stays on the
+// polynomials; larger angles take the library path.
+constexpr float kPolyMaxX = 9.87f;
 
 template <> CR_HD void seg_sc<float>(float x, float& s, float& c) {
   if (x <= kPolyMaxX) {
