@@ -642,7 +642,9 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
         if (lo > T(0)) F += T(0.5) * w.rho_b * lo * lo;
       }
     }
-    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
+    // in the arc model theta <= theta_max is part of the projected set, so the curvature row too
+    // vanishes where BOX = false
+    if ((BOX || MODEL != CR_MODEL_ARC) && ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T vk = c_sqrt(ch.x[i]) - rb.thmax[i];
       F += T(0.5) * w.rho_k * vk * vk;
     }
@@ -687,7 +689,7 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     T cf = cp * Fa + sp * Fl[2];
     T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2] + ag.Dx[i];
     T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2] + ag.Dy[i];
-    if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
+    if ((BOX || MODEL != CR_MODEL_ARC) && ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T th = c_sqrt(ch.x[i]);
       T f = w.rho_k * (th - rb.thmax[i]) / th;
       gx += f * ch.ax[i];
