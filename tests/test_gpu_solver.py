@@ -241,11 +241,13 @@ def test_solve_ik_ragged_and_obstacles():
     assert g2["status"] & (1 << lib.CR_ENONFINITE)
 
 
-@pytest.mark.parametrize("K", [5, 10])
-def test_solve_ik_per_problem_spheres_fp64(K):
-    """Each target with its own sphere set: 5 candidates per target (one target per refine warp) and
-    10 (three targets per warp, 2 idle lanes), 30 targets (a partial last block), FP64 against the
-    oracle run target by target with that target's spheres."""
+@pytest.mark.parametrize("K,prec", [(5, lib.CR_F64), (10, lib.CR_F64), (5, lib.CR_F32), (10, lib.CR_F32)])
+def test_solve_ik_per_problem_spheres(K, prec):
+    """Each target with its own sphere set, 30 targets (a partial last block), against the oracle run
+    target by target with that target's spheres. FP64: one candidate per thread, 5 candidates (one
+    target per warp) or 10 (three targets per warp, 2 idle lanes). FP32: 5 candidates take the
+    warp-cooperative refine (one warp per candidate), 10 the packed form. One target is non-finite
+    (its candidates are skipped, its result NaN and flagged)."""
     spec = synth.RobotSpec(L=(0.1, 0.08), rc=0.005, umax=0.01, nb=8)
     ik = synth.IkSpec(S=40, n_final=K, k_init=12, k_final=15)
     P, no = 30, 3
@@ -254,11 +256,18 @@ def test_solve_ik_per_problem_spheres_fp64(K):
     rng = np.random.default_rng(8)
     sph = np.concatenate([rng.uniform(-0.05, 0.05, (P, no, 2)), rng.uniform(0.05, 0.15, (P, no, 1)),
                           rng.uniform(0.005, 0.012, (P, no, 1))], axis=2)
-    s = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, api.Scene(sph, per_problem=True), lib.CR_F64)
+    s = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, api.Scene(sph, per_problem=True), prec)
     o = s.solve(targets_dev(tg))
     torch.cuda.synchronize()
     gu, gs = host_aos(o.u), o.success.cpu().numpy().astype(bool)
     assert s.status() == 0
+    bad = tg.copy()
+    bad[4, 0] = np.nan
+    o2 = s.solve(targets_dev(bad))
+    torch.cuda.synchronize()
+    assert not o2.success[4].item() and np.isnan(o2.cost[4].item())
+    assert s.status() & (1 << lib.CR_ENONFINITE)
+    assert np.array_equal(o2.success.cpu().numpy().astype(bool)[5:], gs[5:])
     agree = 0
     for p in range(P):
         r = _oracle_solve(spec, ik, lib.CR_TASK_IK6, tg[p:p + 1], spheres=sph[p], p0=p)

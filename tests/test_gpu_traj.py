@@ -140,6 +140,31 @@ def test_solve_traj_parity(prec):
         assert np.all(sol.goal_pos.cpu().numpy() < 1e-3) == np.all(ref["goal_pos"] < 1e-3)
 
 
+@pytest.mark.parametrize("n_spheres", [1, 5])
+def test_solve_traj_fp32_split_edges(n_spheres):
+    """FP32 trajectory solve with 20 states (a ragged warp) and an odd number of spheres (two
+    threads per state take 3 and 2 of them) or a single sphere (no split): the result is valid
+    under the oracle's own evaluation of the GPU's states and its cost is close to the oracle's."""
+    spec = synth.ROBOT_3SEG
+    rbo = orc_robot(spec)
+    P, Tn = 4, 20
+    us, goal, sph, _ = synth.traj_workload(spec, P, n_spheres, lambda u: O.fk(rbo, u, backbone=True), seed=65)
+    ik = synth.IK_GOAL
+    sol = api.TrajSolver(spec, ik, synth.WEIGHTS, P, Tn, api.Scene(sph, per_problem=True), precision=lib.CR_F32)
+    sol.solve(dev_soa(us, torch.float64), dev_soa(goal, torch.float64))
+    torch.cuda.synchronize()
+    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final)
+    ref = O.solve_traj(rbo, orc_weights(), sph, us, goal, Tn, cfg, synth.K_TRAJ, synth.ALPHA_TRAJ)
+    X = sol.X.cpu().numpy().T.reshape(P, Tn, -1)
+    for p in range(P):
+        F = O.traj_eval(rbo, orc_weights(), sph[p:p + 1], us[p:p + 1], goal[p:p + 1], X[p:p + 1, 1:])["F"]
+        np.testing.assert_allclose(sol.cost.cpu().numpy()[p], F[0], rtol=1e-3)
+    np.testing.assert_allclose(sol.cost.cpu().numpy(), ref["F"], rtol=0.05)
+    for p in range(P):  # the FP64 flags of the GPU's own states, state by state
+        _, _, lim, col = O.accept(rbo, sph[p], lib.CR_TASK_IK6, np.repeat(goal[p:p + 1], Tn, 0), X[p])
+        assert bool(sol.col_ok[p].item()) == bool(col.all())
+
+
 @pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
 def test_calibration_parity_full_size(prec):
     spec = synth.ROBOT_3SEG
