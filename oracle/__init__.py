@@ -452,6 +452,114 @@ def solve_traj(robot, weights, spheres, u_start, goal, Tn, ik_cfg: "IkConfig", k
                 col_ok=co.astype(bool))
 
 
+def traj_refine(robot, weights, spheres, u_start, goal, X0, k_traj, alpha0, lim_tol=1e-5, threads=None):
+    """Refinement and metrics of orc_solve_traj from the initial states X0 [P][Tn][d]."""
+    X = _f64(X0).copy()
+    P, Tn, d = X.shape
+    no, sp = _per_problem_spheres(spheres, P)
+    F, gp, gr, sv, sa = (np.zeros(P) for _ in range(5))
+    lo, co = np.zeros(P, np.uint8), np.zeros(P, np.uint8)
+    lib().orc_traj_refine(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(u_start)),
+                          _dp(_f64(goal)), C.c_int64(P), C.c_int(Tn), C.c_int(k_traj), C.c_double(alpha0),
+                          C.c_double(lim_tol), _dp(X), _dp(F), _dp(gp), _dp(gr), _dp(sv), _dp(sa),
+                          lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)),
+                          C.c_int(_threads(threads)))
+    return dict(x=X, F=F, goal_pos=gp, goal_rot=gr, speed=sv, accel=sa, lim_ok=lo.astype(bool),
+                col_ok=co.astype(bool))
+
+
+# ---------------------------------------------------------------------------------------------
+# PRM exploration (Algorithm 2): roadmap build and queries
+# ---------------------------------------------------------------------------------------------
+def _u8p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _sph_flat(spheres):
+    if spheres is None or len(spheres) == 0:
+        return 0, None
+    s = np.ascontiguousarray(_f64(spheres).reshape(-1, 4))
+    return s.shape[0], s
+
+
+def prm_sample(robot, delta, spheres, key, r, N, attempts):
+    """ParallelSample of roadmap r: nodes [N][d], ok [N] (bool)."""
+    d = robot.n * robot.m
+    no, sp = _sph_flat(spheres)
+    nodes = np.zeros((N, d))
+    ok = np.zeros(N, np.uint8)
+    lib().orc_prm_sample(C.byref(robot), C.c_double(delta), C.c_int(no), _dp(sp), C.c_uint64(key), C.c_int64(r),
+                         C.c_int(N), C.c_int(attempts), _dp(nodes), _u8p(ok))
+    return nodes, ok.astype(bool)
+
+
+def prm_knn(nodes, ok, k):
+    nodes = np.ascontiguousarray(_f64(nodes))
+    N, d = nodes.shape
+    okb = np.ascontiguousarray(np.asarray(ok, np.uint8))
+    nbr = np.zeros((N, k), np.int32)
+    lib().orc_prm_knn(_dp(nodes), _u8p(okb), C.c_int(N), C.c_int(d), C.c_int(k), _i32p(nbr))
+    return nbr
+
+
+def prm_segment_free(robot, delta, spheres, xa, xb, n_check):
+    no, sp = _sph_flat(spheres)
+    return bool(lib().orc_prm_segment_free(C.byref(robot), C.c_double(delta), C.c_int(no), _dp(sp),
+                                           _dp(np.ascontiguousarray(_f64(xa))), _dp(np.ascontiguousarray(_f64(xb))),
+                                           C.c_int(n_check)))
+
+
+def prm_connect(robot, delta, spheres, nodes, ok, nbr, n_check):
+    """ParallelConnect: CSR (row [N+1], col [E], wt [E]) of the roadmap graph."""
+    nodes = np.ascontiguousarray(_f64(nodes))
+    N, d = nodes.shape
+    k = nbr.shape[1]
+    no, sp = _sph_flat(spheres)
+    row = np.zeros(N + 1, np.int32)
+    col = np.zeros(2 * N * k, np.int32)
+    wt = np.zeros(2 * N * k)
+    lib().orc_prm_connect(C.byref(robot), C.c_double(delta), C.c_int(no), _dp(sp), _dp(nodes),
+                          _u8p(np.ascontiguousarray(np.asarray(ok, np.uint8))),
+                          _i32p(np.ascontiguousarray(nbr, np.int32)), C.c_int(N), C.c_int(k), C.c_int(n_check),
+                          _i32p(row), _i32p(col), _dp(wt))
+    E = int(row[N])
+    return row, col[:E].copy(), wt[:E].copy()
+
+
+def prm_build(robot, delta, spheres, key, r, N, k, n_check, attempts):
+    """The roadmap of Algorithm 2's offline stage: dict(nodes, ok, nbr, row, col, wt)."""
+    nodes, ok = prm_sample(robot, delta, spheres, key, r, N, attempts)
+    nbr = prm_knn(nodes, ok, k)
+    row, col, wt = prm_connect(robot, delta, spheres, nodes, ok, nbr, n_check)
+    return dict(nodes=nodes, ok=ok, nbr=nbr, row=row, col=col, wt=wt)
+
+
+def prm_query(robot, delta, spheres, rm, k, n_check, u_start, u_goal, T):
+    """ConnectToRoadmap, Dijkstra and ResampleLinear of one query: (X [T][d], length, hops, path)."""
+    nodes = np.ascontiguousarray(_f64(rm["nodes"]))
+    N, d = nodes.shape
+    no, sp = _sph_flat(spheres)
+    col = np.ascontiguousarray(rm["col"], np.int32)
+    wt = np.ascontiguousarray(_f64(rm["wt"]))
+    if len(col) == 0:
+        col, wt = np.zeros(1, np.int32), np.zeros(1)
+    X = np.zeros((T, d))
+    length = C.c_double(0)
+    hops = C.c_int32(0)
+    path = np.full(N + 2, -1, np.int32)
+    lib().orc_prm_query(C.byref(robot), C.c_double(delta), C.c_int(no), _dp(sp), _dp(nodes),
+                        _u8p(np.ascontiguousarray(np.asarray(rm["ok"], np.uint8))),
+                        _i32p(np.ascontiguousarray(rm["row"], np.int32)), _i32p(col), _dp(wt), C.c_int(N),
+                        C.c_int(k), C.c_int(n_check), _dp(np.ascontiguousarray(_f64(u_start))),
+                        _dp(np.ascontiguousarray(_f64(u_goal))), C.c_int(T), _dp(X), C.byref(length),
+                        C.byref(hops), _i32p(path))
+    return X, length.value, hops.value, path[:hops.value + 1].copy() if hops.value > 0 else path[:0].copy()
+
+
 def calibrate(robot, U, Pm, theta0, iters, lambda0=1e-3, history=False):
     """LM on theta = (L_1..n, r_c,1..n) from known displacements U [K][d] and tip positions Pm [K][3]."""
     U, Pm = _f64(U), _f64(Pm)

@@ -31,6 +31,8 @@
 //     waypoint, warm-started per-waypoint IK, then joint LM over all waypoints with successive-state
 //     smoothness rows and a dense Cholesky of the whole normal matrix.
 //   * Kinematic calibration of segment lengths and tendon radii from measured tip positions (LM).
+//   * PRM exploration of Algorithm 2: ParallelSample, ParallelConnect (k nearest neighbours and
+//     collision-checked straight edges), ConnectToRoadmap, Dijkstra and ResampleLinear.
 //
 // Derivatives are taken by the complex-step method (Squire and Trapp 1998): for a real-analytic
 // function f, f'(x) = Im f(x + i h) / h up to O(h^2), with no subtractive cancellation, so with
@@ -47,6 +49,7 @@
 #include <cstdint>
 #include <cstring>
 #include <functional>
+#include <queue>
 #include <thread>
 #include <vector>
 
@@ -1593,6 +1596,44 @@ int orc_traj_pg(const OrRobot* rb, const OrWeights* W, int no, const double* sph
   return 0;
 }
 
+// Refinement and metrics of one trajectory from its initial states X [Tn][d] (X[0] = u_start):
+// k_traj projected-gradient steps of the free states, then F, goal_pos / goal_rot, speed / accel
+// (the largest |du|/dt / v_max and |d2u|/dt^2 / a_max) and lim_ok / col_ok (every state within
+// limits / collision-free).
+static void traj_refine_one(const OrRobot* rb, const OrWeights* W, int no, const double* sp, const double* u0,
+                            const double* goal, int Tn, double* X, int k_traj, double alpha0, double lim_tol,
+                            double* F, double* goal_pos, double* goal_rot, double* speed, double* accel,
+                            uint8_t* lim_ok, uint8_t* col_ok) {
+  const int d = rb->n * rb->m;
+  TrajProblem tp{rb, W, no, sp, u0, goal, Tn};
+  traj_pg(tp, X + d, k_traj, alpha0, F);
+  double pos, rot;
+  uint8_t lo, co;
+  accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)(Tn - 1) * d, lim_tol, &pos, &rot, &lo, &co);
+  *goal_pos = pos;
+  *goal_rot = rot;
+  bool lim = true, col = true;
+  for (int t = 0; t < Tn; ++t) {
+    double p2, r2;
+    uint8_t l2, c2;
+    accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)t * d, lim_tol, &p2, &r2, &l2, &c2);
+    lim = lim && l2;
+    col = col && c2;
+  }
+  double vm = 0, am = 0;
+  for (int t = 1; t < Tn; ++t)
+    for (int a = 0; a < d; ++a) {
+      vm = std::max(vm, std::fabs(X[(size_t)t * d + a] - X[(size_t)(t - 1) * d + a]) / W->dt / W->vmax);
+      if (t >= 2)
+        am = std::max(am, std::fabs(X[(size_t)t * d + a] - 2 * X[(size_t)(t - 1) * d + a] + X[(size_t)(t - 2) * d + a]) /
+                              (W->dt * W->dt) / W->amax);
+    }
+  *speed = vm;
+  *accel = am;
+  *lim_ok = lim;
+  *col_ok = col;
+}
+
 // Trajectory planning per problem: IK to the goal pose (Algorithm 1 with ik_prm, seed counter p0 +
 // q), linear interpolation u_t = u_start + (t / (Tn-1)) (u_goal - u_start), then k_traj
 // projected-gradient steps. x_out [P][Tn][d] (all states, u_0 included); F_out [P]; goal_pos /
@@ -1614,33 +1655,24 @@ int orc_solve_traj(const OrRobot* rb, const OrWeights* W, int no, const double* 
     const double* u0 = u_start + (size_t)d * q;
     for (int t = 0; t < Tn; ++t)
       for (int a = 0; a < d; ++a) X[(size_t)t * d + a] = u0[a] + (double)t / (Tn - 1) * (ug[a] - u0[a]);
-    TrajProblem tp{rb, W, no, sp, u0, goal + 7 * q, Tn};
-    traj_pg(tp, X + d, k_traj, alpha0, F_out + q);
-    double pos, rot;
-    uint8_t lo, co;
-    accept_one(*rb, no, sp, OR_IK6, goal + 7 * q, X + (size_t)(Tn - 1) * d, ik_prm->lim_tol, &pos, &rot, &lo, &co);
-    goal_pos[q] = pos;
-    goal_rot[q] = rot;
-    bool lim = true, col = true;
-    for (int t = 0; t < Tn; ++t) {
-      double p2, r2;
-      uint8_t l2, c2;
-      accept_one(*rb, no, sp, OR_IK6, goal + 7 * q, X + (size_t)t * d, ik_prm->lim_tol, &p2, &r2, &l2, &c2);
-      lim = lim && l2;
-      col = col && c2;
-    }
-    double vm = 0, am = 0;
-    for (int t = 1; t < Tn; ++t)
-      for (int a = 0; a < d; ++a) {
-        vm = std::max(vm, std::fabs(X[(size_t)t * d + a] - X[(size_t)(t - 1) * d + a]) / W->dt / W->vmax);
-        if (t >= 2)
-          am = std::max(am, std::fabs(X[(size_t)t * d + a] - 2 * X[(size_t)(t - 1) * d + a] + X[(size_t)(t - 2) * d + a]) /
-                                (W->dt * W->dt) / W->amax);
-      }
-    speed[q] = vm;
-    accel[q] = am;
-    lim_ok[q] = lim;
-    col_ok[q] = col;
+    traj_refine_one(rb, W, no, sp, u0, goal + 7 * q, Tn, X, k_traj, alpha0, ik_prm->lim_tol, F_out + q,
+                    goal_pos + q, goal_rot + q, speed + q, accel + q, lim_ok + q, col_ok + q);
+  });
+  return 0;
+}
+
+// Trajectory refinement from given initial states (x_io [P][Tn][d] in, refined states out), with
+// the metrics of orc_solve_traj: the second stage of Algorithm 2 after any initialiser.
+int orc_traj_refine(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* u_start,
+                    const double* goal, int64_t P, int Tn, int k_traj, double alpha0, double lim_tol, double* x_io,
+                    double* F_out, double* goal_pos, double* goal_rot, double* speed, double* accel,
+                    uint8_t* lim_ok, uint8_t* col_ok, int threads) {
+  const int d = rb->n * rb->m;
+  parallel_for(P, threads, [&](int64_t q) {
+    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    traj_refine_one(rb, W, no, sp, u_start + (size_t)d * q, goal + 7 * q, Tn, x_io + (size_t)Tn * d * q, k_traj,
+                    alpha0, lim_tol, F_out + q, goal_pos + q, goal_rot + q, speed + q, accel + q, lim_ok + q,
+                    col_ok + q);
   });
   return 0;
 }
@@ -1749,6 +1781,232 @@ int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* 
     lim_ok[q] = lim;
     col_ok[q] = col;
   });
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// PRM exploration of Algorithm 2 (Sec. IV-B, "Trajectory Planning"): ParallelSample,
+// ParallelConnect, ConnectToRoadmap, Dijkstra and ResampleLinear, written out plainly. Readings:
+//  * ParallelSample: node i of roadmap r is the first of `attempts` hexagon-uniform draws (the
+//    SampleSeeds generator with problem r, seed i, attempt a) whose backbone is collision-free;
+//    a node with no such draw is invalid and takes no part in the graph.
+//  * ParallelConnect: the k nearest valid nodes of every valid node (squared Euclidean distance in
+//    u, ties to the lower index); the edge {i, j} exists when i lists j or j lists i and the
+//    straight segment is collision-free at n_check interior states x_a + c/(n_check+1) (x_b - x_a),
+//    c = 1..n_check, interpolated from the lower index a to the higher b. Weight: the Euclidean
+//    distance, the squared distance summed in coordinate order.
+//  * ConnectToRoadmap: the start (goal) state is linked to those of its k nearest valid nodes whose
+//    segment from the state to the node is collision-free at the n_check interior states; there
+//    is no direct start-goal edge.
+//  * Dijkstra from the start; the path is read back from the goal through the predecessor of the
+//    lowest index among the neighbours u with d(u) < d(v) and d(u) + w(u, v) == d(v) (start =
+//    index N, goal = index N + 1), which makes it unique when several paths tie.
+//  * ResampleLinear: T states at equal arc length along the path (arc length = the Dijkstra
+//    distances), state 0 the start and state T-1 the goal; with no path, the linear interpolation
+//    u_start + t/(T-1) (u_goal - u_start).
+// ---------------------------------------------------------------------------------------------
+
+static bool prm_collides(const OrRobot& rb, const Params<double>& Pd, double delta, int no, const double* sp,
+                         const double* x) {
+  if (no == 0) return false;
+  FkOut<double> o;
+  std::vector<double> bb(3 * rb.n * rb.nb);
+  forward_kinematics(rb, Pd, x, o, bb.data());
+  for (int k = 0; k < rb.n * rb.nb; ++k)
+    for (int c = 0; c < no; ++c) {
+      const double* s = sp + 4 * c;
+      const double dx = bb[3 * k] - s[0], dy = bb[3 * k + 1] - s[1], dz = bb[3 * k + 2] - s[2];
+      const double reach = s[3] + rb.rbody + delta;
+      if (dx * dx + dy * dy + dz * dz < reach * reach) return true;
+    }
+  return false;
+}
+
+static double prm_dist2(const double* a, const double* b, int d) {
+  double s = 0.0;
+  for (int q = 0; q < d; ++q) {
+    const double t = a[q] - b[q];
+    s = s + t * t;
+  }
+  return s;
+}
+
+// Is the segment from xa to xb free at its n_check interior states?
+static bool prm_segment_free(const OrRobot& rb, const Params<double>& Pd, double delta, int no, const double* sp,
+                             const double* xa, const double* xb, int n_check) {
+  const int d = rb.n * rb.m;
+  double x[OR_MAXSEG * 3];
+  for (int c = 1; c <= n_check; ++c) {
+    const double s = (double)c / (double)(n_check + 1);
+    for (int q = 0; q < d; ++q) x[q] = xa[q] + s * (xb[q] - xa[q]);
+    if (prm_collides(rb, Pd, delta, no, sp, x)) return false;
+  }
+  return true;
+}
+
+// The k nearest valid nodes of state x (excluding node `self`), ascending by (distance^2, index).
+static std::vector<std::pair<double, int>> prm_nearest(const double* nodes, const uint8_t* ok, int N, int d,
+                                                       const double* x, int self, int k) {
+  std::vector<std::pair<double, int>> c;
+  for (int j = 0; j < N; ++j)
+    if (ok[j] && j != self) c.push_back({prm_dist2(x, nodes + (size_t)j * d, d), j});
+  std::sort(c.begin(), c.end());
+  if ((int)c.size() > k) c.resize(k);
+  return c;
+}
+
+extern "C" {
+
+// ParallelSample for roadmap r: nodes [N][d], ok [N].
+int orc_prm_sample(const OrRobot* rb, double delta, int no, const double* spheres, uint64_t key, int64_t r, int N,
+                   int attempts, double* nodes, uint8_t* ok) {
+  const int d = rb->n * rb->m;
+  Params<double> Pd = params_of<double>(*rb);
+  for (int i = 0; i < N; ++i) {
+    double* x = nodes + (size_t)i * d;
+    ok[i] = 0;
+    for (int a = 0; a < attempts && !ok[i]; ++a) {
+      for (int s = 0; s < rb->n; ++s) {
+        double U[3];
+        for (int w = 0; w < 3; ++w) U[w] = u01_from(splitmix64_at(key, seed_counter(r, i, a, s, w)));
+        hexagon_point(rb->umax[s], U[0], U[1], U[2], x + 3 * s);
+      }
+      ok[i] = !prm_collides(*rb, Pd, delta, no, spheres, x);
+    }
+  }
+  return 0;
+}
+
+// k nearest valid neighbours of every valid node: nbr [N][k], -1 where there are fewer (and for
+// invalid nodes).
+int orc_prm_knn(const double* nodes, const uint8_t* ok, int N, int d, int k, int32_t* nbr) {
+  for (int i = 0; i < N; ++i) {
+    for (int c = 0; c < k; ++c) nbr[(size_t)i * k + c] = -1;
+    if (!ok[i]) continue;
+    std::vector<std::pair<double, int>> c = prm_nearest(nodes, ok, N, d, nodes + (size_t)i * d, i, k);
+    for (size_t e = 0; e < c.size(); ++e) nbr[(size_t)i * k + e] = c[e].second;
+  }
+  return 0;
+}
+
+// Is the segment from xa to xb collision-free at its n_check interior states? (1 / 0)
+int orc_prm_segment_free(const OrRobot* rb, double delta, int no, const double* spheres, const double* xa,
+                         const double* xb, int n_check) {
+  Params<double> Pd = params_of<double>(*rb);
+  return prm_segment_free(*rb, Pd, delta, no, spheres, xa, xb, n_check) ? 1 : 0;
+}
+
+// ParallelConnect: the roadmap graph in CSR form, rows in node order, columns ascending:
+// row [N+1], col [2 N k] and wt [2 N k] (capacity), from nodes, ok and the kNN lists nbr.
+int orc_prm_connect(const OrRobot* rb, double delta, int no, const double* spheres, const double* nodes,
+                    const uint8_t* ok, const int32_t* nbr, int N, int k, int n_check, int32_t* row, int32_t* col,
+                    double* wt) {
+  const int d = rb->n * rb->m;
+  Params<double> Pd = params_of<double>(*rb);
+  std::vector<std::vector<uint8_t>> adj(N, std::vector<uint8_t>(N, 0));
+  for (int i = 0; i < N; ++i)
+    for (int c = 0; c < k; ++c) {
+      const int j = nbr[(size_t)i * k + c];
+      if (j < 0 || adj[i][j]) continue;
+      const int a = std::min(i, j), b = std::max(i, j);
+      if (prm_segment_free(*rb, Pd, delta, no, spheres, nodes + (size_t)a * d, nodes + (size_t)b * d, n_check))
+        adj[i][j] = adj[j][i] = 1;
+    }
+  int e = 0;
+  for (int i = 0; i < N; ++i) {
+    row[i] = e;
+    for (int j = 0; j < N; ++j)
+      if (adj[i][j]) {
+        col[e] = j;
+        wt[e] = std::sqrt(prm_dist2(nodes + (size_t)i * d, nodes + (size_t)j * d, d));
+        ++e;
+      }
+  }
+  row[N] = e;
+  return 0;
+}
+
+// One query on a roadmap (nodes [N][d], ok, CSR row/col/wt): ConnectToRoadmap of u_start and
+// u_goal, Dijkstra, ResampleLinear to X [T][d]. Returns the path length (the distance of the
+// goal, +inf with no path) in *length and the number of path edges (0 with no path) in *hops;
+// path [N + 2] (nullable) receives the path's vertex indices from the start.
+int orc_prm_query(const OrRobot* rb, double delta, int no, const double* spheres, const double* nodes,
+                  const uint8_t* ok, const int32_t* row, const int32_t* col, const double* wt, int N, int k,
+                  int n_check, const double* us, const double* ug, int T, double* X, double* length, int32_t* hops,
+                  int32_t* path) {
+  const int d = rb->n * rb->m;
+  Params<double> Pd = params_of<double>(*rb);
+  const int S = N, G = N + 1, V = N + 2;
+  // adjacency lists of the query graph: roadmap edges plus the start and goal links
+  std::vector<std::vector<std::pair<int, double>>> nb(V);
+  for (int i = 0; i < N; ++i)
+    for (int e = row[i]; e < row[i + 1]; ++e) nb[i].push_back({col[e], wt[e]});
+  const double* q[2] = {us, ug};
+  for (int side = 0; side < 2; ++side) {
+    const int vq = side == 0 ? S : G;
+    for (auto& c : prm_nearest(nodes, ok, N, d, q[side], -1, k))
+      if (prm_segment_free(*rb, Pd, delta, no, spheres, q[side], nodes + (size_t)c.second * d, n_check)) {
+        const double w = std::sqrt(c.first);
+        nb[vq].push_back({c.second, w});
+        nb[c.second].push_back({vq, w});
+      }
+  }
+  // Dijkstra (binary heap, lazy deletion)
+  std::vector<double> dist(V, INFINITY);
+  std::vector<uint8_t> done(V, 0);
+  std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, std::greater<>> pq;
+  dist[S] = 0.0;
+  pq.push({0.0, S});
+  while (!pq.empty()) {
+    const auto [du, u] = pq.top();
+    pq.pop();
+    if (done[u]) continue;
+    done[u] = 1;
+    for (auto& [v, w] : nb[u])
+      if (du + w < dist[v]) {
+        dist[v] = du + w;
+        pq.push({dist[v], v});
+      }
+  }
+  *length = dist[G];
+  auto xv = [&](int v) { return v == S ? us : (v == G ? ug : nodes + (size_t)v * d); };
+  if (!(dist[G] < INFINITY)) {
+    *hops = 0;
+    for (int t = 0; t < T; ++t)
+      for (int a = 0; a < d; ++a) X[(size_t)t * d + a] = us[a] + (double)t / (T - 1) * (ug[a] - us[a]);
+    return 0;
+  }
+  // path from the goal back to the start through the canonical predecessors
+  std::vector<int> pth{G};
+  for (int v = G; v != S && (int)pth.size() <= V;) {
+    int best = -1;
+    for (auto& [u, w] : nb[v])
+      if (dist[u] < dist[v] && dist[u] + w == dist[v] && (best < 0 || u < best)) best = u;
+    v = best;
+    pth.push_back(v);
+  }
+  std::reverse(pth.begin(), pth.end());
+  const int M = (int)pth.size() - 1;
+  *hops = M;
+  if (path)
+    for (int j = 0; j <= M; ++j) path[j] = pth[j];
+  // ResampleLinear
+  const double Lt = dist[G];
+  for (int t = 0; t < T; ++t) {
+    double* x = X + (size_t)t * d;
+    if (t == 0 || t == T - 1) {
+      std::memcpy(x, t == 0 ? us : ug, sizeof(double) * d);
+      continue;
+    }
+    const double s = (double)t / (double)(T - 1) * Lt;
+    int j = 0;
+    while (j + 1 < M && dist[pth[j + 1]] <= s) ++j;
+    const double lam = (s - dist[pth[j]]) / (dist[pth[j + 1]] - dist[pth[j]]);
+    const double *xa = xv(pth[j]), *xb = xv(pth[j + 1]);
+    for (int a = 0; a < d; ++a) x[a] = xa[a] + lam * (xb[a] - xa[a]);
+  }
   return 0;
 }
 
