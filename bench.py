@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     ap.add_argument("--items", type=int, default=synth.N_RAGGED,
                     help="items of the ragged batch (default 16384; smaller for profiling cases)")
-    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "calib", "ragged", "e1", "e2"],
+    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "prm", "calib", "ragged", "e1", "e2"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
@@ -273,6 +273,48 @@ def other_workload(args):
         extra = lambda: {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
                          "collision_free_rate": float(s.col_ok.float().mean()),
                          "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+        dtype = "f32"
+    elif args.workload == "prm":
+        # Algorithm 2: roadmaps built once per scene (offline, timed apart), then per query the goal IK,
+        # the roadmap query (attachment, shortest path, resampling) and the 100 PG steps
+        spec, ik, P, Tn, ps = synth.ROBOT_3SEG, synth.IK_GOAL, synth.P_TRAJ, synth.T_TRAJ, synth.PRM_TRAJ
+
+        def fkb(uu):
+            T, bb = api.fk(api.robot_struct(spec), torch.as_tensor(uu.T.copy(), dtype=torch.float64, device=dev), True)
+            return T.cpu().numpy().T, bb.cpu().numpy().transpose(2, 0, 1)
+
+        us, goal, sph, _ = synth.traj_workload(spec, P, synth.NO_TRAJ, fkb, seed=0)
+        scene = api.Scene(sph, per_problem=True)
+        rm = api.Roadmap(spec, ps, P, device=dev)
+        s = api.TrajSolver(spec, ik, synth.WEIGHTS, P, Tn, scene, device=dev, roadmap=rm)
+        lin = api.TrajSolver(spec, ik, synth.WEIGHTS, P, Tn, scene, device=dev)
+        usd = torch.as_tensor(us.T.copy(), dtype=torch.float64, device=dev)
+        gd = torch.as_tensor(goal.T.copy(), dtype=torch.float64, device=dev)
+        rm.build(scene, synth.WEIGHTS)
+        build_ms = time_steps(torch, lambda: rm.build(scene, synth.WEIGHTS), max(3, args.steps), flush, stream)[1]
+        fn = lambda: s.solve(usd, gd)
+        units, unit = P, "trajectories/s"
+        metric = "trajectory planning trajectories/s with the PRM initialiser (goal IK, roadmap query, 100 PG steps)"
+        wl = f"traj_prm_3seg_256problems_32states_64spheres_roadmap{ps.N}x{ps.k}_check{ps.n_check}_pg100"
+
+        def success(t):
+            return ((t.goal_pos <= 1e-3) & (t.goal_rot <= np.deg2rad(1.0)) & (t.col_ok > 0) & (t.lim_ok > 0)).float()
+
+        def extra():
+            s.solve(usd, gd)
+            lin.solve(usd, gd)
+            torch.cuda.synchronize()
+            h = s.hops.cpu().numpy()
+            return {"roadmap_build_ms": build_ms, "roadmaps": P, "nodes_per_roadmap": ps.N,
+                    "valid_node_rate": float(rm.node_ok.float().mean()),
+                    "edges_per_roadmap": float(rm.row[:, -1].double().mean() / 2),
+                    "path_found_rate": float((h > 0).mean()), "hops_mean": float(h[h > 0].mean()) if (h > 0).any() else 0.0,
+                    "success_rate_prm": float(success(s).mean()), "success_rate_linear": float(success(lin).mean()),
+                    "collision_free_rate_prm": float(s.col_ok.float().mean()),
+                    "collision_free_rate_linear": float(lin.col_ok.float().mean()),
+                    "trajectory_cost_median_prm": float(s.cost.median()),
+                    "trajectory_cost_median_linear": float(lin.cost.median())}
+
         dtype = "f32"
     elif args.workload in ("e1", "e2"):
         # the paper's own IK benchmarks in its (theta, phi, L) parameterisation (Sec. V-B)

@@ -323,6 +323,93 @@ CR_API cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, con
                                uint8_t* lim_ok, uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * PRM exploration of Algorithm 2 (Sec. IV-B, "Trajectory Planning"): ParallelSample and
+ * ParallelConnect build a roadmap per scene once; every query attaches its start and goal states
+ * (ConnectToRoadmap), takes the shortest path (the distances of Dijkstra's algorithm, computed by
+ * synchronous relaxation rounds) and resamples it at equal arc length (ResampleLinear) into the
+ * initial states of the trajectory refinement.
+ *
+ * Readings of the paper (it gives no further detail): node i of roadmap r is the first of
+ * `attempts` draws of the SampleSeeds generator (problem r, seed i, attempt a) whose backbone is
+ * collision-free (invalid if none is); the edge {i, j} exists when either node is among the k
+ * nearest valid nodes of the other (squared Euclidean distance in u, ties to the lower index) and
+ * the segment, interpolated from the lower index to the higher, is collision-free at its n_check
+ * interior states c / (n_check + 1), c = 1..n_check; its weight is the Euclidean distance. The
+ * start (goal) is linked to those of its k nearest valid nodes whose segment from the state is
+ * free at the same interior states; there is no direct start-goal edge. The path is read back
+ * from the goal through the lowest-index neighbour u with d(u) < d(v) and d(u) + w(u, v) == d(v).
+ * The resampled state t (t = 0..T-1) lies at arc length t / (T-1) of the path (state 0 the start,
+ * T-1 the goal); with no path it is u_start + t/(T-1) (u_goal - u_start). Collision: any backbone
+ * sample of the state closer than r + r_body + delta to a sphere centre, decided in FP64.
+ * ------------------------------------------------------------------------------------------- */
+#define CR_PRM_MAX_N 1024
+#define CR_PRM_MAX_K 32
+#define CR_PRM_MAX_CHECK 64
+#define CR_PRM_MAX_ATTEMPTS 8
+
+/* Roadmap settings. Host struct. */
+typedef struct {
+  int32_t N;        /* nodes per roadmap, 2..CR_PRM_MAX_N */
+  int32_t k;        /* nearest neighbours, 1..min(CR_PRM_MAX_K, N - 1) */
+  int32_t n_check;  /* interior states tested per edge, 1..CR_PRM_MAX_CHECK */
+  int32_t attempts; /* draws per node, 1..CR_PRM_MAX_ATTEMPTS */
+  uint64_t seed;    /* key of the node draws */
+} cr_prm_params;
+
+/* R roadmaps of N nodes (host struct of caller-owned device arrays). Roadmap r is built in the
+ * scene's sphere set r (scene->per_problem = 1: R sets) or in the shared set.
+ *   nodes   [3n][R * N]  FP64 node states (node i of roadmap r at column r * N + i; an invalid
+ *                        node holds its last draw)
+ *   node_ok [R * N]      uint8, 1 = valid
+ *   nbr     [R * N][k]   int32 k nearest valid nodes (roadmap-local index), -1 past the last
+ *   row     [R][N + 1]   int32 CSR offsets of each roadmap's graph (local to the roadmap's rows)
+ *   col     [R][2 N k]   int32 neighbours, ascending within a row
+ *   wt      [R][2 N k]   FP64 edge weights (Euclidean distance in u) */
+typedef struct {
+  int64_t R;
+  double* nodes;
+  uint8_t* node_ok;
+  int32_t* nbr;
+  int32_t* row;
+  int32_t* col;
+  double* wt;
+} cr_roadmap;
+
+/* Scratch bytes of cr_prm_build. */
+CR_API size_t cr_prm_workspace_size(const cr_robot* robot, int64_t R, const cr_prm_params* prm);
+
+/* Builds the roadmaps (the offline stage of Algorithm 2). Only w->delta of the weights is used.
+ * Tendon model; map->R in 1..65535; scene->per_problem = 1 requires map->R sphere sets.
+ * Asynchronous on `stream`. */
+CR_API cr_status cr_prm_build(const cr_robot* robot, const cr_scene* scene, const cr_weights* w,
+                              const cr_prm_params* prm, const cr_roadmap* map, void* workspace, size_t ws_bytes,
+                              cr_stream stream);
+
+/* Queries (the online stage up to ResampleLinear): P start / goal state pairs u_start, u_goal
+ * [3n][P] (device, FP64); query p uses roadmap 0 when map->R == 1, else roadmap p (map->R == P),
+ * and sphere set p of a per-problem scene. Outputs (device): X [3n][P * T] FP64 (state t of query
+ * p at column p * T + t), length [P] FP64 (path length, +inf with no path), hops [P] int32 (path
+ * edges, 0 with no path). T in 2..256. */
+CR_API cr_status cr_prm_query(const cr_robot* robot, const cr_scene* scene, const cr_weights* w,
+                              const cr_prm_params* prm, const cr_roadmap* map, const double* u_start,
+                              const double* u_goal, int64_t P, int32_t T, double* X, double* length, int32_t* hops,
+                              cr_stream stream);
+
+/* Scratch bytes of cr_solve_traj_prm. */
+CR_API size_t cr_traj_prm_workspace_size(const cr_robot* robot, int64_t P, int32_t T, const cr_ik_params* goal_ik);
+
+/* Trajectory planning with the PRM initialiser (Algorithm 2): IK to every goal pose as in
+ * cr_solve_traj, cr_prm_query from u_start to the IK state on the prebuilt roadmaps, then the
+ * k_traj projected-gradient steps of cr_solve_traj from the resampled states. Outputs as
+ * cr_solve_traj, plus length [P] and hops [P] of the roadmap path (device, nullable). */
+CR_API cr_status cr_solve_traj_prm(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                                   const cr_ik_params* goal_ik, const cr_prm_params* prm, const cr_roadmap* map,
+                                   int32_t k_traj, double alpha0, double* X_out, double* cost_out, double* goal_pos,
+                                   double* goal_rot, double* speed, double* accel, uint8_t* lim_ok, uint8_t* col_ok,
+                                   double* length, int32_t* hops, void* workspace, size_t ws_bytes,
+                                   cr_stream stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Path following (Sec. IV-A, Eq. constrained_mp; Sec. IV-B, "Path Following")
  * ------------------------------------------------------------------------------------------- */
 

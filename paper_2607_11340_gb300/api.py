@@ -263,29 +263,96 @@ def traj_task_struct(u_start_soa, goal_soa, T: int, weights: synth.WeightSpec) -
     return t
 
 
+def prm_params_struct(spec: synth.PrmSpec) -> lib.cr_prm_params:
+    p = lib.cr_prm_params()
+    p.N, p.k, p.n_check, p.attempts, p.seed = spec.N, spec.k, spec.n_check, spec.attempts, spec.seed
+    return p
+
+
+class Roadmap:
+    """R PRM roadmaps resident on the device (Algorithm 2's offline stage): nodes [d][R*N], node_ok
+    [R*N], nbr [R*N][k], the graphs in CSR form row [R][N+1], col / wt [R][2Nk]."""
+
+    def __init__(self, robot_spec, spec: synth.PrmSpec, R: int, device="cuda"):
+        self.spec, self.R = spec, R
+        self.robot = robot_struct(robot_spec)
+        self.params = prm_params_struct(spec)
+        N, k, d = spec.N, spec.k, robot_spec.d
+        self.nodes = torch.empty(d, R * N, dtype=torch.float64, device=device)
+        self.node_ok = torch.empty(R * N, dtype=torch.uint8, device=device)
+        self.nbr = torch.empty(R * N, k, dtype=torch.int32, device=device)
+        self.row = torch.empty(R, N + 1, dtype=torch.int32, device=device)
+        self.col = torch.empty(R, 2 * N * k, dtype=torch.int32, device=device)
+        self.wt = torch.empty(R, 2 * N * k, dtype=torch.float64, device=device)
+        self.workspace = torch.empty(lib.cr_prm_workspace_size(self.robot, R, self.params), dtype=torch.uint8,
+                                     device=device)
+        self.c = lib.cr_roadmap()
+        self.c.R = R
+        for f in ("nodes", "node_ok", "nbr", "row", "col", "wt"):
+            setattr(self.c, f, getattr(self, f).data_ptr())
+
+    def build(self, scene: Scene | None, weights: synth.WeightSpec):
+        scene = scene or Scene(None)
+        self._scene = scene
+        lib.cr_prm_build(self.robot, scene.c, weights_struct(weights), self.params, self.c, self.workspace)
+        return self
+
+    def graph(self, r: int):
+        """Roadmap r on the host: dict(nodes [N][d], ok, nbr, row, col, wt) as numpy arrays."""
+        N = self.spec.N
+        row = self.row[r].cpu().numpy()
+        E = int(row[N])
+        return dict(nodes=self.nodes[:, r * N:(r + 1) * N].T.cpu().numpy(),
+                    ok=self.node_ok[r * N:(r + 1) * N].cpu().numpy().astype(bool),
+                    nbr=self.nbr[r * N:(r + 1) * N].cpu().numpy(), row=row,
+                    col=self.col[r, :E].cpu().numpy(), wt=self.wt[r, :E].cpu().numpy())
+
+    def query(self, scene: Scene | None, weights, u_start_soa, u_goal_soa, T: int):
+        """ConnectToRoadmap, shortest path, ResampleLinear: X [d][P*T], length [P], hops [P]."""
+        scene = scene or Scene(None)
+        d, P = u_start_soa.shape
+        dev = u_start_soa.device
+        X = torch.empty(d, P * T, dtype=torch.float64, device=dev)
+        length = torch.empty(P, dtype=torch.float64, device=dev)
+        hops = torch.empty(P, dtype=torch.int32, device=dev)
+        lib.cr_prm_query(self.robot, scene.c, weights_struct(weights), self.params, self.c, u_start_soa, u_goal_soa,
+                         P, T, X, length, hops)
+        return X, length, hops
+
+
 class TrajSolver:
-    """Trajectory planning for P problems of T states (goal IK, linear initialisation, projected
-    gradient refinement)."""
+    """Trajectory planning for P problems of T states (goal IK, linear initialisation or, with a
+    roadmap, the PRM initialiser of Algorithm 2, projected gradient refinement)."""
 
     def __init__(self, robot_spec, goal_ik: synth.IkSpec, weights, P, T, scene: Scene | None = None,
-                 precision=lib.CR_F32, k_traj=synth.K_TRAJ, alpha0=synth.ALPHA_TRAJ, device="cuda"):
+                 precision=lib.CR_F32, k_traj=synth.K_TRAJ, alpha0=synth.ALPHA_TRAJ, device="cuda",
+                 roadmap: Roadmap | None = None):
         self.robot = robot_struct(robot_spec)
         self.weights = weights
         self.P, self.T, self.k_traj, self.alpha0 = P, T, k_traj, alpha0
         self.scene = scene or Scene(None)
         self.prm = ik_params_struct(goal_ik, precision)
+        self.roadmap = roadmap
         d = robot_spec.d
-        self.workspace = torch.empty(lib.cr_traj_workspace_size(self.robot, P, self.prm), dtype=torch.uint8,
-                                     device=device)
+        wsb = (lib.cr_traj_prm_workspace_size(self.robot, P, T, self.prm) if roadmap is not None
+               else lib.cr_traj_workspace_size(self.robot, P, self.prm))
+        self.workspace = torch.empty(wsb, dtype=torch.uint8, device=device)
         z = lambda *s, dt=torch.float64: torch.empty(s, dtype=dt, device=device)
         self.X, self.cost, self.goal_pos, self.goal_rot = z(d, P * T), z(P), z(P), z(P)
         self.speed, self.accel = z(P), z(P)
         self.lim_ok, self.col_ok = z(P, dt=torch.uint8), z(P, dt=torch.uint8)
+        self.length, self.hops = z(P), z(P, dt=torch.int32)
 
     def solve(self, u_start_soa, goal_soa, p0: int = 0):
         task = traj_task_struct(u_start_soa, goal_soa, self.T, self.weights)
         self._task = task
         self.prm.p0 = p0
+        if self.roadmap is not None:
+            lib.cr_solve_traj_prm(self.robot, self.scene.c, task, self.prm, self.roadmap.params, self.roadmap.c,
+                                  self.k_traj, self.alpha0, self.X, self.cost, self.goal_pos, self.goal_rot,
+                                  self.speed, self.accel, self.lim_ok, self.col_ok, self.length, self.hops,
+                                  self.workspace)
+            return self
         lib.cr_solve_traj(self.robot, self.scene.c, task, self.prm, self.k_traj, self.alpha0, self.X, self.cost,
                           self.goal_pos, self.goal_rot, self.speed, self.accel, self.lim_ok, self.col_ok,
                           self.workspace)

@@ -1,5 +1,5 @@
 // C ABI of trajectory planning and calibration: cr_traj_cost, cr_traj_workspace_size, cr_solve_traj,
-// cr_calibrate.
+// cr_traj_prm_workspace_size, cr_solve_traj_prm, cr_calibrate.
 #include "cr_traj_impl.cuh"
 
 namespace crk {
@@ -21,11 +21,13 @@ cr_status check_traj_task(const cr_traj_task* t) {
   return CR_OK;
 }
 
+// Workspace of cr_solve_traj; with T > 0 (the PRM initialiser) also the initial states [3n][P*T] and
+// the path length / hop count when the caller passes none.
 struct TrajWs {
-  size_t ik, ug, cost, pos, rot, succ, total;
+  size_t ik, ug, cost, pos, rot, succ, x0, len, hops, total;
 };
 
-TrajWs traj_ws(const cr_robot& r, int64_t P, const cr_ik_params& g) {
+TrajWs traj_ws(const cr_robot& r, int64_t P, const cr_ik_params& g, int T = 0) {
   TrajWs w;
   size_t off = 0;
   w.ik = off; off = align256(off + cr_ik_workspace_size(&r, P, &g));
@@ -34,8 +36,81 @@ TrajWs traj_ws(const cr_robot& r, int64_t P, const cr_ik_params& g) {
   w.pos = off; off = align256(off + (size_t)P * 8);
   w.rot = off; off = align256(off + (size_t)P * 8);
   w.succ = off; off = align256(off + (size_t)P);
+  w.x0 = w.len = w.hops = off;
+  if (T > 0) {
+    w.x0 = off; off = align256(off + (size_t)3 * r.n * P * T * 8);
+    w.len = off; off = align256(off + (size_t)P * 8);
+    w.hops = off; off = align256(off + (size_t)P * 4);
+  }
   w.total = off;
   return w;
+}
+
+// Trajectory planning: goal IK, then the linear initialiser (prm == nullptr) or the PRM query on the
+// roadmaps, then the projected-gradient refinement.
+cr_status solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                     const cr_ik_params* goal_ik, const cr_prm_params* prm, const cr_roadmap* map, int32_t k_traj,
+                     double alpha0, double* X_out, double* cost_out, double* goal_pos, double* goal_rot, double* speed,
+                     double* accel, uint8_t* lim_ok, uint8_t* col_ok, double* length, int32_t* hops, void* workspace,
+                     size_t ws_bytes, cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "trajectory entry points")) ||
+      (st = check_scene(scene)) || (st = check_traj_task(task)))
+    return st;
+  if (!goal_ik) return fail(CR_EINVAL, "goal_ik is NULL");
+  if (k_traj < 0 || !(alpha0 >= 0)) return fail(CR_EINVAL, "k_traj < 0 or alpha0 < 0");
+  const int64_t P = task->P;
+  if (P == 0) return CR_OK;
+  if ((st = check_ptr(X_out, 8, "X_out", true)) || (st = check_ptr(cost_out, 8, "cost_out", true)) ||
+      (st = check_ptr(goal_pos, 8, "goal_pos", true)) || (st = check_ptr(goal_rot, 8, "goal_rot", true)) ||
+      (st = check_ptr(speed, 8, "speed", true)) || (st = check_ptr(accel, 8, "accel", true)) ||
+      (st = check_ptr(lim_ok, 1, "lim_ok", true)) || (st = check_ptr(col_ok, 1, "col_ok", true)) ||
+      (st = check_ptr(length, 8, "length", false)) || (st = check_ptr(hops, 4, "hops", false)) ||
+      (st = check_ptr(workspace, 256, "workspace", true)))
+    return st;
+  TrajWs lay = traj_ws(*robot, P, *goal_ik, prm ? task->T : 0);
+  if (ws_bytes < lay.total) return fail(CR_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, lay.total);
+  unsigned char* ws = (unsigned char*)workspace;
+  // 1. IK to the goal poses (per-problem spheres when the scene has them)
+  cr_task it{};
+  it.kind = CR_TASK_IK6;
+  it.seeds_per_target = 1;
+  it.targets = task->goal;
+  it.n_targets = P;
+  it.w = task->w;
+  double* ug = (double*)(ws + lay.ug);
+  if ((st = cr_solve_ik(robot, scene, &it, goal_ik, ug, (double*)(ws + lay.cost), (double*)(ws + lay.pos),
+                        (double*)(ws + lay.rot), ws + lay.succ, ws + lay.ik, lay.ug - lay.ik, stream)))
+    return st;
+  // 2. initial states: the PRM query (Algorithm 2) or, without a roadmap, the linear interpolation
+  double* x0 = nullptr;
+  if (prm) {
+    x0 = (double*)(ws + lay.x0);
+    double* len = length ? length : (double*)(ws + lay.len);
+    int32_t* hp = hops ? hops : (int32_t*)(ws + lay.hops);
+    if ((st = cr_prm_query(robot, scene, &task->w, prm, map, task->u_start, ug, P, task->T, x0, len, hp, stream)))
+      return st;
+  }
+  // 3. projected-gradient refinement
+  crk::TrajLaunch l{};
+  l.robot = *robot;
+  if (scene) l.scene = *scene;
+  l.task = *task;
+  l.u_goal = ug;
+  l.x_init = x0;
+  l.k_traj = k_traj;
+  l.alpha0 = alpha0;
+  l.lim_tol = goal_ik->lim_tol;
+  l.X_out = X_out;
+  l.F_out = cost_out;
+  l.goal_pos = goal_pos;
+  l.goal_rot = goal_rot;
+  l.speed = speed;
+  l.accel = accel;
+  l.lim_ok = lim_ok;
+  l.col_ok = col_ok;
+  l.stream = stream_of(stream);
+  return goal_ik->precision == CR_F64 ? crk::launch_traj_solve<double>(l) : crk::launch_traj_solve<float>(l);
 }
 
 }  // namespace
@@ -75,53 +150,23 @@ cr_status cr_solve_traj(const cr_robot* robot, const cr_scene* scene, const cr_t
                         const cr_ik_params* goal_ik, int32_t k_traj, double alpha0, double* X_out, double* cost_out,
                         double* goal_pos, double* goal_rot, double* speed, double* accel, uint8_t* lim_ok,
                         uint8_t* col_ok, void* workspace, size_t ws_bytes, cr_stream stream) {
-  cr_status st;
-  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "trajectory entry points")) ||
-      (st = check_scene(scene)) || (st = check_traj_task(task)))
-    return st;
-  if (!goal_ik) return fail(CR_EINVAL, "goal_ik is NULL");
-  if (k_traj < 0 || !(alpha0 >= 0)) return fail(CR_EINVAL, "k_traj < 0 or alpha0 < 0");
-  const int64_t P = task->P;
-  if (P == 0) return CR_OK;
-  if ((st = check_ptr(X_out, 8, "X_out", true)) || (st = check_ptr(cost_out, 8, "cost_out", true)) ||
-      (st = check_ptr(goal_pos, 8, "goal_pos", true)) || (st = check_ptr(goal_rot, 8, "goal_rot", true)) ||
-      (st = check_ptr(speed, 8, "speed", true)) || (st = check_ptr(accel, 8, "accel", true)) ||
-      (st = check_ptr(lim_ok, 1, "lim_ok", true)) || (st = check_ptr(col_ok, 1, "col_ok", true)) ||
-      (st = check_ptr(workspace, 256, "workspace", true)))
-    return st;
-  TrajWs lay = traj_ws(*robot, P, *goal_ik);
-  if (ws_bytes < lay.total) return fail(CR_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, lay.total);
-  unsigned char* ws = (unsigned char*)workspace;
-  // 1. IK to the goal poses (per-problem spheres when the scene has them)
-  cr_task it{};
-  it.kind = CR_TASK_IK6;
-  it.seeds_per_target = 1;
-  it.targets = task->goal;
-  it.n_targets = P;
-  it.w = task->w;
-  double* ug = (double*)(ws + lay.ug);
-  if ((st = cr_solve_ik(robot, scene, &it, goal_ik, ug, (double*)(ws + lay.cost), (double*)(ws + lay.pos),
-                        (double*)(ws + lay.rot), ws + lay.succ, ws + lay.ik, lay.ug - lay.ik, stream)))
-    return st;
-  // 2. linear initialisation and projected-gradient refinement
-  crk::TrajLaunch l{};
-  l.robot = *robot;
-  if (scene) l.scene = *scene;
-  l.task = *task;
-  l.u_goal = ug;
-  l.k_traj = k_traj;
-  l.alpha0 = alpha0;
-  l.lim_tol = goal_ik->lim_tol;
-  l.X_out = X_out;
-  l.F_out = cost_out;
-  l.goal_pos = goal_pos;
-  l.goal_rot = goal_rot;
-  l.speed = speed;
-  l.accel = accel;
-  l.lim_ok = lim_ok;
-  l.col_ok = col_ok;
-  l.stream = stream_of(stream);
-  return goal_ik->precision == CR_F64 ? crk::launch_traj_solve<double>(l) : crk::launch_traj_solve<float>(l);
+  return solve_traj(robot, scene, task, goal_ik, nullptr, nullptr, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot,
+                    speed, accel, lim_ok, col_ok, nullptr, nullptr, workspace, ws_bytes, stream);
+}
+
+size_t cr_traj_prm_workspace_size(const cr_robot* robot, int64_t P, int32_t T, const cr_ik_params* goal_ik) {
+  if (!robot || !goal_ik || P < 0 || T < 2) return 0;
+  return traj_ws(*robot, P, *goal_ik, T).total;
+}
+
+cr_status cr_solve_traj_prm(const cr_robot* robot, const cr_scene* scene, const cr_traj_task* task,
+                            const cr_ik_params* goal_ik, const cr_prm_params* prm, const cr_roadmap* map,
+                            int32_t k_traj, double alpha0, double* X_out, double* cost_out, double* goal_pos,
+                            double* goal_rot, double* speed, double* accel, uint8_t* lim_ok, uint8_t* col_ok,
+                            double* length, int32_t* hops, void* workspace, size_t ws_bytes, cr_stream stream) {
+  if (!prm || !map) return fail(CR_EINVAL, "cr_solve_traj_prm: prm and map are required");
+  return solve_traj(robot, scene, task, goal_ik, prm, map, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot, speed,
+                    accel, lim_ok, col_ok, length, hops, workspace, ws_bytes, stream);
 }
 
 size_t cr_calibrate_workspace_size(const cr_robot* robot, int64_t K) {

@@ -212,6 +212,7 @@ template <typename T> struct TrajArgs {
   const T* upstream;
   // solve
   const double* u_goal;   // [D][P]
+  const double* x_init;   // [D][P*Tn] initial states (nullable: linear interpolation to u_goal)
   int k_traj;
   T alpha0;
   double lim_tol;
@@ -260,8 +261,8 @@ __global__ void __launch_bounds__(256) k_traj_cost(RobotK<T> rb, WeightsK<T> w, 
   }
 }
 
-// Trajectory planning after the goal IK: linear initialisation, k_traj projected-gradient steps of
-// all free states, FP64 metrics of the result.
+// Trajectory planning after the goal IK: linear initialisation (or the given initial states x_init), k_traj
+// projected-gradient steps of all free states, FP64 metrics of the result.
 template <typename T, int N, bool OBST>
 __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, RobotK<double> rbd,
                                                      WeightsK<double> wd, TrajArgs<T> a) {
@@ -291,6 +292,10 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   T u[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) {
+    if (a.x_init) {
+      u[q] = active ? T(a.x_init[q * a.P * Tn + p * Tn + t]) : T(0);
+      continue;
+    }
     double u0 = a.u_start[q * a.P + p], ug = a.u_goal[q * a.P + p];
     u[q] = active ? T(u0 + (double)t / (Tn - 1) * (ug - u0)) : T(0);
   }
@@ -592,6 +597,7 @@ struct TrajLaunch {
   const void* upstream;
   // solve
   const double* u_goal;
+  const double* x_init;  // nullable
   int k_traj;
   double alpha0, lim_tol;
   double *X_out, *F_out, *goal_pos, *goal_rot, *speed, *accel;
@@ -636,6 +642,7 @@ template <typename T> TrajArgs<T> traj_args(const TrajLaunch& l) {
   a.grad = (T*)l.grad;
   a.upstream = (const T*)l.upstream;
   a.u_goal = l.u_goal;
+  a.x_init = l.x_init;
   a.k_traj = l.k_traj;
   a.alpha0 = T(l.alpha0);
   a.lim_tol = l.lim_tol;

@@ -29,7 +29,9 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_static_workspace_capacity", "cr_traj_cost", "cr_traj_workspace_size", "cr_solve_traj",
            "cr_calibrate", "cr_calibrate_workspace_size", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check",
            "cr_batch_workspace_size", "cr_batch_plan_create", "cr_batch_plan_run", "cr_batch_plan_info",
-           "cr_batch_plan_destroy", "cr_solve_batch", "cr_batch_plain_workspace_size", "cr_solve_batch_plain")
+           "cr_batch_plan_destroy", "cr_solve_batch", "cr_batch_plain_workspace_size", "cr_solve_batch_plain",
+           "cr_prm_workspace_size", "cr_prm_build", "cr_prm_query", "cr_traj_prm_workspace_size",
+           "cr_solve_traj_prm")
 
 
 class CrError(RuntimeError):
@@ -95,6 +97,19 @@ class cr_batch_params(C.Structure):
                 ("seeds_per_unit", C.c_int32), ("reserved", C.c_int32)]
 
 
+CR_PRM_MAX_N, CR_PRM_MAX_K, CR_PRM_MAX_CHECK, CR_PRM_MAX_ATTEMPTS = 1024, 32, 64, 8
+
+
+class cr_prm_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("k", C.c_int32), ("n_check", C.c_int32), ("attempts", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class cr_roadmap(C.Structure):
+    _fields_ = [("R", C.c_int64), ("nodes", C.c_void_p), ("node_ok", C.c_void_p), ("nbr", C.c_void_p),
+                ("row", C.c_void_p), ("col", C.c_void_p), ("wt", C.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -144,6 +159,13 @@ _SIGS = {
                        C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
     "cr_solve_batch_plain": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
                              C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
+    "cr_prm_build": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_weights), C.POINTER(cr_prm_params),
+                     C.POINTER(cr_roadmap), _P, C.c_size_t, _P],
+    "cr_prm_query": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_weights), C.POINTER(cr_prm_params),
+                     C.POINTER(cr_roadmap), _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P],
+    "cr_solve_traj_prm": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_traj_task),
+                          C.POINTER(cr_ik_params), C.POINTER(cr_prm_params), C.POINTER(cr_roadmap), C.c_int32,
+                          C.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
 }
 
 
@@ -167,6 +189,10 @@ def load(path: str | None = None):
         L.cr_traj_workspace_size.restype = C.c_size_t
         L.cr_path_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.c_int32, C.POINTER(cr_ik_params)]
         L.cr_path_workspace_size.restype = C.c_size_t
+        L.cr_prm_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.POINTER(cr_prm_params)]
+        L.cr_prm_workspace_size.restype = C.c_size_t
+        L.cr_traj_prm_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64, C.c_int32, C.POINTER(cr_ik_params)]
+        L.cr_traj_prm_workspace_size.restype = C.c_size_t
         L.cr_calibrate_workspace_size.argtypes = [C.POINTER(cr_robot), C.c_int64]
         L.cr_calibrate_workspace_size.restype = C.c_size_t
         for nm in ("cr_batch_workspace_size", "cr_batch_plain_workspace_size"):
@@ -318,6 +344,34 @@ def cr_solve_traj(robot, scene, task, goal_ik, k_traj, alpha0, X_out, cost_out, 
                                 _ptr(X_out), _ptr(cost_out), _ptr(goal_pos), _ptr(goal_rot), _ptr(speed), _ptr(accel),
                                 _ptr(lim_ok), _ptr(col_ok), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_prm_workspace_size(robot, R, prm) -> int:
+    return int(load().cr_prm_workspace_size(C.byref(robot), R, C.byref(prm)))
+
+
+def cr_prm_build(robot, scene, weights, prm, roadmap, workspace, stream=None):
+    _check(load().cr_prm_build(C.byref(robot), C.byref(scene), C.byref(weights), C.byref(prm), C.byref(roadmap),
+                               _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cr_prm_query(robot, scene, weights, prm, roadmap, u_start, u_goal, P, T, X, length, hops, stream=None):
+    _check(load().cr_prm_query(C.byref(robot), C.byref(scene), C.byref(weights), C.byref(prm), C.byref(roadmap),
+                               _ptr(u_start), _ptr(u_goal), P, T, _ptr(X), _ptr(length), _ptr(hops),
+                               _stream(stream)))
+
+
+def cr_traj_prm_workspace_size(robot, P, T, goal_ik) -> int:
+    return int(load().cr_traj_prm_workspace_size(C.byref(robot), P, T, C.byref(goal_ik)))
+
+
+def cr_solve_traj_prm(robot, scene, task, goal_ik, prm, roadmap, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot,
+                      speed, accel, lim_ok, col_ok, length, hops, workspace, stream=None):
+    _check(load().cr_solve_traj_prm(C.byref(robot), C.byref(scene), C.byref(task), C.byref(goal_ik), C.byref(prm),
+                                    C.byref(roadmap), k_traj, alpha0, _ptr(X_out), _ptr(cost_out), _ptr(goal_pos),
+                                    _ptr(goal_rot), _ptr(speed), _ptr(accel), _ptr(lim_ok), _ptr(col_ok),
+                                    _ptr(length), _ptr(hops), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def cr_path_workspace_size(robot, P, H, first_ik) -> int:

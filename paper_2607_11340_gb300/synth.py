@@ -200,6 +200,20 @@ P_TRAJ, T_TRAJ, NO_TRAJ = 256, 32, 64
 IK_GOAL = IkSpec(S=64, n_final=4, k_init=32, k_final=30)     # IK to the goal pose
 K_TRAJ, ALPHA_TRAJ = 100, 1e-3
 
+# PRM initialiser of the trajectory workload (Algorithm 2): one roadmap per problem (each problem has
+# its own spheres) of 256 nodes, 8 nearest neighbours, 8 interior states checked per edge, up to 8
+# draws per node. The paper gives no roadmap size; these are readings.
+@dataclasses.dataclass(frozen=True)
+class PrmSpec:
+    N: int = 256
+    k: int = 8
+    n_check: int = 8
+    attempts: int = 8
+    seed: int = 0x5052_0001
+
+
+PRM_TRAJ = PrmSpec()
+
 # Calibration: 1024 measured tip positions, noise sigma = 0.5 mm, parameters off by up to 5%
 K_CALIB, SIGMA_CALIB, PERTURB_CALIB, ITERS_CALIB = 1024, 5e-4, 0.05, 20
 

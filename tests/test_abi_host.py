@@ -183,3 +183,61 @@ def test_arc_model_is_validated(crlib):
     assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 1, C.byref(p), *([dummy] * 8), dummy, 1 << 30, None) \
         == crlib.CR_EINVAL
     assert C.sizeof(crlib.cr_robot) == crlib.cr_robot.l_max.offset + 8 * crlib.CR_MAX_SEG
+
+
+def test_prm_layout_and_validation(crlib, tmp_path):
+    """PRM structs match the C layout; bad roadmap settings, a roadmap count that fits neither a
+    shared nor a per-query roadmap, and the arc model are refused before any device call."""
+    prog = tmp_path / "prm_layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "cr.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(cr_prm_params), offsetof(cr_prm_params, seed), sizeof(cr_roadmap),
+         offsetof(cr_roadmap, wt));
+  return 0;
+}
+""")
+    exe = tmp_path / "prm_layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out == [C.sizeof(crlib.cr_prm_params), crlib.cr_prm_params.seed.offset, C.sizeof(crlib.cr_roadmap),
+                   crlib.cr_roadmap.wt.offset]
+    L = crlib.load()
+    dummy = C.c_void_p(256)
+    r = _robot(crlib)
+    sc = crlib.cr_scene()
+    w = crlib.cr_weights()
+
+    def prm(N=64, k=8, nc=4, at=8):
+        p = crlib.cr_prm_params()
+        p.N, p.k, p.n_check, p.attempts, p.seed = N, k, nc, at, 1
+        return p
+
+    m = crlib.cr_roadmap()
+    m.R = 2
+    for f in ("nodes", "node_ok", "nbr", "row", "col", "wt"):
+        setattr(m, f, 256)
+    for bad in (prm(N=1), prm(N=2048), prm(k=0), prm(k=64), prm(N=8, k=8), prm(nc=0), prm(nc=65), prm(at=9)):
+        assert L.cr_prm_build(C.byref(r), C.byref(sc), C.byref(w), C.byref(bad), C.byref(m), dummy, 1 << 30,
+                              None) == crlib.CR_EINVAL
+        assert L.cr_prm_workspace_size(C.byref(r), 2, C.byref(bad)) == 0
+    good = prm()
+    assert L.cr_prm_workspace_size(C.byref(r), 2, C.byref(good)) >= 2 * 64 * 8 + 2 * 64 * 2 * 4
+    assert L.cr_prm_build(C.byref(r), C.byref(sc), C.byref(w), C.byref(good), C.byref(m), dummy, 16,
+                          None) == crlib.CR_EINVAL  # workspace too small
+    assert "workspace" in crlib.last_error()
+    # R = 2 roadmaps serve neither 3 queries (needs R = 1 or R = P) ...
+    assert L.cr_prm_query(C.byref(r), C.byref(sc), C.byref(w), C.byref(good), C.byref(m), dummy, dummy, 3, 8,
+                          dummy, dummy, dummy, None) == crlib.CR_EINVAL
+    assert "roadmap count" in crlib.last_error()
+    # ... nor a horizon T outside 2..256
+    assert L.cr_prm_query(C.byref(r), C.byref(sc), C.byref(w), C.byref(good), C.byref(m), dummy, dummy, 2, 1,
+                          dummy, dummy, dummy, None) == crlib.CR_EINVAL
+    r.model = crlib.CR_MODEL_ARC
+    for i in range(3):
+        r.l_min[i], r.l_max[i] = 0.5, 1.5
+    assert L.cr_prm_build(C.byref(r), C.byref(sc), C.byref(w), C.byref(good), C.byref(m), dummy, 1 << 30,
+                          None) == crlib.CR_EINVAL
+    assert "tendon model" in crlib.last_error()
