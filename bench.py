@@ -292,6 +292,10 @@ def other_workload(args):
         gd = torch.as_tensor(goal.T.copy(), dtype=torch.float64, device=dev)
         rm.build(scene, synth.WEIGHTS)
         build_ms = time_steps(torch, lambda: rm.build(scene, synth.WEIGHTS), max(3, args.steps), flush, stream)[1]
+        ugd = torch.empty_like(usd)
+        ugd.copy_(usd.flip(1))  # query timing only: any states in bounds
+        query_ms = time_steps(torch, lambda: rm.query(scene, synth.WEIGHTS, usd, ugd, Tn), max(3, args.steps), flush,
+                              stream)[1]
         fn = lambda: s.solve(usd, gd)
         units, unit = P, "trajectories/s"
         metric = "trajectory planning trajectories/s with the PRM initialiser (goal IK, roadmap query, 100 PG steps)"
@@ -305,7 +309,7 @@ def other_workload(args):
             lin.solve(usd, gd)
             torch.cuda.synchronize()
             h = s.hops.cpu().numpy()
-            return {"roadmap_build_ms": build_ms, "roadmaps": P, "nodes_per_roadmap": ps.N,
+            return {"roadmap_build_ms": build_ms, "roadmap_query_ms": query_ms, "roadmaps": P, "nodes_per_roadmap": ps.N,
                     "valid_node_rate": float(rm.node_ok.float().mean()),
                     "edges_per_roadmap": float(rm.row[:, -1].double().mean() / 2),
                     "path_found_rate": float((h > 0).mean()), "hops_mean": float(h[h > 0].mean()) if (h > 0).any() else 0.0,

@@ -14,15 +14,17 @@ using namespace crh;
 
 namespace {
 
-// Workspace of cr_prm_build: blocked flags [R*N*k] | adjacency bitset [R][N][ceil(N/32)] (uint32).
+// Workspace of cr_prm_build: blocked flags [R*N*k] | adjacency bitset [R][N][ceil(N/32)] (uint32) |
+// FP32 copy of the nodes [3n][R*N].
 struct PrmWs {
-  size_t blocked, adj, total;
+  size_t blocked, adj, nodes32, total;
 };
-PrmWs prm_ws(int64_t R, const cr_prm_params& p) {
+PrmWs prm_ws(int n, int64_t R, const cr_prm_params& p) {
   PrmWs w;
   size_t off = 0;
   w.blocked = off; off = align256(off + (size_t)R * p.N * p.k);
   w.adj = off; off = align256(off + (size_t)R * p.N * crk::prm_words(p.N) * 4);
+  w.nodes32 = off; off = align256(off + (size_t)3 * n * R * p.N * 4);
   w.total = off;
   return w;
 }
@@ -79,7 +81,7 @@ extern "C" {
 
 size_t cr_prm_workspace_size(const cr_robot* robot, int64_t R, const cr_prm_params* prm) {
   if (!robot || !prm || R < 1 || check_prm(prm)) return 0;
-  return prm_ws(R, *prm).total;
+  return prm_ws(robot->n, R, *prm).total;
 }
 
 cr_status cr_prm_build(const cr_robot* robot, const cr_scene* scene, const cr_weights* w, const cr_prm_params* prm,
@@ -91,14 +93,15 @@ cr_status cr_prm_build(const cr_robot* robot, const cr_scene* scene, const cr_we
   if (!w) return fail(CR_EINVAL, "weights are NULL");
   if (map->R > 65535) return fail(CR_EINVAL, "cr_prm_build: R = %lld above 65535", (long long)map->R);
   if ((st = check_ptr(workspace, 256, "workspace", true))) return st;
-  const PrmWs lay = prm_ws(map->R, *prm);
+  const PrmWs lay = prm_ws(robot->n, map->R, *prm);
   if (ws_bytes < lay.total) return fail(CR_EINVAL, "workspace of %zu bytes, %zu needed", ws_bytes, lay.total);
   crk::PrmArgs a = prm_args(*robot, scene, *w, *prm, *map);
   unsigned char* ws = (unsigned char*)workspace;
   a.blocked = ws + lay.blocked;
   a.adj = reinterpret_cast<uint32_t*>(ws + lay.adj);
+  a.nodes32 = reinterpret_cast<float*>(ws + lay.nodes32);
   cudaStream_t s = stream_of(stream);
-  cudaError_t e = cudaMemsetAsync(ws, 0, lay.total, s);
+  cudaError_t e = cudaMemsetAsync(ws, 0, lay.nodes32, s);  // blocked flags and bitset
   if (e != cudaSuccess) return fail(CR_ECUDA, "cr_prm_build: %s", cudaGetErrorString(e));
   switch (robot->n) {
     case 1: return crk::prm_build_n<1>(*robot, a, s);

@@ -17,7 +17,7 @@
 //                 the equal-arc-length resampling.
 //
 // Collision decisions are FP64 (the answer is an integer). An FP32 pass decides first with a
-// margin m_j = 1e-4 (sum L + reach_j + |c_j|_1) per sphere, far above the FP32 error of the backbone
+// margin m_j = 1e-5 (sum L + reach_j + |c_j|_1) per sphere, far above the FP32 error of the backbone
 // points: a pair closer than reach - m collides for certain, a state with no pair within reach + m
 // is free for certain, and only states in between are evaluated again in FP64.
 //
@@ -37,6 +37,9 @@ constexpr int kPrmMaxCheck = 64;
 constexpr int kPrmMaxAttempts = 8;  // the draw counter holds 3 bits of attempt
 constexpr int kPrmQueryThreads = 256;
 constexpr int kPrmKnnWarps = 4;
+// Relative margin of the FP32 collision filter (about 6 um for robots and scenes of 0.3 m, some
+// 60 times the FP32 error of the backbone samples).
+constexpr double kPrmMargin = 1e-5;
 
 struct PrmArgs {
   const double* spheres;  // [R or 1][no][4]
@@ -47,6 +50,7 @@ struct PrmArgs {
   double umax[NMAX];
   double delta;
   double* nodes;          // [D][R*N]
+  float* nodes32;         // [D][R*N] the nodes rounded to FP32 (build workspace: the edge filter's operands)
   unsigned char* ok;      // [R*N]
   int32_t* nbr;           // [R*N][k]
   unsigned char* blocked; // [R*N*k]
@@ -94,7 +98,7 @@ __device__ void prm_stage(const double* sp, int no, const RobotK<double>& rbd, d
   for (int j = threadIdx.x; j < no; j += blockDim.x) {
     const double x = sp[4 * j], y = sp[4 * j + 1], z = sp[4 * j + 2];
     const double reach = sp[4 * j + 3] + rbd.rbody + delta;
-    const double m = 1e-4 * (lsum + reach + fabs(x) + fabs(y) + fabs(z));
+    const double m = kPrmMargin * (lsum + reach + fabs(x) + fabs(y) + fabs(z));
     s.hi[j] = Sphere4<float>{float(x), float(y), float(z), float(reach + m)};
     const double rl = reach - m;
     s.lo2[j] = rl > 0.0 ? float(rl * rl) : 0.0f;
@@ -169,6 +173,35 @@ __device__ __forceinline__ void prm_lerp(const double (&xa)[D], const double (&x
   for (int q = 0; q < D; ++q) x[q] = __dadd_rn(xa[q], __dmul_rn(s, __dsub_rn(xb[q], xa[q])));
 }
 
+// The same state in FP32 for the filter (within a few FP32 roundings of the FP64 state, far inside
+// the margin).
+template <int D>
+__device__ __forceinline__ void prm_lerp32(const double (&xa)[D], const double (&xb)[D], int c, int n_check,
+                                           float (&x)[D]) {
+  const float s = float(c) / float(n_check + 1);
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const float a = float(xa[q]);
+    x[q] = a + s * (float(xb[q]) - a);
+  }
+}
+
+// Does the state c of the segment xa -> xb collide? FP32 filter on the FP32 interpolation; the FP64
+// interpolation and decision only inside the margin band.
+template <int N>
+__device__ bool prm_segment_state_collides(const RobotK<float>& rbf, const RobotK<double>& rbd, const PrmSph& s,
+                                           int no, const double (&xa)[3 * N], const double (&xb)[3 * N], int c,
+                                           int n_check) {
+  if (no == 0) return false;
+  float xf[3 * N];
+  prm_lerp32<3 * N>(xa, xb, c, n_check, xf);
+  const int cl = prm_class32<N>(rbf, s, no, xf);
+  if (cl != 2) return cl == 1;
+  double x[3 * N];
+  prm_lerp<3 * N>(xa, xb, c, n_check, x);
+  return state_collides<double, N>(rbd, s.ex, no, x);
+}
+
 template <int D> __device__ __forceinline__ void prm_load(const double* base, int64_t ld, int64_t col, double (&x)[D]) {
 #pragma unroll
   for (int q = 0; q < D; ++q) x[q] = base[q * ld + col];
@@ -195,7 +228,10 @@ __global__ void __launch_bounds__(128) k_prm_sample(RobotK<float> rbf, RobotK<do
   }
   const int64_t ld = a.R * a.N, c = r * a.N + i;
 #pragma unroll
-  for (int q = 0; q < D; ++q) a.nodes[q * ld + c] = u[q];
+  for (int q = 0; q < D; ++q) {
+    a.nodes[q * ld + c] = u[q];
+    a.nodes32[q * ld + c] = float(u[q]);
+  }
   a.ok[c] = ok ? 1 : 0;
 }
 
@@ -271,12 +307,25 @@ __global__ void __launch_bounds__(256) k_prm_edges(RobotK<float> rbf, RobotK<dou
   const int j = a.nbr[(base + i) * a.k + slot % a.k];
   if (j < 0 || prm_dup(a.nbr, base, a.k, i, j)) return;
   const int lo = i < j ? i : j, hi = i < j ? j : i;
+  if (a.no == 0) return;
   const int64_t ld = a.R * a.N;
-  double xa[D], xb[D], x[D];
-  prm_load<D>(a.nodes, ld, base + lo, xa);
-  prm_load<D>(a.nodes, ld, base + hi, xb);
-  prm_lerp<D>(xa, xb, c, a.n_check, x);
-  if (prm_collides<N>(rbf, rbd, s, a.no, x)) a.blocked[base * a.k + slot] = 1;
+  // FP32 filter on the FP32 interpolation of the FP32 nodes; FP64 only inside the margin band
+  const float sc = float(c) / float(a.n_check + 1);
+  float xf[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    const float fa = a.nodes32[q * ld + base + lo];
+    xf[q] = fa + sc * (a.nodes32[q * ld + base + hi] - fa);
+  }
+  int cl = prm_class32<N>(rbf, s, a.no, xf);
+  if (cl == 2) {
+    double xa[D], xb[D], x[D];
+    prm_load<D>(a.nodes, ld, base + lo, xa);
+    prm_load<D>(a.nodes, ld, base + hi, xb);
+    prm_lerp<D>(xa, xb, c, a.n_check, x);
+    cl = state_collides<double, N>(rbd, s.ex, a.no, x) ? 1 : 0;
+  }
+  if (cl == 1) a.blocked[base * a.k + slot] = 1;
 }
 
 static __global__ void k_prm_adj(PrmArgs a) {
@@ -459,10 +508,10 @@ __global__ void __launch_bounds__(kPrmQueryThreads) k_prm_query(RobotK<float> rb
   for (int e = threadIdx.x; e < (ncand[0] + ncand[1]) * a.n_check; e += blockDim.x) {
     const int ci = e / a.n_check, c = e % a.n_check + 1;
     const int side = ci < ncand[0] ? 0 : 1, slot = side == 0 ? ci : ci - ncand[0];
-    double xv[D], x[D];
+    double xv[D];
     prm_load<D>(a.nodes, ld, base + cand[side * a.k + slot], xv);
-    prm_lerp<D>(side == 0 ? xs : xg, xv, c, a.n_check, x);
-    if (prm_collides<N>(rbf, rbd, s, a.no, x)) blk[side * a.k + slot] = 1;
+    if (prm_segment_state_collides<N>(rbf, rbd, s, a.no, side == 0 ? xs : xg, xv, c, a.n_check))
+      blk[side * a.k + slot] = 1;
   }
   __syncthreads();
   if (threadIdx.x < 2 * a.k) {
@@ -491,8 +540,10 @@ __global__ void __launch_bounds__(kPrmQueryThreads) k_prm_query(RobotK<float> rb
         if (ls[v] < INFINITY && dc[S] + ls[v] < best) best = dc[S] + ls[v];
         if (lg[v] < INFINITY && dc[G] + lg[v] < best) best = dc[G] + lg[v];
       } else if (v == G) {
-        for (int u = 0; u < NN; ++u)
+        for (int c = 0; c < ncand[1]; ++c) {
+          const int u = cand[a.k + c];
           if (lg[u] < INFINITY && dc[u] + lg[u] < best) best = dc[u] + lg[u];
+        }
       }
       changed = changed || best < dc[v];
       dn[v] = best;
@@ -516,9 +567,11 @@ __global__ void __launch_bounds__(kPrmQueryThreads) k_prm_query(RobotK<float> rb
           }
           if (best < 0 && ls[v] < INFINITY && dc[S] < dc[v] && dc[S] + ls[v] == dc[v]) best = S;
           if (best < 0 && lg[v] < INFINITY && dc[G] < dc[v] && dc[G] + lg[v] == dc[v]) best = G;
-        } else {  // v == G
-          for (int u = 0; u < NN && best < 0; ++u)
-            if (lg[u] < INFINITY && dc[u] < dc[v] && dc[u] + lg[u] == dc[v]) best = u;
+        } else {  // v == G: the lowest-index attached node that qualifies
+          for (int c = 0; c < ncand[1]; ++c) {
+            const int u = cand[a.k + c];
+            if (lg[u] < INFINITY && dc[u] < dc[v] && dc[u] + lg[u] == dc[v] && (best < 0 || u < best)) best = u;
+          }
         }
         if (best < 0) { len = 0; break; }
         v = best;

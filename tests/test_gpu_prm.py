@@ -113,7 +113,7 @@ def test_prm_query_degenerate_scene():
 
 def test_fp32_backbone_error_far_below_the_filter_margin():
     """The FP32 pass of the collision decision relies on the FP32 backbone error staying far below
-    its margin 1e-4 (sum L + reach + |c|_1) >= 1e-4 sum L: measured on hexagon-uniform states."""
+    its margin 1e-5 (sum L + reach + |c|_1) >= 1e-5 sum L: measured on hexagon-uniform states."""
     spec = synth.ROBOT_3SEG
     rbo = orc_robot(spec)
     rng = np.random.default_rng(3)
@@ -124,7 +124,7 @@ def test_fp32_backbone_error_far_below_the_filter_margin():
     bb = bb.double().cpu().numpy()
     bb = np.moveaxis(bb, -1, 0).reshape(len(u), -1, 3)
     err = np.abs(bb - bb_ref).max()
-    assert err < 0.1 * 1e-4 * sum(spec.L), err
+    assert err < 0.2 * 1e-5 * sum(spec.L), f"FP32 backbone error {err:.3e} m"
 
 
 @pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
