@@ -65,6 +65,8 @@ crk::PrmArgs prm_args(const cr_robot& r, const cr_scene* scene, const cr_weights
   a.attempts = p.attempts;
   a.seed = p.seed;
   for (int i = 0; i < crk::NMAX; ++i) a.umax[i] = i < r.n ? r.u_max[i] : 0.0;
+  a.coord_max = 0.0;
+  for (int i = 0; i < r.n; ++i) a.coord_max = a.coord_max > r.u_max[i] ? a.coord_max : r.u_max[i];
   a.delta = w.delta;
   a.nodes = m.nodes;
   a.ok = m.node_ok;

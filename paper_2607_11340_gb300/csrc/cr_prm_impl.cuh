@@ -49,6 +49,7 @@ struct PrmArgs {
   uint64_t seed;
   double umax[NMAX];
   double delta;
+  double coord_max;       // largest |node coordinate| (the largest u_max)
   double* nodes;          // [D][R*N]
   float* nodes32;         // [D][R*N] the nodes rounded to FP32 (build workspace: the edge filter's operands)
   unsigned char* ok;      // [R*N]
@@ -235,6 +236,11 @@ __global__ void __launch_bounds__(128) k_prm_sample(RobotK<float> rbf, RobotK<do
   a.ok[c] = ok ? 1 : 0;
 }
 
+// k nearest valid nodes of node i, exactly by (FP64 squared distance, index). FP32 squared distances
+// of the FP32 nodes first: with |coordinates| <= M, u = 2^-24, they differ from the FP64 ones by at
+// most E = 24 u D M^2 + (D + 2) u d^2; t_k, the k-th smallest FP32 value, is then within E of the k-th
+// smallest FP64 value, so every true neighbour has an FP32 value <= t_k + 2E. Only nodes under that
+// threshold (widened 4x) get their FP64 distance; the selection runs on those.
 template <int N>
 __global__ void __launch_bounds__(32 * kPrmKnnWarps) k_prm_knn(PrmArgs a) {
   constexpr int D = 3 * N;
@@ -243,41 +249,96 @@ __global__ void __launch_bounds__(32 * kPrmKnnWarps) k_prm_knn(PrmArgs a) {
   const int64_t r = blockIdx.y;
   const int i = blockIdx.x * kPrmKnnWarps + wid;
   if (i >= a.N) return;
-  double* d2 = reinterpret_cast<double*>(smem_raw) + (size_t)wid * a.N;
+  // per warp: FP64 keys [N] | FP32 squared distances [N] | candidate list [N]
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw) + (size_t)wid * a.N;
+  float* f2 = reinterpret_cast<float*>(smem_raw + (size_t)kPrmKnnWarps * a.N * 8) + (size_t)wid * a.N;
+  int* cl = reinterpret_cast<int*>(smem_raw + (size_t)kPrmKnnWarps * a.N * 12) + (size_t)wid * a.N;
   const int64_t ld = a.R * a.N, base = r * a.N;
   int32_t* out = a.nbr + (base + i) * a.k;
   if (!a.ok[base + i]) {
     for (int c = lane; c < a.k; c += 32) out[c] = -1;
     return;
   }
-  double xi[D];
-  prm_load<D>(a.nodes, ld, base + i, xi);
+  float fi[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) fi[q] = a.nodes32[q * ld + base + i];
   for (int j = lane; j < a.N; j += 32) {
-    double v = INFINITY;
+    float v = INFINITY;
     if (j != i && a.ok[base + j]) {
-      double xj[D];
-      prm_load<D>(a.nodes, ld, base + j, xj);
-      v = prm_dist2<D>(xi, xj);
+      v = 0.0f;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const float t = fi[q] - a.nodes32[q * ld + base + j];
+        v = fmaf(t, t, v);
+      }
     }
-    d2[j] = v;
+    f2[j] = v;
   }
   __syncwarp();
+  // t_k: k rounds of "smallest (value, index) above the previous one"
+  float pv = -1.0f;
+  int pj = -1;
   for (int c = 0; c < a.k; ++c) {
-    double bv = INFINITY;
+    float bv = INFINITY;
     int bj = 0x7fffffff;
     for (int j = lane; j < a.N; j += 32) {
-      const double v = d2[j];
-      if (v < bv) { bv = v; bj = j; }  // ascending j within the lane: ties keep the lower index
+      const float v = f2[j];
+      const bool above = v > pv || (v == pv && j > pj);
+      if (above && (v < bv || (v == bv && j < bj))) { bv = v; bj = j; }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
       const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
       if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
     }
-    const bool found = bv < INFINITY;
+    if (!(bv < INFINITY)) break;
+    pv = bv;
+    pj = bj;
+  }
+  const double u32 = 5.9604644775390625e-8;  // 2^-24
+  float thr = -1.0f;  // FP32 threshold rounded upward
+  if (pj >= 0) {
+    const double t = double(pv) + 8.0 * (24.0 * u32 * D * a.coord_max * a.coord_max + (D + 2) * u32 * double(pv));
+    thr = __double2float_ru(t);
+  }
+  // the candidates in index order (ballot compaction), then their exact FP64 squared distances with
+  // the lanes over the list, kept as bit patterns: for non-negative doubles the unsigned order of the
+  // bits is the order of the values
+  int nc = 0;
+  for (int j0 = 0; j0 < a.N; j0 += 32) {
+    const int j = j0 + lane;
+    const bool cand = j < a.N && f2[j] <= thr;
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (cand) cl[nc + __popc(m & ((1u << lane) - 1u))] = j;
+    nc += __popc(m);
+  }
+  __syncwarp();
+  double xi[D];
+  prm_load<D>(a.nodes, ld, base + i, xi);
+  for (int e = lane; e < nc; e += 32) {
+    double xj[D];
+    prm_load<D>(a.nodes, ld, base + cl[e], xj);
+    key[e] = (unsigned long long)__double_as_longlong(prm_dist2<D>(xi, xj));
+  }
+  __syncwarp();
+  for (int c = 0; c < a.k; ++c) {
+    unsigned long long bv = ~0ull;
+    int bj = 0x7fffffff, be = -1;
+    for (int e = lane; e < nc; e += 32) {
+      const unsigned long long v = key[e];
+      if (v < bv) { bv = v; bj = cl[e]; be = e; }  // ascending index within the lane
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, off);
+      const int oj = __shfl_xor_sync(0xffffffffu, bj, off);
+      const int oe = __shfl_xor_sync(0xffffffffu, be, off);
+      if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; be = oe; }
+    }
+    const bool found = bv != ~0ull;
     if (lane == 0) out[c] = found ? bj : -1;
-    if (found && lane == (bj & 31)) d2[bj] = INFINITY;
+    if (found && lane == (be & 31)) key[be] = ~0ull;
     __syncwarp();
   }
 }
@@ -651,7 +712,8 @@ template <int N> cr_status prm_build_n(const cr_robot& robot, const PrmArgs& a, 
   k_prm_sample<N><<<dim3((a.N + 127) / 128, R), 128, sb, st>>>(rbf, rbd, a);
   cr_status s;
   if ((s = crh::check_launch("k_prm_sample"))) return s;
-  const size_t kb = (size_t)kPrmKnnWarps * a.N * sizeof(double);
+  const size_t kb = (size_t)kPrmKnnWarps * a.N * 16;
+  if ((s = prm_set_smem((const void*)k_prm_knn<N>, kb, "k_prm_knn"))) return s;
   k_prm_knn<N><<<dim3((a.N + kPrmKnnWarps - 1) / kPrmKnnWarps, R), 32 * kPrmKnnWarps, kb, st>>>(a);
   if ((s = crh::check_launch("k_prm_knn"))) return s;
   const int64_t ne = (int64_t)a.N * a.k * a.n_check;
