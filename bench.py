@@ -159,6 +159,43 @@ def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=Non
     return done / dt, done, threads, dt, succ, u
 
 
+def cpu_oracle_traj_prm(us, goal, sph, ps, budget_s=15.0, threads=None):
+    """Oracle trajectories/s with the PRM initialiser (goal IK, roadmap build, query, refinement) on
+    host cores over the first problems: one problem per thread at a time, until the budget is spent.
+    Returns (rate, problems, threads, seconds, success flags)."""
+    import concurrent.futures as cf
+
+    import oracle as O
+
+    O.build()
+    spec, ik = synth.ROBOT_3SEG, synth.IK_GOAL
+    rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius)
+    W = O.make_weights(**synth.WEIGHTS.as_dict())
+    threads = threads or os.cpu_count()
+    Tn = synth.T_TRAJ
+
+    def one(p):
+        cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
+                         alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, seed=ik.seed, p0=p)
+        ug = O.solve_ik(rb, W, sph[p], O.IK6, goal[p:p + 1], cfg, threads=1)["u"][0]
+        rm = O.prm_build(rb, synth.WEIGHTS.delta, sph[p], ps.seed, p, ps.N, ps.k, ps.n_check, ps.attempts)
+        X0 = O.prm_query(rb, synth.WEIGHTS.delta, sph[p], rm, ps.k, ps.n_check, us[p], ug, Tn)[0]
+        r = O.traj_refine(rb, W, sph[p:p + 1], us[p:p + 1], goal[p:p + 1], X0[None], synth.K_TRAJ, synth.ALPHA_TRAJ,
+                          threads=1)
+        return bool(r["col_ok"][0] and r["lim_ok"][0] and r["goal_pos"][0] <= 1e-3
+                    and r["goal_rot"][0] <= np.deg2rad(1.0))
+
+    done, dt, succ = 0, 0.0, []
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while dt < budget_s and done < len(us):
+            m = min(threads, len(us) - done)
+            t0 = time.perf_counter()
+            succ += list(ex.map(one, range(done, done + m)))
+            dt += time.perf_counter() - t0
+            done += m
+    return done / dt, done, threads, dt, np.array(succ)
+
+
 def reference_arm(args):
     """Times the FP64 CPU oracle (as it stands) on the benchmark workload, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -309,7 +346,17 @@ def other_workload(args):
             lin.solve(usd, gd)
             torch.cuda.synchronize()
             h = s.hops.cpu().numpy()
-            return {"roadmap_build_ms": build_ms, "roadmap_query_ms": query_ms, "roadmaps": P, "nodes_per_roadmap": ps.N,
+            base = {}
+            if not args.no_baseline:
+                rate, n, cores, dt, osucc = cpu_oracle_traj_prm(us, goal, sph, ps)
+                gs = success(s)[:n].cpu().numpy().astype(bool)
+                base = {"cpu_baseline": {"value": rate, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+                                         "sample": f"first {n} problems: goal IK, roadmap build, query and "
+                                                   f"refinement per problem ({dt:.1f} s on {cores} threads)"},
+                        "oracle_agreement": {"problems": n, "success_rate_oracle": float(osucc.mean()),
+                                             "success_rate_gpu": float(gs.mean()),
+                                             "success_flag_mismatches": int((gs != osucc).sum())}}
+            return {**base, "roadmap_build_ms": build_ms, "roadmap_query_ms": query_ms, "roadmaps": P, "nodes_per_roadmap": ps.N,
                     "valid_node_rate": float(rm.node_ok.float().mean()),
                     "edges_per_roadmap": float(rm.row[:, -1].double().mean() / 2),
                     "path_found_rate": float((h > 0).mean()), "hops_mean": float(h[h > 0].mean()) if (h > 0).any() else 0.0,
