@@ -169,3 +169,24 @@ def test_solve_traj_prm_parity(prec):
             _, _, lim, col = O.accept(rbo, sph[p], lib.CR_TASK_IK6, np.repeat(goal[p:p + 1], Tn, 0), X[p])
             assert bool(sol.col_ok[p].item()) == bool(col.all())
         assert np.all(sol.hops.cpu().numpy() >= 0)
+
+
+@pytest.mark.parametrize("n,N,k,nc,T", [(1, 64, 5, 3, 9), (2, 2, 1, 2, 5), (4, 80, 6, 3, 256), (6, 64, 5, 2, 17)])
+def test_prm_other_segment_counts(n, N, k, nc, T):
+    """Roadmaps and queries of 1, 2, 4 and 6-segment robots (each a separate kernel instantiation),
+    the smallest roadmap (N = 2, k = 1) and the longest horizon (T = 256), against the oracle."""
+    spec = synth.RobotSpec(L=(0.1,) * n, rc=0.005, umax=0.01, nb=8)
+    P = 2
+    robot, rbo, us, goal, sph, ug = _case(P, 16, seed=100 + n, spec=spec)
+    ps = synth.PrmSpec(N=N, k=k, n_check=nc, attempts=8, seed=0x5052_0006)
+    scene = api.Scene(sph, per_problem=True)
+    rm = api.Roadmap(robot, ps, P).build(scene, synth.WEIGHTS)
+    X, length, hops = rm.query(scene, synth.WEIGHTS, dev_soa(us, torch.float64), dev_soa(ug, torch.float64), T)
+    torch.cuda.synchronize()
+    X = X.cpu().numpy().T.reshape(P, T, -1)
+    for p in range(P):
+        ref = _oracle_map(rbo, sph[p], ps, p)
+        _check_graph(rm.graph(p), ref)
+        Xr, Lr, Hr, _ = O.prm_query(rbo, DELTA, sph[p], ref, ps.k, ps.n_check, us[p], ug[p], T)
+        assert hops[p].item() == Hr and length[p].item() == Lr
+        np.testing.assert_array_equal(X[p], Xr)
