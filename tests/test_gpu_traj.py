@@ -140,11 +140,12 @@ def test_solve_traj_parity(prec):
         assert np.all(sol.goal_pos.cpu().numpy() < 1e-3) == np.all(ref["goal_pos"] < 1e-3)
 
 
-@pytest.mark.parametrize("n_spheres", [1, 5])
+@pytest.mark.parametrize("n_spheres", [1, 5, 9])
 def test_solve_traj_fp32_split_edges(n_spheres):
     """FP32 trajectory solve with 20 states (a ragged warp) and an odd number of spheres (two
-    threads per state take 3 and 2 of them) or a single sphere (no split): the result is valid
-    under the oracle's own evaluation of the GPU's states and its cost is close to the oracle's."""
+    threads per state take 3 and 2, or 5 and 4, of them) or a single sphere (no split): the result
+    is valid under the oracle's own evaluation of the GPU's states and its cost is close to the
+    oracle's."""
     spec = synth.ROBOT_3SEG
     rbo = orc_robot(spec)
     P, Tn = 4, 20
