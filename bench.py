@@ -237,6 +237,25 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def shard_p0(rank: int, P: int) -> int:
+    """Seed-counter offset of a rank's problems: rank r solves problems r P .. (r + 1) P - 1 of the
+    job, so the counter-based seeds of every problem are those of one process solving them all."""
+    return rank * P
+
+
+def max_over_ranks(torch, dist, world, total_ms, device):
+    """The job's time: the largest of the ranks' summed step times (all_reduce MAX)."""
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, P, ms_per_step):
+    """Whole-job throughput: all ranks' problems over the slowest rank's step time."""
+    return world * P / (ms_per_step / 1e3)
+
+
 def time_steps(torch, fn, steps, flush, stream):
     """Median and mean of CUDA-event times of fn() over `steps` steps, L2 flushed before each."""
     ts = []
@@ -549,7 +568,7 @@ def main():
     tg = make_targets(torch, api, lib, spec, P, seed=rank, device=dev)
     tg_dev = torch.as_tensor(tg.T.copy(), dtype=torch.float64, device=dev)
     solver = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, precision=lib.CR_F32, device=dev)
-    p0 = rank * P
+    p0 = shard_p0(rank, P)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MiB > 129 MB L2
     stream = torch.cuda.current_stream()
 
@@ -577,11 +596,8 @@ def main():
     barrier()
     clocks = clk.stop()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    tot = torch.tensor([step_ms.sum()], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    ms_per_step = float(tot.item()) / args.steps
-    value = world * P / (ms_per_step / 1e3)
+    ms_per_step = max_over_ranks(torch, dist, world, step_ms.sum(), dev) / args.steps
+    value = job_rate(world, P, ms_per_step)
     res = solver.out
     succ = float(res.success.float().mean().item())
     pos_med = float(res.pos_err.median().item())
@@ -632,10 +648,7 @@ def main():
         t0 = time.perf_counter()
         solver.solve_host(tg_host, out_host, p0=p0)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_t = torch.tensor([float(np.sum(e2e_ms))], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * P / (float(e2e_t.item()) / args.steps / 1e3)
+    e2e_value = job_rate(world, P, max_over_ranks(torch, dist, world, np.sum(e2e_ms), dev) / args.steps)
     h2d = tg_host.numel() * 8
     d2h = sum(v.numel() * v.element_size() for v in out_host.values())
 
