@@ -12,6 +12,11 @@ CR_PRM_INSTANTIATE(extern, 6)
 
 using namespace crh;
 
+static_assert(crk::kPrmMaxN == CR_PRM_MAX_N && crk::kPrmMaxK == CR_PRM_MAX_K &&
+                  crk::kPrmMaxCheck == CR_PRM_MAX_CHECK && crk::kPrmMaxAttempts == CR_PRM_MAX_ATTEMPTS,
+              "PRM limits of the header and the kernels");
+static_assert(CR_PRM_MAX_N <= 1024, "k_prm_csr runs one thread per node in one block");
+
 namespace {
 
 // Workspace of cr_prm_build: blocked flags [R*N*k] | adjacency bitset [R][N][ceil(N/32)] (uint32) |
