@@ -52,12 +52,21 @@ def test_prm_build_matches_oracle(N, k, nc, n_spheres):
 
 
 def test_prm_build_maximum_sizes():
-    """N = 1024 nodes and k = 32 neighbours on one shared scene."""
-    robot, rbo, us, goal, sph, ug = _case(1, 16, seed=80)
+    """N = 1024 nodes and k = 32 neighbours on one shared scene, and two queries on it."""
+    robot, rbo, us, goal, sph, ug = _case(2, 16, seed=80)
     ps = synth.PrmSpec(N=1024, k=32, n_check=2, attempts=8, seed=0x5052_0002)
-    rm = api.Roadmap(robot, ps, 1).build(api.Scene(sph[0]), synth.WEIGHTS)
+    scene = api.Scene(sph[0])
+    rm = api.Roadmap(robot, ps, 1).build(scene, synth.WEIGHTS)
     torch.cuda.synchronize()
-    _check_graph(rm.graph(0), _oracle_map(rbo, sph[0], ps, 0))
+    ref = _oracle_map(rbo, sph[0], ps, 0)
+    _check_graph(rm.graph(0), ref)
+    X, length, hops = rm.query(scene, synth.WEIGHTS, dev_soa(us, torch.float64), dev_soa(ug, torch.float64), 33)
+    torch.cuda.synchronize()
+    X = X.cpu().numpy().T.reshape(2, 33, -1)
+    for p in range(2):
+        Xr, Lr, Hr, _ = O.prm_query(rbo, DELTA, sph[0], ref, ps.k, ps.n_check, us[p], ug[p], 33)
+        assert hops[p].item() == Hr and length[p].item() == Lr
+        np.testing.assert_array_equal(X[p], Xr)
 
 
 @pytest.mark.parametrize("shared", [False, True])
