@@ -214,3 +214,37 @@ def test_traj_refine_from_linear_equals_solve_traj(orc):
     out = orc.traj_refine(rb, W, sph, us, goal, X0, 5, 1e-3, threads=1)
     for key in ("x", "F", "goal_pos", "goal_rot", "speed", "accel", "lim_ok", "col_ok"):
         np.testing.assert_array_equal(out[key], ref[key])
+
+
+def _tie_roadmap(first):
+    """Two middle nodes A = (4, 3) and B = (4, -3) between start (0, 0) and goal (8, 0) (3-4-5
+    triangles: every weight is exactly 5, both paths exactly 10), no roadmap edges; `first` says
+    which of them has index 0."""
+    d = SPEC.d
+    nodes = np.zeros((2, d))
+    a, b = (0, 1) if first == "A" else (1, 0)
+    nodes[a, :2] = (4.0, 3.0)
+    nodes[b, :2] = (4.0, -3.0)
+    return dict(nodes=nodes, ok=np.ones(2, bool), row=np.zeros(3, np.int32), col=np.zeros(0, np.int32),
+                wt=np.zeros(0)), a
+
+
+@pytest.mark.parametrize("first", ["A", "B"])
+def test_prm_query_tie_takes_the_lowest_index(orc, first):
+    """Exactly tied shortest paths: the path runs through the lower-index middle node, and the
+    equal-arc-length states are the exact points of that polyline."""
+    rb = _rb(orc)
+    rm, a = _tie_roadmap(first)
+    us, ug = np.zeros(SPEC.d), np.zeros(SPEC.d)
+    ug[0] = 8.0
+    X, length, hops, path = orc.prm_query(rb, synth.WEIGHTS.delta, None, rm, 2, 1, us, ug, 5)
+    assert length == 10.0 and hops == 2
+    assert list(path) == [2, 0, 3]  # start (N), the index-0 node, goal (N + 1)
+    mid = rm["nodes"][0]
+    want = np.zeros((5, SPEC.d))
+    want[1, :2] = mid[:2] / 2
+    want[2] = mid
+    want[3, :2] = (mid[:2] + ug[:2]) / 2
+    want[4] = ug
+    np.testing.assert_array_equal(X, want)
+    assert mid[1] == (3.0 if first == "A" else -3.0)
