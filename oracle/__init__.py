@@ -560,6 +560,19 @@ def prm_query(robot, delta, spheres, rm, k, n_check, u_start, u_goal, T):
     return X, length.value, hops.value, path[:hops.value + 1].copy() if hops.value > 0 else path[:0].copy()
 
 
+def self_rows(robot, rho_s, delta, u, gradient=False):
+    """Self-contact rows r [B][rows], cost F [B] and (gradient=True) dF/du [B][d] of states u [B][d]."""
+    u = np.ascontiguousarray(_f64(u).reshape(-1, robot.n * robot.m))
+    B, d = u.shape
+    nr = lib().orc_self_row_count(C.byref(robot))
+    r = np.zeros((B, max(nr, 1)))
+    F = np.zeros(B)
+    g = np.zeros((B, d)) if gradient else None
+    lib().orc_self_rows(C.byref(robot), C.c_double(rho_s), C.c_double(delta), _dp(u), C.c_int64(B), _dp(r), _dp(F),
+                        _dp(g))
+    return r[:, :nr], F, g
+
+
 def calibrate(robot, U, Pm, theta0, iters, lambda0=1e-3, history=False):
     """LM on theta = (L_1..n, r_c,1..n) from known displacements U [K][d] and tip positions Pm [K][3]."""
     U, Pm = _f64(U), _f64(Pm)

@@ -33,6 +33,8 @@
 //   * Kinematic calibration of segment lengths and tendon radii from measured tip positions (LM).
 //   * PRM exploration of Algorithm 2: ParallelSample, ParallelConnect (k nearest neighbours and
 //     collision-checked straight edges), ConnectToRoadmap, Dijkstra and ResampleLinear.
+//   * Self-contact rows between backbone samples of non-adjacent segments (Eq. ik_coll over the
+//     robot itself), as standalone functions.
 //
 // Derivatives are taken by the complex-step method (Squire and Trapp 1998): for a real-analytic
 // function f, f'(x) = Im f(x + i h) / h up to O(h^2), with no subtractive cancellation, so with
@@ -2006,6 +2008,75 @@ int orc_prm_query(const OrRobot* rb, double delta, int no, const double* spheres
     const double lam = (s - dist[pth[j]]) / (dist[pth[j + 1]] - dist[pth[j]]);
     const double *xa = xv(pth[j]), *xb = xv(pth[j + 1]);
     for (int a = 0; a < d; ++a) x[a] = xa[a] + lam * (xb[a] - xa[a]);
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Self-contact rows (the robot itself in Eq. ik_coll's minimum distance, Sec. IV-A), defined here
+// ahead of any residual that uses them. Reading: backbone samples a of segment i and b of segment
+// j >= i + 2 (adjacent segments meet at a joint, so their samples near it are always closer than any
+// clearance), row sqrt(rho_s) max(0, 2 r_body + delta - |p_a - p_b|); rows in the order i, sample of
+// i, j, sample of j. F = 1/2 sum r^2.
+// ---------------------------------------------------------------------------------------------
+static int self_row_count(const OrRobot& rb) {
+  int c = 0;
+  for (int i = 0; i < rb.n; ++i)
+    for (int j = i + 2; j < rb.n; ++j) c += rb.nb * rb.nb;
+  return c;
+}
+
+template <class T>
+static int self_rows(const OrRobot& rb, const Params<T>& P, const T* u, double rho_s, double delta, T* r) {
+  FkOut<T> fk;
+  std::vector<T> bb(3 * rb.n * rb.nb);
+  forward_kinematics(rb, P, u, fk, bb.data());
+  const double gap = 2.0 * rb.rbody + delta;
+  const T s = T(std::sqrt(rho_s));
+  int k = 0;
+  for (int i = 0; i < rb.n; ++i)
+    for (int ka = 0; ka < rb.nb; ++ka)
+      for (int j = i + 2; j < rb.n; ++j)
+        for (int kb = 0; kb < rb.nb; ++kb) {
+          const T* pa = bb.data() + 3 * (i * rb.nb + ka);
+          const T* pb = bb.data() + 3 * (j * rb.nb + kb);
+          T dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+          T d2 = dx * dx + dy * dy + dz * dz;
+          r[k++] = re(d2) < gap * gap ? s * (T(gap) - Sqrt(d2)) : T(0.0);
+        }
+  return k;
+}
+
+extern "C" {
+
+int orc_self_row_count(const OrRobot* rb) { return self_row_count(*rb); }
+
+// Self-contact rows r [B][rows] and cost F [B] of states u [B][d]; with g (nullable) also the
+// complex-step gradient dF/du [B][d].
+int orc_self_rows(const OrRobot* rb, double rho_s, double delta, const double* u, int64_t B, double* r, double* F,
+                  double* g) {
+  const int d = rb->n * rb->m, nr = self_row_count(*rb);
+  Params<double> P = params_of<double>(*rb);
+  Params<cd> Pc = params_of<cd>(*rb);
+  std::vector<cd> rc(nr > 0 ? nr : 1), uc(d);
+  for (int64_t b = 0; b < B; ++b) {
+    const double* x = u + (size_t)d * b;
+    double* rr = r + (size_t)nr * b;
+    self_rows(*rb, P, x, rho_s, delta, rr);
+    double f = 0.0;
+    for (int k = 0; k < nr; ++k) f += 0.5 * rr[k] * rr[k];
+    F[b] = f;
+    if (!g) continue;
+    const double h = 1e-30;
+    for (int q = 0; q < d; ++q) {
+      for (int a = 0; a < d; ++a) uc[a] = cd(x[a], a == q ? h : 0.0);
+      self_rows(*rb, Pc, uc.data(), rho_s, delta, rc.data());
+      cd fc(0.0);
+      for (int k = 0; k < nr; ++k) fc += 0.5 * rc[k] * rc[k];
+      g[(size_t)d * b + q] = fc.imag() / h;
+    }
   }
   return 0;
 }
