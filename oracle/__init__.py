@@ -573,6 +573,22 @@ def self_rows(robot, rho_s, delta, u, gradient=False):
     return r[:, :nr], F, g
 
 
+def routing_b_from_a(robot, u):
+    """Model A per-segment displacements u [B][n m] -> model B actuator displacements q (prefix sums)."""
+    u = np.ascontiguousarray(_f64(u).reshape(-1, robot.n * robot.m))
+    q = np.zeros_like(u)
+    lib().orc_routing_b_from_a(C.byref(robot), _dp(u), C.c_int64(len(u)), _dp(q))
+    return q
+
+
+def routing_a_from_b(robot, q):
+    """Model B actuator displacements q [B][n m] -> model A per-segment displacements u."""
+    q = np.ascontiguousarray(_f64(q).reshape(-1, robot.n * robot.m))
+    u = np.zeros_like(q)
+    lib().orc_routing_a_from_b(C.byref(robot), _dp(q), C.c_int64(len(q)), _dp(u))
+    return u
+
+
 def calibrate(robot, U, Pm, theta0, iters, lambda0=1e-3, history=False):
     """LM on theta = (L_1..n, r_c,1..n) from known displacements U [K][d] and tip positions Pm [K][3]."""
     U, Pm = _f64(U), _f64(Pm)

@@ -35,6 +35,8 @@
 //     collision-checked straight edges), ConnectToRoadmap, Dijkstra and ResampleLinear.
 //   * Self-contact rows between backbone samples of non-adjacent segments (Eq. ik_coll over the
 //     robot itself), as standalone functions.
+//   * Coupled tendon routing (Eq. l_eq summed over the segments a tendon runs through): the map
+//     between per-segment and actuator displacements, as standalone functions.
 //
 // Derivatives are taken by the complex-step method (Squire and Trapp 1998): for a real-analytic
 // function f, f'(x) = Im f(x + i h) / h up to O(h^2), with no subtractive cancellation, so with
@@ -2078,6 +2080,44 @@ int orc_self_rows(const OrRobot* rb, double rho_s, double delta, const double* u
       g[(size_t)d * b + q] = fc.imag() / h;
     }
   }
+  return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Coupled tendon routing (Eq. l_eq read literally: tendon j of the robot runs through several
+// segments and its length is the sum of the per-segment lengths of Eq. 4). Model B: the tendons
+// that terminate at segment s run through segments 1..s at the angles alpha_j, so the actuator
+// displacement of tendon j of segment s is the prefix sum q_sj = sum_{i <= s} u_ij of the
+// per-segment displacements u_ij = l_ij - L_i used everywhere above (model A); conversely
+// u_sj = q_sj - q_(s-1)j. Standalone, ahead of any solver that takes actuator displacements.
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+// u [B][n m] (model A) -> q [B][n m] (model B actuator displacements).
+int orc_routing_b_from_a(const OrRobot* rb, const double* u, int64_t B, double* q) {
+  const int n = rb->n, m = rb->m;
+  for (int64_t b = 0; b < B; ++b)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) {
+        s = s + u[(size_t)b * n * m + i * m + j];
+        q[(size_t)b * n * m + i * m + j] = s;
+      }
+    }
+  return 0;
+}
+
+// q [B][n m] (model B) -> u [B][n m] (model A).
+int orc_routing_a_from_b(const OrRobot* rb, const double* q, int64_t B, double* u) {
+  const int n = rb->n, m = rb->m;
+  for (int64_t b = 0; b < B; ++b)
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double* qb = q + (size_t)b * n * m;
+        u[(size_t)b * n * m + i * m + j] = i == 0 ? qb[j] : qb[i * m + j] - qb[(i - 1) * m + j];
+      }
   return 0;
 }
 

@@ -1,0 +1,52 @@
+"""Pins of the oracle's coupled tendon routing (model B): the actuator displacement of the tendons
+that end at segment s equals Eq. l_eq's sum over segments 1..s of the per-segment tendon lengths
+of Eq. 4 minus the segment lengths (for s = n, the paper's total tendon length l_j(q)); the map
+back to per-segment displacements inverts it; a single segment is model A."""
+import numpy as np
+
+from paper_2607_11340_gb300 import synth
+
+
+def _case(orc, n=4, B=16, seed=3):
+    spec = synth.RobotSpec(L=(0.12, 0.10, 0.08, 0.11)[:n], rc=0.005, umax=0.01)
+    rb = orc.make_robot(list(spec.L), spec.rc, spec.umax)
+    u = synth.hexagon_states(np.random.default_rng(seed), B, n, spec.umax)
+    return spec, rb, u
+
+
+def test_actuator_displacements_are_eq_leq_sums(orc):
+    spec, rb, u = _case(orc)
+    q = orc.routing_b_from_a(rb, u).reshape(len(u), spec.n, 3)
+    tp = orc.bend(rb, u)  # (theta_i, phi_i) by the inverse of Eq. 4
+    for b in range(len(u)):
+        seg = np.array([orc.tendon_lengths(spec.rc, spec.L[i], tp[b, i, 0], tp[b, i, 1]) for i in range(spec.n)])
+        for s in range(spec.n):
+            total = seg[:s + 1].sum(axis=0)  # Eq. l_eq over the segments the tendons run through
+            np.testing.assert_allclose(q[b, s], total - sum(spec.L[:s + 1]), rtol=0, atol=1e-15)
+
+
+def test_routing_round_trip_and_single_segment(orc):
+    spec, rb, u = _case(orc)
+    back = orc.routing_a_from_b(rb, orc.routing_b_from_a(rb, u))
+    np.testing.assert_allclose(back, u, rtol=0, atol=4 * np.finfo(float).eps * spec.umax * spec.n)
+    q = np.random.default_rng(4).uniform(-0.02, 0.02, (8, 12))
+    np.testing.assert_allclose(orc.routing_b_from_a(rb, orc.routing_a_from_b(rb, q)), q, rtol=0,
+                               atol=8 * np.finfo(float).eps * 0.02)
+    spec1, rb1, u1 = _case(orc, n=1)
+    np.testing.assert_array_equal(orc.routing_b_from_a(rb1, u1), u1)
+    np.testing.assert_array_equal(orc.routing_a_from_b(rb1, u1), u1)
+
+
+def test_model_b_fk_is_model_a_fk_of_the_differences(orc):
+    """FK in actuator coordinates: the segment bends follow from the differences of consecutive
+    actuator displacements, so a displacement common to all segments' tendon j (q_sj = c for every
+    s) bends only the first segment."""
+    spec, rb, _ = _case(orc)
+    q = np.zeros((1, 12))
+    q[0, 0::3] = 0.006
+    q[0, 1::3] = -0.003
+    q[0, 2::3] = -0.003
+    u = orc.routing_a_from_b(rb, q)
+    assert np.all(u[0, 3:] == 0) and np.allclose(u[0, :3], [0.006, -0.003, -0.003])
+    tp = orc.bend(rb, u)
+    assert tp[0, 0, 0] > 0 and np.all(tp[0, 1:, 0] == 0)
