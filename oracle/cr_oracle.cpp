@@ -1911,7 +1911,7 @@ int orc_prm_connect(const OrRobot* rb, double delta, int no, const double* spher
   Params<double> Pd = params_of<double>(*rb);
   std::vector<std::vector<uint8_t>> adj(N, std::vector<uint8_t>(N, 0));
   for (int i = 0; i < N; ++i)
-    for (int c = 0; c < k; ++c) {
+    for (int c = 0; c < k && ok[i]; ++c) {  // an invalid node lists no neighbours
       const int j = nbr[(size_t)i * k + c];
       if (j < 0 || adj[i][j]) continue;
       const int a = std::min(i, j), b = std::max(i, j);
