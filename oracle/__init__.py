@@ -581,6 +581,14 @@ def routing_b_from_a(robot, u):
     return q
 
 
+def routing_b_grad(robot, g_u):
+    """Gradient with respect to model B actuator displacements from the model A gradient g_u."""
+    g_u = np.ascontiguousarray(_f64(g_u).reshape(-1, robot.n * robot.m))
+    g_q = np.zeros_like(g_u)
+    lib().orc_routing_b_grad(C.byref(robot), _dp(g_u), C.c_int64(len(g_u)), _dp(g_q))
+    return g_q
+
+
 def routing_a_from_b(robot, q):
     """Model B actuator displacements q [B][n m] -> model A per-segment displacements u."""
     q = np.ascontiguousarray(_f64(q).reshape(-1, robot.n * robot.m))

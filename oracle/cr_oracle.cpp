@@ -2109,6 +2109,19 @@ int orc_routing_b_from_a(const OrRobot* rb, const double* u, int64_t B, double* 
   return 0;
 }
 
+// Gradient in actuator coordinates: with u = D q (u_s = q_s - q_(s-1)), g_q = D^T g_u, i.e.
+// g_q,sj = g_u,sj - g_u,(s+1)j (and g_u,nj for the last segment). g_u, g_q [B][n m].
+int orc_routing_b_grad(const OrRobot* rb, const double* g_u, int64_t B, double* g_q) {
+  const int n = rb->n, m = rb->m;
+  for (int64_t b = 0; b < B; ++b)
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < n; ++i) {
+        const double* g = g_u + (size_t)b * n * m;
+        g_q[(size_t)b * n * m + i * m + j] = i + 1 < n ? g[i * m + j] - g[(i + 1) * m + j] : g[i * m + j];
+      }
+  return 0;
+}
+
 // q [B][n m] (model B) -> u [B][n m] (model A).
 int orc_routing_a_from_b(const OrRobot* rb, const double* q, int64_t B, double* u) {
   const int n = rb->n, m = rb->m;

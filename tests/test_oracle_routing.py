@@ -50,3 +50,24 @@ def test_model_b_fk_is_model_a_fk_of_the_differences(orc):
     assert np.all(u[0, 3:] == 0) and np.allclose(u[0, :3], [0.006, -0.003, -0.003])
     tp = orc.bend(rb, u)
     assert tp[0, 0, 0] > 0 and np.all(tp[0, 1:, 0] == 0)
+
+
+def test_actuator_gradient_is_the_transposed_difference_map(orc):
+    """F_B(q) = F_A(D q) with the IK cost F_A: the gradient from routing_b_grad (D^T of the model A
+    gradient) matches central differences in q; the actuator feasible set is again per-segment
+    hexagons (sum_j q_sj = 0 for every s when every segment's displacements sum to zero)."""
+    spec, rb, u = _case(orc, B=3)
+    W = orc.make_weights(**synth.WEIGHTS.as_dict())
+    tgt = synth.pose_targets(orc.fk(rb, synth.hexagon_states(np.random.default_rng(8), 1, spec.n, spec.umax))[0],
+                             "pose")
+    q = orc.routing_b_from_a(rb, u)
+    assert np.abs(q.reshape(len(q), spec.n, 3).sum(axis=2)).max() < 1e-17
+
+    def F_B(qq):
+        return orc.ik_eval(rb, W, None, orc.IK6, tgt, len(qq), orc.routing_a_from_b(rb, qq), want=("F",))["F"]
+
+    g_u = orc.ik_eval(rb, W, None, orc.IK6, tgt, len(u), u, want=("g",))["g"]
+    g_q = orc.routing_b_grad(rb, g_u)
+    h = 1e-7
+    fd = np.stack([(F_B(q + h * e) - F_B(q - h * e)) / (2 * h) for e in np.eye(q.shape[1])], axis=1)
+    np.testing.assert_allclose(g_q, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
