@@ -26,6 +26,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cr_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libcr_oracle.so")
+# A prebuilt oracle library to load instead (the mutation tests point this at a copy of the oracle
+# with one planted mistake, built in a temporary directory, to show that a pin catches it).
+_SO_OVERRIDE = os.environ.get("CR_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
@@ -35,6 +38,8 @@ IK6, IK5 = 0, 1
 
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (FP64, no fast-math, no FMA contraction)."""
+    if _SO_OVERRIDE:
+        return _SO_OVERRIDE
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
@@ -257,6 +262,37 @@ def lm_linear(A, y, x0, iters, lambda0=1e-3):
     lib().orc_lm_linear(_dp(A), _dp(y), C.c_int(A.shape[0]), C.c_int(A.shape[1]), _dp(x),
                         C.c_int(iters), C.byref(lam), C.byref(nu), C.byref(F))
     return x, lam.value, nu.value, F.value
+
+
+def pg_quadratic(c, b, u0, steps, alpha0):
+    """The stage-one step rule on F(u) = 1/2 |u - c|^2 over per-segment hexagons (3 tendons each,
+    bounds b[i]). Returns (u, F, hist) with hist [steps][3 n + 2] = iterate, alpha, F after each step."""
+    c = _f64(c)
+    u = _f64(u0).copy()
+    b = _f64(np.atleast_1d(b))
+    F = C.c_double(0)
+    hist = np.zeros((steps, u.size + 2))
+    lib().orc_pg_quadratic(_dp(c), C.c_int(b.size), _dp(b), _dp(u), C.c_int(steps), C.c_double(alpha0),
+                           C.byref(F), _dp(hist))
+    return u, F.value, hist
+
+
+def lm_scalar(a, x0, iters, lambda0=1e-3):
+    """LM on r(x) = x^2 - a. Returns dict of per-iteration x, lam, nu, F (at the iteration's start), acc."""
+    out = {k: np.zeros(iters) for k in ("x", "lam", "nu", "F")}
+    acc = np.zeros(iters, np.uint8)
+    lib().orc_lm_scalar(C.c_double(a), C.c_double(x0), C.c_int(iters), C.c_double(lambda0), _dp(out["x"]),
+                        _dp(out["lam"]), _dp(out["nu"]), _dp(out["F"]), acc.ctypes.data_as(C.POINTER(C.c_uint8)))
+    out["acc"] = acc
+    return out
+
+
+def opcount_probe(which):
+    """Op counts (fwd flop, fwd sfu, tangent flop, tangent sfu) of a small hand-countable program."""
+    out = (C.c_longlong * 4)()
+    if lib().orc_opcount_probe(C.c_int(which), out) != 0:
+        raise ValueError(which)
+    return tuple(int(v) for v in out)
 
 
 def cholesky(A):

@@ -600,51 +600,32 @@ struct LmState {
   double lambda, nu, F;
 };
 
-// One LM iteration (fixed-count schedule, no early exit):
-//  1. r, J at x; F = 1/2 |r|^2.
-//  2. A = J^T J + lambda D, D = diag(max(diag(J^T J), 1e-12)) (Marquardt scaling); g = J^T r.
+// Steps 2-5 of one LM iteration, given F = F(x), A = J^T J (nx*nx, row-major, overwritten) and
+// g = J^T r at x, and the cost function for the trial point:
+//  2. A <- A + lambda D, D = diag(max(diag(J^T J), 1e-12)) (Marquardt scaling).
 //  3. Cholesky of A; on a non-positive pivot: lambda <- lambda nu, nu <- 2 nu, x unchanged.
 //  4. delta = -A^{-1} g; gain ratio rho = (F - F(x + delta)) / (1/2 delta^T (lambda D delta - g)).
 //  5. Accept iff F(x + delta) < F: lambda <- lambda max(1/3, 1 - (2 rho - 1)^3), nu <- 2;
-//     otherwise lambda <- lambda nu, nu <- 2 nu.
+//     otherwise lambda <- lambda nu, nu <- 2 nu (Madsen, Nielsen and Tingleff 2004, Sec. 3.2).
+// Every LM of the oracle (IK, calibration, the path's joint solve) goes through this one routine.
 // Returns 1 if the step was accepted.
-static int lm_iteration(const std::function<void(const double*, double*)>& fr, const CResFn& fc,
-                        int nx, int nr, double* x, LmState& st) {
-  std::vector<double> r(nr), J((size_t)nr * nx), A((size_t)nx * nx), D(nx), g(nx), Lm((size_t)nx * nx),
-      delta(nx), xn(nx), rn(nr);
-  fr(x, r.data());
-  double F = 0;
-  for (int k = 0; k < nr; ++k) F += r[k] * r[k];
-  F *= 0.5;
+static int lm_update(int nx, double* A, const double* g, double F, const std::function<double(const double*)>& cost,
+                     double* x, LmState& st) {
+  std::vector<double> D(nx), Lm((size_t)nx * nx), delta(nx), xn(nx), mg(nx);
   st.F = F;
-  cs_jacobian(fc, nx, nr, x, J.data());
   for (int a = 0; a < nx; ++a) {
-    double s = 0;
-    for (int k = 0; k < nr; ++k) s += J[(size_t)k * nx + a] * r[k];
-    g[a] = s;
-    for (int b = 0; b < nx; ++b) {
-      double t = 0;
-      for (int k = 0; k < nr; ++k) t += J[(size_t)k * nx + a] * J[(size_t)k * nx + b];
-      A[a * nx + b] = t;
-    }
+    D[a] = std::max(A[(size_t)a * nx + a], 1e-12);
+    A[(size_t)a * nx + a] += st.lambda * D[a];
   }
-  for (int a = 0; a < nx; ++a) {
-    D[a] = std::max(A[a * nx + a], 1e-12);
-    A[a * nx + a] += st.lambda * D[a];
-  }
-  if (!cholesky(nx, A.data(), Lm.data())) {
+  if (!cholesky(nx, A, Lm.data())) {
     st.lambda *= st.nu;
     st.nu *= 2.0;
     return 0;
   }
-  std::vector<double> mg(nx);
   for (int a = 0; a < nx; ++a) mg[a] = -g[a];
   chol_solve(nx, Lm.data(), mg.data(), delta.data());
   for (int a = 0; a < nx; ++a) xn[a] = x[a] + delta[a];
-  fr(xn.data(), rn.data());
-  double Fn = 0;
-  for (int k = 0; k < nr; ++k) Fn += rn[k] * rn[k];
-  Fn *= 0.5;
+  double Fn = cost(xn.data());
   double pred = 0;
   for (int a = 0; a < nx; ++a) pred += delta[a] * (st.lambda * D[a] * delta[a] - g[a]);
   pred *= 0.5;
@@ -660,6 +641,36 @@ static int lm_iteration(const std::function<void(const double*, double*)>& fr, c
   st.lambda *= st.nu;
   st.nu *= 2.0;
   return 0;
+}
+
+// One LM iteration (fixed-count schedule, no early exit) on a residual function:
+//  1. r, J at x (complex-step J); F = 1/2 |r|^2; A = J^T J, g = J^T r.
+//  2.-5. lm_update.
+static int lm_iteration(const std::function<void(const double*, double*)>& fr, const CResFn& fc,
+                        int nx, int nr, double* x, LmState& st) {
+  std::vector<double> r(nr), J((size_t)nr * nx), A((size_t)nx * nx), g(nx), rn(nr);
+  fr(x, r.data());
+  double F = 0;
+  for (int k = 0; k < nr; ++k) F += r[k] * r[k];
+  F *= 0.5;
+  cs_jacobian(fc, nx, nr, x, J.data());
+  for (int a = 0; a < nx; ++a) {
+    double s = 0;
+    for (int k = 0; k < nr; ++k) s += J[(size_t)k * nx + a] * r[k];
+    g[a] = s;
+    for (int b = 0; b < nx; ++b) {
+      double t = 0;
+      for (int k = 0; k < nr; ++k) t += J[(size_t)k * nx + a] * J[(size_t)k * nx + b];
+      A[a * nx + b] = t;
+    }
+  }
+  auto cost = [&](const double* xx) {
+    fr(xx, rn.data());
+    double Fn = 0;
+    for (int k = 0; k < nr; ++k) Fn += rn[k] * rn[k];
+    return 0.5 * Fn;
+  };
+  return lm_update(nx, A.data(), g.data(), F, cost, x, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -830,34 +841,54 @@ struct IkProblem {
   }
 };
 
-// Stage-one projected-gradient rule (normalised gradient step with an adaptive length alpha):
-// trial x' = Pi(x - alpha g / |g|); accept iff F(x') < F(x), then alpha <- 1.25 alpha, else
-// alpha <- alpha / 2 and x is kept. Fixed number of steps.
-static void pg_run_one(const IkProblem& pb, double* u, int steps, double alpha0, double* F_out) {
-  const OrRobot& rb = *pb.rb;
-  int nx = pb.d();
+// Stage-one projected-gradient rule (normalised gradient step with an adaptive length alpha), on
+// any cost F with gradient grad and feasible-set projection Pi:
+//   trial x' = Pi(x - alpha g / |g|) (no move when g = 0);
+//   accept iff F(x') < F(x): then x <- x', g <- grad F(x'), alpha <- 1.25 alpha;
+//   otherwise x (and its g) stay and alpha <- alpha / 2.
+// A fixed number of steps. Stage one of Algorithm 1 (per seed) and the trajectory refinement (all
+// free states at once, the norm over all of them) both run this one routine. hist (nullable)
+// receives, after every step, x, then alpha and F: [steps][nx + 2].
+static void pg_rule(int nx, double* x, int steps, double alpha0, const std::function<double(const double*)>& cost,
+                    const std::function<void(const double*, double*)>& grad,
+                    const std::function<void(const double*, double*)>& project, double* F_out, double* hist) {
   std::vector<double> g(nx), x1(nx), v(nx), g1(nx);
-  double F = pb.cost(u, nullptr);
-  pb.grad(u, g.data());
+  double F = cost(x);
+  grad(x, g.data());
   double alpha = alpha0;
   for (int it = 0; it < steps; ++it) {
     double gn = 0;
     for (int a = 0; a < nx; ++a) gn += g[a] * g[a];
     gn = std::sqrt(gn);
     double scale = gn > 0 ? alpha / gn : 0.0;
-    for (int a = 0; a < nx; ++a) v[a] = u[a] - scale * g[a];
-    project_state(rb, v.data(), x1.data());
-    double F1 = pb.cost(x1.data(), nullptr);
+    for (int a = 0; a < nx; ++a) v[a] = x[a] - scale * g[a];
+    project(v.data(), x1.data());
+    double F1 = cost(x1.data());
     if (F1 < F) {
-      pb.grad(x1.data(), g1.data());
-      for (int a = 0; a < nx; ++a) { u[a] = x1[a]; g[a] = g1[a]; }
+      grad(x1.data(), g1.data());
+      for (int a = 0; a < nx; ++a) { x[a] = x1[a]; g[a] = g1[a]; }
       F = F1;
       alpha *= 1.25;
     } else {
       alpha *= 0.5;
     }
+    if (hist) {
+      double* h = hist + (size_t)it * (nx + 2);
+      for (int a = 0; a < nx; ++a) h[a] = x[a];
+      h[nx] = alpha;
+      h[nx + 1] = F;
+    }
   }
   if (F_out) *F_out = F;
+}
+
+// Stage one of Algorithm 1 for one seed: pg_rule on its IK cost, projected per segment.
+static void pg_run_one(const IkProblem& pb, double* u, int steps, double alpha0, double* F_out,
+                       double* hist = nullptr) {
+  const OrRobot& rb = *pb.rb;
+  pg_rule(pb.d(), u, steps, alpha0, [&pb](const double* x) { return pb.cost(x, nullptr); },
+          [&pb](const double* x, double* g) { pb.grad(x, g); },
+          [&rb](const double* v, double* x1) { project_state(rb, v, x1); }, F_out, hist);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1057,6 +1088,88 @@ int orc_lm_linear(const double* A, const double* y, int nr, int nx, double* x, i
   double s = 0;
   for (int k = 0; k < nr; ++k) s += r[k] * r[k];
   *F = 0.5 * s;
+  return 0;
+}
+
+// Pins of the step rules on problems that can be solved by hand.
+// pg_rule on F(u) = 1/2 |u - c|^2 (gradient u - c) over nseg hexagons {|u_j| <= b_i, sum_j u_j = 0}
+// (three tendons per segment); hist as in pg_rule, [steps][3 nseg + 2].
+int orc_pg_quadratic(const double* c, int nseg, const double* b, double* u, int steps, double alpha0, double* F,
+                     double* hist) {
+  const int nx = 3 * nseg;
+  pg_rule(nx, u, steps, alpha0,
+          [c, nx](const double* x) {
+            double s = 0;
+            for (int a = 0; a < nx; ++a) s += (x[a] - c[a]) * (x[a] - c[a]);
+            return 0.5 * s;
+          },
+          [c, nx](const double* x, double* g) {
+            for (int a = 0; a < nx; ++a) g[a] = x[a] - c[a];
+          },
+          [b, nseg](const double* v, double* x1) {
+            for (int i = 0; i < nseg; ++i) project_segment(v + 3 * i, 3, b[i], x1 + 3 * i);
+          },
+          F, hist);
+  return 0;
+}
+
+// lm_iteration on the scalar residual r(x) = x^2 - a; after every iteration: x, lambda, nu, F (the
+// cost at the iterate the iteration started from) and the accept flag.
+int orc_lm_scalar(double a, double x0, int iters, double lambda0, double* x_hist, double* lam_hist,
+                  double* nu_hist, double* F_hist, uint8_t* acc) {
+  auto fr = [a](const double* xx, double* rr) { rr[0] = xx[0] * xx[0] - a; };
+  auto fc = [a](const cd* xx, cd* rr) { rr[0] = xx[0] * xx[0] - a; };
+  LmState st{lambda0, 2.0, 0.0};
+  double x = x0;
+  for (int it = 0; it < iters; ++it) {
+    double Fstart = 0.5 * (x * x - a) * (x * x - a);
+    acc[it] = (uint8_t)lm_iteration(fr, fc, 1, 1, &x, st);
+    x_hist[it] = x;
+    lam_hist[it] = st.lambda;
+    nu_hist[it] = st.nu;
+    F_hist[it] = Fstart;
+  }
+  return 0;
+}
+
+// The op-counting scalar on small programs whose counts are known by hand (out as orc_opcount_ik):
+//   which 0: C = A B of two 3x3 matrices that both depend on the input;
+//   which 1: C = A B with only A depending on it;
+//   which 2: y = sum_{k<5} a_k x_k, a linear function with constant a_k;
+//   which 3: one segment of Eq. 2-3 in the minimal (Rodrigues) form, (tx, ty) the input, L constant;
+//   which 4: y = sin(x) cos(x) / sqrt(x).
+int orc_opcount_probe(int which, long long* out) {
+  g_tally = {0, 0, 0, 0};
+  if (which == 0 || which == 1) {
+    Cnt A[3][3], B[3][3], Cm[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        A[i][j] = Cnt(1.0 + i + 0.5 * j, true);
+        B[i][j] = Cnt(2.0 - j + 0.25 * i, which == 0);
+      }
+    matmul3(A, B, Cm);
+  } else if (which == 2) {
+    Cnt y(0.0);
+    Cnt x[5];
+    for (int k = 0; k < 5; ++k) x[k] = Cnt(0.1 * (k + 1), true);
+    y = Cnt(0.5) * x[0];
+    for (int k = 1; k < 5; ++k) y = y + Cnt(0.5 + k) * x[k];
+  } else if (which == 3) {
+    g_count_minimal = true;
+    Cnt R[3][3], d[3];
+    segment_transform(Cnt(0.3, true), Cnt(-0.2, true), Cnt(0.1), R, d);
+    g_count_minimal = false;
+  } else if (which == 4) {
+    Cnt x(0.7, true);
+    Cnt y = Sin(x) * Cos(x) / Sqrt(x);
+    (void)y;
+  } else {
+    return 1;
+  }
+  out[0] = g_tally.f_flop;
+  out[1] = g_tally.f_sfu;
+  out[2] = g_tally.t_flop;
+  out[3] = g_tally.t_sfu;
   return 0;
 }
 
@@ -1316,41 +1429,13 @@ int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* 
 // ---------------------------------------------------------------------------------------------
 
 // normal(x, A, g) returns F(x) and fills A = J^T J (nx*nx, row-major) and g = J^T r; cost(x) = F.
-// Same rule as lm_iteration above.
+// Steps 2-5 are lm_update's.
 static int lm_iteration_ag(const std::function<double(const double*, double*, double*)>& normal,
                            const std::function<double(const double*)>& cost, int nx, double* x,
                            LmState& st) {
-  std::vector<double> A((size_t)nx * nx), g(nx), D(nx), Lm((size_t)nx * nx), delta(nx), xn(nx), mg(nx);
+  std::vector<double> A((size_t)nx * nx), g(nx);
   double F = normal(x, A.data(), g.data());
-  st.F = F;
-  for (int a = 0; a < nx; ++a) {
-    D[a] = std::max(A[(size_t)a * nx + a], 1e-12);
-    A[(size_t)a * nx + a] += st.lambda * D[a];
-  }
-  if (!cholesky(nx, A.data(), Lm.data())) {
-    st.lambda *= st.nu;
-    st.nu *= 2.0;
-    return 0;
-  }
-  for (int a = 0; a < nx; ++a) mg[a] = -g[a];
-  chol_solve(nx, Lm.data(), mg.data(), delta.data());
-  for (int a = 0; a < nx; ++a) xn[a] = x[a] + delta[a];
-  double Fn = cost(xn.data());
-  double pred = 0;
-  for (int a = 0; a < nx; ++a) pred += delta[a] * (st.lambda * D[a] * delta[a] - g[a]);
-  pred *= 0.5;
-  if (Fn < F) {
-    double rho = (F - Fn) / pred;
-    double t = 2.0 * rho - 1.0;
-    st.lambda *= std::max(1.0 / 3.0, 1.0 - t * t * t);
-    st.nu = 2.0;
-    for (int a = 0; a < nx; ++a) x[a] = xn[a];
-    st.F = Fn;
-    return 1;
-  }
-  st.lambda *= st.nu;
-  st.nu *= 2.0;
-  return 0;
+  return lm_update(nx, A.data(), g.data(), F, cost, x, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1435,35 +1520,19 @@ struct TrajProblem {
   }
 };
 
-// Projected-gradient refinement of a trajectory (same step rule as stage one of Algorithm 1, with
-// the norm taken over all free states and the projection applied to every state's segments).
+// Projected-gradient refinement of a trajectory: pg_rule with the norm taken over all free states
+// and the projection applied to every state's segments.
 static void traj_pg(const TrajProblem& tp, double* x, int steps, double alpha0, double* F_out) {
   const OrRobot& rb = *tp.rb;
-  int n = tp.nx(), d = rb.n * rb.m;
-  std::vector<double> g(n), x1(n), v(n), g1(n);
-  double F = tp.cost(x);
-  tp.grad(x, g.data());
-  double alpha = alpha0;
-  for (int it = 0; it < steps; ++it) {
-    double gn = 0;
-    for (int a = 0; a < n; ++a) gn += g[a] * g[a];
-    gn = std::sqrt(gn);
-    double scale = gn > 0 ? alpha / gn : 0.0;
-    for (int a = 0; a < n; ++a) v[a] = x[a] - scale * g[a];
-    for (int t = 0; t < tp.Tn - 1; ++t)
-      for (int i = 0; i < rb.n; ++i)
-        project_segment(&v[(size_t)t * d + rb.m * i], rb.m, rb.umax[i], &x1[(size_t)t * d + rb.m * i]);
-    double F1 = tp.cost(x1.data());
-    if (F1 < F) {
-      tp.grad(x1.data(), g1.data());
-      for (int a = 0; a < n; ++a) { x[a] = x1[a]; g[a] = g1[a]; }
-      F = F1;
-      alpha *= 1.25;
-    } else {
-      alpha *= 0.5;
-    }
-  }
-  if (F_out) *F_out = F;
+  const int d = rb.n * rb.m, Tn = tp.Tn;
+  pg_rule(tp.nx(), x, steps, alpha0, [&tp](const double* xx) { return tp.cost(xx); },
+          [&tp](const double* xx, double* g) { tp.grad(xx, g); },
+          [&rb, d, Tn](const double* v, double* x1) {
+            for (int t = 0; t < Tn - 1; ++t)
+              for (int i = 0; i < rb.n; ++i)
+                project_segment(&v[(size_t)t * d + rb.m * i], rb.m, rb.umax[i], &x1[(size_t)t * d + rb.m * i]);
+          },
+          F_out, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------------
