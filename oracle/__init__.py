@@ -232,7 +232,9 @@ def ik_param_grad(robot, weights, spheres, kind, targets, S, u):
 
 def ik_lm(robot, weights, spheres, kind, targets, S, u0, iters, lambda0=1e-3, history=False,
           threads=None):
-    """Run ``iters`` LM iterations per seed. Returns dict u, lam, nu, F, acc[, hist]."""
+    """Run ``iters`` LM iterations per seed. Returns dict u, lam, nu, F, acc[, hist, Fstart, Ftrial]:
+    with history, the iterate after every iteration [iters][B][d] and, per seed and iteration, the
+    cost where the iteration started and at its trial point [B][iters] (NaN if its Cholesky failed)."""
     no, sp = _spheres(spheres)
     u = _f64(u0).copy()
     tg = _f64(targets).reshape(-1, 7)
@@ -242,13 +244,16 @@ def ik_lm(robot, weights, spheres, kind, targets, S, u0, iters, lambda0=1e-3, hi
     F = np.zeros(B)
     acc = np.zeros((B, iters), dtype=np.uint8)
     hist = np.zeros((iters, B, d)) if history else None
+    trace = np.zeros((B, iters, 2)) if history else None
     lib().orc_ik_lm(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg),
                     C.c_int64(S), _dp(u), C.c_int64(B), C.c_int(iters), _dp(lam), _dp(nu), _dp(F),
-                    _dp(hist), acc.ctypes.data_as(C.POINTER(C.c_uint8)),
+                    _dp(hist), acc.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(trace),
                     C.c_int(_threads(threads)))
     out = dict(u=u, lam=lam, nu=nu, F=F, acc=acc)
     if history:
         out["hist"] = hist
+        out["Fstart"] = trace[:, :, 0].copy()
+        out["Ftrial"] = trace[:, :, 1].copy()
     return out
 
 
@@ -266,12 +271,13 @@ def lm_linear(A, y, x0, iters, lambda0=1e-3):
 
 def pg_quadratic(c, b, u0, steps, alpha0):
     """The stage-one step rule on F(u) = 1/2 |u - c|^2 over per-segment hexagons (3 tendons each,
-    bounds b[i]). Returns (u, F, hist) with hist [steps][3 n + 2] = iterate, alpha, F after each step."""
+    bounds b[i]). Returns (u, F, hist) with hist [steps][3 n + 3] = iterate, alpha, F and the
+    trial's cost after each step."""
     c = _f64(c)
     u = _f64(u0).copy()
     b = _f64(np.atleast_1d(b))
     F = C.c_double(0)
-    hist = np.zeros((steps, u.size + 2))
+    hist = np.zeros((steps, u.size + 3))
     lib().orc_pg_quadratic(_dp(c), C.c_int(b.size), _dp(b), _dp(u), C.c_int(steps), C.c_double(alpha0),
                            C.byref(F), _dp(hist))
     return u, F.value, hist
@@ -285,6 +291,13 @@ def lm_scalar(a, x0, iters, lambda0=1e-3):
                         _dp(out["lam"]), _dp(out["nu"]), _dp(out["F"]), acc.ctypes.data_as(C.POINTER(C.c_uint8)))
     out["acc"] = acc
     return out
+
+
+def opcount_lm_update(nx):
+    """(flops, special calls) of steps 2-5 of one LM iteration on nx unknowns (no cost evaluation)."""
+    out = (C.c_longlong * 2)()
+    lib().orc_opcount_lm_update(C.c_int(nx), out)
+    return int(out[0]), int(out[1])
 
 
 def opcount_probe(which):
@@ -320,16 +333,18 @@ def project_arc(v, thmax, lmin, lmax):
     return u
 
 
-def ik_pg(robot, weights, spheres, kind, targets, S, u0, steps, alpha0, threads=None):
-    """Stage-one projected gradient on every seed. Returns (u, F)."""
+def ik_pg(robot, weights, spheres, kind, targets, S, u0, steps, alpha0, threads=None, history=False):
+    """Stage-one projected gradient on every seed. Returns (u, F), or with history (u, F, hist):
+    hist [B][steps][d + 3] = the iterate, alpha, F and the trial's cost after every step."""
     no, sp = _spheres(spheres)
     u = _f64(u0).copy()
     tg = _f64(targets).reshape(-1, 7)
     F = np.zeros(u.shape[0])
+    hist = np.zeros((u.shape[0], steps, u.shape[1] + 3)) if history else None
     lib().orc_ik_pg(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg),
                     C.c_int64(S), _dp(u), C.c_int64(u.shape[0]), C.c_int(steps),
-                    C.c_double(alpha0), _dp(F), C.c_int(_threads(threads)))
-    return u, F
+                    C.c_double(alpha0), _dp(F), _dp(hist), C.c_int(_threads(threads)))
+    return (u, F, hist) if history else (u, F)
 
 
 def splitmix64_at(s0: int, k: int) -> int:
@@ -419,13 +434,14 @@ def accept(robot, spheres, kind, targets, u, tol=1e-5):
     return pos, rot, lo.astype(bool), co.astype(bool)
 
 
-def opcount_ik(robot, weights, spheres, kind, target, u):
+def opcount_ik(robot, weights, spheres, kind, target, u, box=True):
     """Algorithmic op counts of one IK state evaluation (Rodrigues form):
-    (forward flops, forward special calls, tangent flops, tangent special calls)."""
+    (forward flops, forward special calls, tangent flops, tangent special calls). box=False leaves
+    out the tendon model's bound and sum-zero rows (a projected trial point needs none)."""
     no, sp = _spheres(spheres)
     out = (C.c_longlong * 4)()
-    lib().orc_opcount_ik(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
-                         _dp(_f64(target).reshape(7)), _dp(_f64(u)), out)
+    lib().orc_opcount_ik_form(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind),
+                              _dp(_f64(target).reshape(7)), _dp(_f64(u)), C.c_int(1 if box else 0), out)
     return tuple(int(x) for x in out)
 
 

@@ -255,6 +255,10 @@ static void segment_rodrigues(const T& tx, const T& ty, const T& L, const T& s, 
 }
 
 static bool g_count_minimal = false;  // op counting: use the minimal (Rodrigues) arithmetic form
+// op counting: leave out the rows that vanish on the feasible set of stage one's projection (the form
+// a projected trial point is evaluated in): the tendon model's bound and sum-zero rows, the arc
+// model's length and curvature rows
+static bool g_count_skip_box = false;
 
 // Segment transform T_{i-1}^i of Eq. 1: rotation R (Eq. 2) and translation d (Eq. 3).
 template <class T>
@@ -473,11 +477,11 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
   T sb = T(std::sqrt(W.rho_b)), se = T(std::sqrt(W.rho_eq)), sk = T(std::sqrt(W.rho_k)),
     sc = T(std::sqrt(W.rho_c));
   if (rb.model == OR_MODEL_ARC) {
-    for (int i = 0; i < rb.n; ++i) {
+    for (int i = 0; i < rb.n && !g_count_skip_box; ++i) {
       r[k++] = sb * hinge(u[3 * i + 2] - T(rb.lmax[i]));
       r[k++] = sb * hinge(T(rb.lmin[i]) - u[3 * i + 2]);
     }
-  } else {
+  } else if (!g_count_skip_box) {
     for (int q = 0; q < d; ++q) {
       int i = q / rb.m;
       r[k++] = sb * hinge(u[q] - T(rb.umax[i]));
@@ -489,7 +493,8 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
       r[k++] = se * s;
     }
   }
-  for (int i = 0; i < rb.n; ++i) {
+  // (the arc model's projected set holds theta <= theta_max, so its trial points need no curvature row)
+  for (int i = 0; i < rb.n && !(g_count_skip_box && rb.model == OR_MODEL_ARC); ++i) {
     if (re(fk.th2[i]) > rb.thmax[i] * rb.thmax[i]) r[k++] = sk * (Sqrt(fk.th2[i]) - T(rb.thmax[i]));
     else r[k++] = T(0.0);
   }
@@ -563,41 +568,45 @@ static void cs_jacobian(const CResFn& f, int nx, int nr, const double* x, double
 // ---------------------------------------------------------------------------------------------
 
 // Textbook Cholesky A = L L^T of a dense symmetric n x n matrix (row-major, lower part used).
-// Returns false on a non-positive pivot.
-static bool cholesky(int n, const double* A, double* Lm) {
-  for (int i = 0; i < n * n; ++i) Lm[i] = 0.0;
+// Returns false on a non-positive pivot. (Templated so that the op-counting scalar can count it.)
+template <class T> static bool cholesky_t(int n, const T* A, T* Lm) {
+  for (int i = 0; i < n * n; ++i) Lm[i] = T(0.0);
   for (int j = 0; j < n; ++j) {
-    double s = A[j * n + j];
+    T s = A[j * n + j];
     for (int k = 0; k < j; ++k) s -= Lm[j * n + k] * Lm[j * n + k];
-    if (!(s > 0.0)) return false;
-    double ljj = std::sqrt(s);
+    if (!(re(s) > 0.0)) return false;
+    T ljj = Sqrt(s);
     Lm[j * n + j] = ljj;
     for (int i = j + 1; i < n; ++i) {
-      double t = A[i * n + j];
+      T t = A[i * n + j];
       for (int k = 0; k < j; ++k) t -= Lm[i * n + k] * Lm[j * n + k];
       Lm[i * n + j] = t / ljj;
     }
   }
   return true;
 }
+static bool cholesky(int n, const double* A, double* Lm) { return cholesky_t<double>(n, A, Lm); }
 
 // Solve L L^T x = b.
-static void chol_solve(int n, const double* Lm, const double* b, double* x) {
-  std::vector<double> y(n);
+template <class T> static void chol_solve_t(int n, const T* Lm, const T* b, T* x) {
+  std::vector<T> y(n);
   for (int i = 0; i < n; ++i) {
-    double s = b[i];
+    T s = b[i];
     for (int k = 0; k < i; ++k) s -= Lm[i * n + k] * y[k];
     y[i] = s / Lm[i * n + i];
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = y[i];
+    T s = y[i];
     for (int k = i + 1; k < n; ++k) s -= Lm[k * n + i] * x[k];
     x[i] = s / Lm[i * n + i];
   }
 }
+static void chol_solve(int n, const double* Lm, const double* b, double* x) { chol_solve_t<double>(n, Lm, b, x); }
 
 struct LmState {
   double lambda, nu, F;
+  double Ftrial;  // cost at the trial point of the last iteration (NaN if its Cholesky failed)
+  double Fstart;  // cost at the iterate the last iteration started from
 };
 
 // Steps 2-5 of one LM iteration, given F = F(x), A = J^T J (nx*nx, row-major, overwritten) and
@@ -613,6 +622,7 @@ static int lm_update(int nx, double* A, const double* g, double F, const std::fu
                      double* x, LmState& st) {
   std::vector<double> D(nx), Lm((size_t)nx * nx), delta(nx), xn(nx), mg(nx);
   st.F = F;
+  st.Fstart = F;
   for (int a = 0; a < nx; ++a) {
     D[a] = std::max(A[(size_t)a * nx + a], 1e-12);
     A[(size_t)a * nx + a] += st.lambda * D[a];
@@ -620,12 +630,14 @@ static int lm_update(int nx, double* A, const double* g, double F, const std::fu
   if (!cholesky(nx, A, Lm.data())) {
     st.lambda *= st.nu;
     st.nu *= 2.0;
+    st.Ftrial = NAN;
     return 0;
   }
   for (int a = 0; a < nx; ++a) mg[a] = -g[a];
   chol_solve(nx, Lm.data(), mg.data(), delta.data());
   for (int a = 0; a < nx; ++a) xn[a] = x[a] + delta[a];
   double Fn = cost(xn.data());
+  st.Ftrial = Fn;
   double pred = 0;
   for (int a = 0; a < nx; ++a) pred += delta[a] * (st.lambda * D[a] * delta[a] - g[a]);
   pred *= 0.5;
@@ -848,7 +860,7 @@ struct IkProblem {
 //   otherwise x (and its g) stay and alpha <- alpha / 2.
 // A fixed number of steps. Stage one of Algorithm 1 (per seed) and the trajectory refinement (all
 // free states at once, the norm over all of them) both run this one routine. hist (nullable)
-// receives, after every step, x, then alpha and F: [steps][nx + 2].
+// receives, after every step, x, then alpha, F and the trial's cost F(x'): [steps][nx + 3].
 static void pg_rule(int nx, double* x, int steps, double alpha0, const std::function<double(const double*)>& cost,
                     const std::function<void(const double*, double*)>& grad,
                     const std::function<void(const double*, double*)>& project, double* F_out, double* hist) {
@@ -863,7 +875,7 @@ static void pg_rule(int nx, double* x, int steps, double alpha0, const std::func
     double scale = gn > 0 ? alpha / gn : 0.0;
     for (int a = 0; a < nx; ++a) v[a] = x[a] - scale * g[a];
     project(v.data(), x1.data());
-    double F1 = cost(x1.data());
+    const double F1 = cost(x1.data());
     if (F1 < F) {
       grad(x1.data(), g1.data());
       for (int a = 0; a < nx; ++a) { x[a] = x1[a]; g[a] = g1[a]; }
@@ -873,10 +885,11 @@ static void pg_rule(int nx, double* x, int steps, double alpha0, const std::func
       alpha *= 0.5;
     }
     if (hist) {
-      double* h = hist + (size_t)it * (nx + 2);
+      double* h = hist + (size_t)it * (nx + 3);
       for (int a = 0; a < nx; ++a) h[a] = x[a];
       h[nx] = alpha;
       h[nx + 1] = F;
+      h[nx + 2] = F1;
     }
   }
   if (F_out) *F_out = F;
@@ -1040,20 +1053,25 @@ int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const doubl
 
 // Run `iters` LM iterations on each seed. u[B][d] is updated in place; hist (nullable) receives
 // the iterate after every iteration [iters][B][d]; lam/nu/F (in/out, [B]); acc[B][iters] (nullable)
-// the accept flags. lam/nu must be initialised by the caller (lambda0, 2).
+// the accept flags; trace[B][iters][2] (nullable) the cost at the iteration's start and at its trial
+// point. lam/nu must be initialised by the caller (lambda0, 2).
 int orc_ik_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int iters, double* lam,
-              double* nu, double* F, double* hist, uint8_t* acc, int threads) {
+              double* nu, double* F, double* hist, uint8_t* acc, double* trace, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
     IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
-    LmState st{lam[b], nu[b], 0.0};
+    LmState st{lam[b], nu[b], 0.0, 0.0, 0.0};
     double* x = u + d * b;
     for (int it = 0; it < iters; ++it) {
       int a = lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
                            [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), x, st);
       if (acc) acc[(size_t)iters * b + it] = (uint8_t)a;
       if (hist) std::memcpy(hist + ((size_t)it * B + b) * d, x, sizeof(double) * d);
+      if (trace) {
+        trace[((size_t)iters * b + it) * 2] = st.Fstart;
+        trace[((size_t)iters * b + it) * 2 + 1] = st.Ftrial;
+      }
     }
     lam[b] = st.lambda;
     nu[b] = st.nu;
@@ -1093,7 +1111,7 @@ int orc_lm_linear(const double* A, const double* y, int nr, int nx, double* x, i
 
 // Pins of the step rules on problems that can be solved by hand.
 // pg_rule on F(u) = 1/2 |u - c|^2 (gradient u - c) over nseg hexagons {|u_j| <= b_i, sum_j u_j = 0}
-// (three tendons per segment); hist as in pg_rule, [steps][3 nseg + 2].
+// (three tendons per segment); hist as in pg_rule, [steps][3 nseg + 3].
 int orc_pg_quadratic(const double* c, int nseg, const double* b, double* u, int steps, double alpha0, double* F,
                      double* hist) {
   const int nx = 3 * nseg;
@@ -1138,6 +1156,36 @@ int orc_lm_scalar(double a, double x0, int iters, double lambda0, double* x_hist
 //   which 2: y = sum_{k<5} a_k x_k, a linear function with constant a_k;
 //   which 3: one segment of Eq. 2-3 in the minimal (Rodrigues) form, (tx, ty) the input, L constant;
 //   which 4: y = sin(x) cos(x) / sqrt(x).
+// Op count of steps 2-5 of one LM iteration (lm_update) on nx unknowns, without the cost
+// evaluations: damping of the diagonal, Cholesky, the two triangular solves, the predicted
+// decrease, the gain ratio and the damping update (forward flops and special calls in out[0..1]).
+int orc_opcount_lm_update(int nx, long long* out) {
+  g_tally = {0, 0, 0, 0};
+  std::vector<Cnt> A((size_t)nx * nx), Lm((size_t)nx * nx), g(nx), D(nx), mg(nx), dl(nx);
+  for (int a = 0; a < nx; ++a)
+    for (int b = 0; b < nx; ++b) A[(size_t)a * nx + b] = Cnt(a == b ? 2.0 + a : 0.1 / (1 + a + b));
+  for (int a = 0; a < nx; ++a) g[a] = Cnt(0.5 - 0.1 * a);
+  const Cnt lam(1e-3);
+  for (int a = 0; a < nx; ++a) {
+    D[a] = A[(size_t)a * nx + a];  // max(diag, 1e-12): a comparison, not counted
+    A[(size_t)a * nx + a] += lam * D[a];
+  }
+  cholesky_t<Cnt>(nx, A.data(), Lm.data());
+  for (int a = 0; a < nx; ++a) mg[a] = -g[a];
+  chol_solve_t<Cnt>(nx, Lm.data(), mg.data(), dl.data());
+  Cnt pred(0.0);
+  for (int a = 0; a < nx; ++a) pred += dl[a] * (lam * D[a] * dl[a] - g[a]);
+  pred *= Cnt(0.5);
+  const Cnt F(1.0), Fn(0.5);
+  const Cnt rho = (F - Fn) / pred;
+  const Cnt t = Cnt(2.0) * rho - Cnt(1.0);
+  Cnt lam2 = lam * (Cnt(1.0) - t * t * t);
+  (void)lam2;
+  out[0] = g_tally.f_flop;
+  out[1] = g_tally.f_sfu;
+  return 0;
+}
+
 int orc_opcount_probe(int which, long long* out) {
   g_tally = {0, 0, 0, 0};
   if (which == 0 || which == 1) {
@@ -1186,14 +1234,15 @@ int orc_project_arc(const double* v, int64_t B, double thmax, double lmin, doubl
   return 0;
 }
 
-// Stage-one projected gradient on every seed: u[B][d] in place, F[B] out.
+// Stage-one projected gradient on every seed: u[B][d] in place, F[B] out; hist (nullable)
+// [B][steps][d + 3] as in pg_rule.
 int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int steps, double alpha0,
-              double* F, int threads) {
+              double* F, double* hist, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
     IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
-    pg_run_one(pb, u + d * b, steps, alpha0, F + b);
+    pg_run_one(pb, u + d * b, steps, alpha0, F + b, hist ? hist + (size_t)b * steps * (d + 3) : nullptr);
   });
   return 0;
 }
@@ -1325,6 +1374,10 @@ static void accept_one(const OrRobot& rb, int no, const double* spheres, int kin
   *col_ok = free;
 }
 
+// Cost below which refined candidates count as equally good solutions in the argmin of Algorithm 1
+// (about 8 um of tip position under the default pose weights): their differences are rounding.
+static const double OR_ARGMIN_TIE = 1e-8;
+
 struct OrIkParams {
   int32_t S, n_final, k_init, k_final;
   double lambda0, alpha0, dedup_eps, lim_tol, pos_tol, rot_tol;
@@ -1359,8 +1412,10 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
     orc_topk(Ff.data(), Cf.data(), U.data(), S, d, K, prm->dedup_eps, top.data());
     if (cand_out)
       for (int c = 0; c < K; ++c) cand_out[(size_t)q * K + c] = top[c];
-    // Stage two (ParallelOptimize with k_final LM iterations) and argmin of the final cost.
-    double bestF = INFINITY;
+    // Stage two (ParallelOptimize with k_final LM iterations) and argmin of the final cost. Costs
+    // at or below OR_ARGMIN_TIE are solutions whose differences are rounding: they count as equal
+    // and the first of them in SelectTop order is kept; above it the lowest cost wins.
+    double bestKey = INFINITY, bestF = INFINITY;
     int best = -1;
     std::vector<double> X((size_t)K * d);
     for (int c = 0; c < K; ++c) {
@@ -1372,7 +1427,8 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
         lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
                      [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), x, st);
       double Fc = pb.cost(x, nullptr);
-      if (Fc < bestF) { bestF = Fc; best = c; }
+      const double key = Fc <= OR_ARGMIN_TIE ? 0.0 : Fc;
+      if (key < bestKey) { bestKey = key; bestF = Fc; best = c; }
     }
     double* uo = u_out + (size_t)q * d;
     if (best < 0) {
@@ -1402,24 +1458,34 @@ int orc_accept(const OrRobot* rb, int no, const double* spheres, int kind, const
 // Algorithmic op counts of one IK state evaluation in the minimal (Rodrigues) arithmetic form:
 // out[0..3] = forward flops, forward special-function calls, tangent flops, tangent special calls
 // (the tangent map of the cost w.r.t. u; a reverse sweep transposes it with the same count).
-int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
-                   const double* target, const double* u, long long* out) {
+// box = 0 counts the cost without the rows that vanish on stage one's feasible set (tendon model:
+// bound and sum-zero rows; arc model: length and curvature rows), so a projected trial point needs
+// none of them.
+int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+                        const double* target, const double* u, int box, long long* out) {
   int d = rb->n * rb->m;
   g_count_minimal = true;
+  g_count_skip_box = !box;
   g_tally = {0, 0, 0, 0};
   Params<Cnt> P;
   for (int i = 0; i < rb->n; ++i) { P.L[i] = Cnt(rb->L[i]); P.rc[i] = Cnt(rb->rc[i]); }
   std::vector<Cnt> x(d), r(ik_rows(*rb, no));
   for (int a = 0; a < d; ++a) x[a] = Cnt(u[a], true);
-  ik_residual(*rb, P, *W, no, spheres, kind, target, x.data(), r.data(), (Cnt*)nullptr);
-  Cnt F = half_sq(r.data(), (int)r.size());
+  const int rows = ik_residual(*rb, P, *W, no, spheres, kind, target, x.data(), r.data(), (Cnt*)nullptr);
+  Cnt F = half_sq(r.data(), rows);
   (void)F;
   g_count_minimal = false;
+  g_count_skip_box = false;
   out[0] = g_tally.f_flop;
   out[1] = g_tally.f_sfu;
   out[2] = g_tally.t_flop;
   out[3] = g_tally.t_sfu;
   return 0;
+}
+
+int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+                   const double* target, const double* u, long long* out) {
+  return orc_opcount_ik_form(rb, W, no, spheres, kind, target, u, 1, out);
 }
 
 }  // extern "C"

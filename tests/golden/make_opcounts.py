@@ -2,7 +2,9 @@
 benchmark workload, counted by the oracle's op-counting scalar on the minimal (Rodrigues) form of
 Eq. 2-3. "fwd" = cost (kinematics, pose log, penalty rows); "tan" = the linearised program whose
 transpose is the adjoint (same multiply-add count), so one value-and-gradient evaluation costs
-fwd + tan. Calls only oracle/."""
+fwd + tan. "trial_*" counts leave out the rows that vanish at the projected trial points of stage
+one (tendon model: bound and sum-zero rows; arc model: length and curvature rows). Calls only
+oracle/."""
 import json
 import os
 import sys
@@ -31,7 +33,13 @@ def counts(spec, kind, n_states=64):
     tg = synth.pose_targets(O.fk(rb, u[:1])[0], "pose" if kind == O.IK6 else "axis")[0]
     c = np.array([O.opcount_ik(rb, W, None, kind, tg, u[1 + i]) for i in range(n_states)], dtype=float)
     m = c.mean(axis=0)  # branches (series vs closed form) make the count state-dependent
-    return {"fwd_flop": float(m[0]), "fwd_sfu": float(m[1]), "tan_flop": float(m[2]), "tan_sfu": float(m[3])}
+    out = {"fwd_flop": float(m[0]), "fwd_sfu": float(m[1]), "tan_flop": float(m[2]), "tan_sfu": float(m[3])}
+    # a projected trial point of stage one (feasible: none of the rows that vanish there)
+    c = np.array([O.opcount_ik(rb, W, None, kind, tg, u[1 + i], box=False) for i in range(n_states)], dtype=float)
+    m = c.mean(axis=0)
+    out.update({"trial_fwd_flop": float(m[0]), "trial_fwd_sfu": float(m[1]), "trial_tan_flop": float(m[2]),
+                "trial_tan_sfu": float(m[3])})
+    return out
 
 
 def main():

@@ -246,6 +246,10 @@ def pin_opcount_ik_one_segment(orc):
     u = np.array([0.003, -0.001, -0.002])
     tg = np.array([0.01, 0.0, 0.09, 0.1, 0.0, 0.99, 0.0])
     assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u)) == (168, 3, 187, 2)
+    # without the bound and sum-zero rows (a projected trial point): the 6 bound rows (12 flops) and
+    # the sum-zero row (4, tangent 3) go, and F sums 7 squared rows: 14 + 1 = 15 flops, tangent
+    # 6 x 3 + 5 + 1 = 24: forward 168 - 12 - 4 - 29 + 15 = 138, tangent 187 - 3 - 28 + 24 = 180
+    assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u, box=False)) == (138, 3, 180, 2)
 
 
 def test_opcount_ik_one_segment(orc):
@@ -268,3 +272,71 @@ def test_opcount_rodrigues_matches_forward_kinematics_part(orc):
     np.testing.assert_array_equal(d1, d2)
     seg = np.array(orc.opcount_probe(3))
     assert np.all(d1 >= seg)
+
+
+def test_lm_trace_and_pg_history_are_consistent(orc):
+    """The recorded costs the GPU tests classify near-ties with: an LM iteration is accepted exactly
+    when its trial cost is below its starting cost, the next iteration starts from the accepted
+    cost; a PG step likewise, and its alpha follows the rule."""
+    from paper_2607_11340_gb300 import synth
+
+    spec = synth.ROBOT_3SEG
+    rb = orc.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
+    W = orc.make_weights(**synth.WEIGHTS.as_dict())
+    rng = np.random.default_rng(33)
+    u_true = synth.hexagon_states(rng, 4, 3, spec.umax)
+    tg = synth.pose_targets(orc.fk(rb, u_true)[0], "pose")
+    u0 = np.repeat(u_true, 4, 0) + rng.normal(0, 1.5e-3, (16, 9))
+    r = orc.ik_lm(rb, W, None, 0, tg, 4, u0, 10, history=True)
+    np.testing.assert_array_equal(r["acc"].astype(bool), r["Ftrial"] < r["Fstart"])
+    nxt = np.where(r["acc"][:, :-1].astype(bool), r["Ftrial"][:, :-1], r["Fstart"][:, :-1])
+    np.testing.assert_array_equal(r["Fstart"][:, 1:], nxt)
+    u, F, h = orc.ik_pg(rb, W, None, 0, tg, 4, u0, 12, 1e-3, history=True)
+    Fprev = np.concatenate([orc.ik_eval(rb, W, None, 0, tg, 4, u0)["F"][:, None], h[:, :-1, 10]], axis=1)
+    acc = h[:, :, 11] < Fprev
+    assert 0 < acc.mean() < 1
+    np.testing.assert_array_equal(h[:, :, 10], np.where(acc, h[:, :, 11], Fprev))
+    aprev = np.concatenate([np.full((16, 1), 1e-3), h[:, :-1, 9]], axis=1)
+    np.testing.assert_array_equal(h[:, :, 9], np.where(acc, aprev * 1.25, aprev * 0.5))
+
+
+def test_argmin_keeps_first_rounding_level_solution(orc):
+    """Algorithm 1's argmin: among the refined candidates, costs at or below 1e-8 (solutions whose
+    cost differences are rounding) tie, and the first of them in SelectTop order is kept; above that
+    the lowest cost wins. On a redundant robot (4 segments: 8 free displacements for a 6-DoF pose)
+    several candidates reach exact solutions; the pipeline is recomposed here from the oracle's own
+    steps (seeds, projected gradient, SelectTop, LM) to check which one solve_ik returns."""
+    from paper_2607_11340_gb300 import synth
+
+    spec = synth.ROBOT_4SEG
+    rb = orc.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
+    W = orc.make_weights(**synth.WEIGHTS.as_dict())
+    ik = synth.IkSpec(S=32, n_final=6, k_init=16, k_final=20)
+    cfg = orc.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
+                       alpha0=ik.alpha0, dedup_eps=ik.dedup_eps)
+    tg, _ = synth.ik_workload(spec, 6, "pose", lambda x: orc.fk(rb, x)[0], seed=34)
+    res = orc.solve_ik(rb, W, None, 0, tg, cfg, extra=True)
+    n_tied = 0
+    for p in range(len(tg)):
+        U = orc.seeds(rb, W, None, cfg.seed, p, 1, ik.S).reshape(ik.S, -1)
+        U, _ = orc.ik_pg(rb, W, None, 0, tg[p:p + 1], ik.S, U, ik.k_init, ik.alpha0)
+        X = U[res["cand"][p]]
+        r = orc.ik_lm(rb, W, None, 0, tg[p:p + 1], len(X), X, ik.k_final)
+        F = orc.ik_eval(rb, W, None, 0, tg[p:p + 1], len(X), r["u"])["F"]
+        tied = np.nonzero(F <= 1e-8)[0]
+        n_tied += len(tied) > 1
+        want = tied[0] if len(tied) else int(np.argmin(F))
+        np.testing.assert_array_equal(res["u"][p], r["u"][want])
+        assert res["F"][p] == F[want]
+    assert n_tied >= 3  # the rule decided between several exact solutions on most targets
+
+
+def test_opcount_lm_update(orc):
+    """Steps 2-5 of one LM iteration on n unknowns, counted by hand: damping of the diagonal 2n;
+    Cholesky sum_j [2j (pivot) + (n-1-j)(2j+1) (column)] flops and n square roots; forward and
+    back substitution sum_i (2i+1) each, n^2 + n^2; predicted decrease 5n + 1; gain ratio 2; the
+    damping update 2 + 4 (t = 2 rho - 1, lambda (1 - t^3)).
+      n = 1: 2 + 0 + 2 + 6 + 2 + 2 + 4 = 18 flops, 1 square root;
+      n = 9: 18 + (72 + 204) + 162 + 46 + 8 = 510 flops, 9 square roots."""
+    assert orc.opcount_lm_update(1) == (18, 1)
+    assert orc.opcount_lm_update(9) == (510, 9)
