@@ -427,14 +427,18 @@ def other_workload(args):
                 s.stage1(tgd)
                 s1_med, s1_ms = time_steps(torch, lambda: s.stage1(tgd), args.steps, flush, stream)
                 c = load_counts("ik_arc_3seg_pose")
-                n_eval = units * ik.S * (ik.k_init + 1)
-                fl = c["fwd_flop"] + c["tan_flop"]
-                ach = n_eval * fl / (s1_ms / 1e3) / 1e12
+                acc = s.pg_accepted()
+                n_seed = units * ik.S
+                n_eval = n_seed * (ik.k_init + 1)
+                fl = (n_seed * (c["fwd_flop"] + c["tan_flop"]) + n_seed * ik.k_init * c["trial_fwd_flop"]
+                      + acc * c["trial_tan_flop"])  # the method's work, as for the headline
+                ach = fl / (s1_ms / 1e3) / 1e12
                 sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
                 peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
                 out["roofline"] = {"bound": "alu", "kernel": "k_ik_stage1 (arc model)", "achieved": ach, "peak": peak,
                                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "kernel_ms": s1_ms,
-                                   "evals_per_launch": n_eval, "flop_per_eval": fl}
+                                   "count": "method (oracle op counts; gradients at accepted trials only)",
+                                   "evals_per_launch": n_eval, "flop_per_launch": fl, "pg_accepted_per_launch": acc}
             for name, (s2, tg2, spec2, tgh, sph) in rbs.items():
                 if name == first:
                     continue
@@ -613,10 +617,20 @@ def main():
         ev1[k][1].record(stream)
     torch.cuda.synchronize()
     s1_ms = float(np.mean([a.elapsed_time(b) for a, b in ev1]))
-    n_eval = P * ik.S * (ik.k_init + 1)  # fused value + gradient evaluations per stage-one launch
-    flop_per_eval = counts["fwd_flop"] + counts["tan_flop"]
-    sfu_per_eval = counts["fwd_sfu"] + counts["tan_sfu"]
-    achieved_tflops = n_eval * flop_per_eval / (s1_ms / 1e3) / 1e12
+    accepted = solver.pg_accepted()  # accepted PG steps of the last stage-one launch (device counter)
+    n_eval = P * ik.S * (ik.k_init + 1)  # value evaluations per stage-one launch
+    # The method's own work (oracle op counts): every seed's first value and gradient with all rows;
+    # a value at each of the k_init projected trial points, without the rows that vanish there; a
+    # gradient only where the trial is accepted. The kernel computes the gradient at every trial
+    # (fused, one pass; a warp's lanes accept independently), which is reported beside it.
+    n_seed = P * ik.S
+    flop_method = (n_seed * (counts["fwd_flop"] + counts["tan_flop"]) + n_seed * ik.k_init * counts["trial_fwd_flop"]
+                   + accepted * counts["trial_tan_flop"])
+    sfu_method = (n_seed * (counts["fwd_sfu"] + counts["tan_sfu"]) + n_seed * ik.k_init * counts["trial_fwd_sfu"]
+                  + accepted * counts["trial_tan_sfu"])
+    flop_fused = (n_seed * (counts["fwd_flop"] + counts["tan_flop"])
+                  + n_seed * ik.k_init * (counts["trial_fwd_flop"] + counts["trial_tan_flop"]))
+    achieved_tflops = flop_method / (s1_ms / 1e3) / 1e12
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -685,10 +699,13 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_fp32,
                      "traffic": STAGE1_DRAM_BYTES_PER_TARGET * P,
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                     "kernel_ms": s1_ms, "evals_per_launch": n_eval, "flop_per_eval": flop_per_eval,
+                     "kernel_ms": s1_ms, "count": "method (oracle op counts; gradients at accepted trials only)",
+                     "flop_per_launch": flop_method, "evals_per_launch": n_eval,
+                     "pg_accepted_per_launch": accepted, "pg_accept_rate": accepted / (n_seed * ik.k_init),
                      "frac_of_live_ffma": achieved_tflops / cal["ffma_tflops"],
-                     "sfu_results_per_s": n_eval * sfu_per_eval / (s1_ms / 1e3),
-                     "sfu_frac_of_live_mufu": n_eval * sfu_per_eval / (s1_ms / 1e3) / (cal["mufu_tops"] * 1e12)},
+                     "frac_fused_form": flop_fused / (s1_ms / 1e3) / 1e12 / peak_fp32,
+                     "sfu_results_per_s": sfu_method / (s1_ms / 1e3),
+                     "sfu_frac_of_live_mufu": sfu_method / (s1_ms / 1e3) / (cal["mufu_tops"] * 1e12)},
         "calibration": cal,
         "plain_form": {"value": plain_rate, "unit": UNIT, "targets": Pp, "success_rate": plain_succ,
                        "optimised_success_rate_same_targets": opt_succ_sub, "speedup": value / world / plain_rate},

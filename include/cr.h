@@ -63,6 +63,13 @@ typedef enum { CR_F32 = 0, CR_F64 = 1 } cr_dtype;
 #define CR_MAX_NB 64
 #define CR_MAX_SEEDS 256
 
+/* argmin of Algorithm 1 (the last step of cr_solve_ik and of every solver built on it): refined
+ * candidates whose final FP64 cost is at most CR_ARGMIN_TIE (about 8 um of tip position, or the
+ * rotation equivalent, under the default pose weights) are equally good solutions, whose cost
+ * differences are rounding: the first of them in SelectTop order is kept. Above it, the lowest cost
+ * wins (ties to the earlier candidate). */
+#define CR_ARGMIN_TIE 1e-8
+
 /* Decision variables of a segment (cr_robot.model). Three per segment in both models.
  * CR_MODEL_TENDON: the tendon displacements u_ij = l_ij - L_i of Eq. 4; the exact inverse of Eq. 4
  *   gives the bend (theta_i, phi_i), L_i is the robot's; bounds |u_ij| <= u_max_i, sum_j u_ij = 0.
@@ -227,7 +234,9 @@ CR_API cr_status cr_topk(const float* cost, const float* coll, const void* u, in
  * Solvers
  * ------------------------------------------------------------------------------------------- */
 
-/* Scratch bytes cr_solve_ik needs for P targets. */
+/* Scratch bytes cr_solve_ik needs for P targets. The workspace starts with the status word
+ * (int32, read by cr_poll_status); at byte offset 8 a uint64 counts the projected-gradient steps
+ * that stage one accepted, over all seeds (both are cleared by cr_solve_ik and cr_ik_stage1). */
 CR_API size_t cr_ik_workspace_size(const cr_robot* robot, int64_t P, const cr_ik_params* prm);
 
 /* Algorithm 1 (beam-search IK) for the P targets of `task` (task->seeds_per_target is ignored):

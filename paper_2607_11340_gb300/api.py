@@ -182,6 +182,11 @@ class IkSolver:
         torch.cuda.current_stream().synchronize()
         return out_host
 
+    def pg_accepted(self) -> int:
+        """Accepted projected-gradient steps of the last solve's stage one, over all seeds (the
+        workspace counter the kernels add to; reading it synchronises the stream)."""
+        return int(self.workspace[8:16].view(torch.int64).item())
+
     def status(self) -> int:
         return lib.cr_poll_status(self.workspace)
 

@@ -251,16 +251,17 @@ __device__ void batch_finish(const RobotK<float>& rb, const WeightsK<float>& w, 
       Fk = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, it.no, ud, a.lim_tol, pos, rot, fl);
     }
   }
-  // argmin of the FP64 cost (first minimum in candidate order)
-  double bF = isfinite(Fk) ? Fk : INFINITY;
+  // argmin of the FP64 cost (first minimum in candidate order; costs <= CR_ARGMIN_TIE count as 0)
+  double bkey = isfinite(Fk) ? (Fk <= CR_ARGMIN_TIE ? 0.0 : Fk) : INFINITY;
   int bk = lane;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const double oF = __shfl_xor_sync(FULL, bF, off);
+    const double oF = __shfl_xor_sync(FULL, bkey, off);
     const int ok = __shfl_xor_sync(FULL, bk, off);
-    if (oF < bF || (oF == bF && ok < bk)) { bF = oF; bk = ok; }
+    if (oF < bkey || (oF == bkey && ok < bk)) { bkey = oF; bk = ok; }
   }
-  const bool found = bF < INFINITY;
+  const bool found = bkey < INFINITY;
+  const double bF = __shfl_sync(FULL, Fk, bk & 31);
   if (lane == bk) {
 #pragma unroll
     for (int q = 0; q < D; ++q) bst[q] = ud[q];

@@ -851,15 +851,57 @@ CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3
 // ------------------------------------------------------------------------------------------------
 CR_HD constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
+// Two-float accumulator for the normal equations of the FP32 bulk form. J^T J of an FP32 Jacobian
+// with condition number kappa, rounded to FP32, carries a relative error of about kappa^2 eps32 in
+// its small eigendirections, which the LM step inherits (measured: step errors of 5e-5 of the
+// displacement bound at kappa(J) = 400, against 2e-8 from the rounding of J and r alone). FP64
+// accumulation would avoid that on the FP64 pipe (1/64 of the FP32 rate on this GPU); instead every
+// product of two FP32 numbers is split exactly into p + e (p = x y rounded, e = fma(x, y, -p)) and
+// added to a (hi, lo) pair with the error-free sum of Knuth (TwoSum), all on the FP32 pipe. The
+// explicitly rounded intrinsics keep the compiler from fusing a product into the following sum,
+// which would break the exactness. hi + lo carries about 48 bits; it is converted to FP64 for the
+// Cholesky.
+struct F2 {
+  float hi, lo;
+  CR_HD F2(float v = 0.0f) : hi(v), lo(0.0f) {}
+};
+CR_HD void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// acc += v, acc += x y (exact product for F2), generic for float and double accumulators.
+template <typename TA, typename T> CR_HD void acc_add(TA& acc, T v) { acc += TA(v); }
+template <typename TA, typename T> CR_HD void acc_prod(TA& acc, T x, T y) { acc += TA(x) * TA(y); }
+template <> CR_HD void acc_add<F2, float>(F2& acc, float v) {
+  float s, e;
+  two_sum(acc.hi, v, s, e);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, e);
+}
+template <> CR_HD void acc_prod<F2, float>(F2& acc, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float pe = fmaf(x, y, -p);  // x y - p, exact
+  float s, e;
+  two_sum(acc.hi, p, s, e);
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+CR_HD double to_f64(float v) { return double(v); }
+CR_HD double to_f64(double v) { return v; }
+CR_HD double to_f64(const F2& v) { return double(v.hi) + double(v.lo); }
+// The accumulator of an LM normal matrix for bulk precision T.
+template <typename T> struct NormalAcc { typedef T type; };
+template <> struct NormalAcc<float> { typedef F2 type; };
+
 // A is any indexable packed lower triangle (normally a register array).
 template <typename TA, int D, typename T, typename AArr>
 CR_HD void rank1(AArr&& A, TA (&g)[D], const T (&j)[D], T r) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    TA ja = TA(j[a]);
-    g[a] += ja * TA(r);
+    acc_prod(g[a], j[a], r);
 #pragma unroll
-    for (int b = 0; b <= a; ++b) A[tri(a, b)] += ja * TA(j[b]);
+    for (int b = 0; b <= a; ++b) acc_prod(A[tri(a, b)], j[a], j[b]);
   }
 }
 
@@ -948,20 +990,20 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
     if (MODEL == CR_MODEL_ARC) {  // length bounds: single-entry rows on the length column
       const int q = 3 * i + 2;
       T hi = ch.L[i] - rb.lmax[i], lo = rb.lmin[i] - ch.L[i];
-      if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; g[q] += TA(w.rho_b * hi); A[tri(q, q)] += TA(w.rho_b); }
-      if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; g[q] -= TA(w.rho_b * lo); A[tri(q, q)] += TA(w.rho_b); }
+      if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; acc_add(g[q], w.rho_b * hi); acc_add(A[tri(q, q)], w.rho_b); }
+      if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; acc_add(g[q], -(w.rho_b * lo)); acc_add(A[tri(q, q)], w.rho_b); }
     } else {
       T su = u[3 * i] + u[3 * i + 1] + u[3 * i + 2];
       F += T(0.5) * w.rho_eq * su * su;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         int q = 3 * i + j;
-        g[q] += TA(w.rho_eq * su);
+        acc_add(g[q], w.rho_eq * su);
 #pragma unroll
-        for (int j2 = 0; j2 <= j; ++j2) A[tri(q, 3 * i + j2)] += TA(w.rho_eq);
+        for (int j2 = 0; j2 <= j; ++j2) acc_add(A[tri(q, 3 * i + j2)], w.rho_eq);
         T hi = u[q] - rb.umax[i], lo = -rb.umax[i] - u[q];
-        if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; g[q] += TA(w.rho_b * hi); A[tri(q, q)] += TA(w.rho_b); }
-        if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; g[q] -= TA(w.rho_b * lo); A[tri(q, q)] += TA(w.rho_b); }
+        if (hi > T(0)) { F += T(0.5) * w.rho_b * hi * hi; acc_add(g[q], w.rho_b * hi); acc_add(A[tri(q, q)], w.rho_b); }
+        if (lo > T(0)) { F += T(0.5) * w.rho_b * lo * lo; acc_add(g[q], -(w.rho_b * lo)); acc_add(A[tri(q, q)], w.rho_b); }
       }
     }
     if (ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
@@ -975,9 +1017,9 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
       T rr = w.sk * vk;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        g[3 * i + a] += TA(jj[a] * rr);
+        acc_prod(g[3 * i + a], jj[a], rr);
 #pragma unroll
-        for (int b = 0; b <= a; ++b) A[tri(3 * i + a, 3 * i + b)] += TA(jj[a] * jj[b]);
+        for (int b = 0; b <= a; ++b) acc_prod(A[tri(3 * i + a, 3 * i + b)], jj[a], jj[b]);
       }
     }
   }

@@ -62,7 +62,8 @@ static cr_status solve_ik_common(const cr_robot* robot, const cr_scene* scene, c
   a.success = success;
   a.stream = stream_of(stream);
   if (which & 1) {
-    cudaError_t e = cudaMemsetAsync((unsigned char*)workspace + lay.status, 0, sizeof(int32_t), a.stream);
+    // the status word and, at offset 8, the count of accepted stage-one steps
+    cudaError_t e = cudaMemsetAsync((unsigned char*)workspace + lay.status, 0, 16, a.stream);
     if (e != cudaSuccess) return fail(CR_ECUDA, "cr_solve_ik: %s", cudaGetErrorString(e));
   }
   return prm->precision == CR_F64 ? crk::launch_solve_ik<double>(a, which) : crk::launch_solve_ik<float>(a, which);

@@ -1,0 +1,5 @@
+// Solver kernels of the 6-segment tendon model, FP32 bulk.
+#include "cr_solve_impl.cuh"
+namespace crk {
+CR_SOLVE_N_INSTANTIATE(, float, 6, CR_MODEL_TENDON)
+}

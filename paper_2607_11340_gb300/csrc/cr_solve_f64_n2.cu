@@ -1,0 +1,5 @@
+// Solver kernels of the 2-segment tendon model, FP64.
+#include "cr_solve_impl.cuh"
+namespace crk {
+CR_SOLVE_N_INSTANTIATE(, double, 2, CR_MODEL_TENDON)
+}

@@ -6,7 +6,8 @@
 //  k_ik_refine : one thread per selected candidate: k_final LM iterations (J, r and J^T J in the
 //                bulk precision; Cholesky, solve and gain ratio in FP64), then the FP64
 //                re-evaluation of cost, pose error, limits and clearance.
-//  k_ik_argmin : one thread per target: argmin of the FP64 cost over its candidates.
+//  k_ik_argmin : one thread per target: argmin of the FP64 cost over its candidates (costs at the
+//                rounding level, <= CR_ARGMIN_TIE, tie and the first in SelectTop order wins).
 #pragma once
 
 #include <limits.h>
@@ -18,12 +19,13 @@ namespace crk {
 
 // ------------------------------------------------------------------------------------------------
 // One projected-gradient step (stage one): trial u' = Pi(u - alpha g / |g|); accept iff F(u') < F(u).
+// Returns 1 if the step was accepted.
 // The trial point is feasible, so its bound and sum-zero rows are zero: the FP32 form leaves them out
 // (in FP32 the sum-zero row would only contribute the projection's rounding residue); the FP64 form
 // evaluates them, term by term like the FP64 definition.
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
-CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
+CR_HD int pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                    const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha) {
   constexpr int D = 3 * N;
   T gn2 = T(0);
@@ -43,9 +45,10 @@ CR_HD void pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Ta
     F = F1;
     coll = c1;
     alpha *= T(1.25);
-  } else {
-    alpha *= T(0.5);
+    return 1;
   }
+  alpha *= T(0.5);
+  return 0;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -59,12 +62,14 @@ CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
   double Ad[DD], Dg[D], dl[D], invd[D];
   T F;
   {
-    T A[DD], g[D];
-    F = eval_ik_normal<T, T, N, OBST, MODEL>(rb, w, kind, tg, sph, no, u, A, g);
+    // FP32 bulk: J^T J and J^T r accumulated exactly in two-float pairs (NormalAcc, F2)
+    typedef typename NormalAcc<T>::type TA;
+    TA A[DD], g[D];
+    F = eval_ik_normal<T, TA, N, OBST, MODEL>(rb, w, kind, tg, sph, no, u, A, g);
 #pragma unroll
-    for (int a = 0; a < DD; ++a) Ad[a] = double(A[a]);
+    for (int a = 0; a < DD; ++a) Ad[a] = to_f64(A[a]);
 #pragma unroll
-    for (int q = 0; q < D; ++q) dl[q] = double(g[q]);
+    for (int q = 0; q < D; ++q) dl[q] = to_f64(g[q]);
   }
 #pragma unroll
   for (int q = 0; q < D; ++q) {
@@ -206,6 +211,7 @@ template <typename T> struct IkArgs {
   double* rot_out;
   unsigned char* success;
   int* status;
+  unsigned long long* pg_accepted;  // stage one adds its accepted steps here (the workspace counter)
 };
 
 template <typename T> struct Stage1Smem {
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
     __syncthreads();
   }
   const int s = threadIdx.x;
+  int acc = 0;  // accepted steps of this seed
   if (s < S) {
     TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
     T u[D], g[D], coll = T(0);
@@ -252,13 +259,22 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
     T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
     T alpha = a.alpha0;
     for (int it = 0; it < a.k_init; ++it)
-      pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+      acc += pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
     sF[s] = float(F);
     sC[s] = float(coll);
 #pragma unroll
     for (int q = 0; q < D; ++q) su[q * S + s] = u[q];
   }
+  // accepted steps per warp (every lane of the block is here: blockDim is a multiple of 32), one
+  // slot per warp in `skipped`, which SelectTop does not use
+  acc = __reduce_add_sync(0xffffffffu, acc);
+  if ((threadIdx.x & 31) == 0) skipped[threadIdx.x >> 5] = acc;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int wi = 0; wi < (S + 31) / 32; ++wi) tot += (unsigned)skipped[wi];
+    atomicAdd(a.pg_accepted, tot);
+  }
   if (threadIdx.x < 32) warp_topk<T>(sF, sC, su, S, D, S, a.K, a.eps, sel, taken, skipped);
   __syncthreads();
   const int64_t ldc = a.P * a.K;
@@ -480,12 +496,16 @@ __global__ void __launch_bounds__(128) k_ik_argmin(int64_t P, int K, double pos_
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
   const int64_t PK = P * K;
+  // key: the cost, or 0 for a solution at the rounding level (CR_ARGMIN_TIE): the first such
+  // candidate in SelectTop order wins
   int best = -1;
-  double bF = INFINITY;
+  double bkey = INFINITY;
   for (int k = 0; k < K; ++k) {
-    double F = cand_F[p * K + k];
-    if (isfinite(F) && F < bF) { bF = F; best = k; }
+    const double F = cand_F[p * K + k];
+    const double key = F <= CR_ARGMIN_TIE ? 0.0 : F;
+    if (isfinite(F) && key < bkey) { bkey = key; best = k; }
   }
+  const double bF = best >= 0 ? cand_F[p * K + best] : INFINITY;
   if (best < 0) {
 #pragma unroll
     for (int q = 0; q < D; ++q) u_out[q * P + p] = NAN;
@@ -709,6 +729,7 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
   k.rot_out = a.rot;
   k.success = a.success;
   k.status = (int*)(ws + a.lay.status);
+  k.pg_accepted = (unsigned long long*)(ws + a.lay.status + 8);
   return k;
 }
 
@@ -913,6 +934,25 @@ template <typename T> cr_status launch_seeds_arc(const SolveArgs& a) { CR_ARC_DI
   EXT template cr_status launch_lm_steps_arc<T>(const SolveArgs&);      \
   EXT template cr_status launch_pg_steps_arc<T>(const SolveArgs&);      \
   EXT template cr_status launch_seeds_arc<T>(const SolveArgs&);
+
+// Per segment count (one compilation unit each, so that the units build in parallel and ptxas
+// allocates registers per kernel family).
+#define CR_SOLVE_N_INSTANTIATE(EXT, T, N_, MODEL)                           \
+  EXT template cr_status solve_ik_n<T, N_, MODEL>(const SolveArgs&, int); \
+  EXT template cr_status lm_steps_n<T, N_, MODEL>(const SolveArgs&);      \
+  EXT template cr_status pg_steps_n<T, N_, MODEL>(const SolveArgs&);      \
+  EXT template cr_status seeds_n<T, N_, MODEL>(const SolveArgs&);
+#define CR_SOLVE_ALL_N_EXTERN(T)                         \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 1, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 2, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 3, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 4, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 5, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 6, CR_MODEL_TENDON) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 1, CR_MODEL_ARC)    \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 2, CR_MODEL_ARC)    \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 3, CR_MODEL_ARC)    \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 4, CR_MODEL_ARC)
 
 #define CR_SOLVE_INSTANTIATE(EXT, T)                                \
   EXT template cr_status launch_solve_ik<T>(const SolveArgs&, int); \

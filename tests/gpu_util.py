@@ -49,3 +49,88 @@ def edge_states(spec, rng, count):
     u[1] = 1e-9 * u[2]
     u[3] = u[3] / np.abs(u[3]).max() * spec.umax
     return u
+
+
+# Unit roundoff of the arithmetic that takes an accept decision (FP64, or FP32 for the bulk form).
+EPS = {lib.CR_F64: 2.0 ** -53, lib.CR_F32: 2.0 ** -24}
+
+
+def pose_operand_scale(spec: synth.RobotSpec, w: synth.WeightSpec = synth.WEIGHTS) -> float:
+    """Magnitude of the operands whose differences form the pose rows: w_p times the reach plus
+    w_R times the largest rotation angle. A residual computed in precision eps carries an absolute
+    error of a modest multiple of eps times this scale, however small the residual itself."""
+    reach = sum(spec.L) if spec.lmax is None else spec.n * spec.lmax
+    return w.wp * reach + w.wR * np.pi
+
+
+def near_ties(F_start, F_trial, eps, scale, k=64.0):
+    """Accept decisions F_trial < F_start that rounding can flip. With F = |r|^2 / 2 and each
+    residual known to within k eps scale, F is known to within k eps scale |r| + (k eps scale)^2 / 2,
+    so the sign of F_trial - F_start is decided by the arithmetic, not by the method, when
+    |F_trial - F_start| is below the sum of the two bounds. Elementwise; NaN trials (a failed
+    Cholesky on the reference side) count as ties."""
+    F_start, F_trial = np.asarray(F_start), np.asarray(F_trial)
+    e = k * eps * scale
+    band = e * (np.sqrt(2 * np.abs(F_start)) + np.sqrt(2 * np.abs(np.nan_to_num(F_trial)))) + e * e
+    return ~np.isfinite(F_trial) | (np.abs(F_trial - F_start) <= band)
+
+
+def first_true(mask):
+    """[B][T] -> per row the first index where mask is set (T if none)."""
+    mask = np.asarray(mask, bool)
+    return np.where(mask.any(axis=1), mask.argmax(axis=1), mask.shape[1])
+
+
+def cost_errors(F_gpu, F_ref, r_norm, scale):
+    """Errors of a least-squares cost F = |r|^2 / 2: (plain relative |dF| / F, norm-wise relative to
+    the data |dF| / (F + |r| scale)). Each residual row is a difference of operands of magnitude
+    up to `scale` (pose_operand_scale), which a precision of unit roundoff eps represents only to
+    eps scale; F is then known to within about eps scale |r|, so its attainable relative accuracy,
+    2 eps scale / |r|, degrades without bound as the residual vanishes. The norm-wise measure
+    divides by the size of the data instead, and is the one bounded for every state."""
+    F_gpu, F_ref, r_norm = (np.asarray(x, np.float64) for x in (F_gpu, F_ref, r_norm))
+    d = np.abs(F_gpu - F_ref)
+    return d / np.maximum(F_ref, 1e-300), d / (F_ref + r_norm * scale)
+
+
+def grad_errors(g_gpu, g_ref, J_ref, r_norm, scale):
+    """Errors of g = J^T r per state: (plain, max_q |dg| / max_q |g|; norm-wise relative to the data,
+    max_q |dg| / (max_q |g| + max |J| (|r| + scale))): an error of eps scale in each residual row and
+    of eps |J| in each Jacobian entry moves g by about eps |J| (scale + |r|)."""
+    g_gpu, g_ref = np.asarray(g_gpu, np.float64), np.asarray(g_ref, np.float64)
+    B = len(g_ref)
+    d = np.abs(g_gpu - g_ref).reshape(B, -1).max(axis=1)
+    gm = np.abs(g_ref).reshape(B, -1).max(axis=1)
+    Jm = np.abs(np.asarray(J_ref)).reshape(B, -1).max(axis=1)
+    return d / np.maximum(gm, 1e-300), d / (gm + Jm * (np.asarray(r_norm) + scale))
+
+
+def kink_or_pi(states, spec: synth.RobotSpec, rot_rows, prec, k=64.0, w: synth.WeightSpec = synth.WEIGHTS):
+    """Per state [..., d]: does an iteration starting there depend on rounding in a way the
+    iterate comparison cannot follow? (b) a bound or curvature hinge sits at its kink to within
+    k eps of its scale, so one precision may take the row as active and the other not (their
+    Jacobians then differ by a whole penalty row); (c) in FP32, a rotation error within 0.05 rad of
+    pi, where the FP32 SO(3) log (error ~ eps / sin(angle)) cannot resolve the axis. rot_rows: the
+    oracle's rotation rows [..., 3] (w_R Log), or None for the 5-DoF task. A hinge argument of
+    exactly zero (a state the projection clamped onto its bound) is on the kink in both precisions
+    and is not flagged."""
+    x = np.asarray(states, np.float64)
+    eps = EPS[prec]
+    # a state exactly on the kink (a projection's clamp) is on it in both precisions: not ambiguous
+    band = lambda v, s: (np.abs(v) <= k * eps * s) & (v != 0)
+    n = spec.n
+    kink = np.zeros(x.shape[:-1], bool)
+    for i in range(n):
+        a, b_, c = x[..., 3 * i], x[..., 3 * i + 1], x[..., 3 * i + 2]
+        if spec.lmin is not None:  # arc model: (theta cos phi, theta sin phi, L)
+            th = np.hypot(a, b_)
+            kink |= band(c - spec.lmax, spec.lmax) | band(spec.lmin - c, spec.lmax)
+        else:  # tendon model: |u_ij| <= u_max, theta from the inverse of Eq. 4
+            th = (2.0 / (3.0 * spec.rc)) * np.hypot(a - 0.5 * (b_ + c), (np.sqrt(3.0) / 2.0) * (b_ - c))
+            for u in (a, b_, c):
+                kink |= band(np.abs(u) - spec.umax, spec.umax)
+        kink |= band(th - spec.thmax, spec.thmax)
+    if rot_rows is not None and prec == lib.CR_F32:
+        ang = np.linalg.norm(np.asarray(rot_rows, np.float64), axis=-1) / w.wR
+        kink |= ang > np.pi - 0.05
+    return kink

@@ -2,14 +2,16 @@
 against the FP64 oracle: kinematics, tip Jacobian (with the length columns), cost and gradient with
 length, curvature and clearance rows, bit-identical seeds, LM iterates, and Algorithm 1 on the
 shapes of the paper's IK benchmarks (1 m segments, 128 seeds -> top 8, 200 iterations; the sphere
-lattice). Tolerances as in the tendon-model tests: FP64 1e-12, FP32 1e-5 (norm-wise per state).
+lattice). Tolerances as in the tendon-model tests: FP64 1e-12, FP32 1e-5 (norm-wise per state; the
+FP32 cost and gradient relative to the size of their data, gpu_util.cost_errors / grad_errors).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
-from gpu_util import TDT, TOL, dev_soa, host_aos, orc_robot, orc_weights, rowwise_rel, targets_dev
+from gpu_util import (EPS, TDT, TOL, cost_errors, dev_soa, first_true, grad_errors, host_aos, kink_or_pi, near_ties,
+                      orc_robot, orc_weights, pose_operand_scale, rowwise_rel, targets_dev)
 from paper_2607_11340_gb300 import api, lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -50,16 +52,18 @@ def test_fk_and_jacobian_parity(prec, spec):
     qb = host_aos(qg)
     rbo = orc_robot(spec)
     To, bbo = O.fk(rbo, qb, backbone=True)
-    tol = TOL[prec] * 10
+    tol = TOL[prec]
     reach = spec.n * spec.lmax
-    assert rowwise_rel(host_aos(T)[:, :9], To[:, :9], 1.0).max() <= tol
-    assert rowwise_rel(host_aos(T)[:, 9:], To[:, 9:], reach).max() <= tol
     bbg = bb.double().cpu().numpy().transpose(2, 0, 1)
-    assert rowwise_rel(bbg.reshape(B, -1), bbo.reshape(B, -1), reach).max() <= tol
     Jo = O.tip_jacobian(rbo, qb)
     Jg = J.double().cpu().numpy().transpose(2, 0, 1)
-    assert rowwise_rel(Jg[:, :3].reshape(B, -1), Jo[:, :3].reshape(B, -1)).max() <= tol
-    assert rowwise_rel(Jg[:, 3:].reshape(B, -1), Jo[:, 3:].reshape(B, -1)).max() <= tol
+    e = dict(R=rowwise_rel(host_aos(T)[:, :9], To[:, :9], 1.0).max(),
+             p=rowwise_rel(host_aos(T)[:, 9:], To[:, 9:], reach).max(),
+             backbone=rowwise_rel(bbg.reshape(B, -1), bbo.reshape(B, -1), reach).max(),
+             J_translation=rowwise_rel(Jg[:, :3].reshape(B, -1), Jo[:, :3].reshape(B, -1)).max(),
+             J_rotation=rowwise_rel(Jg[:, 3:].reshape(B, -1), Jo[:, 3:].reshape(B, -1)).max())
+    print(f"arc FK/J n={spec.n} prec={prec}: " + ", ".join(f"{k} {v:.2e}" for k, v in e.items()) + f" (tolerance {tol:.0e})")
+    assert max(e.values()) <= tol
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -85,15 +89,19 @@ def test_cost_grad_parity(prec):
     cost, coll, gu, _ = api.cost_grad(api.robot_struct(spec), api.Scene(spheres), task, qg, grad=True, coll=True)
     torch.cuda.synchronize()
     qb = host_aos(qg)
-    ref = O.ik_eval(rbo, orc_weights(), spheres, lib.CR_TASK_IK6, tg, S, qb, want=("F", "coll", "g"))
-    E = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, qb, want=("r",))["r"][:, 3:6]
-    ok = np.linalg.norm(E, axis=1) < np.pi - 0.05 if prec == lib.CR_F32 else np.ones(len(q), bool)
+    ref = O.ik_eval(rbo, orc_weights(), spheres, lib.CR_TASK_IK6, tg, S, qb, want=("F", "coll", "g", "r", "J"))
+    rn = np.linalg.norm(ref["r"], axis=1)
+    scale = pose_operand_scale(spec)
     tol = TOL[prec]
     assert (ref["coll"] > 0).sum() > 10
-    Fg = cost.double().cpu().numpy()
-    assert (np.abs(Fg - ref["F"]) / np.maximum(ref["F"], 1e-30))[ok].max() <= tol * 10
-    assert (np.abs(coll.double().cpu().numpy() - ref["coll"]) / np.maximum(ref["F"], 1e-30))[ok].max() <= tol * 10
-    assert rowwise_rel(host_aos(gu)[ok], ref["g"][ok]).max() <= tol * 100
+    Fp, Fd = cost_errors(cost.double().cpu().numpy(), ref["F"], rn, scale)
+    _, Cd = cost_errors(coll.double().cpu().numpy(), ref["coll"], rn, scale)
+    gp, gd = grad_errors(host_aos(gu), ref["g"], ref["J"], rn, scale)
+    print(f"arc cost prec={prec}: F plain {Fp.max():.2e} / data {Fd.max():.2e}; clearance part data {Cd.max():.2e}; "
+          f"gradient plain {gp.max():.2e} / data {gd.max():.2e} (tolerance {tol:.0e})")
+    if prec == lib.CR_F64:
+        assert Fp.max() <= tol and gp.max() <= tol
+    assert Fd.max() <= tol and Cd.max() <= tol and gd.max() <= tol
 
 
 def test_seeds_bitwise():
@@ -107,13 +115,15 @@ def test_seeds_bitwise():
         assert np.array_equal(host_aos(out), want)
 
 
-@pytest.mark.parametrize("prec,n", [(lib.CR_F64, 3), (lib.CR_F32, 2)])
+@pytest.mark.parametrize("prec,n", [(lib.CR_F64, 2), (lib.CR_F64, 3), (lib.CR_F32, 2)])
 def test_lm_iterates(prec, n):
-    """20 LM iterations, one call each, against the oracle's iterate history: FP64 1e-10 on the
-    3-segment robot; FP32 bulk (FP64 Cholesky) 1e-4 of the state scale for 95 % of the seeds on the
-    2-segment robot. Three extendable segments have 9 parameters for a 6-DoF pose: the damped step's
-    component in that 3-dimensional null space is set by rounding, so FP32 and FP64 drift apart
-    there along equally good solutions; two segments have a unique solution to follow."""
+    """20 LM iterations, one call each, against the oracle's iterate history, every seed compared up
+    to the first iteration whose outcome rounding decides (a decision tie, a hinge at its kink, in
+    FP32 a rotation error near pi; gpu_util). Bounds in the state's units (rad, m): FP32 bulk (FP64
+    Cholesky, two-float normal equations) 1e-4 and FP64 1e-10 on the 2-segment robot, whose pose
+    fixes the solution; FP64 1e-9 on the 3-segment robot, which is redundant (9 parameters for a
+    6-DoF pose): the damped step's component in the 3-dimensional null space is set by the damping,
+    and rounding-level differences there grow over the iterations (measured 1.4e-10)."""
     spec = synth.arc_robot(n, True)
     rbo = orc_robot(spec)
     rng = np.random.default_rng(602)
@@ -131,11 +141,19 @@ def test_lm_iterates(prec, n):
     for it in range(iters):
         lib.cr_lm_step(api.robot_struct(spec), api.Scene(None).c, task, qg, lam, nu, n_iter=1)
         errs.append(np.abs(host_aos(qg) - ref["hist"][it]).max(axis=1))
-    worst = np.array(errs).max(axis=0)
-    if prec == lib.CR_F64:
-        assert np.mean(worst <= 1e-10) >= 0.99, np.sort(worst)[-5:]
-    else:
-        assert np.mean(worst <= 1e-4) >= 0.95, np.sort(worst)[-8:]
+    err = np.array(errs).T
+    B = P * S
+    xstart = np.concatenate([q0b[:, None, :], ref["hist"][:-1].transpose(1, 0, 2)], axis=1)
+    rs = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tg, S, 0).repeat(iters, 0), 1,
+                   xstart.reshape(B * iters, -1), want=("r",))["r"].reshape(B, iters, -1)
+    tie = near_ties(ref["Fstart"], ref["Ftrial"], EPS[prec], pose_operand_scale(spec))
+    first = first_true(tie | kink_or_pi(xstart, spec, rs[:, :, 3:6], prec))
+    checked = np.arange(iters)[None, :] < first[:, None]
+    tol = 1e-4 if prec == lib.CR_F32 else (1e-10 if n == 2 else 1e-9)
+    print(f"arc LM n={n} prec={prec}: max error {err[checked].max():.2e} over {int(checked.sum())} compared "
+          f"iterations; {int((first < iters).sum())} of {len(first)} seeds reach a rounding-decided iteration")
+    assert err[checked].max() <= tol, np.sort(err[checked])[-5:]
+    assert checked[:, 0].mean() >= 0.9  # the first iteration is compared for (almost) every seed
     assert np.mean(ref["F"] < 1e-12) > 0.5
 
 

@@ -1,8 +1,12 @@
 """GPU parity of the kinematics, Jacobian, cost and adjoint entry points against the FP64 oracle.
 
 Tolerances: FP64 1e-12 and FP32 1e-5, relative, norm-wise per state and per quantity (the largest
-component of that quantity sets the scale). Batches span several 128-thread blocks plus a ragged
-tail, and include the straight and nearly-straight configurations and states on the bounds.
+component of that quantity sets the scale; lengths scale with the reach). The cost and gradient in
+FP32 are measured relative to the size of the data they are formed from (gpu_util.cost_errors,
+grad_errors): a least-squares cost near its zero cannot be computed to a relative accuracy better
+than the rounding of its operands over the residual. Every test prints the measured maxima.
+Batches span several 128-thread blocks plus a ragged tail, and include the straight and
+nearly-straight configurations, states on the bounds, and rotations near pi.
 """
 import math
 
@@ -11,7 +15,8 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_util import TDT, TOL, dev_soa, edge_states, host_aos, orc_robot, orc_weights, rowwise_rel, targets_dev
+from gpu_util import (TDT, TOL, cost_errors, dev_soa, edge_states, grad_errors, host_aos, orc_robot, orc_weights,
+                      pose_operand_scale, rowwise_rel, targets_dev)
 from paper_2607_11340_gb300 import api, lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -41,10 +46,12 @@ def test_fk_parity(prec, spec):
     To, bbo = O.fk(orc_robot(spec), ub, backbone=True)
     Tg = host_aos(T)
     tol = TOL[prec]
-    assert rowwise_rel(Tg[:, :9], To[:, :9], 1.0).max() <= tol * 10
-    assert rowwise_rel(Tg[:, 9:], To[:, 9:], sum(spec.L)).max() <= tol * 10
     bbg = bb.double().cpu().numpy().transpose(2, 0, 1)
-    assert rowwise_rel(bbg.reshape(B, -1), bbo.reshape(B, -1), sum(spec.L)).max() <= tol * 10
+    eR = rowwise_rel(Tg[:, :9], To[:, :9], 1.0).max()
+    ep = rowwise_rel(Tg[:, 9:], To[:, 9:], sum(spec.L)).max()
+    eb = rowwise_rel(bbg.reshape(B, -1), bbo.reshape(B, -1), sum(spec.L)).max()
+    print(f"FK n={spec.n} prec={prec}: R {eR:.2e}, p {ep:.2e}, backbone {eb:.2e} (tolerance {tol:.0e})")
+    assert max(eR, ep, eb) <= tol
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -58,9 +65,11 @@ def test_tip_jacobian_parity(prec):
     torch.cuda.synchronize()
     Jo = O.tip_jacobian(orc_robot(spec), host_aos(ug))
     Jg = J.double().cpu().numpy().transpose(2, 0, 1)
-    tol = TOL[prec] * 10
-    assert rowwise_rel(Jg[:, :3].reshape(B, -1), Jo[:, :3].reshape(B, -1)).max() <= tol
-    assert rowwise_rel(Jg[:, 3:].reshape(B, -1), Jo[:, 3:].reshape(B, -1)).max() <= tol
+    tol = TOL[prec]
+    ep = rowwise_rel(Jg[:, :3].reshape(B, -1), Jo[:, :3].reshape(B, -1)).max()
+    ew = rowwise_rel(Jg[:, 3:].reshape(B, -1), Jo[:, 3:].reshape(B, -1)).max()
+    print(f"J prec={prec}: translation rows {ep:.2e}, rotation rows {ew:.2e} (tolerance {tol:.0e})")
+    assert max(ep, ew) <= tol
 
 
 def _cost_case(spec, kind, rng, P, S, obstacles, thmax=None):
@@ -99,21 +108,26 @@ def test_cost_grad_parity(prec, kind, obstacles):
     gsum = api.reduce_rows(gp)
     torch.cuda.synchronize()
     ub = host_aos(ug)
-    ref = O.ik_eval(rbo, W, spheres, kind, tg, S, ub, want=("F", "coll", "g"))
-    # rotation error near pi makes the FP32 log ill-conditioned; those states are compared in FP64 only
-    E = O.ik_eval(rbo, W, None, kind, tg, S, ub, want=("r",))["r"][:, 3:6]
-    ok = np.linalg.norm(E, axis=1) < math.pi - 0.05 if prec == lib.CR_F32 else np.ones(len(u), bool)
+    ref = O.ik_eval(rbo, W, spheres, kind, tg, S, ub, want=("F", "coll", "g", "r", "J"))
+    rn = np.linalg.norm(ref["r"], axis=1)
+    scale = pose_operand_scale(spec)
     tol = TOL[prec]
-    Fg = cost.double().cpu().numpy()
-    assert (np.abs(Fg - ref["F"]) / np.maximum(ref["F"], 1e-30))[ok].max() <= tol * 10
-    Cg = coll.double().cpu().numpy()
     if obstacles:
         assert (ref["coll"] > 0).sum() > 5
-    assert (np.abs(Cg - ref["coll"]) / np.maximum(ref["F"], 1e-30))[ok].max() <= tol * 10
-    assert rowwise_rel(host_aos(gu)[ok], ref["g"][ok]).max() <= tol * 100
+    if kind == lib.CR_TASK_IK6:  # the batch includes rotation errors near pi
+        assert (np.linalg.norm(ref["r"][:, 3:6], axis=1) / synth.WEIGHTS.wR > math.pi - 0.05).sum() >= 2
+    Fp, Fd = cost_errors(cost.double().cpu().numpy(), ref["F"], rn, scale)
+    Cp, Cd = cost_errors(coll.double().cpu().numpy(), ref["coll"], rn, scale)
+    gp_, gd = grad_errors(host_aos(gu), ref["g"], ref["J"], rn, scale)
     pg = O.ik_param_grad(rbo, W, spheres, kind, tg, S, ub)
-    if ok.all():
-        np.testing.assert_allclose(gsum.cpu().numpy(), pg, rtol=tol * 100, atol=tol * 100 * np.abs(pg).max())
+    ep = np.abs(gsum.cpu().numpy() - pg).max() / np.abs(pg).max()
+    print(f"cost kind={kind} obstacles={obstacles} prec={prec}: F plain {Fp.max():.2e} / data {Fd.max():.2e}; "
+          f"clearance part data {Cd.max():.2e}; gradient plain {gp_.max():.2e} / data {gd.max():.2e}; "
+          f"parameter gradient {ep:.2e} (tolerance {tol:.0e})")
+    if prec == lib.CR_F64:
+        assert Fp.max() <= tol and gp_.max() <= tol
+    assert Fd.max() <= tol and Cd.max() <= tol and gd.max() <= tol
+    assert ep <= tol
 
 
 def test_cost_edge_cases():

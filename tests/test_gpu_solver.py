@@ -8,7 +8,8 @@ import pytest
 import torch
 
 import oracle as O
-from gpu_util import TDT, TOL, dev_soa, host_aos, orc_robot, orc_weights, rowwise_rel, targets_dev
+from gpu_util import (EPS, TDT, TOL, dev_soa, first_true, host_aos, near_ties, orc_robot, orc_weights,
+                      kink_or_pi, pose_operand_scale, rowwise_rel, targets_dev)
 from paper_2607_11340_gb300 import api, lib, synth
 
 pytestmark = pytest.mark.gpu
@@ -72,50 +73,60 @@ def _ik_case(spec, kind, P, S, seed=300, spheres=None):
     return rbo, tg, u0
 
 
-def test_pg_iterates_fp64():
-    spec = synth.ROBOT_3SEG
-    P, S, steps = 24, 16, 12
-    rbo, tg, u0 = _ik_case(spec, lib.CR_TASK_IK6, P, S)
-    ug = dev_soa(u0, torch.float64)
-    alpha = torch.full((P * S,), 1e-3, dtype=torch.float64, device="cuda")
-    F = torch.empty(P * S, dtype=torch.float64, device="cuda")
-    task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
-    lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, steps)
-    uo, Fo = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0, steps, 1e-3)
-    err = np.abs(host_aos(ug) - uo).max(axis=1) / spec.umax
-    assert np.mean(err <= 1e-10) >= 0.99, np.sort(err)[-5:]
-    ok = err <= 1e-10
-    np.testing.assert_allclose(F.cpu().numpy()[ok], Fo[ok], rtol=1e-11)
-
-
-def test_pg_one_step_fp32():
+@pytest.mark.parametrize("prec,steps", [(lib.CR_F64, 64), (lib.CR_F32, 64)])
+def test_pg_iterates(prec, steps):
+    """Stage one's projected-gradient iterates, step by step for k_init = 64 steps (one call per
+    step), against the oracle's history from the same (precision-rounded) seeds. A seed is compared
+    at every step up to the first step whose outcome rounding decides (computed from the oracle's own
+    quantities, gpu_util): (a) its accept decision lies within the rounding band of the deciding
+    precision (near_ties), (b) its starting state has a bound or curvature hinge at its kink to
+    within rounding, (c) in FP32, its rotation error lies within 0.05 rad of pi (kink_or_pi). Bound:
+    1e-4 of the displacement bound in FP32, 1e-10 in FP64, at every compared step of every seed."""
     spec = synth.ROBOT_3SEG
     P, S = 32, 16
     rbo, tg, u0 = _ik_case(spec, lib.CR_TASK_IK6, P, S, seed=301)
-    ug = dev_soa(u0, torch.float32)
-    u0f = host_aos(ug)
-    alpha = torch.full((P * S,), 1e-3, dtype=torch.float32, device="cuda")
-    F = torch.empty(P * S, dtype=torch.float32, device="cuda")
+    ug = dev_soa(u0, TDT[prec])
+    u0b = host_aos(ug)
+    alpha = torch.full((P * S,), 1e-3, dtype=TDT[prec], device="cuda")
+    F = torch.empty(P * S, dtype=TDT[prec], device="cuda")
     task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
-    lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, 1)
-    uo, Fo = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0f, 1, 1e-3)
-    moved_g = np.any(host_aos(ug) != u0f, axis=1)
-    moved_o = np.any(uo != u0f, axis=1)
-    same = moved_g == moved_o
-    assert same.mean() >= 0.98
-    err = np.abs(host_aos(ug) - uo).max(axis=1)[same] / spec.umax
-    assert err.max() <= 1e-4
-    np.testing.assert_allclose(F.double().cpu().numpy()[same], Fo[same], rtol=1e-5)
+    got = []
+    for it in range(steps):
+        lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, 1)
+        got.append(host_aos(ug))
+    got = np.stack(got, axis=1)  # [B][steps][d]
+    _, _, h = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b, steps, 1e-3, history=True)
+    d, B = spec.d, P * S
+    F0 = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b)["F"]
+    Fstart = np.concatenate([F0[:, None], h[:, :-1, d + 1]], axis=1)
+    xstart = np.concatenate([u0b[:, None, :], h[:, :-1, :d]], axis=1)  # [B][steps][d]
+    rs = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tg, S, 0).repeat(steps, 0), 1,
+                   xstart.reshape(B * steps, d), want=("r",))["r"].reshape(B, steps, -1)
+    tie = near_ties(Fstart, h[:, :, d + 2], EPS[prec], pose_operand_scale(spec))
+    ill = kink_or_pi(xstart, spec, rs[:, :, 3:6], prec)
+    first = first_true(tie | ill)
+    checked = np.arange(steps)[None, :] < first[:, None]
+    err = np.abs(got - h[:, :, :d]).max(axis=2) / spec.umax
+    tol = 1e-10 if prec == lib.CR_F64 else 1e-4
+    print(f"PG {'f64' if prec == lib.CR_F64 else 'f32'}: {steps} steps, {B} seeds; max error "
+          f"{err[checked].max():.2e} of the bound over {int(checked.sum())} compared steps; seeds stopped by a "
+          f"decision tie {int(first_true(tie).__lt__(steps).sum())}, by a kink / near-pi start "
+          f"{int(first_true(ill).__lt__(steps).sum())} (median first stop at step "
+          f"{np.median(first[first < steps]) if (first < steps).any() else '-'})")
+    assert checked.sum() >= 0.5 * checked.size
+    assert err[checked].max() <= tol, np.sort(err[checked])[-5:]
 
 
 @pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
 def test_lm_iterates(prec):
-    """20 LM iterations, one call per iteration, against the oracle's iterate history.
-    FP64: 1e-10 of the bound. FP32 bulk (FP64 Cholesky): 1e-4 of the bound for the seeds whose
-    oracle accept decisions are not near-ties."""
+    """20 LM iterations, one call per iteration, against the oracle's iterate history. A seed is
+    compared at every iteration up to the first one whose outcome rounding decides (as in
+    test_pg_iterates: a decision within the rounding band of the precision that takes it, FP64 or
+    the bulk form's FP32; a hinge at its kink; in FP32 a rotation error near pi). Bound at every
+    compared iteration of every seed: 1e-4 of the displacement bound (FP32 bulk, FP64 Cholesky),
+    1e-10 (FP64)."""
     spec = synth.ROBOT_3SEG
     P, S, iters = 32, 4, 20
-    rbo, tg, u_true = None, None, None
     rbo = orc_robot(spec)
     rng = np.random.default_rng(302)
     u_true = synth.hexagon_states(rng, P, 3, spec.umax)
@@ -131,12 +142,22 @@ def test_lm_iterates(prec):
     for it in range(iters):
         lib.cr_lm_step(api.robot_struct(spec), api.Scene(None).c, task, ug, lam, nu, n_iter=1)
         errs.append(np.abs(host_aos(ug) - ref["hist"][it]).max(axis=1) / spec.umax)
-    errs = np.array(errs)
-    worst = errs.max(axis=0)
-    if prec == lib.CR_F64:
-        assert np.mean(worst <= 1e-10) >= 0.99, np.sort(worst)[-5:]
-    else:
-        assert np.mean(worst <= 1e-4) >= 0.95, np.sort(worst)[-8:]
+    err = np.array(errs).T  # [B][iters]
+    B = P * S
+    xstart = np.concatenate([u0b[:, None, :], ref["hist"][:-1].transpose(1, 0, 2)], axis=1)  # [B][iters][d]
+    rs = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tg, S, 0).repeat(iters, 0), 1,
+                   xstart.reshape(B * iters, -1), want=("r",))["r"].reshape(B, iters, -1)
+    tie = near_ties(ref["Fstart"], ref["Ftrial"], EPS[prec], pose_operand_scale(spec))
+    first = first_true(tie | kink_or_pi(xstart, spec, rs[:, :, 3:6], prec))
+    checked = np.arange(iters)[None, :] < first[:, None]
+    tol = 1e-10 if prec == lib.CR_F64 else 1e-4
+    excl = int((first < iters).sum())
+    print(f"LM {'f64' if prec == lib.CR_F64 else 'f32'}: max error {err[checked].max():.2e} of the bound over "
+          f"{int(checked.sum())} compared iterations; {excl} of {len(first)} seeds reach a near-tie "
+          f"(median first at iteration {np.median(first[first < iters]) if excl else '-'}); "
+          f"error of those after it: max {err[~checked].max() if (~checked).any() else 0:.2e}")
+    assert err[checked].max() <= tol, np.sort(err[checked])[-5:]
+    assert checked[:, 0].mean() >= 0.9  # the first iteration is compared for (almost) every seed
     assert np.mean(ref["F"] < 1e-12) > 0.5  # most seeds converge in 20 iterations
 
 

@@ -58,9 +58,11 @@ def test_traj_cost_and_adjoint_parity(prec):
     xb = xg.double().cpu().numpy().T.reshape(x.shape)
     ref = O.traj_eval(rbo, O.make_weights(**W.as_dict()), sph, us, goal, xb, want=("F", "g"))
     tol = TOL[prec]
-    np.testing.assert_allclose(cost.double().cpu().numpy(), ref["F"], rtol=10 * tol)
     g = grad.double().cpu().numpy().T.reshape(x.shape)
-    assert rowwise_rel(g.reshape(len(us), -1), ref["g"].reshape(len(us), -1)).max() <= 100 * tol
+    eF = (np.abs(cost.double().cpu().numpy() - ref["F"]) / ref["F"]).max()
+    eg = rowwise_rel(g.reshape(len(us), -1), ref["g"].reshape(len(us), -1)).max()
+    print(f"trajectory cost prec={prec}: F {eF:.2e}, gradient {eg:.2e} (tolerance {tol:.0e})")
+    assert eF <= tol and eg <= tol
 
 
 def test_traj_gradient_vs_central_differences_fp64():
