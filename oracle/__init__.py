@@ -57,13 +57,13 @@ class Robot(C.Structure):
                 ("rbody", C.c_double), ("lmin", C.c_double * MAXSEG), ("lmax", C.c_double * MAXSEG)]
 
 
-MODEL_TENDON, MODEL_ARC = 0, 1
+MODEL_TENDON, MODEL_ARC, MODEL_COUPLED = 0, 1, 2
 
 
 class Weights(C.Structure):
     _fields_ = [(k, C.c_double) for k in
                 ("wp", "wR", "rho_b", "rho_eq", "rho_k", "rho_c", "w_s", "w_len", "rho_v",
-                 "rho_a", "dt", "vmax", "amax", "delta")]
+                 "rho_a", "dt", "vmax", "amax", "delta", "rho_s")]
 
 
 class IkParams(C.Structure):
@@ -73,12 +73,14 @@ class IkParams(C.Structure):
                 ("rot_tol", C.c_double), ("seed", C.c_uint64), ("p0", C.c_int64)]
 
 
-def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3, lmin=None, lmax=None) -> Robot:
+def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3, lmin=None, lmax=None, coupled=False) -> Robot:
     """Tendon model; with lmin/lmax given, the arc model (per segment (theta cos phi, theta sin phi,
-    L) with lmin <= L <= lmax; L then only sets the nominal length)."""
+    L) with lmin <= L <= lmax; L then only sets the nominal length); with coupled, the tendon model
+    with coupled routing (the state holds the actuator displacements, model B)."""
     n = len(L)
     r = Robot()
-    r.n, r.m, r.nb, r.model = n, m, nb, (MODEL_ARC if lmin is not None else MODEL_TENDON)
+    r.n, r.m, r.nb = n, m, nb
+    r.model = MODEL_ARC if lmin is not None else (MODEL_COUPLED if coupled else MODEL_TENDON)
     if lmin is not None:
         lmin = list(lmin) if np.ndim(lmin) else [lmin] * n
         lmax = list(lmax) if np.ndim(lmax) else [lmax] * n
@@ -94,9 +96,10 @@ def make_robot(L, rc, umax, thmax=None, nb=16, rbody=None, m=3, lmin=None, lmax=
 
 
 def make_weights(**kw) -> Weights:
+    """Weights from keyword values; rho_s (the self-contact rows) defaults to 0 (rows left out)."""
     w = Weights()
     for f, _ in Weights._fields_:
-        setattr(w, f, float(kw[f]))
+        setattr(w, f, float(kw.get(f, 0.0) if f == "rho_s" else kw[f]))
     return w
 
 
@@ -183,8 +186,9 @@ def quat_to_R(q):
     return R.reshape(-1, 3, 3)
 
 
-def ik_rows(robot: Robot, n_spheres: int) -> int:
-    return lib().orc_ik_rows(C.byref(robot), C.c_int(n_spheres))
+def ik_rows(robot: Robot, n_spheres: int, weights: Weights | None = None) -> int:
+    w = weights if weights is not None else make_weights(**{f: 0.0 for f, _ in Weights._fields_})
+    return lib().orc_ik_rows(C.byref(robot), C.byref(w), C.c_int(n_spheres))
 
 
 def _spheres(spheres):
@@ -203,7 +207,7 @@ def ik_eval(robot, weights, spheres, kind, targets, S, u, want=("F",), threads=N
     u = _f64(u)
     tg = _f64(targets).reshape(-1, 7)
     B, d = u.shape
-    nr = ik_rows(robot, no)
+    nr = ik_rows(robot, no, weights)
     out = {}
     r = np.zeros((B, nr)) if "r" in want else None
     F = np.zeros(B) if "F" in want else None
@@ -420,8 +424,9 @@ def solve_ik(robot, weights, spheres, kind, targets, cfg: IkConfig, threads=None
     return out
 
 
-def accept(robot, spheres, kind, targets, u, tol=1e-5):
-    """Final acceptance metrics: (pos err m, rot err rad, limits ok, collision-free)."""
+def accept(robot, spheres, kind, targets, u, tol=1e-5, self_contact=False):
+    """Final acceptance metrics: (pos err m, rot err rad, limits ok, collision-free); with
+    self_contact, collision-free also covers the robot's own segments two or more apart."""
     no, sp = _spheres(spheres)
     tg = _f64(targets).reshape(-1, 7)
     u = _f64(u)
@@ -430,7 +435,8 @@ def accept(robot, spheres, kind, targets, u, tol=1e-5):
     lo, co = np.zeros(P, dtype=np.uint8), np.zeros(P, dtype=np.uint8)
     lib().orc_accept(C.byref(robot), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg), _dp(u),
                      C.c_int64(P), C.c_double(tol), _dp(pos), _dp(rot),
-                     lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)))
+                     lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)),
+                     C.c_int(1 if self_contact else 0))
     return pos, rot, lo.astype(bool), co.astype(bool)
 
 
@@ -456,8 +462,9 @@ def _per_problem_spheres(spheres, P):
     return s.shape[1], np.ascontiguousarray(s)
 
 
-def traj_rows(robot, n_spheres, Tn):
-    return lib().orc_traj_rows(C.byref(robot), C.c_int(n_spheres), C.c_int(Tn))
+def traj_rows(robot, n_spheres, Tn, weights=None):
+    w = weights if weights is not None else make_weights(**{f: 0.0 for f, _ in Weights._fields_})
+    return lib().orc_traj_rows(C.byref(robot), C.byref(w), C.c_int(n_spheres), C.c_int(Tn))
 
 
 def traj_eval(robot, weights, spheres, u_start, goal, x, want=("F",), threads=None):
@@ -469,7 +476,7 @@ def traj_eval(robot, weights, spheres, u_start, goal, x, want=("F",), threads=No
     us, gl = _f64(u_start).reshape(P, d), _f64(goal).reshape(P, 7)
     F = np.zeros(P) if "F" in want else None
     g = np.zeros((P, Tm1, d)) if "g" in want else None
-    r = np.zeros((P, traj_rows(robot, no, Tm1 + 1))) if "r" in want else None
+    r = np.zeros((P, traj_rows(robot, no, Tm1 + 1, weights))) if "r" in want else None
     rc = lib().orc_traj_eval(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(us), _dp(gl),
                              C.c_int(Tm1 + 1), _dp(x), C.c_int64(P), _dp(F), _dp(g), _dp(r),
                              C.c_int(_threads(threads)))
@@ -670,8 +677,9 @@ def calib_jacobian(robot, U, Pm, theta):
     return J
 
 
-def path_rows(robot, n_spheres, H):
-    return lib().orc_path_rows(C.byref(robot), C.c_int(n_spheres), C.c_int(H))
+def path_rows(robot, n_spheres, H, weights=None):
+    w = weights if weights is not None else make_weights(**{f: 0.0 for f, _ in Weights._fields_})
+    return lib().orc_path_rows(C.byref(robot), C.byref(w), C.c_int(n_spheres), C.c_int(H))
 
 
 def path_residual(robot, weights, spheres, wp, x, jacobian=False):
@@ -679,7 +687,7 @@ def path_residual(robot, weights, spheres, wp, x, jacobian=False):
     no, sp = _spheres(spheres)
     x = _f64(x)
     H, d = x.shape
-    nr = path_rows(robot, no, H)
+    nr = path_rows(robot, no, H, weights)
     r = np.zeros(nr)
     J = np.zeros((nr, H * d)) if jacobian else None
     lib().orc_path_residual(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(wp)), C.c_int(H),
@@ -688,23 +696,29 @@ def path_residual(robot, weights, spheres, wp, x, jacobian=False):
 
 
 def path_lm(robot, weights, spheres, wp, x0, iters, lambda0=1e-3, history=False):
+    """Joint LM of one path from x0 [H][d]. With history: the iterates and, per iteration, the cost at
+    its start and at its trial point (Fstart, Ftrial)."""
     no, sp = _spheres(spheres)
     x = _f64(x0).copy()
     H, d = x.shape
     lam, nu, F = C.c_double(lambda0), C.c_double(2.0), C.c_double(0)
     hist = np.zeros((iters, H, d)) if history else None
     acc = np.zeros(iters, np.uint8)
+    trace = np.zeros((iters, 2)) if history else None
     lib().orc_path_lm(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(_f64(wp)), C.c_int(H), _dp(x),
                       C.c_int(iters), C.byref(lam), C.byref(nu), C.byref(F), _dp(hist),
-                      acc.ctypes.data_as(C.POINTER(C.c_uint8)))
+                      acc.ctypes.data_as(C.POINTER(C.c_uint8)), _dp(trace))
     out = dict(x=x, lam=lam.value, nu=nu.value, F=F.value, acc=acc)
     if history:
         out["hist"] = hist
+        out["Fstart"], out["Ftrial"] = trace[:, 0].copy(), trace[:, 1].copy()
     return out
 
 
-def solve_path(robot, weights, spheres, wp, ik_cfg: "IkConfig", k_warm, k_joint, threads=None):
-    """Path following for P paths: spheres [P][no][4] or None, wp [P][H][7]."""
+def solve_path(robot, weights, spheres, wp, ik_cfg: "IkConfig", k_warm, k_joint, threads=None, trace=False):
+    """Path following for P paths: spheres [P][no][4] or None, wp [P][H][7]. With trace, also the
+    start and trial costs of every LM iteration (the warm sweep waypoint by waypoint, then the joint
+    stage) [P][(H-1) k_warm + k_joint][2]."""
     wp = _f64(wp)
     P, H, _ = wp.shape
     no, sp = _per_problem_spheres(spheres, P)
@@ -714,8 +728,12 @@ def solve_path(robot, weights, spheres, wp, ik_cfg: "IkConfig", k_warm, k_joint,
     F = np.zeros(P)
     pos, rot = np.zeros((P, H)), np.zeros((P, H))
     lo, co = np.zeros(P, np.uint8), np.zeros(P, np.uint8)
+    TR = np.zeros((P, (H - 1) * k_warm + k_joint, 2)) if trace else None
     lib().orc_solve_path(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), _dp(wp), C.c_int64(P), C.c_int(H),
                          C.byref(ik_cfg.c()), C.c_int(k_warm), C.c_int(k_joint), _dp(X), _dp(F), _dp(pos), _dp(rot),
                          _dp(SX), lo.ctypes.data_as(C.POINTER(C.c_uint8)), co.ctypes.data_as(C.POINTER(C.c_uint8)),
-                         C.c_int(_threads(threads)))
-    return dict(x=X, stage_x=SX, F=F, pos=pos, rot=rot, lim_ok=lo.astype(bool), col_ok=co.astype(bool))
+                         _dp(TR), C.c_int(_threads(threads)))
+    out = dict(x=X, stage_x=SX, F=F, pos=pos, rot=rot, lim_ok=lo.astype(bool), col_ok=co.astype(bool))
+    if trace:
+        out["trace"] = TR
+    return out

@@ -173,7 +173,12 @@ struct OrRobot {
 // of Sec. IV-A, with L free within [lmin, lmax] (extendable segments) and (theta, phi) written in
 // Cartesian form (theta cos phi, theta sin phi): the same configurations, smooth at theta = 0 where
 // phi is undefined. Three variables per segment in both models.
-enum { OR_MODEL_TENDON = 0, OR_MODEL_ARC = 1 };
+// OR_MODEL_COUPLED: coupled tendon routing (model B, Eq. l_eq read literally, reading 23): the tendons
+// that end at segment s run through segments 1..s, and the state holds their actuator displacements
+// q_sj = sum_{i <= s} u_ij; the kinematics take the per-segment displacements u_s = q_s - q_{s-1}
+// (the inverse of the prefix sum); bounds |q_sj| <= umax_s and sum_j q_sj = 0 act on the actuators.
+enum { OR_MODEL_TENDON = 0, OR_MODEL_ARC = 1, OR_MODEL_COUPLED = 2 };
+#define OR_MAXM 16
 
 struct OrWeights {
   double wp, wR;                         // pose residual weights (1/m, 1/rad)
@@ -181,6 +186,8 @@ struct OrWeights {
   double w_s, w_len, rho_v, rho_a;       // path smoothness, path length, tendon vel / acc
   double dt, vmax, amax;                 // time step, tendon speed / acceleration limits
   double delta;                          // safety margin of Eq. ik_coll (m)
+  double rho_s;                          // self-contact rows (reading: pairs of segments two or more
+                                         // apart); 0 leaves them out
 };
 
 enum { OR_IK6 = 0, OR_IK5 = 1 };
@@ -335,6 +342,11 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
       tx = u[3 * i];
       ty = u[3 * i + 1];
       Li = u[3 * i + 2];
+    } else if (rb.model == OR_MODEL_COUPLED) {
+      T ui[OR_MAXM];
+      for (int j = 0; j < rb.m; ++j) ui[j] = i == 0 ? u[j] : u[rb.m * i + j] - u[rb.m * (i - 1) + j];
+      tendon_to_bend(ui, rb.m, P.rc[i], tx, ty);
+      Li = P.L[i];
     } else {
       tendon_to_bend(u + rb.m * i, rb.m, P.rc[i], tx, ty);
       Li = P.L[i];
@@ -459,6 +471,42 @@ static void pose_residual(int kind, const OrWeights& W, const double* tgt, const
 // Constraint rows (Eq. ik_limits, ik_coll; Eq. penalized_form with squared hinges)
 // ---------------------------------------------------------------------------------------------
 
+// Self-contact rows (the robot itself in Eq. ik_coll's minimum distance, Sec. IV-A). Reading:
+// backbone samples a of segment i and b of segment j >= i + 2 (adjacent segments meet at a joint,
+// so their samples near it are always closer than any clearance), row
+// sqrt(rho_s) max(0, 2 r_body + delta - |p_a - p_b|); rows in the order i, sample of i, j, sample of
+// j. bb: the backbone samples [n*nb][3].
+static int self_row_count(const OrRobot& rb) {
+  int c = 0;
+  for (int i = 0; i < rb.n; ++i)
+    for (int j = i + 2; j < rb.n; ++j) c += rb.nb * rb.nb;
+  return c;
+}
+
+template <class T>
+static int self_rows_bb(const OrRobot& rb, const T* bb, double rho_s, double delta, T* r, T* pen) {
+  const double gap = 2.0 * rb.rbody + delta;
+  const T s = T(std::sqrt(rho_s));
+  int k = 0;
+  for (int i = 0; i < rb.n; ++i)
+    for (int ka = 0; ka < rb.nb; ++ka)
+      for (int j = i + 2; j < rb.n; ++j)
+        for (int kb = 0; kb < rb.nb; ++kb) {
+          const T* pa = bb + 3 * (i * rb.nb + ka);
+          const T* pb = bb + 3 * (j * rb.nb + kb);
+          T dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+          T d2 = dx * dx + dy * dy + dz * dz;
+          if (re(d2) < gap * gap) {
+            const T row = s * (T(gap) - Sqrt(d2));
+            r[k++] = row;
+            if (pen) *pen += row * row;
+          } else {
+            r[k++] = T(0.0);
+          }
+        }
+  return k;
+}
+
 // Per-state constraint rows, appended at r; returns the number of rows.
 // OR_MODEL_TENDON:
 //   2d rows  sqrt(rho_b) max(0, u_ij - umax_i), sqrt(rho_b) max(0, -umax_i - u_ij)
@@ -517,14 +565,20 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
       }
     }
   }
+  // self-contact rows (their squares count as collision penalty too)
+  if (W.rho_s > 0.0) k += self_rows_bb(rb, backbone, W.rho_s, W.delta, r + k, &cp);
   if (coll_pen) *coll_pen = cp;
   return k;
 }
 
-static int state_constraint_count(const OrRobot& rb, int no) {
-  if (rb.model == OR_MODEL_ARC) return 3 * rb.n + rb.n * rb.nb * no;
-  return 2 * rb.n * rb.m + 2 * rb.n + rb.n * rb.nb * no;
+static int state_constraint_count(const OrRobot& rb, const OrWeights& W, int no) {
+  const int self = W.rho_s > 0.0 ? self_row_count(rb) : 0;
+  if (rb.model == OR_MODEL_ARC) return 3 * rb.n + rb.n * rb.nb * no + self;
+  return 2 * rb.n * rb.m + 2 * rb.n + rb.n * rb.nb * no + self;
 }
+
+// Backbone samples are needed by the clearance rows and the self-contact rows.
+static bool needs_backbone(const OrWeights& W, int no) { return no > 0 || W.rho_s > 0.0; }
 
 // Full IK residual of one seed: 6 pose rows followed by the constraint rows.
 template <class T>
@@ -532,14 +586,15 @@ static int ik_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W
                        const double* spheres, int kind, const double* tgt, const T* u, T* r,
                        T* coll_pen) {
   FkOut<T> fk;
-  std::vector<T> bb(no > 0 ? 3 * rb.n * rb.nb : 0);
-  forward_kinematics(rb, P, u, fk, no > 0 ? bb.data() : nullptr);
+  const bool nbb = needs_backbone(W, no);
+  std::vector<T> bb(nbb ? 3 * rb.n * rb.nb : 0);
+  forward_kinematics(rb, P, u, fk, nbb ? bb.data() : nullptr);
   pose_residual(kind, W, tgt, fk.R, fk.p, r);
-  return 6 + state_constraint_rows(rb, W, no, spheres, u, fk, no > 0 ? bb.data() : nullptr, r + 6,
+  return 6 + state_constraint_rows(rb, W, no, spheres, u, fk, nbb ? bb.data() : nullptr, r + 6,
                                    coll_pen);
 }
 
-static int ik_rows(const OrRobot& rb, int no) { return 6 + state_constraint_count(rb, no); }
+static int ik_rows(const OrRobot& rb, const OrWeights& W, int no) { return 6 + state_constraint_count(rb, W, no); }
 
 template <class T> static T half_sq(const T* r, int m) {
   T s(0.0);
@@ -822,7 +877,7 @@ struct IkProblem {
   int kind;
   const double* tgt;
   int d() const { return rb->n * rb->m; }
-  int rows() const { return ik_rows(*rb, no); }
+  int rows() const { return ik_rows(*rb, *W, no); }
   void res(const double* u, double* r) const {
     Params<double> P = params_of<double>(*rb);
     ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r, (double*)nullptr);
@@ -1002,7 +1057,7 @@ int orc_quat_to_R(const double* q, int64_t B, double* R /*[B][9]*/) {
   return 0;
 }
 
-int orc_ik_rows(const OrRobot* rb, int no) { return ik_rows(*rb, no); }
+int orc_ik_rows(const OrRobot* rb, const OrWeights* W, int no) { return ik_rows(*rb, *W, no); }
 
 // IK residuals r[B][rows], cost F[B], collision part of the cost coll[B] (nullable), gradient
 // g[B][d] (nullable) and residual Jacobian J[B][rows][d] (nullable). Target of seed b is
@@ -1039,7 +1094,7 @@ int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const doubl
       Params<cd> P = params_of<cd>(*rb);
       if (q < rb->n) P.L[q] += cd(0.0, CS_H);
       else P.rc[q - rb->n] += cd(0.0, CS_H);
-      int nr = ik_rows(*rb, no);
+      int nr = ik_rows(*rb, *W, no);
       std::vector<cd> x(d), r(nr);
       for (int a = 0; a < d; ++a) x[a] = cd(u[d * b + a], 0.0);
       ik_residual(*rb, P, *W, no, spheres, kind, targets + 7 * (b / S), x.data(), r.data(), (cd*)nullptr);
@@ -1323,9 +1378,11 @@ int orc_topk(const float* cost, const float* coll, const double* u /*[S][d]*/, i
 // angle between tip axes for IK5), limits (|u| <= umax + tol, |sum u| <= tol, or for OR_MODEL_ARC
 // lmin - tol <= L <= lmax + tol; theta <= thmax + tol)
 // and collision-free (every sample at least r_s + r_body from every sphere centre).
+// With self_check, collision-free also requires every pair of samples of segments two or more
+// apart to be at least 2 r_body apart (the self-contact rows' reading, without the margin delta).
 static void accept_one(const OrRobot& rb, int no, const double* spheres, int kind,
                        const double* tgt, const double* u, double tol, double* pos, double* rot,
-                       uint8_t* lim_ok, uint8_t* col_ok) {
+                       uint8_t* lim_ok, uint8_t* col_ok, bool self_check = false) {
   Params<double> Pd = params_of<double>(rb);
   FkOut<double> o;
   std::vector<double> bb(3 * rb.n * rb.nb);
@@ -1371,6 +1428,18 @@ static void accept_one(const OrRobot& rb, int no, const double* spheres, int kin
       double reach = sp[3] + rb.rbody;
       if (dx * dx + dy * dy + dz * dz < reach * reach) free = false;
     }
+  if (self_check) {
+    const double g2 = 4.0 * rb.rbody * rb.rbody;
+    for (int i = 0; i < rb.n && free; ++i)
+      for (int j = i + 2; j < rb.n && free; ++j)
+        for (int ka = 0; ka < rb.nb && free; ++ka)
+          for (int kb = 0; kb < rb.nb && free; ++kb) {
+            const double* pa = &bb[3 * (i * rb.nb + ka)];
+            const double* pb = &bb[3 * (j * rb.nb + kb)];
+            const double dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+            if (dx * dx + dy * dy + dz * dz < g2) free = false;
+          }
+  }
   *col_ok = free;
 }
 
@@ -1439,7 +1508,7 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
     std::memcpy(uo, X.data() + (size_t)best * d, sizeof(double) * d);
     F_out[q] = bestF;
     uint8_t lim_ok, col_ok;
-    accept_one(*rb, no, spheres, kind, tgt, uo, prm->lim_tol, &pos[q], &rot[q], &lim_ok, &col_ok);
+    accept_one(*rb, no, spheres, kind, tgt, uo, prm->lim_tol, &pos[q], &rot[q], &lim_ok, &col_ok, W->rho_s > 0.0);
     success[q] = (pos[q] <= prm->pos_tol && rot[q] <= prm->rot_tol && lim_ok && col_ok) ? 1 : 0;
   });
   return 0;
@@ -1447,11 +1516,11 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
 
 int orc_accept(const OrRobot* rb, int no, const double* spheres, int kind, const double* targets,
                const double* u, int64_t P, double tol, double* pos, double* rot, uint8_t* lim_ok,
-               uint8_t* col_ok) {
+               uint8_t* col_ok, int self_check) {
   int d = rb->n * rb->m;
   for (int64_t q = 0; q < P; ++q)
     accept_one(*rb, no, spheres, kind, targets + 7 * q, u + (size_t)d * q, tol, pos + q, rot + q,
-               lim_ok + q, col_ok + q);
+               lim_ok + q, col_ok + q, self_check != 0);
   return 0;
 }
 
@@ -1469,7 +1538,7 @@ int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const dou
   g_tally = {0, 0, 0, 0};
   Params<Cnt> P;
   for (int i = 0; i < rb->n; ++i) { P.L[i] = Cnt(rb->L[i]); P.rc[i] = Cnt(rb->rc[i]); }
-  std::vector<Cnt> x(d), r(ik_rows(*rb, no));
+  std::vector<Cnt> x(d), r(ik_rows(*rb, *W, no));
   for (int a = 0; a < d; ++a) x[a] = Cnt(u[a], true);
   const int rows = ik_residual(*rb, P, *W, no, spheres, kind, target, x.data(), r.data(), (Cnt*)nullptr);
   Cnt F = half_sq(r.data(), rows);
@@ -1520,13 +1589,14 @@ static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights&
                          const T* x, T* r) {
   const int d = rb.n * rb.m;
   const int nbp = 3 * rb.n * rb.nb;
-  std::vector<T> U((size_t)Tn * d), bb(no > 0 ? (size_t)Tn * nbp : 0);
+  const bool nbb = needs_backbone(W, no);
+  std::vector<T> U((size_t)Tn * d), bb(nbb ? (size_t)Tn * nbp : 0);
   for (int a = 0; a < d; ++a) U[a] = T(u_start[a]);
   for (int t = 1; t < Tn; ++t)
     for (int a = 0; a < d; ++a) U[(size_t)t * d + a] = x[(size_t)(t - 1) * d + a];
   std::vector<FkOut<T>> fk(Tn);
   for (int t = 0; t < Tn; ++t)
-    forward_kinematics(rb, P, &U[(size_t)t * d], fk[t], no > 0 ? &bb[(size_t)t * nbp] : nullptr);
+    forward_kinematics(rb, P, &U[(size_t)t * d], fk[t], nbb ? &bb[(size_t)t * nbp] : nullptr);
   T sl = T(std::sqrt(W.w_len)), sv = T(std::sqrt(W.rho_v)), sa = T(std::sqrt(W.rho_a));
   int k = 0;
   for (int t = 1; t < Tn; ++t) {
@@ -1537,7 +1607,7 @@ static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights&
       r[k++] = sv * hinge(T(-W.vmax) - v);
     }
     k += state_constraint_rows(rb, W, no, spheres, &U[(size_t)t * d], fk[t],
-                               no > 0 ? &bb[(size_t)t * nbp] : (const T*)nullptr, r + k, (T*)nullptr);
+                               nbb ? &bb[(size_t)t * nbp] : (const T*)nullptr, r + k, (T*)nullptr);
     if (t >= 2) {
       for (int q = 0; q < d; ++q) {
         T acc = (U[(size_t)t * d + q] - T(2.0) * U[(size_t)(t - 1) * d + q] + U[(size_t)(t - 2) * d + q]) /
@@ -1552,9 +1622,9 @@ static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights&
   return k;
 }
 
-static int traj_rows(const OrRobot& rb, int no, int Tn) {
+static int traj_rows(const OrRobot& rb, const OrWeights& W, int no, int Tn) {
   const int d = rb.n * rb.m;
-  return (Tn - 1) * (3 + 2 * d + state_constraint_count(rb, no)) + std::max(0, Tn - 2) * 2 * d + 6;
+  return (Tn - 1) * (3 + 2 * d + state_constraint_count(rb, W, no)) + std::max(0, Tn - 2) * 2 * d + 6;
 }
 
 struct TrajProblem {
@@ -1566,7 +1636,7 @@ struct TrajProblem {
   const double* goal;
   int Tn;
   int nx() const { return (Tn - 1) * rb->n * rb->m; }
-  int rows() const { return traj_rows(*rb, no, Tn); }
+  int rows() const { return traj_rows(*rb, *W, no, Tn); }
   double cost(const double* x) const {
     std::vector<double> r(rows());
     Params<double> P = params_of<double>(*rb);
@@ -1621,8 +1691,8 @@ static int path_residual(const OrRobot& rb, const Params<T>& P, const OrWeights&
   return k;
 }
 
-static int path_rows(const OrRobot& rb, int no, int H) {
-  return H * ik_rows(rb, no) + (H - 1) * rb.n * rb.m;
+static int path_rows(const OrRobot& rb, const OrWeights& W, int no, int H) {
+  return H * ik_rows(rb, W, no) + (H - 1) * rb.n * rb.m;
 }
 
 struct PathProblem {
@@ -1635,7 +1705,7 @@ struct PathProblem {
   int d() const { return rb->n * rb->m; }
   int nx() const { return H * d(); }
   double cost(const double* x) const {
-    std::vector<double> r(path_rows(*rb, no, H));
+    std::vector<double> r(path_rows(*rb, *W, no, H));
     Params<double> P = params_of<double>(*rb);
     path_residual(*rb, P, *W, no, spheres, wp, H, x, r.data());
     return half_sq(r.data(), (int)r.size());
@@ -1701,7 +1771,7 @@ static void calib_residual(const OrRobot& rb, const double* U, const double* Pm,
 
 extern "C" {
 
-int orc_traj_rows(const OrRobot* rb, int no, int Tn) { return traj_rows(*rb, no, Tn); }
+int orc_traj_rows(const OrRobot* rb, const OrWeights* W, int no, int Tn) { return traj_rows(*rb, *W, no, Tn); }
 
 // Trajectory cost / gradient / residuals of P problems. u_start [P][d], goal [P][7], spheres
 // [P][no][4] (per problem), x [P][(Tn-1)][d] (the free states u_1..u_{Tn-1}).
@@ -1748,14 +1818,14 @@ static void traj_refine_one(const OrRobot* rb, const OrWeights* W, int no, const
   traj_pg(tp, X + d, k_traj, alpha0, F);
   double pos, rot;
   uint8_t lo, co;
-  accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)(Tn - 1) * d, lim_tol, &pos, &rot, &lo, &co);
+  accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)(Tn - 1) * d, lim_tol, &pos, &rot, &lo, &co, W->rho_s > 0.0);
   *goal_pos = pos;
   *goal_rot = rot;
   bool lim = true, col = true;
   for (int t = 0; t < Tn; ++t) {
     double p2, r2;
     uint8_t l2, c2;
-    accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)t * d, lim_tol, &p2, &r2, &l2, &c2);
+    accept_one(*rb, no, sp, OR_IK6, goal, X + (size_t)t * d, lim_tol, &p2, &r2, &l2, &c2, W->rho_s > 0.0);
     lim = lim && l2;
     col = col && c2;
   }
@@ -1841,7 +1911,7 @@ int orc_calib_jacobian(const OrRobot* rb, const double* U, const double* Pm, int
   return 0;
 }
 
-int orc_path_rows(const OrRobot* rb, int no, int H) { return path_rows(*rb, no, H); }
+int orc_path_rows(const OrRobot* rb, const OrWeights* W, int no, int H) { return path_rows(*rb, *W, no, H); }
 
 // Path residual r [rows] of one path (spheres [no][4], waypoints wp [H][7], x [H][d]); and its full
 // Jacobian J [rows][H d] by complex step over all H d variables (small H; pins the blockwise
@@ -1851,7 +1921,7 @@ int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const doubl
   Params<double> Pd = params_of<double>(*rb);
   path_residual(*rb, Pd, *W, no, spheres, wp, H, x, r);
   if (J) {
-    const int n = H * rb->n * rb->m, nr = path_rows(*rb, no, H);
+    const int n = H * rb->n * rb->m, nr = path_rows(*rb, *W, no, H);
     cs_jacobian([&](const cd* xx, cd* rr) {
       Params<cd> P = params_of<cd>(*rb);
       path_residual(*rb, P, *W, no, spheres, wp, H, xx, rr);
@@ -1861,8 +1931,10 @@ int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const doubl
 }
 
 // Joint LM on one path: x [H][d] in/out, iters iterations; hist [iters][H][d] nullable.
+// trace [iters][2] (nullable): the cost at each iteration's start and at its trial point.
 int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp, int H,
-                double* x, int iters, double* lam, double* nu, double* F_out, double* hist, uint8_t* acc) {
+                double* x, int iters, double* lam, double* nu, double* F_out, double* hist, uint8_t* acc,
+                double* trace) {
   PathProblem pp{rb, W, no, spheres, wp, H};
   LmState st{*lam, *nu, 0.0};
   const int n = pp.nx();
@@ -1871,6 +1943,7 @@ int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* sph
                             [&](const double* xx) { return pp.cost(xx); }, n, x, st);
     if (acc) acc[it] = (uint8_t)a;
     if (hist) std::memcpy(hist + (size_t)it * n, x, sizeof(double) * n);
+    if (trace) { trace[2 * it] = st.Fstart; trace[2 * it + 1] = st.Ftrial; }
   }
   *lam = st.lambda;
   *nu = st.nu;
@@ -1882,16 +1955,19 @@ int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* sph
 // for t >= 1 k_warm LM iterations of the waypoint's IK residual from u*_{t-1}, then k_joint joint
 // LM iterations over the whole path (lambda0 = ik_prm->lambda0). spheres [P][no][4], wp [P][H][7].
 // Outputs x_out [P][H][d], F_out [P] (joint cost), pos / rot [P][H] (per-waypoint errors),
-// stage_x [P][H][d] (nullable: the trajectory before the joint stage), lim_ok / col_ok [P].
+// stage_x [P][H][d] (nullable: the trajectory before the joint stage), lim_ok / col_ok [P];
+// trace [P][(H-1) k_warm + k_joint][2] (nullable): start and trial costs of every LM iteration of the
+// warm sweep (waypoint by waypoint) and then of the joint stage.
 int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp,
                    int64_t P, int H, const OrIkParams* ik_prm, int k_warm, int k_joint, double* x_out,
                    double* F_out, double* pos, double* rot, double* stage_x, uint8_t* lim_ok, uint8_t* col_ok,
-                   int threads) {
+                   double* trace, int threads) {
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
     const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
     const double* wq = wp + (size_t)7 * H * q;
     double* X = x_out + (size_t)H * d * q;
+    double* tr = trace ? trace + 2 * ((size_t)(H - 1) * k_warm + k_joint) * q : nullptr;
     OrIkParams prm = *ik_prm;
     prm.p0 = ik_prm->p0 + q;
     double Fg, pe, re;
@@ -1902,18 +1978,21 @@ int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* 
       std::memcpy(xt, X + (size_t)(t - 1) * d, sizeof(double) * d);
       IkProblem pb{rb, W, no, sp, OR_IK6, wq + 7 * t};
       LmState st{ik_prm->lambda0, 2.0, 0.0};
-      for (int it = 0; it < k_warm; ++it)
+      for (int it = 0; it < k_warm; ++it) {
         lm_iteration([&pb](const double* xx, double* rr) { pb.res(xx, rr); },
                      [&pb](const cd* xx, cd* rr) { pb.cres(xx, rr); }, d, pb.rows(), xt, st);
+        if (tr) { tr[2 * ((t - 1) * k_warm + it)] = st.Fstart; tr[2 * ((t - 1) * k_warm + it) + 1] = st.Ftrial; }
+      }
     }
     if (stage_x) std::memcpy(stage_x + (size_t)H * d * q, X, sizeof(double) * H * d);
     double lam = ik_prm->lambda0, nu = 2.0;
-    orc_path_lm(rb, W, no, sp, wq, H, X, k_joint, &lam, &nu, &F_out[q], nullptr, nullptr);
+    orc_path_lm(rb, W, no, sp, wq, H, X, k_joint, &lam, &nu, &F_out[q], nullptr, nullptr,
+                tr ? tr + 2 * (size_t)(H - 1) * k_warm : nullptr);
     bool lim = true, col = true;
     for (int t = 0; t < H; ++t) {
       uint8_t lo, co;
       accept_one(*rb, no, sp, OR_IK6, wq + 7 * t, X + (size_t)t * d, ik_prm->lim_tol, &pos[(size_t)H * q + t],
-                 &rot[(size_t)H * q + t], &lo, &co);
+                 &rot[(size_t)H * q + t], &lo, &co, W->rho_s > 0.0);
       lim = lim && lo;
       col = col && co;
     }
@@ -2152,38 +2231,14 @@ int orc_prm_query(const OrRobot* rb, double delta, int no, const double* spheres
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------------
-// Self-contact rows (the robot itself in Eq. ik_coll's minimum distance, Sec. IV-A), defined here
-// ahead of any residual that uses them. Reading: backbone samples a of segment i and b of segment
-// j >= i + 2 (adjacent segments meet at a joint, so their samples near it are always closer than any
-// clearance), row sqrt(rho_s) max(0, 2 r_body + delta - |p_a - p_b|); rows in the order i, sample of
-// i, j, sample of j. F = 1/2 sum r^2.
+// Self-contact rows on their own (the rows of self_rows_bb above, from the state's backbone).
 // ---------------------------------------------------------------------------------------------
-static int self_row_count(const OrRobot& rb) {
-  int c = 0;
-  for (int i = 0; i < rb.n; ++i)
-    for (int j = i + 2; j < rb.n; ++j) c += rb.nb * rb.nb;
-  return c;
-}
-
 template <class T>
 static int self_rows(const OrRobot& rb, const Params<T>& P, const T* u, double rho_s, double delta, T* r) {
   FkOut<T> fk;
   std::vector<T> bb(3 * rb.n * rb.nb);
   forward_kinematics(rb, P, u, fk, bb.data());
-  const double gap = 2.0 * rb.rbody + delta;
-  const T s = T(std::sqrt(rho_s));
-  int k = 0;
-  for (int i = 0; i < rb.n; ++i)
-    for (int ka = 0; ka < rb.nb; ++ka)
-      for (int j = i + 2; j < rb.n; ++j)
-        for (int kb = 0; kb < rb.nb; ++kb) {
-          const T* pa = bb.data() + 3 * (i * rb.nb + ka);
-          const T* pb = bb.data() + 3 * (j * rb.nb + kb);
-          T dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
-          T d2 = dx * dx + dy * dy + dz * dz;
-          r[k++] = re(d2) < gap * gap ? s * (T(gap) - Sqrt(d2)) : T(0.0);
-        }
-  return k;
+  return self_rows_bb(rb, bb.data(), rho_s, delta, r, (T*)nullptr);
 }
 
 extern "C" {

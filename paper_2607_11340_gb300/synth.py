@@ -36,6 +36,7 @@ class RobotSpec:
     rbody: float | None = None  # backbone radius for clearance (defaults to rc)
     lmin: float | None = None   # arc model (the paper's (theta, phi, L) per segment): length bounds
     lmax: float | None = None
+    coupled: bool = False       # coupled routing (model B): the state holds the actuator displacements
 
     @property
     def is_arc(self) -> bool:
@@ -70,6 +71,7 @@ class WeightSpec:
     vmax: float = 0.05
     amax: float = 0.5
     delta: float = 1e-3
+    rho_s: float = 0.0      # self-contact rows (segments two or more apart); 0 leaves them out
 
     def as_dict(self) -> dict:
         return dataclasses.asdict(self)
@@ -437,3 +439,41 @@ def e2_workload(spec: RobotSpec, P: int, fk_backbone, seed: int = 0, weights: We
     q = np.concatenate(got_q)[:P]
     return pose_targets(T, "pose"), q, sph
 
+
+
+# Self-contact IK (Eq. ik_coll over the robot itself): a 4-segment robot that can curl into a loop
+# (up to 2 rad per segment), 1024 full-pose targets, half of them the poses of curled states whose
+# segments two or more apart intersect (the solver must find another, contact-free configuration),
+# half FK of hexagon-uniform states; self-contact rows weighted rho_s = 1e4.
+ROBOT_SELF = RobotSpec(L=(0.10,) * 4, rc=0.005, umax=0.010, nb=8)
+IK_SELF = IkSpec(S=128, n_final=8, k_init=32, k_final=30)
+P_SELF = 1024
+WEIGHTS_SELF = dataclasses.replace(WEIGHTS, rho_s=1e4)
+
+
+def curled_states(rng: np.random.Generator, B: int, spec: RobotSpec) -> np.ndarray:
+    """[B][3n] states bent in nearly one plane by 1.6-2.0 rad per segment (within the bounds at any
+    azimuth; an azimuth drift of N(0, 0.08) rad per segment), so that the robot curls into a loop whose
+    ends meet: the tendon displacements of
+    Eq. 4, u_j = -r_c theta cos(alpha_j - phi), plus N(0, 0.2 mm) noise, re-centred to sum zero and
+    clipped to the bounds."""
+    n = spec.n
+    u = np.zeros((B, 3 * n))
+    alpha = np.array([0.0, 2 * np.pi / 3, 4 * np.pi / 3])
+    for b in range(B):
+        phi0 = rng.uniform(0, 2 * np.pi)
+        for i in range(n):
+            th = rng.uniform(1.6, 2.0)
+            phi = phi0 + rng.normal(0, 0.08)
+            u[b, 3 * i:3 * i + 3] = -spec.rc * th * np.cos(alpha - phi)
+    u += rng.normal(0, 2e-4, u.shape)
+    u -= u.reshape(B, n, 3).mean(axis=2).repeat(3, axis=1)
+    return np.clip(u, -spec.umax, spec.umax)
+
+
+def self_contact_workload(spec: RobotSpec, P: int, fk, seed: int = 0):
+    """Targets [P][7]: the first half FK of curled states, the rest FK of hexagon-uniform states;
+    returns (targets, states)."""
+    rng = np.random.default_rng(seed)
+    u = np.concatenate([curled_states(rng, P // 2, spec), hexagon_states(rng, P - P // 2, spec.n, spec.umax)])
+    return pose_targets(fk(u), "pose"), u

@@ -71,3 +71,46 @@ def test_actuator_gradient_is_the_transposed_difference_map(orc):
     h = 1e-7
     fd = np.stack([(F_B(q + h * e) - F_B(q - h * e)) / (2 * h) for e in np.eye(q.shape[1])], axis=1)
     np.testing.assert_allclose(g_q, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+
+
+def test_coupled_model_state_is_the_actuator_displacement(orc):
+    """The coupled model (model B) takes the actuator displacements q as its state: its kinematics,
+    cost and gradient equal the per-segment model's at u = the inverse prefix sum of q; its gradient is
+    D^T of the per-segment gradient (g_q,s = g_u,s - g_u,s+1), its Jacobian J_u D; bounds act on q."""
+    from paper_2607_11340_gb300 import synth
+
+    spec = synth.ROBOT_3SEG
+    rbA = orc.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
+    rbB = orc.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb, coupled=True)
+    W = orc.make_weights(**synth.WEIGHTS.as_dict())
+    rng = np.random.default_rng(41)
+    q = synth.hexagon_states(rng, 12, 3, spec.umax)  # in the actuator bounds (and so sum-zero)
+    u = orc.routing_a_from_b(rbA, q)
+    TA, bbA = orc.fk(rbA, u, backbone=True)
+    TB, bbB = orc.fk(rbB, q, backbone=True)
+    np.testing.assert_array_equal(TA, TB)
+    np.testing.assert_array_equal(bbA, bbB)
+    tg = synth.pose_targets(orc.fk(rbA, synth.hexagon_states(rng, 12, 3, spec.umax))[0], "pose")
+    eA = orc.ik_eval(rbA, W, None, 0, tg, 1, u, want=("g", "J"))
+    eB = orc.ik_eval(rbB, W, None, 0, tg, 1, q, want=("F", "g", "J"))
+    # pose rows: J_q = J_u D with D the prefix-sum inverse: column s of J_q = col s - col s+1 of J_u
+    JA = eA["J"][:, :6, :]
+    Jq = JA.copy()
+    Jq[:, :, :6] -= JA[:, :, 3:]
+    np.testing.assert_allclose(eB["J"][:, :6, :], Jq, rtol=1e-12, atol=1e-12 * np.abs(JA).max())
+    # q inside its bounds and sum-zero: model B's bound and sum-zero rows vanish (u = D q itself may
+    # leave the per-segment bounds, whose rows model A would add), so g_q = D^T (J_u^T r) over the rows
+    # that are functions of the kinematics: the pose rows and the curvature rows (theta of u = D q may
+    # pass theta_max). Model A's rows: 6 pose, 2d bound, n sum-zero, n curvature.
+    rA = orc.ik_eval(rbA, W, None, 0, tg, 1, u, want=("r",))["r"]
+    JAall = eA["J"]
+    kin = np.r_[0:6, 6 + 18 + 3:6 + 18 + 3 + 3]
+    gu_kin = np.einsum("bkq,bk->bq", JAall[:, kin, :], rA[:, kin])
+    gq = gu_kin.copy()
+    gq[:, :6] -= gu_kin[:, 3:]
+    np.testing.assert_allclose(eB["g"], gq, rtol=1e-10, atol=1e-12 * np.abs(gq).max())
+    # the bound rows act on q: a q beyond the bound is penalised even where u is inside
+    q2 = q[:1].copy()
+    q2[0, 3:6] = [spec.umax * 1.2, -spec.umax * 0.6, -spec.umax * 0.6]
+    r2 = orc.ik_eval(rbB, W, None, 0, tg[:1], 1, q2, want=("r",))["r"][0]
+    assert np.any(r2[6:6 + 18] > 0)
