@@ -304,6 +304,14 @@ def opcount_lm_update(nx):
     return int(out[0]), int(out[1])
 
 
+def opcount_pg_step(nx):
+    """(flops, special calls) of the step of one projected-gradient iteration on nx unknowns: the
+    gradient norm, the step length and the move (no projection, no cost evaluation)."""
+    out = (C.c_longlong * 2)()
+    lib().orc_opcount_pg_step(C.c_int(nx), out)
+    return int(out[0]), int(out[1])
+
+
 def opcount_probe(which):
     """Op counts (fwd flop, fwd sfu, tangent flop, tangent sfu) of a small hand-countable program."""
     out = (C.c_longlong * 4)()
@@ -668,6 +676,14 @@ def calibrate(robot, U, Pm, theta0, iters, lambda0=1e-3, history=False):
     if history:
         out["hist"] = hist
     return out
+
+
+def calib_residual(robot, U, Pm, theta):
+    """The calibration residual [3K] (tip position minus measurement per pose) at theta."""
+    U, Pm = _f64(U), _f64(Pm)
+    r = np.zeros(3 * U.shape[0])
+    lib().orc_calib_residual(C.byref(robot), _dp(U), _dp(Pm), C.c_int(U.shape[0]), _dp(_f64(theta)), _dp(r))
+    return r
 
 
 def calib_jacobian(robot, U, Pm, theta):

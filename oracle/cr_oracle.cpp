@@ -361,6 +361,10 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
         segment_transform(sg * tx, sg * ty, sg * Li, Rs, ds);
         T* q = backbone + 3 * (i * rb.nb + (k - 1));
         for (int a = 0; a < 3; ++a) {
+          if (i == 0) {  // the base frame is the identity at the origin
+            q[a] = ds[a];
+            continue;
+          }
           T s = p[a];
           for (int b = 0; b < 3; ++b) s += R[a][b] * ds[b];
           q[a] = s;
@@ -369,6 +373,13 @@ static void forward_kinematics(const OrRobot& rb, const Params<T>& P, const T* u
     }
     T Ri[3][3], di[3];
     segment_transform(tx, ty, Li, Ri, di);
+    if (i == 0) {  // T_0 itself: composing with the identity base frame changes no value
+      for (int a = 0; a < 3; ++a) {
+        p[a] = di[a];
+        for (int b = 0; b < 3; ++b) R[a][b] = Ri[a][b];
+      }
+      continue;
+    }
     T pn[3], Rn[3][3];
     for (int a = 0; a < 3; ++a) {
       T s = p[a];
@@ -916,6 +927,16 @@ struct IkProblem {
 // A fixed number of steps. Stage one of Algorithm 1 (per seed) and the trajectory refinement (all
 // free states at once, the norm over all of them) both run this one routine. hist (nullable)
 // receives, after every step, x, then alpha, F and the trial's cost F(x'): [steps][nx + 3].
+// The step of the rule before the projection: v = x - alpha g / |g| (v = x when g = 0). A template so
+// that the op-counting scalar counts this very code.
+template <class T> static void pg_direction(int nx, const T* x, const T* g, T alpha, T* v) {
+  T gn = T(0);
+  for (int a = 0; a < nx; ++a) gn += g[a] * g[a];
+  gn = Sqrt(gn);
+  const T scale = re(gn) > 0 ? alpha / gn : T(0);
+  for (int a = 0; a < nx; ++a) v[a] = x[a] - scale * g[a];
+}
+
 static void pg_rule(int nx, double* x, int steps, double alpha0, const std::function<double(const double*)>& cost,
                     const std::function<void(const double*, double*)>& grad,
                     const std::function<void(const double*, double*)>& project, double* F_out, double* hist) {
@@ -924,11 +945,7 @@ static void pg_rule(int nx, double* x, int steps, double alpha0, const std::func
   grad(x, g.data());
   double alpha = alpha0;
   for (int it = 0; it < steps; ++it) {
-    double gn = 0;
-    for (int a = 0; a < nx; ++a) gn += g[a] * g[a];
-    gn = std::sqrt(gn);
-    double scale = gn > 0 ? alpha / gn : 0.0;
-    for (int a = 0; a < nx; ++a) v[a] = x[a] - scale * g[a];
+    pg_direction<double>(nx, x, g.data(), alpha, v.data());
     project(v.data(), x1.data());
     const double F1 = cost(x1.data());
     if (F1 < F) {
@@ -1211,6 +1228,19 @@ int orc_lm_scalar(double a, double x0, int iters, double lambda0, double* x_hist
 //   which 2: y = sum_{k<5} a_k x_k, a linear function with constant a_k;
 //   which 3: one segment of Eq. 2-3 in the minimal (Rodrigues) form, (tx, ty) the input, L constant;
 //   which 4: y = sin(x) cos(x) / sqrt(x).
+// Op count of the step of one projected-gradient iteration (pg_direction: the gradient norm, the
+// step length and the move) on nx unknowns, without the projection (comparisons and clamps) and the
+// cost evaluation (forward flops and special calls in out[0..1]).
+int orc_opcount_pg_step(int nx, long long* out) {
+  g_tally = {0, 0, 0, 0};
+  std::vector<Cnt> x(nx), g(nx), v(nx);
+  for (int a = 0; a < nx; ++a) { x[a] = Cnt(1e-3 * (a + 1)); g[a] = Cnt(0.5 - 0.1 * a); }
+  pg_direction<Cnt>(nx, x.data(), g.data(), Cnt(1e-3), v.data());
+  out[0] = g_tally.f_flop;
+  out[1] = g_tally.f_sfu;
+  return 0;
+}
+
 // Op count of steps 2-5 of one LM iteration (lm_update) on nx unknowns, without the cost
 // evaluations: damping of the diagonal, Cholesky, the two triangular solves, the predicted
 // decrease, the gain ratio and the damping update (forward flops and special calls in out[0..1]).
@@ -1901,6 +1931,12 @@ int orc_calibrate(const OrRobot* rb, const double* U, const double* Pm, int K, d
   std::vector<double> r(nr);
   fr(theta, r.data());
   *F_out = half_sq(r.data(), nr);
+  return 0;
+}
+
+// The calibration residual r [3K] at theta (pose k's tip position minus its measurement).
+int orc_calib_residual(const OrRobot* rb, const double* U, const double* Pm, int K, const double* theta, double* r) {
+  calib_residual(*rb, U, Pm, K, theta, r);
   return 0;
 }
 

@@ -3,8 +3,9 @@ benchmark workload, counted by the oracle's op-counting scalar on the minimal (R
 Eq. 2-3. "fwd" = cost (kinematics, pose log, penalty rows); "tan" = the linearised program whose
 transpose is the adjoint (same multiply-add count), so one value-and-gradient evaluation costs
 fwd + tan. "trial_*" counts leave out the rows that vanish at the projected trial points of stage
-one (tendon model: bound and sum-zero rows; arc model: length and curvature rows). Calls only
-oracle/."""
+one (tendon model: bound and sum-zero rows; arc model: length and curvature rows). "pg_step_*" is
+the step rule's own arithmetic per trial point (gradient norm, step length and move, without the
+projection). Calls only oracle/."""
 import json
 import os
 import sys
@@ -39,6 +40,9 @@ def counts(spec, kind, n_states=64):
     m = c.mean(axis=0)
     out.update({"trial_fwd_flop": float(m[0]), "trial_fwd_sfu": float(m[1]), "trial_tan_flop": float(m[2]),
                 "trial_tan_sfu": float(m[3])})
+    # the step rule's own arithmetic per trial (gradient norm, step length, move; not the projection)
+    f, sf = O.opcount_pg_step(u.shape[1])
+    out.update({"pg_step_flop": float(f), "pg_step_sfu": float(sf)})
     return out
 
 

@@ -21,7 +21,7 @@ SRC = os.path.join(ROOT, "oracle", "cr_oracle.cpp")
 MUTANTS = [
     ("pg_growth_x2", "      alpha *= 1.25;", "      alpha *= 2.0;", "pin_pg_interior"),
     ("pg_stale_gradient", "{ x[a] = x1[a]; g[a] = g1[a]; }", "{ x[a] = x1[a]; }", "pin_pg_projected"),
-    ("pg_unnormalised_step", "double scale = gn > 0 ? alpha / gn : 0.0;", "double scale = alpha;",
+    ("pg_unnormalised_step", "const T scale = re(gn) > 0 ? alpha / gn : T(0);", "const T scale = alpha;",
      "pin_pg_interior"),
     ("pg_shrink_quarter", "    } else {\n      alpha *= 0.5;", "    } else {\n      alpha *= 0.25;",
      "pin_pg_stall_at_vertex"),

@@ -229,15 +229,14 @@ def pin_opcount_ik_one_segment(orc):
         k = (-2/m) / r_c (1, constant), tx = k sx, ty = k sy (2; tangent 2): 15 flops, tangent 12;
       theta^2 for the output: 3, tangent 7;
       segment transform (probe 3): 30 + 3 special, tangent 71 + 2;
-      chain from the identity: p = 0 + R d (9 mult + 9 add, R constant; tangent 9 + 6) = 18 / 15;
-        R Ri with R constant = 45 / 45;
+      the tip frame is the segment's own (T_0 is not composed with the identity base frame): 0;
       pose rows: 6 x (difference with a constant target, times a weight) = 12, tangent 6;
       bound rows: 6 x (difference, weight times an exact 0) = 12, tangent 0;
       sum-zero row: 3 adds + weight = 4, tangent 3; curvature row inactive: 0;
       F = 1/2 sum of 14 squared rows: 14 mult + 14 add + 1 = 29; tangent: 7 dependent rows x 3
         + 6 dependent adds + 1 = 28.
-    Forward 15 + 3 + 30 + 18 + 45 + 12 + 12 + 4 + 29 = 168 flops and 3 special calls; tangent
-    12 + 7 + 71 + 15 + 45 + 6 + 0 + 3 + 28 = 187 flops and 2 special calls. The benchmark's
+    Forward 15 + 3 + 30 + 12 + 12 + 4 + 29 = 105 flops and 3 special calls; tangent
+    12 + 7 + 71 + 6 + 0 + 3 + 28 = 127 flops and 2 special calls. The benchmark's
     1-segment denominator (tests/golden/opcounts.json, ik_1seg_axis) is this count."""
     from paper_2607_11340_gb300 import synth
 
@@ -245,11 +244,11 @@ def pin_opcount_ik_one_segment(orc):
     W = orc.make_weights(**synth.WEIGHTS.as_dict())
     u = np.array([0.003, -0.001, -0.002])
     tg = np.array([0.01, 0.0, 0.09, 0.1, 0.0, 0.99, 0.0])
-    assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u)) == (168, 3, 187, 2)
+    assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u)) == (105, 3, 127, 2)
     # without the bound and sum-zero rows (a projected trial point): the 6 bound rows (12 flops) and
     # the sum-zero row (4, tangent 3) go, and F sums 7 squared rows: 14 + 1 = 15 flops, tangent
-    # 6 x 3 + 5 + 1 = 24: forward 168 - 12 - 4 - 29 + 15 = 138, tangent 187 - 3 - 28 + 24 = 180
-    assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u, box=False)) == (138, 3, 180, 2)
+    # 6 x 3 + 5 + 1 = 24: forward 105 - 12 - 4 - 29 + 15 = 75, tangent 127 - 3 - 28 + 24 = 120
+    assert tuple(orc.opcount_ik(rb, W, None, 1, tg, u, box=False)) == (75, 3, 120, 2)
 
 
 def test_opcount_ik_one_segment(orc):
@@ -258,7 +257,9 @@ def test_opcount_ik_one_segment(orc):
 
 def test_opcount_rodrigues_matches_forward_kinematics_part(orc):
     """Every added segment adds the same counted work (its tendon map, its transform, one more
-    chain product and its penalty rows), and that increment contains one probe-3 segment."""
+    chain product and its penalty rows), and that increment contains one probe-3 segment and the
+    chain product of the 1-segment count's tip frame with it: R Ri (R dependent, 45 / 99) and
+    p + R d (9 mult + 9 add = 18; tangent 9 x 3 + 9 = 36)."""
     from paper_2607_11340_gb300 import synth
 
     W = orc.make_weights(**synth.WEIGHTS.as_dict())
@@ -272,6 +273,8 @@ def test_opcount_rodrigues_matches_forward_kinematics_part(orc):
     np.testing.assert_array_equal(d1, d2)
     seg = np.array(orc.opcount_probe(3))
     assert np.all(d1 >= seg)
+    # the increment holds one chain product (45 + 18 forward flops), which the 1-segment count lacks
+    assert d1[0] >= seg[0] + 63
 
 
 def test_lm_trace_and_pg_history_are_consistent(orc):
@@ -340,3 +343,12 @@ def test_opcount_lm_update(orc):
       n = 9: 18 + (72 + 204) + 162 + 46 + 8 = 510 flops, 9 square roots."""
     assert orc.opcount_lm_update(1) == (18, 1)
     assert orc.opcount_lm_update(9) == (510, 9)
+
+
+def test_opcount_pg_step(orc):
+    """The step of one projected-gradient iteration on n unknowns, counted by hand: |g|^2 as a sum
+    from zero, n products and n additions; one square root; the step length alpha / |g|, one
+    division; the move x - (alpha / |g|) g, n products and n subtractions: 4n + 1 flops, 1 square
+    root (n = 9: 37)."""
+    assert orc.opcount_pg_step(1) == (5, 1)
+    assert orc.opcount_pg_step(9) == (37, 1)
