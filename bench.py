@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     ap.add_argument("--items", type=int, default=synth.N_RAGGED,
                     help="items of the ragged batch (default 16384; smaller for profiling cases)")
-    ap.add_argument("--workload", default="ik3", choices=["ik3", "ik1", "path", "traj", "prm", "calib", "ragged", "e1", "e2"],
+    ap.add_argument("--workload", default="ik3",
+                    choices=["ik3", "ik1", "path", "traj", "prm", "calib", "ragged", "e1", "e2", "self"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
@@ -56,6 +57,18 @@ def parse():
 def load_counts(key="ik_3seg_pose"):
     with open(os.path.join(ROOT, "tests", "golden", "opcounts.json")) as f:
         return json.load(f)[key]
+
+
+def method_ops(c, n_seed, k_init, accepted):
+    """The method's own work in stage one (oracle op counts): every seed's first value and gradient
+    with all rows; at each of the k_init steps the step rule's arithmetic and a value at the
+    projected trial point, without the rows that vanish there; a gradient only where the trial is
+    accepted. Returns (flops, special-function calls)."""
+    flop = (n_seed * (c["fwd_flop"] + c["tan_flop"]) + n_seed * k_init * (c["trial_fwd_flop"] + c["pg_step_flop"])
+            + accepted * c["trial_tan_flop"])
+    sfu = (n_seed * (c["fwd_sfu"] + c["tan_sfu"]) + n_seed * k_init * (c["trial_fwd_sfu"] + c["pg_step_sfu"])
+           + accepted * c["trial_tan_sfu"])
+    return flop, sfu
 
 
 def measured_peaks():
@@ -129,14 +142,14 @@ def make_targets(torch, api, lib, spec, P, seed, device):
     return tg
 
 
-def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=None):
+def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=None, weights=synth.WEIGHTS):
     """Oracle solves/s on host cores over a bounded contiguous sample of the targets."""
     import oracle as O
 
     O.build()
     rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb, rbody=spec.body_radius,
                       lmin=spec.lmin, lmax=spec.lmax)
-    W = O.make_weights(**synth.WEIGHTS.as_dict())
+    W = O.make_weights(**weights.as_dict())
     threads = threads or os.cpu_count()
     cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
                      alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, lim_tol=ik.lim_tol, pos_tol=ik.pos_tol,
@@ -386,6 +399,42 @@ def other_workload(args):
                     "trajectory_cost_median_linear": float(lin.cost.median())}
 
         dtype = "f32"
+    elif args.workload == "self":
+        # IK with the self-contact rows (Eq. ik_coll over the robot itself), half the targets posed by
+        # self-intersecting curled states
+        spec, ik, P = synth.ROBOT_SELF, synth.IK_SELF, synth.P_SELF
+
+        def fk_np(uu):
+            T, _ = api.fk(api.robot_struct(spec), torch.as_tensor(uu.T.copy(), dtype=torch.float64, device=dev))
+            return T.cpu().numpy().T
+
+        tg_np, _ = synth.self_contact_workload(spec, P, fk_np, seed=0)
+        tgd = torch.as_tensor(tg_np.T.copy(), dtype=torch.float64, device=dev)
+        s = api.IkSolver(spec, ik, synth.WEIGHTS_SELF, lib.CR_TASK_IK6, P, device=dev)
+        s_off = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK6, P, device=dev)
+        fn = lambda: s.solve(tgd)
+        units, unit = P, "solves/s"
+        metric = "IK solves/s with self-contact rows, 4-segment robot (128 seeds -> top 8, FP32 + FP64 Cholesky)"
+        wl = "ik_self_4seg_1024targets_half_self_intersecting_128seeds_top8_pg32_lm30"
+
+        def extra():
+            s_off.solve(tgd)
+            off_ms = time_steps(torch, lambda: s_off.solve(tgd), args.steps, flush, stream)[1]
+            out = {"success_rate": float(s.out.success.float().mean()),
+                   "success_rate_first_half_self_intersecting_targets": float(s.out.success[:P // 2].float().mean()),
+                   "ms_per_step_without_self_rows": off_ms, "device_status": s.status()}
+            if not args.no_baseline:
+                rate, n, cores, dt, osucc, _ = cpu_oracle_rate(tg_np, spec, ik, budget_s=12.0,
+                                                               weights=synth.WEIGHTS_SELF)
+                gs = s.out.success[:n].cpu().numpy().astype(bool)
+                out["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                       "sample": f"first {n} targets ({dt:.1f} s on {cores} threads)"}
+                out["oracle_agreement"] = {"targets": n, "success_rate_oracle": float(osucc.mean()),
+                                           "success_rate_gpu": float(gs.mean()),
+                                           "success_flag_mismatches": int((gs != osucc).sum())}
+            return out
+
+        dtype = "f32"
     elif args.workload in ("e1", "e2"):
         # the paper's own IK benchmarks in its (theta, phi, L) parameterisation (Sec. V-B)
         ik = synth.IK_E1
@@ -430,8 +479,7 @@ def other_workload(args):
                 acc = s.pg_accepted()
                 n_seed = units * ik.S
                 n_eval = n_seed * (ik.k_init + 1)
-                fl = (n_seed * (c["fwd_flop"] + c["tan_flop"]) + n_seed * ik.k_init * c["trial_fwd_flop"]
-                      + acc * c["trial_tan_flop"])  # the method's work, as for the headline
+                fl, _ = method_ops(c, n_seed, ik.k_init, acc)  # the method's work, as for the headline
                 ach = fl / (s1_ms / 1e3) / 1e12
                 sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
                 peak = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -619,17 +667,12 @@ def main():
     s1_ms = float(np.mean([a.elapsed_time(b) for a, b in ev1]))
     accepted = solver.pg_accepted()  # accepted PG steps of the last stage-one launch (device counter)
     n_eval = P * ik.S * (ik.k_init + 1)  # value evaluations per stage-one launch
-    # The method's own work (oracle op counts): every seed's first value and gradient with all rows;
-    # a value at each of the k_init projected trial points, without the rows that vanish there; a
-    # gradient only where the trial is accepted. The kernel computes the gradient at every trial
-    # (fused, one pass; a warp's lanes accept independently), which is reported beside it.
+    # The method's own work (method_ops). The kernel computes the gradient at every trial (fused, one
+    # pass; a warp's lanes accept independently), which is reported beside it.
     n_seed = P * ik.S
-    flop_method = (n_seed * (counts["fwd_flop"] + counts["tan_flop"]) + n_seed * ik.k_init * counts["trial_fwd_flop"]
-                   + accepted * counts["trial_tan_flop"])
-    sfu_method = (n_seed * (counts["fwd_sfu"] + counts["tan_sfu"]) + n_seed * ik.k_init * counts["trial_fwd_sfu"]
-                  + accepted * counts["trial_tan_sfu"])
-    flop_fused = (n_seed * (counts["fwd_flop"] + counts["tan_flop"])
-                  + n_seed * ik.k_init * (counts["trial_fwd_flop"] + counts["trial_tan_flop"]))
+    flop_method, sfu_method = method_ops(counts, n_seed, ik.k_init, accepted)
+    flop_fused = (n_seed * (counts["fwd_flop"] + counts["tan_flop"]) + n_seed * ik.k_init
+                  * (counts["trial_fwd_flop"] + counts["pg_step_flop"] + counts["trial_tan_flop"]))
     achieved_tflops = flop_method / (s1_ms / 1e3) / 1e12
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -710,7 +753,7 @@ def main():
         "plain_form": {"value": plain_rate, "unit": UNIT, "targets": Pp, "success_rate": plain_succ,
                        "optimised_success_rate_same_targets": opt_succ_sub, "speedup": value / world / plain_rate},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,  # stage one, SelectTop, refine, argmin
         "clocks": clocks,
     }
     if world == 1 and not args.no_baseline:

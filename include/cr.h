@@ -79,7 +79,16 @@ typedef enum { CR_F32 = 0, CR_F64 = 1 } cr_dtype;
  *   pin it); bounds theta_i <= theta_max_i. Entry points that take the arc model: cr_fk,
  *   cr_fk_jac, cr_cost_grad, cr_seeds, cr_lm_step, cr_pg_steps, cr_solve_ik (and its two stages)
  *   for 1..4 segments; the others return CR_EINVAL for it. */
-typedef enum { CR_MODEL_TENDON = 0, CR_MODEL_ARC = 1 } cr_model;
+/* CR_MODEL_COUPLED: coupled tendon routing (Eq. l_eq read literally: tendon j of segment s runs through
+ *   segments 1..s, its length the sum of the per-segment lengths of Eq. 4). The state holds the
+ *   actuator displacements q_sj = sum_{i <= s} u_ij; the kinematics take the per-segment displacements
+ *   u_s = q_s - q_{s-1}, and gradients and Jacobian columns leave through the transpose of that map
+ *   (d/dq_s = d/du_s - d/du_{s+1}). Bounds |q_sj| <= u_max_s and sum_j q_sj = 0 act on the actuators
+ *   (sum_j q_sj = 0 for every s exactly when every segment's displacements sum to zero), so seeds and
+ *   the stage-one projection are those of the tendon model. Taken by cr_fk, cr_fk_jac, cr_cost_grad,
+ *   cr_cost_vjp, cr_seeds, cr_lm_step, cr_pg_steps, cr_solve_ik (and its stages, and the static
+ *   variant), 1..CR_MAX_SEG segments; the others return CR_EINVAL for it. */
+typedef enum { CR_MODEL_TENDON = 0, CR_MODEL_ARC = 1, CR_MODEL_COUPLED = 2 } cr_model;
 #define CR_MAX_SEG_ARC 4
 
 /* Robot geometry (Sec. III, Fig. 2). Host struct. */
@@ -108,6 +117,15 @@ typedef struct {
   double dt, v_max, a_max;            /* time step (s), tendon speed (m/s) and acceleration
                                          (m/s^2) limits */
   double delta;                       /* clearance margin of Eq. ik_coll (m) */
+  double rho_s;                       /* self-contact rows of Eq. ik_coll over the robot itself:
+                                         sqrt(rho_s) max(0, 2 r_body + delta - |p_a - p_b|) for
+                                         backbone samples a, b of segments two or more apart;
+                                         0 leaves them out. Taken by cr_cost_grad, cr_cost_vjp,
+                                         cr_pg_steps, cr_lm_step, cr_solve_ik (and its stages),
+                                         cr_traj_cost and cr_solve_traj, whose acceptance then
+                                         also requires those samples 2 r_body apart; the path,
+                                         batch, PRM and plain solvers return CR_EINVAL for
+                                         rho_s > 0. */
 } cr_weights;
 
 /* Obstacles: spheres for the clearance rows of Eq. ik_coll. Host struct; `spheres` is a device
@@ -236,12 +254,15 @@ CR_API cr_status cr_topk(const float* cost, const float* coll, const void* u, in
 
 /* Scratch bytes cr_solve_ik needs for P targets. The workspace starts with the status word
  * (int32, read by cr_poll_status); at byte offset 8 a uint64 counts the projected-gradient steps
- * that stage one accepted, over all seeds (both are cleared by cr_solve_ik and cr_ik_stage1). */
+ * that stage one accepted, over all seeds (both are cleared by cr_solve_ik and cr_ik_stage1). It
+ * also holds every seed's end state after stage one (P * S states), which SelectTop reads back:
+ * about P * S * (3n + 2) * 4 bytes in FP32 (46 MB for 4096 targets of 256 seeds, 3 segments). */
 CR_API size_t cr_ik_workspace_size(const cr_robot* robot, int64_t P, const cr_ik_params* prm);
 
 /* Algorithm 1 (beam-search IK) for the P targets of `task` (task->seeds_per_target is ignored):
  * SampleSeeds(S) -> k_init projected-gradient steps per seed (registers) -> SelectTop(n_final)
- * (warp shuffles) -> k_final LM iterations per candidate -> FP64 re-evaluation and argmin.
+ * (one warp per target, in a kernel of its own) -> k_final LM iterations per candidate -> FP64
+ * re-evaluation and argmin.
  * Outputs (device, FP64 unless noted): u_out [3n][P], cost_out [P], pos_err [P] (m),
  * rot_err [P] (rad), success [P] (uint8: pos_err <= pos_tol, rot_err <= rot_tol, within limits,
  * collision-free). */
@@ -469,6 +490,27 @@ CR_API cr_status cr_calibrate(const cr_robot* robot, const void* U, const double
                               int32_t iters, double lambda0, double* F_out, double* hist, int32_t dtype,
                               void* workspace, size_t ws_bytes, cr_stream stream);
 
+/* Sharded calibration: the pieces of one cr_calibrate iteration, for processes (one GPU each) that
+ * each hold a share of the K poses. Per iteration every process runs
+ *   cr_calib_sums (its share) -> all-reduce (sum) of `sums` -> cr_calib_trial ->
+ *   cr_calib_cost (its share, at theta_trial) -> all-reduce (sum) of F_trial -> cr_calib_accept,
+ * and so keeps the same theta and damping state as the others. One process with all the poses
+ * reproduces cr_calibrate exactly (same partial sums in the same order, same factorisation, same
+ * rule). Arrays are device FP64: theta, theta_trial [2n]; sums [cr_calib_nv(n)] = packed J^T J (lower
+ * triangle by rows), J^T r, F = 1/2 |r|^2; state [4] = lambda, nu, ok, pred, initialised by the
+ * caller to (lambda0, 2, 0, 0). cr_calib_sums needs cr_calibrate_workspace_size(robot, K) bytes of
+ * workspace; U and P_meas as in cr_calibrate. cr_calib_nv returns 0 for n out of range. */
+CR_API int32_t cr_calib_nv(int32_t n);
+CR_API cr_status cr_calib_sums(const cr_robot* robot, const void* U, const double* P_meas, int64_t K,
+                               const double* theta, double* sums, int32_t dtype, void* workspace, size_t ws_bytes,
+                               cr_stream stream);
+CR_API cr_status cr_calib_trial(const cr_robot* robot, const double* sums, const double* theta, double* state,
+                                double* theta_trial, cr_stream stream);
+CR_API cr_status cr_calib_cost(const cr_robot* robot, const void* U, const double* P_meas, int64_t K,
+                               const double* theta_trial, double* F_trial, int32_t dtype, cr_stream stream);
+CR_API cr_status cr_calib_accept(const cr_robot* robot, const double* sums, const double* F_trial,
+                                 const double* theta_trial, double* theta, double* state, cr_stream stream);
+
 /* Vector-Jacobian product of the IK cost: grad_u_out[:, b] = upstream[b] dF_b/du_b and
  * grad_param_out [2n] (FP64) = sum_b upstream[b] dF_b/d(L, r_c). workspace: [2n][B] in `dtype`.
  * upstream [B], grad_u_out [3n][B] in `dtype`. The adjoint recomputes the forward sweep. */
@@ -571,6 +613,18 @@ CR_API cr_status cr_solve_batch(const cr_robot* family, const cr_weights* w, con
                                 double* u_out, double* cost_out, double* pos_err, double* rot_err,
                                 uint8_t* flags_out, uint64_t* t_done_ns, void* workspace, size_t ws_bytes,
                                 cr_stream stream);
+
+/* Contiguous partition of a ragged batch over `parts` processes (one GPU each) by estimated cost:
+ * the planner's relative time of each item (the one cr_batch_plan_create orders its queue by). On
+ * return bounds[0] = 0 <= bounds[1] <= ... <= bounds[parts] = N and process r takes the items
+ * [bounds[r], bounds[r + 1]), in the caller's order; bounds[r] is the first item whose prefix
+ * cost (through that item) exceeds r / parts of the total, so a part exceeds the mean by at most
+ * one item's cost. The items are independent (no data crosses processes); with
+ * prm->ik.p0 + bounds[r] as a process's p0 its seeds equal those of the unpartitioned batch.
+ * Host only (no GPU work); bounds: host array of parts + 1 values. CR_EINVAL for N < 0, parts < 1,
+ * NULL pointers or a bad item. */
+CR_API cr_status cr_batch_partition(const cr_batch_item* items, int64_t N, const cr_batch_params* prm, int32_t parts,
+                                    int64_t* bounds);
 
 /* The plain form of the same batch, for comparison: one cr_solve_ik / cr_solve_path call per item
  * (P = 1) in the caller's order on `stream`, each followed by a completion stamp. Same outputs,

@@ -13,7 +13,7 @@ from . import synth
 def robot_struct(spec: synth.RobotSpec) -> lib.cr_robot:
     r = lib.cr_robot()
     r.n, r.m, r.n_b = spec.n, 3, spec.nb
-    r.model = lib.CR_MODEL_ARC if spec.is_arc else lib.CR_MODEL_TENDON
+    r.model = lib.CR_MODEL_ARC if spec.is_arc else (lib.CR_MODEL_COUPLED if spec.coupled else lib.CR_MODEL_TENDON)
     for i in range(spec.n):
         r.L[i] = spec.L[i]
         r.r_c[i] = spec.rc
@@ -31,6 +31,7 @@ def weights_struct(w: synth.WeightSpec) -> lib.cr_weights:
     s.rho_b, s.rho_eq, s.rho_k, s.rho_c = w.rho_b, w.rho_eq, w.rho_k, w.rho_c
     s.w_s, s.w_len, s.rho_v, s.rho_a = w.w_s, w.w_len, w.rho_v, w.rho_a
     s.dt, s.v_max, s.a_max, s.delta = w.dt, w.vmax, w.amax, w.delta
+    s.rho_s = w.rho_s
     return s
 
 
@@ -374,6 +375,72 @@ def calibrate(robot_spec, U_soa, P_meas_soa, theta0, iters=synth.ITERS_CALIB, la
     ws = torch.empty(lib.cr_calibrate_workspace_size(robot, U_soa.shape[-1]), dtype=torch.uint8, device=U_soa.device)
     lib.cr_calibrate(robot, U_soa, P_meas_soa, theta, iters, lambda0, F, hist, ws)
     return theta, F, hist
+
+
+def calibrate_lm_sharded(ops, theta, state, iters, allreduce):
+    """The LM iterations of the calibration when the poses are spread over processes (the one place
+    where processes exchange data: a sum over all poses): per iteration this process's partial sums (J^T J, J^T r, F) are all-reduced, every
+    process forms the same trial parameters, the partial trial costs are all-reduced and every process
+    applies the same rule, so theta stays identical everywhere. ``ops`` holds the four pieces (the
+    library's cr_calib_* calls in CalibShard), ``allreduce(t)`` sums a tensor over the processes in
+    place. theta and state (lambda, nu, ok, pred) are updated in place."""
+    for _ in range(iters):
+        sums = ops.sums(theta)
+        allreduce(sums)
+        theta_trial = ops.trial(sums, theta, state)
+        F_trial = ops.cost(theta_trial)
+        allreduce(F_trial)
+        ops.accept(sums, F_trial, theta_trial, theta, state)
+    return theta, state
+
+
+class CalibShard:
+    """One process's share of the calibration poses on its GPU: U_soa [d][K] (float32/64 CUDA),
+    P_meas_soa [3][K] FP64 CUDA; the four pieces of an iteration as library calls."""
+
+    def __init__(self, robot_spec, U_soa, P_meas_soa):
+        self.robot = robot_struct(robot_spec)
+        self.U, self.P = U_soa, P_meas_soa
+        dev = U_soa.device
+        self.nv = lib.cr_calib_nv(robot_spec.n)
+        self.ws = torch.empty(lib.cr_calibrate_workspace_size(self.robot, U_soa.shape[-1]), dtype=torch.uint8,
+                              device=dev)
+        self.theta_trial = torch.empty(2 * robot_spec.n, dtype=torch.float64, device=dev)
+
+    def sums(self, theta):
+        out = torch.empty(self.nv, dtype=torch.float64, device=self.U.device)
+        lib.cr_calib_sums(self.robot, self.U, self.P, theta, out, self.ws)
+        return out
+
+    def trial(self, sums, theta, state):
+        lib.cr_calib_trial(self.robot, sums, theta, state, self.theta_trial)
+        return self.theta_trial
+
+    def cost(self, theta_trial):
+        F = torch.empty(1, dtype=torch.float64, device=self.U.device)
+        lib.cr_calib_cost(self.robot, self.U, self.P, theta_trial, F)
+        return F
+
+    def accept(self, sums, F_trial, theta_trial, theta, state):
+        lib.cr_calib_accept(self.robot, sums, F_trial, theta_trial, theta, state)
+
+
+def calibrate_sharded(robot_spec, U_soa, P_meas_soa, theta0, iters=synth.ITERS_CALIB, lambda0=1e-3, group=None):
+    """calibrate() over the poses of all processes of ``group`` (torch.distributed, NCCL on GPUs), this
+    process holding U_soa / P_meas_soa; without a process group it is calibrate() itself, iteration
+    for iteration. Returns theta [2n] (device), identical on every process."""
+    import torch.distributed as dist
+
+    dev = U_soa.device
+    theta = torch.as_tensor(theta0, dtype=torch.float64, device=dev).clone()
+    state = torch.tensor([lambda0, 2.0, 0.0, 0.0], dtype=torch.float64, device=dev)
+    multi = dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1
+
+    def allreduce(t):
+        if multi:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+
+    return calibrate_lm_sharded(CalibShard(robot_spec, U_soa, P_meas_soa), theta, state, iters, allreduce)[0]
 
 
 # ---------------------------------------------------------------------------------------------

@@ -50,8 +50,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     srcs = _sources()
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
 
+    # an object newer than its source and every shared header is reused (a changed header rebuilds all)
+    hdr = max(os.path.getmtime(p) for p in _deps() if not p.endswith(".cu"))
+
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(hdr, os.path.getmtime(src)):
+            return obj
         cmd = [nvcc()] + NVCC_FLAGS + ARCH + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

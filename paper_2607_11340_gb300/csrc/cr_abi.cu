@@ -42,7 +42,7 @@ cr_status check_robot(const cr_robot* r) {
       return fail(CR_EINVAL, "segment %d: L, r_c, u_max and theta_max must be positive", i);
   }
   if (!(r->r_body >= 0)) return fail(CR_EINVAL, "robot.r_body must be >= 0");
-  if (r->model != CR_MODEL_TENDON && r->model != CR_MODEL_ARC)
+  if (r->model != CR_MODEL_TENDON && r->model != CR_MODEL_ARC && r->model != CR_MODEL_COUPLED)
     return fail(CR_EINVAL, "robot.model = %d is not a cr_model", r->model);
   if (r->model == CR_MODEL_ARC) {
     if (r->n > CR_MAX_SEG_ARC) return fail(CR_EINVAL, "arc model: robot.n = %d above %d", r->n, CR_MAX_SEG_ARC);
@@ -75,8 +75,16 @@ cr_status check_scene_shared(const cr_scene* s) {
   return CR_OK;
 }
 
+cr_status check_self_rows(const cr_weights& w, bool supported, const char* who) {
+  if (!(w.rho_s >= 0.0)) return fail(CR_EINVAL, "%s: weights.rho_s must be >= 0", who);
+  if (w.rho_s > 0.0 && !supported)
+    return fail(CR_EINVAL, "%s: self-contact rows (weights.rho_s > 0) are not built for this solver", who);
+  return CR_OK;
+}
+
 cr_status check_task(const cr_task* t, int64_t B) {
   if (!t) return fail(CR_EINVAL, "task is NULL");
+  if (!(t->w.rho_s >= 0.0)) return fail(CR_EINVAL, "task.w.rho_s must be >= 0");
   if (t->kind != CR_TASK_IK6 && t->kind != CR_TASK_IK5) return fail(CR_EINVAL, "task.kind = %d invalid", t->kind);
   if (t->seeds_per_target < 1) return fail(CR_EINVAL, "task.seeds_per_target must be >= 1");
   if (t->n_targets < 0) return fail(CR_EINVAL, "task.n_targets < 0");
@@ -101,6 +109,10 @@ IkLayout ik_layout(const cr_robot& r, int64_t P, const cr_ik_params& prm) {
   L.cand_flag = off; off = align256(off + PK);
   L.plain_u = off; off = align256(off + (size_t)prm.S * D * 8);
   L.plain_F = off; off = align256(off + (size_t)prm.S * 8 * 3 + 32 * 4 + (size_t)prm.S * 5);
+  const size_t PS = (size_t)P * (size_t)(prm.S > 0 ? prm.S : 0);
+  L.stage_F = off; off = align256(off + PS * 4);
+  L.stage_C = off; off = align256(off + PS * 4);
+  L.stage_u = off; off = align256(off + D * PS * tb);
   L.total = off;
   return L;
 }

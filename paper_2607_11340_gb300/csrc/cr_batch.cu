@@ -418,6 +418,7 @@ cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* w, cons
                                uint64_t* t_done_ns, void* workspace, size_t ws_bytes, cr_stream stream,
                                cr_batch_plan** plan_out) {
   cr_status st;
+  if (w && (st = check_self_rows(*w, false, "cr_batch_plan_create"))) return st;
   if (!plan_out || !w) return fail(CR_EINVAL, "cr_batch_plan_create: NULL plan or weights");
   *plan_out = nullptr;
   if ((st = check_items(family, items, N, prm))) return st;
@@ -514,6 +515,7 @@ cr_status cr_solve_batch(const cr_robot* family, const cr_weights* w, const cr_b
                          double* cost_out, double* pos_err, double* rot_err, uint8_t* flags_out, uint64_t* t_done_ns,
                          void* workspace, size_t ws_bytes, cr_stream stream) {
   if (!prm) return fail(CR_EINVAL, "cr_solve_batch: NULL params");
+  if (w && check_self_rows(*w, false, "cr_solve_batch")) return CR_EINVAL;
   if (N == 0) return check_items(family, items, N, prm);
   cr_batch_params p = *prm;
   if (p.seeds_per_unit == 0) p.seeds_per_unit = 64;
@@ -563,6 +565,7 @@ cr_status cr_solve_batch_plain(const cr_robot* family, const cr_weights* w, cons
                                uint64_t* t_done_ns, void* workspace, size_t ws_bytes, cr_stream stream) {
   cr_status st;
   if (!w) return fail(CR_EINVAL, "cr_solve_batch_plain: NULL weights");
+  if ((st = check_self_rows(*w, false, "cr_solve_batch_plain"))) return st;
   if ((st = check_items(family, items, N, prm))) return st;
   if (N == 0) return CR_OK;
   if ((st = check_outputs(targets, spheres, u_out, cost_out, pos_err, rot_err, flags_out, t_done_ns, workspace,
@@ -622,6 +625,31 @@ cr_status cr_solve_batch_plain(const cr_robot* family, const cr_weights* w, cons
     so += it.n_o;
     st_off += (int64_t)3 * it.n * it.H;
   }
+  return CR_OK;
+}
+
+cr_status cr_batch_partition(const cr_batch_item* items, int64_t N, const cr_batch_params* prm, int32_t parts,
+                             int64_t* bounds) {
+  if (!prm || !bounds || (N > 0 && !items) || N < 0 || parts < 1)
+    return fail(CR_EINVAL, "cr_batch_partition: NULL argument, N < 0 or parts < 1");
+  std::vector<double> pre((size_t)N + 1, 0.0);  // prefix costs in the caller's order
+  for (int64_t i = 0; i < N; ++i) {
+    const cr_batch_item& it = items[i];
+    if ((it.kind != CR_ITEM_IK && it.kind != CR_ITEM_PATH) || it.n < 1 || it.n > CR_MAX_SEG || it.H < 1 ||
+        it.H > CR_BATCH_MAX_H || (it.kind == CR_ITEM_IK && it.H != 1) || it.S < 1 || it.S > CR_MAX_SEEDS ||
+        it.n_o < 0 || it.n_o > CR_BATCH_MAX_SPHERES)
+      return fail(CR_EINVAL, "cr_batch_partition: bad item %lld", (long long)i);
+    pre[(size_t)i + 1] = pre[(size_t)i] + est_cost(it, *prm);
+  }
+  const double total = pre[(size_t)N];
+  bounds[0] = 0;
+  int64_t j = 0;
+  for (int r = 1; r < parts; ++r) {
+    const double goal = total * (double)r / (double)parts;
+    while (j < N && pre[(size_t)j + 1] <= goal) ++j;  // items whose prefix cost stays within r / parts
+    bounds[r] = j;
+  }
+  bounds[parts] = N;
   return CR_OK;
 }
 

@@ -81,6 +81,7 @@ template <typename T> struct WeightsK {
   T rho_b, rho_eq, rho_k, rho_c;
   T sb, se, sk, sc;        // square roots of the penalty weights (row scale)
   T delta;
+  T rho_s, ss;             // self-contact rows (0: none) and the square root of their weight
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -260,6 +261,10 @@ CR_HD void segment_state(const RobotK<T>& rb, const T (&u)[3 * N], int i, T& ax,
     ax = u[3 * i];
     ay = u[3 * i + 1];
     L = u[3 * i + 2];
+  } else if (MODEL == CR_MODEL_COUPLED && i > 0) {
+    // coupled routing: the state holds actuator displacements q; segment i bends with u_i = q_i - q_{i-1}
+    bend_of(rb.K[i], u[3 * i] - u[3 * i - 3], u[3 * i + 1] - u[3 * i - 2], u[3 * i + 2] - u[3 * i - 1], ax, ay);
+    L = rb.L[i];
   } else {
     bend_of(rb.K[i], u[3 * i], u[3 * i + 1], u[3 * i + 2], ax, ay);
     L = rb.L[i];
@@ -280,6 +285,14 @@ CR_HD void bend_cols(const RobotK<T>& rb, int i, T gx, T gy, T& c0, T& c1, T& c2
   }
 }
 
+// A row of u-space derivatives (per-segment displacements) to the state's: the identity, except for
+// coupled routing, where u = D q (u_s = q_s - q_{s-1}) and so d/dq_s = d/du_s - d/du_{s+1}.
+template <int MODEL, typename T, int N> CR_HD void to_actuator(T (&jr)[3 * N]) {
+  if (MODEL != CR_MODEL_COUPLED) return;
+#pragma unroll
+  for (int q = 0; q + 3 < 3 * N; ++q) jr[q] -= jr[q + 3];
+}
+
 template <typename T, int N, int MODEL = CR_MODEL_TENDON>
 CR_HD void chain_forward(const RobotK<T>& rb, const T (&u)[3 * N], Chain<T, N>& ch) {
   T R[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};
@@ -298,6 +311,13 @@ CR_HD void chain_forward(const RobotK<T>& rb, const T (&u)[3 * N], Chain<T, N>& 
     ch.ax[i] = ax; ch.ay[i] = ay; ch.x[i] = x; ch.s[i] = s; ch.c[i] = c; ch.L[i] = Li;
     T Ri[9], di[3];
     seg_transform(ax, ay, x, s, c, Li, Ri, di);
+    if (i == 0) {  // base frame = identity: the products by its zeros are left out
+#pragma unroll
+      for (int a = 0; a < 9; ++a) R[a] = Ri[a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) p[a] = di[a];
+      continue;
+    }
     T t[3];
     matvec(R, di, t);
     p[0] += t[0]; p[1] += t[1]; p[2] += t[2];
@@ -553,14 +573,109 @@ template <typename T, int N> struct StateAgg {
   T G[N][3], M[N][3], Dx[N], Dy[N], DL[N];
 };
 
+// A force gw (dF/dw) at the backbone sample of arc fraction sg of segment i (local point q, world point
+// wp, segment coefficients s, c of the sub-arc): its share of the segment's force / moment sums and of
+// the direct terms in (ax_i, ay_i, L_i), as the sphere rows below accumulate them.
+template <typename T, int N, bool PGRAD, int MODEL>
+CR_HD void agg_sample_force(const Chain<T, N>& ch, int i, T sg, const T (&q)[3], const T (&wp)[3], T s, T c,
+                            const T (&gw)[3], StateAgg<T, N>& ag) {
+  ag.G[i][0] += gw[0]; ag.G[i][1] += gw[1]; ag.G[i][2] += gw[2];
+  T mw[3];
+  cross(wp, gw, mw);
+  ag.M[i][0] += mw[0]; ag.M[i][1] += mw[1]; ag.M[i][2] += mw[2];
+  T gl[3];
+  matTvec(ch.Rb[i], gw, gl);
+  T s3, cp;
+  seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
+  T dd[2][3], wl[2][3];
+  seg_local_derivs(sg * ch.ax[i], sg * ch.ay[i], s, c, s3, cp, sg * ch.L[i], dd, wl);
+  ag.Dx[i] += sg * (gl[0] * dd[0][0] + gl[1] * dd[0][1] + gl[2] * dd[0][2]);
+  ag.Dy[i] += sg * (gl[0] * dd[1][0] + gl[1] * dd[1][1] + gl[2] * dd[1][2]);
+  if (PGRAD || MODEL == CR_MODEL_ARC) ag.DL[i] += (gl[0] * q[0] + gl[1] * q[1] + gl[2] * q[2]) / ch.L[i];
+}
+
+// Self-contact rows (Eq. ik_coll's minimum distance over the robot itself, Sec. IV-A; the rows are
+// defined for backbone samples a of segment i and b of segment j >= i + 2, adjacent segments meeting
+// at a joint): sqrt(rho_s) max(0, gap - |p_a - p_b|), gap = 2 r_body + delta. Adds 1/2 r^2 to coll
+// and, when GRAD, equal and opposite forces at the two samples to the segments' aggregates, which
+// the reverse sweep turns into the gradient like any sample force. Broad phase: every sample of
+// segment i lies within L_i / 2 of its mid-arc point (unit speed in arc length), so a segment pair
+// whose mid-arc points are farther apart than (L_i + L_j) / 2 + gap has no active row, nor a sample
+// of i farther than L_j / 2 + gap from segment j's; both tests carry the 1e-4 rounding margin of the
+// sphere culling. The rows' order and values are the oracle's; only pairs within gap contribute.
+template <typename T, int N, bool GRAD, bool PGRAD, int MODEL>
+CR_HD void self_contact_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Chain<T, N>& ch,
+                                StateAgg<T, N>& ag, T& coll) {
+  if (N < 3 || !(w.rho_s > T(0))) return;
+  const T gap = T(2) * rb.rbody + w.delta;
+  const T inb = c_div(T(1), T(rb.nb));
+  T lsum = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) lsum += ch.L[i];
+  const T marg = T(1e-4) * (lsum + gap);
+  T mid[N][3];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T q[3], s, c;
+    backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(0.5), q, mid[i], s, c);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = i + 2; j < N; ++j) {
+      {
+        const T dx = mid[i][0] - mid[j][0], dy = mid[i][1] - mid[j][1], dz = mid[i][2] - mid[j][2];
+        const T lim = T(0.5) * (ch.L[i] + ch.L[j]) + gap + marg;
+        if (!(dx * dx + dy * dy + dz * dz < lim * lim)) continue;
+      }
+      const T limj = T(0.5) * ch.L[j] + gap + marg;
+      for (int ka = 1; ka <= rb.nb; ++ka) {
+        const T sa = T(ka) * inb;
+        T qa[3], pa[3], s_a, c_a;
+        backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sa, qa, pa, s_a, c_a);
+        {
+          const T ex = pa[0] - mid[j][0], ey = pa[1] - mid[j][1], ez = pa[2] - mid[j][2];
+          if (!(ex * ex + ey * ey + ez * ez < limj * limj)) continue;
+        }
+        T ga[3] = {T(0), T(0), T(0)};
+        bool hit = false;
+        for (int kb = 1; kb <= rb.nb; ++kb) {
+          const T sb = T(kb) * inb;
+          T qb[3], pb[3], s_b, c_b;
+          backbone_point(ch.Rb[j], ch.pb[j], ch.ax[j], ch.ay[j], ch.x[j], ch.L[j], sb, qb, pb, s_b, c_b);
+          const T dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+          const T d2 = dx * dx + dy * dy + dz * dz;
+          if (!(d2 < gap * gap)) continue;
+          const T dist = c_sqrt(d2);
+          const T viol = gap - dist;
+          const T rr = w.ss * viol;
+          coll += T(0.5) * rr * rr;
+          if (GRAD) {
+            const T f = -w.rho_s * viol / dist;
+            const T gw[3] = {f * dx, f * dy, f * dz};  // dF/dp_a; p_b takes -gw
+            ga[0] += gw[0]; ga[1] += gw[1]; ga[2] += gw[2];
+            const T gb[3] = {-gw[0], -gw[1], -gw[2]};
+            agg_sample_force<T, N, PGRAD, MODEL>(ch, j, sb, qb, pb, s_b, c_b, gb, ag);
+            hit = true;
+          }
+        }
+        if (GRAD && hit) agg_sample_force<T, N, PGRAD, MODEL>(ch, i, sa, qa, pa, s_a, c_a, ga, ag);
+      }
+    }
+  }
+}
+
 // Forward phase: chain, clearance rows (and their aggregates when GRAD), and the penalty rows on u
 // (bounds, sum-zero, curvature). Returns their part of F; *coll_out = the clearance part.
 // BOX = false leaves out the bound and sum-zero rows: on the feasible set {|u_j| <= b, sum u_j = 0}
 // they vanish, so callers whose state was just projected onto it skip them (in FP32 the sum-zero
-// row would only add the rounding residue of the projection).
+// row would only add the rounding residue of the projection). OBST compiles the collision rows:
+// the spheres' and, with w.rho_s > 0, the self-contact rows (with_self = false leaves the latter to
+// another thread that evaluates the same state).
 template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
 CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T>* sph, int no,
-                      const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out) {
+                      const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out,
+                      bool with_self = true) {
   chain_forward<T, N, MODEL>(rb, u, ch);
   T coll = T(0);
 #pragma unroll
@@ -624,6 +739,7 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
     }
     }
   }
+  if (OBST && with_self) self_contact_forward<T, N, GRAD, PGRAD, MODEL>(rb, w, ch, ag, coll);
   if (coll_out) *coll_out = coll;
   T F = coll;
 #pragma unroll
@@ -657,26 +773,26 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
 // segment i act on (ax_i, ay_i) through the segment's local derivatives. Adds the penalty gradients
 // and writes dF/du (and dF/dL, dF/dr_c when PGRAD). BOX as in state_forward. In the arc model the
 // state's own lengths take the place of dF/du_i2 (dF/dL_i: everything beyond the segment's end moves
-// with d_i, its own samples scale with L_i).
-template <typename T, int N, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
+// with d_i, its own samples scale with L_i). The moment is kept about the end point of the current
+// segment (moved to the next one by (p_end - p_base) x F), so no large moment about the origin is
+// formed and cancelled. AGG = false: the state has no clearance rows (its aggregates are zero).
+template <typename T, int N, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON, bool AGG = true>
 CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)[3 * N], const Chain<T, N>& ch,
                          const StateAgg<T, N>& ag, const T (&Ftip)[3], const T (&Rtip)[3], T (&gu)[3 * N], T* gL,
                          T* grc) {
   T Fs[3] = {Ftip[0], Ftip[1], Ftip[2]};
-  T Ms[3];
-  cross(ch.p, Fs, Ms);
-  Ms[0] += Rtip[0]; Ms[1] += Rtip[1]; Ms[2] += Rtip[2];
+  T Mp[3] = {Rtip[0], Rtip[1], Rtip[2]};  // moment about the end point of segment i (the tip force acts there)
+  T gnext[3] = {T(0), T(0), T(0)};  // coupled routing: the u-space gradient of segment i + 1
 #pragma unroll
   for (int i = N - 1; i >= 0; --i) {
-    T Pend[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Pend[a] = (i == N - 1) ? ch.p[a] : ch.pb[(i + 1 < N) ? i + 1 : i][a];
-    T PF[3];
-    cross(Pend, Fs, PF);
-    T Mp[3] = {Ms[0] - PF[0], Ms[1] - PF[1], Ms[2] - PF[2]};
     T Fl[3], Ml[3];
-    matTvec(ch.Rb[i], Fs, Fl);
-    matTvec(ch.Rb[i], Mp, Ml);
+    if (i == 0) {  // the base frame is the identity
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { Fl[a] = Fs[a]; Ml[a] = Mp[a]; }
+    } else {
+      matTvec(ch.Rb[i], Fs, Fl);
+      matTvec(ch.Rb[i], Mp, Ml);
+    }
     T s3, cp;
     seg_deriv(ch.x[i], ch.s[i], ch.c[i], s3, cp);
     // Fl . d(d_i)/da_k + Ml . J_l dw/da_k, the products of seg_local_derivs written out:
@@ -687,8 +803,12 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     T sp = T(0.5) * (s3 - cc);
     T Fa = ax * Fl[0] + ay * Fl[1], Ma = ax * Ml[0] + ay * Ml[1];
     T cf = cp * Fa + sp * Fl[2];
-    T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2] + ag.Dx[i];
-    T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2] + ag.Dy[i];
+    T gx = L * (cc * Fl[0] + T(2) * ax * cf) + Ml[1] - s3 * ay * Ma - cc * ay * Ml[2];
+    T gy = L * (cc * Fl[1] + T(2) * ay * cf) - Ml[0] + s3 * ax * Ma + cc * ax * Ml[2];
+    if (AGG) {
+      gx += ag.Dx[i];
+      gy += ag.Dy[i];
+    }
     if ((BOX || MODEL != CR_MODEL_ARC) && ch.x[i] > rb.thmax[i] * rb.thmax[i]) {
       T th = c_sqrt(ch.x[i]);
       T f = w.rho_k * (th - rb.thmax[i]) / th;
@@ -698,9 +818,19 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     T g0, g1, g2;
     bend_cols<MODEL>(rb, i, gx, gy, g0, g1, g2);
     T gj[3] = {g0, g1, g2};
+    if (MODEL == CR_MODEL_COUPLED) {  // dF/dq_i = dF/du_i - dF/du_{i+1} (u = D q)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T gu_ij = gj[j];
+        gj[j] = gu_ij - gnext[j];
+        gnext[j] = gu_ij;
+      }
+    }
+    const T DLi = AGG ? ag.DL[i] : T(0);
     if (MODEL == CR_MODEL_ARC) {
       const T di[3] = {ch.L[i] * ch.c[i] * ch.ax[i], ch.L[i] * ch.c[i] * ch.ay[i], ch.L[i] * ch.s[i]};
-      T gl = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i] + ag.DL[i];
+      T gl = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i];
+      if (AGG) gl += DLi;
       if (BOX) {
         T hi = ch.L[i] - rb.lmax[i], lo = rb.lmin[i] - ch.L[i];
         gl += (hi > T(0) ? w.rho_b * hi : T(0)) - (lo > T(0) ? w.rho_b * lo : T(0));
@@ -725,12 +855,30 @@ CR_HD void state_reverse(const RobotK<T>& rb, const WeightsK<T>& w, const T (&u)
     if (PGRAD) {
       // dF/dL_i: translation d_i = L (...) scales with L; own samples q scale with L too
       T di[3] = {ch.L[i] * ch.c[i] * ch.ax[i], ch.L[i] * ch.c[i] * ch.ay[i], ch.L[i] * ch.s[i]};
-      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i] + ag.DL[i];
+      gL[i] = (Fl[0] * di[0] + Fl[1] * di[1] + Fl[2] * di[2]) / ch.L[i];
+      if (AGG) gL[i] += DLi;
       // dF/dr_c,i: a = K(...) with K = -2/(3 r_c) so da/dr_c = -a / r_c
       grc[i] = -(ch.ax[i] * gx + ch.ay[i] * gy) / rb.rc[i];
     }
-    Fs[0] += ag.G[i][0]; Fs[1] += ag.G[i][1]; Fs[2] += ag.G[i][2];
-    Ms[0] += ag.M[i][0]; Ms[1] += ag.M[i][1]; Ms[2] += ag.M[i][2];
+    if (i > 0) {
+      // to the base of segment i (the end of segment i - 1): M <- M + (p_end - p_base) x F, then the
+      // segment's own samples: force G_i, moment about the base M_i - p_base x G_i (M_i about the origin)
+      T dp[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dp[a] = ((i == N - 1) ? ch.p[a] : ch.pb[(i + 1 < N) ? i + 1 : i][a]) - ch.pb[i][a];
+      T dm[3];
+      cross(dp, Fs, dm);
+      Mp[0] += dm[0]; Mp[1] += dm[1]; Mp[2] += dm[2];
+      if (AGG) {
+        T bg[3];
+        cross(ch.pb[i], ag.G[i], bg);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          Mp[a] += ag.M[i][a] - bg[a];
+          Fs[a] += ag.G[i][a];
+        }
+      }
+    }
   }
 }
 
@@ -770,7 +918,7 @@ CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Targe
   if (!GRAD) return F;
   T Ftip[3], Rtip[3];
   pose_tip_force(kind, w, tg, ch.R, r, e, Ftip, Rtip);
-  state_reverse<T, N, PGRAD, BOX, MODEL>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
+  state_reverse<T, N, PGRAD, BOX, MODEL, OBST>(rb, w, u, ch, ag, Ftip, Rtip, gu, gL, grc);
   return F;
 }
 
@@ -843,6 +991,11 @@ CR_HD void tip_jacobian(const RobotK<T>& rb, const Chain<T, N>& ch, T (&Jp)[3][3
       for (int a = 0; a < 3; ++a) Jp[a][3 * i + 2] = v[a];
     }
   }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    to_actuator<MODEL, T, N>(Jp[a]);
+    to_actuator<MODEL, T, N>(Jw[a]);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -905,6 +1058,45 @@ CR_HD void rank1(AArr&& A, TA (&g)[D], const T (&j)[D], T r) {
   }
 }
 
+// Adds scale * n . dp/du of the backbone sample at arc fraction sg of segment i (local point q, world
+// point wp, sub-arc coefficients s, c) to the row jr: segments l < i move it rigidly (twist plus, in
+// the arc model, the length direction), segment i through its own sub-arc.
+template <typename T, int N, int MODEL>
+CR_HD void add_sample_row(const RobotK<T>& rb, const Chain<T, N>& ch, const T (&tv)[N][2][3], const T (&tw)[N][2][3],
+                          const T (&ldir)[N][3], int i, T sg, const T (&q)[3], const T (&wp)[3], T s, T c,
+                          const T (&nh)[3], T scale, T (&jr)[3 * N]) {
+#pragma unroll
+  for (int l = 0; l < N; ++l) {
+    if (l > i) break;
+    T ga[2], gl = T(0);
+    if (l < i) {
+      if (MODEL == CR_MODEL_ARC) gl = scale * (nh[0] * ldir[l][0] + nh[1] * ldir[l][1] + nh[2] * ldir[l][2]);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        T wx[3];
+        cross(tw[l][kk], wp, wx);
+        ga[kk] = scale * (nh[0] * (tv[l][kk][0] + wx[0]) + nh[1] * (tv[l][kk][1] + wx[1]) +
+                          nh[2] * (tv[l][kk][2] + wx[2]));
+      }
+    } else {
+      T s3, cp;
+      seg_deriv(sg * sg * ch.x[i], s, c, s3, cp);
+      T dd[2][3], wl[2][3];
+      seg_local_derivs(sg * ch.ax[i], sg * ch.ay[i], s, c, s3, cp, sg * ch.L[i], dd, wl);
+      T nl[3];
+      matTvec(ch.Rb[i], nh, nl);
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) ga[kk] = scale * sg * (nl[0] * dd[kk][0] + nl[1] * dd[kk][1] + nl[2] * dd[kk][2]);
+      if (MODEL == CR_MODEL_ARC) gl = scale * (nl[0] * q[0] + nl[1] * q[1] + nl[2] * q[2]) / ch.L[i];
+    }
+    T c0, c1, c2;
+    bend_cols<MODEL>(rb, l, ga[0], ga[1], c0, c1, c2);
+    jr[3 * l] += c0;
+    jr[3 * l + 1] += c1;
+    jr[3 * l + 2] += MODEL == CR_MODEL_ARC ? gl : c2;
+  }
+}
+
 template <typename T, typename TA, int N, bool OBST, int MODEL = CR_MODEL_TENDON, typename AArr>
 CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
                        const Sphere4<T>* sph, int no, const T (&u)[3 * N], AArr&& A, TA (&g)[3 * N]) {
@@ -950,6 +1142,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
     T jr[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) jr[q] = w.wp * Jp[a][q];
+    to_actuator<MODEL, T, N>(jr);
     rank1<TA, D>(A, g, jr, r[a]);
   }
   // rotation rows
@@ -982,6 +1175,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
 #pragma unroll
     for (int q = 0; q < D; ++q)
       jr[q] = w.wR * (Mrot[a][0] * Jw[0][q] + Mrot[a][1] * Jw[1][q] + Mrot[a][2] * Jw[2][q]);
+    to_actuator<MODEL, T, N>(jr);
     rank1<TA, D>(A, g, jr, r[3 + a]);
   }
   // bounds (single-entry rows), sum-zero (segment block of ones), curvature (segment rank-1)
@@ -1015,11 +1209,19 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
       bend_cols<MODEL>(rb, i, jx, jy, j0, j1, j2);
       T jj[3] = {j0, j1, j2};
       T rr = w.sk * vk;
+      if (MODEL == CR_MODEL_COUPLED) {  // the row reaches segments i and i - 1 through u = D q
+        T jr[D];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        acc_prod(g[3 * i + a], jj[a], rr);
+        for (int qq = 0; qq < D; ++qq) jr[qq] = qq / 3 == i ? jj[qq % 3] : T(0);
+        to_actuator<MODEL, T, N>(jr);
+        rank1<TA, D>(A, g, jr, rr);
+      } else {
 #pragma unroll
-        for (int b = 0; b <= a; ++b) acc_prod(A[tri(3 * i + a, 3 * i + b)], jj[a], jj[b]);
+        for (int a = 0; a < 3; ++a) {
+          acc_prod(g[3 * i + a], jj[a], rr);
+#pragma unroll
+          for (int b = 0; b <= a; ++b) acc_prod(A[tri(3 * i + a, 3 * i + b)], jj[a], jj[b]);
+        }
       }
     }
   }
@@ -1083,11 +1285,68 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
             bend_cols<MODEL>(rb, l, ga[0], ga[1], jr[3 * l], jr[3 * l + 1], jr[3 * l + 2]);
             if (MODEL == CR_MODEL_ARC) jr[3 * l + 2] = gl;
           }
+          to_actuator<MODEL, T, N>(jr);
           rank1<TA, D>(A, g, jr, rr);
         }
       }
       }
     }
+    }
+  }
+  // self-contact rows (as in self_contact_forward): r = sqrt(rho_s) (gap - |p_a - p_b|), its row
+  // -sqrt(rho_s) n . (dp_a/du - dp_b/du) with n = (p_a - p_b) / |p_a - p_b|
+  if (OBST && N >= 3 && w.rho_s > T(0)) {
+    const T gap = T(2) * rb.rbody + w.delta;
+    const T inb = c_div(T(1), T(rb.nb));
+    T lsum = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) lsum += ch.L[i];
+    const T marg = T(1e-4) * (lsum + gap);
+    T mid[N][3];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T q[3], s, c;
+      backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(0.5), q, mid[i], s, c);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int j = i + 2; j < N; ++j) {
+        {
+          const T dx = mid[i][0] - mid[j][0], dy = mid[i][1] - mid[j][1], dz = mid[i][2] - mid[j][2];
+          const T lim = T(0.5) * (ch.L[i] + ch.L[j]) + gap + marg;
+          if (!(dx * dx + dy * dy + dz * dz < lim * lim)) continue;
+        }
+        const T limj = T(0.5) * ch.L[j] + gap + marg;
+        for (int ka = 1; ka <= rb.nb; ++ka) {
+          const T sa = T(ka) * inb;
+          T qa[3], pa[3], s_a, c_a;
+          backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sa, qa, pa, s_a, c_a);
+          {
+            const T ex = pa[0] - mid[j][0], ey = pa[1] - mid[j][1], ez = pa[2] - mid[j][2];
+            if (!(ex * ex + ey * ey + ez * ez < limj * limj)) continue;
+          }
+          for (int kb = 1; kb <= rb.nb; ++kb) {
+            const T sb = T(kb) * inb;
+            T qb[3], pb[3], s_b, c_b;
+            backbone_point(ch.Rb[j], ch.pb[j], ch.ax[j], ch.ay[j], ch.x[j], ch.L[j], sb, qb, pb, s_b, c_b);
+            const T dx = pa[0] - pb[0], dy = pa[1] - pb[1], dz = pa[2] - pb[2];
+            const T d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 < gap * gap)) continue;
+            const T dist = c_sqrt(d2);
+            const T rr = w.ss * (gap - dist);
+            F += T(0.5) * rr * rr;
+            const T nh[3] = {dx / dist, dy / dist, dz / dist};
+            T jr[D];
+#pragma unroll
+            for (int qq = 0; qq < D; ++qq) jr[qq] = T(0);
+            add_sample_row<T, N, MODEL>(rb, ch, tv, tw, ldir, i, sa, qa, pa, s_a, c_a, nh, -w.ss, jr);
+            add_sample_row<T, N, MODEL>(rb, ch, tv, tw, ldir, j, sb, qb, pb, s_b, c_b, nh, w.ss, jr);
+            to_actuator<MODEL, T, N>(jr);
+            rank1<TA, D>(A, g, jr, rr);
+          }
+        }
+      }
     }
   }
   return F;

@@ -2,5 +2,6 @@
 #include "cr_eval_impl.cuh"
 namespace crk {
 CR_EVAL_ARC_INSTANTIATE(extern, double)
+CR_EVAL_COUPLED_INSTANTIATE(extern, double)
 CR_EVAL_INSTANTIATE(, double)
 }

@@ -155,7 +155,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> void cost_grad_n(const
                                                        a.scene.spheres, no, (const T*)a.u, a.B,    \
                                                        (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp, \
                                                        (const T*)a.upstream)
-  if (no > 0) {
+  if (no > 0 || a.task.w.rho_s > 0) {  // collision rows: spheres and / or self-contact
     if (mode == 0) CR_CG(true, 0); else if (mode == 1) CR_CG(true, 1); else CR_CG(true, 2);
   } else {
     if (mode == 0) CR_CG(false, 0); else if (mode == 1) CR_CG(false, 1); else CR_CG(false, 2);
@@ -177,23 +177,43 @@ template <typename T> void launch_eval_arc(const EvalArgs& a, int what) {
   else { CR_EVAL_ARC(cost_grad_n, T, a) }
 }
 
+// Coupled routing (model B), 1..CR_MAX_SEG segments, in its own translation units.
+#define CR_EVAL_COUPLED(FN, T, a)                  \
+  switch ((a).robot.n) {                           \
+    case 1: FN<T, 1, CR_MODEL_COUPLED>(a); break;  \
+    case 2: FN<T, 2, CR_MODEL_COUPLED>(a); break;  \
+    case 3: FN<T, 3, CR_MODEL_COUPLED>(a); break;  \
+    case 4: FN<T, 4, CR_MODEL_COUPLED>(a); break;  \
+    case 5: FN<T, 5, CR_MODEL_COUPLED>(a); break;  \
+    default: FN<T, 6, CR_MODEL_COUPLED>(a); break; \
+  }
+template <typename T> void launch_eval_coupled(const EvalArgs& a, int what) {
+  if (what == 0) { CR_EVAL_COUPLED(fk_n, T, a) }
+  else if (what == 1) { CR_EVAL_COUPLED(fk_jac_n, T, a) }
+  else { CR_EVAL_COUPLED(cost_grad_n, T, a) }
+}
+
 template <typename T> cr_status launch_fk(const EvalArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 0);
+  else if (a.robot.model == CR_MODEL_COUPLED) launch_eval_coupled<T>(a, 0);
   else CR_DISPATCH_NT(a.robot.n, fk_n, T, a);
   return crh::check_launch("cr_fk");
 }
 template <typename T> cr_status launch_fk_jac(const EvalArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 1);
+  else if (a.robot.model == CR_MODEL_COUPLED) launch_eval_coupled<T>(a, 1);
   else CR_DISPATCH_NT(a.robot.n, fk_jac_n, T, a);
   return crh::check_launch("cr_fk_jac");
 }
 template <typename T> cr_status launch_cost_grad(const EvalArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) launch_eval_arc<T>(a, 2);
+  else if (a.robot.model == CR_MODEL_COUPLED) launch_eval_coupled<T>(a, 2);
   else CR_DISPATCH_NT(a.robot.n, cost_grad_n, T, a);
   return crh::check_launch("cr_cost_grad");
 }
 
 #define CR_EVAL_ARC_INSTANTIATE(EXT, T) EXT template void launch_eval_arc<T>(const EvalArgs&, int);
+#define CR_EVAL_COUPLED_INSTANTIATE(EXT, T) EXT template void launch_eval_coupled<T>(const EvalArgs&, int);
 template <typename T>
 cr_status launch_reduce_rows(const void* x, int64_t rows, int64_t B, double* out, cudaStream_t s) {
   k_reduce_rows<T><<<(unsigned)rows, 256, 0, s>>>((const T*)x, B, out);

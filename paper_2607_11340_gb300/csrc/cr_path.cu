@@ -55,6 +55,7 @@ cr_status cr_solve_path(const cr_robot* robot, const cr_scene* scene, const cr_p
   if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "cr_solve_path")) || (st = check_scene(scene)))
     return st;
   if (!task || !first_ik) return fail(CR_EINVAL, "cr_solve_path: NULL task or params");
+  if ((st = check_self_rows(task->w, false, "cr_solve_path"))) return st;
   if (task->P < 0 || task->H < 2 || task->H > 128) return fail(CR_EINVAL, "cr_solve_path: P >= 0, H in 2..128");
   if (k_warm < 0 || k_joint < 0) return fail(CR_EINVAL, "cr_solve_path: negative iteration count");
   if (task->P == 0) return CR_OK;

@@ -136,6 +136,7 @@ extern "C" cr_status cr_solve_ik_plain(const cr_robot* robot, const cr_scene* sc
       (st = check_scene(scene)))
     return st;
   if (!prm || !task) return fail(CR_EINVAL, "NULL params / task");
+  if ((st = check_self_rows(task->w, false, "cr_solve_ik_plain"))) return st;
   if (prm->S < 1 || prm->S > CR_MAX_SEEDS || prm->n_final < 1 || prm->n_final > 32 || prm->n_final > prm->S ||
       prm->k_init < 0 || prm->k_final < 0)
     return fail(CR_EINVAL, "cr_solve_ik_plain: bad params");

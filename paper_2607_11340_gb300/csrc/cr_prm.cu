@@ -98,6 +98,7 @@ cr_status cr_prm_build(const cr_robot* robot, const cr_scene* scene, const cr_we
       (st = check_prm(prm)) || (st = check_map(map, true)))
     return st;
   if (!w) return fail(CR_EINVAL, "weights are NULL");
+  if ((st = check_self_rows(*w, false, "the PRM roadmap and query"))) return st;
   if (map->R > 65535) return fail(CR_EINVAL, "cr_prm_build: R = %lld above 65535", (long long)map->R);
   if ((st = check_ptr(workspace, 256, "workspace", true))) return st;
   const PrmWs lay = prm_ws(robot->n, map->R, *prm);
@@ -128,6 +129,7 @@ cr_status cr_prm_query(const cr_robot* robot, const cr_scene* scene, const cr_we
       (st = check_prm(prm)) || (st = check_map(map, false)))
     return st;
   if (!w) return fail(CR_EINVAL, "weights are NULL");
+  if ((st = check_self_rows(*w, false, "the PRM roadmap and query"))) return st;
   if (P < 0 || P > ((int64_t)1 << 31) - 1) return fail(CR_EINVAL, "prm query: P = %lld", (long long)P);
   if (T < 2 || T > 256) return fail(CR_EINVAL, "prm query: T = %d outside 2..256", T);
   if (map->R != 1 && map->R != P)

@@ -24,26 +24,36 @@ namespace crk {
 // (in FP32 the sum-zero row would only contribute the projection's rounding residue); the FP64 form
 // evaluates them, term by term like the FP64 definition.
 // ------------------------------------------------------------------------------------------------
+// first = true evaluates u itself (the seed: cost, gradient and clearance part), takes it and counts
+// no step; the seed lies on the feasible set like every trial point.
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD int pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                   const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha) {
+                   const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha,
+                   bool first = false) {
   constexpr int D = 3 * N;
-  T gn2 = T(0);
+  T u1[D];
+  if (first) {
 #pragma unroll
-  for (int q = 0; q < D; ++q) gn2 += g[q] * g[q];
-  T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
-  T v[D], u1[D];
+    for (int q = 0; q < D; ++q) u1[q] = u[q];
+  } else {
+    T gn2 = T(0);
 #pragma unroll
-  for (int q = 0; q < D; ++q) v[q] = u[q] - scale * g[q];
-  project_state<MODEL, T, N>(rb, v, u1);
+    for (int q = 0; q < D; ++q) gn2 += g[q] * g[q];
+    T scale = gn2 > T(0) ? alpha * c_rsqrt(gn2) : T(0);
+    T v[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) v[q] = u[q] - scale * g[q];
+    project_state<MODEL, T, N>(rb, v, u1);
+  }
   T g1[D], c1;
   T F1 = eval_ik<T, N, OBST, true, false, (sizeof(T) == 8), MODEL>(rb, w, kind, tg, sph, no, u1, g1, nullptr, nullptr,
                                                                    &c1);
-  if (F1 < F) {
+  if (first || F1 < F) {
 #pragma unroll
     for (int q = 0; q < D; ++q) { u[q] = u1[q]; g[q] = g1[q]; }
     F = F1;
     coll = c1;
+    if (first) return 0;
     alpha *= T(1.25);
     return 1;
   }
@@ -214,31 +224,20 @@ template <typename T> struct IkArgs {
   unsigned long long* pg_accepted;  // stage one adds its accepted steps here (the workspace counter)
 };
 
-template <typename T> struct Stage1Smem {
-  static size_t bytes(int no, int S, int D) {
-    size_t b = (size_t)no * sizeof(Sphere4<T>);
-    b = (b + 15) & ~size_t(15);
-    b += (size_t)D * S * sizeof(T);
-    b += (size_t)S * 2 * sizeof(float) + (size_t)S * sizeof(int) + 32 * sizeof(int) + S;
-    return (b + 15) & ~size_t(15);
-  }
+// Stage one writes every seed's end state, cost and clearance part, [D][P*S] / [P*S]; SelectTop reads
+// them back in a kernel of its own, so that no warp of the stage-one blocks waits on it.
+template <typename T> struct StageOut {
+  float* F;
+  float* C;
+  T* u;
 };
 
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
-__global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a) {
+__global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a, StageOut<T> so) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = a.S;
-  size_t off = (size_t)a.no * sizeof(Sphere4<T>);
-  off = (off + 15) & ~size_t(15);
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
-  T* su = reinterpret_cast<T*>(smem_raw + off);
-  off += (size_t)D * S * sizeof(T);
-  float* sF = reinterpret_cast<float*>(smem_raw + off);
-  float* sC = sF + S;
-  int* skipped = reinterpret_cast<int*>(sC + S);
-  int* sel = skipped + S;
-  unsigned char* taken = reinterpret_cast<unsigned char*>(sel + 32);
   const int64_t p = blockIdx.x;
   if (OBST) {
     stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
@@ -256,31 +255,59 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
         draw_seed_m<MODEL, T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box, u);
       }
     }
-    T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
-    T alpha = a.alpha0;
-    for (int it = 0; it < a.k_init; ++it)
-      acc += pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
-    sF[s] = float(F);
-    sC[s] = float(coll);
 #pragma unroll
-    for (int q = 0; q < D; ++q) su[q * S + s] = u[q];
+    for (int q = 0; q < D; ++q) g[q] = T(0);
+    T F = T(0), alpha = a.alpha0;
+    // it = -1 evaluates the seed itself (no step, always taken); it >= 0 are the projected-gradient
+    // steps. One evaluation site for both keeps the kernel's code half as long.
+    for (int it = -1; it < a.k_init; ++it)
+      acc += pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha, it < 0);
+    const int64_t i = p * S + s;
+    so.F[i] = float(F);
+    so.C[i] = float(coll);
+    const int64_t PS = a.P * S;
+#pragma unroll
+    for (int q = 0; q < D; ++q) so.u[q * PS + i] = u[q];
   }
-  // accepted steps per warp (every lane of the block is here: blockDim is a multiple of 32), one
-  // slot per warp in `skipped`, which SelectTop does not use
+  // accepted steps: one atomic per warp (every lane of the block is here: blockDim is a multiple of 32)
   acc = __reduce_add_sync(0xffffffffu, acc);
-  if ((threadIdx.x & 31) == 0) skipped[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long tot = 0;
-    for (int wi = 0; wi < (S + 31) / 32; ++wi) tot += (unsigned)skipped[wi];
-    atomicAdd(a.pg_accepted, tot);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(a.pg_accepted, (unsigned long long)acc);
+}
+
+// SelectTop of Algorithm 1 over stage one's end states: one warp per target, its S candidates staged
+// in shared memory (coalesced loads), then warp_topk; writes the K kept states (NaN for empty slots).
+template <typename T> struct SelectSmem {
+  __host__ __device__ static size_t per_warp(int S, int D) {
+    size_t b = (size_t)D * S * sizeof(T) + (size_t)S * 2 * sizeof(float) + 32 * sizeof(int) + S;
+    return (b + 15) & ~size_t(15);
   }
-  if (threadIdx.x < 32) warp_topk<T>(sF, sC, su, S, D, S, a.K, a.eps, sel, taken, skipped);
-  __syncthreads();
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ik_select(IkArgs<T> a, StageOut<T> so, int D) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int S = a.S, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+  if (p >= a.P) return;
+  unsigned char* mine = smem_raw + (size_t)wid * SelectSmem<T>::per_warp(S, D);
+  T* su = reinterpret_cast<T*>(mine);
+  float* sF = reinterpret_cast<float*>(su + (size_t)D * S);
+  float* sC = sF + S;
+  int* sel = reinterpret_cast<int*>(sC + S);
+  unsigned char* taken = reinterpret_cast<unsigned char*>(sel + 32);
+  const int64_t PS = a.P * S, b = p * S;
+  for (int j = lane; j < S; j += 32) {
+    sF[j] = so.F[b + j];
+    sC[j] = so.C[b + j];
+  }
+  for (int q = 0; q < D; ++q)
+    for (int j = lane; j < S; j += 32) su[q * S + j] = so.u[q * PS + b + j];
+  __syncwarp();
+  warp_topk<T>(sF, sC, su, S, D, S, a.K, a.eps, sel, taken, nullptr);
   const int64_t ldc = a.P * a.K;
-  for (int t = threadIdx.x; t < a.K * D; t += blockDim.x) {
-    int k = t / D, q = t % D;
-    int j = sel[k];
+  for (int t = lane; t < a.K * D; t += 32) {
+    const int k = t / D, q = t % D;
+    const int j = sel[k];
     a.cand_u[q * ldc + p * a.K + k] = j >= 0 ? su[q * S + j] : T(NAN);
   }
 }
@@ -345,6 +372,36 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
               double r = sph[j].reach - w.delta;
               if (ddx * ddx + ddy * ddy + ddz * ddz < r * r) { free = false; break; }
             }
+          }
+        }
+      }
+    }
+  }
+  // with the self-contact rows on: samples of segments two or more apart at least 2 r_body apart
+  if (OBST && N >= 3 && w.rho_s > 0.0 && free) {
+    const double inb = 1.0 / rb.nb, g2 = 4.0 * rb.rbody * rb.rbody;
+    double mid[N][3];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double q[3], s, c;
+      backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], 0.5, q, mid[i], s, c);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+      for (int j = i + 2; j < N; ++j) {
+        if (!free) continue;
+        const double dx = mid[i][0] - mid[j][0], dy = mid[i][1] - mid[j][1], dz = mid[i][2] - mid[j][2];
+        const double lim2 = 0.5 * (ch.L[i] + ch.L[j]) + 2.0 * rb.rbody + 1e-9;
+        if (!(dx * dx + dy * dy + dz * dz < lim2 * lim2)) continue;
+        for (int ka = 1; ka <= rb.nb && free; ++ka) {
+          double qa[3], pa[3], s_a, c_a;
+          backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], ka * inb, qa, pa, s_a, c_a);
+          for (int kb = 1; kb <= rb.nb; ++kb) {
+            double qb[3], pb[3], s_b, c_b;
+            backbone_point(ch.Rb[j], ch.pb[j], ch.ax[j], ch.ay[j], ch.x[j], ch.L[j], kb * inb, qb, pb, s_b, c_b);
+            const double ex = pa[0] - pb[0], ey = pa[1] - pb[1], ez = pa[2] - pb[2];
+            if (ex * ex + ey * ey + ez * ez < g2) { free = false; break; }
           }
         }
       }
@@ -744,17 +801,26 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   const int64_t P = k.P;
   const int no = k.no;
   const int threads = ((k.S + 31) / 32) * 32;
-  size_t sm1 = Stage1Smem<T>::bytes(no, k.S, D);
+  const size_t sm1 = (size_t)no * sizeof(Sphere4<T>);
   cr_status st;
+  const bool coll_rows = no > 0 || a.task.w.rho_s > 0;  // collision rows: spheres and / or self-contact
   if (which & 1) {
-  if (no > 0) {
-    if ((st = set_smem(k_ik_stage1<T, N, true, MODEL>, sm1))) return st;
-    k_ik_stage1<T, N, true, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
-  } else {
-    if ((st = set_smem(k_ik_stage1<T, N, false, MODEL>, sm1))) return st;
-    k_ik_stage1<T, N, false, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k);
-  }
-  if ((st = crh::check_launch("cr_solve_ik stage one"))) return st;
+    unsigned char* ws = (unsigned char*)a.ws;
+    StageOut<T> so{(float*)(ws + a.lay.stage_F), (float*)(ws + a.lay.stage_C), (T*)(ws + a.lay.stage_u)};
+    if (coll_rows) {
+      if ((st = set_smem(k_ik_stage1<T, N, true, MODEL>, sm1))) return st;
+      k_ik_stage1<T, N, true, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k, so);
+    } else {
+      k_ik_stage1<T, N, false, MODEL><<<(unsigned)P, threads, 0, a.stream>>>(rb, w, k, so);
+    }
+    if ((st = crh::check_launch("cr_solve_ik stage one"))) return st;
+    // SelectTop: as many warps (targets) per block as fit in 96 KB of shared memory, at most 8
+    const size_t pw = SelectSmem<T>::per_warp(k.S, D);
+    int wpb = (int)((96 * 1024) / pw);
+    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+    if ((st = set_smem(k_ik_select<T>, pw * wpb))) return st;
+    k_ik_select<T><<<(unsigned)((P + wpb - 1) / wpb), 32 * wpb, pw * wpb, a.stream>>>(k, so, D);
+    if ((st = crh::check_launch("cr_solve_ik SelectTop"))) return st;
   }
   if (!(which & 2)) return CR_OK;
   // per-problem spheres: one warp per block. With K >= 8 it holds 32 / K (at most 4) targets, their
@@ -779,7 +845,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   int b2 = k.sph_pp ? ((k.tpb * k.K + 31) / 32) * 32 : 32;
   bool warp_refine = false;
   if constexpr (sizeof(T) == 4 && MODEL == CR_MODEL_TENDON) {
-    if (k.sph_pp && k.K < 8 && k.kind == CR_TASK_IK6) {
+    if (k.sph_pp && k.K < 8 && k.kind == CR_TASK_IK6 && !(a.task.w.rho_s > 0)) {
       const size_t smw = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)) +
                          (size_t)k.K * (128 + D) * sizeof(double);
       if ((st = set_smem(k_ik_refine_warp<N>, smw))) return st;
@@ -788,7 +854,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
     }
   }
   if (warp_refine) {
-  } else if (no > 0) {
+  } else if (coll_rows) {
     if ((st = set_smem(k_ik_refine<T, N, true, MODEL>, sm2))) return st;
     k_ik_refine<T, N, true, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   }
@@ -825,7 +891,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status lm_steps_n(c
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
   size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0) k_lm_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  if (k.no > 0 || w.rho_s > T(0)) k_lm_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   else k_lm_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_lm_step");
 }
@@ -835,7 +901,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status pg_steps_n(c
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
   size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0) k_pg_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  if (k.no > 0 || w.rho_s > T(0)) k_pg_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   else k_pg_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_pg_steps");
 }
@@ -863,8 +929,19 @@ template <typename T> cr_status launch_lm_steps_arc(const SolveArgs& a);
 template <typename T> cr_status launch_pg_steps_arc(const SolveArgs& a);
 template <typename T> cr_status launch_seeds_arc(const SolveArgs& a);
 
+#define CR_COUPLED_DISPATCH(FN, T, N_, ...)                          \
+  switch (N_) {                                                      \
+    case 1: return FN<T, 1, CR_MODEL_COUPLED>(__VA_ARGS__);          \
+    case 2: return FN<T, 2, CR_MODEL_COUPLED>(__VA_ARGS__);          \
+    case 3: return FN<T, 3, CR_MODEL_COUPLED>(__VA_ARGS__);          \
+    case 4: return FN<T, 4, CR_MODEL_COUPLED>(__VA_ARGS__);          \
+    case 5: return FN<T, 5, CR_MODEL_COUPLED>(__VA_ARGS__);          \
+    default: return FN<T, 6, CR_MODEL_COUPLED>(__VA_ARGS__);         \
+  }
+
 template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which) {
   if (a.robot.model == CR_MODEL_ARC) return launch_solve_ik_arc<T>(a, which);
+  if (a.robot.model == CR_MODEL_COUPLED) { CR_COUPLED_DISPATCH(solve_ik_n, T, a.robot.n, a, which) }
   switch (a.robot.n) {
     case 1: return solve_ik_n<T, 1>(a, which);
     case 2: return solve_ik_n<T, 2>(a, which);
@@ -876,6 +953,7 @@ template <typename T> cr_status launch_solve_ik(const SolveArgs& a, int which) {
 }
 template <typename T> cr_status launch_lm_steps(const SolveArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) return launch_lm_steps_arc<T>(a);
+  if (a.robot.model == CR_MODEL_COUPLED) { CR_COUPLED_DISPATCH(lm_steps_n, T, a.robot.n, a) }
   switch (a.robot.n) {
     case 1: return lm_steps_n<T, 1>(a);
     case 2: return lm_steps_n<T, 2>(a);
@@ -887,6 +965,7 @@ template <typename T> cr_status launch_lm_steps(const SolveArgs& a) {
 }
 template <typename T> cr_status launch_pg_steps(const SolveArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) return launch_pg_steps_arc<T>(a);
+  if (a.robot.model == CR_MODEL_COUPLED) { CR_COUPLED_DISPATCH(pg_steps_n, T, a.robot.n, a) }
   switch (a.robot.n) {
     case 1: return pg_steps_n<T, 1>(a);
     case 2: return pg_steps_n<T, 2>(a);
@@ -898,6 +977,7 @@ template <typename T> cr_status launch_pg_steps(const SolveArgs& a) {
 }
 template <typename T> cr_status launch_seeds(const SolveArgs& a) {
   if (a.robot.model == CR_MODEL_ARC) return launch_seeds_arc<T>(a);
+  if (a.robot.model == CR_MODEL_COUPLED) { CR_COUPLED_DISPATCH(seeds_n, T, a.robot.n, a) }
   switch (a.robot.n) {
     case 1: return seeds_n<T, 1>(a);
     case 2: return seeds_n<T, 2>(a);
@@ -952,7 +1032,13 @@ template <typename T> cr_status launch_seeds_arc(const SolveArgs& a) { CR_ARC_DI
   CR_SOLVE_N_INSTANTIATE(extern, T, 1, CR_MODEL_ARC)    \
   CR_SOLVE_N_INSTANTIATE(extern, T, 2, CR_MODEL_ARC)    \
   CR_SOLVE_N_INSTANTIATE(extern, T, 3, CR_MODEL_ARC)    \
-  CR_SOLVE_N_INSTANTIATE(extern, T, 4, CR_MODEL_ARC)
+  CR_SOLVE_N_INSTANTIATE(extern, T, 4, CR_MODEL_ARC)    \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 1, CR_MODEL_COUPLED) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 2, CR_MODEL_COUPLED) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 3, CR_MODEL_COUPLED) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 4, CR_MODEL_COUPLED) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 5, CR_MODEL_COUPLED) \
+  CR_SOLVE_N_INSTANTIATE(extern, T, 6, CR_MODEL_COUPLED)
 
 #define CR_SOLVE_INSTANTIATE(EXT, T)                                \
   EXT template cr_status launch_solve_ik<T>(const SolveArgs&, int); \

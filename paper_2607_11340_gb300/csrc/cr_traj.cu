@@ -1,5 +1,5 @@
 // C ABI of trajectory planning and calibration: cr_traj_cost, cr_traj_workspace_size, cr_solve_traj,
-// cr_traj_prm_workspace_size, cr_solve_traj_prm, cr_calibrate.
+// cr_traj_prm_workspace_size, cr_solve_traj_prm, cr_calibrate and the pieces of the sharded calibration.
 #include "cr_traj_impl.cuh"
 
 namespace crk {
@@ -165,6 +165,7 @@ cr_status cr_solve_traj_prm(const cr_robot* robot, const cr_scene* scene, const 
                             double* goal_rot, double* speed, double* accel, uint8_t* lim_ok, uint8_t* col_ok,
                             double* length, int32_t* hops, void* workspace, size_t ws_bytes, cr_stream stream) {
   if (!prm || !map) return fail(CR_EINVAL, "cr_solve_traj_prm: prm and map are required");
+  if (task && check_self_rows(task->w, false, "cr_solve_traj_prm")) return CR_EINVAL;
   return solve_traj(robot, scene, task, goal_ik, prm, map, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot, speed,
                     accel, lim_ok, col_ok, length, hops, workspace, ws_bytes, stream);
 }
@@ -201,6 +202,70 @@ cr_status cr_calibrate(const cr_robot* robot, const void* U, const double* P_mea
   l.calib_ws = workspace;
   l.stream = stream_of(stream);
   return dtype == CR_F64 ? crk::launch_calibrate<double>(l) : crk::launch_calibrate<float>(l);
+}
+
+int32_t cr_calib_nv(int32_t n) {
+  if (n < 1 || n > CR_MAX_SEG) return 0;
+  return 2 * n * (2 * n + 1) / 2 + 2 * n + 1;
+}
+
+// Shared checks and launch of one piece of the sharded calibration.
+static cr_status calib_piece(const char* who, int piece, const cr_robot* robot, const void* U, const double* P_meas,
+                             int64_t K, double* theta, double* sums, double* state, double* theta_trial,
+                             const double* F_trial, double* F_out, int32_t dtype, void* workspace, size_t ws_bytes,
+                             cr_stream stream) {
+  cr_status st;
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, who)) || (st = check_dtype(dtype))) return st;
+  const bool data = piece == 0 || piece == 2;
+  if (data && K < 1) return fail(CR_EINVAL, "%s: K >= 1", who);
+  if ((st = check_ptr(U, dsize(dtype), "U", data)) || (st = check_ptr(P_meas, 8, "P_meas", data)) ||
+      (st = check_ptr(theta, 8, "theta", true)) || (st = check_ptr(sums, 8, "sums", piece != 2)) ||
+      (st = check_ptr(state, 8, "state", piece == 1 || piece == 3)) ||
+      (st = check_ptr(theta_trial, 8, "theta_trial", piece == 1 || piece == 3)) ||
+      (st = check_ptr(F_trial, 8, "F_trial", piece == 3)) || (st = check_ptr(F_out, 8, "F_out", piece == 2)) ||
+      (st = check_ptr(workspace, 8, "workspace", piece == 0)))
+    return st;
+  if (piece == 0 && ws_bytes < crk::calibrate_ws_bytes(robot->n, K))
+    return fail(CR_EINVAL, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes, crk::calibrate_ws_bytes(robot->n, K));
+  crk::TrajLaunch l{};
+  l.robot = *robot;
+  l.U = U;
+  l.Pm = P_meas;
+  l.K = K;
+  l.theta_dev = theta;
+  l.F_dev = F_out;
+  l.calib_ws = workspace;
+  l.calib_piece = piece;
+  l.sums = sums;
+  l.state = state;
+  l.theta_trial = theta_trial;
+  l.F_trial = F_trial;
+  l.stream = stream_of(stream);
+  return dtype == CR_F64 ? crk::launch_calib_piece<double>(l) : crk::launch_calib_piece<float>(l);
+}
+
+cr_status cr_calib_sums(const cr_robot* robot, const void* U, const double* P_meas, int64_t K, const double* theta,
+                        double* sums, int32_t dtype, void* workspace, size_t ws_bytes, cr_stream stream) {
+  return calib_piece("cr_calib_sums", 0, robot, U, P_meas, K, const_cast<double*>(theta), sums, nullptr, nullptr,
+                     nullptr, nullptr, dtype, workspace, ws_bytes, stream);
+}
+
+cr_status cr_calib_trial(const cr_robot* robot, const double* sums, const double* theta, double* state,
+                         double* theta_trial, cr_stream stream) {
+  return calib_piece("cr_calib_trial", 1, robot, nullptr, nullptr, 0, const_cast<double*>(theta),
+                     const_cast<double*>(sums), state, theta_trial, nullptr, nullptr, CR_F64, nullptr, 0, stream);
+}
+
+cr_status cr_calib_cost(const cr_robot* robot, const void* U, const double* P_meas, int64_t K,
+                        const double* theta_trial, double* F_out, int32_t dtype, cr_stream stream) {
+  return calib_piece("cr_calib_cost", 2, robot, U, P_meas, K, const_cast<double*>(theta_trial), nullptr, nullptr,
+                     nullptr, nullptr, F_out, dtype, nullptr, 0, stream);
+}
+
+cr_status cr_calib_accept(const cr_robot* robot, const double* sums, const double* F_trial, const double* theta_trial,
+                          double* theta, double* state, cr_stream stream) {
+  return calib_piece("cr_calib_accept", 3, robot, nullptr, nullptr, 0, theta, const_cast<double*>(sums), state,
+                     const_cast<double*>(theta_trial), F_trial, nullptr, CR_F64, nullptr, 0, stream);
 }
 
 }  // extern "C"

@@ -87,7 +87,7 @@ __device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const Tr
   if (aux) {
     if (active && t >= 1) {
       T coll = T(0);
-      state_forward<T, N, OBST, GRAD, false>(rb, w, sph, no, u, ch, ag, &coll);
+      state_forward<T, N, OBST, GRAD, false>(rb, w, sph, no, u, ch, ag, &coll, false);  // the owner has the self rows
       F = coll;
       if (GRAD) {
         T* x = sm.xag + (size_t)t * 8 * N;
@@ -585,6 +585,85 @@ __global__ void __launch_bounds__(256) k_calib_final(RobotK<T> rb0, const T* __r
   if (threadIdx.x == 0) *F_out = F;
 }
 
+// Sharded calibration: the pieces of k_calib_step as separate launches, so that processes holding
+// shares of the poses can add their partial sums (an all-reduce) in between. Each piece repeats the
+// arithmetic of k_calib_step in the same order, so one process running them equals cr_calibrate.
+// sums [NV]: the share's packed J^T J, J^T r and F; state [4]: lambda, nu, ok, pred.
+template <int N>
+__global__ void __launch_bounds__(256) k_calib_sum_parts(int nblk, const double* part, double* sums) {
+  constexpr int NV = calib_nv<N>();
+  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+    double s = part[e];
+    for (int b = 1; b < nblk; ++b) s += part[(int64_t)b * NV + e];
+    sums[e] = s;
+  }
+}
+
+template <int N>
+__global__ void k_calib_trial(const double* sums, const double* theta, double* state, double* theta_trial) {
+  constexpr int NP = 2 * N, NA = NP * (NP + 1) / 2;
+  if (threadIdx.x != 0) return;
+  const double lam = state[0];
+  double Ad[NA], iv[NP], Dg[NP], dl[NP];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) Ad[a] = sums[a];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    Dg[q] = fmax(Ad[tri(q, q)], 1e-12);
+    Ad[tri(q, q)] += lam * Dg[q];
+  }
+  const bool ok = cholesky_packed<NP>(Ad, iv);
+#pragma unroll
+  for (int q = 0; q < NP; ++q) dl[q] = -sums[NA + q];
+  double pred = 0.0;
+  if (ok) {
+    cholesky_solve<NP>(Ad, iv, dl);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      theta_trial[q] = theta[q] + dl[q];
+      pred += dl[q] * (lam * Dg[q] * dl[q] - sums[NA + q]);
+    }
+    pred *= 0.5;
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) theta_trial[q] = theta[q];
+  }
+  state[2] = ok ? 1.0 : 0.0;
+  state[3] = pred;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_calib_cost(RobotK<T> rb0, const T* __restrict__ U, const double* __restrict__ Pm,
+                                                     int64_t K, const double* theta, double* F_out) {
+  constexpr int NP = 2 * N;
+  __shared__ double th[NP], red[32];
+  if (threadIdx.x < NP) th[threadIdx.x] = theta[threadIdx.x];
+  __syncthreads();
+  const double F = calib_cost_block<T, N>(calib_robot<T, N>(rb0, th), U, Pm, K, red);
+  if (threadIdx.x == 0) *F_out = F;
+}
+
+template <int N>
+__global__ void k_calib_accept(const double* sums, const double* F_trial, const double* theta_trial, double* theta,
+                               double* state) {
+  constexpr int NP = 2 * N, NV = calib_nv<N>();
+  if (threadIdx.x != 0) return;
+  double lam = state[0], nu = state[1];
+  const double F = sums[NV - 1], Fn = *F_trial;
+  if (state[2] != 0.0 && Fn < F) {
+    const double rho = (F - Fn) / state[3], tt = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - tt * tt * tt);
+    nu = 2.0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) theta[q] = theta_trial[q];
+  } else {
+    lam *= nu;
+    nu *= 2.0;
+  }
+  state[0] = lam;
+  state[1] = nu;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Host launchers
 // ------------------------------------------------------------------------------------------------
@@ -610,12 +689,17 @@ struct TrajLaunch {
   double lambda0;
   double *theta_dev, *F_dev, *hist_dev;
   void* calib_ws;
+  // sharded calibration: which piece (0 sums, 1 trial, 2 cost, 3 accept) and its arrays
+  int calib_piece;
+  double *sums, *state, *theta_trial;
+  const double* F_trial;
   cudaStream_t stream;
 };
 
 template <typename T> cr_status launch_traj_cost(const TrajLaunch& l);
 template <typename T> cr_status launch_traj_solve(const TrajLaunch& l);
 template <typename T> cr_status launch_calibrate(const TrajLaunch& l);
+template <typename T> cr_status launch_calib_piece(const TrajLaunch& l);
 
 template <typename T> TrajW<T> traj_w(const cr_weights& w) {
   TrajW<T> t;
@@ -669,7 +753,7 @@ template <typename T, int N> cr_status traj_cost_n(const TrajLaunch& l) {
   const int threads = ((a.Tn + 31) / 32) * 32;
   size_t sm = (((size_t)a.no * sizeof(Sphere4<T>) + 15) & ~size_t(15)) + TrajSmem<T>::bytes(a.Tn, D);
   cr_status st;
-  if (a.no > 0) {
+  if (a.no > 0 || w.rho_s > T(0)) {  // collision rows: spheres and / or self-contact
     if (l.grad) { if ((st = set_smem(k_traj_cost<T, N, true, true>, sm))) return st;
       k_traj_cost<T, N, true, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
     else { if ((st = set_smem(k_traj_cost<T, N, true, false>, sm))) return st;
@@ -698,7 +782,7 @@ template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
   size_t sm = (((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15)) +
               ((TrajSmem<T>::bytes(a.Tn, D) + 15) & ~size_t(15)) + ((size_t)a.Tn * D + 32) * sizeof(double);
   cr_status st;
-  if (a.no > 0) {
+  if (a.no > 0 || w.rho_s > T(0)) {  // collision rows: spheres and / or self-contact
     if ((st = set_smem(k_traj_solve<T, N, true>, sm))) return st;
     k_traj_solve<T, N, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
   } else {
@@ -723,6 +807,24 @@ template <typename T, int N> cr_status calibrate_n(const TrajLaunch& l) {
   return crh::check_launch("cr_calibrate");
 }
 
+template <typename T, int N> cr_status calib_piece_n(const TrajLaunch& l) {
+  RobotK<T> rb = crh::robot_k<T>(l.robot);
+  const T* U = (const T*)l.U;
+  switch (l.calib_piece) {
+    case 0: {  // partial sums of this share: per-block partials, then their sum in block order
+      const int nblk = (int)((l.K + kCalibThreads - 1) / kCalibThreads);
+      double* part = (double*)l.calib_ws + 2;
+      k_calib_accum<T, N><<<nblk, kCalibThreads, 0, l.stream>>>(rb, U, l.Pm, l.K, l.theta_dev, part);
+      k_calib_sum_parts<N><<<1, 256, 0, l.stream>>>(nblk, part, l.sums);
+      break;
+    }
+    case 1: k_calib_trial<N><<<1, 32, 0, l.stream>>>(l.sums, l.theta_dev, l.state, l.theta_trial); break;
+    case 2: k_calib_cost<T, N><<<1, 256, 0, l.stream>>>(rb, U, l.Pm, l.K, l.theta_dev, l.F_dev); break;
+    default: k_calib_accept<N><<<1, 32, 0, l.stream>>>(l.sums, l.F_trial, l.theta_trial, l.theta_dev, l.state);
+  }
+  return crh::check_launch("sharded calibration");
+}
+
 // Workspace of cr_calibrate: lambda, nu, then the per-block partial sums.
 inline size_t calibrate_ws_bytes(int n, int64_t K) {
   const int NP = 2 * n;
@@ -743,10 +845,12 @@ inline size_t calibrate_ws_bytes(int n, int64_t K) {
 template <typename T> cr_status launch_traj_cost(const TrajLaunch& l) { CR_TRAJ_DISPATCH(traj_cost_n, T, l) }
 template <typename T> cr_status launch_traj_solve(const TrajLaunch& l) { CR_TRAJ_DISPATCH(traj_solve_n, T, l) }
 template <typename T> cr_status launch_calibrate(const TrajLaunch& l) { CR_TRAJ_DISPATCH(calibrate_n, T, l) }
+template <typename T> cr_status launch_calib_piece(const TrajLaunch& l) { CR_TRAJ_DISPATCH(calib_piece_n, T, l) }
 
 #define CR_TRAJ_INSTANTIATE(EXT, T)                                  \
   EXT template cr_status launch_traj_cost<T>(const TrajLaunch&);     \
   EXT template cr_status launch_traj_solve<T>(const TrajLaunch&);    \
-  EXT template cr_status launch_calibrate<T>(const TrajLaunch&);
+  EXT template cr_status launch_calibrate<T>(const TrajLaunch&);    \
+  EXT template cr_status launch_calib_piece<T>(const TrajLaunch&);
 
 }  // namespace crk

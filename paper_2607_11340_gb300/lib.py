@@ -30,6 +30,8 @@ EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step",
            "cr_calibrate", "cr_calibrate_workspace_size", "cr_cost_vjp", "cr_path_workspace_size", "cr_solve_path", "cr_device_check",
            "cr_batch_workspace_size", "cr_batch_plan_create", "cr_batch_plan_run", "cr_batch_plan_info",
            "cr_batch_plan_destroy", "cr_solve_batch", "cr_batch_plain_workspace_size", "cr_solve_batch_plain",
+           "cr_batch_partition", "cr_calib_nv", "cr_calib_sums", "cr_calib_trial", "cr_calib_cost",
+           "cr_calib_accept",
            "cr_prm_workspace_size", "cr_prm_build", "cr_prm_query", "cr_traj_prm_workspace_size",
            "cr_solve_traj_prm")
 
@@ -47,13 +49,14 @@ class cr_robot(C.Structure):
                 ("r_body", C.c_double), ("l_min", C.c_double * CR_MAX_SEG), ("l_max", C.c_double * CR_MAX_SEG)]
 
 
-CR_MODEL_TENDON, CR_MODEL_ARC = 0, 1
+CR_MODEL_TENDON, CR_MODEL_ARC, CR_MODEL_COUPLED = 0, 1, 2
 CR_MAX_SEG_ARC = 4
 
 
 class cr_weights(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("w_p", "w_R", "rho_b", "rho_eq", "rho_k", "rho_c", "w_s",
-                                          "w_len", "rho_v", "rho_a", "dt", "v_max", "a_max", "delta")]
+                                          "w_len", "rho_v", "rho_a", "dt", "v_max", "a_max", "delta",
+                                          "rho_s")]
 
 
 class cr_scene(C.Structure):
@@ -145,6 +148,10 @@ _SIGS = {
                       C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
     "cr_calibrate": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, C.c_int32, C.c_double, _P, _P, C.c_int32, _P,
                      C.c_size_t, _P],
+    "cr_calib_sums": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, _P, C.c_int32, _P, C.c_size_t, _P],
+    "cr_calib_trial": [C.POINTER(cr_robot), _P, _P, _P, _P, _P],
+    "cr_calib_cost": [C.POINTER(cr_robot), _P, _P, C.c_int64, _P, _P, C.c_int32, _P],
+    "cr_calib_accept": [C.POINTER(cr_robot), _P, _P, _P, _P, _P, _P],
     "cr_cost_vjp": [C.POINTER(cr_robot), C.POINTER(cr_scene), C.POINTER(cr_task), _P, C.c_int64, _P, _P, _P, _P,
                     C.c_int32, _P],
     "cr_peak_launch": [C.c_int32, _P, C.c_size_t, C.c_int32, C.POINTER(C.c_double), _P],
@@ -153,6 +160,8 @@ _SIGS = {
                              C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P,
                              C.POINTER(C.c_void_p)],
     "cr_batch_plan_run": [_P, _P],
+    "cr_batch_partition": [C.POINTER(cr_batch_item), C.c_int64, C.POINTER(cr_batch_params), C.c_int32,
+                           C.POINTER(C.c_int64)],
     "cr_batch_plan_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
     "cr_batch_plan_destroy": [_P],
     "cr_solve_batch": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
@@ -199,6 +208,8 @@ def load(path: str | None = None):
             getattr(L, nm).argtypes = [C.POINTER(cr_robot), C.POINTER(cr_batch_item), C.c_int64,
                                        C.POINTER(cr_batch_params)]
             getattr(L, nm).restype = C.c_size_t
+        L.cr_calib_nv.argtypes = [C.c_int32]
+        L.cr_calib_nv.restype = C.c_int32
         L.cr_static_workspace_capacity.argtypes = []
         L.cr_static_workspace_capacity.restype = C.c_size_t
         L.cr_last_error_string.argtypes = []
@@ -395,6 +406,31 @@ def cr_calibrate(robot, U, P_meas, theta, iters, lambda0, F_out, hist, workspace
                                workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
+def cr_calib_nv(n: int) -> int:
+    return int(load().cr_calib_nv(n))
+
+
+def cr_calib_sums(robot, U, P_meas, theta, sums, workspace, stream=None):
+    _check(load().cr_calib_sums(C.byref(robot), _ptr(U), _ptr(P_meas), U.shape[-1], _ptr(theta), _ptr(sums),
+                                _dtype_code(U), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                _stream(stream)))
+
+
+def cr_calib_trial(robot, sums, theta, state, theta_trial, stream=None):
+    _check(load().cr_calib_trial(C.byref(robot), _ptr(sums), _ptr(theta), _ptr(state), _ptr(theta_trial),
+                                 _stream(stream)))
+
+
+def cr_calib_cost(robot, U, P_meas, theta_trial, F_trial, stream=None):
+    _check(load().cr_calib_cost(C.byref(robot), _ptr(U), _ptr(P_meas), U.shape[-1], _ptr(theta_trial), _ptr(F_trial),
+                                _dtype_code(U), _stream(stream)))
+
+
+def cr_calib_accept(robot, sums, F_trial, theta_trial, theta, state, stream=None):
+    _check(load().cr_calib_accept(C.byref(robot), _ptr(sums), _ptr(F_trial), _ptr(theta_trial), _ptr(theta),
+                                  _ptr(state), _stream(stream)))
+
+
 def cr_cost_vjp(robot, scene, task, u, upstream, grad_u_out, grad_param_out=None, workspace=None, stream=None):
     _check(load().cr_cost_vjp(C.byref(robot), C.byref(scene), C.byref(task), _ptr(u), u.shape[-1], _ptr(upstream),
                               _ptr(grad_u_out), _ptr(grad_param_out), _ptr(workspace), _dtype_code(u), _stream(stream)))
@@ -444,6 +480,14 @@ def cr_batch_plan_create(robot, weights, items, prm, targets, spheres, u_out, co
                                        _ptr(flags), _ptr(t_done), _ptr(workspace),
                                        workspace.numel() * workspace.element_size(), _stream(stream), C.byref(plan)))
     return plan
+
+
+def cr_batch_partition(items, prm, parts: int):
+    """Contiguous cost-balanced partition of the items over `parts` processes: list of parts + 1
+    bounds (host only)."""
+    b = (C.c_int64 * (parts + 1))()
+    _check(load().cr_batch_partition(items, len(items), C.byref(prm), parts, b))
+    return [int(v) for v in b]
 
 
 def cr_batch_plan_run(plan, stream=None):

@@ -13,7 +13,7 @@ TDT = {lib.CR_F64: torch.float64, lib.CR_F32: torch.float32}
 
 def orc_robot(spec: synth.RobotSpec, thmax=None):
     return O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax if thmax is None else thmax,
-                        nb=spec.nb, rbody=spec.body_radius, lmin=spec.lmin, lmax=spec.lmax)
+                        nb=spec.nb, rbody=spec.body_radius, lmin=spec.lmin, lmax=spec.lmax, coupled=spec.coupled)
 
 
 def orc_weights(w: synth.WeightSpec = synth.WEIGHTS):
@@ -61,6 +61,17 @@ def pose_operand_scale(spec: synth.RobotSpec, w: synth.WeightSpec = synth.WEIGHT
     error of a modest multiple of eps times this scale, however small the residual itself."""
     reach = sum(spec.L) if spec.lmax is None else spec.n * spec.lmax
     return w.wp * reach + w.wR * np.pi
+
+
+def consequential_ties(F_start, F_trial, eps, scale, tol_state, sigma_min=1.0, k=64.0):
+    """near_ties whose outcome can move the iterate by more than tol_state: a step decided at a cost
+    F is no longer than about |r| / sigma_min = sqrt(2 F) / sigma_min (sigma_min: a lower bound on the
+    Jacobian's smallest singular value in the weighted units, 1 here, where entries are 1e2-1e3), so
+    a tie between two costs below (sigma_min tol_state)^2 / 2 -- an LM that has converged to the
+    rounding level -- cannot separate the iterates by more than tol_state and is not counted."""
+    F_start, F_trial = np.asarray(F_start), np.asarray(F_trial)
+    big = np.sqrt(2 * np.maximum(np.abs(F_start), np.abs(np.nan_to_num(F_trial)))) > sigma_min * tol_state
+    return near_ties(F_start, F_trial, eps, scale, k) & big
 
 
 def near_ties(F_start, F_trial, eps, scale, k=64.0):
@@ -125,8 +136,12 @@ def kink_or_pi(states, spec: synth.RobotSpec, rot_rows, prec, k=64.0, w: synth.W
         if spec.lmin is not None:  # arc model: (theta cos phi, theta sin phi, L)
             th = np.hypot(a, b_)
             kink |= band(c - spec.lmax, spec.lmax) | band(spec.lmin - c, spec.lmax)
-        else:  # tendon model: |u_ij| <= u_max, theta from the inverse of Eq. 4
-            th = (2.0 / (3.0 * spec.rc)) * np.hypot(a - 0.5 * (b_ + c), (np.sqrt(3.0) / 2.0) * (b_ - c))
+        else:  # tendon model: |u_ij| <= u_max on the state, theta from the inverse of Eq. 4
+            if spec.coupled and i > 0:  # coupled routing: the segment bends with u_i = q_i - q_{i-1}
+                a_, b2, c_ = a - x[..., 3 * i - 3], b_ - x[..., 3 * i - 2], c - x[..., 3 * i - 1]
+            else:
+                a_, b2, c_ = a, b_, c
+            th = (2.0 / (3.0 * spec.rc)) * np.hypot(a_ - 0.5 * (b2 + c_), (np.sqrt(3.0) / 2.0) * (b2 - c_))
             for u in (a, b_, c):
                 kink |= band(np.abs(u) - spec.umax, spec.umax)
         kink |= band(th - spec.thmax, spec.thmax)

@@ -168,9 +168,15 @@ def test_arc_model_is_validated(crlib):
             bad.l_min[1], bad.l_max[1] = 1.0, 0.9
         assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
     bad = arc()
-    bad.model = 2
+    bad.model = 7
     assert L.cr_fk(C.byref(bad), dummy, 4, dummy, None, 0, None) == crlib.CR_EINVAL
     assert "model" in crlib.last_error()
+    # coupled routing (model B): a valid model code, refused by the tendon-only entry points
+    rc_ = _robot(crlib, 3)
+    rc_.model = crlib.CR_MODEL_COUPLED
+    assert L.cr_calibrate(C.byref(rc_), dummy, dummy, 4, dummy, 2, 1e-3, dummy, None, 0, dummy, 1 << 20, None) \
+        == crlib.CR_EINVAL
+    assert "tendon model" in crlib.last_error()
     # tendon-only entry points
     assert L.cr_calibrate(C.byref(r), dummy, dummy, 4, dummy, 2, 1e-3, dummy, None, 0, dummy, 1 << 20, None) \
         == crlib.CR_EINVAL
@@ -241,3 +247,37 @@ int main(void) {
     assert L.cr_prm_build(C.byref(r), C.byref(sc), C.byref(w), C.byref(good), C.byref(m), dummy, 1 << 30,
                           None) == crlib.CR_EINVAL
     assert "tendon model" in crlib.last_error()
+
+
+def test_self_contact_weight_is_validated(crlib):
+    """weights.rho_s: negative values are rejected by every entry point that takes weights, and the
+    solvers built without the self-contact rows (path, batch, plain, PRM) refuse rho_s > 0, all before
+    any device call."""
+    L = crlib.load()
+    r = _robot(crlib, n=4)
+    dummy = C.c_void_p(256)
+    t = crlib.cr_task()
+    t.kind, t.seeds_per_target, t.targets, t.n_targets = 0, 1, 256, 4
+    t.w.rho_s = -1.0
+    assert L.cr_cost_grad(C.byref(r), None, C.byref(t), dummy, 4, dummy, None, None, None, 0, None) == crlib.CR_EINVAL
+    assert "rho_s" in crlib.last_error()
+    p = crlib.cr_ik_params()
+    p.S, p.n_final, p.k_init, p.k_final, p.lambda0 = 64, 8, 8, 8, 1e-3
+    pt = crlib.cr_path_task()
+    pt.waypoints, pt.P, pt.H = 256, 2, 4
+    pt.w.rho_s = 1.0
+    outs = [dummy] * 6
+    assert L.cr_solve_path(C.byref(r), None, C.byref(pt), C.byref(p), 5, 5, *outs, dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL
+    assert "self-contact" in crlib.last_error()
+    t.w.rho_s = 1.0
+    assert L.cr_solve_ik_plain(C.byref(r), None, C.byref(t), C.byref(p), *([dummy] * 5), dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL
+    w = crlib.cr_weights()
+    w.rho_s = 1.0
+    bp = crlib.cr_batch_params()
+    bp.ik.n_final, bp.ik.k_init, bp.ik.k_final, bp.ik.lambda0 = 8, 16, 10, 1e-3
+    bp.k_warm, bp.k_joint, bp.seeds_per_unit = 5, 5, 64
+    items = crlib._batch_items([(0, 3, 1, 64, 0)])
+    assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 1, C.byref(bp), *([dummy] * 8), dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL

@@ -64,12 +64,18 @@ def test_batch_matches_plain_form_and_is_deterministic():
         assert torch.equal(first[k].nan_to_num(-7), getattr(s, k).nan_to_num(-7)), k
     plain = s.solve_plain()
     torch.cuda.synchronize()
-    # the same problems, seeds and settings: the same verdict on every item (the states themselves
-    # may differ: the batch kernel and the per-problem kernels are different compilation units,
-    # whose FP32 rounding may differ, and stage one amplifies that into other local minima)
+    # the same problems, seeds and settings. The states are not bit-identical: the batch kernel and
+    # the per-problem kernels are separate compilation units whose FP32 code (contractions, register
+    # allocation) differs in the last bits, and stage one carries that into other local minima. Both
+    # are compared on the unique part: the verdict per item; their states are each valid under the
+    # oracle (test_batch_results_valid_under_oracle).
     fb = s.flags.cpu().numpy() & 1
     fp = plain["flags"].cpu().numpy() & 1
-    assert (fb == fp).mean() >= 0.9, (fb, fp)
+    du = [float(np.abs(s.item_states(i).cpu().numpy() - s.item_states(i, plain["u"]).cpu().numpy()).max())
+          for i in range(len(fb))]
+    print(f"batch vs per-problem form: verdicts agree on {int((fb == fp).sum())} of {len(fb)} items; "
+          f"items with states within 2e-5 (m): {sum(d <= 2e-5 for d in du)}; largest state difference {max(du):.2e}")
+    assert np.sum(fb != fp) <= 1, (fb, fp)
     assert fb.sum() >= len(fb) // 2
 
 
@@ -124,7 +130,9 @@ def test_batch_success_rate_matches_oracle():
         else:
             o = O.solve_ik(rbo, orc_weights(), sp, 0, tg, cfg)
             succ_o[i] = bool(o["success"][0])
-    assert abs(succ_g.mean() - succ_o.mean()) <= 0.1, (succ_g.mean(), succ_o.mean())
+    print(f"40 items: success GPU {succ_g.mean():.3f} oracle {succ_o.mean():.3f}, mismatches {int((succ_g != succ_o).sum())}")
+    # the 1-point comparison runs on 200 items in tests/test_gpu_success_parity.py
+    assert np.sum(succ_g != succ_o) <= 2
 
 
 def test_batch_autotuned_plan_full_size_sample():
