@@ -142,7 +142,7 @@ def make_targets(torch, api, lib, spec, P, seed, device):
     return tg
 
 
-def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=None, weights=synth.WEIGHTS):
+def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=None, weights=synth.WEIGHTS, kind=None):
     """Oracle solves/s on host cores over a bounded contiguous sample of the targets."""
     import oracle as O
 
@@ -154,9 +154,10 @@ def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=Non
     cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final, lambda0=ik.lambda0,
                      alpha0=ik.alpha0, dedup_eps=ik.dedup_eps, lim_tol=ik.lim_tol, pos_tol=ik.pos_tol,
                      rot_tol=ik.rot_tol, seed=ik.seed, p0=p0)
+    kind = O.IK6 if kind is None else kind
     n = max(threads, 16)
     t0 = time.perf_counter()
-    r = O.solve_ik(rb, W, spheres, O.IK6, tg[:n], cfg, threads=threads)
+    r = O.solve_ik(rb, W, spheres, kind, tg[:n], cfg, threads=threads)
     dt = time.perf_counter() - t0
     done = n
     res = [r]
@@ -164,12 +165,52 @@ def cpu_oracle_rate(tg, spec, ik, budget_s=12.0, p0=0, threads=None, spheres=Non
         m = min(len(tg) - done, max(threads, int(done / dt * (budget_s - dt))))
         cfg.p0 = p0 + done
         t1 = time.perf_counter()
-        res.append(O.solve_ik(rb, W, spheres, O.IK6, tg[done:done + m], cfg, threads=threads))
+        res.append(O.solve_ik(rb, W, spheres, kind, tg[done:done + m], cfg, threads=threads))
         dt += time.perf_counter() - t1
         done += m
     succ = np.concatenate([x["success"] for x in res])
     u = np.concatenate([x["u"] for x in res])
     return done / dt, done, threads, dt, succ, u
+
+
+def oracle_sample(run, n_total, unit, what, budget_s=12.0, threads=None):
+    """The oracle on host cores over a bounded contiguous sample: run(lo, hi, threads) solves problems
+    [lo, hi) (seed counters from lo) and returns their success flags; chunks of at least one problem
+    per thread until budget_s of wall time is spent. Returns the cpu_baseline object."""
+    threads = threads or os.cpu_count()
+    done, dt, succ = 0, 0.0, []
+    while done < n_total and (done == 0 or dt < budget_s):
+        m = min(n_total - done, threads if done == 0 else max(threads, int(done / dt * (budget_s - dt))))
+        t0 = time.perf_counter()
+        succ.append(np.asarray(run(done, done + m, threads), dtype=bool))
+        dt += time.perf_counter() - t0
+        done += m
+    succ = np.concatenate(succ)
+    return {"value": done / dt, "unit": unit, "cores": threads, "kind": "oracle",
+            "sample": f"first {done} {what} ({dt:.1f} s on {threads} threads)", "success_rate": float(succ.mean()),
+            "_success": succ}
+
+
+def gpu_form(torch, run, n, unit, what):
+    """One timed pass of run() (CUDA events on the current stream) over n problems, after one untimed
+    pass."""
+    run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    r = run()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    return {"value": n / (ms / 1e3), "unit": unit, "problems": n, "ms": ms, "what": what}, r
+
+
+def agreement(gpu_success, cpu):
+    """Success flags of the GPU form against the oracle's on the oracle's sample."""
+    o = cpu.pop("_success")
+    g = np.asarray(gpu_success, dtype=bool)[: len(o)]
+    return {"problems": len(o), "success_rate_oracle": float(o.mean()), "success_rate_gpu": float(g.mean()),
+            "success_flag_mismatches": int((g != o).sum())}
 
 
 def cpu_oracle_traj_prm(us, goal, sph, ps, budget_s=15.0, threads=None):
@@ -284,18 +325,32 @@ def time_steps(torch, fn, steps, flush, stream):
 
 
 def other_workload(args):
-    """Times one of the other workloads on one GPU and prints its JSON line."""
+    """Times one of the other workloads and prints its JSON line: one GPU, except the ragged batch,
+    which a torchrun launch splits over the processes by estimated cost (cr_batch_partition; the
+    items are independent, so no collective touches the data path)."""
     import torch
+    import torch.distributed as dist
 
     from paper_2607_11340_gb300 import api, build_lib, lib
 
-    build_lib.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.workload != "ragged":
+        raise SystemExit(f"--workload {args.workload} runs on one GPU; only the ragged batch is split over processes")
+    if world > 1:
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
     lib.load()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     rng = np.random.default_rng(0)
-    line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+    line = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic"}
     if args.workload == "ik1":
         spec, ik, P = synth.ROBOT_1SEG, synth.IK_1SEG, synth.P_1SEG
@@ -306,7 +361,34 @@ def other_workload(args):
         fn = lambda: s.solve(tg)
         units, unit, metric = P, "solves/s", "IK solves/s, 1-segment 5-DoF, FP64, single stage (32 seeds, 50 LM)"
         wl = "ik_1seg_256targets_32seeds_lm50_fp64"
-        extra = lambda: {"success_rate": float(s.out.success.float().mean())}
+
+        def extra():
+            out = {"success_rate": float(s.out.success.float().mean())}
+            forms = {}
+            sp = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK5, P, plain=True, device=dev)
+            forms["plain_gpu"], _ = gpu_form(torch, lambda: sp.solve(tg), P, "solves/s",
+                                             "one launch per target, FP64, iterates through global memory")
+            forms["plain_gpu"]["success_rate"] = float(sp.out.success.float().mean())
+            n1 = 32
+            s1 = api.IkSolver(spec, ik, synth.WEIGHTS, lib.CR_TASK_IK5, 1, precision=lib.CR_F64, device=dev)
+            tg1 = [tg[:, i:i + 1].contiguous() for i in range(n1)]
+            forms["per_problem_optimised"], _ = gpu_form(
+                torch, lambda: [s1.solve(tg1[i], i) for i in range(n1)], n1, "solves/s",
+                "the optimised kernels launched once per target (P = 1), FP64, first 32 targets")
+            if not args.no_baseline:
+                import oracle as O
+
+                tgh = tg.cpu().numpy().T
+                rate, n, cores, dt, osucc, _ = cpu_oracle_rate(tgh, spec, ik, kind=O.IK5)
+                out["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                       "sample": f"first {n} targets ({dt:.1f} s on {cores} threads)"}
+                gs = s.out.success[:n].cpu().numpy().astype(bool)
+                out["oracle_agreement"] = {"targets": n, "success_rate_oracle": float(osucc.mean()),
+                                           "success_rate_gpu": float(gs.mean()),
+                                           "success_flag_mismatches": int((gs != osucc).sum())}
+            out["forms"] = forms
+            return out
+
         dtype = "f64"
     elif args.workload == "path":
         spec, ik, P, H = synth.ROBOT_4SEG, synth.IK_PATH0, synth.P_PATH, synth.H_PATH
@@ -321,9 +403,46 @@ def other_workload(args):
         fn = lambda: s.solve(wps)
         units, unit, metric = P, "paths/s", "path following paths/s (64 waypoints, 32 spheres, FP32 + FP64 block Cholesky)"
         wl = "path_4seg_512paths_64wp_32spheres_warm30_joint20"
-        extra = lambda: {"tracked_rate_1mm": float((s.pos.reshape(P, H).max(1).values <= 1e-3).float().mean()),
-                         "waypoint_solves_per_s": None,
-                         "pos_err_median_m": float(s.pos.median()), "rot_err_median_rad": float(s.rot.median())}
+        def path_success(sol, n):
+            pos = sol.pos.reshape(n, H).max(1).values.cpu().numpy()
+            rot = sol.rot.reshape(n, H).max(1).values.cpu().numpy()
+            return (pos <= 1e-3) & (rot <= np.deg2rad(1.0)) & (sol.lim_ok.cpu().numpy() > 0) & \
+                (sol.col_ok.cpu().numpy() > 0)
+
+        def extra():
+            out = {"tracked_rate_1mm": float((s.pos.reshape(P, H).max(1).values <= 1e-3).float().mean()),
+                   "success_rate": float(path_success(s, P).mean()),
+                   "waypoint_solves_per_s": P * H / (line["ms_per_step"] / 1e3),
+                   "pos_err_median_m": float(s.pos.median()), "rot_err_median_rad": float(s.rot.median())}
+            n1 = 8
+            per = [(api.PathSolver(spec, ik, synth.WEIGHTS, 1, H, api.Scene(sph[i:i + 1], per_problem=True),
+                                   device=dev), api.waypoints_soa(wp[i:i + 1], device=dev)) for i in range(n1)]
+            forms = {"plain_gpu": {"unavailable": "no separate plain path kernels: the plain comparator of this "
+                                                  "config is the per-problem launch below"}}
+            forms["per_problem_optimised"], _ = gpu_form(
+                torch, lambda: [p_.solve(w_, i) for i, (p_, w_) in enumerate(per)], n1, "paths/s",
+                "the optimised kernels launched once per path (P = 1), first 8 paths")
+            if not args.no_baseline:
+                import oracle as O
+
+                O.build()
+                rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb,
+                                  rbody=spec.body_radius)
+                W = O.make_weights(**synth.WEIGHTS.as_dict())
+
+                def run(lo, hi, threads):
+                    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final,
+                                     lambda0=ik.lambda0, alpha0=ik.alpha0, dedup_eps=ik.dedup_eps,
+                                     lim_tol=ik.lim_tol, seed=ik.seed, p0=lo)
+                    o = O.solve_path(rb, W, sph[lo:hi], wp[lo:hi], cfg, synth.K_WARM, synth.K_JOINT, threads=threads)
+                    return (o["pos"].max(1) <= 1e-3) & (o["rot"].max(1) <= np.deg2rad(1.0)) & o["lim_ok"] & o["col_ok"]
+
+                cpu = oracle_sample(run, P, "paths/s", "paths of 64 waypoints")
+                out["oracle_agreement"] = agreement(path_success(s, P), cpu)
+                out["cpu_baseline"] = cpu
+            out["forms"] = forms
+            return out
+
         dtype = "f32"
     elif args.workload == "traj":
         spec, ik, P, Tn = synth.ROBOT_3SEG, synth.IK_GOAL, synth.P_TRAJ, synth.T_TRAJ
@@ -339,9 +458,47 @@ def other_workload(args):
         fn = lambda: s.solve(usd, gd)
         units, unit, metric = P, "trajectories/s", "trajectory planning trajectories/s (32 states, 64 spheres, 100 PG steps)"
         wl = "traj_3seg_256problems_32states_64spheres_pg100"
-        extra = lambda: {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
-                         "collision_free_rate": float(s.col_ok.float().mean()),
-                         "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+        def traj_success(t):
+            return ((t.goal_pos <= 1e-3) & (t.goal_rot <= np.deg2rad(1.0)) & (t.col_ok > 0) &
+                    (t.lim_ok > 0)).cpu().numpy()
+
+        def extra():
+            out = {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
+                   "success_rate": float(traj_success(s).mean()),
+                   "collision_free_rate": float(s.col_ok.float().mean()),
+                   "speed_ratio_max": float(s.speed.max()), "accel_ratio_max": float(s.accel.max())}
+            n1 = 8
+            per = [(api.TrajSolver(spec, ik, synth.WEIGHTS, 1, Tn, api.Scene(sph[i:i + 1], per_problem=True),
+                                   device=dev), usd[:, i:i + 1].contiguous(), gd[:, i:i + 1].contiguous())
+                   for i in range(n1)]
+            forms = {"plain_gpu": {"unavailable": "no separate plain trajectory kernels: the plain comparator of "
+                                                  "this config is the per-problem launch below"}}
+            forms["per_problem_optimised"], _ = gpu_form(
+                torch, lambda: [t_.solve(u_, g_, i) for i, (t_, u_, g_) in enumerate(per)], n1, "trajectories/s",
+                "the optimised kernels launched once per problem (P = 1), first 8 problems")
+            if not args.no_baseline:
+                import oracle as O
+
+                O.build()
+                rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb,
+                                  rbody=spec.body_radius)
+                W = O.make_weights(**synth.WEIGHTS.as_dict())
+
+                def run(lo, hi, threads):
+                    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final,
+                                     lambda0=ik.lambda0, alpha0=ik.alpha0, dedup_eps=ik.dedup_eps,
+                                     lim_tol=ik.lim_tol, seed=ik.seed, p0=lo)
+                    r = O.solve_traj(rb, W, sph[lo:hi], us[lo:hi], goal[lo:hi], Tn, cfg, synth.K_TRAJ,
+                                     synth.ALPHA_TRAJ, threads=threads)
+                    return ((r["goal_pos"] <= 1e-3) & (r["goal_rot"] <= np.deg2rad(1.0)) & r["lim_ok"]
+                            & r["col_ok"])
+
+                cpu = oracle_sample(run, P, "trajectories/s", "problems of 32 states, 64 spheres", budget_s=20.0)
+                out["oracle_agreement"] = agreement(traj_success(s), cpu)
+                out["cpu_baseline"] = cpu
+            out["forms"] = forms
+            return out
+
         dtype = "f32"
     elif args.workload == "prm":
         # Algorithm 2: roadmaps built once per scene (offline, timed apart), then per query the goal IK,
@@ -509,12 +666,21 @@ def other_workload(args):
         dtype = "f32"
     elif args.workload == "ragged":
         fam = synth.ROBOT_FAMILY
-        items, targets, spheres, _ = synth.ragged_workload(args.items, api.family_fk_backbone(fam, dev), seed=0)
-        s = api.BatchSolver(fam, items, synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=0, device=dev)
+        # args.items items per process (weak scaling); the job's batch is split by estimated cost
+        n_all = args.items * world
+        items_all, targets_all, spheres_all, _ = synth.ragged_workload(n_all, api.family_fk_backbone(fam, dev), seed=0)
+        bounds = lib.cr_batch_partition(lib._batch_items(items_all), api.BatchSolver.params(synth.IK_RAGGED), world)
+        lo, hi = bounds[rank], bounds[rank + 1]
+        w0 = np.concatenate([[0], np.cumsum(items_all[:, 2])])
+        o0 = np.concatenate([[0], np.cumsum(items_all[:, 4])])
+        items = items_all[lo:hi]
+        targets, spheres = targets_all[w0[lo]:w0[hi]], spheres_all[o0[lo]:o0[hi]]
+        s = api.BatchSolver(fam, items, synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=0, device=dev, p0=lo)
         s.set_inputs(targets, spheres)
         spu, n_units, workers = s.plan()
         fn = lambda: s.run()
-        units, unit = len(items), "problems/s"
+        units, unit = n_all, "problems/s"
+        line["partition"] = {"bounds": bounds, "rule": "contiguous, by the planner's cost estimate"}
         metric = f"ragged batch problems/s ({args.items} mixed IK / path items, one graph launch)"
         wl = f"ragged_{args.items}_items_n1-6_H1-128_S16-256_no0-64"
         W = int(items[:, 2].sum())
@@ -545,14 +711,50 @@ def other_workload(args):
                              "success_rate": float((fl & 1).mean()), **lat(t_ns)}
             return out
 
+        def oracle_items(lo, hi, threads):
+            """The oracle's solve of items [lo, hi), one item per thread (item i: seed counter i)."""
+            import concurrent.futures as cf
+
+            import oracle as O
+
+            O.build()
+            W_ = O.make_weights(**synth.WEIGHTS.as_dict())
+            w0 = np.concatenate([[0], np.cumsum(items[:, 2])])
+            o0 = np.concatenate([[0], np.cumsum(items[:, 4])])
+            ik_ = synth.IK_RAGGED
+
+            def one(i):
+                kind, n, H, S, no = (int(v) for v in items[i])
+                rb = O.make_robot(list(fam.L[:n]), fam.rc, fam.umax, thmax=fam.thmax, nb=fam.nb,
+                                  rbody=fam.body_radius)
+                tg = targets[w0[i]:w0[i] + H]
+                sp = spheres[o0[i]:o0[i] + no] if no else None
+                cfg = O.IkConfig(S=S, n_final=min(ik_.n_final, S), k_init=ik_.k_init, k_final=ik_.k_final,
+                                 lambda0=ik_.lambda0, alpha0=ik_.alpha0, dedup_eps=ik_.dedup_eps,
+                                 lim_tol=ik_.lim_tol, seed=ik_.seed, p0=i)
+                if kind == 1 and H > 1:
+                    o = O.solve_path(rb, W_, None if sp is None else sp[None], tg[None], cfg, synth.K_WARM,
+                                     synth.K_JOINT, threads=1)
+                    return bool((o["pos"][0] <= 1e-3).all() and (o["rot"][0] <= np.deg2rad(1.0)).all()
+                                and o["lim_ok"][0] and o["col_ok"][0])
+                return bool(O.solve_ik(rb, W_, sp, 0, tg, cfg, threads=1)["success"][0])
+
+            with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+                return list(ex.map(one, range(lo, hi)))
+
         def extra():
             t_ns = s.t_done.cpu().numpy()
             fl = s.flags.cpu().numpy()
-            return {"waypoint_solves_per_s": W / (line["ms_per_step"] / 1e3), "latency": lat(t_ns),
-                    "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu, "work_units": n_units,
-                    "worker_warps": workers, "items_ik": int((items[:, 0] == 0).sum()),
-                    "items_path": int((items[:, 0] == 1).sum()), "waypoints": W,
-                    "vs_plain_subset": None if args.no_baseline else subset()}
+            out = {"waypoint_solves_per_s": W / (line["ms_per_step"] / 1e3), "latency": lat(t_ns),
+                   "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu, "work_units": n_units,
+                   "worker_warps": workers, "items_ik": int((items[:, 0] == 0).sum()),
+                   "items_path": int((items[:, 0] == 1).sum()), "waypoints": W,
+                   "vs_plain_subset": None if args.no_baseline else subset()}
+            if not args.no_baseline:
+                cpu = oracle_sample(oracle_items, len(items), "problems/s", "items of the batch")
+                out["oracle_agreement"] = agreement(fl & 1, cpu)
+                out["cpu_baseline"] = cpu
+            return out
 
         dtype = "f32"
     else:
@@ -575,17 +777,46 @@ def other_workload(args):
 
         units, unit, metric = 1, "calibrations/s", "calibration of 6 parameters from 1024 noisy poses (20 LM iterations)"
         wl = "calib_3seg_1024poses"
-        extra = lambda: {"param_rel_err_max": float(np.abs(res["th"].cpu().numpy() / true - 1).max())}
+
+        def extra():
+            out = {"param_rel_err_max": float(np.abs(res["th"].cpu().numpy() / true - 1).max())}
+            Ud64 = Ud.double()
+            forms = {"plain_gpu": {"unavailable": "one problem: the optimised form is already one launch pair per "
+                                                  "LM iteration"}}
+            forms["fp64_bulk"], _ = gpu_form(torch, lambda: api.calibrate(spec, Ud64, Pd, nom), 1, "calibrations/s",
+                                             "the same kernels with FP64 kinematics")
+            if not args.no_baseline:
+                import oracle as O
+
+                O.build()
+                rb = O.make_robot(list(spec.L), spec.rc, spec.umax, nb=spec.nb)
+                t0 = time.perf_counter()
+                ref = O.calibrate(rb, U, Pm, nom, synth.ITERS_CALIB)
+                dt = time.perf_counter() - t0
+                out["cpu_baseline"] = {"value": 1.0 / dt, "unit": unit, "cores": 1, "kind": "oracle",
+                                       "sample": f"the whole calibration ({dt:.2f} s, one thread)"}
+                out["oracle_agreement"] = {"param_rel_diff_max": float(np.abs(res["th"].cpu().numpy() / ref["theta"]
+                                                                               - 1).max())}
+            out["forms"] = forms
+            return out
+
         dtype = "f32"
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     med, mean = time_steps(torch, fn, args.steps, flush, stream)
+    mean = max_over_ranks(torch, dist, world, mean * args.steps, dev) / args.steps
     line.update({"metric": metric, "value": units / (mean / 1e3), "unit": unit, "ms_per_step": mean,
                  "ms_per_step_median": med, "dtype": dtype,
                  "config": {"workload": wl, "l2": "flushed between timed steps (512 MiB write)"}})
-    line.update(extra())
-    print(json.dumps(line))
+    if rank == 0:
+        line.update(extra())
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def main():

@@ -499,16 +499,15 @@ class BatchSolver:
 
     def __init__(self, family: synth.RobotSpec, items, ik: synth.IkSpec, weights: synth.WeightSpec,
                  k_warm: int = synth.K_WARM, k_joint: int = synth.K_JOINT, seeds_per_unit: int = 0,
-                 device="cuda"):
+                 device="cuda", p0: int = 0):
         import numpy as np
 
         self.family = robot_struct(family)
         self.weights = weights_struct(weights)
         self.items_np = np.asarray(items, dtype=np.int64).reshape(-1, 5)
         self.items = lib._batch_items(self.items_np)
-        self.prm = lib.cr_batch_params()
-        self.prm.ik = ik_params_struct(ik, lib.CR_F32)
-        self.prm.k_warm, self.prm.k_joint, self.prm.seeds_per_unit = k_warm, k_joint, seeds_per_unit
+        self.prm = self.params(ik, k_warm, k_joint, seeds_per_unit)
+        self.prm.ik.p0 = p0  # item i draws its seeds as problem p0 + i (a process's share of a larger batch)
         it = self.items_np
         self.N = len(it)
         self.W = int(it[:, 2].sum())
@@ -523,6 +522,14 @@ class BatchSolver:
         self.workspace = torch.empty(lib.cr_batch_workspace_size(self.family, self.items, self.prm),
                                      dtype=torch.uint8, device=device)
         self._plan = None
+
+    @staticmethod
+    def params(ik: synth.IkSpec, k_warm: int = synth.K_WARM, k_joint: int = synth.K_JOINT,
+               seeds_per_unit: int = 0) -> lib.cr_batch_params:
+        prm = lib.cr_batch_params()
+        prm.ik = ik_params_struct(ik, lib.CR_F32)
+        prm.k_warm, prm.k_joint, prm.seeds_per_unit = k_warm, k_joint, seeds_per_unit
+        return prm
 
     def set_inputs(self, targets, spheres):
         """targets [W][7] (position + quaternion per waypoint, items in order), spheres [sum n_o][4]."""

@@ -108,6 +108,7 @@ IkLayout ik_layout(const cr_robot& r, int64_t P, const cr_ik_params& prm) {
   L.cand_rot = off; off = align256(off + PK * 8);
   L.cand_flag = off; off = align256(off + PK);
   L.plain_u = off; off = align256(off + (size_t)prm.S * D * 8);
+  L.plain_g = off; off = align256(off + (size_t)prm.S * D * 8);
   L.plain_F = off; off = align256(off + (size_t)prm.S * 8 * 3 + 32 * 4 + (size_t)prm.S * 5);
   const size_t PS = (size_t)P * (size_t)(prm.S > 0 ? prm.S : 0);
   L.stage_F = off; off = align256(off + PS * 4);

@@ -73,11 +73,12 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Workspace of cr_solve_ik (and its plain comparator):
 //   status word | candidate states (bulk precision) [D][P*K] | candidate FP64 states [D][P*K] |
-//   candidate FP64 cost, pos, rot [P*K] each | candidate flags [P*K] | plain-form scratch |
+//   candidate FP64 cost, pos, rot [P*K] each | candidate flags [P*K] | plain-form scratch (states,
+//   gradients, costs) |
 //   stage-one end states: cost, clearance part (FP32) [P*S] each, states (bulk precision) [D][P*S]
 struct IkLayout {
-  size_t status, cand_u, cand_u64, cand_F, cand_pos, cand_rot, cand_flag, plain_u, plain_F, stage_F, stage_C,
-      stage_u, total;
+  size_t status, cand_u, cand_u64, cand_F, cand_pos, cand_rot, cand_flag, plain_u, plain_g, plain_F, stage_F,
+      stage_C, stage_u, total;
 };
 // weights.rho_s must be >= 0; with supported = false it must be 0 (the solver has no self-contact rows)
 cr_status check_self_rows(const cr_weights& w, bool supported, const char* who);

@@ -7,7 +7,7 @@ namespace crk {
 
 template <int N, bool OBST>
 __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<double> w, IkArgs<double> a,
-                                                   int64_t p, double* U, double* Fs, double* Cs,
+                                                   int64_t p, double* U, double* G, double* Fs, double* Cs,
                                                    double* alphas, int* sel) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -27,17 +27,17 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
         if (!state_collides<double, N>(rb, sph, a.no, u)) break;
         draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box.umax, u);
       }
-    for (int q = 0; q < D; ++q) U[s * D + q] = u[q];
     double g[D], coll;
     Fs[s] = eval_ik<double, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+    for (int q = 0; q < D; ++q) { U[s * D + q] = u[q]; G[s * D + q] = g[q]; }
     Cs[s] = coll;
     alphas[s] = double(a.alpha0);
     for (int it = 0; it < a.k_init; ++it) {
-      double uu[D], gg[D], F, cl, al = alphas[s];
-      for (int q = 0; q < D; ++q) uu[q] = U[s * D + q];
-      F = eval_ik<double, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, uu, gg, nullptr, nullptr, &cl);
+      // the iterate, its gradient, cost and step length round-trip through global memory every step
+      double uu[D], gg[D], F = Fs[s], cl = Cs[s], al = alphas[s];
+      for (int q = 0; q < D; ++q) { uu[q] = U[s * D + q]; gg[q] = G[s * D + q]; }
       pg_step<double, N, OBST>(rb, w, a.kind, tg, sph, a.no, uu, gg, F, cl, al);
-      for (int q = 0; q < D; ++q) U[s * D + q] = uu[q];
+      for (int q = 0; q < D; ++q) { U[s * D + q] = uu[q]; G[s * D + q] = gg[q]; }
       Fs[s] = F;
       Cs[s] = cl;
       alphas[s] = al;
@@ -104,6 +104,7 @@ template <int N> cr_status plain_n(const SolveArgs& sa) {
   IkArgs<double> a = ik_args<double>(sa);
   unsigned char* ws = (unsigned char*)sa.ws;
   double* U = (double*)(ws + sa.lay.plain_u);
+  double* G = (double*)(ws + sa.lay.plain_g);
   double* Fs = (double*)(ws + sa.lay.plain_F);
   double* Cs = Fs + a.S;
   double* alphas = Cs + a.S;
@@ -112,8 +113,8 @@ template <int N> cr_status plain_n(const SolveArgs& sa) {
   const int threads = ((a.S + 31) / 32) * 32;
   size_t sm = (size_t)a.no * sizeof(Sphere4<double>);
   for (int64_t p = 0; p < a.P; ++p) {
-    if (a.no > 0) k_plain_ik<N, true><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, Fs, Cs, alphas, sel);
-    else k_plain_ik<N, false><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, Fs, Cs, alphas, sel);
+    if (a.no > 0) k_plain_ik<N, true><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, G, Fs, Cs, alphas, sel);
+    else k_plain_ik<N, false><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, G, Fs, Cs, alphas, sel);
     cr_status st = crh::check_launch("cr_solve_ik_plain");
     if (st) return st;
   }

@@ -7,10 +7,13 @@ clearance, each side judged by its own FP64 acceptance. The assertion is |rate_g
 <= 0.01, with the sample size stated per test; each test prints both rates and the per-problem
 flag mismatches. Where a config's full shape is too slow for the oracle (paths of 64 waypoints,
 trajectories of 32 states with 64 spheres), the sample uses a shorter horizon of the same robot
-and scene recipe, stated in the test.
+and scene recipe, stated in the test. Where rounding-level branch choices make a config's per-problem
+outcomes coin flips on a few percent of problems (paths), the sample is large enough that their
+unbiased noise stays well inside one point.
 """
 import concurrent.futures as cf
 import dataclasses
+import functools
 import os
 
 import numpy as np
@@ -77,16 +80,35 @@ def test_ik_e1_shape_success_200():
     assert _report("IK E1 shape (arc model)", out.success.cpu().numpy(), o["success"])
 
 
+PATH_N, PATH_H = 2000, 8
+
+
+@functools.lru_cache(maxsize=1)
+def _path_case():
+    """The path workload's robot and scene recipe, PATH_N paths of PATH_H waypoints, with the oracle's
+    solve (computed once for both precisions)."""
+    spec, ik = synth.ROBOT_4SEG, synth.IK_PATH0
+    rbo = orc_robot(spec)
+    wp, _, sph = synth.path_workload(spec, PATH_N, PATH_H, synth.NO_PATH, lambda u: O.fk(rbo, u, backbone=True),
+                                     seed=15)
+    o = O.solve_path(rbo, orc_weights(), sph, wp, _ik_cfg(ik), synth.K_WARM, synth.K_JOINT)
+    tol_r = np.deg2rad(1.0)
+    so = (o["pos"].max(1) <= 1e-3) & (o["rot"].max(1) <= tol_r) & o["lim_ok"] & o["col_ok"]
+    return wp, sph, so
+
+
 @pytest.mark.parametrize("prec", [lib.CR_F32, lib.CR_F64])
-def test_path_success_200(prec):
+def test_path_success(prec):
     """Path following on the path workload's robot and scene recipe (4 segments, 16 backbone samples
     per segment, 32 spheres per path, first-waypoint IK of 64 seeds, 30 warm LM iterations per
-    waypoint, 20 joint LM iterations), 200 paths of 16 waypoints (64 in the full workload: the
-    oracle's dense joint solve grows as H^3)."""
+    waypoint, 20 joint LM iterations) on 2000 paths of 8 waypoints (64 in the full workload). About
+    one path in twenty takes a different, equally valid branch on the two sides (a warm start that
+    converged onto a bound's kink, a cost tie of the redundant degrees of freedom), and those
+    outcomes are coin flips without bias: 2000 paths keep the count difference they cause well
+    inside one percentage point (20 paths); 200 did not resolve it."""
     spec, ik = synth.ROBOT_4SEG, synth.IK_PATH0
-    P, H = 200, 16
-    rbo = orc_robot(spec)
-    wp, _, sph = synth.path_workload(spec, P, H, synth.NO_PATH, lambda u: O.fk(rbo, u, backbone=True), seed=15)
+    P, H = PATH_N, PATH_H
+    wp, sph, so = _path_case()
     s = api.PathSolver(spec, ik, synth.WEIGHTS, P, H, api.Scene(sph, per_problem=True), prec, synth.K_WARM,
                        synth.K_JOINT)
     s.solve(api.waypoints_soa(wp), 0)
@@ -94,8 +116,6 @@ def test_path_success_200(prec):
     tol_r = np.deg2rad(1.0)
     pos, rot = s.pos.cpu().numpy().reshape(P, H), s.rot.cpu().numpy().reshape(P, H)
     g = (pos.max(1) <= 1e-3) & (rot.max(1) <= tol_r) & (s.lim_ok.cpu().numpy() > 0) & (s.col_ok.cpu().numpy() > 0)
-    o = O.solve_path(rbo, orc_weights(), sph, wp, _ik_cfg(ik), synth.K_WARM, synth.K_JOINT)
-    so = (o["pos"].max(1) <= 1e-3) & (o["rot"].max(1) <= tol_r) & o["lim_ok"] & o["col_ok"]
     assert _report(f"path prec={prec}", g, so)
 
 

@@ -136,10 +136,11 @@ def test_solve_traj_parity(prec):
     if prec == lib.CR_F64:
         # 100 normalised steps: near convergence the step direction g / |g| of a small gradient carries
         # the rounding of g relative to |g|, so FP64 states drift apart by up to alpha times that
-        # (measured 6.5e-9 m, 6.5e-7 of the bound, after the goal IK's argmin change of candidate)
-        np.testing.assert_allclose(X, ref["x"], atol=1e-8)
-        # iterates agree to 1e-8 m; with |dF/du| ~ F / 1e-3 m that allows 1e-5 relative in F
-        np.testing.assert_allclose(sol.cost.cpu().numpy(), ref["F"], rtol=1e-5)
+        # (measured 6.5e-9 m and 1.1e-8 m, about 1e-6 of the bound, on two builds whose gradients round
+        # differently); the bound is 1e-7 m, 1e-5 of the displacement bound
+        np.testing.assert_allclose(X, ref["x"], atol=1e-7)
+        # with |dF/du| ~ F / 1e-3 m, states within 1e-7 m allow 1e-4 relative in F
+        np.testing.assert_allclose(sol.cost.cpu().numpy(), ref["F"], rtol=1e-4)
     else:
         np.testing.assert_allclose(sol.cost.cpu().numpy(), ref["F"], rtol=0.05)
         assert np.all(sol.goal_pos.cpu().numpy() < 1e-3) == np.all(ref["goal_pos"] < 1e-3)
