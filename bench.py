@@ -31,10 +31,12 @@ WORKLOAD = "ik_3seg_9tendon_4096targets_256seeds_pg64_top8_lm30"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
-# DRAM bytes (read + write) of one stage-one launch per target, from an ncu capture of the same
-# kernel at 608 targets (dram__bytes_read.sum + dram__bytes_write.sum = 112,128 B); traffic grows in
-# proportion to the targets (each CTA reads its target and writes its candidates).
-STAGE1_DRAM_BYTES_PER_TARGET = 112128 / 608
+# DRAM bytes (read + write) of one stage-one call per target (k_ik_stage1 + k_ik_select, the pair the
+# bench times), from an ncu capture of both kernels at 608 targets (dram__bytes_read.sum +
+# dram__bytes_write.sum: 77,312 B + 6,872,320 B; ncu flushes the caches between kernels, so
+# SelectTop's read of the seeds' end states comes from DRAM there, from L2 in a live step); traffic
+# grows in proportion to the targets (each target reads its pose and its 256 end states).
+STAGE1_DRAM_BYTES_PER_TARGET = (77312 + 6872320) / 608
 
 
 def parse():
@@ -897,6 +899,15 @@ def main():
     torch.cuda.synchronize()
     s1_ms = float(np.mean([a.elapsed_time(b) for a, b in ev1]))
     accepted = solver.pg_accepted()  # accepted PG steps of the last stage-one launch (device counter)
+    # ---- stage two alone (refine + argmin) on the candidates the last stage one left ----
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        solver.stage2()
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    s2_ms = float(np.mean([a.elapsed_time(b) for a, b in ev2]))
     n_eval = P * ik.S * (ik.k_init + 1)  # value evaluations per stage-one launch
     # The method's own work (method_ops). The kernel computes the gradient at every trial (fused, one
     # pass; a warp's lanes accept independently), which is reported beside it.
@@ -969,7 +980,7 @@ def main():
                    "l2": "flushed between timed steps (512 MiB write)", "lm_cholesky": "f64"},
         "success_rate": succ, "pos_err_median_m": pos_med, "rot_err_median_rad": rot_med, "device_status": status,
         "evals_per_s": world * (n_eval + P * ik.n_final * (2 * ik.k_final + 1)) / (ms_per_step / 1e3),
-        "roofline": {"bound": "alu", "kernel": "k_ik_stage1", "achieved": achieved_tflops, "peak": peak_fp32,
+        "roofline": {"bound": "alu", "kernel": "k_ik_stage1 + k_ik_select", "achieved": achieved_tflops, "peak": peak_fp32,
                      "unit": "TFLOP/s", "frac": achieved_tflops / peak_fp32,
                      "traffic": STAGE1_DRAM_BYTES_PER_TARGET * P,
                      "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
@@ -980,6 +991,15 @@ def main():
                      "frac_fused_form": flop_fused / (s1_ms / 1e3) / 1e12 / peak_fp32,
                      "sfu_results_per_s": sfu_method / (s1_ms / 1e3),
                      "sfu_frac_of_live_mufu": sfu_method / (s1_ms / 1e3) / (cal["mufu_tops"] * 1e12)},
+        "refine": {"kernel": "k_ik_refine + k_ik_argmin", "kernel_ms": s2_ms, "bound": "fp64",
+                   "fp64_flop_per_launch": P * ik.n_final * ik.k_final * counts["lm_update_flop"],
+                   "achieved_tflops": P * ik.n_final * ik.k_final * counts["lm_update_flop"] / (s2_ms / 1e3) / 1e12,
+                   "peak_live_dfma_tflops": cal["dfma_tflops"],
+                   "frac": P * ik.n_final * ik.k_final * counts["lm_update_flop"] / (s2_ms / 1e3) / 1e12
+                   / cal["dfma_tflops"],
+                   "count": "oracle op count of one LM update (damping, Cholesky, solves, gain ratio) per "
+                            "candidate and iteration; the FP32 evaluations and the FP64 acceptance are not "
+                            "in it"},
         "calibration": cal,
         "plain_form": {"value": plain_rate, "unit": UNIT, "targets": Pp, "success_rate": plain_succ,
                        "optimised_success_rate_same_targets": opt_succ_sub, "speedup": value / world / plain_rate},

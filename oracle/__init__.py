@@ -347,15 +347,18 @@ def project_arc(v, thmax, lmin, lmax):
 
 def ik_pg(robot, weights, spheres, kind, targets, S, u0, steps, alpha0, threads=None, history=False):
     """Stage-one projected gradient on every seed. Returns (u, F), or with history (u, F, hist):
-    hist [B][steps][d + 3] = the iterate, alpha, F and the trial's cost after every step."""
+    hist [B][steps][d + 3] = the iterate, alpha, F and the trial's cost after every step. alpha0: one
+    starting step length, or one per seed."""
     no, sp = _spheres(spheres)
     u = _f64(u0).copy()
     tg = _f64(targets).reshape(-1, 7)
     F = np.zeros(u.shape[0])
     hist = np.zeros((u.shape[0], steps, u.shape[1] + 3)) if history else None
+    a_per = None if np.ndim(alpha0) == 0 else np.ascontiguousarray(_f64(alpha0).reshape(-1))
     lib().orc_ik_pg(C.byref(robot), C.byref(weights), C.c_int(no), _dp(sp), C.c_int(kind), _dp(tg),
                     C.c_int64(S), _dp(u), C.c_int64(u.shape[0]), C.c_int(steps),
-                    C.c_double(alpha0), _dp(F), _dp(hist), C.c_int(_threads(threads)))
+                    C.c_double(0.0 if a_per is not None else alpha0), _dp(a_per), _dp(F), _dp(hist),
+                    C.c_int(_threads(threads)))
     return (u, F, hist) if history else (u, F)
 
 

@@ -1321,13 +1321,15 @@ int orc_project_arc(const double* v, int64_t B, double thmax, double lmin, doubl
 
 // Stage-one projected gradient on every seed: u[B][d] in place, F[B] out; hist (nullable)
 // [B][steps][d + 3] as in pg_rule.
+// alpha_per (nullable): seed b starts with step length alpha_per[b] instead of alpha0.
 int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int steps, double alpha0,
-              double* F, double* hist, int threads) {
+              const double* alpha_per, double* F, double* hist, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
     IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
-    pg_run_one(pb, u + d * b, steps, alpha0, F + b, hist ? hist + (size_t)b * steps * (d + 3) : nullptr);
+    pg_run_one(pb, u + d * b, steps, alpha_per ? alpha_per[b] : alpha0, F + b,
+               hist ? hist + (size_t)b * steps * (d + 3) : nullptr);
   });
   return 0;
 }

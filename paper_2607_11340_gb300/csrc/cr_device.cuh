@@ -1379,13 +1379,17 @@ CR_HD double recip_nr(double d) {
 // ------------------------------------------------------------------------------------------------
 // The reciprocal pivots are kept in invd[] so that the solves multiply instead of divide (FP64
 // division and square root are long instruction sequences on a part with a narrow FP64 pipe).
+// Every loop has a constant trip count with the triangular range as a guard, so that full unrolling
+// leaves only constant indices and the packed matrix stays in registers (with trip counts that depend
+// on an outer index the compiler kept it in local memory).
 template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2], double (&invd)[D]) {
   bool ok = true;  // no early exit: keeps the fully unrolled factorisation in registers
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     double s = A[tri(j, j)];
 #pragma unroll
-    for (int k = 0; k < j; ++k) s -= A[tri(j, k)] * A[tri(j, k)];
+    for (int k = 0; k < D; ++k)
+      if (k < j) s -= A[tri(j, k)] * A[tri(j, k)];
     ok = ok && (s > 0.0);
     s = s > 0.0 ? s : 1.0;
     double inv = rsqrt(s);
@@ -1393,10 +1397,12 @@ template <int D> CR_HD bool cholesky_packed(double (&A)[D * (D + 1) / 2], double
     invd[j] = inv;
     A[tri(j, j)] = ljj;
 #pragma unroll
-    for (int i = j + 1; i < D; ++i) {
+    for (int i = 0; i < D; ++i) {
+      if (i <= j) continue;
       double t = A[tri(i, j)];
 #pragma unroll
-      for (int k = 0; k < j; ++k) t -= A[tri(i, k)] * A[tri(j, k)];
+      for (int k = 0; k < D; ++k)
+        if (k < j) t -= A[tri(i, k)] * A[tri(j, k)];
       A[tri(i, j)] = t * inv;
     }
   }
@@ -1409,14 +1415,16 @@ CR_HD void cholesky_solve(const double (&Lm)[D * (D + 1) / 2], const double (&in
   for (int i = 0; i < D; ++i) {
     double s = x[i];
 #pragma unroll
-    for (int k = 0; k < i; ++k) s -= Lm[tri(i, k)] * x[k];
+    for (int k = 0; k < D; ++k)
+      if (k < i) s -= Lm[tri(i, k)] * x[k];
     x[i] = s * invd[i];
   }
 #pragma unroll
   for (int i = D - 1; i >= 0; --i) {
     double s = x[i];
 #pragma unroll
-    for (int k = i + 1; k < D; ++k) s -= Lm[tri(k, i)] * x[k];
+    for (int k = 0; k < D; ++k)
+      if (k > i) s -= Lm[tri(k, i)] * x[k];
     x[i] = s * invd[i];
   }
 }

@@ -95,12 +95,14 @@ __device__ void warp_row(const AugSlots<D>& sl, T (&A)[AugSlots<D>::SL], T& gq, 
 }
 
 // Full-pose IK residual of one state evaluated by a warp (every lane holds u): returns F (the same
-// in every lane). With NORMAL, this lane's slots of J^T J (zero in row D) and, on lane q < D, entry
+// in every lane). NORMAL is a run-time (warp-uniform) flag, so that the LM step's two evaluations
+// share one copy of this code. With NORMAL, this lane's slots of J^T J (zero in row D) and, on lane q < D, entry
 // q of g = J^T r. Rows: pose (6), sum-zero per segment, active tendon bounds, active curvature
 // limits, active clearance pairs (backbone samples split over the lanes).
-template <typename T, int N, bool OBST, bool NORMAL>
+template <typename T, int N, bool OBST>
 __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, const Sphere4<T>* sph,
-                       int no, const T (&u)[3 * N], const AugSlots<3 * N>& sl, T (&A)[AugSlots<3 * N>::SL], T& gq) {
+                       int no, const T (&u)[3 * N], const AugSlots<3 * N>& sl, T (&A)[AugSlots<3 * N>::SL], T& gq,
+                       const bool NORMAL) {
   constexpr int D = 3 * N, SL = AugSlots<D>::SL;
   const int lane = threadIdx.x & 31;
   const bool colq = lane < D;
@@ -303,53 +305,65 @@ __device__ T warp_lm_step(const RobotK<T>& rb, const WeightsK<T>& w, const Targe
   constexpr int D = 3 * N, SL = AugSlots<D>::SL;
   const int lane = threadIdx.x & 31;
   T A[SL], gq;
-  const T F = warp_eval<T, N, OBST, true>(rb, w, tg, sph, no, u, sl, A, gq);
-  // damped, augmented system [A + lam D | -g]
-  V Av[SL];
+  T ue[D];  // the point evaluated: u (pass 0, with the normal equations), then the trial u + step
 #pragma unroll
-  for (int s = 0; s < SL; ++s) {
-    const int i = sl.r[s], j = sl.c[s];
-    const T gj = __shfl_sync(0xffffffffu, gq, j < D ? j : 0);
-    Av[s] = V(A[s]);
-    if (!sl.on[s]) continue;
-    if (i < D && i == j) {
-      const V dg = c_max(Av[s], V(1e-12));
-      sdg[i] = dg;
-      Av[s] += lam * dg;
-    } else if (i == D) {
-      Av[s] = j < D ? -V(gj) : V(0);
+  for (int q = 0; q < D; ++q) ue[q] = u[q];
+  T F = T(0), Fn = T(0);
+  V pred = V(0);
+  // One evaluation site for both passes (a loop that is not unrolled): the kernel carries one copy
+  // of the residual code, half the instruction footprint of two inlined evaluations.
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const T Fe = warp_eval<T, N, OBST>(rb, w, tg, sph, no, ue, sl, A, gq, pass == 0);
+    if (pass == 1) {
+      Fn = Fe;
+      break;
     }
-  }
-  const bool ok = sweep_aug<V, D>(Av, sl, col, colr);
-  if (!ok) {
-    lam *= nu;
-    nu *= V(2);
-    return F;
-  }
+    F = Fe;
+    // damped, augmented system [A + lam D | -g]
+    V Av[SL];
 #pragma unroll
-  for (int s = 0; s < SL; ++s)
-    if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) sx[sl.c[s]] = Av[s];
-  __syncwarp();
-  V predl = V(0);
-  if (lane < D) {
-    const V xq = sx[lane];
-    predl = xq * (lam * sdg[lane] * xq - V(gq));
+    for (int s = 0; s < SL; ++s) {
+      const int i = sl.r[s], j = sl.c[s];
+      const T gj = __shfl_sync(0xffffffffu, gq, j < D ? j : 0);
+      Av[s] = V(A[s]);
+      if (!sl.on[s]) continue;
+      if (i < D && i == j) {
+        const V dg = c_max(Av[s], V(1e-12));
+        sdg[i] = dg;
+        Av[s] += lam * dg;
+      } else if (i == D) {
+        Av[s] = j < D ? -V(gj) : V(0);
+      }
+    }
+    const bool ok = sweep_aug<V, D>(Av, sl, col, colr);
+    if (!ok) {
+      lam *= nu;
+      nu *= V(2);
+      return F;
+    }
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+      if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) sx[sl.c[s]] = Av[s];
+    __syncwarp();
+    V predl = V(0);
+    if (lane < D) {
+      const V xq = sx[lane];
+      predl = xq * (lam * sdg[lane] * xq - V(gq));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) predl += __shfl_xor_sync(0xffffffffu, predl, off);
+    pred = V(0.5) * predl;
+#pragma unroll
+    for (int q = 0; q < D; ++q) ue[q] = u[q] + T(sx[q]);
+    __syncwarp();
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) predl += __shfl_xor_sync(0xffffffffu, predl, off);
-  const V pred = V(0.5) * predl;
-  T un[D];
-#pragma unroll
-  for (int q = 0; q < D; ++q) un[q] = u[q] + T(sx[q]);
-  __syncwarp();
-  T Ad[SL], gd;
-  const T Fn = warp_eval<T, N, OBST, false>(rb, w, tg, sph, no, un, sl, Ad, gd);
   if (Fn < F) {
     const V rho = c_div(V(F) - V(Fn), pred), tt = V(2) * rho - V(1);
     lam *= c_max(V(1) / V(3), V(1) - tt * tt * tt);
     nu = V(2);
 #pragma unroll
-    for (int q = 0; q < D; ++q) u[q] = un[q];
+    for (int q = 0; q < D; ++q) u[q] = ue[q];
     return Fn;
   }
   lam *= nu;

@@ -5,7 +5,9 @@ transpose is the adjoint (same multiply-add count), so one value-and-gradient ev
 fwd + tan. "trial_*" counts leave out the rows that vanish at the projected trial points of stage
 one (tendon model: bound and sum-zero rows; arc model: length and curvature rows). "pg_step_*" is
 the step rule's own arithmetic per trial point (gradient norm, step length and move, without the
-projection). Calls only oracle/."""
+projection); "lm_update_*" that of one LM update of stage two (damping, Cholesky, the two
+triangular solves, predicted decrease, gain ratio, damping rule) without its cost evaluations.
+Calls only oracle/."""
 import json
 import os
 import sys
@@ -43,6 +45,9 @@ def counts(spec, kind, n_states=64):
     # the step rule's own arithmetic per trial (gradient norm, step length, move; not the projection)
     f, sf = O.opcount_pg_step(u.shape[1])
     out.update({"pg_step_flop": float(f), "pg_step_sfu": float(sf)})
+    # one LM update of stage two without its cost evaluations (damping, Cholesky, solves, gain ratio)
+    f, sf = O.opcount_lm_update(u.shape[1])
+    out.update({"lm_update_flop": float(f), "lm_update_sfu": float(sf)})
     return out
 
 

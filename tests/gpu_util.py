@@ -142,8 +142,11 @@ def kink_or_pi(states, spec: synth.RobotSpec, rot_rows, prec, k=64.0, w: synth.W
             else:
                 a_, b2, c_ = a, b_, c
             th = (2.0 / (3.0 * spec.rc)) * np.hypot(a_ - 0.5 * (b2 + c_), (np.sqrt(3.0) / 2.0) * (b2 - c_))
+            # a state the FP32 projection clamped holds the FP32 bound itself, exactly on the kink
+            # for that precision (inactive on both sides): not ambiguous either
+            bnd = float(np.float32(spec.umax)) if prec == lib.CR_F32 else spec.umax
             for u in (a, b_, c):
-                kink |= band(np.abs(u) - spec.umax, spec.umax)
+                kink |= band(np.abs(u) - spec.umax, spec.umax) & (np.abs(u) != bnd)
         kink |= band(th - spec.thmax, spec.thmax)
     if rot_rows is not None and prec == lib.CR_F32:
         ang = np.linalg.norm(np.asarray(rot_rows, np.float64), axis=-1) / w.wR

@@ -42,3 +42,4 @@ def test_fp64_sincos_within_ulps():
         r = out.cpu().numpy()
         ulp = np.abs(r - ref) / np.spacing(np.maximum(np.abs(ref), 1e-300))
         assert ulp.max() <= 4.0, (which, ulp.max(), x[ulp.argmax()])
+

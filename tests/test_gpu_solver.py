@@ -75,15 +75,21 @@ def _ik_case(spec, kind, P, S, seed=300, spheres=None):
 
 @pytest.mark.parametrize("prec,steps", [(lib.CR_F64, 64), (lib.CR_F32, 64)])
 def test_pg_iterates(prec, steps):
-    """Stage one's projected-gradient iterates, step by step for k_init = 64 steps (one call per
-    step), against the oracle's history from the same (precision-rounded) seeds. A seed is compared
-    at every step up to the first step whose outcome rounding decides (computed from the oracle's own
-    quantities, gpu_util): (a) its accept decision lies within the rounding band of the deciding
-    precision (near_ties), (b) its starting state has a bound or curvature hinge at its kink to
-    within rounding, (c) in FP32, its rotation error lies within 0.05 rad of pi (kink_or_pi), (d) the
-    GPU took its decision the other way, which must then be explained by the measured difference of
-    the two runs' states (below). Bound: 1e-4 of the displacement bound in FP32, 1e-10 in FP64, at
-    every compared step of every seed."""
+    """Stage one's projected-gradient steps (one call per step, 64 steps, 512 seeds) against the
+    oracle, in two views.
+
+    Step by step (the bound that is asserted everywhere): every GPU step k is compared with one
+    oracle step from the GPU's own iterate k-1 and step length, so a difference cannot come from an
+    earlier step. Steps whose outcome rounding decides are left out (computed from the oracle's own
+    one-step quantities, gpu_util): (a) the accept decision within the rounding band of the deciding
+    precision (near_ties), (b) a bound or curvature hinge at its kink in the starting state, (c) in
+    FP32 a rotation error within 0.05 rad of pi (kink_or_pi). Bound: 1e-4 of the displacement bound
+    in FP32, 1e-10 in FP64.
+
+    Whole trajectories: each seed against the oracle's own 64-step history from the same seed, up to
+    its first rounding-decided step. The normalised step x - alpha g / |g| can magnify a difference
+    by several times per step (by up to 1 + alpha |H| / |g|), so rounding differences of a few steps
+    can grow past the bound without any decision changing; 99 % of the seeds must stay within it."""
     spec = synth.ROBOT_3SEG
     P, S = 32, 16
     rbo, tg, u0 = _ik_case(spec, lib.CR_TASK_IK6, P, S, seed=301)
@@ -92,54 +98,59 @@ def test_pg_iterates(prec, steps):
     alpha = torch.full((P * S,), 1e-3, dtype=TDT[prec], device="cuda")
     F = torch.empty(P * S, dtype=TDT[prec], device="cuda")
     task = api.task_struct(lib.CR_TASK_IK6, targets_dev(tg), S, synth.WEIGHTS)
-    got = []
+    got, alph = [], []
     for it in range(steps):
         lib.cr_pg_steps(api.robot_struct(spec), api.Scene(None).c, task, ug, alpha, F, 1)
         got.append(host_aos(ug))
+        alph.append(alpha.double().cpu().numpy())
     got = np.stack(got, axis=1)  # [B][steps][d]
-    _, _, h = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b, steps, 1e-3, history=True)
+    alph = np.stack(alph, axis=1)  # [B][steps]: step length after each step
     d, B = spec.d, P * S
+    tol = 1e-10 if prec == lib.CR_F64 else 1e-4
+    scale = pose_operand_scale(spec)
+    tgB = np.repeat(tg, S, 0)
+
+    # ---- step by step: oracle steps from the GPU's iterates
+    xs = np.concatenate([u0b[:, None, :], got[:, :-1]], axis=1)  # GPU state before step k
+    a_s = np.concatenate([np.full((B, 1), 1e-3), alph[:, :-1]], axis=1)
+    one = np.zeros((B, steps, d))
+    Fs1 = np.zeros((B, steps))
+    Ft1 = np.zeros((B, steps))
+    for k in range(steps):
+        _, _, hk = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tgB, 1, xs[:, k], 1, a_s[:, k], history=True)
+        one[:, k] = hk[:, 0, :d]
+        Ft1[:, k] = hk[:, 0, d + 2]
+    Fs1 = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tgB, steps, 0), 1, xs.reshape(B * steps, d),
+                    want=("F",))["F"].reshape(B, steps)
+    rs1 = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tgB, steps, 0), 1, xs.reshape(B * steps, d),
+                    want=("r",))["r"].reshape(B, steps, -1)
+    dec1 = near_ties(Fs1, Ft1, EPS[prec], scale) | kink_or_pi(xs, spec, rs1[:, :, 3:6], prec)
+    err1 = np.abs(got - one).max(axis=2) / spec.umax
+    ok1 = ~dec1
+    print(f"PG {'f64' if prec == lib.CR_F64 else 'f32'} step by step: {int(ok1.sum())} of {B * steps} steps compared "
+          f"({int(dec1.sum())} rounding-decided left out); max error {err1[ok1].max():.2e} of the bound")
+    assert ok1.mean() >= 0.7  # late steps of converged seeds are mostly ties (about 80 % compared)
+    assert err1[ok1].max() <= tol, np.sort(err1[ok1])[-5:]
+
+    # ---- whole trajectories against the oracle's own history
+    _, _, h = O.ik_pg(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b, steps, 1e-3, history=True)
     F0 = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, tg, S, u0b)["F"]
     Fstart = np.concatenate([F0[:, None], h[:, :-1, d + 1]], axis=1)
-    xstart = np.concatenate([u0b[:, None, :], h[:, :-1, :d]], axis=1)  # [B][steps][d]
-    ev = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tg, S, 0).repeat(steps, 0), 1,
-                   xstart.reshape(B * steps, d), want=("r", "g"))
-    rs = ev["r"].reshape(B, steps, -1)
-    gnorm = np.linalg.norm(ev["g"].reshape(B, steps, d), axis=2)
-    Ftrial = h[:, :, d + 2]
-    tie = near_ties(Fstart, Ftrial, EPS[prec], pose_operand_scale(spec))
+    xstart = np.concatenate([u0b[:, None, :], h[:, :-1, :d]], axis=1)
+    rs = O.ik_eval(rbo, orc_weights(), None, lib.CR_TASK_IK6, np.repeat(tg, S, 0).repeat(steps, 0), 1,
+                   xstart.reshape(B * steps, d), want=("r",))["r"].reshape(B, steps, -1)
+    tie = near_ties(Fstart, h[:, :, d + 2], EPS[prec], scale)
     ill = kink_or_pi(xstart, spec, rs[:, :, 3:6], prec)
-    # (d) a decision the GPU took the other way: the comparison stops there too, but only if the
-    # decision's margin |F(trial) - F(start)| is within what the two runs' observed difference can
-    # move it: the start states differ by delta (measured, the GPU's against the oracle's), the trial
-    # points by at most 2 delta plus the step's rounding (alpha times a few hundred eps), each
-    # changing F by at most |grad F| times that, on top of the evaluation band of near_ties.
-    got_prev = np.concatenate([u0b[:, None, :], got[:, :-1]], axis=1)
-    acc_gpu = np.any(got != got_prev, axis=2)
-    acc_orc = Ftrial < Fstart
-    flip = acc_gpu != acc_orc
-    delta = np.linalg.norm(got_prev - xstart, axis=2)
-    alpha = np.concatenate([np.full((B, 1), 1e-3), h[:, :-1, d]], axis=1)
-    e = 64 * EPS[prec] * pose_operand_scale(spec)
-    band = e * (np.sqrt(2 * np.abs(Fstart)) + np.sqrt(2 * np.abs(Ftrial))) + e * e
-    explained = np.abs(Ftrial - Fstart) <= band + gnorm * (3 * delta + 256 * EPS[prec] * alpha * np.sqrt(d))
-    first_flag = first_true(tie | ill)
-    first_flip = first_true(flip)
-    first = np.minimum(first_flag, first_flip)
+    first = first_true(tie | ill)
     checked = np.arange(steps)[None, :] < first[:, None]
     err = np.abs(got - h[:, :, :d]).max(axis=2) / spec.umax
-    tol = 1e-10 if prec == lib.CR_F64 else 1e-4
-    lone = (first_flip < first_flag)  # a flipped decision the a-priori classification did not flag
-    unexplained = lone & ~explained[np.arange(B), np.minimum(first_flip, steps - 1)]
-    print(f"PG {'f64' if prec == lib.CR_F64 else 'f32'}: {steps} steps, {B} seeds; max error "
-          f"{err[checked].max():.2e} of the bound over {int(checked.sum())} compared steps; seeds stopped by a "
-          f"decision tie {int(first_true(tie).__lt__(steps).sum())}, by a kink / near-pi start "
-          f"{int(first_true(ill).__lt__(steps).sum())}, by a flipped decision within the observed drift "
-          f"{int((lone & ~unexplained).sum())} (median first stop at step "
-          f"{np.median(first[first < steps]) if (first < steps).any() else '-'})")
-    assert not unexplained.any(), np.nonzero(unexplained)[0]
+    seed_ok = np.all(~checked | (err <= tol), axis=1)
+    print(f"PG {'f64' if prec == lib.CR_F64 else 'f32'} trajectories: {int(checked.sum())} steps compared up to the first "
+          f"rounding-decided one; {int(seed_ok.sum())} of {B} seeds within the bound throughout (max error "
+          f"{err[checked].max():.2e}); seeds stopped by a decision tie {int((first_true(tie) < steps).sum())}, by a "
+          f"kink / near-pi start {int((first_true(ill) < steps).sum())}")
     assert checked.sum() >= 0.5 * checked.size
-    assert err[checked].max() <= tol, np.sort(err[checked])[-5:]
+    assert seed_ok.mean() >= 0.99
 
 
 @pytest.mark.parametrize("prec", [lib.CR_F64, lib.CR_F32])
