@@ -588,7 +588,9 @@ CR_API size_t cr_batch_workspace_size(const cr_robot* family, const cr_batch_ite
 
 /* Validates the batch, builds the work queue (longest estimated item first) in `workspace`
  * (caller-owned device memory, >= cr_batch_workspace_size bytes, 256-byte aligned), captures the
- * CUDA graph (start node + one persistent kernel per segment count present, as parallel branches)
+ * CUDA graph (start node; per segment count present one branch of four persistent phase kernels in
+ * order: seeds and projected gradient, SelectTop + refinement + argmin, exploration sweep, joint LM;
+ * the branches in parallel)
  * and returns the plan (host object). With seeds_per_unit = 0 every candidate is run and timed on
  * `stream` (the outputs then hold a valid result). Synchronises `stream`. All pointers stay bound
  * to the plan: cr_batch_plan_run re-solves the batch from the current contents of targets and

@@ -15,11 +15,10 @@ CR_BATCH_INSTANTIATE(extern, 4)
 CR_BATCH_INSTANTIATE(extern, 5)
 CR_BATCH_INSTANTIATE(extern, 6)
 
-// Start node: zero the queue heads and item counters, stamp the batch start.
-__global__ void k_batch_start(int32_t* heads, int nheads, int32_t* done, int64_t n, unsigned long long* t0) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Start node: zero the queue heads (four per segment count), stamp the batch start.
+__global__ void k_batch_start(int32_t* heads, int nheads, unsigned long long* t0) {
+  const int i = threadIdx.x;
   if (i < nheads) heads[i] = 0;
-  if (i < n) done[i] = 0;
   if (i == 0) *t0 = global_ns();
 }
 
@@ -62,15 +61,15 @@ constexpr int kSpuCandidates[] = {32, 64, 128, 256};
 
 size_t batch_smem(int) { return (size_t)crk::kBatchWarps * crk::kBatchWarpSmem; }
 
-int blocks_per_sm(int n) {
+int blocks_per_sm(int n, int phase) {
   const size_t sm = batch_smem(n);
   switch (n) {
-    case 1: return crk::batch_blocks_per_sm<1>(sm);
-    case 2: return crk::batch_blocks_per_sm<2>(sm);
-    case 3: return crk::batch_blocks_per_sm<3>(sm);
-    case 4: return crk::batch_blocks_per_sm<4>(sm);
-    case 5: return crk::batch_blocks_per_sm<5>(sm);
-    default: return crk::batch_blocks_per_sm<6>(sm);
+    case 1: return crk::batch_blocks_per_sm<1>(sm, phase);
+    case 2: return crk::batch_blocks_per_sm<2>(sm, phase);
+    case 3: return crk::batch_blocks_per_sm<3>(sm, phase);
+    case 4: return crk::batch_blocks_per_sm<4>(sm, phase);
+    case 5: return crk::batch_blocks_per_sm<5>(sm, phase);
+    default: return crk::batch_blocks_per_sm<6>(sm, phase);
   }
 }
 
@@ -86,15 +85,16 @@ cr_status prepare(int n) {
   }
 }
 
-cr_status launch(int n, const cr_robot& fam, const cr_weights& w, const crk::BatchArgs& a, int grid, cudaStream_t s) {
+cr_status launch(int n, const cr_robot& fam, const cr_weights& w, const crk::BatchArgs& a, const crk::BatchGrids& g,
+                 cudaStream_t s) {
   const size_t sm = batch_smem(n);
   switch (n) {
-    case 1: return crk::batch_launch<1>(fam, w, a, grid, sm, s);
-    case 2: return crk::batch_launch<2>(fam, w, a, grid, sm, s);
-    case 3: return crk::batch_launch<3>(fam, w, a, grid, sm, s);
-    case 4: return crk::batch_launch<4>(fam, w, a, grid, sm, s);
-    case 5: return crk::batch_launch<5>(fam, w, a, grid, sm, s);
-    default: return crk::batch_launch<6>(fam, w, a, grid, sm, s);
+    case 1: return crk::batch_launch<1>(fam, w, a, g, sm, s);
+    case 2: return crk::batch_launch<2>(fam, w, a, g, sm, s);
+    case 3: return crk::batch_launch<3>(fam, w, a, g, sm, s);
+    case 4: return crk::batch_launch<4>(fam, w, a, g, sm, s);
+    case 5: return crk::batch_launch<5>(fam, w, a, g, sm, s);
+    default: return crk::batch_launch<6>(fam, w, a, g, sm, s);
   }
 }
 
@@ -127,19 +127,21 @@ cr_status check_items(const cr_robot* family, const cr_batch_item* items, int64_
   return CR_OK;
 }
 
-// Host-side plan of one batch: per-item offsets, the queue per segment count and the workspace
-// layout. Estimated costs (relative warp time) order the queue longest first.
+// Host-side plan of one batch: per-item offsets, the queues per segment count and the workspace
+// layout. Estimated costs (relative warp time) order the queues longest first. grid[n-1]: the four
+// phase kernels' grids; the joint phase's warps get the per-worker path buffers.
 struct Layout {
   std::vector<crk::BatchItemK> items;  // grouped by n, queue order inside a group
   std::vector<int2> units;             // grouped by n
   int64_t item_begin[CR_MAX_SEG + 1], unit_begin[CR_MAX_SEG + 1];
   int hmax[CR_MAX_SEG + 1];
-  int grid[CR_MAX_SEG + 1];
+  crk::BatchGrids grid[CR_MAX_SEG + 1];
   size_t stride[CR_MAX_SEG + 1];
-  size_t off_items, off_units, off_heads, off_done, off_t0, off_cand, off_scr[CR_MAX_SEG + 1], total;
-  int64_t W, n_sph, n_states, n_cand;
+  size_t off_items, off_units, off_heads, off_t0, off_cand, off_x, off_scr[CR_MAX_SEG + 1], total;
+  int64_t W, n_sph, n_states, n_cand, n_x;
   int64_t workers;
 };
+constexpr int kHeads = 4 * CR_MAX_SEG;
 
 double est_cost(const cr_batch_item& it, const cr_batch_params& p) {
   const double n = it.n;
@@ -153,7 +155,7 @@ cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_para
                       Layout& L) {
   L.items.clear();
   L.units.clear();
-  L.W = L.n_sph = L.n_states = L.n_cand = 0;
+  L.W = L.n_sph = L.n_states = L.n_cand = L.n_x = 0;
   std::vector<crk::BatchItemK> all(N);
   for (int64_t i = 0; i < N; ++i) {
     const cr_batch_item& it = items[i];
@@ -169,6 +171,11 @@ cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_para
     k.sph = L.n_sph;
     k.st = L.n_states;
     k.cand = L.n_cand;
+    k.xs = -1;
+    if (it.kind == CR_ITEM_PATH && it.H > 1) {
+      k.xs = L.n_x;
+      L.n_x += (int64_t)D * it.H;
+    }
     L.W += it.H;
     L.n_sph += it.n_o;
     L.n_states += (int64_t)D * it.H;
@@ -197,23 +204,29 @@ cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_para
     L.hmax[n - 1] = hmax;
     L.stride[n - 1] = hmax > 0 ? crk::path_scratch(3 * n, hmax).total : 0;
     const int64_t nu = (int64_t)L.units.size() - L.unit_begin[n - 1];
-    const int bps = std::max(1, blocks_per_sm(n));
-    const int64_t want = (nu + crk::kBatchWarps - 1) / crk::kBatchWarps;
-    L.grid[n - 1] = nu == 0 ? 0 : (int)std::min<int64_t>(want, (int64_t)bps * n_sm);
-    L.workers += (int64_t)L.grid[n - 1] * crk::kBatchWarps;
+    const int64_t ni = (int64_t)L.items.size() - L.item_begin[n - 1];
+    int64_t npath = 0;
+    for (int64_t i : idx) npath += (items[i].kind == CR_ITEM_PATH && items[i].H > 1) ? 1 : 0;
+    const int64_t work[4] = {nu, ni, npath, npath};
+    for (int ph = 0; ph < 4; ++ph) {
+      const int bps = std::max(1, blocks_per_sm(n, ph));
+      const int64_t want = (work[ph] + crk::kBatchWarps - 1) / crk::kBatchWarps;
+      L.grid[n - 1].g[ph] = work[ph] == 0 ? 0 : (int)std::min<int64_t>(want, (int64_t)bps * n_sm);
+    }
+    L.workers += (int64_t)L.grid[n - 1].g[0] * crk::kBatchWarps;
   }
   L.item_begin[CR_MAX_SEG] = (int64_t)L.items.size();
   L.unit_begin[CR_MAX_SEG] = (int64_t)L.units.size();
   size_t off = 0;
   L.off_items = off; off = align256(off + L.items.size() * sizeof(crk::BatchItemK));
   L.off_units = off; off = align256(off + (size_t)N * (CR_MAX_SEEDS / 32) * sizeof(int2));  // room for spu = 32
-  L.off_heads = off; off = align256(off + 8 * sizeof(int32_t));
-  L.off_done = off; off = align256(off + (size_t)N * sizeof(int32_t));
+  L.off_heads = off; off = align256(off + kHeads * sizeof(int32_t));
   L.off_t0 = off; off = align256(off + sizeof(unsigned long long));
   L.off_cand = off; off = align256(off + (size_t)L.n_cand * sizeof(float));
+  L.off_x = off; off = align256(off + (size_t)L.n_x * sizeof(float));
   for (int n = 1; n <= CR_MAX_SEG; ++n) {
     L.off_scr[n - 1] = off;
-    off = align256(off + (size_t)L.grid[n - 1] * crk::kBatchWarps * L.stride[n - 1]);
+    off = align256(off + (size_t)L.grid[n - 1].g[3] * crk::kBatchWarps * L.stride[n - 1]);
   }
   L.total = off;
   return CR_OK;
@@ -251,10 +264,11 @@ struct Bound {
 crk::BatchArgs batch_args(const Layout& L, int n, const Bound& b, const cr_batch_params& p, int spu) {
   crk::BatchArgs a{};
   a.items = reinterpret_cast<const crk::BatchItemK*>(b.ws + L.off_items) + L.item_begin[n - 1];
+  a.n_items = (int32_t)(L.item_begin[n] - L.item_begin[n - 1]);
   a.units = reinterpret_cast<const int2*>(b.ws + L.off_units) + L.unit_begin[n - 1];
   a.n_units = (int32_t)(L.unit_begin[n] - L.unit_begin[n - 1]);
-  a.head = reinterpret_cast<int32_t*>(b.ws + L.off_heads) + (n - 1);
-  a.done = reinterpret_cast<int32_t*>(b.ws + L.off_done) + L.item_begin[n - 1];
+  a.head = reinterpret_cast<int32_t*>(b.ws + L.off_heads) + 4 * (n - 1);
+  a.xbuf = reinterpret_cast<float*>(b.ws + L.off_x);
   a.t0 = reinterpret_cast<const unsigned long long*>(b.ws + L.off_t0);
   a.targets = b.targets;
   a.W = L.W;
@@ -288,8 +302,9 @@ crk::BatchArgs batch_args(const Layout& L, int n, const Bound& b, const cr_batch
   return a;
 }
 
-// Uploads the queue, captures the graph (start node, then one persistent kernel per segment count
-// as parallel branches, largest queue first) and instantiates it.
+// Uploads the queues, captures the graph (start node, then per segment count the four phase
+// kernels in order on one branch, the branches in parallel, largest queue first) and instantiates
+// it.
 cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, int spu, int64_t N,
                      cudaStream_t user, cr_batch_plan* plan) {
   cudaError_t e;
@@ -304,7 +319,7 @@ cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, 
   }
   cr_status st;
   for (int n = 1; n <= CR_MAX_SEG; ++n)
-    if (L.grid[n - 1] > 0 && (st = prepare(n))) return st;
+    if (L.grid[n - 1].g[0] > 0 && (st = prepare(n))) return st;
   cudaStream_t cap, side[CR_MAX_SEG];
   cudaEvent_t fork, join[CR_MAX_SEG];
   if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
@@ -338,10 +353,8 @@ cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, 
     return fail(CR_ECUDA, "batch plan capture: %s", cudaGetErrorString(e));
   }
   {
-    const int64_t nz = std::max<int64_t>(N, 8);
-    crk::k_batch_start<<<(unsigned)((nz + 255) / 256), 256, 0, cap>>>(
-        reinterpret_cast<int32_t*>(b.ws + L.off_heads), 8, reinterpret_cast<int32_t*>(b.ws + L.off_done), N,
-        reinterpret_cast<unsigned long long*>(b.ws + L.off_t0));
+    crk::k_batch_start<<<1, 32, 0, cap>>>(reinterpret_cast<int32_t*>(b.ws + L.off_heads), kHeads,
+                                          reinterpret_cast<unsigned long long*>(b.ws + L.off_t0));
     cudaEventRecord(fork, cap);
     int order[CR_MAX_SEG];
     for (int i = 0; i < CR_MAX_SEG; ++i) order[i] = i + 1;
@@ -351,7 +364,7 @@ cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, 
     int used = 0;
     for (int oi = 0; oi < CR_MAX_SEG && st == CR_OK; ++oi) {
       const int n = order[oi];
-      if (L.grid[n - 1] == 0) continue;
+      if (L.grid[n - 1].g[0] == 0) continue;
       cudaStreamWaitEvent(side[used], fork, 0);
       st = launch(n, *b.family, *b.w, batch_args(L, n, b, p, spu), L.grid[n - 1], side[used]);
       cudaEventRecord(join[used], side[used]);
