@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     ap.add_argument("--items", type=int, default=synth.N_RAGGED,
                     help="items of the ragged batch (default 16384; smaller for profiling cases)")
+    ap.add_argument("--breakdown", action="store_true",
+                    help="ragged workload: also time the batch's IK items and its path items (n <= 3, n >= 4) as "
+                         "batches of their own")
     ap.add_argument("--workload", default="ik3",
                     choices=["ik3", "ik1", "path", "traj", "prm", "calib", "ragged", "e1", "e2", "self"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
@@ -756,6 +759,22 @@ def other_workload(args):
                 cpu = oracle_sample(oracle_items, len(items), "problems/s", "items of the batch")
                 out["oracle_agreement"] = agreement(fl & 1, cpu)
                 out["cpu_baseline"] = cpu
+            if args.breakdown:
+                w0 = np.concatenate([[0], np.cumsum(items[:, 2])])
+                o0 = np.concatenate([[0], np.cumsum(items[:, 4])])
+                bd = {}
+                for name, sel in (("ik_items", items[:, 0] == 0), ("path_items", items[:, 0] == 1),
+                                  ("path_items_n_le_3", (items[:, 0] == 1) & (items[:, 1] <= 3)),
+                                  ("path_items_n_ge_4", (items[:, 0] == 1) & (items[:, 1] >= 4))):
+                    idx = np.nonzero(sel)[0]
+                    sub = api.BatchSolver(fam, items[idx], synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=spu,
+                                          device=dev)
+                    sub.set_inputs(np.concatenate([targets[w0[i]:w0[i + 1]] for i in idx]),
+                                   np.concatenate([spheres[o0[i]:o0[i + 1]] for i in idx] + [np.zeros((0, 4))]))
+                    sub.plan()
+                    r, _ = gpu_form(torch, lambda: sub.run(), len(idx), "problems/s", "the subset as a batch of its own")
+                    bd[name] = {"items": len(idx), "ms": r["ms"]}
+                out["breakdown"] = bd
             return out
 
         dtype = "f32"
