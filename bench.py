@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--targets", type=int, default=synth.P_3SEG, help="targets per GPU (default 4096)")
     ap.add_argument("--items", type=int, default=synth.N_RAGGED,
                     help="items of the ragged batch (default 16384; smaller for profiling cases)")
+    ap.add_argument("--paths", type=int, default=synth.P_PATH,
+                    help="path workload: paths (default 512; smaller for profiling cases)")
     ap.add_argument("--breakdown", action="store_true",
                     help="ragged workload: also time the batch's IK items and its path items (n <= 3, n >= 4) as "
                          "batches of their own")
@@ -396,7 +398,7 @@ def other_workload(args):
 
         dtype = "f64"
     elif args.workload == "path":
-        spec, ik, P, H = synth.ROBOT_4SEG, synth.IK_PATH0, synth.P_PATH, synth.H_PATH
+        spec, ik, P, H = synth.ROBOT_4SEG, synth.IK_PATH0, args.paths, synth.H_PATH
 
         def fkb(uu):
             T, bb = api.fk(api.robot_struct(spec), torch.as_tensor(uu.T.copy(), dtype=torch.float64, device=dev), True)
@@ -407,7 +409,7 @@ def other_workload(args):
         wps = api.waypoints_soa(wp, device=dev)
         fn = lambda: s.solve(wps)
         units, unit, metric = P, "paths/s", "path following paths/s (64 waypoints, 32 spheres, FP32 + FP64 block Cholesky)"
-        wl = "path_4seg_512paths_64wp_32spheres_warm30_joint20"
+        wl = f"path_4seg_{P}paths_64wp_32spheres_warm30_joint20"
         def path_success(sol, n):
             pos = sol.pos.reshape(n, H).max(1).values.cpu().numpy()
             rot = sol.rot.reshape(n, H).max(1).values.cpu().numpy()

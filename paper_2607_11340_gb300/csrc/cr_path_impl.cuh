@@ -173,6 +173,131 @@ __device__ bool joint_solve_warp(const TA* Af, const double* g, double* z, doubl
   return ok;
 }
 
+// Packs slot values v (this lane's slots of a swept block, the D x D part) into Zs [DD] (packed
+// lower triangle) for the block-times-vector products of the back substitution.
+template <int D>
+__device__ inline void unpack_block(const AugSlots<D>& sl, const double (&v)[AugSlots<D>::SL], double* Zs) {
+#pragma unroll
+  for (int s = 0; s < AugSlots<D>::SL; ++s)
+    if (sl.on[s] && sl.r[s] < D) Zs[tri(sl.r[s], sl.c[s])] = v[s];
+}
+
+// The same block-tridiagonal system as joint_solve_warp, eliminated from both ends at once (a
+// twisted factorisation) by two warps: warp 0 eliminates t = 0 .. m-1 forward (S_t = M_t - w_s^2
+// S_{t-1}^-1, z_t = S_t^-1 (r_t + w_s z_{t-1})), warp 1 eliminates t = H-1 .. m+1 backward (T_t = M_t -
+// w_s^2 T_{t+1}^-1, y_t = T_t^-1 (r_t + w_s y_{t+1})); warp 0 then solves the middle block,
+// (M_m - w_s^2 S_{m-1}^-1 - w_s^2 T_{m+1}^-1) x_m = r_m + w_s z_{m-1} + w_s y_{m+1}, and the two warps
+// substitute back towards their ends (x_t = z_t + w_s S_t^-1 x_{t+1} below m, x_t = y_t + w_s
+// T_t^-1 x_{t-1} above). The two sequential chains are half as long. Every thread of the block
+// calls it (it synchronises the block); warps 0 and 1 work, col / colr / Zs hold one scratch per
+// working warp ([2][32], [2][32], [2][DD]). Returns whether every pivot was positive.
+template <typename TA, int D>
+__device__ bool joint_solve_twisted(const TA* Af, const double* g, double* z, double* Zg, double* col, double* colr,
+                                    double* Zs, int* okf, int H, double ws, double lam) {
+  constexpr int SL = AugSlots<D>::SL, DD = D * (D + 1) / 2, ZS = aug_stride<D>();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = H / 2;
+  const double ws2 = ws * ws;
+  const AugSlots<D> sl = aug_slots<D>(lane);
+  double* mycol = col + 32 * wid;
+  double* mycolr = colr + 32 * wid;
+  double* myZs = Zs + DD * wid;
+  if (threadIdx.x == 0) *okf = 1;
+  __syncthreads();
+  // diagonal block of waypoint t with its damping, plus ws^2 times the slots of prev / prev2 (the
+  // neighbours' -S^-1), and the right-hand side -g_t + ws (the neighbours' z, rows zn1 / zn2)
+  auto build = [&](int t, const double* prev, const double* prev2, int zn1, int zn2, double (&v)[SL]) {
+    const double nb = double((t > 0) + (t + 1 < H));
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      if (!sl.on[s]) continue;
+      const int i = sl.r[s], j = sl.c[s];
+      double a;
+      if (i < D) {
+        a = double(Af[(size_t)t * DD + tri(i, j)]);
+        if (i == j) {
+          a += ws * nb;
+          a += lam * fmax(a, 1e-12);
+        }
+        if (prev) a = fma(ws2, prev[s], a);
+        if (prev2) a = fma(ws2, prev2[s], a);
+      } else {
+        a = 0.0;
+        if (j < D) {
+          a = -g[t * D + j];
+          if (zn1 >= 0) a += ws * z[zn1 * D + j];
+          if (zn2 >= 0) a += ws * z[zn2 * D + j];
+        }
+      }
+      v[s] = a;
+    }
+  };
+  double v[SL];
+  bool ok = true;
+  if (wid < 2) {
+    const int dir = wid == 0 ? 1 : -1;
+    const int t0 = wid == 0 ? 0 : H - 1, t1 = wid == 0 ? m : m;  // exclusive end
+    for (int t = t0; t != t1; t += dir) {
+      double prevs[SL];
+      const bool has_prev = t != t0;
+#pragma unroll
+      for (int s = 0; s < SL; ++s) prevs[s] = v[s];
+      build(t, has_prev ? prevs : nullptr, nullptr, has_prev ? t - dir : -1, -1, v);
+      ok = sweep_aug<double, D>(v, sl, mycol, mycolr) && ok;
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        Zg[(size_t)t * ZS + s * 32 + lane] = v[s];
+        if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) z[t * D + sl.c[s]] = v[s];
+      }
+      __syncwarp();
+    }
+    if (!ok && lane == 0) atomicAnd(okf, 0);
+  }
+  __syncthreads();
+  // middle block (warp 0)
+  if (wid == 0) {
+    double pl[SL], pr[SL];
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      pl[s] = m > 0 ? Zg[(size_t)(m - 1) * ZS + s * 32 + lane] : 0.0;
+      pr[s] = m + 1 < H ? Zg[(size_t)(m + 1) * ZS + s * 32 + lane] : 0.0;
+    }
+    build(m, m > 0 ? pl : nullptr, m + 1 < H ? pr : nullptr, m > 0 ? m - 1 : -1, m + 1 < H ? m + 1 : -1, v);
+    const bool okm = sweep_aug<double, D>(v, sl, mycol, mycolr);
+#pragma unroll
+    for (int s = 0; s < SL; ++s)
+      if (sl.on[s] && sl.r[s] == D && sl.c[s] < D) z[m * D + sl.c[s]] = v[s];
+    if (!okm && lane == 0) atomicAnd(okf, 0);
+  }
+  __syncthreads();
+  // back substitution towards the ends: x_t = z_t - ws V_t x_n, V_t = -S_t^-1 (or -T_t^-1) as
+  // stored, n the neighbour on the middle's side
+  if (wid < 2) {
+    const int dir = wid == 0 ? -1 : 1;
+    const int t0 = wid == 0 ? m - 1 : m + 1, t1 = wid == 0 ? -1 : H;
+    for (int t = t0; t != t1; t += dir) {
+      double vb[SL];
+#pragma unroll
+      for (int s = 0; s < SL; ++s) vb[s] = Zg[(size_t)t * ZS + s * 32 + lane];
+      unpack_block<D>(sl, vb, myZs);
+      __syncwarp();
+      const int n = t - dir;
+      if (lane < D) {
+        double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; j += 2) {
+          acc0 = fma(myZs[lane >= j ? tri(lane, j) : tri(j, lane)], z[n * D + j], acc0);
+          if (j + 1 < D) acc1 = fma(myZs[lane >= j + 1 ? tri(lane, j + 1) : tri(j + 1, lane)], z[n * D + j + 1], acc1);
+        }
+        z[t * D + lane] = fma(-ws, acc0 + acc1, z[t * D + lane]);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  return *okf != 0;
+}
+
 // One CTA per path, one thread per waypoint (blockDim = H rounded up to a warp). Per iteration:
 // every thread forms its waypoint's J^T J block and gradient (bulk precision) plus the smoothness
 // terms; warp 0 solves the block system in FP64; all threads evaluate the trial path.
@@ -185,7 +310,7 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
   const int tid = threadIdx.x, H = a.H;
   const int64_t PH = a.P * H;
   // shared layout: spheres (T, double) | g [H][D] | z [H][D] | col, colr [32] | Zs [DD] | red [32] |
-  // misc [8] | Af [H][DD] (T) | ush [H][D] (T)
+  // misc [8] | col2, colr2 [2][32], Zs2 [2][DD] | Af [H][DD] (T) | ush [H][D] (T)
   size_t off = 0;
   Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
   off += (size_t)a.no * sizeof(Sphere4<T>);
@@ -199,7 +324,10 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
   double* Zs = colr + 32;
   double* red = Zs + DD;
   double* misc = red + 32;  // [8]: ok flag
-  T* Af = reinterpret_cast<T*>(misc + 8);
+  double* col2 = misc + 8;  // the twisted solve's scratch: col, colr [2][32], Zs [2][DD]
+  double* colr2 = col2 + 64;
+  double* Zs2 = colr2 + 64;
+  T* Af = reinterpret_cast<T*>(Zs2 + 2 * DD);
   T* ush = Af + (size_t)H * DD;
   double* Zg = a.Z + (size_t)p * H * aug_stride<D>();
   if (OBST) {
@@ -268,8 +396,12 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     }
     const double F = block_sum(Fl, red);
     __syncthreads();
-    // 2. FP64 block elimination (warp 0)
-    if (tid < 32) {
+    // 2. FP64 block elimination: from both ends by two warps (from 4 waypoints on), else by warp 0
+    if (H >= 4 && blockDim.x >= 64) {
+      const bool okw = joint_solve_twisted<T, D>(Af, g, z, Zg, col2, colr2, Zs2, reinterpret_cast<int*>(misc + 1), H,
+                                                 ws, lam);
+      if (tid == 0) misc[0] = okw ? 1.0 : 0.0;
+    } else if (tid < 32) {
       const bool okw = joint_solve_warp<T, D>(Af, g, z, Zg, col, colr, Zs, H, ws, lam);
       if (tid == 0) misc[0] = okw ? 1.0 : 0.0;
     }
@@ -383,7 +515,7 @@ template <typename T> PathArgs<T> path_args(const PathLaunch& l) {
 inline size_t path_joint_smem(int no, int H, int D, size_t tsize) {
   size_t off = (size_t)no * (4 * tsize + 32);
   off = (off + 15) & ~size_t(15);
-  off += sizeof(double) * ((size_t)2 * H * D + 64 + (size_t)D * (D + 1) / 2 + 32 + 8);
+  off += sizeof(double) * ((size_t)2 * H * D + 64 + (size_t)D * (D + 1) / 2 + 32 + 8 + 128 + (size_t)D * (D + 1));
   off += tsize * ((size_t)H * D * (D + 1) / 2 + (size_t)H * D);
   return off;
 }
