@@ -8,7 +8,9 @@ CUDA path, and the CUDA path never imports it.
 Arrays here are row-major "array of structures": states ``u[B][d]`` with ``d = 3 n`` and the
 tendons of segment i at ``u[:, 3 i : 3 i + 3]``; targets ``[P][7]`` = position then unit
 quaternion (w, x, y, z) for full-pose IK, or position then tip axis (and a zero) for 5-DoF IK;
-spheres ``[N_o][4]`` = centre then radius.
+obstacles either spheres ``[N_o][4]`` = centre then radius, or a pair ``(spheres, prims)`` adding
+primitive records ``[N_p][16]`` (``OBS`` doubles each: kind, radius, then the kind's parameters;
+see ``obstacle_records``). Per-problem obstacle sets carry a leading ``[P]`` axis on both.
 
 Functions with no independent pin say "parity unpinned" in their docstring.
 """
@@ -191,11 +193,57 @@ def ik_rows(robot: Robot, n_spheres: int, weights: Weights | None = None) -> int
     return lib().orc_ik_rows(C.byref(robot), C.byref(w), C.c_int(n_spheres))
 
 
-def _spheres(spheres):
-    if spheres is None or len(spheres) == 0:
+OBS = 16  # doubles per obstacle record
+SPHERE, CAPSULE, BOX = 0, 1, 2
+
+
+def obstacle_records(spheres=None, prims=None, P=None):
+    """Obstacle records as the oracle reads them (Eq. ik_coll's clearance rows, with Sec. IV-C's
+    convex pieces): ``[n][OBS]`` = kind, radius r, then
+      sphere  (0): centre;
+      capsule (1): end points a, b;
+      box     (2): centre, half extents, orientation quaternion (w, x, y, z), box frame to world;
+    zeros elsewhere. Spheres ``[n_o][4]`` become kind-0 records ahead of the primitive records
+    ``[n_p][OBS]``. With P, both inputs carry a leading ``[P]`` axis and so does the result."""
+    lead = () if P is None else (P,)
+    parts = []
+    if spheres is not None:
+        s = _f64(spheres).reshape(lead + (-1, 4))
+        rec = np.zeros(s.shape[:-1] + (OBS,))
+        rec[..., 1] = s[..., 3]
+        rec[..., 2:5] = s[..., 0:3]
+        parts.append(rec)
+    if prims is not None:
+        parts.append(_f64(prims).reshape(lead + (-1, OBS)))
+    if not parts:
+        return np.zeros(lead + (0, OBS))
+    return np.ascontiguousarray(np.concatenate(parts, axis=-2))
+
+
+def obstacle_sd(record, x, gradient=False):
+    """Signed distance of points x [B][3] to the core of one obstacle record [OBS] (a sphere's
+    centre, a capsule's segment, a solid box), and with gradient its derivative in x [B][3]."""
+    rec = _f64(record).reshape(OBS)
+    x = _f64(x).reshape(-1, 3)
+    sd = np.zeros(x.shape[0])
+    g = np.zeros_like(x) if gradient else None
+    lib().orc_obstacle_sd(_dp(rec), _dp(x), C.c_int64(x.shape[0]), _dp(sd), _dp(g))
+    return (sd, g) if gradient else sd
+
+
+def _split_obstacles(obs):
+    if isinstance(obs, tuple):
+        return obs
+    return obs, None
+
+
+def _spheres(obs):
+    """obs: None, spheres [no][4], or (spheres or None, prims [np][OBS] or None) -> (n, records)."""
+    sp, pr = _split_obstacles(obs)
+    rec = obstacle_records(sp, pr)
+    if rec.shape[0] == 0:
         return 0, None
-    s = _f64(spheres).reshape(-1, 4)
-    return s.shape[0], s
+    return rec.shape[0], rec
 
 
 def ik_eval(robot, weights, spheres, kind, targets, S, u, want=("F",), threads=None):
@@ -465,12 +513,14 @@ def opcount_ik(robot, weights, spheres, kind, target, u, box=True):
 # ---------------------------------------------------------------------------------------------
 # Trajectory planning, path following, calibration
 # ---------------------------------------------------------------------------------------------
-def _per_problem_spheres(spheres, P):
-    """spheres [P][no][4] (or None) -> (no, flat array)."""
-    if spheres is None:
+def _per_problem_spheres(obs, P):
+    """obs: None, spheres [P][no][4], or (spheres or None, prims [P][np][OBS] or None)
+    -> (obstacles per problem, records [P][n][OBS])."""
+    sp, pr = _split_obstacles(obs)
+    rec = obstacle_records(sp, pr, P=P)
+    if rec.shape[1] == 0:
         return 0, None
-    s = _f64(spheres).reshape(P, -1, 4)
-    return s.shape[1], np.ascontiguousarray(s)
+    return rec.shape[1], rec
 
 
 def traj_rows(robot, n_spheres, Tn, weights=None):
@@ -550,6 +600,9 @@ def _i32p(a):
 
 
 def _sph_flat(spheres):
+    """PRM obstacles: spheres [no][4] only."""
+    if isinstance(spheres, tuple):
+        raise ValueError("the PRM functions take sphere obstacles only")
     if spheres is None or len(spheres) == 0:
         return 0, None
     s = np.ascontiguousarray(_f64(spheres).reshape(-1, 4))

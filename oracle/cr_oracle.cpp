@@ -35,6 +35,8 @@
 //     collision-checked straight edges), ConnectToRoadmap, Dijkstra and ResampleLinear.
 //   * Self-contact rows between backbone samples of non-adjacent segments (Eq. ik_coll over the
 //     robot itself), as standalone functions.
+//   * Obstacles as convex pieces (Sec. IV-C): spheres, capsules and boxes, each entering the
+//     clearance rows through its signed distance.
 //   * Coupled tendon routing (Eq. l_eq summed over the segments a tendon runs through): the map
 //     between per-segment and actuator displacements, as standalone functions.
 //
@@ -452,6 +454,83 @@ static void quat_to_R(const double* q, double R[3][3]) {
   R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Obstacles of the clearance rows (Eq. ik_coll). Sec. IV-C approximates a non-convex obstacle by a
+// union of convex pieces; the pieces here are spheres, capsules and boxes. Each obstacle is a record
+// of OR_OBS doubles: [0] kind, [1] radius r, then the kind's parameters. The clearance of a point x
+// is its signed distance sd(x) to the obstacle's core set, less r:
+//   kind 0, sphere:  core = the centre c = [2..4]; sd = |x - c|.
+//   kind 1, capsule: core = the segment from a = [2..4] to b = [5..7]; sd = the distance from x to
+//                    its nearest point a + t (b - a), t in [0, 1] (t = 0 when a = b).
+//   kind 2, box:     core = the solid box with centre c = [2..4], half extents h = [5..7] and
+//                    orientation the quaternion (w, x, y, z) = [8..11] (box frame to world, taken
+//                    normalised). In box coordinates p = R^T (x - c), with q_a = |p_a| - h_a:
+//                    outside (some q_a > 0) sd = the Euclidean distance to the box,
+//                    sqrt(sum_a max(q_a, 0)^2); inside, sd = max_a q_a <= 0, minus the distance to
+//                    the nearest face. With r > 0 the obstacle is a box with rounded edges.
+// Any other kind reads as a sphere. A state's rows are sqrt(rho_c) max(0, r + r_body + delta - sd(p))
+// over its backbone samples p and the obstacles.
+static const int OR_OBS = 16;
+
+static inline int obstacle_kind(const double* ob) {
+  const int k = (int)ob[0];
+  return k == 1 || k == 2 ? k : 0;
+}
+
+template <class T> static T obstacle_sd(const double* ob, const T* x) {
+  const int kind = obstacle_kind(ob);
+  if (kind == 1) {
+    const double e[3] = {ob[5] - ob[2], ob[6] - ob[3], ob[7] - ob[4]};
+    const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    const T w[3] = {x[0] - T(ob[2]), x[1] - T(ob[3]), x[2] - T(ob[4])};
+    T t(0.0);
+    if (ee > 0.0) t = (w[0] * T(e[0]) + w[1] * T(e[1]) + w[2] * T(e[2])) / T(ee);
+    if (re(t) < 0.0) t = T(0.0);
+    if (re(t) > 1.0) t = T(1.0);
+    const T d[3] = {w[0] - t * T(e[0]), w[1] - t * T(e[1]), w[2] - t * T(e[2])};
+    return Sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  }
+  if (kind == 2) {
+    double R[3][3];
+    quat_to_R(ob + 8, R);
+    const T w[3] = {x[0] - T(ob[2]), x[1] - T(ob[3]), x[2] - T(ob[4])};
+    T q[3];
+    bool outside = false;
+    for (int a = 0; a < 3; ++a) {
+      T p = T(R[0][a]) * w[0] + T(R[1][a]) * w[1] + T(R[2][a]) * w[2];
+      if (re(p) < 0.0) p = T(0.0) - p;
+      q[a] = p - T(ob[5 + a]);
+      if (re(q[a]) > 0.0) outside = true;
+    }
+    if (outside) {
+      T s(0.0);
+      for (int a = 0; a < 3; ++a)
+        if (re(q[a]) > 0.0) s = s + q[a] * q[a];
+      return Sqrt(s);
+    }
+    T m = q[0];
+    for (int a = 1; a < 3; ++a)
+      if (re(q[a]) > re(m)) m = q[a];
+    return m;
+  }
+  const T d[3] = {x[0] - T(ob[2]), x[1] - T(ob[3]), x[2] - T(ob[4])};
+  return Sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+// Is x closer than `reach` to the core of obstacle ob? On true, sd = its signed distance. Spheres
+// decide on the squared distance, so that no square root is taken for an inactive pair.
+template <class T> static bool obstacle_within(const double* ob, const T* x, double reach, T& sd) {
+  if (obstacle_kind(ob) == 0) {
+    const T dx = x[0] - T(ob[2]), dy = x[1] - T(ob[3]), dz = x[2] - T(ob[4]);
+    const T d2 = dx * dx + dy * dy + dz * dz;
+    if (!(re(d2) < reach * reach)) return false;
+    sd = Sqrt(d2);
+    return true;
+  }
+  sd = obstacle_sd(ob, x);
+  return re(sd) < reach;
+}
+
 // Pose residual rows (6): IK6 -> [w_p (p - p_t); w_R Log(R_t^T R)]; IK5 -> [w_p (p - p_t); w_R (z - z_t)]
 // where z is the tip axis (third column of R) and z_t the target axis.
 template <class T>
@@ -526,10 +605,10 @@ static int self_rows_bb(const OrRobot& rb, const T* bb, double rho_s, double del
 //   2n rows  sqrt(rho_b) max(0, L_i - lmax_i), sqrt(rho_b) max(0, lmin_i - L_i)
 // both:
 //   n rows   sqrt(rho_k) max(0, theta_i - thmax_i)
-//   n*nb*no  sqrt(rho_c) max(0, r_s + r_body + delta - |p_ik - c_s|)   (sample-sphere pairs)
+//   n*nb*no  sqrt(rho_c) max(0, r_o + r_body + delta - sd_o(p_ik))   (sample-obstacle pairs)
 template <class T>
 static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
-                                 const double* spheres, const T* u, const FkOut<T>& fk,
+                                 const double* obs, const T* u, const FkOut<T>& fk,
                                  const T* backbone, T* r, T* coll_pen) {
   int k = 0;
   const int d = rb.n * rb.m;
@@ -562,12 +641,11 @@ static int state_constraint_rows(const OrRobot& rb, const OrWeights& W, int no,
     for (int q = 0; q < rb.n * rb.nb; ++q) {
       const T* x = backbone + 3 * q;
       for (int s = 0; s < no; ++s) {
-        const double* sp = spheres + 4 * s;
-        T dx = x[0] - T(sp[0]), dy = x[1] - T(sp[1]), dz = x[2] - T(sp[2]);
-        double reach = sp[3] + rb.rbody + W.delta;
-        T dist2 = dx * dx + dy * dy + dz * dz;
-        if (re(dist2) < reach * reach) {
-          T row = sc * (T(reach) - Sqrt(dist2));
+        const double* ob = obs + OR_OBS * s;
+        const double reach = ob[1] + rb.rbody + W.delta;
+        T sd;
+        if (obstacle_within(ob, x, reach, sd)) {
+          T row = sc * (T(reach) - sd);
           r[k++] = row;
           cp += row * row;
         } else {
@@ -594,14 +672,14 @@ static bool needs_backbone(const OrWeights& W, int no) { return no > 0 || W.rho_
 // Full IK residual of one seed: 6 pose rows followed by the constraint rows.
 template <class T>
 static int ik_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
-                       const double* spheres, int kind, const double* tgt, const T* u, T* r,
+                       const double* obs, int kind, const double* tgt, const T* u, T* r,
                        T* coll_pen) {
   FkOut<T> fk;
   const bool nbb = needs_backbone(W, no);
   std::vector<T> bb(nbb ? 3 * rb.n * rb.nb : 0);
   forward_kinematics(rb, P, u, fk, nbb ? bb.data() : nullptr);
   pose_residual(kind, W, tgt, fk.R, fk.p, r);
-  return 6 + state_constraint_rows(rb, W, no, spheres, u, fk, nbb ? bb.data() : nullptr, r + 6,
+  return 6 + state_constraint_rows(rb, W, no, obs, u, fk, nbb ? bb.data() : nullptr, r + 6,
                                    coll_pen);
 }
 
@@ -884,24 +962,24 @@ struct IkProblem {
   const OrRobot* rb;
   const OrWeights* W;
   int no;
-  const double* spheres;
+  const double* obs;
   int kind;
   const double* tgt;
   int d() const { return rb->n * rb->m; }
   int rows() const { return ik_rows(*rb, *W, no); }
   void res(const double* u, double* r) const {
     Params<double> P = params_of<double>(*rb);
-    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r, (double*)nullptr);
+    ik_residual(*rb, P, *W, no, obs, kind, tgt, u, r, (double*)nullptr);
   }
   void cres(const cd* u, cd* r) const {
     Params<cd> P = params_of<cd>(*rb);
-    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r, (cd*)nullptr);
+    ik_residual(*rb, P, *W, no, obs, kind, tgt, u, r, (cd*)nullptr);
   }
   double cost(const double* u, double* coll) const {
     std::vector<double> r(rows());
     Params<double> P = params_of<double>(*rb);
     double cp = 0;
-    ik_residual(*rb, P, *W, no, spheres, kind, tgt, u, r.data(), &cp);
+    ik_residual(*rb, P, *W, no, obs, kind, tgt, u, r.data(), &cp);
     if (coll) *coll = 0.5 * cp;
     return half_sq(r.data(), rows());
   }
@@ -1065,6 +1143,21 @@ int orc_so3_log(const double* E /*[B][9]*/, int64_t B, double* w /*[B][3]*/) {
   return 0;
 }
 
+// Signed distance sd of points x [B][3] to the core of obstacle record ob [OR_OBS], and with
+// grad != NULL its gradient d sd / dx [B][3] (complex step).
+int orc_obstacle_sd(const double* ob, const double* x, int64_t B, double* sd, double* grad) {
+  for (int64_t b = 0; b < B; ++b) {
+    sd[b] = obstacle_sd(ob, x + 3 * b);
+    if (!grad) continue;
+    for (int a = 0; a < 3; ++a) {
+      cd xc[3] = {x[3 * b], x[3 * b + 1], x[3 * b + 2]};
+      xc[a] += cd(0.0, 1e-30);
+      grad[3 * b + a] = obstacle_sd(ob, xc).imag() / 1e-30;
+    }
+  }
+  return 0;
+}
+
 int orc_quat_to_R(const double* q, int64_t B, double* R /*[B][9]*/) {
   for (int64_t b = 0; b < B; ++b) {
     double M[3][3];
@@ -1079,12 +1172,12 @@ int orc_ik_rows(const OrRobot* rb, const OrWeights* W, int no) { return ik_rows(
 // IK residuals r[B][rows], cost F[B], collision part of the cost coll[B] (nullable), gradient
 // g[B][d] (nullable) and residual Jacobian J[B][rows][d] (nullable). Target of seed b is
 // targets[7 * (b / S)].
-int orc_ik_eval(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_ik_eval(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
                 const double* targets, int64_t S, const double* u, int64_t B, double* r, double* F,
                 double* coll, double* g, double* J, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
-    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    IkProblem pb{rb, W, no, obs, kind, targets + 7 * (b / S)};
     int nr = pb.rows();
     std::vector<double> rr(nr);
     pb.res(u + d * b, rr.data());
@@ -1101,7 +1194,7 @@ int orc_ik_eval(const OrRobot* rb, const OrWeights* W, int no, const double* sph
 
 // Gradient of the summed IK cost with respect to the kinematic parameters (L_i, r_c,i),
 // complex step on each parameter: grad[2n] = d/dL_1..n then d/dr_c,1..n of sum_b F_b.
-int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const double* obs,
                       int kind, const double* targets, int64_t S, const double* u, int64_t B,
                       double* grad) {
   int d = rb->n * rb->m;
@@ -1114,7 +1207,7 @@ int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const doubl
       int nr = ik_rows(*rb, *W, no);
       std::vector<cd> x(d), r(nr);
       for (int a = 0; a < d; ++a) x[a] = cd(u[d * b + a], 0.0);
-      ik_residual(*rb, P, *W, no, spheres, kind, targets + 7 * (b / S), x.data(), r.data(), (cd*)nullptr);
+      ik_residual(*rb, P, *W, no, obs, kind, targets + 7 * (b / S), x.data(), r.data(), (cd*)nullptr);
       cd F = half_sq(r.data(), nr);
       acc += F.imag() / CS_H;
     }
@@ -1127,12 +1220,12 @@ int orc_ik_param_grad(const OrRobot* rb, const OrWeights* W, int no, const doubl
 // the iterate after every iteration [iters][B][d]; lam/nu/F (in/out, [B]); acc[B][iters] (nullable)
 // the accept flags; trace[B][iters][2] (nullable) the cost at the iteration's start and at its trial
 // point. lam/nu must be initialised by the caller (lambda0, 2).
-int orc_ik_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_ik_lm(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int iters, double* lam,
               double* nu, double* F, double* hist, uint8_t* acc, double* trace, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
-    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    IkProblem pb{rb, W, no, obs, kind, targets + 7 * (b / S)};
     LmState st{lam[b], nu[b], 0.0, 0.0, 0.0};
     double* x = u + d * b;
     for (int it = 0; it < iters; ++it) {
@@ -1322,12 +1415,12 @@ int orc_project_arc(const double* v, int64_t B, double thmax, double lmin, doubl
 // Stage-one projected gradient on every seed: u[B][d] in place, F[B] out; hist (nullable)
 // [B][steps][d + 3] as in pg_rule.
 // alpha_per (nullable): seed b starts with step length alpha_per[b] instead of alpha0.
-int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
               const double* targets, int64_t S, double* u, int64_t B, int steps, double alpha0,
               const double* alpha_per, double* F, double* hist, int threads) {
   int d = rb->n * rb->m;
   parallel_for(B, threads, [&](int64_t b) {
-    IkProblem pb{rb, W, no, spheres, kind, targets + 7 * (b / S)};
+    IkProblem pb{rb, W, no, obs, kind, targets + 7 * (b / S)};
     pg_run_one(pb, u + d * b, steps, alpha_per ? alpha_per[b] : alpha0, F + b,
                hist ? hist + (size_t)b * steps * (d + 3) : nullptr);
   });
@@ -1336,9 +1429,10 @@ int orc_ik_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spher
 
 uint64_t orc_splitmix64_at(uint64_t s0, uint64_t k) { return splitmix64_at(s0, k); }
 
-// Seeds of problem p (global index p0 + q): u[P][S][d]. With spheres, a seed whose backbone is
-// closer than r_s + r_body + delta to a sphere is redrawn (attempts 0..7; the last draw is kept).
-int orc_seeds(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, uint64_t base,
+// Seeds of problem p (global index p0 + q): u[P][S][d]. With obstacles, a seed with a backbone sample
+// closer than r_o + r_body + delta to an obstacle's core is redrawn (attempts 0..7; the last draw is
+// kept).
+int orc_seeds(const OrRobot* rb, const OrWeights* W, int no, const double* obs, uint64_t base,
               int64_t p0, int64_t P, int64_t S, double* u) {
   int d = rb->n * rb->m;
   Params<double> Pd = params_of<double>(*rb);
@@ -1363,10 +1457,9 @@ int orc_seeds(const OrRobot* rb, const OrWeights* W, int no, const double* spher
         bool hit = false;
         for (int k = 0; k < rb->n * rb->nb && !hit; ++k)
           for (int c = 0; c < no && !hit; ++c) {
-            const double* sp = spheres + 4 * c;
-            double dx = bb[3 * k] - sp[0], dy = bb[3 * k + 1] - sp[1], dz = bb[3 * k + 2] - sp[2];
-            double reach = sp[3] + rb->rbody + W->delta;
-            if (dx * dx + dy * dy + dz * dz < reach * reach) hit = true;
+            const double* ob = obs + OR_OBS * c;
+            double sd;
+            if (obstacle_within(ob, &bb[3 * k], ob[1] + rb->rbody + W->delta, sd)) hit = true;
           }
         if (!hit) break;
       }
@@ -1409,10 +1502,10 @@ int orc_topk(const float* cost, const float* coll, const double* u /*[S][d]*/, i
 // Final acceptance of one solution: position error (m), rotation error (rad: Log angle for IK6,
 // angle between tip axes for IK5), limits (|u| <= umax + tol, |sum u| <= tol, or for OR_MODEL_ARC
 // lmin - tol <= L <= lmax + tol; theta <= thmax + tol)
-// and collision-free (every sample at least r_s + r_body from every sphere centre).
+// and collision-free (every sample at least r_o + r_body from every obstacle's core).
 // With self_check, collision-free also requires every pair of samples of segments two or more
 // apart to be at least 2 r_body apart (the self-contact rows' reading, without the margin delta).
-static void accept_one(const OrRobot& rb, int no, const double* spheres, int kind,
+static void accept_one(const OrRobot& rb, int no, const double* obs, int kind,
                        const double* tgt, const double* u, double tol, double* pos, double* rot,
                        uint8_t* lim_ok, uint8_t* col_ok, bool self_check = false) {
   Params<double> Pd = params_of<double>(rb);
@@ -1455,10 +1548,9 @@ static void accept_one(const OrRobot& rb, int no, const double* spheres, int kin
   bool free = true;
   for (int k = 0; k < rb.n * rb.nb && free; ++k)
     for (int c = 0; c < no && free; ++c) {
-      const double* sp = spheres + 4 * c;
-      double dx = bb[3 * k] - sp[0], dy = bb[3 * k + 1] - sp[1], dz = bb[3 * k + 2] - sp[2];
-      double reach = sp[3] + rb.rbody;
-      if (dx * dx + dy * dy + dz * dz < reach * reach) free = false;
+      const double* ob = obs + OR_OBS * c;
+      double sd;
+      if (obstacle_within(ob, &bb[3 * k], ob[1] + rb.rbody, sd)) free = false;
     }
   if (self_check) {
     const double g2 = 4.0 * rb.rbody * rb.rbody;
@@ -1488,7 +1580,7 @@ struct OrIkParams {
 
 // Algorithm 1 per problem. Outputs u_out[P][d], F_out[P], pos[P], rot[P], success[P];
 // cand_out (nullable) [P][n_final] the SelectTop indices; stage1_F (nullable) [P][S].
-int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
                  const double* targets, int64_t P, const OrIkParams* prm, double* u_out,
                  double* F_out, double* pos, double* rot, uint8_t* success, int32_t* cand_out,
                  double* stage1_F, int threads) {
@@ -1496,9 +1588,9 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
   int S = prm->S, K = prm->n_final;
   parallel_for(P, threads, [&](int64_t q) {
     const double* tgt = targets + 7 * q;
-    IkProblem pb{rb, W, no, spheres, kind, tgt};
+    IkProblem pb{rb, W, no, obs, kind, tgt};
     std::vector<double> U((size_t)S * d), F(S), C(S);
-    orc_seeds(rb, W, no, spheres, prm->seed, prm->p0 + q, 1, S, U.data());
+    orc_seeds(rb, W, no, obs, prm->seed, prm->p0 + q, 1, S, U.data());
     // Stage one (ParallelOptimize with k_init steps): projected gradient on every seed.
     for (int s = 0; s < S; ++s) {
       if (prm->k_init > 0) pg_run_one(pb, U.data() + (size_t)s * d, prm->k_init, prm->alpha0, &F[s]);
@@ -1540,18 +1632,18 @@ int orc_solve_ik(const OrRobot* rb, const OrWeights* W, int no, const double* sp
     std::memcpy(uo, X.data() + (size_t)best * d, sizeof(double) * d);
     F_out[q] = bestF;
     uint8_t lim_ok, col_ok;
-    accept_one(*rb, no, spheres, kind, tgt, uo, prm->lim_tol, &pos[q], &rot[q], &lim_ok, &col_ok, W->rho_s > 0.0);
+    accept_one(*rb, no, obs, kind, tgt, uo, prm->lim_tol, &pos[q], &rot[q], &lim_ok, &col_ok, W->rho_s > 0.0);
     success[q] = (pos[q] <= prm->pos_tol && rot[q] <= prm->rot_tol && lim_ok && col_ok) ? 1 : 0;
   });
   return 0;
 }
 
-int orc_accept(const OrRobot* rb, int no, const double* spheres, int kind, const double* targets,
+int orc_accept(const OrRobot* rb, int no, const double* obs, int kind, const double* targets,
                const double* u, int64_t P, double tol, double* pos, double* rot, uint8_t* lim_ok,
                uint8_t* col_ok, int self_check) {
   int d = rb->n * rb->m;
   for (int64_t q = 0; q < P; ++q)
-    accept_one(*rb, no, spheres, kind, targets + 7 * q, u + (size_t)d * q, tol, pos + q, rot + q,
+    accept_one(*rb, no, obs, kind, targets + 7 * q, u + (size_t)d * q, tol, pos + q, rot + q,
                lim_ok + q, col_ok + q, self_check != 0);
   return 0;
 }
@@ -1562,7 +1654,7 @@ int orc_accept(const OrRobot* rb, int no, const double* spheres, int kind, const
 // box = 0 counts the cost without the rows that vanish on stage one's feasible set (tendon model:
 // bound and sum-zero rows; arc model: length and curvature rows), so a projected trial point needs
 // none of them.
-int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
                         const double* target, const double* u, int box, long long* out) {
   int d = rb->n * rb->m;
   g_count_minimal = true;
@@ -1572,7 +1664,7 @@ int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const dou
   for (int i = 0; i < rb->n; ++i) { P.L[i] = Cnt(rb->L[i]); P.rc[i] = Cnt(rb->rc[i]); }
   std::vector<Cnt> x(d), r(ik_rows(*rb, *W, no));
   for (int a = 0; a < d; ++a) x[a] = Cnt(u[a], true);
-  const int rows = ik_residual(*rb, P, *W, no, spheres, kind, target, x.data(), r.data(), (Cnt*)nullptr);
+  const int rows = ik_residual(*rb, P, *W, no, obs, kind, target, x.data(), r.data(), (Cnt*)nullptr);
   Cnt F = half_sq(r.data(), rows);
   (void)F;
   g_count_minimal = false;
@@ -1584,9 +1676,9 @@ int orc_opcount_ik_form(const OrRobot* rb, const OrWeights* W, int no, const dou
   return 0;
 }
 
-int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, int kind,
+int orc_opcount_ik(const OrRobot* rb, const OrWeights* W, int no, const double* obs, int kind,
                    const double* target, const double* u, long long* out) {
-  return orc_opcount_ik_form(rb, W, no, spheres, kind, target, u, 1, out);
+  return orc_opcount_ik_form(rb, W, no, obs, kind, target, u, 1, out);
 }
 
 }  // extern "C"
@@ -1617,7 +1709,7 @@ static int lm_iteration_ag(const std::function<double(const double*, double*, do
 // u_{Tn-1}. Tendon lengths are L_i + u_ij with fixed L_i, so tendon speeds are differences of u.
 template <class T>
 static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
-                         const double* spheres, const double* u_start, const double* goal, int Tn,
+                         const double* obs, const double* u_start, const double* goal, int Tn,
                          const T* x, T* r) {
   const int d = rb.n * rb.m;
   const int nbp = 3 * rb.n * rb.nb;
@@ -1638,7 +1730,7 @@ static int traj_residual(const OrRobot& rb, const Params<T>& P, const OrWeights&
       r[k++] = sv * hinge(v - T(W.vmax));
       r[k++] = sv * hinge(T(-W.vmax) - v);
     }
-    k += state_constraint_rows(rb, W, no, spheres, &U[(size_t)t * d], fk[t],
+    k += state_constraint_rows(rb, W, no, obs, &U[(size_t)t * d], fk[t],
                                nbb ? &bb[(size_t)t * nbp] : (const T*)nullptr, r + k, (T*)nullptr);
     if (t >= 2) {
       for (int q = 0; q < d; ++q) {
@@ -1663,7 +1755,7 @@ struct TrajProblem {
   const OrRobot* rb;
   const OrWeights* W;
   int no;
-  const double* spheres;
+  const double* obs;
   const double* u_start;
   const double* goal;
   int Tn;
@@ -1672,7 +1764,7 @@ struct TrajProblem {
   double cost(const double* x) const {
     std::vector<double> r(rows());
     Params<double> P = params_of<double>(*rb);
-    traj_residual(*rb, P, *W, no, spheres, u_start, goal, Tn, x, r.data());
+    traj_residual(*rb, P, *W, no, obs, u_start, goal, Tn, x, r.data());
     return half_sq(r.data(), rows());
   }
   // gradient of F by complex step on F itself
@@ -1682,7 +1774,7 @@ struct TrajProblem {
     Params<cd> P = params_of<cd>(*rb);
     for (int c = 0; c < n; ++c) {
       for (int q = 0; q < n; ++q) xc[q] = cd(x[q], q == c ? CS_H : 0.0);
-      traj_residual(*rb, P, *W, no, spheres, u_start, goal, Tn, xc.data(), r.data());
+      traj_residual(*rb, P, *W, no, obs, u_start, goal, Tn, xc.data(), r.data());
       g[c] = half_sq(r.data(), rows()).imag() / CS_H;
     }
   }
@@ -1712,11 +1804,11 @@ static void traj_pg(const TrajProblem& tp, double* x, int steps, double alpha0, 
 // sqrt(w_s)(u_t - u_{t-1}) for t = 1..H-1 (d each).
 template <class T>
 static int path_residual(const OrRobot& rb, const Params<T>& P, const OrWeights& W, int no,
-                         const double* spheres, const double* wp, int H, const T* x, T* r) {
+                         const double* obs, const double* wp, int H, const T* x, T* r) {
   const int d = rb.n * rb.m;
   int k = 0;
   for (int t = 0; t < H; ++t)
-    k += ik_residual(rb, P, W, no, spheres, OR_IK6, wp + 7 * t, x + (size_t)t * d, r + k, (T*)nullptr);
+    k += ik_residual(rb, P, W, no, obs, OR_IK6, wp + 7 * t, x + (size_t)t * d, r + k, (T*)nullptr);
   T ss = T(std::sqrt(W.w_s));
   for (int t = 1; t < H; ++t)
     for (int q = 0; q < d; ++q) r[k++] = ss * (x[(size_t)t * d + q] - x[(size_t)(t - 1) * d + q]);
@@ -1731,7 +1823,7 @@ struct PathProblem {
   const OrRobot* rb;
   const OrWeights* W;
   int no;
-  const double* spheres;
+  const double* obs;
   const double* wp;
   int H;
   int d() const { return rb->n * rb->m; }
@@ -1739,7 +1831,7 @@ struct PathProblem {
   double cost(const double* x) const {
     std::vector<double> r(path_rows(*rb, *W, no, H));
     Params<double> P = params_of<double>(*rb);
-    path_residual(*rb, P, *W, no, spheres, wp, H, x, r.data());
+    path_residual(*rb, P, *W, no, obs, wp, H, x, r.data());
     return half_sq(r.data(), (int)r.size());
   }
   // F, A = J^T J and g = J^T r. The waypoint rows of t depend only on u_t, so their Jacobian block
@@ -1750,7 +1842,7 @@ struct PathProblem {
     for (int a = 0; a < n; ++a) g[a] = 0.0;
     double F = 0.0;
     for (int t = 0; t < H; ++t) {
-      IkProblem pb{rb, W, no, spheres, OR_IK6, wp + 7 * t};
+      IkProblem pb{rb, W, no, obs, OR_IK6, wp + 7 * t};
       int nr = pb.rows();
       std::vector<double> r(nr), J((size_t)nr * dd);
       pb.res(x + (size_t)t * dd, r.data());
@@ -1805,32 +1897,32 @@ extern "C" {
 
 int orc_traj_rows(const OrRobot* rb, const OrWeights* W, int no, int Tn) { return traj_rows(*rb, *W, no, Tn); }
 
-// Trajectory cost / gradient / residuals of P problems. u_start [P][d], goal [P][7], spheres
-// [P][no][4] (per problem), x [P][(Tn-1)][d] (the free states u_1..u_{Tn-1}).
-int orc_traj_eval(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+// Trajectory cost / gradient / residuals of P problems. u_start [P][d], goal [P][7], obs
+// [P][no][OR_OBS] (per problem), x [P][(Tn-1)][d] (the free states u_1..u_{Tn-1}).
+int orc_traj_eval(const OrRobot* rb, const OrWeights* W, int no, const double* obs,
                   const double* u_start, const double* goal, int Tn, const double* x, int64_t P,
                   double* F, double* g, double* r, int threads) {
   if (Tn < 2) return 1;
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
-    TrajProblem tp{rb, W, no, no > 0 ? spheres + (size_t)4 * no * q : nullptr, u_start + (size_t)d * q,
+    TrajProblem tp{rb, W, no, no > 0 ? obs + (size_t)OR_OBS * no * q : nullptr, u_start + (size_t)d * q,
                    goal + 7 * q, Tn};
     const double* xq = x + (size_t)tp.nx() * q;
     if (F) F[q] = tp.cost(xq);
     if (g) tp.grad(xq, g + (size_t)tp.nx() * q);
     if (r) {
       Params<double> Pd = params_of<double>(*rb);
-      traj_residual(*rb, Pd, *W, no, tp.spheres, tp.u_start, tp.goal, Tn, xq, r + (size_t)tp.rows() * q);
+      traj_residual(*rb, Pd, *W, no, tp.obs, tp.u_start, tp.goal, Tn, xq, r + (size_t)tp.rows() * q);
     }
   });
   return 0;
 }
 
-int orc_traj_pg(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* u_start,
+int orc_traj_pg(const OrRobot* rb, const OrWeights* W, int no, const double* obs, const double* u_start,
                 const double* goal, int Tn, double* x, int64_t P, int steps, double alpha0, double* F, int threads) {
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
-    TrajProblem tp{rb, W, no, no > 0 ? spheres + (size_t)4 * no * q : nullptr, u_start + (size_t)d * q,
+    TrajProblem tp{rb, W, no, no > 0 ? obs + (size_t)OR_OBS * no * q : nullptr, u_start + (size_t)d * q,
                    goal + 7 * q, Tn};
     traj_pg(tp, x + (size_t)tp.nx() * q, steps, alpha0, F + q);
   });
@@ -1880,13 +1972,13 @@ static void traj_refine_one(const OrRobot* rb, const OrWeights* W, int no, const
 // projected-gradient steps. x_out [P][Tn][d] (all states, u_0 included); F_out [P]; goal_pos /
 // goal_rot [P]; speed / accel [P]: the largest |du|/dt / v_max and |d2u|/dt^2 / a_max; lim_ok /
 // col_ok [P]: every state within limits / collision-free.
-int orc_solve_traj(const OrRobot* rb, const OrWeights* W, int no, const double* spheres,
+int orc_solve_traj(const OrRobot* rb, const OrWeights* W, int no, const double* obs,
                    const double* u_start, const double* goal, int64_t P, int Tn, const OrIkParams* ik_prm,
                    int k_traj, double alpha0, double* x_out, double* F_out, double* goal_pos, double* goal_rot,
                    double* speed, double* accel, uint8_t* lim_ok, uint8_t* col_ok, int threads) {
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
-    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    const double* sp = no > 0 ? obs + (size_t)OR_OBS * no * q : nullptr;
     OrIkParams prm = *ik_prm;
     prm.p0 = ik_prm->p0 + q;
     double ug[OR_MAXSEG * 3], Fg, pe, re;
@@ -1904,13 +1996,13 @@ int orc_solve_traj(const OrRobot* rb, const OrWeights* W, int no, const double* 
 
 // Trajectory refinement from given initial states (x_io [P][Tn][d] in, refined states out), with
 // the metrics of orc_solve_traj: the second stage of Algorithm 2 after any initialiser.
-int orc_traj_refine(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* u_start,
+int orc_traj_refine(const OrRobot* rb, const OrWeights* W, int no, const double* obs, const double* u_start,
                     const double* goal, int64_t P, int Tn, int k_traj, double alpha0, double lim_tol, double* x_io,
                     double* F_out, double* goal_pos, double* goal_rot, double* speed, double* accel,
                     uint8_t* lim_ok, uint8_t* col_ok, int threads) {
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
-    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    const double* sp = no > 0 ? obs + (size_t)OR_OBS * no * q : nullptr;
     traj_refine_one(rb, W, no, sp, u_start + (size_t)d * q, goal + 7 * q, Tn, x_io + (size_t)Tn * d * q, k_traj,
                     alpha0, lim_tol, F_out + q, goal_pos + q, goal_rot + q, speed + q, accel + q, lim_ok + q,
                     col_ok + q);
@@ -1951,18 +2043,18 @@ int orc_calib_jacobian(const OrRobot* rb, const double* U, const double* Pm, int
 
 int orc_path_rows(const OrRobot* rb, const OrWeights* W, int no, int H) { return path_rows(*rb, *W, no, H); }
 
-// Path residual r [rows] of one path (spheres [no][4], waypoints wp [H][7], x [H][d]); and its full
+// Path residual r [rows] of one path (obs [no][OR_OBS], waypoints wp [H][7], x [H][d]); and its full
 // Jacobian J [rows][H d] by complex step over all H d variables (small H; pins the blockwise
 // assembly of the normal equations).
-int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp,
+int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const double* obs, const double* wp,
                       int H, const double* x, double* r, double* J) {
   Params<double> Pd = params_of<double>(*rb);
-  path_residual(*rb, Pd, *W, no, spheres, wp, H, x, r);
+  path_residual(*rb, Pd, *W, no, obs, wp, H, x, r);
   if (J) {
     const int n = H * rb->n * rb->m, nr = path_rows(*rb, *W, no, H);
     cs_jacobian([&](const cd* xx, cd* rr) {
       Params<cd> P = params_of<cd>(*rb);
-      path_residual(*rb, P, *W, no, spheres, wp, H, xx, rr);
+      path_residual(*rb, P, *W, no, obs, wp, H, xx, rr);
     }, n, nr, x, J);
   }
   return 0;
@@ -1970,10 +2062,10 @@ int orc_path_residual(const OrRobot* rb, const OrWeights* W, int no, const doubl
 
 // Joint LM on one path: x [H][d] in/out, iters iterations; hist [iters][H][d] nullable.
 // trace [iters][2] (nullable): the cost at each iteration's start and at its trial point.
-int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp, int H,
+int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* obs, const double* wp, int H,
                 double* x, int iters, double* lam, double* nu, double* F_out, double* hist, uint8_t* acc,
                 double* trace) {
-  PathProblem pp{rb, W, no, spheres, wp, H};
+  PathProblem pp{rb, W, no, obs, wp, H};
   LmState st{*lam, *nu, 0.0};
   const int n = pp.nx();
   for (int it = 0; it < iters; ++it) {
@@ -1991,18 +2083,18 @@ int orc_path_lm(const OrRobot* rb, const OrWeights* W, int no, const double* sph
 
 // Path following per path: IK at waypoint 0 (Algorithm 1 with ik_prm, seed counter p0 + q), then
 // for t >= 1 k_warm LM iterations of the waypoint's IK residual from u*_{t-1}, then k_joint joint
-// LM iterations over the whole path (lambda0 = ik_prm->lambda0). spheres [P][no][4], wp [P][H][7].
+// LM iterations over the whole path (lambda0 = ik_prm->lambda0). obs [P][no][OR_OBS], wp [P][H][7].
 // Outputs x_out [P][H][d], F_out [P] (joint cost), pos / rot [P][H] (per-waypoint errors),
 // stage_x [P][H][d] (nullable: the trajectory before the joint stage), lim_ok / col_ok [P];
 // trace [P][(H-1) k_warm + k_joint][2] (nullable): start and trial costs of every LM iteration of the
 // warm sweep (waypoint by waypoint) and then of the joint stage.
-int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* spheres, const double* wp,
+int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* obs, const double* wp,
                    int64_t P, int H, const OrIkParams* ik_prm, int k_warm, int k_joint, double* x_out,
                    double* F_out, double* pos, double* rot, double* stage_x, uint8_t* lim_ok, uint8_t* col_ok,
                    double* trace, int threads) {
   const int d = rb->n * rb->m;
   parallel_for(P, threads, [&](int64_t q) {
-    const double* sp = no > 0 ? spheres + (size_t)4 * no * q : nullptr;
+    const double* sp = no > 0 ? obs + (size_t)OR_OBS * no * q : nullptr;
     const double* wq = wp + (size_t)7 * H * q;
     double* X = x_out + (size_t)H * d * q;
     double* tr = trace ? trace + 2 * ((size_t)(H - 1) * k_warm + k_joint) * q : nullptr;
@@ -2062,6 +2154,7 @@ int orc_solve_path(const OrRobot* rb, const OrWeights* W, int no, const double* 
 //  * ResampleLinear: T states at equal arc length along the path (arc length = the Dijkstra
 //    distances), state 0 the start and state T-1 the goal; with no path, the linear interpolation
 //    u_start + t/(T-1) (u_goal - u_start).
+// The PRM functions take sphere obstacles only, as [no][4] = (centre, radius).
 // ---------------------------------------------------------------------------------------------
 
 static bool prm_collides(const OrRobot& rb, const Params<double>& Pd, double delta, int no, const double* sp,

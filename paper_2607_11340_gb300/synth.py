@@ -12,6 +12,9 @@ Recipes (all numpy PCG64, ``np.random.default_rng(seed)``):
   * full-pose targets: FK of in-bound states, giving position plus unit quaternion (w >= 0).
   * 5-DoF targets: position plus tip axis (the third column of R).
   * spheres: centre uniform in a box, radius uniform in [r_lo, r_hi].
+  * capsules and boxes: centre uniform in a box, direction / orientation uniformly random (a
+    normalised Gaussian vector / quaternion), half lengths and radii uniform in ranges; shelves
+    as boxes of a fixed layout.
 
 The paper's benchmarks (1000 uniform IK targets, a 27-sphere lattice, shelf and cabinet scenes,
 letter-shaped paths) are replaced by these synthetic stand-ins of the same shape.
@@ -187,6 +190,129 @@ def spheres_uniform(rng: np.random.Generator, count: int, lo, hi, r_lo: float, r
     c = rng.uniform(lo, hi, size=(count, 3))
     r = rng.uniform(r_lo, r_hi, size=(count, 1))
     return np.concatenate([c, r], axis=1)
+
+
+# Obstacle primitives (capsules, boxes): records of PRIM_DOUBLES values, the layout of the library's
+# scene: kind, radius, then end points (capsule) or centre, half extents and orientation quaternion
+# (w, x, y, z) (box). The paper's shelf and cabinet scenes are unions of such convex pieces.
+PRIM_DOUBLES = 16
+PRIM_CAPSULE, PRIM_BOX = 1, 2
+
+
+def capsule_record(a, b, r: float) -> np.ndarray:
+    rec = np.zeros(PRIM_DOUBLES)
+    rec[0], rec[1] = PRIM_CAPSULE, r
+    rec[2:5], rec[5:8] = a, b
+    return rec
+
+
+def box_record(c, h, q, r: float = 0.0) -> np.ndarray:
+    rec = np.zeros(PRIM_DOUBLES)
+    rec[0], rec[1] = PRIM_BOX, r
+    rec[2:5], rec[5:8], rec[8:12] = c, h, q
+    return rec
+
+
+def random_quaternions(rng: np.random.Generator, count: int) -> np.ndarray:
+    """Uniform random rotations: normalised 4-D Gaussian vectors, w >= 0."""
+    q = rng.normal(size=(count, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    q[q[:, 0] < 0] *= -1.0
+    return q
+
+
+def prims_uniform(rng: np.random.Generator, n_capsules: int, n_boxes: int, lo, hi, r_lo: float, r_hi: float,
+                  half_lo: float, half_hi: float, rounded: float = 0.5) -> np.ndarray:
+    """[n_capsules + n_boxes][PRIM_DOUBLES]: capsules with centre uniform in [lo, hi], a uniformly
+    random direction, half length in [half_lo, half_hi] and radius in [r_lo, r_hi]; boxes with centre
+    uniform in [lo, hi], half extents in [half_lo, half_hi] each, a uniformly random orientation and,
+    with probability ``rounded``, an edge radius in [r_lo, r_hi] (else sharp)."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    out = []
+    for _ in range(n_capsules):
+        c = rng.uniform(lo, hi)
+        v = rng.normal(size=3)
+        v *= rng.uniform(half_lo, half_hi) / np.linalg.norm(v)
+        out.append(capsule_record(c - v, c + v, rng.uniform(r_lo, r_hi)))
+    q = random_quaternions(rng, n_boxes)
+    for k in range(n_boxes):
+        c = rng.uniform(lo, hi)
+        h = rng.uniform(half_lo, half_hi, size=3)
+        r = rng.uniform(r_lo, r_hi) if rng.uniform() < rounded else 0.0
+        out.append(box_record(c, h, q[k], r))
+    return np.array(out).reshape(-1, PRIM_DOUBLES)
+
+
+def prims_clear_of(rng: np.random.Generator, n_capsules: int, n_boxes: int, points: np.ndarray, margin_box: float,
+                   r_lo: float, r_hi: float, half_lo: float, half_hi: float, clearance: float, sd,
+                   max_tries: int = 100000) -> np.ndarray:
+    """Primitives drawn as in ``prims_uniform`` inside the bounding box of ``points`` [M][3] dilated by
+    ``margin_box``, each redrawn while its surface is closer than ``clearance`` to any of the points.
+    ``sd(record, points) -> [M]`` is the caller's signed distance to the primitive's core."""
+    lo = points.min(axis=0) - margin_box
+    hi = points.max(axis=0) + margin_box
+    out = []
+    for nc, nbx in ((n_capsules, 0), (0, n_boxes)):
+        got = 0
+        tries = 0
+        while got < nc + nbx and tries < max_tries:
+            tries += 1
+            rec = prims_uniform(rng, nc and 1, nbx and 1, lo, hi, r_lo, r_hi, half_lo, half_hi)[0]
+            if np.min(sd(rec, points)) >= rec[1] + clearance:
+                out.append(rec)
+                got += 1
+        if got < nc + nbx:
+            raise RuntimeError("could not place the primitives")
+    return np.array(out).reshape(-1, PRIM_DOUBLES)
+
+
+def shelf_prims(centre, yaw: float, width: float, depth: float, height: float, n_boards: int,
+                thickness: float) -> np.ndarray:
+    """A shelf as boxes: two side walls, a back panel, top and bottom and n_boards - 2 boards in
+    between, open towards -x in the shelf's frame (rotated by yaw about z, bottom at centre)."""
+    cz, sz = math.cos(0.5 * yaw), math.sin(0.5 * yaw)
+    q = np.array([cz, 0.0, 0.0, sz])
+    rot = np.array([[math.cos(yaw), -math.sin(yaw), 0.0], [math.sin(yaw), math.cos(yaw), 0.0], [0.0, 0.0, 1.0]])
+    centre = np.asarray(centre, dtype=np.float64)
+    t = 0.5 * thickness
+    parts = [((0.0, -0.5 * width + t, 0.5 * height), (0.5 * depth, t, 0.5 * height)),
+             ((0.0, 0.5 * width - t, 0.5 * height), (0.5 * depth, t, 0.5 * height)),
+             ((0.5 * depth - t, 0.0, 0.5 * height), (t, 0.5 * width, 0.5 * height))]
+    for k in range(n_boards):
+        z = t + k * (height - thickness) / max(n_boards - 1, 1)
+        parts.append(((0.0, 0.0, z), (0.5 * depth, 0.5 * width, t)))
+    return np.array([box_record(centre + rot @ np.array(c), h, q) for c, h in parts])
+
+
+# Trajectories among shelves (stands in for the shelf scenes of Sec. V-C): per problem a shelf of
+# 6 boxes (3 boards) 0.13 m from the base axis at a uniformly random azimuth, open towards the robot,
+# plus capsules uniform around the robot; start and goal are the first two of 64 in-bound draws
+# whose backbone clears every obstacle by r_body + delta.
+N_SHELF_CAPS = 4
+
+
+def shelf_traj_workload(robot: RobotSpec, P: int, clearance_cost, seed: int = 0, n_caps: int = N_SHELF_CAPS):
+    """Returns u_start [P][d], goal states [P][d] and primitives [P][6 + n_caps][PRIM_DOUBLES].
+    ``clearance_cost(states [M][d], prims [n][PRIM_DOUBLES]) -> [M]`` is the caller's clearance
+    part of the cost (zero when every backbone sample clears every obstacle by r_body + delta)."""
+    rng = np.random.default_rng(seed)
+    reach = float(sum(robot.L))
+    starts, goals, scenes = [], [], []
+    while len(scenes) < P:
+        psi = rng.uniform(0.0, 2.0 * math.pi)
+        c = 0.13 * np.array([math.cos(psi), math.sin(psi), 0.0])
+        shelf = shelf_prims(c, psi + math.pi, 0.22, 0.12, 0.32, 3, 0.008)
+        caps = prims_uniform(rng, n_caps, 0, [-reach, -reach, 0.05], [reach, reach, reach], 0.004, 0.01, 0.02, 0.06)
+        prims = np.concatenate([shelf, caps])
+        cand = hexagon_states(rng, 64, robot.n, robot.umax)
+        free = np.flatnonzero(np.asarray(clearance_cost(cand, prims)) == 0.0)
+        if len(free) < 2:
+            continue
+        starts.append(cand[free[0]])
+        goals.append(cand[free[1]])
+        scenes.append(prims)
+    return np.array(starts), np.array(goals), np.array(scenes)
 
 
 # ---------------------------------------------------------------------------------------------
