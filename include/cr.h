@@ -59,7 +59,7 @@ typedef enum {
 typedef enum { CR_F32 = 0, CR_F64 = 1 } cr_dtype;
 
 #define CR_MAX_SEG 6
-#define CR_MAX_SPHERES 256
+#define CR_MAX_SPHERES 256 /* obstacles (spheres + primitives) per scene or problem */
 #define CR_MAX_NB 64
 #define CR_MAX_SEEDS 256
 
@@ -102,7 +102,7 @@ typedef struct {
   double r_c[CR_MAX_SEG];       /* tendon routing radii (m) */
   double u_max[CR_MAX_SEG];     /* bound |u_ij| <= u_max_i (m), Eq. ik_limits */
   double theta_max[CR_MAX_SEG]; /* bending-angle limit (rad), Eq. ik_limits */
-  double r_body;                /* backbone radius added to every sphere radius (m) */
+  double r_body;                /* backbone radius added to every obstacle radius (m) */
   double l_min[CR_MAX_SEG];     /* CR_MODEL_ARC: length bounds l_min_i <= L_i <= l_max_i (m) */
   double l_max[CR_MAX_SEG];
 } cr_robot;
@@ -128,14 +128,36 @@ typedef struct {
                                          rho_s > 0. */
 } cr_weights;
 
-/* Obstacles: spheres for the clearance rows of Eq. ik_coll. Host struct; `spheres` is a device
- * array [n_o][4] = (centre x, y, z, radius), FP64, shared by all problems; with per_problem = 1 it
- * is [P][n_o][4] and problem p uses its own n_o spheres (trajectory and path workloads place
- * obstacles around each problem). */
+/* Obstacle primitives beyond spheres: the convex pieces into which Sec. IV-C decomposes a
+ * non-convex obstacle (a shelf or a cabinet of Sec. V-C is a set of boxes). A primitive is a record
+ * of CR_PRIM_DOUBLES doubles: [0] kind, [1] radius r >= 0, then
+ *   CR_PRIM_CAPSULE: [2..4] end point a, [5..7] end point b;
+ *   CR_PRIM_BOX:     [2..4] centre c, [5..7] half extents h >= 0, [8..11] orientation quaternion
+ *                    (w, x, y, z), box frame to world (normalised when read);
+ * the rest unused. Its clearance rows are those of a sphere with the centre distance replaced by
+ * the signed distance sd(x) from the backbone sample x to the primitive's core set (the segment
+ * [a, b]; the solid box, sd < 0 inside it): sqrt(rho_c) max(0, r + r_body + delta - sd(x)). A box
+ * with r > 0 has rounded edges. A record of any other kind is read as a sphere of radius r centred at
+ * [2..4]. */
+#define CR_PRIM_DOUBLES 16
+#define CR_PRIM_SPHERE 0
+#define CR_PRIM_CAPSULE 1
+#define CR_PRIM_BOX 2
+
+/* Obstacles: spheres and primitives for the clearance rows of Eq. ik_coll. Host struct; `spheres`
+ * is a device array [n_o][4] = (centre x, y, z, radius), FP64, shared by all problems; with
+ * per_problem = 1 it is [P][n_o][4] and problem p uses its own n_o spheres (trajectory and path
+ * workloads place obstacles around each problem). `prims` is a device array [n_p][CR_PRIM_DOUBLES]
+ * (FP64), [P][n_p][CR_PRIM_DOUBLES] with per_problem = 1. n_o + n_p <= CR_MAX_SPHERES. Primitives are
+ * taken by cr_cost_grad, cr_cost_vjp, cr_pg_steps, cr_lm_step, cr_seeds, cr_solve_ik (and its stages
+ * and cr_solve_ik_static), cr_solve_ik_plain, cr_traj_cost, cr_solve_traj and cr_solve_path; the
+ * batch and PRM entry points return CR_EINVAL for n_p > 0. */
 typedef struct {
   const double* spheres;
   int32_t n_o;         /* 0..CR_MAX_SPHERES */
-  int32_t per_problem; /* 0: one sphere set for all problems; 1: one set per problem */
+  int32_t per_problem; /* 0: one obstacle set for all problems; 1: one set per problem */
+  const double* prims; /* device [n_p][CR_PRIM_DOUBLES] (or per problem); NULL when n_p = 0 */
+  int32_t n_p;         /* 0..CR_MAX_SPHERES - n_o */
 } cr_scene;
 
 typedef enum {
@@ -195,7 +217,8 @@ CR_API cr_status cr_fk_jac(const cr_robot* robot, const void* u, int64_t B, void
 /* Per-state cost F_b = 1/2 sum r^2 of an IK task, with rows
  *   pose (6), bounds sqrt(rho_b) max(0, +-u - u_max) (2 per tendon), sum-zero sqrt(rho_eq) sum_j u_ij
  *   (1 per segment), curvature sqrt(rho_k) max(0, theta_i - theta_max_i) (1 per segment) and
- *   clearance sqrt(rho_c) max(0, r_s + r_body + delta - |x_k - c_s|) per (sample, sphere) pair.
+ *   clearance sqrt(rho_c) max(0, r_s + r_body + delta - |x_k - c_s|) per (sample, sphere) pair and
+ *   sqrt(rho_c) max(0, r + r_body + delta - sd(x_k)) per (sample, primitive) pair.
  * cost_out [B] (required), coll_out [B] (nullable: the clearance part of F_b), grad_u_out [3n][B]
  * (nullable: dF_b / du), grad_param_out [2n][B] (nullable: dF_b / dL_i for i < n, then dF_b / dr_c,i),
  * all in `dtype`. The gradients come from a hand-written reverse sweep over the segments. */
@@ -234,8 +257,8 @@ CR_API cr_status cr_pg_steps(const cr_robot* robot, const cr_scene* scene, const
 
 /* SampleSeeds of Algorithm 1: S seeds for each of P problems (global index p0 + p), uniform on
  * each segment's feasible hexagon, from the counter-based SplitMix64 generator keyed by `seed`.
- * With spheres, a seed whose backbone comes closer than r_s + r_body + delta to a sphere is
- * redrawn, at most 8 draws. u_out [3n][P * S] in `dtype` (seed s of problem p at p * S + s). */
+ * With obstacles, a seed whose backbone comes closer than r + r_body + delta to an obstacle's core
+ * (a sphere's centre, a primitive's core set) is redrawn, at most 8 draws. u_out [3n][P * S] in `dtype` (seed s of problem p at p * S + s). */
 CR_API cr_status cr_seeds(const cr_robot* robot, const cr_scene* scene, const cr_weights* w,
                    uint64_t seed, int64_t p0, int64_t P, int32_t S, void* u_out, int32_t dtype,
                    cr_stream stream);

@@ -36,21 +36,26 @@ def weights_struct(w: synth.WeightSpec) -> lib.cr_weights:
 
 
 class Scene:
-    """Spheres resident on the device in FP64: [n_o][4] (centre, radius) shared by all problems, or
-    [P][n_o][4] with per_problem=True (each problem its own set)."""
+    """Obstacles resident on the device in FP64: spheres [n_o][4] (centre, radius) and primitive
+    records [n_p][CR_PRIM_DOUBLES] (capsules, boxes) shared by all problems, or [P][n_o][4] and
+    [P][n_p][CR_PRIM_DOUBLES] with per_problem=True (each problem its own set)."""
 
-    def __init__(self, spheres=None, device="cuda", per_problem=False):
-        if spheres is None or len(spheres) == 0:
-            self.spheres = None
-            self.n_o = 0
-        else:
-            t = torch.as_tensor(spheres, dtype=torch.float64, device=device)
-            self.spheres = (t.reshape(t.shape[0], -1, 4) if per_problem else t.reshape(-1, 4)).contiguous()
-            self.n_o = self.spheres.shape[-2]
+    def __init__(self, spheres=None, device="cuda", per_problem=False, prims=None):
+        def resident(a, width):
+            if a is None or len(a) == 0:
+                return None, 0
+            t = torch.as_tensor(a, dtype=torch.float64, device=device)
+            t = (t.reshape(t.shape[0], -1, width) if per_problem else t.reshape(-1, width)).contiguous()
+            return (t, t.shape[-2]) if t.shape[-2] > 0 else (None, 0)
+
+        self.spheres, self.n_o = resident(spheres, 4)
+        self.prims, self.n_p = resident(prims, lib.CR_PRIM_DOUBLES)
         self.c = lib.cr_scene()
         self.c.spheres = self.spheres.data_ptr() if self.spheres is not None else None
         self.c.n_o = self.n_o
-        self.c.per_problem = 1 if (per_problem and self.n_o > 0) else 0
+        self.c.prims = self.prims.data_ptr() if self.prims is not None else None
+        self.c.n_p = self.n_p
+        self.c.per_problem = 1 if (per_problem and self.n_o + self.n_p > 0) else 0
 
 
 def task_struct(kind: int, targets_soa: torch.Tensor, S: int, weights: synth.WeightSpec) -> lib.cr_task:

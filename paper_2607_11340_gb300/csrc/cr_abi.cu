@@ -62,16 +62,27 @@ cr_status check_scene(const cr_scene* s) {
   if (!s) return CR_OK;  // no scene = no obstacles
   if (s->n_o < 0 || s->n_o > CR_MAX_SPHERES)
     return fail(CR_EINVAL, "scene.n_o = %d outside 0..%d", s->n_o, CR_MAX_SPHERES);
+  if (s->n_p < 0 || s->n_p > CR_MAX_SPHERES - s->n_o)
+    return fail(CR_EINVAL, "scene.n_p = %d: n_o + n_p must lie in 0..%d", s->n_p, CR_MAX_SPHERES);
   if (s->per_problem != 0 && s->per_problem != 1) return fail(CR_EINVAL, "scene.per_problem must be 0 or 1");
-  if (s->n_o > 0) return check_ptr(s->spheres, 8, "scene.spheres", true);
+  cr_status st = CR_OK;
+  if (s->n_o > 0 && (st = check_ptr(s->spheres, 8, "scene.spheres", true))) return st;
+  if (s->n_p > 0 && (st = check_ptr(s->prims, 8, "scene.prims", true))) return st;
   return CR_OK;
 }
 
 cr_status check_scene_shared(const cr_scene* s) {
   cr_status st = check_scene(s);
   if (st) return st;
-  if (s && s->per_problem && s->n_o > 0)
-    return fail(CR_EINVAL, "this entry point takes one sphere set for the whole batch (per_problem = 0)");
+  if (s && s->per_problem && s->n_o + s->n_p > 0)
+    return fail(CR_EINVAL, "this entry point takes one obstacle set for the whole batch (per_problem = 0)");
+  return CR_OK;
+}
+
+cr_status check_scene_spheres_only(const cr_scene* s, const char* who) {
+  cr_status st = check_scene(s);
+  if (st) return st;
+  if (s && s->n_p > 0) return fail(CR_EINVAL, "%s takes sphere obstacles only (scene.n_p = %d)", who, s->n_p);
   return CR_OK;
 }
 

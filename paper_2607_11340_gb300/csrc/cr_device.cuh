@@ -468,9 +468,15 @@ CR_HD void pose_rows(int kind, const WeightsK<T>& w, const TargetK<T>& tg, const
 // Spheres as the kernels see them: (centre, reach = r_s + r_body + delta), staged in shared memory.
 template <typename T> struct Sphere4 { T x, y, z, reach; };
 
+// Threads tid, tid + nthr, ... of the caller's group stage the entries (by default the whole block).
 template <typename T>
-__device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T delta, Sphere4<T>* sh) {
-  for (int j = threadIdx.x; j < no; j += blockDim.x) {
+__device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T delta, Sphere4<T>* sh, int tid = -1,
+                              int nthr = 0) {
+  if (tid < 0) {
+    tid = threadIdx.x;
+    nthr = blockDim.x;
+  }
+  for (int j = tid; j < no; j += nthr) {
     Sphere4<T> s;
     s.x = T(sp[4 * j]);
     s.y = T(sp[4 * j + 1]);
@@ -478,6 +484,156 @@ __device__ void stage_spheres(const double* sp, int no, const RobotK<T>& rb, T d
     s.reach = T(sp[4 * j + 3]) + rb.rbody + delta;
     sh[j] = s;
   }
+}
+
+// Primitives (capsules, boxes: the convex pieces of Sec. IV-C) as the kernels see them. Each also
+// has a bounding sphere in the Sphere4 table, after the n_o spheres (table index n_o + jp), whose
+// reach bounds that of every point of the primitive, so that the broad phase treats both alike.
+template <typename T> struct PrimK {
+  T c[3];    // capsule: end point a; box: centre
+  T e[3];    // capsule: b - a; box: half extents
+  T R[9];    // box: rotation, box frame to world, row-major
+  T iee;     // capsule: 1 / |b - a|^2 (0 when a = b)
+  T reach;   // r + r_body + delta
+  int kind;  // CR_PRIM_CAPSULE, CR_PRIM_BOX; any other value: a sphere centred at c
+};
+
+// Stage primitive records pr [np][CR_PRIM_DOUBLES] (FP64): the records into sh, their bounding
+// spheres into bnd. The rotation and the bounds are formed in FP64 and rounded once to T.
+template <typename T>
+__device__ void stage_prims(const double* pr, int np, const RobotK<T>& rb, T delta, Sphere4<T>* bnd, PrimK<T>* sh,
+                            int tid, int nthr) {
+  for (int j = tid; j < np; j += nthr) {
+    const double* r = pr + (size_t)CR_PRIM_DOUBLES * j;
+    const int kind = (int)r[0];
+    const double reach = r[1] + (double)rb.rbody + (double)delta;
+    PrimK<T> P;
+    P.kind = kind == CR_PRIM_CAPSULE || kind == CR_PRIM_BOX ? kind : CR_PRIM_SPHERE;
+    P.reach = T(reach);
+    double e[3] = {0.0, 0.0, 0.0}, ctr[3] = {r[2], r[3], r[4]}, rad = 0.0;
+    for (int a = 0; a < 9; ++a) P.R[a] = T(a % 4 == 0 ? 1 : 0);
+    P.iee = T(0);
+    if (P.kind == CR_PRIM_CAPSULE) {
+      for (int a = 0; a < 3; ++a) e[a] = r[5 + a] - r[2 + a];
+      const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+      P.iee = ee > 0.0 ? T(1.0 / ee) : T(0);
+      for (int a = 0; a < 3; ++a) ctr[a] = r[2 + a] + 0.5 * e[a];
+      rad = 0.5 * sqrt(ee);
+    } else if (P.kind == CR_PRIM_BOX) {
+      for (int a = 0; a < 3; ++a) e[a] = r[5 + a];
+      rad = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      // unit quaternion (w, x, y, z) -> rotation matrix
+      double qw = r[8], qx = r[9], qy = r[10], qz = r[11];
+      const double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+      qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+      const double M[9] = {1.0 - 2.0 * (qy * qy + qz * qz), 2.0 * (qx * qy - qw * qz), 2.0 * (qx * qz + qw * qy),
+                           2.0 * (qx * qy + qw * qz), 1.0 - 2.0 * (qx * qx + qz * qz), 2.0 * (qy * qz - qw * qx),
+                           2.0 * (qx * qz - qw * qy), 2.0 * (qy * qz + qw * qx), 1.0 - 2.0 * (qx * qx + qy * qy)};
+      for (int a = 0; a < 9; ++a) P.R[a] = T(M[a]);
+    }
+    for (int a = 0; a < 3; ++a) {
+      P.c[a] = T(r[2 + a]);
+      P.e[a] = T(e[a]);
+    }
+    sh[j] = P;
+    bnd[j] = Sphere4<T>{T(ctr[0]), T(ctr[1]), T(ctr[2]), T(rad + reach)};
+  }
+}
+
+// The obstacles one evaluation sees: the Sphere4 table s (n_o spheres, then the bounding spheres of
+// the primitives) and the primitive records p; table entries j >= ns are primitive j - ns. Built
+// from a bare sphere table it holds spheres only.
+template <typename T> struct ObsK {
+  const Sphere4<T>* s;
+  const PrimK<T>* p;
+  int ns;
+  CR_HD ObsK(const Sphere4<T>* s_) : s(s_), p(nullptr), ns(1 << 30) {}
+  CR_HD ObsK(const Sphere4<T>* s_, const PrimK<T>* p_, int ns_) : s(s_), p(p_), ns(ns_) {}
+  // the table from entry k on (its entry j is entry k + j of this one)
+  CR_HD ObsK from(int k) const { return ObsK(s + k, p, ns - k); }
+};
+
+// Shared-memory bytes of a staged obstacle set: the Sphere4 table (no + np entries), then the
+// primitive records from the next 16-byte boundary.
+template <typename T> __host__ __device__ inline size_t obstacles_smem(int no, int np) {
+  const size_t t = ((size_t)(no + np) * sizeof(Sphere4<T>) + 15) & ~(size_t)15;
+  return t + (size_t)np * sizeof(PrimK<T>);
+}
+
+// Stage spheres sp [no][4] and primitive records pr [np][CR_PRIM_DOUBLES] at base (threads tid,
+// tid + nthr, ... of the caller's group, by default the whole block; the caller synchronises the
+// group before use).
+template <typename T>
+__device__ ObsK<T> stage_obstacles(const double* sp, int no, const double* pr, int np, const RobotK<T>& rb, T delta,
+                                   unsigned char* base, int tid = -1, int nthr = 0) {
+  if (tid < 0) {
+    tid = threadIdx.x;
+    nthr = blockDim.x;
+  }
+  Sphere4<T>* tab = reinterpret_cast<Sphere4<T>*>(base);
+  PrimK<T>* prm = reinterpret_cast<PrimK<T>*>(base + (((size_t)(no + np) * sizeof(Sphere4<T>) + 15) & ~(size_t)15));
+  stage_spheres(sp, no, rb, delta, tab, tid, nthr);
+  if (np > 0) stage_prims(pr, np, rb, delta, tab + no, prm, tid, nthr);
+  return ObsK<T>(tab, prm, no);
+}
+
+// Clearance of point x against primitive P within `reach` (P.reach for the rows): true when
+// sd(x) < reach, with sd the signed distance from x to the primitive's core; then viol = reach - sd
+// and n = d sd / dx (unit). Capsule: distance to the nearest point a + t (b - a), t clamped to
+// [0, 1]. Box, in box coordinates p = R^T (x - c) and q_a = |p_a| - h_a: outside, the distance to
+// the box (offset sign(p_a) max(q_a, 0) per axis); inside, sd = max_a q_a, n = the outward normal of
+// that face (the first axis among equal maxima).
+template <typename T>
+CR_HD bool prim_active(const PrimK<T>& P, const T (&x)[3], T reach, T& viol, T (&n)[3]) {
+  const T w0 = x[0] - P.c[0], w1 = x[1] - P.c[1], w2 = x[2] - P.c[2];
+  if (P.kind == CR_PRIM_BOX) {
+    T p[3], q[3];
+    bool out = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      p[a] = P.R[a] * w0 + P.R[3 + a] * w1 + P.R[6 + a] * w2;
+      q[a] = c_abs(p[a]) - P.e[a];
+      out = out || q[a] > T(0);
+    }
+    if (out) {
+      T o[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) o[a] = q[a] > T(0) ? (p[a] < T(0) ? -q[a] : q[a]) : T(0);
+      const T d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+      if (!(d2 < reach * reach)) return false;
+      const T dist = c_sqrt(d2);
+      viol = reach - dist;
+      const T id = T(1) / dist;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) n[b] = (P.R[3 * b] * o[0] + P.R[3 * b + 1] * o[1] + P.R[3 * b + 2] * o[2]) * id;
+      return true;
+    }
+    int am = 0;
+    if (q[1] > q[am]) am = 1;
+    if (q[2] > q[am]) am = 2;
+    viol = reach - q[am];
+    const T sg = p[am] < T(0) ? T(-1) : T(1);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) n[b] = sg * P.R[3 * b + am];
+    return viol > T(0);
+  }
+  T d0 = w0, d1 = w1, d2c = w2;
+  if (P.kind == CR_PRIM_CAPSULE) {
+    T t = (w0 * P.e[0] + w1 * P.e[1] + w2 * P.e[2]) * P.iee;
+    t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+    d0 = w0 - t * P.e[0];
+    d1 = w1 - t * P.e[1];
+    d2c = w2 - t * P.e[2];
+  }
+  const T d2 = d0 * d0 + d1 * d1 + d2c * d2c;
+  if (!(d2 < reach * reach)) return false;
+  const T dist = c_sqrt(d2);
+  viol = reach - dist;
+  const T id = T(1) / dist;
+  n[0] = d0 * id;
+  n[1] = d1 * id;
+  n[2] = d2c * id;
+  return true;
 }
 
 // Broad phase of the clearance rows. Spheres j0 .. j0 + cnt - 1 (cnt <= 64) that may come within reach
@@ -673,9 +829,10 @@ CR_HD void self_contact_forward(const RobotK<T>& rb, const WeightsK<T>& w, const
 // the spheres' and, with w.rho_s > 0, the self-contact rows (with_self = false leaves the latter to
 // another thread that evaluates the same state).
 template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
-CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T>* sph, int no,
+CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, ObsK<T> ob, int no,
                       const T (&u)[3 * N], Chain<T, N>& ch, StateAgg<T, N>& ag, T* coll_out,
                       bool with_self = true) {
+  const Sphere4<T>* sph = ob.s;
   chain_forward<T, N, MODEL>(rb, u, ch);
   T coll = T(0);
 #pragma unroll
@@ -703,7 +860,22 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, const Sphere4<T
         T gw[3] = {T(0), T(0), T(0)};
         bool hit = false;
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
-          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
+          const int jo = j0 + __ffsll((long long)bits) - 1;
+          if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
+            const PrimK<T>& P = ob.p[jo - ob.ns];
+            T viol, nv[3];
+            if (prim_active(P, wp, P.reach, viol, nv)) {
+              T rr = w.sc * viol;
+              coll += T(0.5) * rr * rr;
+              if (GRAD) {
+                T f = -w.rho_c * viol;
+                gw[0] += f * nv[0]; gw[1] += f * nv[1]; gw[2] += f * nv[2];
+                hit = true;
+              }
+            }
+            continue;
+          }
+          Sphere4<T> S = sph[jo];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
           if (d2 < S.reach * S.reach) {
@@ -907,7 +1079,7 @@ CR_HD void pose_tip_force(int kind, const WeightsK<T>& w, const TargetK<T>& tg, 
 // Cost (and adjoint) of an IK state: the two phases around the pose rows. BOX as in state_forward.
 template <typename T, int N, bool OBST, bool GRAD, bool PGRAD, bool BOX = true, int MODEL = CR_MODEL_TENDON>
 CR_HD T eval_ik(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                const Sphere4<T>* sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
+                ObsK<T> sph, int no, const T (&u)[3 * N], T (&gu)[3 * N], T* gL, T* grc,
                 T* coll_out) {
   Chain<T, N> ch;
   StateAgg<T, N> ag;
@@ -1099,8 +1271,9 @@ CR_HD void add_sample_row(const RobotK<T>& rb, const Chain<T, N>& ch, const T (&
 
 template <typename T, typename TA, int N, bool OBST, int MODEL = CR_MODEL_TENDON, typename AArr>
 CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                       const Sphere4<T>* sph, int no, const T (&u)[3 * N], AArr&& A, TA (&g)[3 * N]) {
+                       ObsK<T> ob, int no, const T (&u)[3 * N], AArr&& A, TA (&g)[3 * N]) {
   constexpr int D = 3 * N;
+  const Sphere4<T>* sph = ob.s;
 #pragma unroll
   for (int a = 0; a < D * (D + 1) / 2; ++a) A[a] = TA(0);
 #pragma unroll
@@ -1242,15 +1415,22 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sg, q, wp, s, c);
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
-          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
-          T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
-          T d2 = dx * dx + dy * dy + dz * dz;
-          if (!(d2 < S.reach * S.reach)) continue;
-          T dist = c_sqrt(d2);
-          T viol = S.reach - dist;
+          const int jo = j0 + __ffsll((long long)bits) - 1;
+          T viol, nh[3];
+          if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
+            const PrimK<T>& P = ob.p[jo - ob.ns];
+            if (!prim_active(P, wp, P.reach, viol, nh)) continue;
+          } else {
+            Sphere4<T> S = sph[jo];
+            T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
+            T d2 = dx * dx + dy * dy + dz * dz;
+            if (!(d2 < S.reach * S.reach)) continue;
+            T dist = c_sqrt(d2);
+            viol = S.reach - dist;
+            nh[0] = dx / dist; nh[1] = dy / dist; nh[2] = dz / dist;
+          }
           T rr = w.sc * viol;
           F += T(0.5) * rr * rr;
-          T nh[3] = {dx / dist, dy / dist, dz / dist};
           // d r / d w = -sqrt(rho_c) n
           T jr[D];
 #pragma unroll
@@ -1595,9 +1775,10 @@ CR_HD void draw_seed_m(uint64_t key, uint64_t p, uint64_t s, int attempt, const 
   else draw_seed<T, N>(key, p, s, attempt, bx.umax, u);
 }
 
-// Does any backbone sample of state u come within reach of a sphere?
+// Does any backbone sample of state u come within reach of an obstacle?
 template <typename T, int N, int MODEL = CR_MODEL_TENDON>
-CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, const T (&u)[3 * N]) {
+CR_HD bool state_collides(const RobotK<T>& rb, ObsK<T> ob, int no, const T (&u)[3 * N]) {
+  const Sphere4<T>* sph = ob.s;
   Chain<T, N> ch;
   chain_forward<T, N, MODEL>(rb, u, ch);
   const T inb = T(1) / T(rb.nb);
@@ -1614,7 +1795,14 @@ CR_HD bool state_collides(const RobotK<T>& rb, const Sphere4<T>* sph, int no, co
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(k) * inb, q, wp, s, c);
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
-          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
+          const int jo = j0 + __ffsll((long long)bits) - 1;
+          if (jo >= ob.ns) {
+            const PrimK<T>& P = ob.p[jo - ob.ns];
+            T viol, nv[3];
+            if (prim_active(P, wp, P.reach, viol, nv)) return true;
+            continue;
+          }
+          Sphere4<T> S = sph[jo];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
         }

@@ -63,13 +63,14 @@ template <typename T, int N, bool OBST, int MODE, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, int kind,
                                                     const double* __restrict__ targets, int64_t P,
                                                     int S, const double* __restrict__ spheres, int no,
+                                                    const double* __restrict__ prims, int np,
                                                     const T* __restrict__ u, int64_t B, T* cost,
                                                     T* coll, T* gu, T* gp, const T* __restrict__ upstream) {
   constexpr int D = 3 * N;
-  extern __shared__ unsigned char smem_raw[];
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ObsK<T> ob(nullptr);
   if (OBST) {
-    stage_spheres(spheres, no, rb, w.delta, sph);
+    ob = stage_obstacles(spheres, no, prims, np, rb, w.delta, smem_raw);
     __syncthreads();
   }
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(128) k_cost_grad(RobotK<T> rb, WeightsK<T> w, 
   for (int q = 0; q < D; ++q) uu[q] = u[q * B + b];
   TargetK<T> tg = load_target<T>(targets, P, b / S, kind);
   T g[D], gL[N], grc[N], cl;
-  T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2), true, MODEL>(rb, w, kind, tg, sph, no, uu, g, gL, grc, &cl);
+  T F = eval_ik<T, N, OBST, (MODE >= 1), (MODE >= 2), true, MODEL>(rb, w, kind, tg, ob, no + np, uu, g, gL, grc,
+                                                                    &cl);
   if (cost) cost[b] = F;
   if (coll) coll[b] = cl;
   const T up = upstream ? upstream[b] : T(1);  // vector-Jacobian product weight
@@ -145,17 +147,18 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> void fk_jac_n(const Ev
 template <typename T, int N, int MODEL = CR_MODEL_TENDON> void cost_grad_n(const EvalArgs& a) {
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
-  int no = a.scene.n_o;
+  int no = a.scene.n_o, np = a.scene.n_p;
   int mode = a.gp ? 2 : (a.gu ? 1 : 0);
-  size_t sm = (size_t)no * sizeof(Sphere4<T>);
+  size_t sm = obstacles_smem<T>(no, np);
   unsigned g = grid_of(a.B, 128);
 #define CR_CG(OB, MO)                                                                              \
   k_cost_grad<T, N, OB, MO, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.task.kind, a.task.targets,   \
                                                        a.task.n_targets, a.task.seeds_per_target,  \
-                                                       a.scene.spheres, no, (const T*)a.u, a.B,    \
+                                                       a.scene.spheres, no, a.scene.prims, np,     \
+                                                       (const T*)a.u, a.B,                         \
                                                        (T*)a.cost, (T*)a.coll, (T*)a.gu, (T*)a.gp, \
                                                        (const T*)a.upstream)
-  if (no > 0 || a.task.w.rho_s > 0) {  // collision rows: spheres and / or self-contact
+  if (no + np > 0 || a.task.w.rho_s > 0) {  // collision rows: obstacles and / or self-contact
     if (mode == 0) CR_CG(true, 0); else if (mode == 1) CR_CG(true, 1); else CR_CG(true, 2);
   } else {
     if (mode == 0) CR_CG(false, 0); else if (mode == 1) CR_CG(false, 1); else CR_CG(false, 2);

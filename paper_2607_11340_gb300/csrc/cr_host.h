@@ -24,6 +24,7 @@ cr_status check_robot(const cr_robot* r);
 cr_status check_tendon_model(const cr_robot* r, const char* what);  // CR_EINVAL for the arc model
 cr_status check_scene(const cr_scene* s);
 cr_status check_scene_shared(const cr_scene* s);
+cr_status check_scene_spheres_only(const cr_scene* s, const char* who);
 cr_status check_task(const cr_task* t, int64_t B);
 cr_status check_dtype(int32_t dtype);
 cr_status check_ptr(const void* p, size_t align, const char* name, bool required);

@@ -24,6 +24,8 @@ template <typename T> struct PathArgs {
   int H;
   const double* spheres;  // [P][no][4] when sph_pp, else [no][4]
   int no;
+  const double* prims;    // [P][np][CR_PRIM_DOUBLES] when sph_pp, else [np][CR_PRIM_DOUBLES]
+  int np;
   int sph_pp;
   int k_warm, k_joint;
   double lambda0, lim_tol;
@@ -42,14 +44,14 @@ template <typename T> struct PathArgs {
 // ------------------------------------------------------------------------------------------------
 // Exploration: warp-cooperative LM on one waypoint's IK residual
 // ------------------------------------------------------------------------------------------------
-// Per-warp shared scratch: spheres [no] | col, colr, sx, sdg [32 each]
-template <typename T> __host__ __device__ inline size_t warm_warp_bytes(int no) {
-  return (((size_t)no * sizeof(Sphere4<T>) + 15) / 16 * 16) + 4 * 32 * sizeof(T);
+// Per-warp shared scratch: obstacles (no spheres, np primitives) | col, colr, sx, sdg [32 each]
+template <typename T> __host__ __device__ inline size_t warm_warp_bytes(int no, int np) {
+  return ((obstacles_smem<T>(no, np) + 15) / 16 * 16) + 4 * 32 * sizeof(T);
 }
 
 template <typename T, int N, bool OBST>
 __device__ void warm_sweep_warp(const RobotK<T>& rb, const WeightsK<T>& w, const double* wp, int64_t PH, int64_t base,
-                                int H, int k_warm, T lam0, const Sphere4<T>* sph, int no, T (&u)[3 * N], T* scratch,
+                                int H, int k_warm, T lam0, ObsK<T> sph, int no, T (&u)[3 * N], T* scratch,
                                 T* Xout, int64_t xstride) {
   constexpr int D = 3 * N;
   const int lane = threadIdx.x & 31;
@@ -76,18 +78,14 @@ __global__ void __maxnreg__(255) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathAr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t p = (int64_t)blockIdx.x * 4 + wid;
-  unsigned char* mine = smem_raw + (size_t)wid * warm_warp_bytes<T>(a.no);
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(mine);
-  T* scratch = reinterpret_cast<T*>(mine + ((size_t)a.no * sizeof(Sphere4<T>) + 15) / 16 * 16);
+  unsigned char* mine = smem_raw + (size_t)wid * warm_warp_bytes<T>(a.no, a.np);
+  T* scratch = reinterpret_cast<T*>(mine + (obstacles_smem<T>(a.no, a.np) + 15) / 16 * 16);
   const bool live = p < a.P;
+  ObsK<T> sph(nullptr);
   if (OBST && live) {
-    const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
-    for (int j = lane; j < a.no; j += 32) {
-      Sphere4<T> s;
-      s.x = T(sp[4 * j]); s.y = T(sp[4 * j + 1]); s.z = T(sp[4 * j + 2]);
-      s.reach = T(sp[4 * j + 3]) + rb.rbody + w.delta;
-      sph[j] = s;
-    }
+    const int64_t q = a.sph_pp ? p : 0;
+    sph = stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
+                          a.np, rb, w.delta, mine, lane, 32);
   }
   __syncwarp();
   if (!live) return;
@@ -97,7 +95,8 @@ __global__ void __maxnreg__(255) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathAr
 #pragma unroll
   for (int q = 0; q < D; ++q) u[q] = T(a.u0[q * a.P + p]);
   if (lane < D) a.X[lane * PH + p * H] = T(a.u0[lane * a.P + p]);
-  warm_sweep_warp<T, N, OBST>(rb, w, a.wp, PH, p * H, H, a.k_warm, T(a.lambda0), sph, a.no, u, scratch, a.X + p * H, PH);
+  warm_sweep_warp<T, N, OBST>(rb, w, a.wp, PH, p * H, H, a.k_warm, T(a.lambda0), sph, a.no + a.np, u, scratch,
+                              a.X + p * H, PH);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -309,14 +308,11 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
   const int64_t p = blockIdx.x;
   const int tid = threadIdx.x, H = a.H;
   const int64_t PH = a.P * H;
-  // shared layout: spheres (T, double) | g [H][D] | z [H][D] | col, colr [32] | Zs [DD] | red [32] |
+  // shared layout: obstacles (T, double) | g [H][D] | z [H][D] | col, colr [32] | Zs [DD] | red [32] |
   // misc [8] | col2, colr2 [2][32], Zs2 [2][DD] | Af [H][DD] (T) | ush [H][D] (T)
-  size_t off = 0;
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
-  off += (size_t)a.no * sizeof(Sphere4<T>);
-  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw + off);
-  off += (size_t)a.no * sizeof(Sphere4<double>);
-  off = (off + 15) & ~size_t(15);
+  const int nob = a.no + a.np;
+  const size_t offd = (obstacles_smem<T>(a.no, a.np) + 15) & ~size_t(15);
+  size_t off = offd + ((obstacles_smem<double>(a.no, a.np) + 15) & ~size_t(15));
   double* g = reinterpret_cast<double*>(smem_raw + off);
   double* z = g + (size_t)H * D;
   double* col = z + (size_t)H * D;
@@ -330,10 +326,14 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
   T* Af = reinterpret_cast<T*>(Zs2 + 2 * DD);
   T* ush = Af + (size_t)H * DD;
   double* Zg = a.Z + (size_t)p * H * aug_stride<D>();
+  ObsK<T> sph(nullptr);
+  ObsK<double> sphd(nullptr);
   if (OBST) {
-    const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
-    stage_spheres(sp, a.no, rb, w.delta, sph);
-    stage_spheres(sp, a.no, rbd, wd.delta, sphd);
+    const int64_t q = a.sph_pp ? p : 0;
+    const double* sp = a.spheres + q * a.no * 4;
+    const double* pr = a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr;
+    sph = stage_obstacles(sp, a.no, pr, a.np, rb, w.delta, smem_raw);
+    sphd = stage_obstacles(sp, a.no, pr, a.np, rbd, wd.delta, smem_raw + offd);
   }
   const bool wthr = tid < H;
   T u[D];
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     double Fl = 0.0;
     if (wthr) {
       T dummy[D];
-      Fl = double(eval_ik<T, N, OBST, false, false>(rb, w, CR_TASK_IK6, tg, sph, a.no, uu, dummy, nullptr, nullptr, nullptr));
+      Fl = double(eval_ik<T, N, OBST, false, false>(rb, w, CR_TASK_IK6, tg, sph, nob, uu, dummy, nullptr, nullptr, nullptr));
 #pragma unroll
       for (int q = 0; q < D; ++q) ush[tid * D + q] = uu[q];
     }
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     double Fl = 0.0;
     if (wthr) {
       T At[DD], gt[D];
-      Fl = double(eval_ik_normal<T, T, N, OBST>(rb, w, CR_TASK_IK6, tg, sph, a.no, u, At, gt));
+      Fl = double(eval_ik_normal<T, T, N, OBST>(rb, w, CR_TASK_IK6, tg, sph, nob, u, At, gt));
 #pragma unroll
       for (int e = 0; e < DD; ++e) Af[tid * DD + e] = At[e];
 #pragma unroll
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     for (int q = 0; q < D; ++q) a.X_out[q * PH + p * H + tid] = ud[q];
     TargetK<double> tgd = load_target<double>(a.wp, PH, p * H + tid, CR_TASK_IK6);
     double pos, rot;
-    accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+    accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, tgd, sphd, nob, ud, a.lim_tol, pos, rot, flags);
     a.pos[p * H + tid] = pos;
     a.rot[p * H + tid] = rot;
   }
@@ -494,7 +494,9 @@ template <typename T> PathArgs<T> path_args(const PathLaunch& l) {
   a.H = l.H;
   a.spheres = l.scene.spheres;
   a.no = l.scene.n_o;
-  a.sph_pp = (l.scene.per_problem && l.scene.n_o > 0) ? 1 : 0;
+  a.prims = l.scene.prims;
+  a.np = l.scene.n_p;
+  a.sph_pp = (l.scene.per_problem && l.scene.n_o + l.scene.n_p > 0) ? 1 : 0;
   a.k_warm = l.k_warm;
   a.k_joint = l.k_joint;
   a.lambda0 = l.lambda0;
@@ -512,9 +514,9 @@ template <typename T> PathArgs<T> path_args(const PathLaunch& l) {
   return a;
 }
 
-inline size_t path_joint_smem(int no, int H, int D, size_t tsize) {
-  size_t off = (size_t)no * (4 * tsize + 32);
-  off = (off + 15) & ~size_t(15);
+template <typename T> inline size_t path_joint_smem(int no, int np, int H, int D) {
+  const size_t tsize = sizeof(T);
+  size_t off = ((obstacles_smem<T>(no, np) + 15) & ~size_t(15)) + ((obstacles_smem<double>(no, np) + 15) & ~size_t(15));
   off += sizeof(double) * ((size_t)2 * H * D + 64 + (size_t)D * (D + 1) / 2 + 32 + 8 + 128 + (size_t)D * (D + 1));
   off += tsize * ((size_t)H * D * (D + 1) / 2 + (size_t)H * D);
   return off;
@@ -532,9 +534,9 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   PathArgs<T> a = path_args<T>(l);
   cr_status st;
   // exploration sweep
-  size_t smw = 4 * warm_warp_bytes<T>(a.no);
+  size_t smw = 4 * warm_warp_bytes<T>(a.no, a.np);
   unsigned gw = (unsigned)((a.P + 3) / 4);
-  if (a.no > 0) {
+  if (a.no + a.np > 0) {
     if ((st = set_smem(k_path_warm<T, N, true>, smw))) return st;
     k_path_warm<T, N, true><<<gw, 128, smw, l.stream>>>(rb, w, a);
   } else {
@@ -544,8 +546,8 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   if ((st = crh::check_launch("cr_solve_path exploration"))) return st;
   // refinement
   const int threads = ((a.H + 31) / 32) * 32;
-  size_t smj = path_joint_smem(a.no, a.H, D, sizeof(T));
-  if (a.no > 0) {
+  size_t smj = path_joint_smem<T>(a.no, a.np, a.H, D);
+  if (a.no + a.np > 0) {
     if ((st = set_smem(k_path_joint<T, N, true>, smj))) return st;
     k_path_joint<T, N, true><<<(unsigned)a.P, threads, smj, l.stream>>>(rb, w, rbd, wd, a);
   } else {

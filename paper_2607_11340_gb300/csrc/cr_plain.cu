@@ -11,9 +11,10 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
                                                    double* alphas, int* sel) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Sphere4<double>* sph = reinterpret_cast<Sphere4<double>*>(smem_raw);
+  ObsK<double> sph(nullptr);
+  const int nob = a.no + a.np;
   if (OBST) {
-    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
+    sph = stage_problem_obstacles(a, p, rb, w.delta, smem_raw);
     __syncthreads();
   }
   const int S = a.S, K = a.K;
@@ -22,13 +23,13 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
   if (s < S) {
     double u[D];
     draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.box.umax, u);
-    if (OBST && a.no > 0)
+    if (OBST && nob > 0)
       for (int att = 1; att < 8; ++att) {
-        if (!state_collides<double, N>(rb, sph, a.no, u)) break;
+        if (!state_collides<double, N>(rb, sph, nob, u)) break;
         draw_seed<double, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box.umax, u);
       }
     double g[D], coll;
-    Fs[s] = eval_ik<double, N, OBST, true, false>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+    Fs[s] = eval_ik<double, N, OBST, true, false>(rb, w, a.kind, tg, sph, nob, u, g, nullptr, nullptr, &coll);
     for (int q = 0; q < D; ++q) { U[s * D + q] = u[q]; G[s * D + q] = g[q]; }
     Cs[s] = coll;
     alphas[s] = double(a.alpha0);
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
       // the iterate, its gradient, cost and step length round-trip through global memory every step
       double uu[D], gg[D], F = Fs[s], cl = Cs[s], al = alphas[s];
       for (int q = 0; q < D; ++q) { uu[q] = U[s * D + q]; gg[q] = G[s * D + q]; }
-      pg_step<double, N, OBST>(rb, w, a.kind, tg, sph, a.no, uu, gg, F, cl, al);
+      pg_step<double, N, OBST>(rb, w, a.kind, tg, sph, nob, uu, gg, F, cl, al);
       for (int q = 0; q < D; ++q) { U[s * D + q] = uu[q]; G[s * D + q] = gg[q]; }
       Fs[s] = F;
       Cs[s] = cl;
@@ -85,10 +86,10 @@ __global__ void __launch_bounds__(256) k_plain_ik(RobotK<double> rb, WeightsK<do
     if (j >= 0) {
       double lam = a.lambda0, nu = 2.0, Fi;
       for (int it = 0; it < a.k_final; ++it) {
-        lm_iteration<double, N, OBST>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, Fi);
+        lm_iteration<double, N, OBST>(rb, w, a.kind, tg, sph, nob, u, lam, nu, Fi);
         for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = u[q];
       }
-      F = accept_fp64<N, OBST>(rb, w, a.kind, tg, sph, a.no, u, a.lim_tol, pos, rot, flags);
+      F = accept_fp64<N, OBST>(rb, w, a.kind, tg, sph, nob, u, a.lim_tol, pos, rot, flags);
     }
     for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = u[q];
     a.cand_F[c] = F;
@@ -111,9 +112,9 @@ template <int N> cr_status plain_n(const SolveArgs& sa) {
   int* sel = (int*)(alphas + a.S);
   // sel[32] | skipped[S] | taken[S] live after the three double arrays
   const int threads = ((a.S + 31) / 32) * 32;
-  size_t sm = (size_t)a.no * sizeof(Sphere4<double>);
+  size_t sm = obstacles_smem<double>(a.no, a.np);  // at most 45 KB (CR_MAX_SPHERES obstacles)
   for (int64_t p = 0; p < a.P; ++p) {
-    if (a.no > 0) k_plain_ik<N, true><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, G, Fs, Cs, alphas, sel);
+    if (a.no + a.np > 0) k_plain_ik<N, true><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, G, Fs, Cs, alphas, sel);
     else k_plain_ik<N, false><<<1, threads, sm, sa.stream>>>(rb, w, a, p, U, G, Fs, Cs, alphas, sel);
     cr_status st = crh::check_launch("cr_solve_ik_plain");
     if (st) return st;

@@ -94,8 +94,8 @@ size_t cr_prm_workspace_size(const cr_robot* robot, int64_t R, const cr_prm_para
 cr_status cr_prm_build(const cr_robot* robot, const cr_scene* scene, const cr_weights* w, const cr_prm_params* prm,
                        const cr_roadmap* map, void* workspace, size_t ws_bytes, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "the PRM roadmap")) || (st = check_scene(scene)) ||
-      (st = check_prm(prm)) || (st = check_map(map, true)))
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "the PRM roadmap")) ||
+      (st = check_scene_spheres_only(scene, "the PRM roadmap")) || (st = check_prm(prm)) || (st = check_map(map, true)))
     return st;
   if (!w) return fail(CR_EINVAL, "weights are NULL");
   if ((st = check_self_rows(*w, false, "the PRM roadmap and query"))) return st;
@@ -125,8 +125,8 @@ cr_status cr_prm_query(const cr_robot* robot, const cr_scene* scene, const cr_we
                        const cr_roadmap* map, const double* u_start, const double* u_goal, int64_t P, int32_t T,
                        double* X, double* length, int32_t* hops, cr_stream stream) {
   cr_status st;
-  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "the PRM query")) || (st = check_scene(scene)) ||
-      (st = check_prm(prm)) || (st = check_map(map, false)))
+  if ((st = check_robot(robot)) || (st = check_tendon_model(robot, "the PRM query")) ||
+      (st = check_scene_spheres_only(scene, "the PRM query")) || (st = check_prm(prm)) || (st = check_map(map, false)))
     return st;
   if (!w) return fail(CR_EINVAL, "weights are NULL");
   if ((st = check_self_rows(*w, false, "the PRM roadmap and query"))) return st;

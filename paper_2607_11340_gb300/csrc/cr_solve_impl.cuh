@@ -28,7 +28,7 @@ namespace crk {
 // no step; the seed lies on the feasible set like every trial point.
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD int pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                   const Sphere4<T>* sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha,
+                   ObsK<T> sph, int no, T (&u)[3 * N], T (&g)[3 * N], T& F, T& coll, T& alpha,
                    bool first = false) {
   constexpr int D = 3 * N;
   T u1[D];
@@ -66,7 +66,7 @@ CR_HD int pg_step(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const Tar
 // ------------------------------------------------------------------------------------------------
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD int lm_iteration(const RobotK<T>& rb, const WeightsK<T>& w, int kind, const TargetK<T>& tg,
-                       const Sphere4<T>* sph, int no, T (&u)[3 * N], double& lam, double& nu, T& Fout) {
+                       ObsK<T> sph, int no, T (&u)[3 * N], double& lam, double& nu, T& Fout) {
   constexpr int D = 3 * N;
   constexpr int DD = D * (D + 1) / 2;
   double Ad[DD], Dg[D], dl[D], invd[D];
@@ -201,8 +201,10 @@ template <typename T> struct IkArgs {
   int64_t P;
   const double* spheres;
   int no;
-  int sph_pp;  // spheres are per problem: [P][no][4]
-  int tpb;     // per-problem spheres: targets per refine block (their sphere sets staged side by side)
+  const double* prims;  // primitive records [np][CR_PRIM_DOUBLES] (per problem: [P][np][..])
+  int np;
+  int sph_pp;  // obstacles are per problem: spheres [P][no][4], primitives [P][np][CR_PRIM_DOUBLES]
+  int tpb;     // per-problem obstacles: targets per refine block (their obstacle sets staged side by side)
   int S, K, k_init, k_final;
   T alpha0, eps;
   double lambda0, lim_tol, pos_tol, rot_tol;
@@ -232,15 +234,29 @@ template <typename T> struct StageOut {
   T* u;
 };
 
+// Stage the obstacle set of problem p (set 0 of a shared scene) at base, in precision T.
+template <typename T, typename A>
+__device__ ObsK<T> stage_problem_obstacles(const A& a, int64_t p, const RobotK<T>& rb, T delta, unsigned char* base) {
+  const int64_t q = a.sph_pp ? p : 0;
+  return stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
+                         a.np, rb, delta, base);
+}
+
+// Bytes of one staged obstacle set in FP64 and in T, side by side (the refine kernels').
+template <typename T> __host__ __device__ inline size_t refine_set_bytes(int no, int np) {
+  return ((obstacles_smem<double>(no, np) + 15) & ~(size_t)15) + ((obstacles_smem<T>(no, np) + 15) & ~(size_t)15);
+}
+
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a, StageOut<T> so) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int S = a.S;
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
   const int64_t p = blockIdx.x;
+  const int nob = a.no + a.np;
+  ObsK<T> sph(nullptr);
   if (OBST) {
-    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
+    sph = stage_problem_obstacles(a, p, rb, w.delta, smem_raw);
     __syncthreads();
   }
   const int s = threadIdx.x;
@@ -249,9 +265,9 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
     TargetK<T> tg = load_target<T>(a.targets, a.P, p, a.kind);
     T u[D], g[D], coll = T(0);
     draw_seed_m<MODEL, T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, 0, a.box, u);
-    if (OBST && a.no > 0) {
+    if (OBST && nob > 0) {
       for (int att = 1; att < 8; ++att) {
-        if (!state_collides<T, N, MODEL>(rb, sph, a.no, u)) break;
+        if (!state_collides<T, N, MODEL>(rb, sph, nob, u)) break;
         draw_seed_m<MODEL, T, N>(a.seed, (uint64_t)(a.p0 + p), (uint64_t)s, att, a.box, u);
       }
     }
@@ -261,7 +277,7 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
     // it = -1 evaluates the seed itself (no step, always taken); it >= 0 are the projected-gradient
     // steps. One evaluation site for both keeps the kernel's code half as long.
     for (int it = -1; it < a.k_init; ++it)
-      acc += pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha, it < 0);
+      acc += pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, nob, u, g, F, coll, alpha, it < 0);
     const int64_t i = p * S + s;
     so.F[i] = float(F);
     so.C[i] = float(coll);
@@ -315,11 +331,12 @@ __global__ void __launch_bounds__(256) k_ik_select(IkArgs<T> a, StageOut<T> so, 
 // FP64 acceptance of one state: cost, pose errors, limit and clearance flags.
 template <int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, int kind,
-                         const TargetK<double>& tg, const Sphere4<double>* sph, int no,
+                         const TargetK<double>& tg, ObsK<double> ob, int no,
                          const double (&u)[3 * N], double lim_tol, double& pos, double& rot,
                          unsigned char& flags) {
+  const Sphere4<double>* sph = ob.s;
   double dummy[3 * N];
-  double F = eval_ik<double, N, OBST, false, false, true, MODEL>(rb, w, kind, tg, sph, no, u, dummy, nullptr, nullptr,
+  double F = eval_ik<double, N, OBST, false, false, true, MODEL>(rb, w, kind, tg, ob, no, u, dummy, nullptr, nullptr,
                                                                 nullptr);
   Chain<double, N> ch;
   chain_forward<double, N, MODEL>(rb, u, ch);
@@ -350,7 +367,7 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
     }
     if (sqrt(ch.x[i]) > rb.thmax[i] + 1e-6) lim = false;
   }
-  // clearance without the margin (radius r_s + r_body); the broad phase uses the larger reach
+  // clearance without the margin (radius r_o + r_body); the broad phase uses the larger reach
   bool free = true;
   if (OBST && no > 0) {
     const double inb = 1.0 / rb.nb;
@@ -368,6 +385,12 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
             backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], k * inb, q, wp, s, c);
             for (uint64_t bits = gm; bits; bits &= bits - 1) {
               const int j = j0 + __ffsll((long long)bits) - 1;
+              if (j >= ob.ns) {
+                const PrimK<double>& P = ob.p[j - ob.ns];
+                double viol, nv[3];
+                if (prim_active(P, wp, P.reach - w.delta, viol, nv)) { free = false; break; }
+                continue;
+              }
               double ddx = wp[0] - sph[j].x, ddy = wp[1] - sph[j].y, ddz = wp[2] - sph[j].z;
               double r = sph[j].reach - w.delta;
               if (ddx * ddx + ddy * ddy + ddz * ddz < r * r) { free = false; break; }
@@ -416,9 +439,9 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
                                                     WeightsK<double> wd, IkArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nset = a.sph_pp ? a.tpb : 1;  // sphere sets staged by this block
-  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw + (size_t)nset * a.no * sizeof(Sphere4<double>));
+  const int nob = a.no + a.np;
+  ObsK<double> sphd(nullptr);
+  ObsK<T> sph(nullptr);
   const int64_t PK = a.P * a.K;
   // shared sphere set: one candidate per thread; per-problem sets: tpb targets per block, K threads
   // each
@@ -426,21 +449,20 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
   const int64_t c = a.sph_pp ? ((int64_t)blockIdx.x * a.tpb + jt) * a.K + (int)threadIdx.x % a.K
                              : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (OBST) {
-    if (a.sph_pp) {
-      const int64_t t0 = (int64_t)blockIdx.x * a.tpb;
-      const int ntb = (int)(a.P - t0 < a.tpb ? a.P - t0 : a.tpb);
-      for (int e = threadIdx.x; e < ntb * a.no; e += blockDim.x) {
-        const double* q = a.spheres + ((t0 + e / a.no) * a.no + e % a.no) * 4;
-        sphd[e] = Sphere4<double>{q[0], q[1], q[2], q[3] + rbd.rbody + wd.delta};
-        sph[e] = Sphere4<T>{T(q[0]), T(q[1]), T(q[2]), T(q[3]) + rb.rbody + w.delta};
+    // the block's obstacle sets (tpb of them with per-problem scenes), each in FP64 and in T
+    const size_t setb = refine_set_bytes<T>(a.no, a.np), offt = (obstacles_smem<double>(a.no, a.np) + 15) & ~(size_t)15;
+    const int64_t t0 = a.sph_pp ? (int64_t)blockIdx.x * a.tpb : 0;
+    const int ntb = a.sph_pp ? (int)(a.P - t0 < a.tpb ? a.P - t0 : a.tpb) : 1;
+    for (int t = 0; t < ntb; ++t) {
+      unsigned char* base = smem_raw + (size_t)t * setb;
+      const ObsK<double> od = stage_problem_obstacles(a, t0 + t, rbd, wd.delta, base);
+      const ObsK<T> ot = stage_problem_obstacles(a, t0 + t, rb, w.delta, base + offt);
+      if (t == jt) {
+        sphd = od;
+        sph = ot;
       }
-    } else {
-      stage_spheres(a.spheres, a.no, rbd, wd.delta, sphd);
-      stage_spheres(a.spheres, a.no, rb, w.delta, sph);
     }
     __syncthreads();
-    sphd += jt * a.no;
-    sph += jt * a.no;
   }
   if (c >= PK || (a.sph_pp && jt >= a.tpb)) return;
   const int64_t p = c / a.K;
@@ -453,7 +475,7 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
     double lam = a.lambda0, nu = 2.0;
     T F;
     for (int it = 0; it < a.k_final; ++it)
-      lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+      lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, nob, u, lam, nu, F);
   }
   double ud[D];
 #pragma unroll
@@ -462,7 +484,7 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
   unsigned char flags = 0;
   if (valid) {
     TargetK<double> tgd = load_target<double>(a.targets, a.P, p, a.kind);
-    F = accept_fp64<N, OBST, MODEL>(rbd, wd, a.kind, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+    F = accept_fp64<N, OBST, MODEL>(rbd, wd, a.kind, tgd, sphd, nob, ud, a.lim_tol, pos, rot, flags);
   }
 #pragma unroll
   for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
@@ -484,9 +506,8 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
                                                        WeightsK<double> wd, IkArgs<float> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw);
-  Sphere4<float>* sph = reinterpret_cast<Sphere4<float>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<double>));
-  double* scr = reinterpret_cast<double*>(smem_raw + (size_t)a.no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)));
+  const int nob = a.no + a.np;
+  double* scr = reinterpret_cast<double*>(smem_raw + refine_set_bytes<float>(a.no, a.np));
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;  // blockDim = 32 K: warp wid, candidate wid
   double* sud = scr + (size_t)a.K * 128;                       // refined states [K][D] for the acceptance
   double* col = scr + wid * 128;
@@ -494,12 +515,9 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
   double* sx = colr + 32;
   double* sdg = sx + 32;
   const int64_t p = blockIdx.x;
-  const double* sp = a.spheres + p * a.no * 4;
-  for (int e = threadIdx.x; e < a.no; e += blockDim.x) {
-    const double* q = sp + 4 * e;
-    sphd[e] = Sphere4<double>{q[0], q[1], q[2], q[3] + rbd.rbody + wd.delta};
-    sph[e] = Sphere4<float>{float(q[0]), float(q[1]), float(q[2]), float(q[3]) + rb.rbody + w.delta};
-  }
+  const ObsK<double> sphd = stage_problem_obstacles(a, p, rbd, wd.delta, smem_raw);
+  const ObsK<float> sph =
+      stage_problem_obstacles(a, p, rb, w.delta, smem_raw + ((obstacles_smem<double>(a.no, a.np) + 15) & ~(size_t)15));
   __syncthreads();
   const int64_t PK = a.P * a.K;
   {
@@ -512,7 +530,7 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
       const AugSlots<D> sl = aug_slots<D>(lane);
       double lam = a.lambda0, nu = 2.0;
       for (int it = 0; it < a.k_final; ++it)
-        warp_lm_step<float, N, true, double>(rb, w, tg, sph, a.no, u, sl, lam, nu, col, colr, sx, sdg);
+        warp_lm_step<float, N, true, double>(rb, w, tg, sph, nob, u, sl, lam, nu, col, colr, sx, sdg);
     }
     if (lane == 0) {
 #pragma unroll
@@ -531,7 +549,7 @@ __global__ void __launch_bounds__(256, 1) k_ik_refine_warp(RobotK<float> rb, Wei
     unsigned char flags = 0;
     if (isfinite(ud[0])) {
       const TargetK<double> tgd = load_target<double>(a.targets, a.P, p, CR_TASK_IK6);
-      F = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+      F = accept_fp64<N, true>(rbd, wd, CR_TASK_IK6, tgd, sphd, nob, ud, a.lim_tol, pos, rot, flags);
     }
 #pragma unroll
     for (int q = 0; q < D; ++q) a.cand_u64[q * PK + c] = ud[q];
@@ -594,6 +612,8 @@ template <typename T> struct StepArgs {
   int S;
   const double* spheres;
   int no;
+  const double* prims;
+  int np;
   T* u;
   int64_t B;
   int iters;
@@ -609,11 +629,12 @@ template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  ObsK<T> sph(nullptr);
   if (OBST) {
-    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    sph = stage_obstacles(a.spheres, a.no, a.prims, a.np, rb, w.delta, smem_raw);
     __syncthreads();
   }
+  const int nob = a.no + a.np;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B) return;
   T u[D];
@@ -624,10 +645,10 @@ __global__ void __launch_bounds__(128) k_lm_steps(RobotK<T> rb, WeightsK<T> w, S
   int nacc = 0;
   T F = T(0);
   for (int it = 0; it < a.iters; ++it)
-    nacc += lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, lam, nu, F);
+    nacc += lm_iteration<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, nob, u, lam, nu, F);
   if (a.iters == 0 || a.F64) {
     T dummy[D];
-    F = eval_ik<T, N, OBST, false, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, dummy, nullptr, nullptr,
+    F = eval_ik<T, N, OBST, false, false, true, MODEL>(rb, w, a.kind, tg, sph, nob, u, dummy, nullptr, nullptr,
                                                        nullptr);
   }
 #pragma unroll
@@ -642,37 +663,40 @@ template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_pg_steps(RobotK<T> rb, WeightsK<T> w, StepArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  ObsK<T> sph(nullptr);
   if (OBST) {
-    stage_spheres(a.spheres, a.no, rb, w.delta, sph);
+    sph = stage_obstacles(a.spheres, a.no, a.prims, a.np, rb, w.delta, smem_raw);
     __syncthreads();
   }
+  const int nob = a.no + a.np;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B) return;
   T u[D], g[D], coll;
 #pragma unroll
   for (int q = 0; q < D; ++q) u[q] = a.u[q * a.B + b];
   TargetK<T> tg = load_target<T>(a.targets, a.P, b / a.S, a.kind);
-  T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, nullptr, nullptr, &coll);
+  T F = eval_ik<T, N, OBST, true, false, true, MODEL>(rb, w, a.kind, tg, sph, nob, u, g, nullptr, nullptr, &coll);
   T alpha = a.alpha[b];
   for (int it = 0; it < a.iters; ++it)
-    pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, a.no, u, g, F, coll, alpha);
+    pg_step<T, N, OBST, MODEL>(rb, w, a.kind, tg, sph, nob, u, g, F, coll, alpha);
 #pragma unroll
   for (int q = 0; q < D; ++q) a.u[q * a.B + b] = u[q];
   a.alpha[b] = alpha;
   a.F[b] = F;
 }
 
-// sph_pp = 0: blocks of 128 consecutive seeds; sph_pp = 1: blockIdx.y = problem, its own spheres.
+// sph_pp = 0: blocks of 128 consecutive seeds; sph_pp = 1: blockIdx.y = problem, its own obstacles.
 template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
 __global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, const double* spheres, int no,
-                                                int sph_pp, uint64_t key, int64_t p0, int64_t P, int S,
-                                                SeedBox box, T* u_out) {
+                                                const double* prims, int np, int sph_pp, uint64_t key, int64_t p0,
+                                                int64_t P, int S, SeedBox box, T* u_out) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
+  ObsK<T> sph(nullptr);
   if (OBST) {
-    stage_spheres(spheres + (sph_pp ? (int64_t)blockIdx.y * no * 4 : 0), no, rb, w.delta, sph);
+    const int64_t q = sph_pp ? (int64_t)blockIdx.y : 0;
+    sph = stage_obstacles(spheres + q * no * 4, no, np > 0 ? prims + q * np * CR_PRIM_DOUBLES : nullptr, np, rb,
+                          w.delta, smem_raw);
     __syncthreads();
   }
   const int64_t PS = P * S;
@@ -682,9 +706,9 @@ __global__ void __launch_bounds__(128) k_seeds(RobotK<T> rb, WeightsK<T> w, cons
   const int64_t p = i / S, s = i % S;
   T u[D];
   draw_seed_m<MODEL, T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, 0, box, u);
-  if (OBST && no > 0) {
+  if (OBST && no + np > 0) {
     for (int att = 1; att < 8; ++att) {
-      if (!state_collides<T, N, MODEL>(rb, sph, no, u)) break;
+      if (!state_collides<T, N, MODEL>(rb, sph, no + np, u)) break;
       draw_seed_m<MODEL, T, N>(key, (uint64_t)(p0 + p), (uint64_t)s, att, box, u);
     }
   }
@@ -759,7 +783,9 @@ template <typename T> IkArgs<T> ik_args(const SolveArgs& a) {
   k.P = a.task.n_targets;
   k.spheres = a.scene.spheres;
   k.no = a.scene.n_o;
-  k.sph_pp = (a.scene.per_problem && a.scene.n_o > 0) ? 1 : 0;
+  k.prims = a.scene.prims;
+  k.np = a.scene.n_p;
+  k.sph_pp = (a.scene.per_problem && a.scene.n_o + a.scene.n_p > 0) ? 1 : 0;
   k.tpb = 1;
   k.S = p.S;
   k.K = p.n_final;
@@ -799,11 +825,11 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   WeightsK<double> wd = crh::weights_k<double>(a.task.w);
   IkArgs<T> k = ik_args<T>(a);
   const int64_t P = k.P;
-  const int no = k.no;
+  const int no = k.no, np = k.np;
   const int threads = ((k.S + 31) / 32) * 32;
-  const size_t sm1 = (size_t)no * sizeof(Sphere4<T>);
+  const size_t sm1 = obstacles_smem<T>(no, np);
   cr_status st;
-  const bool coll_rows = no > 0 || a.task.w.rho_s > 0;  // collision rows: spheres and / or self-contact
+  const bool coll_rows = no + np > 0 || a.task.w.rho_s > 0;  // collision rows: obstacles and / or self-contact
   if (which & 1) {
     unsigned char* ws = (unsigned char*)a.ws;
     StageOut<T> so{(float*)(ws + a.lay.stage_F), (float*)(ws + a.lay.stage_C), (T*)(ws + a.lay.stage_u)};
@@ -823,13 +849,13 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
     if ((st = crh::check_launch("cr_solve_ik SelectTop"))) return st;
   }
   if (!(which & 2)) return CR_OK;
-  // per-problem spheres: one warp per block. With K >= 8 it holds 32 / K (at most 4) targets, their
-  // sphere sets side by side in shared memory, so that the FP64 instructions run with all lanes busy
+  // per-problem obstacles: one warp per block. With K >= 8 it holds 32 / K (at most 4) targets, their
+  // obstacle sets side by side in shared memory, so that the FP64 instructions run with all lanes busy
   // (the FP64 pipe charges a whole warp). With fewer candidates per target it holds one: more
   // targets per warp make the lanes' clearance loops diverge (the warp runs the union of their
   // trips), which costs more than the idle FP64 lanes (measured on the 4-candidate goal IK of the
   // trajectory workload).
-  const size_t per_set = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<T>));
+  const size_t per_set = no + np > 0 ? refine_set_bytes<T>(no, np) : 0;
   k.tpb = 1;
   if (k.sph_pp && k.K >= 8) {
     k.tpb = 32 / k.K;
@@ -846,8 +872,7 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   bool warp_refine = false;
   if constexpr (sizeof(T) == 4 && MODEL == CR_MODEL_TENDON) {
     if (k.sph_pp && k.K < 8 && k.kind == CR_TASK_IK6 && !(a.task.w.rho_s > 0)) {
-      const size_t smw = (size_t)no * (sizeof(Sphere4<double>) + sizeof(Sphere4<float>)) +
-                         (size_t)k.K * (128 + D) * sizeof(double);
+      const size_t smw = refine_set_bytes<float>(no, np) + (size_t)k.K * (128 + D) * sizeof(double);
       if ((st = set_smem(k_ik_refine_warp<N>, smw))) return st;
       k_ik_refine_warp<N><<<(unsigned)P, 32 * k.K, smw, a.stream>>>(rb, w, rbd, wd, k);
       warp_refine = true;
@@ -874,6 +899,8 @@ template <typename T> StepArgs<T> step_args(const SolveArgs& a) {
   k.S = a.task.seeds_per_target;
   k.spheres = a.scene.spheres;
   k.no = a.scene.n_o;
+  k.prims = a.scene.prims;
+  k.np = a.scene.n_p;
   k.u = (T*)a.u;
   k.B = a.B;
   k.iters = a.iters;
@@ -890,8 +917,8 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status lm_steps_n(c
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
-  size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0 || w.rho_s > T(0)) k_lm_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  size_t sm = obstacles_smem<T>(k.no, k.np);
+  if (k.no + k.np > 0 || w.rho_s > T(0)) k_lm_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   else k_lm_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_lm_step");
 }
@@ -900,8 +927,8 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status pg_steps_n(c
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   StepArgs<T> k = step_args<T>(a);
-  size_t sm = (size_t)k.no * sizeof(Sphere4<T>);
-  if (k.no > 0 || w.rho_s > T(0)) k_pg_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
+  size_t sm = obstacles_smem<T>(k.no, k.np);
+  if (k.no + k.np > 0 || w.rho_s > T(0)) k_pg_steps<T, N, true, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   else k_pg_steps<T, N, false, MODEL><<<grid1(a.B, 128), 128, sm, a.stream>>>(rb, w, k);
   return crh::check_launch("cr_pg_steps");
 }
@@ -910,16 +937,16 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status seeds_n(cons
   RobotK<T> rb = crh::robot_k<T>(a.robot);
   WeightsK<T> w = crh::weights_k<T>(a.task.w);
   const SeedBox box = seed_box(a.robot);
-  int no = a.scene.n_o;
+  int no = a.scene.n_o, np = a.scene.n_p;
   int pp = a.scene.per_problem ? 1 : 0;
-  size_t sm = (size_t)no * sizeof(Sphere4<T>);
+  size_t sm = obstacles_smem<T>(no, np);
   dim3 g = pp ? dim3(grid1(a.S, 128), (unsigned)a.P) : dim3(grid1(a.P * a.S, 128));
-  if (no > 0)
-    k_seeds<T, N, true, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, box,
-                                                         (T*)a.u);
+  if (no + np > 0)
+    k_seeds<T, N, true, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.scene.prims, np, pp, a.key,
+                                                         a.p0, a.P, a.S, box, (T*)a.u);
   else
-    k_seeds<T, N, false, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, pp, a.key, a.p0, a.P, a.S, box,
-                                                          (T*)a.u);
+    k_seeds<T, N, false, MODEL><<<g, 128, sm, a.stream>>>(rb, w, a.scene.spheres, no, a.scene.prims, np, pp, a.key,
+                                                          a.p0, a.P, a.S, box, (T*)a.u);
   return crh::check_launch("cr_seeds");
 }
 

@@ -166,6 +166,8 @@ cr_status cr_solve_traj_prm(const cr_robot* robot, const cr_scene* scene, const 
                             double* length, int32_t* hops, void* workspace, size_t ws_bytes, cr_stream stream) {
   if (!prm || !map) return fail(CR_EINVAL, "cr_solve_traj_prm: prm and map are required");
   if (task && check_self_rows(task->w, false, "cr_solve_traj_prm")) return CR_EINVAL;
+  cr_status st = check_scene_spheres_only(scene, "cr_solve_traj_prm");
+  if (st) return st;
   return solve_traj(robot, scene, task, goal_ik, prm, map, k_traj, alpha0, X_out, cost_out, goal_pos, goal_rot, speed,
                     accel, lim_ok, col_ok, length, hops, workspace, ws_bytes, stream);
 }

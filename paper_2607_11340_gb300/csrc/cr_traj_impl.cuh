@@ -76,7 +76,7 @@ template <typename T> struct TrajSmem {
 // owner through shared memory, the owner runs everything else and hands the gradient back.
 template <typename T, int N, bool OBST, bool GRAD>
 __device__ T traj_state_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TrajW<T>& tw, int t, int Tn,
-                             const T (&u)[3 * N], const TargetK<T>& goal, const Sphere4<T>* sph, int no,
+                             const T (&u)[3 * N], const TargetK<T>& goal, ObsK<T> sph, int no,
                              TrajSmem<T>& sm, T (&gu)[3 * N], bool split = false, bool aux = false) {
   constexpr int D = 3 * N;
   const bool active = t < Tn;
@@ -204,6 +204,8 @@ template <typename T> struct TrajArgs {
   int Tn;
   const double* spheres;
   int no;
+  const double* prims;
+  int np;
   int sph_pp;
   // cost / gradient
   const T* x;             // [D][P*(Tn-1)]
@@ -227,18 +229,26 @@ template <typename T> struct TrajArgs {
   unsigned char* col_ok;
 };
 
+// Stage problem p's obstacle set (the shared one without per-problem scenes) at base.
+template <typename T, typename A>
+__device__ ObsK<T> stage_traj_obstacles(const A& a, int64_t p, const RobotK<T>& rb, T delta, unsigned char* base) {
+  const int64_t q = a.sph_pp ? p : 0;
+  return stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
+                         a.np, rb, delta, base);
+}
+
 template <typename T, int N, bool OBST, bool GRAD>
 __global__ void __launch_bounds__(256) k_traj_cost(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, TrajArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t p = blockIdx.x;
   const int t = threadIdx.x, Tn = a.Tn;
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
-  size_t off = ((size_t)a.no * sizeof(Sphere4<T>) + 15) & ~size_t(15);
+  size_t off = (obstacles_smem<T>(a.no, a.np) + 15) & ~size_t(15);
   TrajSmem<T> sm;
   sm.carve(smem_raw + off, Tn, D);
+  ObsK<T> sph(nullptr);
   if (OBST) {
-    stage_spheres(a.spheres + (a.sph_pp ? p * a.no * 4 : 0), a.no, rb, w.delta, sph);
+    sph = stage_traj_obstacles(a, p, rb, w.delta, smem_raw);
     __syncthreads();
   }
   const int64_t ld = a.P * (Tn - 1);
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(256) k_traj_cost(RobotK<T> rb, WeightsK<T> w, 
   }
   TargetK<T> goal = load_target<T>(a.goal, a.P, p, CR_TASK_IK6);
   T gu[D];
-  T F = traj_state_eval<T, N, OBST, GRAD>(rb, w, tw, t, Tn, u, goal, sph, a.no, sm, gu);
+  T F = traj_state_eval<T, N, OBST, GRAD>(rb, w, tw, t, Tn, u, goal, sph, a.no + a.np, sm, gu);
   T Ft = block_sum(F, sm.red);
   if (t == 0) a.cost[p] = Ft;
   if (GRAD && t >= 1 && t < Tn) {
@@ -270,25 +280,26 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t p = blockIdx.x;
   const int Tn = a.Tn, Wt = ((Tn + 31) / 32) * 32;
-  // split evaluation (blockDim = 2 Wt): thread t and t + Wt share state t, each with half the spheres
+  // split evaluation (blockDim = 2 Wt): thread t and t + Wt share state t, each with half the obstacles
   const bool split = (int)blockDim.x == 2 * Wt;
   const bool aux = split && (int)threadIdx.x >= Wt;
   const int t = aux ? (int)threadIdx.x - Wt : (int)threadIdx.x;
-  Sphere4<T>* sph = reinterpret_cast<Sphere4<T>*>(smem_raw);
-  Sphere4<double>* sphd = reinterpret_cast<Sphere4<double>*>(smem_raw + (size_t)a.no * sizeof(Sphere4<T>));
-  size_t off = ((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15);
+  const int nob = a.no + a.np;
+  const size_t offd = (obstacles_smem<T>(a.no, a.np) + 15) & ~size_t(15);
+  size_t off = offd + ((obstacles_smem<double>(a.no, a.np) + 15) & ~size_t(15));
   TrajSmem<T> sm;
   sm.carve(smem_raw + off, Tn, D);
+  ObsK<T> sph(nullptr);
+  ObsK<double> sphd(nullptr);
   if (OBST) {
-    const double* sp = a.spheres + (a.sph_pp ? p * a.no * 4 : 0);
-    stage_spheres(sp, a.no, rb, w.delta, sph);
-    stage_spheres(sp, a.no, rbd, wd.delta, sphd);
+    sph = stage_traj_obstacles(a, p, rb, w.delta, smem_raw);
+    sphd = stage_traj_obstacles(a, p, rbd, wd.delta, smem_raw + offd);
     __syncthreads();
   }
   const bool active = t < Tn;
-  const int nh = split ? (a.no + 1) / 2 : a.no;
-  const Sphere4<T>* sph_m = aux ? sph + nh : sph;
-  const int no_m = aux ? a.no - nh : nh;
+  const int nh = split ? (nob + 1) / 2 : nob;
+  const ObsK<T> sph_m = aux ? sph.from(nh) : sph;
+  const int no_m = aux ? nob - nh : nh;
   T u[D];
 #pragma unroll
   for (int q = 0; q < D; ++q) {
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   unsigned char flags = 3;
   if (owner) {
     TargetK<double> gd = load_target<double>(a.goal, a.P, p, CR_TASK_IK6);
-    accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, gd, sphd, a.no, ud, a.lim_tol, pos, rot, flags);
+    accept_fp64<N, OBST>(rbd, wd, CR_TASK_IK6, gd, sphd, nob, ud, a.lim_tol, pos, rot, flags);
   }
   // speed / acceleration ratios in FP64 over the states shared in a double buffer
   double* sd = reinterpret_cast<double*>(smem_raw + off + ((TrajSmem<T>::bytes(Tn, D) + 15) & ~size_t(15)));
@@ -720,7 +731,9 @@ template <typename T> TrajArgs<T> traj_args(const TrajLaunch& l) {
   a.Tn = l.task.T;
   a.spheres = l.scene.spheres;
   a.no = l.scene.n_o;
-  a.sph_pp = (l.scene.per_problem && l.scene.n_o > 0) ? 1 : 0;
+  a.prims = l.scene.prims;
+  a.np = l.scene.n_p;
+  a.sph_pp = (l.scene.per_problem && l.scene.n_o + l.scene.n_p > 0) ? 1 : 0;
   a.x = (const T*)l.x;
   a.cost = (T*)l.cost;
   a.grad = (T*)l.grad;
@@ -751,9 +764,9 @@ template <typename T, int N> cr_status traj_cost_n(const TrajLaunch& l) {
   TrajW<T> tw = traj_w<T>(l.task.w);
   TrajArgs<T> a = traj_args<T>(l);
   const int threads = ((a.Tn + 31) / 32) * 32;
-  size_t sm = (((size_t)a.no * sizeof(Sphere4<T>) + 15) & ~size_t(15)) + TrajSmem<T>::bytes(a.Tn, D);
+  size_t sm = ((obstacles_smem<T>(a.no, a.np) + 15) & ~size_t(15)) + TrajSmem<T>::bytes(a.Tn, D);
   cr_status st;
-  if (a.no > 0 || w.rho_s > T(0)) {  // collision rows: spheres and / or self-contact
+  if (a.no + a.np > 0 || w.rho_s > T(0)) {  // collision rows: obstacles and / or self-contact
     if (l.grad) { if ((st = set_smem(k_traj_cost<T, N, true, true>, sm))) return st;
       k_traj_cost<T, N, true, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, a); }
     else { if ((st = set_smem(k_traj_cost<T, N, true, false>, sm))) return st;
@@ -775,14 +788,15 @@ template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
   WeightsK<double> wd = crh::weights_k<double>(l.task.w);
   TrajW<T> tw = traj_w<T>(l.task.w);
   TrajArgs<T> a = traj_args<T>(l);
-  // FP32 with spheres: two threads per state share the clearance rows (the FP64 form keeps one, its
+  // FP32 with obstacles: two threads per state share the clearance rows (the FP64 form keeps one, its
   // sums in the oracle's order)
   const int Wt = ((a.Tn + 31) / 32) * 32;
-  const int threads = (sizeof(T) == 4 && a.no >= 2 && 2 * Wt <= 256) ? 2 * Wt : Wt;
-  size_t sm = (((size_t)a.no * (sizeof(Sphere4<T>) + sizeof(Sphere4<double>)) + 15) & ~size_t(15)) +
+  const int threads = (sizeof(T) == 4 && a.no + a.np >= 2 && 2 * Wt <= 256) ? 2 * Wt : Wt;
+  size_t sm = ((obstacles_smem<T>(a.no, a.np) + 15) & ~size_t(15)) +
+              ((obstacles_smem<double>(a.no, a.np) + 15) & ~size_t(15)) +
               ((TrajSmem<T>::bytes(a.Tn, D) + 15) & ~size_t(15)) + ((size_t)a.Tn * D + 32) * sizeof(double);
   cr_status st;
-  if (a.no > 0 || w.rho_s > T(0)) {  // collision rows: spheres and / or self-contact
+  if (a.no + a.np > 0 || w.rho_s > T(0)) {  // collision rows: obstacles and / or self-contact
     if ((st = set_smem(k_traj_solve<T, N, true>, sm))) return st;
     k_traj_solve<T, N, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
   } else {

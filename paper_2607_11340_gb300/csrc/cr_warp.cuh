@@ -100,10 +100,11 @@ __device__ void warp_row(const AugSlots<D>& sl, T (&A)[AugSlots<D>::SL], T& gq, 
 // q of g = J^T r. Rows: pose (6), sum-zero per segment, active tendon bounds, active curvature
 // limits, active clearance pairs (backbone samples split over the lanes).
 template <typename T, int N, bool OBST>
-__device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, const Sphere4<T>* sph,
+__device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, ObsK<T> ob,
                        int no, const T (&u)[3 * N], const AugSlots<3 * N>& sl, T (&A)[AugSlots<3 * N>::SL], T& gq,
                        const bool NORMAL) {
   constexpr int D = 3 * N, SL = AugSlots<D>::SL;
+  const Sphere4<T>* sph = ob.s;
   const int lane = threadIdx.x & 31;
   const bool colq = lane < D;
   const int myl = colq ? lane / 3 : 0, mya = colq ? lane % 3 : 0;
@@ -239,23 +240,37 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
           backbone_point(ch.Rb[ii], ch.pb[ii], ch.ax[ii], ch.ay[ii], ch.x[ii], ch.L[ii], T(mine ? k : 1) * inb, q,
                          wpt, s, c);
           for (uint64_t bits = um; bits; bits &= bits - 1) {
-            const Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
-            const T dx = wpt[0] - S.x, dy = wpt[1] - S.y, dz = wpt[2] - S.z;
-            const T d2 = dx * dx + dy * dy + dz * dz;
-            const bool act = mine && d2 < S.reach * S.reach;
-            T idist = T(0), viol = T(0);
-            if (act) {
-              idist = c_rsqrt(d2);
-              viol = S.reach - d2 * idist;
-              Fsplit += T(0.5) * w.rho_c * viol * viol;
+            const int jo = j0 + __ffsll((long long)bits) - 1;
+            bool act;
+            T viol = T(0), nvx = T(0), nvy = T(0), nvz = T(0);
+            if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
+              const PrimK<T>& P = ob.p[jo - ob.ns];
+              T nv[3];
+              act = mine && prim_active(P, wpt, P.reach, viol, nv);
+              if (act) {
+                nvx = nv[0]; nvy = nv[1]; nvz = nv[2];
+              } else {
+                viol = T(0);
+              }
+            } else {
+              const Sphere4<T> S = sph[jo];
+              const T dx = wpt[0] - S.x, dy = wpt[1] - S.y, dz = wpt[2] - S.z;
+              const T d2 = dx * dx + dy * dy + dz * dz;
+              act = mine && d2 < S.reach * S.reach;
+              if (act) {
+                const T idist = c_rsqrt(d2);
+                viol = S.reach - d2 * idist;
+                nvx = dx * idist; nvy = dy * idist; nvz = dz * idist;
+              }
             }
+            if (act) Fsplit += T(0.5) * w.rho_c * viol * viol;
             if (!NORMAL) continue;
             unsigned m = __ballot_sync(0xffffffffu, act);
             while (m) {
               const int src = __ffs(m) - 1;
               m &= m - 1;
-              const T nx = __shfl_sync(0xffffffffu, dx * idist, src), ny = __shfl_sync(0xffffffffu, dy * idist, src),
-                      nz = __shfl_sync(0xffffffffu, dz * idist, src);
+              const T nx = __shfl_sync(0xffffffffu, nvx, src), ny = __shfl_sync(0xffffffffu, nvy, src),
+                      nz = __shfl_sync(0xffffffffu, nvz, src);
               const T rr = w.sc * __shfl_sync(0xffffffffu, viol, src);
               const T px = __shfl_sync(0xffffffffu, wpt[0], src), py = __shfl_sync(0xffffffffu, wpt[1], src),
                       pz = __shfl_sync(0xffffffffu, wpt[2], src);
@@ -299,7 +314,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
 // the gain ratio formed, in V (T for exploration, double for a refinement). Returns the cost after
 // the step. The warp's scratch: col, colr, sx, sdg (D + 1 values of V each).
 template <typename T, int N, bool OBST, typename V = T>
-__device__ T warp_lm_step(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, const Sphere4<T>* sph,
+__device__ T warp_lm_step(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<T>& tg, ObsK<T> sph,
                           int no, T (&u)[3 * N], const AugSlots<3 * N>& sl, V& lam, V& nu, V* col, V* colr, V* sx,
                           V* sdg) {
   constexpr int D = 3 * N, SL = AugSlots<D>::SL;

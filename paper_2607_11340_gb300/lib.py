@@ -21,6 +21,8 @@ CR_MAX_SEG = 6
 CR_MAX_SPHERES = 256
 CR_MAX_NB = 64
 CR_MAX_SEEDS = 256
+CR_PRIM_DOUBLES = 16
+CR_PRIM_SPHERE, CR_PRIM_CAPSULE, CR_PRIM_BOX = 0, 1, 2
 
 EXPORTS = ("cr_fk", "cr_fk_jac", "cr_cost_grad", "cr_reduce_rows", "cr_lm_step", "cr_pg_steps",
            "cr_seeds", "cr_topk", "cr_ik_workspace_size", "cr_solve_ik", "cr_ik_stage1", "cr_ik_stage2",
@@ -60,7 +62,8 @@ class cr_weights(C.Structure):
 
 
 class cr_scene(C.Structure):
-    _fields_ = [("spheres", C.c_void_p), ("n_o", C.c_int32), ("per_problem", C.c_int32)]
+    _fields_ = [("spheres", C.c_void_p), ("n_o", C.c_int32), ("per_problem", C.c_int32), ("prims", C.c_void_p),
+                ("n_p", C.c_int32)]
 
 
 class cr_task(C.Structure):

@@ -43,6 +43,7 @@ def test_struct_layout_matches_c(crlib, tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(cr_robot), sizeof(cr_weights), sizeof(cr_scene), sizeof(cr_task), sizeof(cr_ik_params));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(cr_robot, r_body), offsetof(cr_robot, l_max), offsetof(cr_task, w), offsetof(cr_ik_params, seed), offsetof(cr_ik_params, precision));
+  printf("%zu %zu %d\\n", offsetof(cr_scene, prims), offsetof(cr_scene, n_p), CR_PRIM_DOUBLES);
   return 0;
 }
 """)
@@ -53,7 +54,7 @@ int main(void) {
     py = [C.sizeof(L.cr_robot), C.sizeof(L.cr_weights), C.sizeof(L.cr_scene), C.sizeof(L.cr_task),
           C.sizeof(L.cr_ik_params), L.cr_robot.r_body.offset, L.cr_robot.l_max.offset, L.cr_task.w.offset,
           L.cr_ik_params.seed.offset,
-          L.cr_ik_params.precision.offset]
+          L.cr_ik_params.precision.offset, L.cr_scene.prims.offset, L.cr_scene.n_p.offset, L.CR_PRIM_DOUBLES]
     assert [int(x) for x in out] == py
 
 
@@ -281,3 +282,37 @@ def test_self_contact_weight_is_validated(crlib):
     items = crlib._batch_items([(0, 3, 1, 64, 0)])
     assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 1, C.byref(bp), *([dummy] * 8), dummy, 1 << 30, None) \
         == crlib.CR_EINVAL
+
+
+def test_scene_primitives_are_validated(crlib):
+    """n_p outside 0..CR_MAX_SPHERES - n_o, a NULL or misaligned primitive array, and primitives given
+    to the PRM entry points are rejected before any device call."""
+    L = crlib.load()
+    dummy = C.c_void_p(256)
+    r = _robot(crlib)
+    t = crlib.cr_task()
+    t.kind, t.seeds_per_target, t.targets, t.n_targets = 0, 1, 256, 8
+
+    def cost_grad(sc):
+        return L.cr_cost_grad(C.byref(r), C.byref(sc), C.byref(t), dummy, 8, dummy, None, None, None, 0, None)
+
+    sc = crlib.cr_scene()
+    sc.n_p = -1
+    assert cost_grad(sc) == crlib.CR_EINVAL
+    sc.n_o, sc.spheres, sc.n_p, sc.prims = 200, 256, 57, 256
+    assert cost_grad(sc) == crlib.CR_EINVAL and "n_p" in crlib.last_error()
+    sc.n_o, sc.n_p, sc.prims = 0, 4, None
+    assert cost_grad(sc) == crlib.CR_EINVAL and "prims" in crlib.last_error()
+    sc.prims = 260
+    assert cost_grad(sc) == crlib.CR_EINVAL
+    sc.prims = 256
+    w = crlib.cr_weights()
+    p = crlib.cr_prm_params()
+    p.N, p.k, p.n_check, p.attempts, p.seed = 64, 8, 4, 8, 1
+    m = crlib.cr_roadmap()
+    m.R = 1
+    for f in ("nodes", "node_ok", "nbr", "row", "col", "wt"):
+        setattr(m, f, 256)
+    assert L.cr_prm_build(C.byref(r), C.byref(sc), C.byref(w), C.byref(p), C.byref(m), dummy, 1 << 30,
+                          None) == crlib.CR_EINVAL
+    assert "sphere obstacles only" in crlib.last_error()
