@@ -56,7 +56,7 @@ def parse():
                     help="ragged workload: also time the batch's IK items and its path items (n <= 3, n >= 4) as "
                          "batches of their own")
     ap.add_argument("--workload", default="ik3",
-                    choices=["ik3", "ik1", "path", "traj", "prm", "calib", "ragged", "e1", "e2", "self"],
+                    choices=["ik3", "ik1", "path", "traj", "shelf", "prm", "calib", "ragged", "e1", "e2", "self"],
                     help="ik3: the headline two-stage IK; the others time the other workloads")
     return ap.parse_args()
 
@@ -504,6 +504,65 @@ def other_workload(args):
                 out["oracle_agreement"] = agreement(traj_success(s), cpu)
                 out["cpu_baseline"] = cpu
             out["forms"] = forms
+            return out
+
+        dtype = "f32"
+    elif args.workload == "shelf":
+        # trajectory planning among shelves (boxes) and capsules, each problem its own scene
+        spec, ik, P, Tn = synth.ROBOT_3SEG, synth.IK_GOAL, synth.P_TRAJ, synth.T_TRAJ
+        rbs = api.robot_struct(spec)
+
+        def clearance(cand, prims):
+            ug = torch.as_tensor(cand.T.copy(), dtype=torch.float64, device=dev)
+            tgt = torch.zeros((7, 1), dtype=torch.float64, device=dev)
+            tgt[3] = 1.0
+            task = api.task_struct(lib.CR_TASK_IK6, tgt, cand.shape[0], synth.WEIGHTS)
+            _, cl, _, _ = api.cost_grad(rbs, api.Scene(None, prims=prims, device=dev), task, ug, grad=False,
+                                        coll=True)
+            return cl.cpu().numpy()
+
+        us, ugoal, prims = synth.shelf_traj_workload(spec, P, clearance, seed=0)
+        Tg, _ = api.fk(rbs, torch.as_tensor(ugoal.T.copy(), dtype=torch.float64, device=dev))
+        goal = synth.pose_targets(Tg.cpu().numpy().T, "pose")
+        s = api.TrajSolver(spec, ik, synth.WEIGHTS, P, Tn, api.Scene(None, per_problem=True, prims=prims, device=dev),
+                           device=dev)
+        usd = torch.as_tensor(us.T.copy(), dtype=torch.float64, device=dev)
+        gd = torch.as_tensor(goal.T.copy(), dtype=torch.float64, device=dev)
+        fn = lambda: s.solve(usd, gd)
+        units, unit = P, "trajectories/s"
+        metric = (f"trajectory planning among shelves trajectories/s (32 states, 6 boxes + {synth.N_SHELF_CAPS} "
+                  "capsules per problem, 100 PG steps)")
+        wl = f"shelf_traj_3seg_256problems_32states_6boxes_{synth.N_SHELF_CAPS}capsules_pg100"
+
+        def traj_success(t):
+            return ((t.goal_pos <= 1e-3) & (t.goal_rot <= np.deg2rad(1.0)) & (t.col_ok > 0) &
+                    (t.lim_ok > 0)).cpu().numpy()
+
+        def extra():
+            out = {"goal_reached_rate": float((s.goal_pos <= 1e-3).float().mean()),
+                   "success_rate": float(traj_success(s).mean()),
+                   "collision_free_rate": float(s.col_ok.float().mean())}
+            if not args.no_baseline:
+                import oracle as O
+
+                O.build()
+                rb = O.make_robot(list(spec.L), spec.rc, spec.umax, thmax=spec.thmax, nb=spec.nb,
+                                  rbody=spec.body_radius)
+                W = O.make_weights(**synth.WEIGHTS.as_dict())
+
+                def run(lo, hi, threads):
+                    cfg = O.IkConfig(S=ik.S, n_final=ik.n_final, k_init=ik.k_init, k_final=ik.k_final,
+                                     lambda0=ik.lambda0, alpha0=ik.alpha0, dedup_eps=ik.dedup_eps,
+                                     lim_tol=ik.lim_tol, seed=ik.seed, p0=lo)
+                    r = O.solve_traj(rb, W, (None, prims[lo:hi]), us[lo:hi], goal[lo:hi], Tn, cfg, synth.K_TRAJ,
+                                     synth.ALPHA_TRAJ, threads=threads)
+                    return ((r["goal_pos"] <= 1e-3) & (r["goal_rot"] <= np.deg2rad(1.0)) & r["lim_ok"]
+                            & r["col_ok"])
+
+                cpu = oracle_sample(run, P, "trajectories/s", "problems of 32 states among a shelf and capsules",
+                                    budget_s=20.0)
+                out["oracle_agreement"] = agreement(traj_success(s), cpu)
+                out["cpu_baseline"] = cpu
             return out
 
         dtype = "f32"

@@ -551,6 +551,10 @@ template <typename T> struct ObsK {
   CR_HD ObsK(const Sphere4<T>* s_, const PrimK<T>* p_, int ns_) : s(s_), p(p_), ns(ns_) {}
   // the table from entry k on (its entry j is entry k + j of this one)
   CR_HD ObsK from(int k) const { return ObsK(s + k, p, ns - k); }
+  // whether primitives may follow the spheres: every primitive branch tests this first, so that in
+  // a kernel that builds its view from a bare sphere table (p a constant null pointer) the
+  // primitive code folds away
+  CR_HD bool prims() const { return p != nullptr; }
 };
 
 // Shared-memory bytes of a staged obstacle set: the Sphere4 table (no + np entries), then the
@@ -575,6 +579,41 @@ __device__ ObsK<T> stage_obstacles(const double* sp, int no, const double* pr, i
   stage_spheres(sp, no, rb, delta, tab, tid, nthr);
   if (np > 0) stage_prims(pr, np, rb, delta, tab + no, prm, tid, nthr);
   return ObsK<T>(tab, prm, no);
+}
+
+// Signed distance from x to primitive P's core (the quantity prim_active compares with a reach).
+template <typename T> CR_HD T prim_sd(const PrimK<T>& P, const T (&x)[3]) {
+  const T w0 = x[0] - P.c[0], w1 = x[1] - P.c[1], w2 = x[2] - P.c[2];
+  if (P.kind == CR_PRIM_BOX) {
+    T q[3], o2 = T(0), qm;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      q[a] = c_abs(P.R[a] * w0 + P.R[3 + a] * w1 + P.R[6 + a] * w2) - P.e[a];
+      if (q[a] > T(0)) o2 += q[a] * q[a];
+    }
+    qm = q[0] > q[1] ? q[0] : q[1];
+    qm = qm > q[2] ? qm : q[2];
+    return qm > T(0) ? c_sqrt(o2) : qm;
+  }
+  T d0 = w0, d1 = w1, d2 = w2;
+  if (P.kind == CR_PRIM_CAPSULE) {
+    T t = (w0 * P.e[0] + w1 * P.e[1] + w2 * P.e[2]) * P.iee;
+    t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+    d0 -= t * P.e[0];
+    d1 -= t * P.e[1];
+    d2 -= t * P.e[2];
+  }
+  return c_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+// stage_obstacles, or with PRIMS = false the spheres alone behind a bare view (no primitive code is
+// compiled into the kernel that uses it; the caller launches that form for scenes without primitives).
+template <bool PRIMS, typename T>
+__device__ ObsK<T> stage_obstacles_as(const double* sp, int no, const double* pr, int np, const RobotK<T>& rb, T delta,
+                                      unsigned char* base, int tid = -1, int nthr = 0) {
+  if (PRIMS) return stage_obstacles(sp, no, pr, np, rb, delta, base, tid, nthr);
+  stage_spheres(sp, no, rb, delta, reinterpret_cast<Sphere4<T>*>(base), tid, nthr);
+  return ObsK<T>(reinterpret_cast<const Sphere4<T>*>(base));
 }
 
 // Clearance of point x against primitive P within `reach` (P.reach for the rows): true when
@@ -642,9 +681,41 @@ CR_HD bool prim_active(const PrimK<T>& P, const T (&x)[3], T reach, T& viol, T (
 // whose centre is farther than L_i / 2 + reach from that point reaches none of them. The margin (a
 // 1e-4 fraction of the magnitudes involved) covers rounding, so a culled pair is one the exact
 // per-sample test rejects as well and the active set is unchanged.
+// The bits of the 64-entry chunk from table entry j0 on that are spheres (the rest are primitives).
+template <typename T> CR_HD uint64_t sphere_bits(const ObsK<T>& ob, int j0) {
+  const int cs = ob.ns - j0;
+  return cs >= 64 ? ~0ull : (cs <= 0 ? 0ull : (1ull << cs) - 1ull);
+}
+
+// Exact broad-phase test of the primitives among the candidates mask (bits relative to j0) that
+// passed their bounding spheres: sd is 1-Lipschitz, so no point of the ball of radius rad about m
+// comes within reach when sd(m) >= reach + rad (a shelf board, whose bounding sphere is large, then
+// culls like a slab of its own thickness); the margin is the bounding test's. Kept out of line: the
+// sphere-only scenes never call it, and the callers' unrolled loops stay short.
+template <typename T>
+__device__ __noinline__ uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T mz, T rad,
+                                                 T lsum) {
+  const T m[3] = {mx, my, mz};
+  for (uint64_t b = mask & ~sphere_bits(ob, j0); b; b &= b - 1) {
+    const int jj = __ffsll((long long)b) - 1;
+    const Sphere4<T> S = ob.s[j0 + jj];
+    const PrimK<T>& P = ob.p[j0 + jj - ob.ns];
+    const T marg = T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
+    if (!(prim_sd(P, m) < P.reach + rad + marg)) mask &= ~(1ull << jj);
+  }
+  return mask;
+}
+
+// Broad phase of the clearance rows. Spheres j0 .. j0 + cnt - 1 (cnt <= 64) that may come within reach
+// of some backbone sample of segment i are the set bits of mask[i]. The backbone has unit speed in arc
+// length, so every sample of segment i lies within L_i / 2 of the segment's mid-arc point; a sphere
+// whose centre is farther than L_i / 2 + reach from that point reaches none of them. The margin (a
+// 1e-4 fraction of the magnitudes involved) covers rounding, so a culled pair is one the exact
+// per-sample test rejects as well and the active set is unchanged.
 template <typename T, int N>
-CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, const Sphere4<T>* sph, int j0, int cnt,
+CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, ObsK<T> ob, int j0, int cnt,
                                 uint64_t (&mask)[N]) {
+  const Sphere4<T>* sph = ob.s;
   T lsum = T(0);
 #pragma unroll
   for (int i = 0; i < N; ++i) lsum += ch.L[i];
@@ -660,6 +731,7 @@ CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, cons
       const T lim = half + S.reach + T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
       if (dx * dx + dy * dy + dz * dz < lim * lim) mk |= 1ull << j;
     }
+    if (ob.prims() && (mk & ~sphere_bits(ob, j0))) mk = prim_exact_cull(ob, j0, mk, m[0], m[1], m[2], half, lsum);
     mask[i] = mk;
   }
 }
@@ -670,7 +742,8 @@ CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, cons
 constexpr int kCullGroup = 4;  // backbone samples per second-level ball
 template <typename T, int N>
 CR_HD uint64_t group_sphere_mask(const RobotK<T>& rb, const Chain<T, N>& ch, int i, int k0, int k1,
-                                 const Sphere4<T>* sph, int j0, uint64_t cand) {
+                                 ObsK<T> ob, int j0, uint64_t cand) {
+  const Sphere4<T>* sph = ob.s;
   T lsum = T(0);
 #pragma unroll
   for (int l = 0; l < N; ++l) lsum += ch.L[l];
@@ -686,14 +759,16 @@ CR_HD uint64_t group_sphere_mask(const RobotK<T>& rb, const Chain<T, N>& ch, int
     const T lim = rad + S.reach + T(1e-4) * (lsum + S.reach + c_abs(S.x) + c_abs(S.y) + c_abs(S.z));
     if (dx * dx + dy * dy + dz * dz < lim * lim) out |= 1ull << jj;
   }
+  if (ob.prims() && (out & ~sphere_bits(ob, j0))) out = prim_exact_cull(ob, j0, out, m[0], m[1], m[2], rad, lsum);
   return out;
 }
 
 // The same sets computed by a warp: lane l tests spheres j0 + l and j0 + l + 32 against every
 // segment and the ballots assemble the masks (identical in all lanes afterwards).
 template <typename T, int N>
-__device__ void warp_segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, const Sphere4<T>* sph, int j0,
+__device__ void warp_segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, ObsK<T> ob, int j0,
                                           int cnt, uint64_t (&mask)[N]) {
+  const Sphere4<T>* sph = ob.s;
   const int lane = threadIdx.x & 31;
   T lsum = T(0);
 #pragma unroll
@@ -716,6 +791,7 @@ __device__ void warp_segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>
       }
       mk |= (uint64_t)__ballot_sync(0xffffffffu, hit) << (32 * h);
     }
+    if (ob.prims() && (mk & ~sphere_bits(ob, j0))) mk = prim_exact_cull(ob, j0, mk, m[0], m[1], m[2], half, lsum);
     mask[i] = mk;
   }
 }
@@ -845,13 +921,13 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, ObsK<T> ob, int
     const T inb = T(1) / T(rb.nb);
     for (int j0 = 0; j0 < no; j0 += 64) {
     uint64_t mk[N];
-    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+    segment_sphere_masks(rb, ch, ob, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
       for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
       const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
-      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, ob, j0, mk[i]);
       if (!gm) continue;
       for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
@@ -859,23 +935,9 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, ObsK<T> ob, int
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], sg, q, wp, s, c);
         T gw[3] = {T(0), T(0), T(0)};
         bool hit = false;
-        for (uint64_t bits = gm; bits; bits &= bits - 1) {
-          const int jo = j0 + __ffsll((long long)bits) - 1;
-          if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
-            const PrimK<T>& P = ob.p[jo - ob.ns];
-            T viol, nv[3];
-            if (prim_active(P, wp, P.reach, viol, nv)) {
-              T rr = w.sc * viol;
-              coll += T(0.5) * rr * rr;
-              if (GRAD) {
-                T f = -w.rho_c * viol;
-                gw[0] += f * nv[0]; gw[1] += f * nv[1]; gw[2] += f * nv[2];
-                hit = true;
-              }
-            }
-            continue;
-          }
-          Sphere4<T> S = sph[jo];
+        const uint64_t sb = sphere_bits(ob, j0);
+        for (uint64_t bits = gm & sb; bits; bits &= bits - 1) {
+          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           T d2 = dx * dx + dy * dy + dz * dz;
           if (d2 < S.reach * S.reach) {
@@ -886,6 +948,19 @@ CR_HD T state_forward(const RobotK<T>& rb, const WeightsK<T>& w, ObsK<T> ob, int
             if (GRAD) {
               T f = -w.rho_c * viol / dist;
               gw[0] += f * dx; gw[1] += f * dy; gw[2] += f * dz;
+              hit = true;
+            }
+          }
+        }
+        for (uint64_t bits = ob.prims() ? gm & ~sb : 0ull; bits; bits &= bits - 1) {  // primitives: sd(x) rows
+          const PrimK<T>& P = ob.p[j0 + __ffsll((long long)bits) - 1 - ob.ns];
+          T viol, nv[3];
+          if (prim_active(P, wp, P.reach, viol, nv)) {
+            T rr = w.sc * viol;
+            coll += T(0.5) * rr * rr;
+            if (GRAD) {
+              T f = -w.rho_c * viol;
+              gw[0] += f * nv[0]; gw[1] += f * nv[1]; gw[2] += f * nv[2];
               hit = true;
             }
           }
@@ -1402,13 +1477,13 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
     const T inb = T(1) / T(rb.nb);
     for (int j0 = 0; j0 < no; j0 += 64) {
     uint64_t mk[N];
-    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+    segment_sphere_masks(rb, ch, ob, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
       for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
       const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
-      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, ob, j0, mk[i]);
       if (!gm) continue;
       for (int k = k0; k <= k1; ++k) {
         T sg = T(k) * inb;
@@ -1417,7 +1492,7 @@ CR_HD T eval_ik_normal(const RobotK<T>& rb, const WeightsK<T>& w, int kind, cons
         for (uint64_t bits = gm; bits; bits &= bits - 1) {
           const int jo = j0 + __ffsll((long long)bits) - 1;
           T viol, nh[3];
-          if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
+          if (ob.prims() && jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
             const PrimK<T>& P = ob.p[jo - ob.ns];
             if (!prim_active(P, wp, P.reach, viol, nh)) continue;
           } else {
@@ -1784,27 +1859,26 @@ CR_HD bool state_collides(const RobotK<T>& rb, ObsK<T> ob, int no, const T (&u)[
   const T inb = T(1) / T(rb.nb);
   for (int j0 = 0; j0 < no; j0 += 64) {
     uint64_t mk[N];
-    segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+    segment_sphere_masks(rb, ch, ob, j0, no - j0 < 64 ? no - j0 : 64, mk);
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
       for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {
       const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
-      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+      const uint64_t gm = group_sphere_mask<T, N>(rb, ch, i, k0, k1, ob, j0, mk[i]);
       if (!gm) continue;
       for (int k = k0; k <= k1; ++k) {
         T q[3], wp[3], s, c;
         backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], T(k) * inb, q, wp, s, c);
-        for (uint64_t bits = gm; bits; bits &= bits - 1) {
-          const int jo = j0 + __ffsll((long long)bits) - 1;
-          if (jo >= ob.ns) {
-            const PrimK<T>& P = ob.p[jo - ob.ns];
-            T viol, nv[3];
-            if (prim_active(P, wp, P.reach, viol, nv)) return true;
-            continue;
-          }
-          Sphere4<T> S = sph[jo];
+        const uint64_t sb = sphere_bits(ob, j0);
+        for (uint64_t bits = gm & sb; bits; bits &= bits - 1) {
+          Sphere4<T> S = sph[j0 + __ffsll((long long)bits) - 1];
           T dx = wp[0] - S.x, dy = wp[1] - S.y, dz = wp[2] - S.z;
           if (dx * dx + dy * dy + dz * dz < S.reach * S.reach) return true;
+        }
+        for (uint64_t bits = ob.prims() ? gm & ~sb : 0ull; bits; bits &= bits - 1) {
+          const PrimK<T>& P = ob.p[j0 + __ffsll((long long)bits) - 1 - ob.ns];
+          T viol, nv[3];
+          if (prim_active(P, wp, P.reach, viol, nv)) return true;
         }
       }
       }

@@ -70,9 +70,9 @@ __device__ void warm_sweep_warp(const RobotK<T>& rb, const WeightsK<T>& w, const
   }
 }
 
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, bool PRIMS = true>
 // 128 threads; the register cap is explicit (the default heuristic settles below what the exploration
-// step needs and spills).
+// step needs and spills). PRIMS = false: the form for scenes without primitives.
 __global__ void __maxnreg__(255) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,8 +84,9 @@ __global__ void __maxnreg__(255) k_path_warm(RobotK<T> rb, WeightsK<T> w, PathAr
   ObsK<T> sph(nullptr);
   if (OBST && live) {
     const int64_t q = a.sph_pp ? p : 0;
-    sph = stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
-                          a.np, rb, w.delta, mine, lane, 32);
+    sph = stage_obstacles_as<PRIMS>(a.spheres + q * a.no * 4, a.no,
+                                    a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr, a.np, rb, w.delta, mine,
+                                    lane, 32);
   }
   __syncwarp();
   if (!live) return;
@@ -300,7 +301,7 @@ __device__ bool joint_solve_twisted(const TA* Af, const double* g, double* z, do
 // One CTA per path, one thread per waypoint (blockDim = H rounded up to a warp). Per iteration:
 // every thread forms its waypoint's J^T J block and gradient (bulk precision) plus the smoothness
 // terms; warp 0 solves the block system in FP64; all threads evaluate the trial path.
-template <typename T, int N, bool OBST>
+template <typename T, int N, bool OBST, bool PRIMS = true>
 __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
                                                      WeightsK<double> wd, PathArgs<T> a) {
   constexpr int D = 3 * N, DD = D * (D + 1) / 2;
@@ -332,8 +333,8 @@ __global__ void __launch_bounds__(128) k_path_joint(RobotK<T> rb, WeightsK<T> w,
     const int64_t q = a.sph_pp ? p : 0;
     const double* sp = a.spheres + q * a.no * 4;
     const double* pr = a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr;
-    sph = stage_obstacles(sp, a.no, pr, a.np, rb, w.delta, smem_raw);
-    sphd = stage_obstacles(sp, a.no, pr, a.np, rbd, wd.delta, smem_raw + offd);
+    sph = stage_obstacles_as<PRIMS>(sp, a.no, pr, a.np, rb, w.delta, smem_raw);
+    sphd = stage_obstacles_as<PRIMS>(sp, a.no, pr, a.np, rbd, wd.delta, smem_raw + offd);
   }
   const bool wthr = tid < H;
   T u[D];
@@ -536,9 +537,12 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   // exploration sweep
   size_t smw = 4 * warm_warp_bytes<T>(a.no, a.np);
   unsigned gw = (unsigned)((a.P + 3) / 4);
-  if (a.no + a.np > 0) {
+  if (a.np > 0) {
     if ((st = set_smem(k_path_warm<T, N, true>, smw))) return st;
     k_path_warm<T, N, true><<<gw, 128, smw, l.stream>>>(rb, w, a);
+  } else if (a.no > 0) {  // spheres only: the form without primitive code
+    if ((st = set_smem(k_path_warm<T, N, true, false>, smw))) return st;
+    k_path_warm<T, N, true, false><<<gw, 128, smw, l.stream>>>(rb, w, a);
   } else {
     if ((st = set_smem(k_path_warm<T, N, false>, smw))) return st;
     k_path_warm<T, N, false><<<gw, 128, smw, l.stream>>>(rb, w, a);
@@ -547,9 +551,12 @@ template <typename T, int N> cr_status path_n(const PathLaunch& l) {
   // refinement
   const int threads = ((a.H + 31) / 32) * 32;
   size_t smj = path_joint_smem<T>(a.no, a.np, a.H, D);
-  if (a.no + a.np > 0) {
+  if (a.np > 0) {
     if ((st = set_smem(k_path_joint<T, N, true>, smj))) return st;
     k_path_joint<T, N, true><<<(unsigned)a.P, threads, smj, l.stream>>>(rb, w, rbd, wd, a);
+  } else if (a.no > 0) {
+    if ((st = set_smem(k_path_joint<T, N, true, false>, smj))) return st;
+    k_path_joint<T, N, true, false><<<(unsigned)a.P, threads, smj, l.stream>>>(rb, w, rbd, wd, a);
   } else {
     if ((st = set_smem(k_path_joint<T, N, false>, smj))) return st;
     k_path_joint<T, N, false><<<(unsigned)a.P, threads, smj, l.stream>>>(rb, w, rbd, wd, a);

@@ -116,7 +116,7 @@ __device__ int prm_class32(const RobotK<float>& rb, const PrmSph& s, int no, con
   bool unsure = false;
   for (int j0 = 0; j0 < no; j0 += 64) {
     uint64_t mk[N];
-    segment_sphere_masks(rb, ch, s.hi, j0, no - j0 < 64 ? no - j0 : 64, mk);
+    segment_sphere_masks(rb, ch, ObsK<float>(s.hi), j0, no - j0 < 64 ? no - j0 : 64, mk);
     for (int i = 0; i < N; ++i) {
       if (!mk[i]) continue;
       for (int k0 = 1; k0 <= rb.nb; k0 += kCullGroup) {

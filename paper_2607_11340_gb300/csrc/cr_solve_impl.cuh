@@ -234,12 +234,13 @@ template <typename T> struct StageOut {
   T* u;
 };
 
-// Stage the obstacle set of problem p (set 0 of a shared scene) at base, in precision T.
-template <typename T, typename A>
+// Stage the obstacle set of problem p (set 0 of a shared scene) at base, in precision T (PRIMS:
+// stage_obstacles_as).
+template <bool PRIMS = true, typename T, typename A>
 __device__ ObsK<T> stage_problem_obstacles(const A& a, int64_t p, const RobotK<T>& rb, T delta, unsigned char* base) {
   const int64_t q = a.sph_pp ? p : 0;
-  return stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
-                         a.np, rb, delta, base);
+  return stage_obstacles_as<PRIMS>(a.spheres + q * a.no * 4, a.no,
+                                   a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr, a.np, rb, delta, base);
 }
 
 // Bytes of one staged obstacle set in FP64 and in T, side by side (the refine kernels').
@@ -247,7 +248,7 @@ template <typename T> __host__ __device__ inline size_t refine_set_bytes(int no,
   return ((obstacles_smem<double>(no, np) + 15) & ~(size_t)15) + ((obstacles_smem<T>(no, np) + 15) & ~(size_t)15);
 }
 
-template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON, bool PRIMS = true>
 __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, IkArgs<T> a, StageOut<T> so) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) k_ik_stage1(RobotK<T> rb, WeightsK<T> w, 
   const int nob = a.no + a.np;
   ObsK<T> sph(nullptr);
   if (OBST) {
-    sph = stage_problem_obstacles(a, p, rb, w.delta, smem_raw);
+    sph = stage_problem_obstacles<PRIMS>(a, p, rb, w.delta, smem_raw);
     __syncthreads();
   }
   const int s = threadIdx.x;
@@ -373,19 +374,19 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
     const double inb = 1.0 / rb.nb;
     for (int j0 = 0; j0 < no && free; j0 += 64) {
       uint64_t mk[N];
-      segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+      segment_sphere_masks(rb, ch, ob, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
       for (int i = 0; i < N; ++i) {
         if (!mk[i] || !free) continue;
         for (int k0 = 1; k0 <= rb.nb && free; k0 += kCullGroup) {
           const int k1 = k0 + kCullGroup - 1 < rb.nb ? k0 + kCullGroup - 1 : rb.nb;
-          const uint64_t gm = group_sphere_mask<double, N>(rb, ch, i, k0, k1, sph, j0, mk[i]);
+          const uint64_t gm = group_sphere_mask<double, N>(rb, ch, i, k0, k1, ob, j0, mk[i]);
           for (int k = k0; k <= k1 && gm && free; ++k) {
             double q[3], wp[3], s, c;
             backbone_point(ch.Rb[i], ch.pb[i], ch.ax[i], ch.ay[i], ch.x[i], ch.L[i], k * inb, q, wp, s, c);
             for (uint64_t bits = gm; bits; bits &= bits - 1) {
               const int j = j0 + __ffsll((long long)bits) - 1;
-              if (j >= ob.ns) {
+              if (ob.prims() && j >= ob.ns) {
                 const PrimK<double>& P = ob.p[j - ob.ns];
                 double viol, nv[3];
                 if (prim_active(P, wp, P.reach - w.delta, viol, nv)) { free = false; break; }
@@ -434,7 +435,7 @@ CR_HD double accept_fp64(const RobotK<double>& rb, const WeightsK<double>& w, in
   return F;
 }
 
-template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON>
+template <typename T, int N, bool OBST, int MODEL = CR_MODEL_TENDON, bool PRIMS = true>
 __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, RobotK<double> rbd,
                                                     WeightsK<double> wd, IkArgs<T> a) {
   constexpr int D = 3 * N;
@@ -455,8 +456,8 @@ __global__ void __launch_bounds__(128) k_ik_refine(RobotK<T> rb, WeightsK<T> w, 
     const int ntb = a.sph_pp ? (int)(a.P - t0 < a.tpb ? a.P - t0 : a.tpb) : 1;
     for (int t = 0; t < ntb; ++t) {
       unsigned char* base = smem_raw + (size_t)t * setb;
-      const ObsK<double> od = stage_problem_obstacles(a, t0 + t, rbd, wd.delta, base);
-      const ObsK<T> ot = stage_problem_obstacles(a, t0 + t, rb, w.delta, base + offt);
+      const ObsK<double> od = stage_problem_obstacles<PRIMS>(a, t0 + t, rbd, wd.delta, base);
+      const ObsK<T> ot = stage_problem_obstacles<PRIMS>(a, t0 + t, rb, w.delta, base + offt);
       if (t == jt) {
         sphd = od;
         sph = ot;
@@ -834,8 +835,19 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
     unsigned char* ws = (unsigned char*)a.ws;
     StageOut<T> so{(float*)(ws + a.lay.stage_F), (float*)(ws + a.lay.stage_C), (T*)(ws + a.lay.stage_u)};
     if (coll_rows) {
-      if ((st = set_smem(k_ik_stage1<T, N, true, MODEL>, sm1))) return st;
-      k_ik_stage1<T, N, true, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k, so);
+      // tendon-model scenes without primitives take the form compiled without primitive code
+      bool done = false;
+      if constexpr (MODEL == CR_MODEL_TENDON) {
+        if (np == 0) {
+          if ((st = set_smem(k_ik_stage1<T, N, true, MODEL, false>, sm1))) return st;
+          k_ik_stage1<T, N, true, MODEL, false><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k, so);
+          done = true;
+        }
+      }
+      if (!done) {
+        if ((st = set_smem(k_ik_stage1<T, N, true, MODEL>, sm1))) return st;
+        k_ik_stage1<T, N, true, MODEL><<<(unsigned)P, threads, sm1, a.stream>>>(rb, w, k, so);
+      }
     } else {
       k_ik_stage1<T, N, false, MODEL><<<(unsigned)P, threads, 0, a.stream>>>(rb, w, k, so);
     }
@@ -880,8 +892,18 @@ template <typename T, int N, int MODEL = CR_MODEL_TENDON> cr_status solve_ik_n(c
   }
   if (warp_refine) {
   } else if (coll_rows) {
-    if ((st = set_smem(k_ik_refine<T, N, true, MODEL>, sm2))) return st;
-    k_ik_refine<T, N, true, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+    bool done = false;
+    if constexpr (MODEL == CR_MODEL_TENDON) {
+      if (np == 0) {
+        if ((st = set_smem(k_ik_refine<T, N, true, MODEL, false>, sm2))) return st;
+        k_ik_refine<T, N, true, MODEL, false><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+        done = true;
+      }
+    }
+    if (!done) {
+      if ((st = set_smem(k_ik_refine<T, N, true, MODEL>, sm2))) return st;
+      k_ik_refine<T, N, true, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
+    }
   }
   else k_ik_refine<T, N, false, MODEL><<<g2, b2, sm2, a.stream>>>(rb, w, rbd, wd, k);
   if ((st = crh::check_launch("cr_solve_ik refine"))) return st;

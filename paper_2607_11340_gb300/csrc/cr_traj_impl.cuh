@@ -229,12 +229,13 @@ template <typename T> struct TrajArgs {
   unsigned char* col_ok;
 };
 
-// Stage problem p's obstacle set (the shared one without per-problem scenes) at base.
-template <typename T, typename A>
+// Stage problem p's obstacle set (the shared one without per-problem scenes) at base (PRIMS:
+// stage_obstacles_as).
+template <bool PRIMS = true, typename T, typename A>
 __device__ ObsK<T> stage_traj_obstacles(const A& a, int64_t p, const RobotK<T>& rb, T delta, unsigned char* base) {
   const int64_t q = a.sph_pp ? p : 0;
-  return stage_obstacles(a.spheres + q * a.no * 4, a.no, a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr,
-                         a.np, rb, delta, base);
+  return stage_obstacles_as<PRIMS>(a.spheres + q * a.no * 4, a.no,
+                                   a.np > 0 ? a.prims + q * a.np * CR_PRIM_DOUBLES : nullptr, a.np, rb, delta, base);
 }
 
 template <typename T, int N, bool OBST, bool GRAD>
@@ -273,8 +274,8 @@ __global__ void __launch_bounds__(256) k_traj_cost(RobotK<T> rb, WeightsK<T> w, 
 
 // Trajectory planning after the goal IK: linear initialisation (or the given initial states x_init), k_traj
 // projected-gradient steps of all free states, FP64 metrics of the result.
-template <typename T, int N, bool OBST>
-__global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, RobotK<double> rbd,
+template <typename T, int N, bool OBST, bool PRIMS = true>
+__global__ void __launch_bounds__(256, 1) k_traj_solve(RobotK<T> rb, WeightsK<T> w, TrajW<T> tw, RobotK<double> rbd,
                                                      WeightsK<double> wd, TrajArgs<T> a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -292,8 +293,8 @@ __global__ void __launch_bounds__(256) k_traj_solve(RobotK<T> rb, WeightsK<T> w,
   ObsK<T> sph(nullptr);
   ObsK<double> sphd(nullptr);
   if (OBST) {
-    sph = stage_traj_obstacles(a, p, rb, w.delta, smem_raw);
-    sphd = stage_traj_obstacles(a, p, rbd, wd.delta, smem_raw + offd);
+    sph = stage_traj_obstacles<PRIMS>(a, p, rb, w.delta, smem_raw);
+    sphd = stage_traj_obstacles<PRIMS>(a, p, rbd, wd.delta, smem_raw + offd);
     __syncthreads();
   }
   const bool active = t < Tn;
@@ -796,9 +797,12 @@ template <typename T, int N> cr_status traj_solve_n(const TrajLaunch& l) {
               ((obstacles_smem<double>(a.no, a.np) + 15) & ~size_t(15)) +
               ((TrajSmem<T>::bytes(a.Tn, D) + 15) & ~size_t(15)) + ((size_t)a.Tn * D + 32) * sizeof(double);
   cr_status st;
-  if (a.no + a.np > 0 || w.rho_s > T(0)) {  // collision rows: obstacles and / or self-contact
+  if (a.np > 0) {
     if ((st = set_smem(k_traj_solve<T, N, true>, sm))) return st;
     k_traj_solve<T, N, true><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
+  } else if (a.no > 0 || w.rho_s > T(0)) {  // spheres and / or self-contact: the form without primitive code
+    if ((st = set_smem(k_traj_solve<T, N, true, false>, sm))) return st;
+    k_traj_solve<T, N, true, false><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);
   } else {
     if ((st = set_smem(k_traj_solve<T, N, false>, sm))) return st;
     k_traj_solve<T, N, false><<<(unsigned)a.P, threads, sm, l.stream>>>(rb, w, tw, rbd, wd, a);

@@ -222,7 +222,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
     const T inb = c_div(T(1), T(rb.nb));
     for (int j0 = 0; j0 < no; j0 += 64) {
       uint64_t mk[N];
-      warp_segment_sphere_masks(rb, ch, sph, j0, no - j0 < 64 ? no - j0 : 64, mk);
+      warp_segment_sphere_masks(rb, ch, ob, j0, no - j0 < 64 ? no - j0 : 64, mk);
 #pragma unroll
       for (int ii = 0; ii < N; ++ii) {
         if (!mk[ii]) continue;
@@ -232,7 +232,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
           // second level: this lane's group of kCullGroup samples, then the union over the warp
           const int kg0 = (k - 1) / kCullGroup * kCullGroup + 1;
           const int kg1 = kg0 + kCullGroup - 1 < rb.nb ? kg0 + kCullGroup - 1 : rb.nb;
-          const uint64_t gml = mine ? group_sphere_mask<T, N>(rb, ch, ii, kg0, kg1, sph, j0, mk[ii]) : 0ull;
+          const uint64_t gml = mine ? group_sphere_mask<T, N>(rb, ch, ii, kg0, kg1, ob, j0, mk[ii]) : 0ull;
           const uint64_t um = (uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)gml) |
                               ((uint64_t)__reduce_or_sync(0xffffffffu, (unsigned)(gml >> 32)) << 32);
           if (!um) continue;
@@ -243,7 +243,7 @@ __device__ T warp_eval(const RobotK<T>& rb, const WeightsK<T>& w, const TargetK<
             const int jo = j0 + __ffsll((long long)bits) - 1;
             bool act;
             T viol = T(0), nvx = T(0), nvy = T(0), nvz = T(0);
-            if (jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
+            if (ob.prims() && jo >= ob.ns) {  // a primitive: the same row with sd(x) for the centre distance
               const PrimK<T>& P = ob.p[jo - ob.ns];
               T nv[3];
               act = mine && prim_active(P, wpt, P.reach, viol, nv);
