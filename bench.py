@@ -758,7 +758,8 @@ def other_workload(args):
 
         def subset(nsub=256):
             """The plain per-problem form against the batch on the first nsub items, same order."""
-            sub = api.BatchSolver(fam, items[:nsub], synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=spu, device=dev)
+            sub = api.BatchSolver(fam, items[:nsub], synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=spu, device=dev,
+                                   seed_regs=s.seed_regs)
             sub.set_inputs(targets[: int(items[:nsub, 2].sum())], spheres[: int(items[:nsub, 4].sum())])
             sub.plan()
             sub.run()
@@ -812,7 +813,8 @@ def other_workload(args):
             t_ns = s.t_done.cpu().numpy()
             fl = s.flags.cpu().numpy()
             out = {"waypoint_solves_per_s": W / (line["ms_per_step"] / 1e3), "latency": lat(t_ns),
-                   "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu, "work_units": n_units,
+                   "success_rate": float((fl & 1).mean()), "seeds_per_unit": spu,
+                   "seed_phase_registers": {1: "wide", 2: "tight"}.get(s.seed_regs), "work_units": n_units,
                    "worker_warps": workers, "items_ik": int((items[:, 0] == 0).sum()),
                    "items_path": int((items[:, 0] == 1).sum()), "waypoints": W,
                    "vs_plain_subset": None if args.no_baseline else subset()}
@@ -829,7 +831,7 @@ def other_workload(args):
                                   ("path_items_n_ge_4", (items[:, 0] == 1) & (items[:, 1] >= 4))):
                     idx = np.nonzero(sel)[0]
                     sub = api.BatchSolver(fam, items[idx], synth.IK_RAGGED, synth.WEIGHTS, seeds_per_unit=spu,
-                                          device=dev)
+                                          device=dev, seed_regs=s.seed_regs)
                     sub.set_inputs(np.concatenate([targets[w0[i]:w0[i + 1]] for i in idx]),
                                    np.concatenate([spheres[o0[i]:o0[i + 1]] for i in idx] + [np.zeros((0, 4))]))
                     sub.plan()

@@ -600,12 +600,16 @@ typedef struct {
   int32_t k_warm, k_joint;
   int32_t seeds_per_unit; /* seeds one warp takes per work unit: 32, 64, 128 or 256; 0: chosen by
                              timing the candidates in cr_batch_plan_create */
-  int32_t reserved;
+  int32_t seed_regs;      /* register budget of the seeds phase: 1 wide (168 registers per thread
+                             for n <= 4, 255 above), 2 tight (128, 168: more resident warps, with
+                             spills where a state does not fit); 0: chosen by timing together with
+                             seeds_per_unit in cr_batch_plan_create (wide in cr_solve_batch) */
 } cr_batch_params;
 
 typedef struct cr_batch_plan cr_batch_plan;
 
-/* Workspace bytes for the batch (also covers every seeds_per_unit candidate); 0 on bad input. */
+/* Workspace bytes for the batch (also covers every seeds_per_unit and seed_regs candidate); 0 on bad
+ * input. */
 CR_API size_t cr_batch_workspace_size(const cr_robot* family, const cr_batch_item* items, int64_t N,
                                       const cr_batch_params* prm);
 
@@ -614,11 +618,11 @@ CR_API size_t cr_batch_workspace_size(const cr_robot* family, const cr_batch_ite
  * CUDA graph (start node; per segment count present one branch of four persistent phase kernels in
  * order: seeds and projected gradient, SelectTop + refinement + argmin, exploration sweep, joint LM;
  * the branches in parallel)
- * and returns the plan (host object). With seeds_per_unit = 0 every candidate is run and timed on
- * `stream` (the outputs then hold a valid result). Synchronises `stream`. All pointers stay bound
+ * and returns the plan (host object). With seeds_per_unit = 0 or seed_regs = 0 every open
+ * combination of the two is run and timed on `stream` (the outputs then hold a valid result). Synchronises `stream`. All pointers stay bound
  * to the plan: cr_batch_plan_run re-solves the batch from the current contents of targets and
  * spheres. CR_EINVAL for a bad item (kind, n, H, S, n_o out of range, IK with H != 1), NULL or
- * misaligned pointers, or a short workspace. */
+ * misaligned pointers, or a short workspace; CR_EINVAL for seed_regs outside 0..2. */
 CR_API cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* w, const cr_batch_item* items,
                                       int64_t N, const cr_batch_params* prm, const double* targets,
                                       const double* spheres, double* u_out, double* cost_out, double* pos_err,
@@ -626,10 +630,10 @@ CR_API cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* 
                                       size_t ws_bytes, cr_stream stream, cr_batch_plan** plan);
 /* One graph launch on `stream` (asynchronous). Two runs of one plan must not overlap. */
 CR_API cr_status cr_batch_plan_run(cr_batch_plan* plan, cr_stream stream);
-/* The plan's seeds per unit, number of work units and resident worker warps (host pointers, each
- * may be NULL). */
+/* The plan's seeds per unit, number of work units, resident worker warps of the seeds phase and
+ * register budget of that phase (1 wide, 2 tight) (host pointers, each may be NULL). */
 CR_API cr_status cr_batch_plan_info(const cr_batch_plan* plan, int32_t* seeds_per_unit, int64_t* units,
-                                    int64_t* workers);
+                                    int64_t* workers, int32_t* seed_regs);
 /* Frees the plan (graph, streams, events); the caller makes sure no run is in flight. */
 CR_API cr_status cr_batch_plan_destroy(cr_batch_plan* plan);
 /* Plan, run, synchronise and free in one call (seeds_per_unit 0 takes 64, without timing). */

@@ -504,14 +504,15 @@ class BatchSolver:
 
     def __init__(self, family: synth.RobotSpec, items, ik: synth.IkSpec, weights: synth.WeightSpec,
                  k_warm: int = synth.K_WARM, k_joint: int = synth.K_JOINT, seeds_per_unit: int = 0,
-                 device="cuda", p0: int = 0):
+                 device="cuda", p0: int = 0, seed_regs: int = 0):
         import numpy as np
 
         self.family = robot_struct(family)
         self.weights = weights_struct(weights)
         self.items_np = np.asarray(items, dtype=np.int64).reshape(-1, 5)
         self.items = lib._batch_items(self.items_np)
-        self.prm = self.params(ik, k_warm, k_joint, seeds_per_unit)
+        self.prm = self.params(ik, k_warm, k_joint, seeds_per_unit, seed_regs)
+        self.seed_regs = 0  # the plan's register budget of the seeds phase (1 wide, 2 tight) once planned
         self.prm.ik.p0 = p0  # item i draws its seeds as problem p0 + i (a process's share of a larger batch)
         it = self.items_np
         self.N = len(it)
@@ -530,10 +531,11 @@ class BatchSolver:
 
     @staticmethod
     def params(ik: synth.IkSpec, k_warm: int = synth.K_WARM, k_joint: int = synth.K_JOINT,
-               seeds_per_unit: int = 0) -> lib.cr_batch_params:
+               seeds_per_unit: int = 0, seed_regs: int = 0) -> lib.cr_batch_params:
         prm = lib.cr_batch_params()
         prm.ik = ik_params_struct(ik, lib.CR_F32)
         prm.k_warm, prm.k_joint, prm.seeds_per_unit = k_warm, k_joint, seeds_per_unit
+        prm.seed_regs = seed_regs
         return prm
 
     def set_inputs(self, targets, spheres):
@@ -548,7 +550,8 @@ class BatchSolver:
         self._plan = lib.cr_batch_plan_create(self.family, self.weights, self.items, self.prm, self.targets,
                                               self.spheres, self.u, self.cost, self.pos, self.rot, self.flags,
                                               self.t_done, self.workspace)
-        return lib.cr_batch_plan_info(self._plan)
+        spu, units, workers, self.seed_regs = lib.cr_batch_plan_info(self._plan)
+        return spu, units, workers
 
     def run(self):
         if self._plan is None:

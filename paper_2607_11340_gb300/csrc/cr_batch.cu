@@ -50,6 +50,7 @@ using namespace crh;
 struct cr_batch_plan {
   int device;
   int32_t spu;
+  int32_t seed_regs;  // 1: the seeds phase's wide register budget, 2: the tight one
   int64_t units, workers;
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -61,15 +62,16 @@ constexpr int kSpuCandidates[] = {32, 64, 128, 256};
 
 size_t batch_smem(int) { return (size_t)crk::kBatchWarps * crk::kBatchWarpSmem; }
 
-int blocks_per_sm(int n, int phase) {
+// rb: register budget of the seeds phase (0 wide, 1 tight)
+int blocks_per_sm(int n, int phase, int rb) {
   const size_t sm = batch_smem(n);
   switch (n) {
-    case 1: return crk::batch_blocks_per_sm<1>(sm, phase);
-    case 2: return crk::batch_blocks_per_sm<2>(sm, phase);
-    case 3: return crk::batch_blocks_per_sm<3>(sm, phase);
-    case 4: return crk::batch_blocks_per_sm<4>(sm, phase);
-    case 5: return crk::batch_blocks_per_sm<5>(sm, phase);
-    default: return crk::batch_blocks_per_sm<6>(sm, phase);
+    case 1: return crk::batch_blocks_per_sm<1>(sm, phase, rb);
+    case 2: return crk::batch_blocks_per_sm<2>(sm, phase, rb);
+    case 3: return crk::batch_blocks_per_sm<3>(sm, phase, rb);
+    case 4: return crk::batch_blocks_per_sm<4>(sm, phase, rb);
+    case 5: return crk::batch_blocks_per_sm<5>(sm, phase, rb);
+    default: return crk::batch_blocks_per_sm<6>(sm, phase, rb);
   }
 }
 
@@ -86,15 +88,15 @@ cr_status prepare(int n) {
 }
 
 cr_status launch(int n, const cr_robot& fam, const cr_weights& w, const crk::BatchArgs& a, const crk::BatchGrids& g,
-                 cudaStream_t s) {
+                 int rb, cudaStream_t s) {
   const size_t sm = batch_smem(n);
   switch (n) {
-    case 1: return crk::batch_launch<1>(fam, w, a, g, sm, s);
-    case 2: return crk::batch_launch<2>(fam, w, a, g, sm, s);
-    case 3: return crk::batch_launch<3>(fam, w, a, g, sm, s);
-    case 4: return crk::batch_launch<4>(fam, w, a, g, sm, s);
-    case 5: return crk::batch_launch<5>(fam, w, a, g, sm, s);
-    default: return crk::batch_launch<6>(fam, w, a, g, sm, s);
+    case 1: return crk::batch_launch<1>(fam, w, a, g, sm, rb, s);
+    case 2: return crk::batch_launch<2>(fam, w, a, g, sm, rb, s);
+    case 3: return crk::batch_launch<3>(fam, w, a, g, sm, rb, s);
+    case 4: return crk::batch_launch<4>(fam, w, a, g, sm, rb, s);
+    case 5: return crk::batch_launch<5>(fam, w, a, g, sm, rb, s);
+    default: return crk::batch_launch<6>(fam, w, a, g, sm, rb, s);
   }
 }
 
@@ -124,6 +126,7 @@ cr_status check_items(const cr_robot* family, const cr_batch_item* items, int64_
   const int spu = prm->seeds_per_unit;
   if (spu != 0 && spu != 32 && spu != 64 && spu != 128 && spu != 256)
     return fail(CR_EINVAL, "batch: seeds_per_unit %d not in {0, 32, 64, 128, 256}", spu);
+  if (prm->seed_regs < 0 || prm->seed_regs > 2) return fail(CR_EINVAL, "batch: seed_regs %d not in {0, 1, 2}", prm->seed_regs);
   return CR_OK;
 }
 
@@ -140,6 +143,7 @@ struct Layout {
   size_t off_items, off_units, off_heads, off_t0, off_cand, off_x, off_scr[CR_MAX_SEG + 1], total;
   int64_t W, n_sph, n_states, n_cand, n_x;
   int64_t workers;
+  int rb;  // register budget of the seeds phase: 0 wide, 1 tight
 };
 constexpr int kHeads = 4 * CR_MAX_SEG;
 
@@ -152,7 +156,7 @@ double est_cost(const cr_batch_item& it, const cr_batch_params& p) {
 }
 
 cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_params& p, int spu, int n_sm,
-                      Layout& L) {
+                      Layout& L, int rb = 0) {
   L.items.clear();
   L.units.clear();
   L.W = L.n_sph = L.n_states = L.n_cand = L.n_x = 0;
@@ -209,7 +213,7 @@ cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_para
     for (int64_t i : idx) npath += (items[i].kind == CR_ITEM_PATH && items[i].H > 1) ? 1 : 0;
     const int64_t work[4] = {nu, ni, npath, npath};
     for (int ph = 0; ph < 4; ++ph) {
-      const int bps = std::max(1, blocks_per_sm(n, ph));
+      const int bps = std::max(1, blocks_per_sm(n, ph, rb));
       const int64_t want = (work[ph] + crk::kBatchWarps - 1) / crk::kBatchWarps;
       L.grid[n - 1].g[ph] = work[ph] == 0 ? 0 : (int)std::min<int64_t>(want, (int64_t)bps * n_sm);
     }
@@ -229,6 +233,7 @@ cr_status make_layout(const cr_batch_item* items, int64_t N, const cr_batch_para
     off = align256(off + (size_t)L.grid[n - 1].g[3] * crk::kBatchWarps * L.stride[n - 1]);
   }
   L.total = off;
+  L.rb = rb;
   return CR_OK;
 }
 
@@ -366,7 +371,7 @@ cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, 
       const int n = order[oi];
       if (L.grid[n - 1].g[0] == 0) continue;
       cudaStreamWaitEvent(side[used], fork, 0);
-      st = launch(n, *b.family, *b.w, batch_args(L, n, b, p, spu), L.grid[n - 1], side[used]);
+      st = launch(n, *b.family, *b.w, batch_args(L, n, b, p, spu), L.grid[n - 1], L.rb, side[used]);
       cudaEventRecord(join[used], side[used]);
       cudaStreamWaitEvent(cap, join[used], 0);
       ++used;
@@ -389,6 +394,7 @@ cr_status build_plan(const Layout& L, const Bound& b, const cr_batch_params& p, 
   plan->graph = graph;
   plan->exec = exec;
   plan->spu = spu;
+  plan->seed_regs = L.rb + 1;
   plan->units = (int64_t)L.units.size();
   plan->workers = L.workers;
   return CR_OK;
@@ -450,25 +456,32 @@ cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* w, cons
           static_cast<unsigned char*>(workspace)};
   cudaStream_t user = stream_of(stream);
   Layout L;
-  if (prm->seeds_per_unit != 0) {
-    make_layout(items, N, *prm, prm->seeds_per_unit, n_sm, L);
-    if ((st = build_plan(L, b, *prm, prm->seeds_per_unit, N, user, plan))) {
+  // the candidates: seeds per unit x register budget of the seeds phase, each fixed by prm or open
+  int spus[4], nspu = 0, rbs[2], nrb = 0;
+  if (prm->seeds_per_unit != 0) spus[nspu++] = prm->seeds_per_unit;
+  else for (int spu : kSpuCandidates) spus[nspu++] = spu;
+  if (prm->seed_regs != 0) rbs[nrb++] = prm->seed_regs - 1;
+  else { rbs[nrb++] = 0; rbs[nrb++] = 1; }
+  if (nspu * nrb == 1) {
+    make_layout(items, N, *prm, spus[0], n_sm, L, rbs[0]);
+    if ((st = build_plan(L, b, *prm, spus[0], N, user, plan))) {
       cr_batch_plan_destroy(plan);
       return st;
     }
     *plan_out = plan;
     return CR_OK;
   }
-  // seeds per unit by timing: each candidate is captured, run once to warm up, then timed
+  // by timing: each candidate is captured, run once to warm up, then timed
   float best_ms = 0.f;
-  int best = 0;
+  int best = 0, best_rb = 0;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cr_batch_plan_destroy(plan);
     return fail(CR_ECUDA, "cr_batch_plan_create: event creation failed");
   }
-  for (int spu : kSpuCandidates) {
-    make_layout(items, N, *prm, spu, n_sm, L);
+  for (int c = 0; c < nspu * nrb && st == CR_OK; ++c) {
+    const int spu = spus[c / nrb], rb = rbs[c % nrb];
+    make_layout(items, N, *prm, spu, n_sm, L, rb);
     if ((st = build_plan(L, b, *prm, spu, N, user, plan))) break;
     cudaGraphLaunch(plan->exec, user);
     cudaEventRecord(e0, user);
@@ -484,12 +497,13 @@ cr_status cr_batch_plan_create(const cr_robot* family, const cr_weights* w, cons
     if (best == 0 || ms < best_ms) {
       best_ms = ms;
       best = spu;
+      best_rb = rb;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st == CR_OK) {
-    make_layout(items, N, *prm, best, n_sm, L);
+    make_layout(items, N, *prm, best, n_sm, L, best_rb);
     st = build_plan(L, b, *prm, best, N, user, plan);
   }
   if (st != CR_OK) {
@@ -507,11 +521,13 @@ cr_status cr_batch_plan_run(cr_batch_plan* plan, cr_stream stream) {
   return CR_OK;
 }
 
-cr_status cr_batch_plan_info(const cr_batch_plan* plan, int32_t* seeds_per_unit, int64_t* units, int64_t* workers) {
+cr_status cr_batch_plan_info(const cr_batch_plan* plan, int32_t* seeds_per_unit, int64_t* units, int64_t* workers,
+                             int32_t* seed_regs) {
   if (!plan) return fail(CR_EINVAL, "cr_batch_plan_info: NULL plan");
   if (seeds_per_unit) *seeds_per_unit = plan->spu;
   if (units) *units = plan->units;
   if (workers) *workers = plan->workers;
+  if (seed_regs) *seed_regs = plan->seed_regs;
   return CR_OK;
 }
 
@@ -532,6 +548,7 @@ cr_status cr_solve_batch(const cr_robot* family, const cr_weights* w, const cr_b
   if (N == 0) return check_items(family, items, N, prm);
   cr_batch_params p = *prm;
   if (p.seeds_per_unit == 0) p.seeds_per_unit = 64;
+  if (p.seed_regs == 0) p.seed_regs = 1;
   cr_batch_plan* plan = nullptr;
   cr_status st = cr_batch_plan_create(family, w, items, N, &p, targets, spheres, u_out, cost_out, pos_err, rot_err,
                                       flags_out, t_done_ns, workspace, ws_bytes, stream, &plan);

@@ -270,9 +270,13 @@ __device__ inline int batch_pop(int32_t* head, int n) {
 
 __device__ inline bool batch_is_path(const BatchItemK& it) { return it.kind == CR_ITEM_PATH && it.H > 1; }
 
+// Register budgets of the seeds phase, picked by the planner's timing: RB = 0 the wide cap, RB = 1 a
+// tight one (more resident warps per SM, at the price of spills where the state does not fit).
+constexpr int batch_seeds_regs(int n, int rb) { return rb == 0 ? (n <= 4 ? 168 : 255) : (n <= 4 ? 128 : 168); }
+
 // Phase 1: stage one of the work units (seed groups), lanes over seeds.
-template <int N>
-__global__ void __maxnreg__(N <= 4 ? 168 : 255) k_batch_seeds(RobotK<float> rb, WeightsK<float> w, BatchArgs a) {
+template <int N, int RB = 0>
+__global__ void __maxnreg__(batch_seeds_regs(N, RB)) k_batch_seeds(RobotK<float> rb, WeightsK<float> w, BatchArgs a) {
   constexpr int D = 3 * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BatchSmem b = batch_smem_of(smem_raw);
@@ -491,7 +495,9 @@ struct BatchGrids {
   int g[4];
 };
 template <int N> cr_status batch_prepare(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_seeds<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_seeds<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_seeds<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_batch_refine<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
@@ -501,11 +507,14 @@ template <int N> cr_status batch_prepare(size_t smem) {
   if (e != cudaSuccess) return crh::fail(CR_ECUDA, "k_batch phases <%d>: %s", N, cudaGetErrorString(e));
   return CR_OK;
 }
-template <int N> int batch_blocks_per_sm(size_t smem, int phase) {
+template <int N> int batch_blocks_per_sm(size_t smem, int phase, int rb) {
   int nb = 0;
   cudaError_t e;
   switch (phase) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_seeds<N>, 32 * kBatchWarps, smem); break;
+    case 0:
+      e = rb == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_seeds<N, 0>, 32 * kBatchWarps, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_seeds<N, 1>, 32 * kBatchWarps, smem);
+      break;
     case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_refine<N>, 32 * kBatchWarps, smem); break;
     case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_warm<N>, 32 * kBatchWarps, smem); break;
     default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_joint<N>, 32 * kBatchWarps, smem);
@@ -513,7 +522,7 @@ template <int N> int batch_blocks_per_sm(size_t smem, int phase) {
   return e == cudaSuccess ? nb : 0;
 }
 template <int N> cr_status batch_launch(const cr_robot& family, const cr_weights& wts, const BatchArgs& a,
-                                        const BatchGrids& gr, size_t smem, cudaStream_t s) {
+                                        const BatchGrids& gr, size_t smem, int rb_seeds, cudaStream_t s) {
   cr_robot r = family;
   r.n = N;
   const RobotK<float> rb = crh::robot_k<float>(r);
@@ -521,7 +530,10 @@ template <int N> cr_status batch_launch(const cr_robot& family, const cr_weights
   const RobotK<double> rbd = crh::robot_k<double>(r);
   const WeightsK<double> wd = crh::weights_k<double>(wts);
   const unsigned bs = 32 * kBatchWarps;
-  if (gr.g[0] > 0) k_batch_seeds<N><<<gr.g[0], bs, smem, s>>>(rb, w, a);
+  if (gr.g[0] > 0) {
+    if (rb_seeds == 0) k_batch_seeds<N, 0><<<gr.g[0], bs, smem, s>>>(rb, w, a);
+    else k_batch_seeds<N, 1><<<gr.g[0], bs, smem, s>>>(rb, w, a);
+  }
   if (gr.g[1] > 0) k_batch_refine<N><<<gr.g[1], bs, smem, s>>>(rb, w, rbd, wd, a);
   if (gr.g[2] > 0) k_batch_warm<N><<<gr.g[2], bs, smem, s>>>(rb, w, a);
   if (gr.g[3] > 0) k_batch_joint<N><<<gr.g[3], bs, smem, s>>>(rb, w, rbd, wd, a);
@@ -530,8 +542,8 @@ template <int N> cr_status batch_launch(const cr_robot& family, const cr_weights
 
 #define CR_BATCH_INSTANTIATE(EXT, N)                                                                               \
   EXT template cr_status batch_prepare<N>(size_t);                                                                 \
-  EXT template int batch_blocks_per_sm<N>(size_t, int);                                                            \
+  EXT template int batch_blocks_per_sm<N>(size_t, int, int);                                                       \
   EXT template cr_status batch_launch<N>(const cr_robot&, const cr_weights&, const BatchArgs&, const BatchGrids&, \
-                                         size_t, cudaStream_t);
+                                         size_t, int, cudaStream_t);
 
 }  // namespace crk

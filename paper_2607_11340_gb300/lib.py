@@ -100,7 +100,7 @@ class cr_batch_item(C.Structure):
 
 class cr_batch_params(C.Structure):
     _fields_ = [("ik", cr_ik_params), ("k_warm", C.c_int32), ("k_joint", C.c_int32),
-                ("seeds_per_unit", C.c_int32), ("reserved", C.c_int32)]
+                ("seeds_per_unit", C.c_int32), ("seed_regs", C.c_int32)]
 
 
 CR_PRM_MAX_N, CR_PRM_MAX_K, CR_PRM_MAX_CHECK, CR_PRM_MAX_ATTEMPTS = 1024, 32, 64, 8
@@ -165,7 +165,8 @@ _SIGS = {
     "cr_batch_plan_run": [_P, _P],
     "cr_batch_partition": [C.POINTER(cr_batch_item), C.c_int64, C.POINTER(cr_batch_params), C.c_int32,
                            C.POINTER(C.c_int64)],
-    "cr_batch_plan_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+    "cr_batch_plan_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                           C.POINTER(C.c_int32)],
     "cr_batch_plan_destroy": [_P],
     "cr_solve_batch": [C.POINTER(cr_robot), C.POINTER(cr_weights), C.POINTER(cr_batch_item), C.c_int64,
                        C.POINTER(cr_batch_params), _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P],
@@ -498,9 +499,9 @@ def cr_batch_plan_run(plan, stream=None):
 
 
 def cr_batch_plan_info(plan):
-    spu, units, workers = C.c_int32(), C.c_int64(), C.c_int64()
-    _check(load().cr_batch_plan_info(plan, C.byref(spu), C.byref(units), C.byref(workers)))
-    return spu.value, units.value, workers.value
+    spu, units, workers, regs = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int32()
+    _check(load().cr_batch_plan_info(plan, C.byref(spu), C.byref(units), C.byref(workers), C.byref(regs)))
+    return spu.value, units.value, workers.value, regs.value
 
 
 def cr_batch_plan_destroy(plan):

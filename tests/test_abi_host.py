@@ -146,6 +146,11 @@ def test_batch_items_are_validated(crlib):
     assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 2, C.byref(p), *outs, dummy, 1 << 30, None) \
         == crlib.CR_EINVAL
     assert "seeds_per_unit" in crlib.last_error()
+    p.seeds_per_unit, p.seed_regs = 64, 3
+    assert L.cr_solve_batch(C.byref(r), C.byref(w), items, 2, C.byref(p), *outs, dummy, 1 << 30, None) \
+        == crlib.CR_EINVAL
+    assert "seed_regs" in crlib.last_error()
+    p.seed_regs = 0
     assert C.sizeof(crlib.cr_batch_item) == 24
     assert crlib.cr_batch_params.k_warm.offset == C.sizeof(crlib.cr_ik_params)
 
