@@ -690,10 +690,11 @@ template <typename T> CR_HD uint64_t sphere_bits(const ObsK<T>& ob, int j0) {
 // Exact broad-phase test of the primitives among the candidates mask (bits relative to j0) that
 // passed their bounding spheres: sd is 1-Lipschitz, so no point of the ball of radius rad about m
 // comes within reach when sd(m) >= reach + rad (a shelf board, whose bounding sphere is large, then
-// culls like a slab of its own thickness); the margin is the bounding test's. Kept out of line: the
-// sphere-only scenes never call it, and the callers' unrolled loops stay short.
+// culls like a slab of its own thickness); the margin is the bounding test's. Inlined: kernels for
+// scenes without primitives build a view whose primitive pointer is a constant null, and the call
+// folds away there.
 template <typename T>
-__device__ __noinline__ uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T mz, T rad,
+CR_HD uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T mz, T rad,
                                                  T lsum) {
   const T m[3] = {mx, my, mz};
   for (uint64_t b = mask & ~sphere_bits(ob, j0); b; b &= b - 1) {
