@@ -530,7 +530,8 @@ def traj_rows(robot, n_spheres, Tn, weights=None):
 
 def traj_eval(robot, weights, spheres, u_start, goal, x, want=("F",), threads=None):
     """Trajectory cost F [P], gradient g [P][Tn-1][d], residuals r [P][rows].
-    x: free states [P][Tn-1][d]; u_start [P][d]; goal [P][7]; spheres [P][no][4] or None."""
+    x: free states [P][Tn-1][d]; u_start [P][d]; goal [P][7]; spheres [P][no][4], a (spheres, prims) pair
+    with a leading [P] axis on both, or None."""
     x = _f64(x)
     P, Tm1, d = x.shape
     no, sp = _per_problem_spheres(spheres, P)
@@ -755,7 +756,7 @@ def path_rows(robot, n_spheres, H, weights=None):
 
 
 def path_residual(robot, weights, spheres, wp, x, jacobian=False):
-    """One path: spheres [no][4] or None, wp [H][7], x [H][d] -> r (and the full J by complex step)."""
+    """One path: spheres [no][4] (or a (spheres, prims) pair) or None, wp [H][7], x [H][d] -> r (and the full J by complex step)."""
     no, sp = _spheres(spheres)
     x = _f64(x)
     H, d = x.shape
@@ -788,7 +789,7 @@ def path_lm(robot, weights, spheres, wp, x0, iters, lambda0=1e-3, history=False)
 
 
 def solve_path(robot, weights, spheres, wp, ik_cfg: "IkConfig", k_warm, k_joint, threads=None, trace=False):
-    """Path following for P paths: spheres [P][no][4] or None, wp [P][H][7]. With trace, also the
+    """Path following for P paths: spheres [P][no][4] (or a per-problem (spheres, prims) pair) or None, wp [P][H][7]. With trace, also the
     start and trial costs of every LM iteration (the warm sweep waypoint by waypoint, then the joint
     stage) [P][(H-1) k_warm + k_joint][2]."""
     wp = _f64(wp)

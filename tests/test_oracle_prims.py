@@ -217,3 +217,44 @@ def test_acceptance_against_primitives(orc):
     for rec in (through, clear, along):
         flags.append(bool(orc.accept(rb, (None, rec[None, :]), 0, tg, u)[3][0]))
     assert flags == [False, True, False]
+
+
+def test_trajectory_and_path_obstacles_per_problem(orc):
+    """Per-problem obstacle sets in the trajectory and path residuals: the cost with problem p's
+    spheres and primitives, less the cost without obstacles, is the clearance part of the IK cost of
+    the states that carry rows (trajectory states 1..T-1; every waypoint of a path) with that same
+    set, so each problem reads its own records."""
+    spec, rb, W = _setup(orc)
+    rng = np.random.default_rng(9)
+    P, Tn = 3, 5
+    us = synth.hexagon_states(rng, P, 3, spec.umax)
+    x = synth.hexagon_states(rng, P * (Tn - 1), 3, spec.umax).reshape(P, Tn - 1, 9)
+    goal = synth.pose_targets(orc.fk(rb, synth.hexagon_states(rng, P, 3, spec.umax))[0], "pose")
+    _, bb = orc.fk(rb, x.reshape(-1, 9), backbone=True)
+    sph = np.stack([synth.spheres_uniform(rng, 2, [-0.1, -0.1, 0.05], [0.1, 0.1, 0.3], 0.01, 0.03)
+                    for _ in range(P)])
+    prims = np.stack([_prims_near(rng, bb.reshape(P, -1, 3)[p]) for p in range(P)])
+    with_obs = orc.traj_eval(rb, W, (sph, prims), us, goal, x)["F"]
+    without = orc.traj_eval(rb, W, None, us, goal, x)["F"]
+    tg = np.zeros((1, 7))
+    tg[0, 3] = 1.0
+    for p in range(P):
+        coll = orc.ik_eval(rb, W, (sph[p], prims[p]), 0, tg, Tn - 1, x[p], want=("coll",))["coll"]
+        assert coll.sum() > 0
+        assert abs((with_obs[p] - without[p]) - coll.sum()) <= 1e-9 * max(1.0, coll.sum())
+    # paths: the residual rows of waypoint t's IK block with the path's own set
+    wp = np.stack([synth.pose_targets(orc.fk(rb, x[p])[0], "pose") for p in range(P)])
+    for p in range(P):
+        r_obs = orc.path_residual(rb, W, (sph[p], prims[p]), wp[p], x[p])
+        r_none = orc.path_residual(rb, W, None, wp[p], x[p])
+        coll = orc.ik_eval(rb, W, (sph[p], prims[p]), 0, wp[p], 1, x[p], want=("coll",))["coll"]
+        assert abs(0.5 * (r_obs @ r_obs - r_none @ r_none) - coll.sum()) <= 1e-9 * max(1.0, coll.sum())
+
+
+def _prims_near(rng, pts):
+    """A capsule and a box around points of the given backbones (some samples inside the box)."""
+    c = pts[rng.integers(len(pts))]
+    d = pts[rng.integers(len(pts))]
+    q = synth.random_quaternions(rng, 1)[0]
+    return np.stack([synth.capsule_record(c + [0.006, 0.0, 0.0], c + [0.006, 0.02, 0.0], 0.003),
+                     synth.box_record(d, [0.012, 0.008, 0.006], q, 0.002)])
