@@ -675,12 +675,6 @@ CR_HD bool prim_active(const PrimK<T>& P, const T (&x)[3], T reach, T& viol, T (
   return true;
 }
 
-// Broad phase of the clearance rows. Spheres j0 .. j0 + cnt - 1 (cnt <= 64) that may come within reach
-// of some backbone sample of segment i are the set bits of mask[i]. The backbone has unit speed in arc
-// length, so every sample of segment i lies within L_i / 2 of the segment's mid-arc point; a sphere
-// whose centre is farther than L_i / 2 + reach from that point reaches none of them. The margin (a
-// 1e-4 fraction of the magnitudes involved) covers rounding, so a culled pair is one the exact
-// per-sample test rejects as well and the active set is unchanged.
 // The bits of the 64-entry chunk from table entry j0 on that are spheres (the rest are primitives).
 template <typename T> CR_HD uint64_t sphere_bits(const ObsK<T>& ob, int j0) {
   const int cs = ob.ns - j0;
@@ -694,8 +688,7 @@ template <typename T> CR_HD uint64_t sphere_bits(const ObsK<T>& ob, int j0) {
 // scenes without primitives build a view whose primitive pointer is a constant null, and the call
 // folds away there.
 template <typename T>
-CR_HD uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T mz, T rad,
-                                                 T lsum) {
+CR_HD uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T mz, T rad, T lsum) {
   const T m[3] = {mx, my, mz};
   for (uint64_t b = mask & ~sphere_bits(ob, j0); b; b &= b - 1) {
     const int jj = __ffsll((long long)b) - 1;
@@ -713,6 +706,8 @@ CR_HD uint64_t prim_exact_cull(ObsK<T> ob, int j0, uint64_t mask, T mx, T my, T 
 // whose centre is farther than L_i / 2 + reach from that point reaches none of them. The margin (a
 // 1e-4 fraction of the magnitudes involved) covers rounding, so a culled pair is one the exact
 // per-sample test rejects as well and the active set is unchanged.
+// Table entries from ns on are primitives' bounding spheres; one that passes is then tested exactly
+// (prim_exact_cull).
 template <typename T, int N>
 CR_HD void segment_sphere_masks(const RobotK<T>& rb, const Chain<T, N>& ch, ObsK<T> ob, int j0, int cnt,
                                 uint64_t (&mask)[N]) {
